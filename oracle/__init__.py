@@ -1,0 +1,160 @@
+"""CPU oracle for the particle collision and projection operator (arXiv 2501.05340).
+
+TEST INFRASTRUCTURE ONLY. Plain FP64 C (``oracle.c``) behind ctypes. Only the
+tests, ``__graft_entry__.smoke()`` and the benchmark's CPU-baseline leg may load
+it; the library under ``paper_2501_05340_gb300`` never does and shares no code
+with it. Arrays are numpy, SoA ``[3][n]`` / ``[4][n]``, in the caller's order.
+"""
+import ctypes
+import os
+import subprocess
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "oracle.c")
+_LIB = os.path.join(_HERE, "liboracle.so")
+_lib = None
+
+
+def build(force=False):
+    """Compile ``liboracle.so`` next to the source (strict IEEE: no FP contraction)."""
+    if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < max(
+            os.path.getmtime(_SRC), os.path.getmtime(os.path.join(_HERE, "oracle.h"))):
+        tmp = _LIB + ".tmp%d" % os.getpid()
+        subprocess.check_call(["gcc", "-O2", "-ffp-contract=off", "-fno-fast-math", "-fPIC", "-shared",
+                               "-o", tmp, _SRC, "-lm"])
+        os.replace(tmp, _LIB)
+    return _LIB
+
+
+def _load():
+    global _lib
+    if _lib is None:
+        build()
+        lib = ctypes.CDLL(_LIB)
+        P = ctypes.c_void_p
+        i64, i32, d = ctypes.c_int64, ctypes.c_int, ctypes.c_double
+        lib.or_gauss_legendre.argtypes = [i32, P, P]
+        lib.or_contact_time.argtypes = [P, P, P, P, d, d, d]
+        lib.or_contact_time.restype = d
+        for f in (lib.or_candidates_bruteforce, lib.or_candidates_cells):
+            f.argtypes = [i64, P, P, P, d, i64, P, P, P]
+            f.restype = i64
+        lib.or_match_greedy.argtypes = [i64, P, i64, P, P, P, P, P]
+        lib.or_match_greedy.restype = i64
+        lib.or_match_rounds.argtypes = [i64, P, i64, P, P, P, P, P, P]
+        lib.or_match_rounds.restype = i64
+        lib.or_respond_advance.argtypes = [i64, P, P, P, P, P, d, d]
+        lib.or_respond_advance.restype = None
+        lib.or_collide_step.argtypes = [i64, P, P, P, P, P, d, d, i32, P, P]
+        lib.or_collide_step.restype = i64
+        lib.or_mesh_map.argtypes = [P, d, P, P]
+        lib.or_mesh_map.restype = None
+        lib.or_project.argtypes = [i64, P, P, i32, i32, d, d, i32, d, P, P]
+        lib.or_project.restype = i32
+        _lib = lib
+    return _lib
+
+
+def _p(a):
+    return a.ctypes.data_as(ctypes.c_void_p)
+
+
+def _f64(a):
+    return np.ascontiguousarray(a, dtype=np.float64)
+
+
+def gauss_legendre(n1):
+    """Legendre-Gauss nodes (ascending) and weights on [-1, 1]."""
+    eta, w = np.zeros(n1), np.zeros(n1)
+    if _load().or_gauss_legendre(n1, _p(eta), _p(w)):
+        raise ValueError("bad n1")
+    return eta, w
+
+
+def contact_time(xi, xj, vi, vj, ri, rj, dt):
+    """Smaller positive root of |dx + t dv| = ri + rj if it is a candidate, else inf."""
+    a = [_f64(u) for u in (xi, xj, vi, vj)]
+    return _load().or_contact_time(*[_p(u) for u in a], float(ri), float(rj), float(dt))
+
+
+def candidates(x, v, r, dt, method="cells"):
+    """Candidate pairs (i<j, input indices) and their contact times, sorted by (i, j)."""
+    x, v, r = _f64(x), _f64(v), _f64(r)
+    n = r.shape[0]
+    f = _load().or_candidates_cells if method == "cells" else _load().or_candidates_bruteforce
+    cap = max(64, 4 * n)
+    while True:
+        ci, cj = np.zeros(cap, np.int64), np.zeros(cap, np.int64)
+        ct = np.zeros(cap)
+        cnt = f(n, _p(x), _p(v), _p(r), float(dt), cap, _p(ci), _p(cj), _p(ct))
+        if cnt < 0:
+            raise MemoryError("oracle candidates")
+        if cnt <= cap:
+            break
+        cap = cnt
+    ci, cj, ct = ci[:cnt], cj[:cnt], ct[:cnt]
+    o = np.lexsort((cj, ci))
+    return ci[o], cj[o], ct[o]
+
+
+def match(ids, ci, cj, ct, n, method="greedy"):
+    """Matching of a candidate list: returns (partner, tc, npairs[, rounds])."""
+    ids = np.ascontiguousarray(ids, dtype=np.int32)
+    ci, cj = np.ascontiguousarray(ci, np.int64), np.ascontiguousarray(cj, np.int64)
+    ct = _f64(ct)
+    partner, tc = np.zeros(n, np.int64), np.zeros(n)
+    lib = _load()
+    if method == "greedy":
+        k = lib.or_match_greedy(n, _p(ids), len(ci), _p(ci), _p(cj), _p(ct), _p(partner), _p(tc))
+        return partner, tc, k
+    rounds = np.zeros(1, np.int64)
+    k = lib.or_match_rounds(n, _p(ids), len(ci), _p(ci), _p(cj), _p(ct), _p(partner), _p(tc), _p(rounds))
+    return partner, tc, k, int(rounds[0])
+
+
+def respond_advance(x, v, m, partner, tc, e, dt):
+    """Response of committed pairs + free flight + wrap; returns new (x, v)."""
+    x, v = _f64(x).copy(), _f64(v).copy()
+    m = _f64(m)
+    partner = np.ascontiguousarray(partner, np.int64)
+    tc = _f64(tc)
+    _load().or_respond_advance(m.shape[0], _p(x), _p(v), _p(m), _p(partner), _p(tc), float(e), float(dt))
+    return x, v
+
+
+def collide_step(x, v, r, m, ids, e, dt, method="cells"):
+    """One collision step in the input order; returns (x', v', partner, tc, npairs)."""
+    x, v = _f64(x).copy(), _f64(v).copy()
+    r, m = _f64(r), _f64(m)
+    ids = np.ascontiguousarray(ids, np.int32)
+    n = r.shape[0]
+    partner, tc = np.zeros(n, np.int64), np.zeros(n)
+    k = _load().or_collide_step(n, _p(x), _p(v), _p(r), _p(m), _p(ids), float(e), float(dt),
+                                1 if method == "bruteforce" else 0, _p(partner), _p(tc))
+    if k < 0:
+        raise MemoryError("oracle collide")
+    return x, v, partner, tc, k
+
+
+def mesh_map(xi, amp):
+    """Curved periodic mapping of one logical point: (X, det J)."""
+    xi = _f64(xi)
+    X, dj = np.zeros(3), np.zeros(1)
+    _load().or_mesh_map(_p(xi), float(amp), _p(X), _p(dj))
+    return X, float(dj[0])
+
+
+def project(x, q, ne, degree, sigma, cutoff_sigmas=3.0, cutoff="box", amp=0.0):
+    """Field [ne^3][4][n1^3] and normalisation Z[n] of the Gaussian deposition."""
+    x, q = _f64(x), _f64(q)
+    n = x.shape[-1]
+    n1 = degree + 1
+    field = np.zeros((ne ** 3, 4, n1 ** 3))
+    Z = np.zeros(n)
+    rc = _load().or_project(n, _p(x), _p(q), ne, degree, float(sigma), float(cutoff_sigmas),
+                            0 if cutoff == "box" else 1, float(amp), _p(field), _p(Z))
+    if rc:
+        raise ValueError("or_project failed (%d)" % rc)
+    return field, Z

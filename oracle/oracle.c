@@ -1,0 +1,534 @@
+/*
+ * CPU oracle for the particle collision and projection operator
+ * (arXiv 2501.05340). TEST INFRASTRUCTURE ONLY: tests, the smoke check and the
+ * benchmark's CPU baseline load it; the product path never does.
+ *
+ * Plain FP64 C, compiled with -O2 -ffp-contract=off -fno-fast-math so that
+ * every + - * / sqrt below is one IEEE double operation in the written order.
+ * Function-by-function citations:
+ *   or_gauss_legendre      Sec. 3.1 (Legendre-Gauss points of the DGSEM)
+ *   or_contact_time        Sec. 3.3, Eqs. collision-detect 1-2 and the rules after them
+ *   or_candidates_*        Sec. 4.3 (halo criterion |d| <= d_max + r + r')
+ *   or_match_*             Sec. 4.3 (one collision per particle per step)
+ *   or_respond_advance     Sec. 2.4 (J_n = -m_r (1+e) v_r.n, frictionless), Sec. 3.3 update
+ *   or_project             Sec. 2.3 / 4.2 (deposition operator P, Gaussian shape function)
+ * Readings where the paper is silent or garbled are listed at each function.
+ */
+#include "oracle.h"
+
+#include <math.h>
+#include <stdlib.h>
+#include <string.h>
+
+/* ------------------------------------------------------------------ Gauss */
+
+/* Legendre polynomial P_n(x) and P_{n-1}(x) by the three-term recurrence
+ * (k+1) P_{k+1} = (2k+1) x P_k - k P_{k-1}. */
+static void legendre(int n, double x, double* pn, double* pn1) {
+  double p0 = 1.0, p1 = x;
+  if (n == 0) { *pn = 1.0; *pn1 = 0.0; return; }
+  for (int k = 1; k < n; ++k) {
+    double p2 = ((2.0 * k + 1.0) * x * p1 - k * p0) / (k + 1.0);
+    p0 = p1;
+    p1 = p2;
+  }
+  *pn = p1;
+  *pn1 = p0;
+}
+
+int or_gauss_legendre(int n1, double* eta, double* w) {
+  if (n1 < 1 || n1 > 64 || !eta || !w) return 1;
+  const double pi = 3.14159265358979323846;
+  for (int i = 0; i < n1; ++i) {
+    /* initial guess near the i-th largest root, then Newton on P_n */
+    double x = cos(pi * (i + 0.75) / (n1 + 0.5));
+    double pn = 0, pn1 = 0, dp = 0;
+    for (int it = 0; it < 100; ++it) {
+      legendre(n1, x, &pn, &pn1);
+      dp = n1 * (x * pn - pn1) / (x * x - 1.0);
+      double dx = pn / dp;
+      x -= dx;
+      if (fabs(dx) < 1e-17) break;
+    }
+    legendre(n1, x, &pn, &pn1);
+    dp = n1 * (x * pn - pn1) / (x * x - 1.0);
+    eta[n1 - 1 - i] = x; /* ascending order */
+    w[n1 - 1 - i] = 2.0 / ((1.0 - x * x) * dp * dp);
+  }
+  if (n1 % 2 == 1) eta[n1 / 2] = 0.0; /* the middle root is exactly zero */
+  return 0;
+}
+
+/* ------------------------------------------------------------------ contact */
+
+/* Periodic minimum image of a coordinate difference of two points in [0,1). */
+static double minimg(double d) {
+  if (d > 0.5) return d - 1.0;
+  if (d < -0.5) return d + 1.0;
+  return d;
+}
+
+/* Reading of the garbled Eq. collision-detect 2: dx_p = x_1 - x_2 and
+ * dv_p = v_1 - v_2. With a = dv.dv, b = dx.dv, c = dx.dx - R^2 the roots of
+ * a t^2 + 2 b t + c = 0 are both positive iff c > 0 and b < 0 (this is also the
+ * "particles approach" rule), real and distinct iff b^2 - a c > 0 (a grazing
+ * double root carries no normal velocity). The smaller root is written as
+ * c / (-b + sqrt(b^2 - a c)), the cancellation-free form of (-b - sqrt(.))/a.
+ * The root must satisfy t <= dt (inclusive). */
+double or_contact_time(const double xi[3], const double xj[3], const double vi[3], const double vj[3],
+                       double ri, double rj, double dt) {
+  double dx0 = minimg(xi[0] - xj[0]);
+  double dx1 = minimg(xi[1] - xj[1]);
+  double dx2 = minimg(xi[2] - xj[2]);
+  double dv0 = vi[0] - vj[0];
+  double dv1 = vi[1] - vj[1];
+  double dv2 = vi[2] - vj[2];
+  double R = ri + rj;
+  double a = (dv0 * dv0 + dv1 * dv1) + dv2 * dv2;
+  double b = (dx0 * dv0 + dx1 * dv1) + dx2 * dv2;
+  double c = ((dx0 * dx0 + dx1 * dx1) + dx2 * dx2) - R * R;
+  if (!(b < 0.0)) return INFINITY;
+  if (!(c > 0.0)) return INFINITY;
+  double disc = b * b - a * c;
+  if (!(disc > 0.0)) return INFINITY;
+  double t = c / (-b + sqrt(disc));
+  if (t <= dt) return t;
+  return INFINITY;
+}
+
+static void load3(const double* a, int64_t n, int64_t i, double out[3]) {
+  out[0] = a[i];
+  out[1] = a[n + i];
+  out[2] = a[2 * n + i];
+}
+
+int64_t or_candidates_bruteforce(int64_t n, const double* x, const double* v, const double* r, double dt,
+                                 int64_t cap, int64_t* ci, int64_t* cj, double* ct) {
+  int64_t cnt = 0;
+  for (int64_t i = 0; i < n; ++i) {
+    double xi[3], vi[3];
+    load3(x, n, i, xi);
+    load3(v, n, i, vi);
+    for (int64_t j = i + 1; j < n; ++j) {
+      double xj[3], vj[3];
+      load3(x, n, j, xj);
+      load3(v, n, j, vj);
+      double t = or_contact_time(xi, xj, vi, vj, r[i], r[j], dt);
+      if (t <= dt) {
+        if (cnt < cap) { ci[cnt] = i; cj[cnt] = j; ct[cnt] = t; }
+        ++cnt;
+      }
+    }
+  }
+  return cnt;
+}
+
+static int64_t cell_of(double y, int64_t nc) {
+  int64_t c = (int64_t)floor(y * (double)nc);
+  if (c < 0) c = 0;
+  if (c >= nc) c = nc - 1;
+  return c;
+}
+
+int64_t or_candidates_cells(int64_t n, const double* x, const double* v, const double* r, double dt,
+                            int64_t cap, int64_t* ci, int64_t* cj, double* ct) {
+  /* Any pair with a root t <= dt starts within R + |dv| dt <= 2 r_max + 2 v_max dt
+   * of each other (Sec. 4.3: d_max from the fastest particle and the time step). */
+  double rmax = 0.0, v2max = 0.0;
+  for (int64_t i = 0; i < n; ++i) {
+    if (r[i] > rmax) rmax = r[i];
+    double s = v[i] * v[i] + v[n + i] * v[n + i] + v[2 * n + i] * v[2 * n + i];
+    if (s > v2max) v2max = s;
+  }
+  double reach = (2.0 * rmax + 2.0 * sqrt(v2max) * dt) * (1.0 + 1e-9) + 1e-12;
+  int64_t nc = (int64_t)floor(1.0 / reach);
+  if (nc > 1024) nc = 1024;
+  if (nc < 3) return or_candidates_bruteforce(n, x, v, r, dt, cap, ci, cj, ct);
+  int64_t ncell = nc * nc * nc;
+  int64_t* head = (int64_t*)malloc(sizeof(int64_t) * (size_t)ncell);
+  int64_t* next = (int64_t*)malloc(sizeof(int64_t) * (size_t)(n > 0 ? n : 1));
+  int64_t* cell = (int64_t*)malloc(sizeof(int64_t) * (size_t)(n > 0 ? n : 1));
+  if (!head || !next || !cell) { free(head); free(next); free(cell); return -1; }
+  for (int64_t c = 0; c < ncell; ++c) head[c] = -1;
+  for (int64_t i = n - 1; i >= 0; --i) {
+    int64_t c = (cell_of(x[2 * n + i], nc) * nc + cell_of(x[n + i], nc)) * nc + cell_of(x[i], nc);
+    cell[i] = c;
+    next[i] = head[c];
+    head[c] = i;
+  }
+  int64_t cnt = 0;
+  for (int64_t i = 0; i < n; ++i) {
+    int64_t cx = cell[i] % nc, cy = (cell[i] / nc) % nc, cz = cell[i] / (nc * nc);
+    double xi[3], vi[3];
+    load3(x, n, i, xi);
+    load3(v, n, i, vi);
+    for (int64_t dz = -1; dz <= 1; ++dz)
+      for (int64_t dy = -1; dy <= 1; ++dy)
+        for (int64_t dx = -1; dx <= 1; ++dx) {
+          int64_t c = (((cz + dz + nc) % nc) * nc + (cy + dy + nc) % nc) * nc + (cx + dx + nc) % nc;
+          for (int64_t j = head[c]; j >= 0; j = next[j]) {
+            if (j <= i) continue;
+            double xj[3], vj[3];
+            load3(x, n, j, xj);
+            load3(v, n, j, vj);
+            double t = or_contact_time(xi, xj, vi, vj, r[i], r[j], dt);
+            if (t <= dt) {
+              if (cnt < cap) { ci[cnt] = i; cj[cnt] = j; ct[cnt] = t; }
+              ++cnt;
+            }
+          }
+        }
+  }
+  free(head);
+  free(next);
+  free(cell);
+  return cnt;
+}
+
+/* ------------------------------------------------------------------ matching */
+
+typedef struct {
+  double t;
+  int32_t lo, hi; /* ids, lo < hi */
+  int64_t i, j;   /* indices */
+} edge_t;
+
+static int edge_cmp(const void* pa, const void* pb) {
+  const edge_t* a = (const edge_t*)pa;
+  const edge_t* b = (const edge_t*)pb;
+  if (a->t < b->t) return -1;
+  if (a->t > b->t) return 1;
+  if (a->lo != b->lo) return a->lo < b->lo ? -1 : 1;
+  if (a->hi != b->hi) return a->hi < b->hi ? -1 : 1;
+  return 0;
+}
+
+/* Reading: the paper commits the first valid pair found in its deterministic
+ * element order and removes both particles from further tests. Here the order
+ * is the earliest contact first, ties broken by (smaller id, larger id). */
+int64_t or_match_greedy(int64_t n, const int32_t* id, int64_t ncand, const int64_t* ci, const int64_t* cj,
+                        const double* ct, int64_t* partner, double* tc) {
+  for (int64_t i = 0; i < n; ++i) { partner[i] = -1; tc[i] = INFINITY; }
+  edge_t* e = (edge_t*)malloc(sizeof(edge_t) * (size_t)(ncand > 0 ? ncand : 1));
+  if (!e) return -1;
+  for (int64_t k = 0; k < ncand; ++k) {
+    int32_t a = id[ci[k]], b = id[cj[k]];
+    e[k].t = ct[k];
+    e[k].lo = a < b ? a : b;
+    e[k].hi = a < b ? b : a;
+    e[k].i = ci[k];
+    e[k].j = cj[k];
+  }
+  qsort(e, (size_t)ncand, sizeof(edge_t), edge_cmp);
+  int64_t pairs = 0;
+  for (int64_t k = 0; k < ncand; ++k) {
+    if (partner[e[k].i] < 0 && partner[e[k].j] < 0) {
+      partner[e[k].i] = e[k].j;
+      partner[e[k].j] = e[k].i;
+      tc[e[k].i] = e[k].t;
+      tc[e[k].j] = e[k].t;
+      ++pairs;
+    }
+  }
+  free(e);
+  return pairs;
+}
+
+/* (t, id of other) order seen from one endpoint. */
+static int better(double t1, int32_t id1, double t2, int32_t id2) {
+  if (t1 < t2) return 1;
+  if (t1 > t2) return 0;
+  return id1 < id2;
+}
+
+int64_t or_match_rounds(int64_t n, const int32_t* id, int64_t ncand, const int64_t* ci, const int64_t* cj,
+                        const double* ct, int64_t* partner, double* tc, int64_t* rounds) {
+  for (int64_t i = 0; i < n; ++i) { partner[i] = -1; tc[i] = INFINITY; }
+  /* adjacency lists (CSR) of the candidate graph */
+  int64_t* deg = (int64_t*)calloc((size_t)n + 1, sizeof(int64_t));
+  int64_t* adj = (int64_t*)malloc(sizeof(int64_t) * (size_t)(2 * ncand + 1));
+  int64_t* fill = (int64_t*)calloc((size_t)n + 1, sizeof(int64_t));
+  int64_t* best = (int64_t*)malloc(sizeof(int64_t) * (size_t)(n > 0 ? n : 1));
+  if (!deg || !adj || !fill || !best) { free(deg); free(adj); free(fill); free(best); return -1; }
+  for (int64_t k = 0; k < ncand; ++k) { deg[ci[k] + 1]++; deg[cj[k] + 1]++; }
+  for (int64_t i = 0; i < n; ++i) deg[i + 1] += deg[i];
+  for (int64_t k = 0; k < ncand; ++k) {
+    adj[deg[ci[k]] + fill[ci[k]]++] = k;
+    adj[deg[cj[k]] + fill[cj[k]]++] = k;
+  }
+  int64_t pairs = 0, nr = 0;
+  for (;;) {
+    int any = 0;
+    for (int64_t i = 0; i < n; ++i) {
+      best[i] = -1;
+      if (partner[i] >= 0) continue;
+      double bt = INFINITY;
+      int32_t bid = 0;
+      for (int64_t a = deg[i]; a < deg[i + 1]; ++a) {
+        int64_t k = adj[a];
+        int64_t o = ci[k] == i ? cj[k] : ci[k];
+        if (partner[o] >= 0) continue;
+        if (best[i] < 0 || better(ct[k], id[o], bt, bid)) { best[i] = o; bt = ct[k]; bid = id[o]; }
+      }
+      if (best[i] >= 0) any = 1;
+    }
+    if (!any) break;
+    int64_t committed = 0;
+    for (int64_t i = 0; i < n; ++i) {
+      int64_t j = best[i];
+      if (j > i && best[j] == i) {
+        partner[i] = j;
+        partner[j] = i;
+        /* the edge's contact time */
+        for (int64_t a = deg[i]; a < deg[i + 1]; ++a) {
+          int64_t k = adj[a];
+          if ((ci[k] == i && cj[k] == j) || (ci[k] == j && cj[k] == i)) { tc[i] = tc[j] = ct[k]; break; }
+        }
+        ++committed;
+      }
+    }
+    ++nr;
+    pairs += committed;
+    if (committed == 0) break; /* cannot happen for a strict total order; guards the loop */
+  }
+  if (rounds) *rounds = nr;
+  free(deg);
+  free(adj);
+  free(fill);
+  free(best);
+  return pairs;
+}
+
+/* ------------------------------------------------------------------ response */
+
+/* y - floor(y) lies in [0,1]; a tiny negative y rounds it to exactly 1.0, which
+ * is mapped back to 0.0 so that every coordinate stays in [0,1). */
+static double wrap01(double y) {
+  double w = y - floor(y);
+  if (w == 1.0) w = 0.0;
+  return w;
+}
+
+/* Frictionless hard-sphere response. With s = dx + t dv the contact vector
+ * (from particle j to particle i, dx = minimg(x_i - x_j), dv = v_i - v_j),
+ * n = -s/|s| is the unit normal from i to j (Sec. 2.4: "from particle 1 to
+ * particle 2"). v_r = v_i - v_j, m_r = m_i m_j/(m_i + m_j),
+ * J = -m_r (1 + e) (v_r . n), v_i' = v_i + (J/m_i) n, v_j' = v_j - (J/m_j) n.
+ * Reading of the garbled position update of Sec. 3.3: the particle moves with
+ * its old velocity to the contact point and with its new one for the rest of
+ * the step, x' = x + t v + (dt - t) v'. Free particles: x' = x + dt v. */
+void or_respond_advance(int64_t n, double* x, double* v, const double* m, const int64_t* partner,
+                        const double* tc, double e, double dt) {
+  double* xn = (double*)malloc(sizeof(double) * (size_t)(3 * n > 0 ? 3 * n : 1));
+  double* vn = (double*)malloc(sizeof(double) * (size_t)(3 * n > 0 ? 3 * n : 1));
+  if (!xn || !vn) { free(xn); free(vn); return; }
+  for (int64_t i = 0; i < n; ++i) {
+    int64_t j = partner[i];
+    if (j < 0) {
+      for (int k = 0; k < 3; ++k) {
+        vn[k * n + i] = v[k * n + i];
+        xn[k * n + i] = x[k * n + i] + dt * v[k * n + i];
+      }
+      continue;
+    }
+    double t = tc[i];
+    double dx[3], dv[3], s[3], nrm[3];
+    for (int k = 0; k < 3; ++k) {
+      dx[k] = minimg(x[k * n + i] - x[k * n + j]);
+      dv[k] = v[k * n + i] - v[k * n + j];
+    }
+    for (int k = 0; k < 3; ++k) s[k] = dx[k] + t * dv[k];
+    double sl = sqrt((s[0] * s[0] + s[1] * s[1]) + s[2] * s[2]);
+    for (int k = 0; k < 3; ++k) nrm[k] = -s[k] / sl;
+    double vrn = (dv[0] * nrm[0] + dv[1] * nrm[1]) + dv[2] * nrm[2];
+    double mr = (m[i] * m[j]) / (m[i] + m[j]);
+    double J = -mr * (1.0 + e) * vrn;
+    double gi = J / m[i];
+    for (int k = 0; k < 3; ++k) {
+      double vold = v[k * n + i];
+      double vnew = vold + gi * nrm[k];
+      vn[k * n + i] = vnew;
+      xn[k * n + i] = (x[k * n + i] + t * vold) + (dt - t) * vnew;
+    }
+  }
+  for (int64_t a = 0; a < 3 * n; ++a) {
+    v[a] = vn[a];
+    x[a] = wrap01(xn[a]);
+  }
+  free(xn);
+  free(vn);
+}
+
+int64_t or_collide_step(int64_t n, double* x, double* v, const double* r, const double* m, const int32_t* id,
+                        double e, double dt, int method, int64_t* partner, double* tc) {
+  int64_t cap = n > 16 ? 4 * n : 64;
+  for (;;) {
+    int64_t* ci = (int64_t*)malloc(sizeof(int64_t) * (size_t)cap);
+    int64_t* cj = (int64_t*)malloc(sizeof(int64_t) * (size_t)cap);
+    double* ct = (double*)malloc(sizeof(double) * (size_t)cap);
+    if (!ci || !cj || !ct) { free(ci); free(cj); free(ct); return -1; }
+    int64_t nc = method == 1 ? or_candidates_bruteforce(n, x, v, r, dt, cap, ci, cj, ct)
+                             : or_candidates_cells(n, x, v, r, dt, cap, ci, cj, ct);
+    if (nc < 0) { free(ci); free(cj); free(ct); return -1; }
+    if (nc > cap) { free(ci); free(cj); free(ct); cap = nc; continue; }
+    int64_t pairs = or_match_greedy(n, id, nc, ci, cj, ct, partner, tc);
+    free(ci);
+    free(cj);
+    free(ct);
+    if (pairs < 0) return -1;
+    or_respond_advance(n, x, v, m, partner, tc, e, dt);
+    return pairs;
+  }
+}
+
+/* ------------------------------------------------------------------ projection */
+
+void or_mesh_map(const double xi[3], double amp, double X[3], double* detJ) {
+  const double tp = 6.283185307179586476925286766559;
+  double s[3], c[3];
+  for (int k = 0; k < 3; ++k) { s[k] = sin(tp * xi[k]); c[k] = cos(tp * xi[k]); }
+  X[0] = xi[0] + amp * s[1] * s[2];
+  X[1] = xi[1] + amp * s[2] * s[0];
+  X[2] = xi[2] + amp * s[0] * s[1];
+  /* D Phi = I + amp*2pi*[[0, c1 s2, s1 c2], [c0 s2, 0, s0 c2], [c0 s1, s0 c1, 0]] */
+  double g = amp * tp;
+  double A[3][3] = {{1.0, g * c[1] * s[2], g * s[1] * c[2]},
+                    {g * c[0] * s[2], 1.0, g * s[0] * c[2]},
+                    {g * c[0] * s[1], g * s[0] * c[1], 1.0}};
+  *detJ = A[0][0] * (A[1][1] * A[2][2] - A[1][2] * A[2][1]) - A[0][1] * (A[1][0] * A[2][2] - A[1][2] * A[2][0]) +
+          A[0][2] * (A[1][0] * A[2][1] - A[1][1] * A[2][0]);
+}
+
+/* Neumaier's improvement of Kahan summation: s + c carries the running sum. */
+static void neu_add(double* s, double* c, double t) {
+  double u = *s + t;
+  if (fabs(*s) >= fabs(t))
+    *c += (*s - u) + t;
+  else
+    *c += (t - u) + *s;
+  *s = u;
+}
+
+/* 1-D node indices (e*n1 + i) whose logical coordinate lies within `rad` of y
+ * in the periodic minimum image; a plain scan over all ne*n1 1-D nodes. */
+static int near_nodes(double y, double rad, int ne, int n1, const double* eta, int* out) {
+  int cnt = 0;
+  double h = 1.0 / ne;
+  for (int e = 0; e < ne; ++e)
+    for (int i = 0; i < n1; ++i) {
+      double X = (e + 0.5 * (eta[i] + 1.0)) * h;
+      if (fabs(minimg(X - y)) <= rad) out[cnt++] = e * n1 + i;
+    }
+  return cnt;
+}
+
+/* Visit every Gauss node within the cutoff of particle xp: pass 0 adds
+ * W_g K(X_g - xp) to the Neumaier pair (zs, zc); pass 1 adds q_c K / zp to
+ * node g of every component c. */
+typedef struct {
+  int ne, n1;
+  int64_t nodes;
+  double h, rc, inv2s2, amp;
+  int cutoff_kind;
+  const double *eta, *w;
+  int *lx, *ly, *lz;
+  double* field;
+  double* comp;
+} proj_ctx;
+
+static void visit_support(const proj_ctx* P, const double xp[3], int pass, double* zs, double* zc, double zp,
+                          const double qc[4]) {
+  int n1 = P->n1, ne = P->ne;
+  double rad = P->rc + fabs(P->amp);
+  int nx = near_nodes(xp[0], rad, ne, n1, P->eta, P->lx);
+  int ny = near_nodes(xp[1], rad, ne, n1, P->eta, P->ly);
+  int nz = near_nodes(xp[2], rad, ne, n1, P->eta, P->lz);
+  double hh = 0.5 * P->h;
+  for (int c3 = 0; c3 < nz; ++c3)
+    for (int b3 = 0; b3 < ny; ++b3)
+      for (int a3 = 0; a3 < nx; ++a3) {
+        int gx = P->lx[a3], gy = P->ly[b3], gz = P->lz[c3];
+        int ex = gx / n1, i = gx % n1, ey = gy / n1, j = gy % n1, ez = gz / n1, k = gz % n1;
+        double xi[3] = {(ex + 0.5 * (P->eta[i] + 1.0)) * P->h, (ey + 0.5 * (P->eta[j] + 1.0)) * P->h,
+                        (ez + 0.5 * (P->eta[k] + 1.0)) * P->h};
+        double X[3], detJ = 1.0;
+        if (P->amp != 0.0) {
+          or_mesh_map(xi, P->amp, X, &detJ);
+        } else {
+          X[0] = xi[0];
+          X[1] = xi[1];
+          X[2] = xi[2];
+        }
+        double d0 = minimg(X[0] - xp[0]), d1 = minimg(X[1] - xp[1]), d2 = minimg(X[2] - xp[2]);
+        double d2s = (d0 * d0 + d1 * d1) + d2 * d2;
+        if (P->cutoff_kind == 0) {
+          if (!(fabs(d0) <= P->rc && fabs(d1) <= P->rc && fabs(d2) <= P->rc)) continue;
+        } else {
+          if (!(d2s <= P->rc * P->rc)) continue;
+        }
+        double K = exp(-d2s * P->inv2s2);
+        if (pass == 0) {
+          double W = P->w[i] * P->w[j] * P->w[k] * hh * hh * hh * detJ;
+          neu_add(zs, zc, W * K);
+        } else {
+          double wk = K / zp;
+          int64_t e = ((int64_t)ez * ne + ey) * ne + ex;
+          int64_t base = e * 4 * P->nodes + ((int64_t)k * n1 + j) * n1 + i;
+          for (int cc = 0; cc < 4; ++cc) {
+            int64_t g = base + (int64_t)cc * P->nodes;
+            neu_add(&P->field[g], &P->comp[g], qc[cc] * wk);
+          }
+        }
+      }
+}
+
+/* Reading: the kernel K(d) = exp(-|d|^2/(2 sigma^2)) is cut at cutoff_sigmas*sigma
+ * (box or sphere, inclusive); the discrete normalisation Z_p makes each particle's
+ * quadrature-weighted deposit sum to its source, the Gaussian counterpart of the
+ * denominator of the IDW deposition in Sec. 2.3. */
+int or_project(int64_t n, const double* x, const double* q, int ne, int degree, double sigma, double cutoff_sigmas,
+               int cutoff_kind, double amp, double* field, double* Z) {
+  if (n < 0 || ne < 1 || degree < 0 || degree > 15 || !(sigma > 0.0) || !(cutoff_sigmas > 0.0)) return 1;
+  if (cutoff_kind != 0 && cutoff_kind != 1) return 1;
+  if (amp != 0.0 && cutoff_kind != 1) return 1;
+  int n1 = degree + 1;
+  double eta[16], w[16];
+  if (or_gauss_legendre(n1, eta, w)) return 1;
+  proj_ctx P;
+  P.ne = ne;
+  P.n1 = n1;
+  P.nodes = (int64_t)n1 * n1 * n1;
+  P.h = 1.0 / ne;
+  P.rc = cutoff_sigmas * sigma;
+  P.inv2s2 = 1.0 / (2.0 * sigma * sigma);
+  P.amp = amp;
+  P.cutoff_kind = cutoff_kind;
+  P.eta = eta;
+  P.w = w;
+  int64_t nf = (int64_t)ne * ne * ne * 4 * P.nodes;
+  P.lx = (int*)malloc(sizeof(int) * (size_t)(ne * n1));
+  P.ly = (int*)malloc(sizeof(int) * (size_t)(ne * n1));
+  P.lz = (int*)malloc(sizeof(int) * (size_t)(ne * n1));
+  P.comp = (double*)calloc((size_t)nf, sizeof(double));
+  P.field = field;
+  if (!P.lx || !P.ly || !P.lz || !P.comp) {
+    free(P.lx); free(P.ly); free(P.lz); free(P.comp);
+    return 2;
+  }
+  for (int64_t a = 0; a < nf; ++a) field[a] = 0.0;
+  for (int64_t p = 0; p < n; ++p) {
+    double xp[3] = {x[p], x[n + p], x[2 * n + p]};
+    double qc[4] = {q[p], q[n + p], q[2 * n + p], q[3 * n + p]};
+    double zs = 0.0, zc = 0.0;
+    visit_support(&P, xp, 0, &zs, &zc, 0.0, qc);
+    double zp = zs + zc;
+    if (Z) Z[p] = zp;
+    if (zp > 0.0) visit_support(&P, xp, 1, NULL, NULL, zp, qc);
+  }
+  for (int64_t a = 0; a < nf; ++a) field[a] += P.comp[a];
+  free(P.lx);
+  free(P.ly);
+  free(P.lz);
+  free(P.comp);
+  return 0;
+}

@@ -1,0 +1,90 @@
+/*
+ * CPU oracle for the particle collision and projection operator of
+ * Schwarz, Kopper, de Staercke, Beck, "Efficient computation of particle-fluid and
+ * particle-particle interactions in compressible flow" (arXiv 2501.05340).
+ *
+ * TEST INFRASTRUCTURE ONLY. Plain, slow, FP64 C code that states what the GPU
+ * path must compute. Only the tests, the smoke check and the benchmark's CPU
+ * baseline may load it. It shares no code with the CUDA library.
+ *
+ * Layouts: per-particle vectors are SoA, x[3][n] means x[0..n) are the first
+ * coordinates, x[n..2n) the second, x[2n..3n) the third. The domain is the
+ * periodic unit cube [0,1)^3. Fields are field[elem][comp][k][j][i] with
+ * elem = (ez*ne + ey)*ne + ex and i the fastest node index.
+ */
+#ifndef PC_ORACLE_H
+#define PC_ORACLE_H
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* Legendre-Gauss nodes eta[0..n1) (ascending) and weights w[0..n1) on [-1,1]
+ * (Sec. 3.1: (N+1)^3 Legendre-Gauss points per element). Returns 0 on success. */
+int or_gauss_legendre(int n1, double* eta, double* w);
+
+/* Contact time of one pair (Sec. 3.3, Eq. collision-detect): the smaller root of
+ * |dx + t dv| = r_i + r_j with dx = minimg(x_i - x_j), dv = v_i - v_j, if both
+ * roots are positive, the particles approach, and the root is <= dt.
+ * Returns the root, or +infinity when the pair is not a candidate. */
+double or_contact_time(const double xi[3], const double xj[3], const double vi[3], const double vj[3],
+                       double ri, double rj, double dt);
+
+/* All candidate pairs (i<j, input index) by testing every pair. Writes at most
+ * cap entries; returns the number of candidates found (may exceed cap). */
+int64_t or_candidates_bruteforce(int64_t n, const double* x, const double* v, const double* r, double dt,
+                                 int64_t cap, int64_t* ci, int64_t* cj, double* ct);
+
+/* Same set via a cell list whose side is at least the largest possible reach
+ * 2 r_max + 2 v_max dt (the halo criterion of Sec. 4.3). Falls back to the
+ * brute force when fewer than 3 cells fit per side. */
+int64_t or_candidates_cells(int64_t n, const double* x, const double* v, const double* r, double dt,
+                            int64_t cap, int64_t* ci, int64_t* cj, double* ct);
+
+/* One collision per particle (Sec. 4.3): global greedy matching of the
+ * candidates in the strict order (t, min id, max id). partner[i] = index of the
+ * partner or -1, tc[i] = contact time or +inf. Returns the number of pairs. */
+int64_t or_match_greedy(int64_t n, const int32_t* id, int64_t ncand, const int64_t* ci, const int64_t* cj,
+                        const double* ct, int64_t* partner, double* tc);
+
+/* Same matching by rounds: every free particle picks its earliest free candidate
+ * (ties to the smaller partner id); mutually-picked pairs are committed; repeat
+ * until no free particle has a free candidate. *rounds receives the number of
+ * rounds that committed at least one pair. Returns the number of pairs. */
+int64_t or_match_rounds(int64_t n, const int32_t* id, int64_t ncand, const int64_t* ci, const int64_t* cj,
+                        const double* ct, int64_t* partner, double* tc, int64_t* rounds);
+
+/* Hard-sphere response of one committed pair (Sec. 2.4 jump relations, Sec. 3.3
+ * velocity and position update) and free flight of everything else, then
+ * periodic wrap. Arrays are updated in place. */
+void or_respond_advance(int64_t n, double* x, double* v, const double* m, const int64_t* partner,
+                        const double* tc, double e, double dt);
+
+/* One whole collision step: candidates, greedy matching, response, advance.
+ * partner/tc (length n) receive the matching. method: 0 cell list, 1 brute
+ * force. Returns the number of pairs, or -1 on allocation failure. */
+int64_t or_collide_step(int64_t n, double* x, double* v, const double* r, const double* m, const int32_t* id,
+                        double e, double dt, int method, int64_t* partner, double* tc);
+
+/* Physical position of a logical point xi in [0,1)^3 under the periodic mesh
+ * mapping x = xi + amp*(sin 2pi xi_y sin 2pi xi_z, sin 2pi xi_z sin 2pi xi_x,
+ * sin 2pi xi_x sin 2pi xi_y) (amp = 0 is the affine Cartesian mesh), and the
+ * determinant of its Jacobian. */
+void or_mesh_map(const double xi[3], double amp, double X[3], double* detJ);
+
+/* Projection of particle sources onto the Gauss nodes (Sec. 2.3 / 4.2 with a
+ * Gaussian shape function): F[g,c] = sum_p q[c,p] K(X_g - x_p) / Z_p with
+ * Z_p = sum_g W_g K(X_g - x_p), W_g = w_i w_j w_k (h/2)^3 det J at the node,
+ * K(d) = exp(-|d|^2 / (2 sigma^2)) inside the cutoff and 0 outside.
+ * cutoff_kind 0: box |d_axis| <= cutoff_sigmas*sigma on every axis;
+ * 1: sphere |d| <= cutoff_sigmas*sigma. d is the periodic minimum image.
+ * Sums use Neumaier compensated summation. Z (length n) may be NULL.
+ * Returns 0 on success, nonzero on bad input or allocation failure. */
+int or_project(int64_t n, const double* x, const double* q, int ne, int degree, double sigma, double cutoff_sigmas,
+               int cutoff_kind, double amp, double* field, double* Z);
+
+#ifdef __cplusplus
+}
+#endif
+#endif
