@@ -1,0 +1,130 @@
+/*
+ * pc — per-time-step particle operator of arXiv 2501.05340 on one GB300 (sm_103a).
+ *
+ *   collide: deterministic hard-sphere binary collisions (Sec. 2.4, 3.3, 4.3)
+ *   project: Gaussian projection of particle sources onto the Legendre-Gauss
+ *            nodes of hexahedral DG elements with discrete normalisation (Sec. 2.3, 4.2)
+ *
+ * C ABI: plain pointers and sizes, no C++ or torch types. All particle, source
+ * and field buffers are DEVICE memory owned by the caller; the context owns its
+ * scratch, sized once by pc_init (no allocation in pc_collide / pc_project).
+ * Every call queues its work on the context's stream and returns without
+ * waiting for the GPU, unless stated otherwise.
+ *
+ * Domain: the periodic unit cube [0,1)^3. Per-particle vectors are SoA: a
+ * "[3][n]" array holds the n first coordinates, then the n second, then the n
+ * third. Fields are field[elem][comp][k][j][i] with elem = (ez*ne + ey)*ne + ex
+ * and i the fastest Gauss-node index; comp 0..2 momentum, 3 energy.
+ *
+ * Errors: every call returns a pc_status. Argument errors are detected before any
+ * work is queued and leave all buffers untouched. Conditions found on the GPU
+ * (matching did not converge, a candidate list overflowed) are recorded in the
+ * context and reported by the next pc_get_stats / pc_sync, which wait for the
+ * stream. pc_last_error gives a one-line message for the last failure.
+ */
+#ifndef PC_H
+#define PC_H
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  PC_OK = 0,
+  PC_EINVAL = 1,       /* invalid argument (null pointer, size, parameter out of range) */
+  PC_ENOMEM = 2,       /* device allocation failed (pc_init only) */
+  PC_ECUDA = 3,        /* a CUDA runtime call or kernel launch failed */
+  PC_ENOCONVERGE = 4,  /* the matching rounds reached their cap (cannot happen for valid input) */
+  PC_ECAPACITY = 5,    /* a particle had more candidate partners than the per-particle capacity */
+} pc_status;
+
+typedef struct pc_ctx pc_ctx;
+
+/* Operator configuration, fixed for the lifetime of a context. */
+typedef struct {
+  int64_t n_max;        /* largest particle count a call will pass (> 0) */
+  int32_t ne;           /* elements per side of the periodic unit cube (>= 3) */
+  int32_t degree;       /* DG degree N: N+1 Legendre-Gauss nodes per axis, 0..15 */
+  double sigma;         /* Gaussian kernel width (> 0) */
+  double cutoff_sigmas; /* kernel cutoff radius in units of sigma (> 0); 3 in the paper's workloads */
+  int32_t cutoff_kind;  /* 0: box |d_axis| <= cutoff on every axis (separable); 1: sphere |d| <= cutoff */
+  double restitution;   /* normal restitution coefficient e in [0, 1] (Sec. 2.4) */
+  double reach_hint;    /* expected largest 2 r_max + 2 v_max dt; sizes the collision cells.
+                           Larger actual reaches stay exact (more cells are searched). (> 0) */
+  int32_t cand_cap;     /* candidate partners kept per particle and step (1..32; 0 = 16) */
+  void* stream;         /* cudaStream_t for all work (NULL = legacy default stream) */
+} pc_config;
+
+/* Device SoA particle state (FP64). */
+typedef struct {
+  int64_t n;     /* particle count, 0 <= n <= n_max */
+  int32_t* id;   /* [n] unique ids; ties in contact time go to the smaller id */
+  double* x;     /* [3][n] centres in [0,1) */
+  double* v;     /* [3][n] velocities */
+  double* r;     /* [n] radii (> 0) */
+  double* m;     /* [n] masses (> 0) */
+  double* q;     /* [4][n] sources (3 momentum + 1 energy), or NULL */
+} pc_particles;
+
+typedef struct {
+  int64_t pairs;          /* collisions committed in the last pc_collide */
+  int64_t candidates;     /* candidate pairs (finite contact time) counted from both ends */
+  int64_t worklist;       /* particles left after the first matching round */
+  int64_t rounds;         /* matching rounds in the last pc_collide (>= 1 when pairs > 0) */
+  int64_t fp64_solves;    /* exact FP64 contact solves after the FP32 reject filter */
+  int64_t max_candidates; /* largest per-particle candidate count */
+  int32_t cells_per_side; /* collision cells per side */
+  int32_t stencil;        /* neighbour cells searched on each side in the last step */
+  int32_t device_status;  /* pc_status recorded on the GPU (PC_OK when clean) */
+} pc_stats;
+
+/* Create a context: validates cfg, builds the Gauss tables, chooses the collision
+ * cells (side >= reach_hint, at least 3 per side) and allocates all scratch on
+ * the current CUDA device. *ctx is NULL on failure. */
+pc_status pc_init(pc_ctx** ctx, const pc_config* cfg);
+
+/* One collision step of length dt (Sec. 3.3, 4.3). Reads `in` in any order and
+ * writes `out` (distinct buffers, same n; `out->q` may be NULL only if `in->q` is):
+ * particles sorted by collision cell of their start-of-step position (ties by id),
+ * advanced by dt. Candidate pairs: both roots of |dx + t dv| = r_i + r_j positive,
+ * approaching, smaller root t <= dt, dx the periodic minimum image. Each particle
+ * collides at most once per step; pairs are chosen earliest-contact-first with
+ * ties to the smaller id pair, which is the greedy matching in the order
+ * (t, min id, max id). Response: frictionless impulse J = -m_r (1+e) v_r.n, then
+ * x' = x + t v + (dt - t) v'; free particles x' = x + dt v; then x' wrapped into
+ * [0,1). FP64 arithmetic in a fixed operation order without fused multiply-add,
+ * so pairs, times, x' and v' are bit-identical to a plain IEEE implementation. */
+pc_status pc_collide(pc_ctx* ctx, const pc_particles* in, pc_particles* out, double dt);
+
+/* Projection (Sec. 2.3, 4.2 with a Gaussian shape function): for every Gauss node
+ * X_g, field[g][c] = sum_p q[c][p] K(X_g - x_p) / Z_p, Z_p = sum_g W_g K(X_g - x_p),
+ * W_g = w_i w_j w_k (h/2)^3, K(d) = exp(-|d|^2/(2 sigma^2)) inside the cutoff and 0
+ * outside, d the periodic minimum image. Hence sum_g W_g field[g][c] = sum_p q[c][p].
+ * p->q must be non-NULL. field: device [ne^3][4][(N+1)^3] doubles, overwritten.
+ * Accuracy: within 1e-12 of the exact sum, normwise per component. */
+pc_status pc_project(pc_ctx* ctx, const pc_particles* p, double* field);
+
+/* Copy the pairs of the last pc_collide to HOST memory: ids[2k], ids[2k+1] (smaller
+ * id first) and t[k], sorted by the smaller id. Writes min(cap, count) pairs and
+ * the count to *npairs. Waits for the stream. */
+pc_status pc_get_pairs(pc_ctx* ctx, int32_t* ids, double* t, int64_t cap, int64_t* npairs);
+
+/* Counters of the last pc_collide into HOST memory; returns the device status.
+ * Waits for the stream. */
+pc_status pc_get_stats(pc_ctx* ctx, pc_stats* out);
+
+/* Wait for the stream; returns PC_ECUDA on an asynchronous CUDA error, else the
+ * device status recorded since the last pc_sync (and clears it). */
+pc_status pc_sync(pc_ctx* ctx);
+
+/* Message of the last failure on this context (static storage of the context). */
+const char* pc_last_error(const pc_ctx* ctx);
+
+/* Release all scratch. Waits for the stream. NULL is accepted. */
+void pc_destroy(pc_ctx* ctx);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* PC_H */

@@ -1,0 +1,132 @@
+// Counting sort of particles into bins (collision cells or mesh elements):
+// exclusive scan of the bin counts, scatter, and a per-bin ordering by id so that
+// the sorted order is canonical, independent of the atomic slot assignment.
+// This is the GPU counterpart of the per-step sort of particles by host element
+// (Sec. 4.3), with a uniform cell grid in place of the element list.
+#include "pc_internal.cuh"
+
+namespace {
+
+constexpr int kScanThreads = 256;
+constexpr int kScanPer = PC_SCAN_TILE / kScanThreads;  // 8 elements per thread
+
+__device__ __forceinline__ int warp_incl_scan(int v) {
+  const int lane = threadIdx.x & 31;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    int u = __shfl_up_sync(0xffffffffu, v, o);
+    if (lane >= o) v += u;
+  }
+  return v;
+}
+
+// Block-wide exclusive scan of one value per thread; returns the block total in *total.
+__device__ __forceinline__ int block_excl_scan(int v, int* total) {
+  __shared__ int wsum[kScanThreads / 32];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  int inc = warp_incl_scan(v);
+  if (lane == 31) wsum[warp] = inc;
+  __syncthreads();
+  if (warp == 0) {
+    int s = lane < kScanThreads / 32 ? wsum[lane] : 0;
+    s = warp_incl_scan(s);
+    if (lane < kScanThreads / 32) wsum[lane] = s;
+  }
+  __syncthreads();
+  int prefix = warp > 0 ? wsum[warp - 1] : 0;
+  *total = wsum[kScanThreads / 32 - 1];
+  __syncthreads();
+  return prefix + inc - v;
+}
+
+__global__ void k_scan_reduce(const int32_t* __restrict__ in, int64_t n, int32_t* __restrict__ blocksums) {
+  const int64_t base = (int64_t)blockIdx.x * PC_SCAN_TILE;
+  int s = 0;
+#pragma unroll
+  for (int r = 0; r < kScanPer; ++r) {
+    int64_t i = base + threadIdx.x + (int64_t)r * kScanThreads;
+    if (i < n) s += in[i];
+  }
+  int total;
+  (void)block_excl_scan(s, &total);
+  if (threadIdx.x == 0) blocksums[blockIdx.x] = total;
+}
+
+// One block: exclusive scan of nb block sums in place; out_total receives the sum.
+__global__ void k_scan_blocksums(int32_t* __restrict__ bs, int64_t nb, int32_t* __restrict__ out_total) {
+  int carry = 0;
+  for (int64_t base = 0; base < nb; base += kScanThreads) {
+    int64_t i = base + threadIdx.x;
+    int v = i < nb ? bs[i] : 0;
+    int total;
+    int ex = block_excl_scan(v, &total);
+    if (i < nb) bs[i] = carry + ex;
+    carry += total;
+  }
+  if (threadIdx.x == 0) *out_total = carry;
+}
+
+__global__ void k_scan_apply(const int32_t* __restrict__ in, int32_t* __restrict__ out, int64_t n,
+                             const int32_t* __restrict__ bs) {
+  const int64_t base = (int64_t)blockIdx.x * PC_SCAN_TILE + (int64_t)threadIdx.x * kScanPer;
+  int v[kScanPer];
+  int s = 0;
+#pragma unroll
+  for (int r = 0; r < kScanPer; ++r) {
+    v[r] = (base + r < n) ? in[base + r] : 0;
+    s += v[r];
+  }
+  int total;
+  int ex = block_excl_scan(s, &total) + bs[blockIdx.x];
+#pragma unroll
+  for (int r = 0; r < kScanPer; ++r) {
+    if (base + r < n) out[base + r] = ex;
+    ex += v[r];
+  }
+}
+
+__global__ void k_bin_scatter(int64_t n, const int32_t* __restrict__ key, const int32_t* __restrict__ slot,
+                              const int32_t* __restrict__ start, int32_t* __restrict__ perm) {
+  int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) perm[start[key[i]] + slot[i]] = (int32_t)i;
+}
+
+// Insertion sort of each bin's entries by particle id (bins hold a few particles).
+__global__ void k_bin_order(int64_t nbins, const int32_t* __restrict__ start, const int32_t* __restrict__ id,
+                            int32_t* __restrict__ perm) {
+  int64_t b = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (b >= nbins) return;
+  const int beg = start[b], end = start[b + 1];
+  if (end - beg < 2) return;
+  for (int a = beg + 1; a < end; ++a) {
+    const int32_t p = perm[a];
+    const int32_t pid = id[p];
+    int c = a - 1;
+    while (c >= beg && id[perm[c]] > pid) {
+      perm[c + 1] = perm[c];
+      --c;
+    }
+    perm[c + 1] = p;
+  }
+}
+
+}  // namespace
+
+cudaError_t pc_exclusive_scan(const int32_t* in, int32_t* out, int64_t n, int32_t* blocksums, cudaStream_t s) {
+  const int64_t nb = (n + PC_SCAN_TILE - 1) / PC_SCAN_TILE;
+  if (nb == 0) return cudaMemsetAsync(out, 0, sizeof(int32_t), s);
+  k_scan_reduce<<<(unsigned)nb, kScanThreads, 0, s>>>(in, n, blocksums);
+  k_scan_blocksums<<<1, kScanThreads, 0, s>>>(blocksums, nb, out + n);
+  k_scan_apply<<<(unsigned)nb, kScanThreads, 0, s>>>(in, out, n, blocksums);
+  return cudaGetLastError();
+}
+
+cudaError_t pc_bin_finish(int64_t n, int64_t nbins, const int32_t* key, const int32_t* slot, const int32_t* id,
+                          int32_t* cnt, int32_t* start, int32_t* blocksums, int32_t* perm, cudaStream_t s) {
+  PC_CUDA_TRY(pc_exclusive_scan(cnt, start, nbins, blocksums, s));
+  if (n > 0) {
+    k_bin_scatter<<<pc_blocks(n, 256), 256, 0, s>>>(n, key, slot, start, perm);
+    k_bin_order<<<pc_blocks(nbins, 256), 256, 0, s>>>(nbins, start, id, perm);
+  }
+  return cudaGetLastError();
+}

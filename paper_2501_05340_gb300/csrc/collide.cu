@@ -1,0 +1,556 @@
+// Collision step of the particle operator (arXiv 2501.05340, Sec. 2.4, 3.3, 4.3).
+//
+// Compiled with -fmad=false: every double expression below is evaluated as
+// separate IEEE operations in source order, so contact times, velocities and
+// positions are bit-identical to a plain FP64 implementation of the same
+// formulas. The FP32 pre-filter is conservative by construction (see
+// filter_keep) and only decides which pairs reach the exact FP64 test.
+//
+// Pipeline (one stream, no host synchronisation):
+//   keys      cell of every particle, atomic slot in its cell, max |v|^2 and max r
+//   bin       exclusive scan of the cell counts, scatter, per-cell order by id
+//   gather    sorted FP64 copies of x, v, r, id plus FP32 copies for the filter
+//   search    per particle: all candidates j in the neighbour cells, sorted by (t, id)
+//   match     round 1 over all particles: commit mutually-earliest pairs
+//   finish    one CTA: further rounds over the particles left with candidates
+//   respond   impulse, velocity and position update, wrap, write the output state
+#include <math.h>
+
+#include "pc_internal.cuh"
+
+namespace {
+
+constexpr int kMaxCap = 32;
+
+__device__ __forceinline__ double minimg(double d) {
+  if (d > 0.5) return d - 1.0;
+  if (d < -0.5) return d + 1.0;
+  return d;
+}
+
+__device__ __forceinline__ float minimgf(float d) {
+  if (d > 0.5f) return d - 1.0f;
+  if (d < -0.5f) return d + 1.0f;
+  return d;
+}
+
+// y - floor(y) in [0,1]; a tiny negative y rounds it to exactly 1.0, mapped to 0.0.
+__device__ __forceinline__ double wrap01(double y) {
+  double w = y - floor(y);
+  if (w == 1.0) w = 0.0;
+  return w;
+}
+
+__device__ __forceinline__ int cell_of(double y, int nc) {
+  int c = (int)(y * (double)nc);
+  c = c < 0 ? 0 : c;
+  return c >= nc ? nc - 1 : c;
+}
+
+__device__ __forceinline__ int wrapi(int a, int n) {
+  a %= n;
+  return a < 0 ? a + n : a;
+}
+
+__device__ __forceinline__ void raise_status(unsigned long long* counters, int code) {
+  atomicMax(&counters[CNT_STATUS], (unsigned long long)code);
+}
+
+// Smaller positive root of |dx + t dv| = R with dx = minimg(x_i - x_j), dv = v_i - v_j
+// when b < 0, c > 0, b^2 - a c > 0 and the root is <= dt; +inf otherwise.
+// Same operations in the same order as the plain definition (Sec. 3.3).
+__device__ double contact_time_exact(const double xi[3], const double xj[3], const double vi[3],
+                                     const double vj[3], double R, double dt) {
+  const double dx0 = minimg(xi[0] - xj[0]);
+  const double dx1 = minimg(xi[1] - xj[1]);
+  const double dx2 = minimg(xi[2] - xj[2]);
+  const double dv0 = vi[0] - vj[0];
+  const double dv1 = vi[1] - vj[1];
+  const double dv2 = vi[2] - vj[2];
+  const double a = (dv0 * dv0 + dv1 * dv1) + dv2 * dv2;
+  const double b = (dx0 * dv0 + dx1 * dv1) + dx2 * dv2;
+  const double c = ((dx0 * dx0 + dx1 * dx1) + dx2 * dx2) - R * R;
+  if (!(b < 0.0)) return CUDART_INF;
+  if (!(c > 0.0)) return CUDART_INF;
+  const double disc = b * b - a * c;
+  if (!(disc > 0.0)) return CUDART_INF;
+  const double t = c / (-b + sqrt(disc));
+  return t <= dt ? t : CUDART_INF;
+}
+
+// Conservative FP32 reject test. A pair accepted by the FP64 test satisfies
+// |dx| <= (R + |dv| dt)(1 + O(1e-15)) and dx.dv < 0 (the root formula gives
+// c <= 2|b| t and |b| <= |dx||dv|). The FP32 copies of coordinates in [0,1)
+// differ from the FP64 values by at most 2^-25, a wrapped difference adds at most
+// 2^-25, so |dxf - dx| <= 1.2e-7 per axis (2.1e-7 in norm); each FP32 velocity
+// component is within 2^-24 relative, so |dvf - dv| <= 2.1e-7 vmax in norm with
+// vmax the largest speed of the step. The test keeps every pair within
+// R + |dvf| dt + 4e-7 + 2.5e-7 vmax dt (1e-5 relative slack on top), and every
+// pair whose FP32 dx.dv is not clearly positive.
+__device__ __forceinline__ bool filter_keep(const float dxf[3], const float dvf[3], float Rf, float dt, float vmax) {
+  const float d2 = dxf[0] * dxf[0] + dxf[1] * dxf[1] + dxf[2] * dxf[2];
+  const float v2 = dvf[0] * dvf[0] + dvf[1] * dvf[1] + dvf[2] * dvf[2];
+  const float vm = sqrtf(v2);
+  const float reach = (Rf + vm * dt + 4.0e-7f + 2.5e-7f * vmax * dt) * 1.00001f;
+  if (d2 > reach * reach) return false;
+  const float bf = dxf[0] * dvf[0] + dxf[1] * dvf[1] + dxf[2] * dvf[2];
+  const float bslack = (4.0e-7f + 1.0e-6f * sqrtf(d2)) * (vm + vmax);
+  return !(bf > bslack);
+}
+
+// ------------------------------------------------------------------ keys
+
+__global__ void k_collide_keys(int64_t n, const double* __restrict__ x, const double* __restrict__ v,
+                               const double* __restrict__ r, const double* __restrict__ m, int nc,
+                               int32_t* __restrict__ key, int32_t* __restrict__ slot, int32_t* __restrict__ cnt,
+                               unsigned long long* __restrict__ counters) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  double v2 = 0.0, rr = 0.0;
+  if (i < n) {
+    const double x0 = x[i], x1 = x[n + i], x2 = x[2 * n + i];
+    const double v0 = v[i], v1 = v[n + i], vv2 = v[2 * n + i];
+    rr = r[i];
+    const double mm = m[i];
+    const bool ok = (x0 >= 0.0 && x0 < 1.0) && (x1 >= 0.0 && x1 < 1.0) && (x2 >= 0.0 && x2 < 1.0) &&
+                    (rr > 0.0 && rr < 0.25) && (mm > 0.0 && mm < CUDART_INF) && isfinite(v0) && isfinite(v1) &&
+                    isfinite(vv2);
+    if (!ok) raise_status(counters, PC_EINVAL);
+    const int k = (cell_of(x2, nc) * nc + cell_of(x1, nc)) * nc + cell_of(x0, nc);
+    key[i] = k;
+    slot[i] = atomicAdd(&cnt[k], 1);
+    v2 = (v0 * v0 + v1 * v1) + vv2 * vv2;
+    if (!(v2 < CUDART_INF)) v2 = 0.0;
+    if (!(rr > 0.0 && rr < 0.25)) rr = 0.0;
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    v2 = fmax(v2, __shfl_xor_sync(0xffffffffu, v2, o));
+    rr = fmax(rr, __shfl_xor_sync(0xffffffffu, rr, o));
+  }
+  if ((threadIdx.x & 31) == 0) {
+    // non-negative doubles order like their bit patterns
+    atomicMax(&counters[CNT_VMAX2], (unsigned long long)__double_as_longlong(v2));
+    atomicMax(&counters[CNT_RMAX], (unsigned long long)__double_as_longlong(rr));
+  }
+}
+
+// ------------------------------------------------------------------ gather
+
+__global__ void k_collide_gather(int64_t n, const int32_t* __restrict__ perm, const double* __restrict__ x,
+                                 const double* __restrict__ v, const double* __restrict__ r,
+                                 const int32_t* __restrict__ id, double* __restrict__ sx, double* __restrict__ sv,
+                                 double* __restrict__ sr, int32_t* __restrict__ sid, float* __restrict__ sxf,
+                                 float* __restrict__ svf, float* __restrict__ srf) {
+  const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= n) return;
+  const int64_t p = perm[k];
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+    const double xa = x[a * n + p], va = v[a * n + p];
+    sx[a * n + k] = xa;
+    sv[a * n + k] = va;
+    sxf[a * n + k] = (float)xa;
+    svf[a * n + k] = (float)va;
+  }
+  const double rr = r[p];
+  sr[k] = rr;
+  srf[k] = (float)rr;
+  sid[k] = id[p];
+}
+
+// ------------------------------------------------------------------ search
+
+struct SearchArgs {
+  int64_t n;
+  int nc;
+  int cap;
+  double dt;
+  const double *sx, *sv, *sr;
+  const int32_t* sid;
+  const float *sxf, *svf, *srf;
+  const int32_t* start;
+  int32_t* cand_j;
+  double* cand_t;
+  int32_t* ncand;
+  int32_t* best;
+  unsigned long long* counters;
+};
+
+// Neighbour cells searched on each side: the largest possible reach
+// 2 r_max + 2 v_max dt (Sec. 4.3, halo criterion) in units of the cell side,
+// plus one for the rounding of cell indices.
+__device__ __forceinline__ int stencil_radius(const unsigned long long* counters, int nc, double dt, double* reach) {
+  const double v2 = __longlong_as_double((long long)counters[CNT_VMAX2]);
+  const double rm = __longlong_as_double((long long)counters[CNT_RMAX]);
+  const double re = (2.0 * rm + 2.0 * sqrt(v2) * dt) * (1.0 + 1e-9) + 1e-12;
+  *reach = re;
+  double s = floor(re * (double)nc * (1.0 + 1e-9)) + 1.0;
+  if (s > (double)nc) s = (double)nc;
+  return (int)s;
+}
+
+__device__ __forceinline__ void consider(const SearchArgs& A, int64_t k, int64_t j, const double xi[3],
+                                         const double vi[3], double ri, const float xf[3], const float vf[3],
+                                         float rf, float dtf, float vmaxf, double* lt, int* lj, int& cnt,
+                                         int& found, int& solves) {
+  const int64_t n = A.n;
+  float dxf[3], dvf[3];
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+    dxf[a] = minimgf(xf[a] - A.sxf[a * n + j]);
+    dvf[a] = vf[a] - A.svf[a * n + j];
+  }
+  if (!filter_keep(dxf, dvf, rf + A.srf[j], dtf, vmaxf)) return;
+  ++solves;
+  const double xj[3] = {A.sx[j], A.sx[n + j], A.sx[2 * n + j]};
+  const double vj[3] = {A.sv[j], A.sv[n + j], A.sv[2 * n + j]};
+  const double t = contact_time_exact(xi, xj, vi, vj, ri + A.sr[j], A.dt);
+  if (!(t <= A.dt)) return;
+  ++found;
+  const int jid = A.sid[j];
+  // insertion into the list sorted by (t, id), keeping the cap best
+  int pos = cnt;
+  while (pos > 0 && (lt[pos - 1] > t || (lt[pos - 1] == t && A.sid[lj[pos - 1]] > jid))) --pos;
+  if (pos >= A.cap) return;
+  int last = cnt < A.cap ? cnt : A.cap - 1;
+  for (int q = last; q > pos; --q) {
+    lt[q] = lt[q - 1];
+    lj[q] = lj[q - 1];
+  }
+  lt[pos] = t;
+  lj[pos] = (int)j;
+  if (cnt < A.cap) ++cnt;
+}
+
+__global__ void __launch_bounds__(256) k_search(SearchArgs A) {
+  const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const int64_t n = A.n;
+  double reach;
+  const int s = stencil_radius(A.counters, A.nc, A.dt, &reach);
+  if (k == 0) {
+    atomicMax(&A.counters[CNT_STENCIL], (unsigned long long)s);
+    if (!(reach < 0.5)) raise_status(A.counters, PC_EINVAL);
+  }
+  int found = 0, solves = 0, cnt = 0;
+  if (k < n) {
+    double lt[kMaxCap];
+    int lj[kMaxCap];
+    const double xi[3] = {A.sx[k], A.sx[n + k], A.sx[2 * n + k]};
+    const double vi[3] = {A.sv[k], A.sv[n + k], A.sv[2 * n + k]};
+    const double ri = A.sr[k];
+    const float xf[3] = {A.sxf[k], A.sxf[n + k], A.sxf[2 * n + k]};
+    const float vf[3] = {A.svf[k], A.svf[n + k], A.svf[2 * n + k]};
+    const float rf = A.srf[k];
+    const float dtf = (float)A.dt * 1.000001f;
+    const float vmaxf = (float)sqrt(__longlong_as_double((long long)A.counters[CNT_VMAX2])) * 1.000001f;
+    const int nc = A.nc;
+    const int cx = cell_of(xi[0], nc), cy = cell_of(xi[1], nc), cz = cell_of(xi[2], nc);
+    const int span = 2 * s + 1;
+    const bool full = span >= nc;  // the stencil covers the whole axis: visit every cell once
+    const int cnt_ax = full ? nc : span;
+    for (int oz = 0; oz < cnt_ax; ++oz) {
+      const int zc = full ? oz : wrapi(cz - s + oz, nc);
+      for (int oy = 0; oy < cnt_ax; ++oy) {
+        const int yc = full ? oy : wrapi(cy - s + oy, nc);
+        const int64_t row = ((int64_t)zc * nc + yc) * nc;
+        if (!full && cx - s >= 0 && cx + s < nc) {
+          const int beg = A.start[row + cx - s], end = A.start[row + cx + s + 1];
+          for (int j = beg; j < end; ++j)
+            if (j != k) consider(A, k, j, xi, vi, ri, xf, vf, rf, dtf, vmaxf, lt, lj, cnt, found, solves);
+        } else {
+          for (int ox = 0; ox < cnt_ax; ++ox) {
+            const int xc = full ? ox : wrapi(cx - s + ox, nc);
+            const int beg = A.start[row + xc], end = A.start[row + xc + 1];
+            for (int j = beg; j < end; ++j)
+              if (j != k) consider(A, k, j, xi, vi, ri, xf, vf, rf, dtf, vmaxf, lt, lj, cnt, found, solves);
+          }
+        }
+      }
+    }
+    for (int q = 0; q < cnt; ++q) {
+      A.cand_j[(int64_t)q * n + k] = lj[q];
+      A.cand_t[(int64_t)q * n + k] = lt[q];
+    }
+    A.ncand[k] = cnt;
+    A.best[k] = cnt > 0 ? lj[0] : -1;
+    if (found > A.cap) raise_status(A.counters, PC_ECAPACITY);
+  }
+  // warp-aggregated statistics
+  int fsum = found, ssum = solves, fmax = found;
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    fsum += __shfl_xor_sync(0xffffffffu, fsum, o);
+    ssum += __shfl_xor_sync(0xffffffffu, ssum, o);
+    fmax = max(fmax, __shfl_xor_sync(0xffffffffu, fmax, o));
+  }
+  if ((threadIdx.x & 31) == 0) {
+    if (fsum) atomicAdd(&A.counters[CNT_CANDS], (unsigned long long)fsum);
+    if (ssum) atomicAdd(&A.counters[CNT_SOLVES], (unsigned long long)ssum);
+    if (fmax) atomicMax(&A.counters[CNT_MAXCAND], (unsigned long long)fmax);
+  }
+}
+
+// ------------------------------------------------------------------ matching
+
+struct MatchArgs {
+  int64_t n;
+  int cap;
+  const int32_t* cand_j;
+  const double* cand_t;
+  const int32_t* ncand;
+  int32_t* best;
+  const int32_t* sid;
+  int32_t* partner;
+  double* tcoll;
+  int32_t* work;
+  int32_t *pair_lo, *pair_hi;
+  double* pair_t;
+  unsigned long long* counters;
+};
+
+__device__ __forceinline__ void record_pair(const MatchArgs& M, int64_t k, int64_t b, double t) {
+  const int32_t ik = M.sid[k], ib = M.sid[b];
+  if (ik < ib) {
+    const unsigned long long q = atomicAdd(&M.counters[CNT_PAIRS], 1ull);
+    M.pair_lo[q] = ik;
+    M.pair_hi[q] = ib;
+    M.pair_t[q] = t;
+  }
+}
+
+// Round 1: every particle's earliest candidate is its pick; mutual picks collide.
+__global__ void k_match_first(MatchArgs M) {
+  const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= M.n) return;
+  const int b = M.best[k];
+  if (b >= 0 && M.best[b] == (int)k) {
+    const double t = M.cand_t[k];
+    M.partner[k] = b;
+    M.tcoll[k] = t;
+    record_pair(M, k, b, t);
+    if (M.sid[k] < M.sid[b]) atomicMax(&M.counters[CNT_ROUNDS], 1ull);
+  } else {
+    M.partner[k] = -1;
+    M.tcoll[k] = CUDART_INF;
+    if (b >= 0) {
+      const unsigned long long w = atomicAdd(&M.counters[CNT_WORK], 1ull);
+      M.work[w] = (int32_t)k;
+    }
+  }
+}
+
+// Further rounds in one CTA over the particles that still had candidates after
+// round 1: pick the earliest candidate that is still free, commit mutual picks.
+// Each round that has a pick commits at least the globally earliest remaining
+// pair, so the loop ends after at most |work| + 1 rounds; the cap is a guard.
+constexpr int kFinishThreads = 1024;
+
+__global__ void __launch_bounds__(kFinishThreads) k_match_finish(MatchArgs M) {
+  const int64_t nw = (int64_t)M.counters[CNT_WORK];
+  if (nw == 0) return;
+  const int64_t n = M.n;
+  unsigned long long rounds = M.counters[CNT_ROUNDS];
+  for (int64_t r = 0;; ++r) {
+    int any = 0;
+    for (int64_t w = threadIdx.x; w < nw; w += kFinishThreads) {
+      const int64_t k = M.work[w];
+      if (M.partner[k] >= 0) continue;
+      const int c = M.ncand[k];
+      int nb = -1;
+      for (int q = 0; q < c; ++q) {
+        const int j = M.cand_j[(int64_t)q * n + k];
+        if (M.partner[j] < 0) {
+          nb = j;
+          break;
+        }
+      }
+      M.best[k] = nb;
+      any |= nb >= 0;
+    }
+    if (!__syncthreads_or(any)) break;
+    if (r > nw + 1) {
+      if (threadIdx.x == 0) raise_status(M.counters, PC_ENOCONVERGE);
+      break;
+    }
+    int committed = 0;
+    for (int64_t w = threadIdx.x; w < nw; w += kFinishThreads) {
+      const int64_t k = M.work[w];
+      if (M.partner[k] >= 0) continue;
+      const int b = M.best[k];
+      if (b >= 0 && M.best[b] == (int)k) {
+        const int c = M.ncand[k];
+        double t = CUDART_INF;
+        for (int q = 0; q < c; ++q)
+          if (M.cand_j[(int64_t)q * n + k] == b) {
+            t = M.cand_t[(int64_t)q * n + k];
+            break;
+          }
+        M.partner[k] = b;
+        M.tcoll[k] = t;
+        record_pair(M, k, b, t);
+        committed = 1;
+      }
+    }
+    if (__syncthreads_or(committed)) ++rounds;
+  }
+  if (threadIdx.x == 0) M.counters[CNT_ROUNDS] = rounds;
+}
+
+// ------------------------------------------------------------------ respond
+
+struct RespondArgs {
+  int64_t n;
+  double dt, e;
+  const double *sx, *sv, *sr;
+  const int32_t* sid;
+  const int32_t* partner;
+  const double* tcoll;
+  const int32_t* perm;
+  const double* m_in;
+  const double* q_in;
+  double *x_out, *v_out, *r_out, *m_out, *q_out;
+  int32_t* id_out;
+};
+
+// Frictionless hard-sphere response (Sec. 2.4) from the particle's own side:
+// s = dx + t dv (from partner to self), n = -s/|s|, v_r.n, m_r = m_i m_j/(m_i + m_j),
+// J = -m_r (1 + e) v_r.n, v' = v + (J/m_i) n, x' = x + t v + (dt - t) v' (Sec. 3.3).
+__global__ void k_respond(RespondArgs R) {
+  const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const int64_t n = R.n;
+  if (k >= n) return;
+  const int64_t p = R.perm[k];
+  const int32_t j = R.partner[k];
+  const double mi = R.m_in[p];
+  double xo[3], vo[3];
+  const double xi[3] = {R.sx[k], R.sx[n + k], R.sx[2 * n + k]};
+  const double vi[3] = {R.sv[k], R.sv[n + k], R.sv[2 * n + k]};
+  if (j < 0) {
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+      vo[a] = vi[a];
+      xo[a] = xi[a] + R.dt * vi[a];
+    }
+  } else {
+    const double t = R.tcoll[k];
+    const double mj = R.m_in[R.perm[j]];
+    double dx[3], dv[3], s[3], nr[3];
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+      dx[a] = minimg(xi[a] - R.sx[a * n + j]);
+      dv[a] = vi[a] - R.sv[a * n + j];
+    }
+#pragma unroll
+    for (int a = 0; a < 3; ++a) s[a] = dx[a] + t * dv[a];
+    const double sl = sqrt((s[0] * s[0] + s[1] * s[1]) + s[2] * s[2]);
+#pragma unroll
+    for (int a = 0; a < 3; ++a) nr[a] = -s[a] / sl;
+    const double vrn = (dv[0] * nr[0] + dv[1] * nr[1]) + dv[2] * nr[2];
+    const double mr = (mi * mj) / (mi + mj);
+    const double J = -mr * (1.0 + R.e) * vrn;
+    const double gi = J / mi;
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+      const double vnew = vi[a] + gi * nr[a];
+      vo[a] = vnew;
+      xo[a] = (xi[a] + t * vi[a]) + (R.dt - t) * vnew;
+    }
+  }
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+    R.x_out[a * n + k] = wrap01(xo[a]);
+    R.v_out[a * n + k] = vo[a];
+  }
+  R.r_out[k] = R.sr[k];
+  R.m_out[k] = mi;
+  R.id_out[k] = R.sid[k];
+  if (R.q_out) {
+#pragma unroll
+    for (int c = 0; c < 4; ++c) R.q_out[c * n + k] = R.q_in[c * n + p];
+  }
+}
+
+}  // namespace
+
+pc_status pc_collide_impl(pc_ctx* ctx, const pc_particles* in, pc_particles* out, double dt) {
+  const int64_t n = in->n;
+  cudaStream_t st = ctx->stream;
+  cudaError_t e = cudaSuccess;
+  e = cudaMemsetAsync(ctx->counters, 0, sizeof(unsigned long long) * CNT_N, st);
+  if (e == cudaSuccess && n == 0) return PC_OK;
+  if (e == cudaSuccess) e = cudaMemsetAsync(ctx->cnt, 0, sizeof(int32_t) * (size_t)ctx->ncell, st);
+  if (e != cudaSuccess) goto fail;
+  k_collide_keys<<<pc_blocks(n, 256), 256, 0, st>>>(n, in->x, in->v, in->r, in->m, ctx->nc, ctx->key, ctx->slot,
+                                                     ctx->cnt, ctx->counters);
+  e = pc_bin_finish(n, ctx->ncell, ctx->key, ctx->slot, in->id, ctx->cnt, ctx->start, ctx->blocksums, ctx->perm, st);
+  if (e != cudaSuccess) goto fail;
+  k_collide_gather<<<pc_blocks(n, 256), 256, 0, st>>>(n, ctx->perm, in->x, in->v, in->r, in->id, ctx->sx, ctx->sv,
+                                                       ctx->sr, ctx->sid, ctx->sxf, ctx->svf, ctx->srf);
+  {
+    SearchArgs A;
+    A.n = n;
+    A.nc = ctx->nc;
+    A.cap = ctx->cap;
+    A.dt = dt;
+    A.sx = ctx->sx;
+    A.sv = ctx->sv;
+    A.sr = ctx->sr;
+    A.sid = ctx->sid;
+    A.sxf = ctx->sxf;
+    A.svf = ctx->svf;
+    A.srf = ctx->srf;
+    A.start = ctx->start;
+    A.cand_j = ctx->cand_j;
+    A.cand_t = ctx->cand_t;
+    A.ncand = ctx->ncand;
+    A.best = ctx->best;
+    A.counters = ctx->counters;
+    k_search<<<pc_blocks(n, 256), 256, 0, st>>>(A);
+  }
+  {
+    MatchArgs M;
+    M.n = n;
+    M.cap = ctx->cap;
+    M.cand_j = ctx->cand_j;
+    M.cand_t = ctx->cand_t;
+    M.ncand = ctx->ncand;
+    M.best = ctx->best;
+    M.sid = ctx->sid;
+    M.partner = ctx->partner;
+    M.tcoll = ctx->tcoll;
+    M.work = ctx->work;
+    M.pair_lo = ctx->pair_lo;
+    M.pair_hi = ctx->pair_hi;
+    M.pair_t = ctx->pair_t;
+    M.counters = ctx->counters;
+    k_match_first<<<pc_blocks(n, 256), 256, 0, st>>>(M);
+    k_match_finish<<<1, kFinishThreads, 0, st>>>(M);
+  }
+  {
+    RespondArgs R;
+    R.n = n;
+    R.dt = dt;
+    R.e = ctx->cfg.restitution;
+    R.sx = ctx->sx;
+    R.sv = ctx->sv;
+    R.sr = ctx->sr;
+    R.sid = ctx->sid;
+    R.partner = ctx->partner;
+    R.tcoll = ctx->tcoll;
+    R.perm = ctx->perm;
+    R.m_in = in->m;
+    R.q_in = in->q;
+    R.x_out = out->x;
+    R.v_out = out->v;
+    R.r_out = out->r;
+    R.m_out = out->m;
+    R.q_out = in->q ? out->q : nullptr;
+    R.id_out = out->id;
+    k_respond<<<pc_blocks(n, 256), 256, 0, st>>>(R);
+  }
+  e = cudaGetLastError();
+  if (e == cudaSuccess) return PC_OK;
+fail:
+  snprintf(ctx->err, sizeof(ctx->err), "pc_collide: %s", cudaGetErrorString(e));
+  return PC_ECUDA;
+}

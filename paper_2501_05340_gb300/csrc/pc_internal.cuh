@@ -1,0 +1,84 @@
+// Internal declarations of the pc library (not part of the C ABI).
+#pragma once
+#include <cuda_runtime.h>
+#include <math_constants.h>
+#include <stdint.h>
+#include <stdio.h>
+
+#include "pc.h"
+
+// Device counters of one pc_collide / pc_project (64-bit, atomically updated).
+enum {
+  CNT_PAIRS = 0,
+  CNT_CANDS,
+  CNT_WORK,
+  CNT_ROUNDS,
+  CNT_SOLVES,
+  CNT_MAXCAND,
+  CNT_STENCIL,
+  CNT_STATUS,  // pc_status raised on the GPU (max of codes)
+  CNT_VMAX2,   // max |v|^2 as the bits of a non-negative double
+  CNT_RMAX,    // max r as the bits of a non-negative double
+  CNT_N
+};
+
+struct pc_ctx {
+  pc_config cfg;
+  cudaStream_t stream;
+  int device;
+  // collision cells
+  int nc;
+  int64_t ncell;
+  // projection geometry
+  int n1;
+  int rho;   // neighbour elements searched on each side
+  int win;   // factor window per axis: (2 rho + 1) n1 nodes
+  double h;
+  // binning scratch (shared by collide and project; sized for the larger grid)
+  int64_t nbins_max;
+  int32_t *cnt, *start, *blocksums;
+  int32_t *key, *slot, *perm;
+  // collide scratch (sorted order)
+  double *sx, *sv, *sr;
+  int32_t* sid;
+  float *sxf, *svf, *srf;
+  int32_t cap;
+  int32_t* cand_j;
+  double* cand_t;
+  int32_t *ncand, *best, *partner, *work;
+  double* tcoll;
+  int32_t *pair_lo, *pair_hi;
+  double* pair_t;
+  unsigned long long* counters;    // device [CNT_N]
+  unsigned long long* h_counters;  // pinned host copy
+  // projection scratch
+  double* fac;  // [3][win][n_max] normalised 1-D kernel factors, sorted order
+  double* sq;   // [4][n_max] sources, sorted order
+  // Legendre-Gauss nodes and weights (passed to the kernels as arguments)
+  double eta[16], w[16];
+  char err[256];
+};
+
+// ---- binning (bin.cu) --------------------------------------------------------
+// Exclusive scan of in[0..n) into out[0..n], out[n] = total. blocksums holds
+// ceil(n / PC_SCAN_TILE) entries.
+#define PC_SCAN_TILE 2048
+cudaError_t pc_exclusive_scan(const int32_t* in, int32_t* out, int64_t n, int32_t* blocksums, cudaStream_t s);
+// Given key[i] (bin) and slot[i] (rank inside its bin in arbitrary order), write the
+// permutation sorted by (bin, id): perm[k] = input index of the k-th particle.
+cudaError_t pc_bin_finish(int64_t n, int64_t nbins, const int32_t* key, const int32_t* slot, const int32_t* id,
+                          int32_t* cnt, int32_t* start, int32_t* blocksums, int32_t* perm, cudaStream_t s);
+
+// ---- collide (collide.cu) ----------------------------------------------------
+pc_status pc_collide_impl(pc_ctx* ctx, const pc_particles* in, pc_particles* out, double dt);
+
+// ---- project (project.cu) ----------------------------------------------------
+pc_status pc_project_impl(pc_ctx* ctx, const pc_particles* p, double* field);
+
+#define PC_CUDA_TRY(expr)                          \
+  do {                                             \
+    cudaError_t _e = (expr);                       \
+    if (_e != cudaSuccess) return _e;              \
+  } while (0)
+
+static inline int pc_blocks(int64_t n, int threads) { return (int)((n + threads - 1) / threads); }

@@ -1,0 +1,200 @@
+"""Python binding of the pc C ABI (``include/pc.h``): argument marshalling only.
+
+Every step of the operator runs in the CUDA library ``libpc.so``; there is no
+CPU fallback. Importing this module builds the library if it is missing or
+stale (nvcc, sm_103a) and raises if that fails.
+
+Particle state lives in torch CUDA tensors (SoA, float64): ``x[3, n]``,
+``v[3, n]``, ``r[n]``, ``m[n]``, ``q[4, n]`` and ``id[n]`` (int32).
+"""
+import ctypes
+
+import numpy as np
+import torch
+
+from . import build as _build
+
+c_i64, c_i32, c_d, c_p = ctypes.c_int64, ctypes.c_int32, ctypes.c_double, ctypes.c_void_p
+
+PC_OK, PC_EINVAL, PC_ENOMEM, PC_ECUDA, PC_ENOCONVERGE, PC_ECAPACITY = range(6)
+STATUS_NAMES = {0: "PC_OK", 1: "PC_EINVAL", 2: "PC_ENOMEM", 3: "PC_ECUDA", 4: "PC_ENOCONVERGE", 5: "PC_ECAPACITY"}
+
+
+class PcConfig(ctypes.Structure):
+    _fields_ = [("n_max", c_i64), ("ne", c_i32), ("degree", c_i32), ("sigma", c_d), ("cutoff_sigmas", c_d),
+                ("cutoff_kind", c_i32), ("restitution", c_d), ("reach_hint", c_d), ("cand_cap", c_i32),
+                ("stream", c_p)]
+
+
+class PcParticles(ctypes.Structure):
+    _fields_ = [("n", c_i64), ("id", c_p), ("x", c_p), ("v", c_p), ("r", c_p), ("m", c_p), ("q", c_p)]
+
+
+class PcStats(ctypes.Structure):
+    _fields_ = [("pairs", c_i64), ("candidates", c_i64), ("worklist", c_i64), ("rounds", c_i64),
+                ("fp64_solves", c_i64), ("max_candidates", c_i64), ("cells_per_side", c_i32), ("stencil", c_i32),
+                ("device_status", c_i32)]
+
+
+class PcError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__("%s: %s" % (STATUS_NAMES.get(status, status), msg))
+        self.status = status
+
+
+_lib = None
+
+
+def library():
+    """The loaded ``libpc.so`` (built on first use)."""
+    global _lib
+    if _lib is None:
+        path = _build.build()
+        lib = ctypes.CDLL(path)
+        lib.pc_init.argtypes = [ctypes.POINTER(c_p), ctypes.POINTER(PcConfig)]
+        lib.pc_collide.argtypes = [c_p, ctypes.POINTER(PcParticles), ctypes.POINTER(PcParticles), c_d]
+        lib.pc_project.argtypes = [c_p, ctypes.POINTER(PcParticles), c_p]
+        lib.pc_get_pairs.argtypes = [c_p, c_p, c_p, c_i64, ctypes.POINTER(c_i64)]
+        lib.pc_get_stats.argtypes = [c_p, ctypes.POINTER(PcStats)]
+        lib.pc_sync.argtypes = [c_p]
+        lib.pc_last_error.argtypes = [c_p]
+        lib.pc_last_error.restype = ctypes.c_char_p
+        lib.pc_destroy.argtypes = [c_p]
+        lib.pc_destroy.restype = None
+        for f in ("pc_init", "pc_collide", "pc_project", "pc_get_pairs", "pc_get_stats", "pc_sync"):
+            getattr(lib, f).restype = ctypes.c_int
+        _lib = lib
+    return _lib
+
+
+def _ptr(t):
+    return c_p(t.data_ptr()) if t is not None else c_p(0)
+
+
+class State:
+    """FP64 device particle state (SoA torch tensors)."""
+
+    def __init__(self, x, v, r, m, id, q=None):
+        self.x, self.v, self.r, self.m, self.id, self.q = x, v, r, m, id, q
+        n = r.shape[0]
+        for name, t, shape, dt in (("x", x, (3, n), torch.float64), ("v", v, (3, n), torch.float64),
+                                   ("r", r, (n,), torch.float64), ("m", m, (n,), torch.float64),
+                                   ("id", id, (n,), torch.int32)):
+            if tuple(t.shape) != shape or t.dtype != dt or not t.is_contiguous() or not t.is_cuda:
+                raise ValueError("State.%s must be a contiguous CUDA %s tensor of shape %s" % (name, dt, shape))
+        if q is not None and (tuple(q.shape) != (4, n) or q.dtype != torch.float64 or not q.is_contiguous()):
+            raise ValueError("State.q must be a contiguous CUDA float64 tensor of shape (4, n)")
+
+    @property
+    def n(self):
+        return self.r.shape[0]
+
+    @staticmethod
+    def empty(n, device="cuda", with_q=True):
+        f = dict(dtype=torch.float64, device=device)
+        return State(torch.empty(3, n, **f), torch.empty(3, n, **f), torch.empty(n, **f), torch.empty(n, **f),
+                     torch.empty(n, dtype=torch.int32, device=device),
+                     torch.empty(4, n, **f) if with_q else None)
+
+    @staticmethod
+    def from_arrays(d, device="cuda", with_q=True):
+        """From a dict of numpy arrays (x[3][n], v, r, m, id, q) as drawn by ``inputs.draw``."""
+        t = lambda a, dt=torch.float64: torch.as_tensor(np.ascontiguousarray(a)).to(device=device, dtype=dt)
+        return State(t(d["x"]), t(d["v"]), t(d["r"]), t(d["m"]), t(d["id"], torch.int32),
+                     t(d["q"]) if with_q and "q" in d else None)
+
+    def copy_(self, other):
+        for a in ("x", "v", "r", "m", "id"):
+            getattr(self, a).copy_(getattr(other, a))
+        if self.q is not None and other.q is not None:
+            self.q.copy_(other.q)
+        return self
+
+    def struct(self):
+        return PcParticles(self.n, _ptr(self.id), _ptr(self.x), _ptr(self.v), _ptr(self.r), _ptr(self.m),
+                           _ptr(self.q))
+
+    def numpy(self):
+        out = dict(x=self.x.cpu().numpy(), v=self.v.cpu().numpy(), r=self.r.cpu().numpy(), m=self.m.cpu().numpy(),
+                   id=self.id.cpu().numpy())
+        if self.q is not None:
+            out["q"] = self.q.cpu().numpy()
+        return out
+
+
+class Context:
+    """One operator instance (pc_init). All calls run on ``stream`` (default: torch's current)."""
+
+    def __init__(self, n_max, ne, degree, sigma, restitution, reach_hint, cutoff_sigmas=3.0, cand_cap=16,
+                 stream=None):
+        lib = library()
+        if stream is None:
+            stream = torch.cuda.current_stream()
+        self.stream = stream
+        self.cfg = PcConfig(int(n_max), int(ne), int(degree), float(sigma), float(cutoff_sigmas), 0,
+                            float(restitution), float(reach_hint), int(cand_cap), c_p(stream.cuda_stream))
+        h = c_p()
+        st = lib.pc_init(ctypes.byref(h), ctypes.byref(self.cfg))
+        if st != PC_OK:
+            raise PcError(st, "pc_init failed")
+        self._h = h
+        self.n1 = degree + 1
+        self.ne = ne
+
+    def _check(self, st):
+        if st != PC_OK:
+            raise PcError(st, library().pc_last_error(self._h).decode())
+
+    def collide(self, src, dst, dt):
+        """One collision step src -> dst (distinct states, same n)."""
+        a, b = src.struct(), dst.struct()
+        self._check(library().pc_collide(self._h, ctypes.byref(a), ctypes.byref(b), float(dt)))
+
+    def project(self, state, field):
+        """field[ne^3, 4, n1^3] (float64, CUDA) <- projection of state.q at state.x."""
+        nel = self.ne ** 3
+        if tuple(field.shape) != (nel, 4, self.n1 ** 3) or field.dtype != torch.float64 or not field.is_contiguous():
+            raise ValueError("field must be contiguous float64 of shape (%d, 4, %d)" % (nel, self.n1 ** 3))
+        s = state.struct()
+        self._check(library().pc_project(self._h, ctypes.byref(s), _ptr(field)))
+
+    def new_field(self):
+        return torch.empty(self.ne ** 3, 4, self.n1 ** 3, dtype=torch.float64, device="cuda")
+
+    def pairs(self):
+        """Pairs of the last collide: (ids[k, 2] smaller first, t[k]) sorted by the smaller id."""
+        n = c_i64()
+        self._check(library().pc_get_pairs(self._h, c_p(0), c_p(0), 0, ctypes.byref(n)))
+        ids = np.zeros((n.value, 2), np.int32)
+        t = np.zeros(n.value)
+        self._check(library().pc_get_pairs(self._h, ids.ctypes.data_as(c_p), t.ctypes.data_as(c_p), n.value,
+                                           ctypes.byref(n)))
+        return ids, t
+
+    def stats(self):
+        s = PcStats()
+        st = library().pc_get_stats(self._h, ctypes.byref(s))
+        d = {k: getattr(s, k) for k, _ in PcStats._fields_}
+        d["status"] = st
+        return d
+
+    def sync(self):
+        self._check(library().pc_sync(self._h))
+
+    def close(self):
+        if getattr(self, "_h", None):
+            library().pc_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def reach_of(r, v, dt, margin=1.05):
+    """2 r_max + 2 v_max dt with a margin: a good reach_hint for a workload."""
+    r = np.asarray(r)
+    v = np.asarray(v)
+    return margin * (2 * float(r.max()) + 2 * float(np.sqrt((v * v).sum(axis=0)).max()) * dt)

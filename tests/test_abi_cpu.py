@@ -1,0 +1,48 @@
+"""The C-ABI library builds, loads and exports every symbol its headers declare,
+and rejects invalid arguments before touching the GPU (no GPU needed)."""
+import ctypes
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _declared():
+    names = set()
+    inc = os.path.join(ROOT, "include")
+    for f in os.listdir(inc):
+        if f.endswith(".h"):
+            src = open(os.path.join(inc, f)).read()
+            src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+            names |= set(re.findall(r"\b(pc_[a-z0-9_]+)\s*\(", src))
+    return names
+
+
+def test_library_exports_declared_symbols():
+    from paper_2501_05340_gb300 import build
+    lib = ctypes.CDLL(build.build())
+    names = _declared()
+    assert {"pc_init", "pc_collide", "pc_project", "pc_destroy"} <= names
+    for s in sorted(names):
+        assert hasattr(lib, s), s
+
+
+def test_argument_validation_without_gpu():
+    from paper_2501_05340_gb300 import pc
+    lib = pc.library()
+    h = ctypes.c_void_p()
+    assert lib.pc_init(ctypes.byref(h), None) == pc.PC_EINVAL
+    bad = [dict(n_max=0), dict(ne=2), dict(degree=16), dict(sigma=0.0), dict(restitution=1.5),
+           dict(reach_hint=0.0), dict(cand_cap=33), dict(sigma=0.2)]  # sigma=0.2: cutoff beyond half the box
+    for b in bad:
+        kw = dict(n_max=100, ne=8, degree=3, sigma=0.02, cutoff_sigmas=3.0, cutoff_kind=0, restitution=0.9,
+                  reach_hint=0.04, cand_cap=16, stream=None)
+        kw.update(b)
+        cfg = pc.PcConfig(**kw)
+        assert lib.pc_init(ctypes.byref(h), ctypes.byref(cfg)) == pc.PC_EINVAL, b
+        assert not h.value
+    assert lib.pc_collide(None, None, None, 1e-3) == pc.PC_EINVAL
+    assert lib.pc_project(None, None, None) == pc.PC_EINVAL
+    lib.pc_destroy(None)

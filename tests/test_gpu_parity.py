@@ -1,0 +1,248 @@
+"""Parity of the CUDA path (through the C ABI) with the CPU oracle.
+
+Collisions: pair sets, contact times, positions and velocities bit-identical.
+Projection: fields within 1e-12 normwise per component (max |F - F_ref| / max |F_ref|).
+"""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2501_05340_gb300 import inputs
+from tests.gpu_helpers import by_id, field_err, oracle_pairs, quad_weights
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+if not torch.cuda.is_available():
+    pytest.skip("needs a CUDA GPU", allow_module_level=True)
+
+from paper_2501_05340_gb300 import pc  # noqa: E402
+
+FIELD_TOL = 1e-12
+
+
+def make_ctx(w, n, dt, **kw):
+    wl = w["workload"]
+    reach = pc.reach_of(w["r"], w["v"], dt)
+    return pc.Context(n, wl.ne, wl.degree, wl.sigma, w["e"], reach, cutoff_sigmas=wl.cutoff_sigmas, **kw)
+
+
+def compare_collide_step(ctx, src, dst, cur, dt, e):
+    """One GPU step src->dst against one oracle step on cur (id order). Returns the new oracle state."""
+    ctx.collide(src, dst, dt)
+    ctx.sync()
+    gids, gt = ctx.pairs()
+    x1, v1, partner, tc, k = oracle.collide_step(cur["x"], cur["v"], cur["r"], cur["m"], cur["id"], e, dt)
+    oids, ot = oracle_pairs(partner, tc, cur["id"])
+    assert np.array_equal(gids, oids), "pair sets differ"
+    assert np.array_equal(gt, ot), "contact times differ"
+    g = by_id(dst.numpy())
+    assert np.array_equal(g["id"], cur["id"])
+    assert np.array_equal(g["v"], v1), "velocities differ"
+    assert np.array_equal(g["x"], x1), "positions differ"
+    assert np.array_equal(g["r"], cur["r"]) and np.array_equal(g["m"], cur["m"])
+    if "q" in cur:
+        assert np.array_equal(g["q"], cur["q"])
+    nxt = dict(cur)
+    nxt["x"], nxt["v"] = x1, v1
+    return nxt, k
+
+
+def test_small_rollout_bit_identical():
+    """8192 spheres d=0.02, e=0.9, dt=2e-3: 100 steps, every step bit-identical."""
+    w = inputs.draw("small_8192", seed=0)
+    dt, e = w["dt"], w["e"]
+    a = pc.State.from_arrays(w)
+    b = pc.State.empty(a.n)
+    ctx = make_ctx(w, a.n, dt)
+    cur = {k: w[k] for k in ("x", "v", "r", "m", "id", "q")}
+    total = 0
+    for s in range(100):
+        cur, k = compare_collide_step(ctx, a, b, cur, dt, e)
+        total += k
+        a, b = b, a
+    assert total > 1000
+
+
+def test_dense_full_size_steps_bit_identical():
+    """1,048,576 spheres (phi ~0.19) at the full size: 3 steps, every pair and bit."""
+    w = inputs.draw("dense_1m", seed=1)
+    dt, e = w["dt"], w["e"]
+    a = pc.State.from_arrays(w)
+    b = pc.State.empty(a.n)
+    ctx = make_ctx(w, a.n, dt)
+    cur = {k: w[k] for k in ("x", "v", "r", "m", "id", "q")}
+    for s in range(3):
+        cur, k = compare_collide_step(ctx, a, b, cur, dt, e)
+        assert k > 20000
+        st = ctx.stats()
+        assert st["status"] == 0 and st["stencil"] == 1
+        a, b = b, a
+
+
+@pytest.mark.parametrize("n", [1, 2, 31, 33, 1007])
+def test_ragged_sizes(n):
+    w = inputs.draw("dense_1m", seed=3, n=n)
+    dt = 30 * w["dt"]
+    a = pc.State.from_arrays(w)
+    b = pc.State.empty(n)
+    ctx = make_ctx(w, n, dt)
+    cur = {k: w[k] for k in ("x", "v", "r", "m", "id", "q")}
+    for s in range(3):
+        cur, _ = compare_collide_step(ctx, a, b, cur, dt, w["e"])
+        a, b = b, a
+
+
+def test_empty_input():
+    w = inputs.draw("small_8192", n=16)
+    ctx = make_ctx(w, 16, w["dt"])
+    a, b = pc.State.empty(0), pc.State.empty(0)
+    ctx.collide(a, b, 1e-3)
+    f = ctx.new_field()
+    ctx.project(a, f)
+    ctx.sync()
+    assert float(f.abs().max()) == 0.0
+
+
+def test_pair_across_periodic_corner():
+    """Two spheres approaching through the corner of the periodic cube."""
+    x = np.array([[0.999, 0.001], [0.999, 0.001], [0.999, 0.001]])
+    v = np.array([[1.0, -1.0], [1.0, -1.0], [1.0, -1.0]])
+    d = dict(x=x, v=v, r=np.array([0.001, 0.001]), m=np.array([1.0, 2.0]), id=np.array([7, 3], np.int32),
+             q=np.ones((4, 2)))
+    a = pc.State.from_arrays(d)
+    b = pc.State.empty(2)
+    ctx = pc.Context(2, 8, 3, 0.02, 0.7, 0.01)
+    cur = dict(d)
+    cur = by_id(cur)
+    nxt, k = compare_collide_step(ctx, a, b, cur, 1e-3, 0.7)
+    assert k == 1
+
+
+def test_clustered_cells():
+    """Many particles in few cells (high occupancy, many candidates per particle)."""
+    w = inputs.draw("dense_1m", seed=5, n=3000)
+    w["x"] = w["x"] * 0.25  # compress into 1/64 of the box: overlapping pairs are ignored (c <= 0)
+    dt = 3 * w["dt"]
+    a = pc.State.from_arrays(w)
+    b = pc.State.empty(a.n)
+    ctx = make_ctx(w, a.n, dt, cand_cap=32)
+    cur = {k: w[k] for k in ("x", "v", "r", "m", "id", "q")}
+    for s in range(3):
+        cur, k = compare_collide_step(ctx, a, b, cur, dt, w["e"])
+        a, b = b, a
+
+
+def test_candidate_overflow_is_reported():
+    # particle 0 has two approaching partners; with cand_cap=1 the list overflows
+    x = np.array([[0.5, 0.503, 0.497], [0.5, 0.5, 0.5], [0.5, 0.5, 0.5]])
+    v = np.array([[0.0, -1.0, 1.0], [0.0, 0.0, 0.0], [0.0, 0.0, 0.0]])
+    d = dict(x=x, v=v, r=np.full(3, 0.001), m=np.ones(3), id=np.arange(3, dtype=np.int32))
+    a = pc.State.from_arrays(d, with_q=False)
+    b = pc.State.empty(3, with_q=False)
+    ctx = pc.Context(3, 8, 3, 0.02, 0.9, 0.01, cand_cap=1)
+    ctx.collide(a, b, 1e-2)
+    with pytest.raises(pc.PcError) as ei:
+        ctx.sync()
+    assert ei.value.status == pc.PC_ECAPACITY
+
+
+def test_invalid_positions_are_reported():
+    d = dict(x=np.array([[0.5, 1.5], [0.5, 0.5], [0.5, 0.5]]), v=np.zeros((3, 2)), r=np.full(2, 0.001),
+             m=np.ones(2), id=np.arange(2, dtype=np.int32))
+    a = pc.State.from_arrays(d, with_q=False)
+    b = pc.State.empty(2, with_q=False)
+    ctx = pc.Context(2, 8, 3, 0.02, 0.9, 0.01)
+    ctx.collide(a, b, 1e-3)
+    with pytest.raises(pc.PcError) as ei:
+        ctx.sync()
+    assert ei.value.status == pc.PC_EINVAL
+
+
+def test_determinism_bitwise():
+    w = inputs.draw("small_8192", seed=2)
+    outs = []
+    for rep in range(2):
+        a = pc.State.from_arrays(w)
+        b = pc.State.empty(a.n)
+        ctx = make_ctx(w, a.n, w["dt"])
+        f = ctx.new_field()
+        for s in range(10):
+            ctx.collide(a, b, w["dt"])
+            a, b = b, a
+        ctx.project(a, f)
+        ctx.sync()
+        outs.append((a.numpy(), f.cpu().numpy()))
+    for k in ("x", "v", "id"):
+        assert np.array_equal(outs[0][0][k], outs[1][0][k])
+    assert np.array_equal(outs[0][1], outs[1][1])
+
+
+# ----------------------------------------------------------------- projection
+
+def test_project_small_full_field():
+    w = inputs.draw("small_8192", seed=0)
+    wl = w["workload"]
+    a = pc.State.from_arrays(w)
+    ctx = make_ctx(w, a.n, w["dt"])
+    f = ctx.new_field()
+    ctx.project(a, f)
+    ctx.sync()
+    F = f.cpu().numpy()
+    R, Z = oracle.project(w["x"], w["q"], wl.ne, wl.degree, wl.sigma, wl.cutoff_sigmas)
+    err = field_err(F, R)
+    assert np.all(err <= FIELD_TOL), err
+    tot = np.einsum("ecg,g->c", F, quad_weights(wl.ne, wl.degree))
+    assert np.all(np.abs(tot - w["q"].sum(axis=1)) <= 1e-12 * np.abs(w["q"]).sum(axis=1))
+
+
+def test_project_after_rollout_matches_oracle():
+    """collide+project steps: the field of the GPU state equals the oracle's field of the oracle state."""
+    w = inputs.draw("small_8192", seed=4)
+    wl = w["workload"]
+    a = pc.State.from_arrays(w)
+    b = pc.State.empty(a.n)
+    ctx = make_ctx(w, a.n, w["dt"])
+    f = ctx.new_field()
+    cur = {k: w[k] for k in ("x", "v", "r", "m", "id", "q")}
+    for s in range(5):
+        cur, _ = compare_collide_step(ctx, a, b, cur, w["dt"], w["e"])
+        ctx.project(b, f)
+        a, b = b, a
+    ctx.sync()
+    R, _ = oracle.project(cur["x"], cur["q"], wl.ne, wl.degree, wl.sigma, wl.cutoff_sigmas)
+    assert np.all(field_err(f.cpu().numpy(), R) <= FIELD_TOL)
+
+
+def _neighbourhood_particles(x, elems, ne, rho):
+    e = np.minimum((x * ne).astype(np.int64), ne - 1)
+    keep = np.zeros(x.shape[1], bool)
+    for el in elems:
+        ex, ey, ez = el % ne, (el // ne) % ne, el // (ne * ne)
+        d = [((e[0] - ex + ne // 2) % ne) - ne // 2, ((e[1] - ey + ne // 2) % ne) - ne // 2,
+             ((e[2] - ez + ne // 2) % ne) - ne // 2]
+        keep |= (np.abs(d[0]) <= rho) & (np.abs(d[1]) <= rho) & (np.abs(d[2]) <= rho)
+    return keep
+
+
+@pytest.mark.parametrize("name,n", [("dense_1m", None), ("dense_1m", 50000)])
+def test_project_dense_sampled_elements(name, n):
+    """Full-size dense field: conservation everywhere, and sampled elements against the
+    oracle run on the particles that can reach them."""
+    w = inputs.draw(name, seed=6, n=n)
+    wl = w["workload"]
+    a = pc.State.from_arrays(w)
+    ctx = make_ctx(w, a.n, w["dt"])
+    f = ctx.new_field()
+    ctx.project(a, f)
+    ctx.sync()
+    F = f.cpu().numpy()
+    tot = np.einsum("ecg,g->c", F, quad_weights(wl.ne, wl.degree))
+    assert np.all(np.abs(tot - w["q"].sum(axis=1)) <= 1e-11 * np.abs(w["q"]).sum(axis=1))
+    rng = np.random.default_rng(0)
+    elems = rng.choice(wl.ne ** 3, 6, replace=False)
+    keep = _neighbourhood_particles(w["x"], elems, wl.ne, 1)
+    R, _ = oracle.project(w["x"][:, keep], w["q"][:, keep], wl.ne, wl.degree, wl.sigma, wl.cutoff_sigmas)
+    scale = np.abs(F).max(axis=(0, 2))
+    err = np.abs(F[elems] - R[elems]).max(axis=(0, 2)) / scale
+    assert np.all(err <= FIELD_TOL), err
