@@ -77,7 +77,21 @@ typedef struct {
   int32_t cells_per_side; /* collision cells per side */
   int32_t stencil;        /* neighbour cells searched on each side in the last step */
   int32_t device_status;  /* pc_status recorded on the GPU (PC_OK when clean) */
+  int64_t kernel_launches; /* kernels this context has launched since pc_init */
 } pc_stats;
+
+/* Phases timed by pc_set_timing / pc_get_timing. */
+typedef enum {
+  PC_PH_BIN = 0,     /* collide: cell keys, scan, scatter, per-cell order */
+  PC_PH_GATHER = 1,  /* collide: sorted copies of the state */
+  PC_PH_SEARCH = 2,  /* collide: contact search */
+  PC_PH_MATCH = 3,   /* collide: matching rounds */
+  PC_PH_RESPOND = 4, /* collide: response, advance, output state */
+  PC_PH_PBIN = 5,    /* project: element keys, scan, scatter, per-element order */
+  PC_PH_FACTORS = 6, /* project: normalised 1-D kernel factors */
+  PC_PH_DEPOSIT = 7, /* project: per-element gather of the deposit */
+  PC_NPHASE = 8
+} pc_phase;
 
 /* Create a context: validates cfg, builds the Gauss tables, chooses the collision
  * cells (side >= reach_hint, at least 3 per side) and allocates all scratch on
@@ -117,6 +131,17 @@ pc_status pc_get_stats(pc_ctx* ctx, pc_stats* out);
 /* Wait for the stream; returns PC_ECUDA on an asynchronous CUDA error, else the
  * device status recorded since the last pc_sync (and clears it). */
 pc_status pc_sync(pc_ctx* ctx);
+
+/* Per-phase GPU timers, the counterpart of the per-stage timers of Sec. 4.4. While
+ * on, every phase of pc_collide / pc_project records a pair of CUDA events on the
+ * context's stream (no synchronisation). Off by default. */
+pc_status pc_set_timing(pc_ctx* ctx, int on);
+
+/* HOST outputs: ms[PC_NPHASE] summed phase durations and count[PC_NPHASE] recorded
+ * phase instances since the previous call (either may be NULL); clears the records.
+ * Records beyond 4096 phase instances between two calls are dropped (count stops).
+ * Waits for the stream. */
+pc_status pc_get_timing(pc_ctx* ctx, double* ms, int64_t* count);
 
 /* Message of the last failure on this context (static storage of the context). */
 const char* pc_last_error(const pc_ctx* ctx);

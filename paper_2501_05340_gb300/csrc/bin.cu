@@ -112,21 +112,25 @@ __global__ void k_bin_order(int64_t nbins, const int32_t* __restrict__ start, co
 
 }  // namespace
 
-cudaError_t pc_exclusive_scan(const int32_t* in, int32_t* out, int64_t n, int32_t* blocksums, cudaStream_t s) {
+cudaError_t pc_exclusive_scan(const int32_t* in, int32_t* out, int64_t n, int32_t* blocksums, cudaStream_t s,
+                              int64_t* launches) {
   const int64_t nb = (n + PC_SCAN_TILE - 1) / PC_SCAN_TILE;
   if (nb == 0) return cudaMemsetAsync(out, 0, sizeof(int32_t), s);
   k_scan_reduce<<<(unsigned)nb, kScanThreads, 0, s>>>(in, n, blocksums);
   k_scan_blocksums<<<1, kScanThreads, 0, s>>>(blocksums, nb, out + n);
   k_scan_apply<<<(unsigned)nb, kScanThreads, 0, s>>>(in, out, n, blocksums);
+  *launches += 3;
   return cudaGetLastError();
 }
 
 cudaError_t pc_bin_finish(int64_t n, int64_t nbins, const int32_t* key, const int32_t* slot, const int32_t* id,
-                          int32_t* cnt, int32_t* start, int32_t* blocksums, int32_t* perm, cudaStream_t s) {
-  PC_CUDA_TRY(pc_exclusive_scan(cnt, start, nbins, blocksums, s));
+                          int32_t* cnt, int32_t* start, int32_t* blocksums, int32_t* perm, cudaStream_t s,
+                          int64_t* launches) {
+  PC_CUDA_TRY(pc_exclusive_scan(cnt, start, nbins, blocksums, s, launches));
   if (n > 0) {
     k_bin_scatter<<<pc_blocks(n, 256), 256, 0, s>>>(n, key, slot, start, perm);
     k_bin_order<<<pc_blocks(nbins, 256), 256, 0, s>>>(nbins, start, id, perm);
+    *launches += 2;
   }
   return cudaGetLastError();
 }

@@ -480,12 +480,23 @@ pc_status pc_collide_impl(pc_ctx* ctx, const pc_particles* in, pc_particles* out
   if (e == cudaSuccess && n == 0) return PC_OK;
   if (e == cudaSuccess) e = cudaMemsetAsync(ctx->cnt, 0, sizeof(int32_t) * (size_t)ctx->ncell, st);
   if (e != cudaSuccess) goto fail;
-  k_collide_keys<<<pc_blocks(n, 256), 256, 0, st>>>(n, in->x, in->v, in->r, in->m, ctx->nc, ctx->key, ctx->slot,
-                                                     ctx->cnt, ctx->counters);
-  e = pc_bin_finish(n, ctx->ncell, ctx->key, ctx->slot, in->id, ctx->cnt, ctx->start, ctx->blocksums, ctx->perm, st);
+  {
+    const int tb = pc_phase_begin(ctx, PC_PH_BIN);
+    k_collide_keys<<<pc_blocks(n, 256), 256, 0, st>>>(n, in->x, in->v, in->r, in->m, ctx->nc, ctx->key, ctx->slot,
+                                                       ctx->cnt, ctx->counters);
+    ctx->launches += 1;
+    e = pc_bin_finish(n, ctx->ncell, ctx->key, ctx->slot, in->id, ctx->cnt, ctx->start, ctx->blocksums, ctx->perm, st,
+                      &ctx->launches);
+    pc_phase_end(ctx, tb);
+  }
   if (e != cudaSuccess) goto fail;
-  k_collide_gather<<<pc_blocks(n, 256), 256, 0, st>>>(n, ctx->perm, in->x, in->v, in->r, in->id, ctx->sx, ctx->sv,
-                                                       ctx->sr, ctx->sid, ctx->sxf, ctx->svf, ctx->srf);
+  {
+    const int tg = pc_phase_begin(ctx, PC_PH_GATHER);
+    k_collide_gather<<<pc_blocks(n, 256), 256, 0, st>>>(n, ctx->perm, in->x, in->v, in->r, in->id, ctx->sx, ctx->sv,
+                                                         ctx->sr, ctx->sid, ctx->sxf, ctx->svf, ctx->srf);
+    ctx->launches += 1;
+    pc_phase_end(ctx, tg);
+  }
   {
     SearchArgs A;
     A.n = n;
@@ -505,7 +516,10 @@ pc_status pc_collide_impl(pc_ctx* ctx, const pc_particles* in, pc_particles* out
     A.ncand = ctx->ncand;
     A.best = ctx->best;
     A.counters = ctx->counters;
+    const int ts = pc_phase_begin(ctx, PC_PH_SEARCH);
     k_search<<<pc_blocks(n, 256), 256, 0, st>>>(A);
+    ctx->launches += 1;
+    pc_phase_end(ctx, ts);
   }
   {
     MatchArgs M;
@@ -523,8 +537,11 @@ pc_status pc_collide_impl(pc_ctx* ctx, const pc_particles* in, pc_particles* out
     M.pair_hi = ctx->pair_hi;
     M.pair_t = ctx->pair_t;
     M.counters = ctx->counters;
+    const int tm = pc_phase_begin(ctx, PC_PH_MATCH);
     k_match_first<<<pc_blocks(n, 256), 256, 0, st>>>(M);
     k_match_finish<<<1, kFinishThreads, 0, st>>>(M);
+    ctx->launches += 2;
+    pc_phase_end(ctx, tm);
   }
   {
     RespondArgs R;
@@ -546,7 +563,10 @@ pc_status pc_collide_impl(pc_ctx* ctx, const pc_particles* in, pc_particles* out
     R.m_out = out->m;
     R.q_out = in->q ? out->q : nullptr;
     R.id_out = out->id;
+    const int tr = pc_phase_begin(ctx, PC_PH_RESPOND);
     k_respond<<<pc_blocks(n, 256), 256, 0, st>>>(R);
+    ctx->launches += 1;
+    pc_phase_end(ctx, tr);
   }
   e = cudaGetLastError();
   if (e == cudaSuccess) return PC_OK;

@@ -68,6 +68,10 @@ void free_all(pc_ctx* c) {
   for (void* p : ptrs)
     if (p) cudaFree(p);
   if (c->h_counters) cudaFreeHost(c->h_counters);
+  if (c->ev) {
+    for (int i = 0; i < 2 * PC_EVPOOL; ++i) cudaEventDestroy(c->ev[i]);
+    free(c->ev);
+  }
 }
 
 bool particles_ok(const pc_particles* p, int64_t n_max) {
@@ -218,6 +222,7 @@ pc_status pc_get_stats(pc_ctx* ctx, pc_stats* out) {
   out->cells_per_side = ctx->nc;
   out->stencil = (int32_t)h[CNT_STENCIL];
   out->device_status = (int32_t)h[CNT_STATUS];
+  out->kernel_launches = ctx->launches;
   return (pc_status)h[CNT_STATUS];
 }
 
@@ -243,6 +248,42 @@ pc_status pc_get_pairs(pc_ctx* ctx, int32_t* ids, double* t, int64_t cap, int64_
     t[a] = tt[order[a]];
   }
   *npairs = (int64_t)np;
+  return PC_OK;
+}
+
+pc_status pc_set_timing(pc_ctx* ctx, int on) {
+  if (!ctx) return PC_EINVAL;
+  if (on && !ctx->ev) {
+    ctx->ev = (cudaEvent_t*)calloc(2 * PC_EVPOOL, sizeof(cudaEvent_t));
+    if (!ctx->ev) return fail(ctx, PC_ENOMEM, "pc_set_timing: out of host memory");
+    for (int i = 0; i < 2 * PC_EVPOOL; ++i)
+      if (cudaEventCreate(&ctx->ev[i]) != cudaSuccess) {
+        for (int k = 0; k < i; ++k) cudaEventDestroy(ctx->ev[k]);
+        free(ctx->ev);
+        ctx->ev = nullptr;
+        return fail(ctx, PC_ECUDA, "pc_set_timing: cudaEventCreate failed");
+      }
+  }
+  ctx->timing = on ? 1 : 0;
+  return PC_OK;
+}
+
+pc_status pc_get_timing(pc_ctx* ctx, double* ms, int64_t* count) {
+  if (!ctx) return PC_EINVAL;
+  if (ms)
+    for (int p = 0; p < PC_NPHASE; ++p) ms[p] = 0.0;
+  if (count)
+    for (int p = 0; p < PC_NPHASE; ++p) count[p] = 0;
+  if (cudaStreamSynchronize(ctx->stream) != cudaSuccess) return fail(ctx, PC_ECUDA, "pc_get_timing: CUDA error");
+  for (int i = 0; i < ctx->nrec; ++i) {
+    float t = 0.f;
+    if (cudaEventElapsedTime(&t, ctx->ev[2 * i], ctx->ev[2 * i + 1]) != cudaSuccess)
+      return fail(ctx, PC_ECUDA, "pc_get_timing: cudaEventElapsedTime failed");
+    const int p = ctx->rec_phase[i];
+    if (ms) ms[p] += t;
+    if (count) count[p] += 1;
+  }
+  ctx->nrec = 0;
   return PC_OK;
 }
 

@@ -22,6 +22,8 @@ enum {
   CNT_N
 };
 
+#define PC_EVPOOL 4096
+
 struct pc_ctx {
   pc_config cfg;
   cudaStream_t stream;
@@ -56,18 +58,38 @@ struct pc_ctx {
   double* sq;   // [4][n_max] sources, sorted order
   // Legendre-Gauss nodes and weights (passed to the kernels as arguments)
   double eta[16], w[16];
+  // per-phase timers (pc_set_timing) and the launch counter
+  int timing;
+  cudaEvent_t* ev;  // [2 * PC_EVPOOL], created when timing is first switched on
+  int nrec;
+  unsigned char rec_phase[PC_EVPOOL];
+  int64_t launches;
   char err[256];
 };
+
+// Start a timed phase: returns the record index, or -1 when timing is off or full.
+static inline int pc_phase_begin(pc_ctx* c, int phase) {
+  if (!c->timing || !c->ev || c->nrec >= PC_EVPOOL) return -1;
+  const int i = c->nrec++;
+  c->rec_phase[i] = (unsigned char)phase;
+  cudaEventRecord(c->ev[2 * i], c->stream);
+  return i;
+}
+static inline void pc_phase_end(pc_ctx* c, int i) {
+  if (i >= 0) cudaEventRecord(c->ev[2 * i + 1], c->stream);
+}
 
 // ---- binning (bin.cu) --------------------------------------------------------
 // Exclusive scan of in[0..n) into out[0..n], out[n] = total. blocksums holds
 // ceil(n / PC_SCAN_TILE) entries.
 #define PC_SCAN_TILE 2048
-cudaError_t pc_exclusive_scan(const int32_t* in, int32_t* out, int64_t n, int32_t* blocksums, cudaStream_t s);
+cudaError_t pc_exclusive_scan(const int32_t* in, int32_t* out, int64_t n, int32_t* blocksums, cudaStream_t s,
+                              int64_t* launches);
 // Given key[i] (bin) and slot[i] (rank inside its bin in arbitrary order), write the
 // permutation sorted by (bin, id): perm[k] = input index of the k-th particle.
 cudaError_t pc_bin_finish(int64_t n, int64_t nbins, const int32_t* key, const int32_t* slot, const int32_t* id,
-                          int32_t* cnt, int32_t* start, int32_t* blocksums, int32_t* perm, cudaStream_t s);
+                          int32_t* cnt, int32_t* start, int32_t* blocksums, int32_t* perm, cudaStream_t s,
+                          int64_t* launches);
 
 // ---- collide (collide.cu) ----------------------------------------------------
 pc_status pc_collide_impl(pc_ctx* ctx, const pc_particles* in, pc_particles* out, double dt);

@@ -189,10 +189,16 @@ pc_status pc_project_impl(pc_ctx* ctx, const pc_particles* p, double* field) {
   const int64_t nel = (int64_t)ne * ne * ne;
   cudaError_t e = cudaMemsetAsync(ctx->cnt, 0, sizeof(int32_t) * (size_t)nel, st);
   if (e != cudaSuccess) goto fail;
-  if (n > 0) {
-    k_elem_keys<<<pc_blocks(n, 256), 256, 0, st>>>(n, p->x, ne, ctx->key, ctx->slot, ctx->cnt, ctx->counters);
+  {
+    const int tb = pc_phase_begin(ctx, PC_PH_PBIN);
+    if (n > 0) {
+      k_elem_keys<<<pc_blocks(n, 256), 256, 0, st>>>(n, p->x, ne, ctx->key, ctx->slot, ctx->cnt, ctx->counters);
+      ctx->launches += 1;
+    }
+    e = pc_bin_finish(n, nel, ctx->key, ctx->slot, p->id, ctx->cnt, ctx->start, ctx->blocksums, ctx->perm, st,
+                      &ctx->launches);
+    pc_phase_end(ctx, tb);
   }
-  e = pc_bin_finish(n, nel, ctx->key, ctx->slot, p->id, ctx->cnt, ctx->start, ctx->blocksums, ctx->perm, st);
   if (e != cudaSuccess) goto fail;
   if (n > 0) {
     FactorArgs F;
@@ -213,7 +219,10 @@ pc_status pc_project_impl(pc_ctx* ctx, const pc_particles* p, double* field) {
     F.q = p->q;
     F.fac = ctx->fac;
     F.sq = ctx->sq;
+    const int tf = pc_phase_begin(ctx, PC_PH_FACTORS);
     k_proj_factors<<<pc_blocks(n, 128), 128, 0, st>>>(F);
+    ctx->launches += 1;
+    pc_phase_end(ctx, tf);
   }
   {
     GatherArgs G;
@@ -232,7 +241,10 @@ pc_status pc_project_impl(pc_ctx* ctx, const pc_particles* p, double* field) {
     G.field = field;
     e = cudaFuncSetAttribute(k_proj_gather, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) goto fail;
+    const int td = pc_phase_begin(ctx, PC_PH_DEPOSIT);
     k_proj_gather<<<(unsigned)nel, 32 * G.nwarps, smem, st>>>(G);
+    ctx->launches += 1;
+    pc_phase_end(ctx, td);
   }
   e = cudaGetLastError();
   if (e == cudaSuccess) return PC_OK;

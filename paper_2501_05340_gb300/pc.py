@@ -33,7 +33,9 @@ class PcParticles(ctypes.Structure):
 class PcStats(ctypes.Structure):
     _fields_ = [("pairs", c_i64), ("candidates", c_i64), ("worklist", c_i64), ("rounds", c_i64),
                 ("fp64_solves", c_i64), ("max_candidates", c_i64), ("cells_per_side", c_i32), ("stencil", c_i32),
-                ("device_status", c_i32)]
+                ("device_status", c_i32), ("kernel_launches", c_i64)]
+
+PHASES = ("bin", "gather", "search", "match", "respond", "pbin", "factors", "deposit")
 
 
 class PcError(RuntimeError):
@@ -57,11 +59,14 @@ def library():
         lib.pc_get_pairs.argtypes = [c_p, c_p, c_p, c_i64, ctypes.POINTER(c_i64)]
         lib.pc_get_stats.argtypes = [c_p, ctypes.POINTER(PcStats)]
         lib.pc_sync.argtypes = [c_p]
+        lib.pc_set_timing.argtypes = [c_p, ctypes.c_int]
+        lib.pc_get_timing.argtypes = [c_p, c_p, c_p]
         lib.pc_last_error.argtypes = [c_p]
         lib.pc_last_error.restype = ctypes.c_char_p
         lib.pc_destroy.argtypes = [c_p]
         lib.pc_destroy.restype = None
-        for f in ("pc_init", "pc_collide", "pc_project", "pc_get_pairs", "pc_get_stats", "pc_sync"):
+        for f in ("pc_init", "pc_collide", "pc_project", "pc_get_pairs", "pc_get_stats", "pc_sync", "pc_set_timing",
+                  "pc_get_timing"):
             getattr(lib, f).restype = ctypes.c_int
         _lib = lib
     return _lib
@@ -177,6 +182,16 @@ class Context:
         d = {k: getattr(s, k) for k, _ in PcStats._fields_}
         d["status"] = st
         return d
+
+    def set_timing(self, on=True):
+        self._check(library().pc_set_timing(self._h, 1 if on else 0))
+
+    def timing(self):
+        """{phase: (ms summed, instances)} since the previous call (waits for the stream)."""
+        ms = np.zeros(len(PHASES))
+        cnt = np.zeros(len(PHASES), np.int64)
+        self._check(library().pc_get_timing(self._h, ms.ctypes.data_as(c_p), cnt.ctypes.data_as(c_p)))
+        return {p: (float(ms[i]), int(cnt[i])) for i, p in enumerate(PHASES)}
 
     def sync(self):
         self._check(library().pc_sync(self._h))
