@@ -1,8 +1,9 @@
 """Compile the CUDA library ``libpc.so`` in-tree for sm_103a (GB300).
 
 Each translation unit is compiled in parallel with its own flags, then linked:
-``collide.cu`` without fused multiply-add (bit-exact FP64 contact solve and
-response); the others with the default contraction.
+``collide.cu`` and ``project.cu`` without implicit fused multiply-add (bit-exact
+FP64 contact solve and response; double-float arithmetic that places every FMA
+explicitly); the others with the default contraction.
 """
 import os
 import subprocess
@@ -21,7 +22,7 @@ UNITS = {
     "pc_abi.cu": [],
     "bin.cu": [],
     "collide.cu": ["-fmad=false"],
-    "project.cu": [],
+    "project.cu": ["-fmad=false"],
 }
 
 

@@ -95,7 +95,8 @@ pc_status pc_init(pc_ctx** out, const pc_config* cfg) {
   if (!(c.reach_hint > 0.0) || c.cand_cap < 0 || c.cand_cap > 32) return PC_EINVAL;
   const double rc = c.cutoff_sigmas * c.sigma;
   const int rho = (int)ceil(rc * c.ne * (1.0 + 1e-12));
-  if (rho < 1 || 2 * rho + 1 > c.ne || !(rc < 0.5)) return PC_EINVAL;
+  if (rho < 1 || rho > 2 || 2 * rho + 1 > c.ne || !(rc < 0.5)) return PC_EINVAL;
+  if ((2 * rho + 1) * (c.degree + 1) > 64) return PC_EINVAL;
 
   pc_ctx* ctx = (pc_ctx*)calloc(1, sizeof(pc_ctx));
   if (!ctx) return PC_ENOMEM;
@@ -117,6 +118,23 @@ pc_status pc_init(pc_ctx** out, const pc_config* cfg) {
   ctx->h = 1.0 / c.ne;
   ctx->cap = c.cand_cap == 0 ? 16 : c.cand_cap;
   gauss_rule(ctx->n1, ctx->eta, ctx->w);
+  {
+    // exp2(j/64) and ln(2)/64 split into floats for the df32 exponential
+    DfExpTable& T = ctx->exp_tab;
+    for (int j = 0; j < 64; ++j) {
+      const double v = exp2((double)j / 64.0);
+      T.th[j] = (float)v;
+      T.tl[j] = (float)(v - (double)T.th[j]);
+    }
+    const double L = log(2.0) / 64.0;
+    int ex = 0;
+    const double m = frexp(L, &ex);                 // L = m 2^ex, m in [0.5, 1)
+    const double L1 = ldexp(floor(ldexp(m, 11)), ex - 11);  // 11 significant bits
+    T.L1 = (float)L1;
+    T.L2 = (float)(L - L1);
+    T.L3 = (float)((L - L1) - (double)T.L2);
+    T.inv = (float)(64.0 / log(2.0));
+  }
 
   const int64_t n = c.n_max;
   const int64_t nel = (int64_t)c.ne * c.ne * c.ne;

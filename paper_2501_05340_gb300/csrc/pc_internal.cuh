@@ -5,6 +5,7 @@
 #include <stdint.h>
 #include <stdio.h>
 
+#include "df32.cuh"
 #include "pc.h"
 
 // Device counters of one pc_collide / pc_project (64-bit, atomically updated).
@@ -54,8 +55,9 @@ struct pc_ctx {
   unsigned long long* counters;    // device [CNT_N]
   unsigned long long* h_counters;  // pinned host copy
   // projection scratch
-  double* fac;  // [3][win][n_max] normalised 1-D kernel factors, sorted order
-  double* sq;   // [4][n_max] sources, sorted order
+  float2* fac;  // [3][win][n_max] normalised 1-D kernel factors (df32), sorted order
+  float2* sq;   // [4][n_max] sources times (2/h)^3 (df32), sorted order
+  DfExpTable exp_tab;
   // Legendre-Gauss nodes and weights (passed to the kernels as arguments)
   double eta[16], w[16];
   // per-phase timers (pc_set_timing) and the launch counter

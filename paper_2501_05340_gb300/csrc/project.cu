@@ -16,6 +16,9 @@
 // order is canonical (by element, then id).
 #include <math.h>
 
+#include <string.h>
+
+#include "df32.cuh"
 #include "pc_internal.cuh"
 
 namespace {
@@ -50,22 +53,34 @@ __global__ void k_elem_keys(int64_t n, const double* __restrict__ x, int ne, int
   slot[i] = atomicAdd(&cnt[k], 1);
 }
 
+constexpr int kMaxWin = 64;  // (2 rho + 1) n1 <= 64 (checked by pc_init)
+
 struct FactorArgs {
   int64_t n;
   int ne, n1, rho, win;
-  double h, rc, inv2s2;
-  double eta[16], w[16];  // Legendre-Gauss nodes and weights on [-1, 1]
+  double h, rc;
+  float rce;           // cutoff radius in element units (rc ne), float
+  f2 c2;               // h^2 / (2 sigma^2): exponent factor for distances in element units
+  f2 scale;            // (2/h)^3
+  f2 sw[kMaxWin];      // window node offsets o + (eta_i + 1)/2 (element units), o = w/n1 - rho
+  f2 wq[16];           // Gauss weights
+  double eta[16];      // Gauss nodes (for the exact FP64 cutoff decision)
+  DfExpTable tab;
   const int32_t* perm;
   const double* x;
   const double* q;
-  double* fac;  // [3][win][n]
-  double* sq;   // [4][n]
+  float2* fac;  // [3][win][n] normalised 1-D factors k_a / Z_a (df32)
+  float2* sq;   // [4][n] sources times (2/h)^3 (df32)
 };
 
-// fac[a][w][k] = k_a(X_w - x_a) / Za for the window node w = (o + rho) n1 + i of
-// element (own element + o), with k_a(d) = exp(-d^2 / (2 sigma^2)) for |d| <= rc
-// and 0 beyond; Za = sum_w w_i k_a.
-__global__ void k_proj_factors(FactorArgs F) {
+// fac[a][w][k] = k_a(X_w - x_a) / Z_a over the window nodes w of the particle's
+// own element and its rho neighbours on each side, k_a(d) = exp(-d^2/(2 sigma^2))
+// for |d| <= rc (0 beyond), Z_a = sum_w w_i k_a. Distances are taken in element
+// units relative to the own element (one FP64 subtraction per particle and axis),
+// then everything runs in df32. A node whose df32 distance is within 1e-5
+// relative of the cutoff is re-decided with the FP64 expression of the plain
+// definition, so both sides include exactly the same nodes.
+__global__ void __launch_bounds__(128) k_proj_factors(FactorArgs F) {
   const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   const int64_t n = F.n;
   if (k >= n) return;
@@ -73,113 +88,219 @@ __global__ void k_proj_factors(FactorArgs F) {
   for (int a = 0; a < 3; ++a) {
     const double xa = F.x[a * n + p];
     const int ea = cell_of(xa, F.ne);
-    double Z = 0.0;
+    const f2 t = df_from_double(xa * (double)F.ne - (double)ea);
+    f2 Z = {0.0f, 0.0f};
     for (int w = 0; w < F.win; ++w) {
-      const int o = w / F.n1 - F.rho, i = w % F.n1;
-      const int ge = wrapi(ea + o, F.ne);
-      const double X = ((double)ge + 0.5 * (F.eta[i] + 1.0)) * F.h;
-      const double d = minimg(X - xa);
-      const double f = fabs(d) <= F.rc ? exp(-d * d * F.inv2s2) : 0.0;
-      F.fac[((int64_t)a * F.win + w) * n + k] = f;
-      Z += F.w[i] * f;
+      const int i = w % F.n1;
+      const f2 dl = df_add(F.sw[w], df_neg(t));
+      const float ad = fabsf(dl.h);
+      bool inside;
+      if (fabsf(ad - F.rce) > 1e-5f * F.rce) {
+        inside = ad < F.rce;
+      } else {
+        const int o = w / F.n1 - F.rho;
+        const int ge = wrapi(ea + o, F.ne);
+        const double X = ((double)ge + 0.5 * (F.eta[i] + 1.0)) * F.h;
+        inside = fabs(minimg(X - xa)) <= F.rc;
+      }
+      f2 f = {0.0f, 0.0f};
+      if (inside) {
+        f2 d2 = two_prod(dl.h, dl.h);
+        d2.l = fmaf(2.0f * dl.h, dl.l, d2.l);
+        d2 = fast_two_sum(d2.h, d2.l);
+        f = df_exp_neg(df_neg(df_mul(d2, F.c2)), F.tab);
+        Z = df_add(Z, df_mul(f, F.wq[i]));
+      }
+      F.fac[((int64_t)a * F.win + w) * n + k] = make_float2(f.h, f.l);
     }
-    const double iz = 1.0 / Z;
-    for (int w = 0; w < F.win; ++w) F.fac[((int64_t)a * F.win + w) * n + k] *= iz;
+    const f2 rz = df_recip(Z);
+    for (int w = 0; w < F.win; ++w) {
+      float2* slot = &F.fac[((int64_t)a * F.win + w) * n + k];
+      const float2 v = *slot;
+      if (v.x != 0.0f) {
+        const f2 r = df_mul({v.x, v.y}, rz);
+        *slot = make_float2(r.h, r.l);
+      }
+    }
   }
 #pragma unroll
-  for (int c = 0; c < 4; ++c) F.sq[c * n + k] = F.q[c * n + p];
+  for (int c = 0; c < 4; ++c) {
+    const f2 qs = df_mul(df_from_double(F.q[c * n + p]), F.scale);
+    F.sq[c * n + k] = make_float2(qs.h, qs.l);
+  }
 }
 
-struct GatherArgs {
+struct DepositArgs {
   int64_t n;
-  int ne, n1, rho, win, nwarps;
-  double scale;  // (2/h)^3
+  int ne, n1, rho, win, nwarps, batch;
   const int32_t* start;
-  const double* fac;
-  const double* sq;
+  const float2* fac;
+  const float2* sq;
   double* field;
 };
 
-__global__ void k_proj_gather(GatherArgs G) {
-  extern __shared__ double smem[];
-  const int n1 = G.n1, nodes = n1 * n1 * n1, NW = G.nwarps;
+// floor(u / d) for 0 <= u < 2^16 / d, d <= 16, with M = ceil(2^16 / d).
+__device__ __forceinline__ int div_small(int u, int M) { return (u * M) >> 16; }
+
+// One CTA per element. The particles of the (2 rho + 1)^3 neighbouring elements are
+// taken in batches; batch b goes to warp b mod NW, whose lanes first stage one
+// particle each (factor slices on this element's nodes, support box, the products
+// A[c][i] = q_c kx_i and YZ[j][k] = ky_j kz_k in df32), then all lanes sweep the
+// support box of each staged particle in turn, adding A YZ onto a warp-private
+// df32 accumulator in shared memory (TwoSum on the high part, the errors summed in
+// the low part). The warps' accumulators are added in a fixed order at the end,
+// so the result does not depend on scheduling.
+__global__ void k_proj_deposit(DepositArgs G) {
+  extern __shared__ float2 sm2[];
+  const int n1 = G.n1, nodes = n1 * n1 * n1, NW = G.nwarps, BS = G.batch;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  double* acc = smem;                               // [NW][4][nodes]
-  double* stage = smem + (size_t)NW * 4 * nodes;    // [NW][3*16 + 4]
-  double* my = acc + (size_t)warp * 4 * nodes;
-  double* fs = stage + warp * 52;
-  for (int a = threadIdx.x; a < NW * 4 * nodes; a += blockDim.x) acc[a] = 0.0;
-  __syncthreads();
+  const int per_p = 4 * n1 + n1 * n1;                   // staged float2 per particle
+  float2* acc = sm2;                                     // [NW][4][nodes]
+  float2* stage = sm2 + (size_t)NW * 4 * nodes;          // [NW][BS][per_p]
+  int* boxes = (int*)(stage + (size_t)NW * BS * per_p);  // [NW][BS][2]
+  int* pre = boxes + NW * BS * 2;                        // [(2 rho+1)^3 + 1] prefix of range sizes
+  int* rbeg = pre + 126;                                 // [(2 rho+1)^3] range starts
+  float2* my = acc + (size_t)warp * 4 * nodes;
+  float2* st = stage + (size_t)warp * BS * per_p;
+  int* bx = boxes + warp * BS * 2;
+  for (int a = threadIdx.x; a < NW * 4 * nodes; a += blockDim.x) acc[a] = make_float2(0.0f, 0.0f);
   const int64_t n = G.n;
-  const int ne = G.ne;
+  const int ne = G.ne, rho = G.rho, span = 2 * rho + 1, nrange = span * span * span;
   const int e = blockIdx.x;
   const int ex = e % ne, ey = (e / ne) % ne, ez = e / (ne * ne);
-  int turn = 0;  // running particle count over the neighbour ranges, split round-robin over warps
-  for (int dz = -G.rho; dz <= G.rho; ++dz)
-    for (int dy = -G.rho; dy <= G.rho; ++dy)
-      for (int dx = -G.rho; dx <= G.rho; ++dx) {
-        const int nb = (wrapi(ez + dz, ne) * ne + wrapi(ey + dy, ne)) * ne + wrapi(ex + dx, ne);
-        const int beg = G.start[nb], end = G.start[nb + 1];
-        // this element sits at offset -d in the window of a particle of element e + d
-        const int wx = (G.rho - dx) * n1, wy = (G.rho - dy) * n1, wz = (G.rho - dz) * n1;
-        for (int j = beg; j < end; ++j, ++turn) {
-          if (turn % NW != warp) continue;
-          for (int u = lane; u < 3 * n1; u += 32) {
-            const int a = u / n1, i = u % n1;
-            const int wa = a == 0 ? wx : (a == 1 ? wy : wz);
-            fs[a * 16 + i] = G.fac[((int64_t)a * G.win + wa + i) * n + j];
-          }
-          if (lane < 4) fs[48 + lane] = G.sq[(int64_t)lane * n + j];
-          __syncwarp();
-          int lo[3], cntv[3];
-#pragma unroll
-          for (int a = 0; a < 3; ++a) {
-            int l = n1, h = -1;
-            for (int i = 0; i < n1; ++i)
-              if (fs[a * 16 + i] != 0.0) {
-                l = min(l, i);
-                h = i;
-              }
-            lo[a] = l;
-            cntv[a] = h - l + 1;
-          }
-          if (cntv[0] > 0 && cntv[1] > 0 && cntv[2] > 0) {
-            const int nbox = cntv[0] * cntv[1] * cntv[2];
-            const double q0 = fs[48], q1 = fs[49], q2 = fs[50], q3 = fs[51];
-            for (int u = lane; u < nbox; u += 32) {
-              const int i = lo[0] + u % cntv[0];
-              const int jj = lo[1] + (u / cntv[0]) % cntv[1];
-              const int kk = lo[2] + u / (cntv[0] * cntv[1]);
-              const double wgt = (fs[i] * fs[16 + jj]) * fs[32 + kk];
-              const int g = (kk * n1 + jj) * n1 + i;
-              my[g] += q0 * wgt;
-              my[nodes + g] += q1 * wgt;
-              my[2 * nodes + g] += q2 * wgt;
-              my[3 * nodes + g] += q3 * wgt;
+  if (threadIdx.x == 0) {
+    int s = 0;
+    for (int r = 0; r < nrange; ++r) {
+      const int dx = r % span - rho, dy = (r / span) % span - rho, dz = r / (span * span) - rho;
+      const int nb = (wrapi(ez + dz, ne) * ne + wrapi(ey + dy, ne)) * ne + wrapi(ex + dx, ne);
+      const int b0 = G.start[nb], b1 = G.start[nb + 1];
+      pre[r] = s;
+      rbeg[r] = b0;
+      s += b1 - b0;
+    }
+    pre[nrange] = s;
+  }
+  __syncthreads();
+  const int total = pre[nrange];
+  const int nbatch = (total + BS - 1) / BS;
+  for (int b = warp; b < nbatch; b += NW) {
+    // ---- stage: lane l < BS takes particle b*BS + l
+    if (lane < BS) {
+      const int idx = b * BS + lane;
+      int box = 0, box2 = 0;
+      if (idx < total) {
+        int r = 0;
+        while (pre[r + 1] <= idx) ++r;
+        const int j = rbeg[r] + (idx - pre[r]);
+        const int dx = r % span - rho, dy = (r / span) % span - rho, dz = r / (span * span) - rho;
+        const int wo[3] = {(rho - dx) * n1, (rho - dy) * n1, (rho - dz) * n1};
+        int lo[3], cnt[3];
+        for (int a = 0; a < 3; ++a) {
+          int l = -1, h = -2;
+          for (int i = 0; i < n1; ++i) {
+            const float2 f = G.fac[((int64_t)a * G.win + wo[a] + i) * n + j];
+            if (f.x != 0.0f) {
+              if (l < 0) l = i;
+              h = i;
             }
           }
-          __syncwarp();
+          lo[a] = l < 0 ? 0 : l;
+          cnt[a] = h - l + 1 > 0 ? h - l + 1 : 0;
+        }
+        float2* sp = st + (size_t)lane * per_p;
+        if (cnt[0] && cnt[1] && cnt[2]) {
+          // A[c][ii] = q_c kx_(lo_x + ii)
+          for (int c = 0; c < 4; ++c) {
+            const float2 qv = G.sq[(int64_t)c * n + j];
+            for (int ii = 0; ii < cnt[0]; ++ii) {
+              const float2 f = G.fac[((int64_t)0 * G.win + wo[0] + lo[0] + ii) * n + j];
+              const f2 v = df_mul({qv.x, qv.y}, {f.x, f.y});
+              sp[c * n1 + ii] = make_float2(v.h, v.l);
+            }
+          }
+          // YZ[row], row = jj + cnt_y kk
+          for (int kk = 0; kk < cnt[2]; ++kk) {
+            const float2 fz = G.fac[((int64_t)2 * G.win + wo[2] + lo[2] + kk) * n + j];
+            for (int jj = 0; jj < cnt[1]; ++jj) {
+              const float2 fy = G.fac[((int64_t)1 * G.win + wo[1] + lo[1] + jj) * n + j];
+              const f2 v = df_mul({fy.x, fy.y}, {fz.x, fz.y});
+              sp[4 * n1 + jj + cnt[1] * kk] = make_float2(v.h, v.l);
+            }
+          }
+          box = lo[0] | (cnt[0] << 5) | (lo[1] << 10) | (cnt[1] << 15) | (lo[2] << 20) | (cnt[2] << 25);
+          box2 = 1;
         }
       }
+      bx[2 * lane] = box;
+      bx[2 * lane + 1] = box2;
+    }
+    __syncwarp();
+    // ---- sweep the support box of each staged particle
+    for (int q = 0; q < BS; ++q) {
+      if (!bx[2 * q + 1]) continue;
+      const int box = bx[2 * q];
+      const int lx = box & 31, cx = (box >> 5) & 31, ly = (box >> 10) & 31, cy = (box >> 15) & 31;
+      const int lz = (box >> 20) & 31, cz = (box >> 25) & 31;
+      const int nbox = cx * cy * cz;
+      const int Mx = (65536 + cx - 1) / cx, My = (65536 + cy - 1) / cy;
+      const float2* sp = st + (size_t)q * per_p;
+      for (int u = lane; u < nbox; u += 32) {
+        const int row = div_small(u, Mx);
+        const int ii = u - row * cx;
+        const int kk = div_small(row, My);
+        const int jj = row - kk * cy;
+        const int g = ((lz + kk) * n1 + ly + jj) * n1 + lx + ii;
+        const float2 yz = sp[4 * n1 + row];
+#pragma unroll
+        for (int c = 0; c < 4; ++c) {
+          const float2 a = sp[c * n1 + ii];
+          const float pp = a.x * yz.x;
+          float pe = fmaf(a.x, yz.x, -pp);
+          pe = fmaf(a.x, yz.y, pe);
+          pe = fmaf(a.y, yz.x, pe);
+          float2 S = my[c * nodes + g];
+          const f2 s = two_sum(S.x, pp);
+          S.x = s.h;
+          S.y += s.l + pe;
+          my[c * nodes + g] = S;
+        }
+      }
+    }
+    __syncwarp();
+  }
   __syncthreads();
   double* out = G.field + (int64_t)e * 4 * nodes;
   for (int a = threadIdx.x; a < 4 * nodes; a += blockDim.x) {
-    double s = 0.0;
-    for (int w = 0; w < NW; ++w) s += acc[(size_t)w * 4 * nodes + a];
-    out[a] = s * G.scale;
+    f2 s = {0.0f, 0.0f};
+    for (int w = 0; w < NW; ++w) {
+      const float2 v = acc[(size_t)w * 4 * nodes + a];
+      s = df_add(s, {v.x, v.y});
+    }
+    out[a] = df_to_double(s);
   }
 }
 
 }  // namespace
 
-static int gather_warps(int n1, size_t* smem) {
+static void deposit_shape(int n1, int rho, int* nwarps, int* batch, size_t* smem) {
   const size_t nodes = (size_t)n1 * n1 * n1;
-  const size_t per = (4 * nodes + 52) * sizeof(double);
-  int nw = (int)((200 * 1024) / per);
-  if (nw > 8) nw = 8;
-  if (nw < 1) nw = 1;
-  *smem = per * nw;
-  return nw;
+  const size_t per_p = 4 * (size_t)n1 + (size_t)n1 * n1;
+  const size_t budget = 200 * 1024;
+  const size_t fixed = (126 + 126) * sizeof(int) + 64;
+  static const int kWarps[] = {16, 12, 8, 6, 4, 2, 1};
+  for (int nw : kWarps)
+    for (int bs = 32; bs >= 8; bs /= 2) {
+      const size_t need = nw * (4 * nodes + bs * per_p) * sizeof(float2) + nw * bs * 2 * sizeof(int) + fixed;
+      if (need <= budget) {
+        *nwarps = nw;
+        *batch = bs;
+        *smem = need;
+        return;
+      }
+    }
+  *nwarps = 1;
+  *batch = 4;
+  *smem = (4 * nodes + 4 * per_p) * sizeof(float2) + 8 * sizeof(int) + fixed;
 }
 
 pc_status pc_project_impl(pc_ctx* ctx, const pc_particles* p, double* field) {
@@ -202,6 +323,7 @@ pc_status pc_project_impl(pc_ctx* ctx, const pc_particles* p, double* field) {
   if (e != cudaSuccess) goto fail;
   if (n > 0) {
     FactorArgs F;
+    memset(&F, 0, sizeof(F));
     F.n = n;
     F.ne = ne;
     F.n1 = ctx->n1;
@@ -209,11 +331,20 @@ pc_status pc_project_impl(pc_ctx* ctx, const pc_particles* p, double* field) {
     F.win = ctx->win;
     F.h = ctx->h;
     F.rc = ctx->cfg.cutoff_sigmas * ctx->cfg.sigma;
-    F.inv2s2 = 1.0 / (2.0 * ctx->cfg.sigma * ctx->cfg.sigma);
-    for (int i = 0; i < 16; ++i) {
-      F.eta[i] = i < ctx->n1 ? ctx->eta[i] : 0.0;
-      F.w[i] = i < ctx->n1 ? ctx->w[i] : 0.0;
+    F.rce = (float)(F.rc * ne);
+    const double c2 = ctx->h * ctx->h / (2.0 * ctx->cfg.sigma * ctx->cfg.sigma);
+    F.c2 = {(float)c2, (float)(c2 - (double)(float)c2)};
+    const double sc = 8.0 * (double)ne * ne * ne;
+    F.scale = {(float)sc, (float)(sc - (double)(float)sc)};
+    for (int w = 0; w < ctx->win; ++w) {
+      const double v = (double)(w / ctx->n1 - ctx->rho) + 0.5 * (ctx->eta[w % ctx->n1] + 1.0);
+      F.sw[w] = {(float)v, (float)(v - (double)(float)v)};
     }
+    for (int i = 0; i < ctx->n1; ++i) {
+      F.wq[i] = {(float)ctx->w[i], (float)(ctx->w[i] - (double)(float)ctx->w[i])};
+      F.eta[i] = ctx->eta[i];
+    }
+    F.tab = ctx->exp_tab;
     F.perm = ctx->perm;
     F.x = p->x;
     F.q = p->q;
@@ -225,24 +356,22 @@ pc_status pc_project_impl(pc_ctx* ctx, const pc_particles* p, double* field) {
     pc_phase_end(ctx, tf);
   }
   {
-    GatherArgs G;
+    DepositArgs G;
     G.n = n;
     G.ne = ne;
     G.n1 = ctx->n1;
     G.rho = ctx->rho;
     G.win = ctx->win;
     size_t smem = 0;
-    G.nwarps = gather_warps(ctx->n1, &smem);
-    const double s = 2.0 / ctx->h;
-    G.scale = s * s * s;
+    deposit_shape(ctx->n1, ctx->rho, &G.nwarps, &G.batch, &smem);
     G.start = ctx->start;
     G.fac = ctx->fac;
     G.sq = ctx->sq;
     G.field = field;
-    e = cudaFuncSetAttribute(k_proj_gather, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    e = cudaFuncSetAttribute(k_proj_deposit, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) goto fail;
     const int td = pc_phase_begin(ctx, PC_PH_DEPOSIT);
-    k_proj_gather<<<(unsigned)nel, 32 * G.nwarps, smem, st>>>(G);
+    k_proj_deposit<<<(unsigned)nel, 32 * G.nwarps, smem, st>>>(G);
     ctx->launches += 1;
     pc_phase_end(ctx, td);
   }

@@ -246,3 +246,39 @@ def test_project_dense_sampled_elements(name, n):
     scale = np.abs(F).max(axis=(0, 2))
     err = np.abs(F[elems] - R[elems]).max(axis=(0, 2)) / scale
     assert np.all(err <= FIELD_TOL), err
+
+
+@pytest.mark.parametrize("cs", [1.0, 6.0])
+def test_project_other_cutoffs(cs):
+    """Cutoff 1 sigma (most nodes near the edge) and 6 sigma (exp down to -18)."""
+    w = inputs.draw("small_8192", seed=7, n=3000)
+    wl = w["workload"]
+    a = pc.State.from_arrays(w)
+    ctx = pc.Context(a.n, wl.ne, wl.degree, wl.sigma, w["e"], 0.05, cutoff_sigmas=cs)
+    f = ctx.new_field()
+    ctx.project(a, f)
+    ctx.sync()
+    R, _ = oracle.project(w["x"], w["q"], wl.ne, wl.degree, wl.sigma, cs)
+    assert np.all(field_err(f.cpu().numpy(), R) <= FIELD_TOL)
+
+
+def test_project_dirac_limit_on_node():
+    """sigma far below the node spacing with the particle on a node: F = q / W at that node."""
+    ne, n1 = 8, 4
+    eta, om = np.polynomial.legendre.leggauss(n1)
+    h = 1 / ne
+    xp = np.array([[(3 + 0.5 * (eta[1] + 1)) * h], [(5 + 0.5 * (eta[2] + 1)) * h], [(6 + 0.5 * (eta[0] + 1)) * h]])
+    d = dict(x=xp, v=np.zeros((3, 1)), r=np.full(1, 1e-3), m=np.ones(1), id=np.zeros(1, np.int32),
+             q=np.array([[1.0], [2.0], [-3.0], [4.0]]))
+    a = pc.State.from_arrays(d)
+    ctx = pc.Context(1, ne, n1 - 1, 1e-4, 0.9, 0.05)
+    f = ctx.new_field()
+    ctx.project(a, f)
+    ctx.sync()
+    R, _ = oracle.project(xp, d["q"], ne, n1 - 1, 1e-4, 3.0)
+    F = f.cpu().numpy()
+    assert np.all(field_err(F, R) <= FIELD_TOL)
+    e = (6 * ne + 5) * ne + 3
+    g = (0 * n1 + 2) * n1 + 1
+    W = om[1] * om[2] * om[0] * (h / 2) ** 3
+    assert np.allclose(F[e, :, g], d["q"][:, 0] / W, rtol=1e-12)
