@@ -139,30 +139,40 @@ struct DepositArgs {
   double* field;
 };
 
-// floor(u / d) for 0 <= u < 2^16 / d, d <= 16, with M = ceil(2^16 / d).
-__device__ __forceinline__ int div_small(int u, int M) { return (u * M) >> 16; }
+// floor(t / d) for t < 2^32 / d via a 32-bit reciprocal M = ceil(2^32 / d); the
+// reciprocal of d = 1 does not fit in 32 bits and is encoded as 0.
+__device__ __forceinline__ unsigned div_by(unsigned t, unsigned M) { return M ? __umulhi(t, M) : t; }
+__host__ __device__ __forceinline__ unsigned recip_of(unsigned d) {
+  return d <= 1 ? 0u : (unsigned)((0x100000000ull + d - 1) / d);
+}
 
 // One CTA per element. The particles of the (2 rho + 1)^3 neighbouring elements are
-// taken in batches; batch b goes to warp b mod NW, whose lanes first stage one
-// particle each (factor slices on this element's nodes, support box, the products
-// A[c][i] = q_c kx_i and YZ[j][k] = ky_j kz_k in df32), then all lanes sweep the
-// support box of each staged particle in turn, adding A YZ onto a warp-private
-// df32 accumulator in shared memory (TwoSum on the high part, the errors summed in
-// the low part). The warps' accumulators are added in a fixed order at the end,
-// so the result does not depend on scheduling.
+// taken in batches of BS; batch b goes to warp b mod NW. Staging is spread over the
+// warp's lanes: (S0) per particle its index and factor-window offsets, (S1) the
+// factor slices on this element's nodes and the sources, (S2) the support box,
+// (S3) the df32 products A[c][i] = q_c kx_i and YZ[row] = ky_j kz_k. (S4) all lanes
+// sweep each staged particle's support box, adding A YZ onto a warp-private df32
+// accumulator in shared memory (TwoSum on the high part, errors summed in the low
+// part). The warps' accumulators are added in a fixed order at the end, so the
+// result does not depend on scheduling.
 __global__ void k_proj_deposit(DepositArgs G) {
   extern __shared__ float2 sm2[];
   const int n1 = G.n1, nodes = n1 * n1 * n1, NW = G.nwarps, BS = G.batch;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int per_p = 4 * n1 + n1 * n1;                   // staged float2 per particle
-  float2* acc = sm2;                                     // [NW][4][nodes]
-  float2* stage = sm2 + (size_t)NW * 4 * nodes;          // [NW][BS][per_p]
-  int* boxes = (int*)(stage + (size_t)NW * BS * per_p);  // [NW][BS][2]
-  int* pre = boxes + NW * BS * 2;                        // [(2 rho+1)^3 + 1] prefix of range sizes
-  int* rbeg = pre + 126;                                 // [(2 rho+1)^3] range starts
+  const int per_p = 4 * n1 + n1 * n1;  // A and YZ per particle
+  const int raw_p = 3 * n1 + 4;        // factor slices + sources per particle
+  float2* acc = sm2;                                                  // [NW][4][nodes]
+  float2* stage = acc + (size_t)NW * 4 * nodes;                       // [NW][BS][per_p]
+  float2* raw = stage + (size_t)NW * BS * per_p;                      // [NW][BS][raw_p]
+  int* meta = (int*)(raw + (size_t)NW * BS * raw_p);                  // [NW][BS][4]: j, wo0, wo1, wo2
+  int* bx = meta + NW * BS * 4;                                       // [NW][BS]: packed box (or -1)
+  int* pre = bx + NW * BS;                                            // [126] prefix of range sizes
+  int* rbeg = pre + 126;                                              // [125] range starts
   float2* my = acc + (size_t)warp * 4 * nodes;
   float2* st = stage + (size_t)warp * BS * per_p;
-  int* bx = boxes + warp * BS * 2;
+  float2* rw = raw + (size_t)warp * BS * raw_p;
+  int* mt = meta + warp * BS * 4;
+  int* bw = bx + warp * BS;
   for (int a = threadIdx.x; a < NW * 4 * nodes; a += blockDim.x) acc[a] = make_float2(0.0f, 0.0f);
   const int64_t n = G.n;
   const int ne = G.ne, rho = G.rho, span = 2 * rho + 1, nrange = span * span * span;
@@ -183,71 +193,105 @@ __global__ void k_proj_deposit(DepositArgs G) {
   __syncthreads();
   const int total = pre[nrange];
   const int nbatch = (total + BS - 1) / BS;
+  const unsigned Mraw = recip_of(raw_p), Mper = recip_of(per_p), Mn1 = recip_of(n1);
   for (int b = warp; b < nbatch; b += NW) {
-    // ---- stage: lane l < BS takes particle b*BS + l
+    // S0: particle index and window offsets
     if (lane < BS) {
       const int idx = b * BS + lane;
-      int box = 0, box2 = 0;
+      int j = -1, w0 = 0, w1 = 0, w2 = 0;
       if (idx < total) {
         int r = 0;
         while (pre[r + 1] <= idx) ++r;
-        const int j = rbeg[r] + (idx - pre[r]);
-        const int dx = r % span - rho, dy = (r / span) % span - rho, dz = r / (span * span) - rho;
-        const int wo[3] = {(rho - dx) * n1, (rho - dy) * n1, (rho - dz) * n1};
-        int lo[3], cnt[3];
-        for (int a = 0; a < 3; ++a) {
-          int l = -1, h = -2;
-          for (int i = 0; i < n1; ++i) {
-            const float2 f = G.fac[((int64_t)a * G.win + wo[a] + i) * n + j];
-            if (f.x != 0.0f) {
-              if (l < 0) l = i;
-              h = i;
-            }
-          }
-          lo[a] = l < 0 ? 0 : l;
-          cnt[a] = h - l + 1 > 0 ? h - l + 1 : 0;
-        }
-        float2* sp = st + (size_t)lane * per_p;
-        if (cnt[0] && cnt[1] && cnt[2]) {
-          // A[c][ii] = q_c kx_(lo_x + ii)
-          for (int c = 0; c < 4; ++c) {
-            const float2 qv = G.sq[(int64_t)c * n + j];
-            for (int ii = 0; ii < cnt[0]; ++ii) {
-              const float2 f = G.fac[((int64_t)0 * G.win + wo[0] + lo[0] + ii) * n + j];
-              const f2 v = df_mul({qv.x, qv.y}, {f.x, f.y});
-              sp[c * n1 + ii] = make_float2(v.h, v.l);
-            }
-          }
-          // YZ[row], row = jj + cnt_y kk
-          for (int kk = 0; kk < cnt[2]; ++kk) {
-            const float2 fz = G.fac[((int64_t)2 * G.win + wo[2] + lo[2] + kk) * n + j];
-            for (int jj = 0; jj < cnt[1]; ++jj) {
-              const float2 fy = G.fac[((int64_t)1 * G.win + wo[1] + lo[1] + jj) * n + j];
-              const f2 v = df_mul({fy.x, fy.y}, {fz.x, fz.y});
-              sp[4 * n1 + jj + cnt[1] * kk] = make_float2(v.h, v.l);
-            }
-          }
-          box = lo[0] | (cnt[0] << 5) | (lo[1] << 10) | (cnt[1] << 15) | (lo[2] << 20) | (cnt[2] << 25);
-          box2 = 1;
-        }
+        j = rbeg[r] + (idx - pre[r]);
+        w0 = (rho - (r % span - rho)) * n1;
+        w1 = (rho - ((r / span) % span - rho)) * n1;
+        w2 = (rho - (r / (span * span) - rho)) * n1;
       }
-      bx[2 * lane] = box;
-      bx[2 * lane + 1] = box2;
+      mt[4 * lane] = j;
+      mt[4 * lane + 1] = w0;
+      mt[4 * lane + 2] = w1;
+      mt[4 * lane + 3] = w2;
     }
     __syncwarp();
-    // ---- sweep the support box of each staged particle
+    // S1: factor slices and sources
+    for (int t = lane; t < BS * raw_p; t += 32) {
+      const int p = (int)div_by((unsigned)t, Mraw);
+      const int r = t - p * raw_p;
+      const int j = mt[4 * p];
+      float2 v = make_float2(0.0f, 0.0f);
+      if (j >= 0) {
+        if (r < 3 * n1) {
+          const int a = (int)div_by((unsigned)r, Mn1);
+          const int i = r - a * n1;
+          v = G.fac[((int64_t)a * G.win + mt[4 * p + 1 + a] + i) * n + j];
+        } else {
+          v = G.sq[(int64_t)(r - 3 * n1) * n + j];
+        }
+      }
+      rw[t] = v;
+    }
+    __syncwarp();
+    // S2: support box of each particle on this element
+    if (lane < BS) {
+      const float2* f = rw + lane * raw_p;
+      int lo[3], cnt[3];
+      for (int a = 0; a < 3; ++a) {
+        int l = -1, h = -2;
+        for (int i = 0; i < n1; ++i)
+          if (f[a * n1 + i].x != 0.0f) {
+            if (l < 0) l = i;
+            h = i;
+          }
+        lo[a] = l < 0 ? 0 : l;
+        cnt[a] = h >= l ? h - l + 1 : 0;
+      }
+      bw[lane] = (mt[4 * lane] >= 0 && cnt[0] && cnt[1] && cnt[2])
+                     ? (lo[0] | (cnt[0] << 5) | (lo[1] << 10) | (cnt[1] << 15) | (lo[2] << 20) | (cnt[2] << 25))
+                     : -1;
+    }
+    __syncwarp();
+    // S3: products
+    for (int t = lane; t < BS * per_p; t += 32) {
+      const int p = (int)div_by((unsigned)t, Mper);
+      const int box = bw[p];
+      if (box < 0) continue;
+      const int r = t - p * per_p;
+      const float2* f = rw + p * raw_p;
+      const int lx = box & 31, cx = (box >> 5) & 31, ly = (box >> 10) & 31, cy = (box >> 15) & 31;
+      const int lz = (box >> 20) & 31, cz = (box >> 25) & 31;
+      if (r < 4 * n1) {
+        const int c = (int)div_by((unsigned)r, Mn1);
+        const int ii = r - c * n1;
+        if (ii < cx) {
+          const float2 fx = f[lx + ii], qv = f[3 * n1 + c];
+          const f2 v = df_mul({qv.x, qv.y}, {fx.x, fx.y});
+          st[p * per_p + r] = make_float2(v.h, v.l);
+        }
+      } else {
+        const int row = r - 4 * n1;
+        if (row < cy * cz) {
+          const int kk = (int)div_by((unsigned)row, recip_of(cy));
+          const int jj = row - kk * cy;
+          const float2 fy = f[n1 + ly + jj], fz = f[2 * n1 + lz + kk];
+          const f2 v = df_mul({fy.x, fy.y}, {fz.x, fz.y});
+          st[p * per_p + r] = make_float2(v.h, v.l);
+        }
+      }
+    }
+    __syncwarp();
+    // S4: sweep the support box of each staged particle
     for (int q = 0; q < BS; ++q) {
-      if (!bx[2 * q + 1]) continue;
-      const int box = bx[2 * q];
+      const int box = bw[q];
+      if (box < 0) continue;
       const int lx = box & 31, cx = (box >> 5) & 31, ly = (box >> 10) & 31, cy = (box >> 15) & 31;
       const int lz = (box >> 20) & 31, cz = (box >> 25) & 31;
       const int nbox = cx * cy * cz;
-      const int Mx = (65536 + cx - 1) / cx, My = (65536 + cy - 1) / cy;
+      const unsigned Mx = recip_of(cx), My = recip_of(cy);
       const float2* sp = st + (size_t)q * per_p;
       for (int u = lane; u < nbox; u += 32) {
-        const int row = div_small(u, Mx);
+        const int row = (int)div_by((unsigned)u, Mx);
         const int ii = u - row * cx;
-        const int kk = div_small(row, My);
+        const int kk = (int)div_by((unsigned)row, My);
         const int jj = row - kk * cy;
         const int g = ((lz + kk) * n1 + ly + jj) * n1 + lx + ii;
         const float2 yz = sp[4 * n1 + row];
@@ -282,15 +326,15 @@ __global__ void k_proj_deposit(DepositArgs G) {
 
 }  // namespace
 
-static void deposit_shape(int n1, int rho, int* nwarps, int* batch, size_t* smem) {
+static void deposit_shape(int n1, int* nwarps, int* batch, size_t* smem) {
   const size_t nodes = (size_t)n1 * n1 * n1;
-  const size_t per_p = 4 * (size_t)n1 + (size_t)n1 * n1;
+  const size_t per_p = 4 * (size_t)n1 + (size_t)n1 * n1, raw_p = 3 * (size_t)n1 + 4;
   const size_t budget = 200 * 1024;
-  const size_t fixed = (126 + 126) * sizeof(int) + 64;
+  const size_t fixed = (126 + 125) * sizeof(int) + 64;
   static const int kWarps[] = {16, 12, 8, 6, 4, 2, 1};
   for (int nw : kWarps)
     for (int bs = 32; bs >= 8; bs /= 2) {
-      const size_t need = nw * (4 * nodes + bs * per_p) * sizeof(float2) + nw * bs * 2 * sizeof(int) + fixed;
+      const size_t need = nw * (4 * nodes + bs * (per_p + raw_p)) * sizeof(float2) + nw * bs * 5 * sizeof(int) + fixed;
       if (need <= budget) {
         *nwarps = nw;
         *batch = bs;
@@ -299,8 +343,8 @@ static void deposit_shape(int n1, int rho, int* nwarps, int* batch, size_t* smem
       }
     }
   *nwarps = 1;
-  *batch = 4;
-  *smem = (4 * nodes + 4 * per_p) * sizeof(float2) + 8 * sizeof(int) + fixed;
+  *batch = 8;
+  *smem = (4 * nodes + 8 * (per_p + raw_p)) * sizeof(float2) + 8 * 5 * sizeof(int) + fixed;
 }
 
 pc_status pc_project_impl(pc_ctx* ctx, const pc_particles* p, double* field) {
@@ -363,7 +407,7 @@ pc_status pc_project_impl(pc_ctx* ctx, const pc_particles* p, double* field) {
     G.rho = ctx->rho;
     G.win = ctx->win;
     size_t smem = 0;
-    deposit_shape(ctx->n1, ctx->rho, &G.nwarps, &G.batch, &smem);
+    deposit_shape(ctx->n1, &G.nwarps, &G.batch, &smem);
     G.start = ctx->start;
     G.fac = ctx->fac;
     G.sq = ctx->sq;
