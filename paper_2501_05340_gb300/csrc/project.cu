@@ -133,6 +133,7 @@ __global__ void __launch_bounds__(128) k_proj_factors(FactorArgs F) {
 struct DepositArgs {
   int64_t n;
   int ne, n1, rho, win, nwarps, batch;
+  unsigned Mraw, Mper, Mn1;  // recip_of(3 n1 + 4), recip_of(4 n1 + n1^2), recip_of(n1)
   const int32_t* start;
   const float2* fac;
   const float2* sq;
@@ -168,12 +169,14 @@ __global__ void k_proj_deposit(DepositArgs G) {
   int* bx = meta + NW * BS * 4;                                       // [NW][BS]: packed box (or -1)
   int* pre = bx + NW * BS;                                            // [126] prefix of range sizes
   int* rbeg = pre + 126;                                              // [125] range starts
+  unsigned* rtab = (unsigned*)(rbeg + 125);                           // [33] recip_of(d), d = 0..32
   float2* my = acc + (size_t)warp * 4 * nodes;
   float2* st = stage + (size_t)warp * BS * per_p;
   float2* rw = raw + (size_t)warp * BS * raw_p;
   int* mt = meta + warp * BS * 4;
   int* bw = bx + warp * BS;
   for (int a = threadIdx.x; a < NW * 4 * nodes; a += blockDim.x) acc[a] = make_float2(0.0f, 0.0f);
+  if (threadIdx.x < 33) rtab[threadIdx.x] = recip_of(threadIdx.x);
   const int64_t n = G.n;
   const int ne = G.ne, rho = G.rho, span = 2 * rho + 1, nrange = span * span * span;
   const int e = blockIdx.x;
@@ -193,7 +196,7 @@ __global__ void k_proj_deposit(DepositArgs G) {
   __syncthreads();
   const int total = pre[nrange];
   const int nbatch = (total + BS - 1) / BS;
-  const unsigned Mraw = recip_of(raw_p), Mper = recip_of(per_p), Mn1 = recip_of(n1);
+  const unsigned Mraw = G.Mraw, Mper = G.Mper, Mn1 = G.Mn1;
   for (int b = warp; b < nbatch; b += NW) {
     // S0: particle index and window offsets
     if (lane < BS) {
@@ -270,7 +273,7 @@ __global__ void k_proj_deposit(DepositArgs G) {
       } else {
         const int row = r - 4 * n1;
         if (row < cy * cz) {
-          const int kk = (int)div_by((unsigned)row, recip_of(cy));
+          const int kk = (int)div_by((unsigned)row, rtab[cy]);
           const int jj = row - kk * cy;
           const float2 fy = f[n1 + ly + jj], fz = f[2 * n1 + lz + kk];
           const f2 v = df_mul({fy.x, fy.y}, {fz.x, fz.y});
@@ -286,7 +289,7 @@ __global__ void k_proj_deposit(DepositArgs G) {
       const int lx = box & 31, cx = (box >> 5) & 31, ly = (box >> 10) & 31, cy = (box >> 15) & 31;
       const int lz = (box >> 20) & 31, cz = (box >> 25) & 31;
       const int nbox = cx * cy * cz;
-      const unsigned Mx = recip_of(cx), My = recip_of(cy);
+      const unsigned Mx = rtab[cx], My = rtab[cy];
       const float2* sp = st + (size_t)q * per_p;
       for (int u = lane; u < nbox; u += 32) {
         const int row = (int)div_by((unsigned)u, Mx);
@@ -330,7 +333,7 @@ static void deposit_shape(int n1, int* nwarps, int* batch, size_t* smem) {
   const size_t nodes = (size_t)n1 * n1 * n1;
   const size_t per_p = 4 * (size_t)n1 + (size_t)n1 * n1, raw_p = 3 * (size_t)n1 + 4;
   const size_t budget = 200 * 1024;
-  const size_t fixed = (126 + 125) * sizeof(int) + 64;
+  const size_t fixed = (126 + 125 + 33) * sizeof(int) + 64;
   static const int kWarps[] = {16, 12, 8, 6, 4, 2, 1};
   for (int nw : kWarps)
     for (int bs = 32; bs >= 8; bs /= 2) {
@@ -408,6 +411,9 @@ pc_status pc_project_impl(pc_ctx* ctx, const pc_particles* p, double* field) {
     G.win = ctx->win;
     size_t smem = 0;
     deposit_shape(ctx->n1, &G.nwarps, &G.batch, &smem);
+    G.Mraw = recip_of(3 * ctx->n1 + 4);
+    G.Mper = recip_of(4 * ctx->n1 + ctx->n1 * ctx->n1);
+    G.Mn1 = recip_of(ctx->n1);
     G.start = ctx->start;
     G.fac = ctx->fac;
     G.sq = ctx->sq;
