@@ -143,6 +143,37 @@ pc_status pc_set_timing(pc_ctx* ctx, int on);
  * Waits for the stream. */
 pc_status pc_get_timing(pc_ctx* ctx, double* ms, int64_t* count);
 
+/* Size in bytes of the fixed device array used by pc_project_noalloc. */
+#define PC_NOALLOC_SCRATCH_BYTES (32u << 20)
+
+/* The projection of pc_project for callers that may not allocate device memory:
+ * for instance a plugin inside a host solver whose memory manager owns all of
+ * the GPU's memory and forbids allocations by anyone else, or a time-critical
+ * loop that cannot afford an allocation's latency or failure. There is no
+ * counterpart in the paper; it computes exactly what pc_project computes.
+ *
+ * It needs no context and allocates nothing: no cudaMalloc, cudaFree or
+ * allocating library call. Its scratch is one fixed device array of
+ * PC_NOALLOC_SCRATCH_BYTES (32 MiB) compiled into the library, which every GPU
+ * that loads the library holds until the process exits. The caller passes the
+ * inputs (p: device SoA, p->q required) and the output (field: device
+ * [ne^3][4][(N+1)^3] doubles, overwritten); cfg supplies ne, degree, sigma,
+ * cutoff_sigmas, cutoff_kind (0) and stream; the other fields are ignored.
+ * About 12 + 24 (2 rho + 1)(N+1) + 32 bytes per particle plus 8 ne^3 bytes must
+ * fit in the array (rho = ceil(cutoff_sigmas sigma ne)); larger problems return
+ * PC_ECAPACITY with the required size in msg.
+ *
+ * The first call on each device looks up the array's device address
+ * (cudaGetSymbolAddress) with that device current; make that first call before
+ * any stream capture. The work is queued on cfg->stream and the call returns
+ * without waiting; checks made on the GPU (positions outside [0,1)) are not
+ * reported. All calls share the one array, which keeps the previous call's
+ * contents (what must start at zero is cleared by each call): calls that overlap
+ * on the GPU, on any streams, race and give wrong results. msg (optional, may be
+ * NULL) receives a one-line message of at most msg_len - 1 characters. */
+pc_status pc_project_noalloc(const pc_config* cfg, const pc_particles* p, double* field, char* msg,
+                             int64_t msg_len);
+
 /* Message of the last failure on this context (static storage of the context). */
 const char* pc_last_error(const pc_ctx* ctx);
 

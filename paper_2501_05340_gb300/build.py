@@ -23,6 +23,7 @@ UNITS = {
     "bin.cu": [],
     "collide.cu": ["-fmad=false"],
     "project.cu": ["-fmad=false"],
+    "noalloc.cu": [],
 }
 
 

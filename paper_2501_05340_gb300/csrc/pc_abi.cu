@@ -11,12 +11,10 @@
 
 #include "pc_internal.cuh"
 
-namespace {
-
 // Legendre-Gauss rule with n1 points on [-1, 1] (the DGSEM solution points,
 // Sec. 3.1): Newton iteration on P_n1 evaluated by Bonnet's recurrence, started
 // from the Chebyshev-like estimate cos(pi (k - 1/4) / (n1 + 1/2)).
-void gauss_rule(int n1, double* x, double* w) {
+void pc_gauss_rule(int n1, double* x, double* w) {
   const double pi = 3.141592653589793238462643383279502884;
   for (int k = 1; k <= n1; ++k) {
     double z = cos(pi * (k - 0.25) / (n1 + 0.5));
@@ -50,6 +48,26 @@ void gauss_rule(int n1, double* x, double* w) {
   }
   if (n1 & 1) x[n1 / 2] = 0.0;
 }
+
+// exp2(j/64) and ln(2)/64 split into floats for the df32 exponential.
+void pc_build_exp_table(DfExpTable* tab) {
+  DfExpTable& T = *tab;
+  for (int j = 0; j < 64; ++j) {
+    const double v = exp2((double)j / 64.0);
+    T.th[j] = (float)v;
+    T.tl[j] = (float)(v - (double)T.th[j]);
+  }
+  const double L = log(2.0) / 64.0;
+  int ex = 0;
+  const double m = frexp(L, &ex);                          // L = m 2^ex, m in [0.5, 1)
+  const double L1 = ldexp(floor(ldexp(m, 11)), ex - 11);  // 11 significant bits
+  T.L1 = (float)L1;
+  T.L2 = (float)(L - L1);
+  T.L3 = (float)((L - L1) - (double)T.L2);
+  T.inv = (float)(64.0 / log(2.0));
+}
+
+namespace {
 
 template <typename T>
 cudaError_t dalloc(T** p, size_t count) {
@@ -117,24 +135,8 @@ pc_status pc_init(pc_ctx** out, const pc_config* cfg) {
   ctx->win = (2 * rho + 1) * ctx->n1;
   ctx->h = 1.0 / c.ne;
   ctx->cap = c.cand_cap == 0 ? 16 : c.cand_cap;
-  gauss_rule(ctx->n1, ctx->eta, ctx->w);
-  {
-    // exp2(j/64) and ln(2)/64 split into floats for the df32 exponential
-    DfExpTable& T = ctx->exp_tab;
-    for (int j = 0; j < 64; ++j) {
-      const double v = exp2((double)j / 64.0);
-      T.th[j] = (float)v;
-      T.tl[j] = (float)(v - (double)T.th[j]);
-    }
-    const double L = log(2.0) / 64.0;
-    int ex = 0;
-    const double m = frexp(L, &ex);                 // L = m 2^ex, m in [0.5, 1)
-    const double L1 = ldexp(floor(ldexp(m, 11)), ex - 11);  // 11 significant bits
-    T.L1 = (float)L1;
-    T.L2 = (float)(L - L1);
-    T.L3 = (float)((L - L1) - (double)T.L2);
-    T.inv = (float)(64.0 / log(2.0));
-  }
+  pc_gauss_rule(ctx->n1, ctx->eta, ctx->w);
+  pc_build_exp_table(&ctx->exp_tab);
 
   const int64_t n = c.n_max;
   const int64_t nel = (int64_t)c.ne * c.ne * c.ne;

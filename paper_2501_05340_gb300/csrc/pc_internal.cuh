@@ -93,6 +93,10 @@ cudaError_t pc_bin_finish(int64_t n, int64_t nbins, const int32_t* key, const in
                           int32_t* cnt, int32_t* start, int32_t* blocksums, int32_t* perm, cudaStream_t s,
                           int64_t* launches);
 
+// ---- tables (pc_abi.cu) -----------------------------------------------------
+void pc_gauss_rule(int n1, double* x, double* w);
+void pc_build_exp_table(DfExpTable* tab);
+
 // ---- collide (collide.cu) ----------------------------------------------------
 pc_status pc_collide_impl(pc_ctx* ctx, const pc_particles* in, pc_particles* out, double dt);
 

@@ -61,6 +61,9 @@ def library():
         lib.pc_sync.argtypes = [c_p]
         lib.pc_set_timing.argtypes = [c_p, ctypes.c_int]
         lib.pc_get_timing.argtypes = [c_p, c_p, c_p]
+        lib.pc_project_noalloc.argtypes = [ctypes.POINTER(PcConfig), ctypes.POINTER(PcParticles), c_p,
+                                            ctypes.c_char_p, c_i64]
+        lib.pc_project_noalloc.restype = ctypes.c_int
         lib.pc_last_error.argtypes = [c_p]
         lib.pc_last_error.restype = ctypes.c_char_p
         lib.pc_destroy.argtypes = [c_p]
@@ -206,6 +209,24 @@ class Context:
             self.close()
         except Exception:
             pass
+
+
+NOALLOC_SCRATCH_BYTES = 32 << 20
+
+
+def project_noalloc(state, field, ne, degree, sigma, cutoff_sigmas=3.0, stream=None):
+    """pc_project_noalloc: the projection without a context and without any device
+    allocation, for callers that may not allocate (its scratch is a fixed 32 MiB
+    device array inside the library). Calls that overlap on the GPU race."""
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    cfg = PcConfig(0, int(ne), int(degree), float(sigma), float(cutoff_sigmas), 0, 0.0, 0.0, 0,
+                   c_p(stream.cuda_stream))
+    s = state.struct()
+    msg = ctypes.create_string_buffer(256)
+    st = library().pc_project_noalloc(ctypes.byref(cfg), ctypes.byref(s), _ptr(field), msg, 256)
+    if st != PC_OK:
+        raise PcError(st, msg.value.decode())
 
 
 def reach_of(r, v, dt, margin=1.05):
