@@ -36,7 +36,8 @@ typedef enum {
   PC_ENOMEM = 2,       /* device allocation failed (pc_init only) */
   PC_ECUDA = 3,        /* a CUDA runtime call or kernel launch failed */
   PC_ENOCONVERGE = 4,  /* the matching rounds reached their cap (cannot happen for valid input) */
-  PC_ECAPACITY = 5,    /* a particle had more candidate partners than the per-particle capacity */
+  PC_ECAPACITY = 5,    /* a capacity was exceeded (candidate partners per particle, fixed scratch) */
+  PC_ETIMEOUT = 6,     /* a bounded wait inside a kernel expired (the kernel stopped cleanly) */
 } pc_status;
 
 typedef struct pc_ctx pc_ctx;
@@ -66,6 +67,24 @@ typedef struct {
   double* m;     /* [n] masses (> 0) */
   double* q;     /* [4][n] sources (3 momentum + 1 energy), or NULL */
 } pc_particles;
+
+/* Device particle state of the mixed-precision path (FP32 storage).
+ * Positions are cell-relative: cell[p] is the linear index (cz*nc + cy)*nc + cx of
+ * the context's nc^3 collision grid (pc_cells_per_side) and o[a][p] in [0,1) the
+ * FP32 offset inside that cell in cell units, so the position is (c_a + o_a)/nc. */
+typedef struct {
+  int64_t n;      /* particle count, 0 <= n <= n_max */
+  int32_t* id;    /* [n] unique ids */
+  int32_t* cell;  /* [n] linear collision cell */
+  float* o;       /* [3][n] offsets in cell units, [0,1) */
+  float* v;       /* [3][n] velocities */
+  float* r;       /* [n] radii (> 0) */
+  float* m;       /* [n] masses (> 0) */
+  float* q;       /* [4][n] sources, or NULL */
+} pc_particles_f32;
+
+/* Tensor-core operand type of pc_project_f32. */
+typedef enum { PC_TC_F16 = 0, PC_TC_BF16 = 1 } pc_tc_type;
 
 typedef struct {
   int64_t pairs;          /* collisions committed in the last pc_collide */
@@ -118,6 +137,38 @@ pc_status pc_collide(pc_ctx* ctx, const pc_particles* in, pc_particles* out, dou
  * p->q must be non-NULL. field: device [ne^3][4][(N+1)^3] doubles, overwritten.
  * Accuracy: within 1e-12 of the exact sum, normwise per component. */
 pc_status pc_project(pc_ctx* ctx, const pc_particles* p, double* field);
+
+/* ---- mixed-precision path ---- */
+
+/* Collision cells per side of the context's grid (the nc of pc_particles_f32). */
+int32_t pc_cells_per_side(const pc_ctx* ctx);
+
+/* Convert an FP64 state to the FP32 cell-relative storage, same order:
+ * s = x nc (FP64), c = floor(s) clamped to [0, nc), o = float(s - c); an offset
+ * that rounds to 1 is carried into the next cell (periodically). v, r, m, q are
+ * rounded to FP32. out->q may be NULL. Device buffers; queued on the stream. */
+pc_status pc_quantize(pc_ctx* ctx, const pc_particles* in, pc_particles_f32* out);
+
+/* One collision step on the FP32 cell-relative storage (`in` -> `out`, distinct,
+ * out sorted by cell, ties by id). Same pair selection as pc_collide, on the exact
+ * FP64 values of the stored state in cell units: x = c + o, v nc, (r_i + r_j) nc,
+ * periodic box of nc cells. A certified FP32 filter on cell-relative differences
+ * rejects pairs before the FP64 solve. Colliding pairs: FP64 response (as
+ * pc_collide, positions in cell units), new position stored as cell + FP32
+ * offset, velocity rounded to FP32. Free particles: o' = o + float(dt nc) v in
+ * FP32 with a carry into the neighbouring cell. Bit-identical to a plain
+ * implementation of these rules. */
+pc_status pc_collide_f32(pc_ctx* ctx, const pc_particles_f32* in, pc_particles_f32* out, double dt);
+
+/* Projection of p->q (as pc_project) on the tensor cores: per element the
+ * separable deposit is the dense contraction D[jk][c i] = sum_p (ky_j kz_k)(q_c kx_i),
+ * each factor split into high and low parts of tc_type (FP16 or BF16), the three
+ * significant products accumulated in FP32 (tcgen05, accumulators in tensor
+ * memory). Kernel factors in FP32; cutoff decisions near the cutoff are made in
+ * FP64 on the stored position, as in pc_project. field: device FP32
+ * [ne^3][4][(N+1)^3], overwritten. Requires N + 1 <= 8 and (2 rho + 1)(N + 1) <= 32,
+ * rho = ceil(cutoff_sigmas sigma ne). */
+pc_status pc_project_f32(pc_ctx* ctx, const pc_particles_f32* p, float* field, int32_t tc_type);
 
 /* Copy the pairs of the last pc_collide to HOST memory: ids[2k], ids[2k+1] (smaller
  * id first) and t[k], sorted by the smaller id. Writes min(cap, count) pairs and

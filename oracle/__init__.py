@@ -49,6 +49,8 @@ def _load():
         lib.or_respond_advance.restype = None
         lib.or_collide_step.argtypes = [i64, P, P, P, P, P, d, d, i32, P, P]
         lib.or_collide_step.restype = i64
+        lib.or_collide_step_cellrel.argtypes = [i64, i32, P, P, P, P, P, P, d, d, P, P]
+        lib.or_collide_step_cellrel.restype = i64
         lib.or_mesh_map.argtypes = [P, d, P, P]
         lib.or_mesh_map.restype = None
         lib.or_project.argtypes = [i64, P, P, i32, i32, d, d, i32, d, P, P]
@@ -136,6 +138,44 @@ def collide_step(x, v, r, m, ids, e, dt, method="cells"):
     if k < 0:
         raise MemoryError("oracle collide")
     return x, v, partner, tc, k
+
+
+def quantize(x, nc):
+    """FP64 positions in [0,1) -> (linear cell, FP32 offsets in cell units) of an nc^3 grid:
+    s = x nc, c = floor(s) (clamped), o = float32(s - c), and o == 1 carried into the next cell."""
+    x = _f64(x)
+    s = x * float(nc)
+    c = np.clip(np.floor(s), 0, nc - 1).astype(np.int64)
+    o = (s - c).astype(np.float32)
+    carry = o >= np.float32(1.0)
+    o[carry] = 0.0
+    c[carry] = (c[carry] + 1) % nc
+    cell = ((c[2] * nc + c[1]) * nc + c[0]).astype(np.int32)
+    return cell, np.ascontiguousarray(o)
+
+
+def dequantize(cell, o, nc):
+    """Linear cell + FP32 offsets -> FP64 positions (c + o) / nc in [0,1)."""
+    cell = np.asarray(cell, np.int64)
+    c = np.stack([cell % nc, (cell // nc) % nc, cell // (nc * nc)]).astype(np.float64)
+    return (c + np.asarray(o, np.float64)) / float(nc)
+
+
+def collide_step_cellrel(cell, o, v, r, m, ids, nc, e, dt):
+    """One step of the mixed-storage method; returns (cell', o', v', partner, tc, npairs)."""
+    cell = np.ascontiguousarray(cell, np.int32).copy()
+    o = np.ascontiguousarray(o, np.float32).copy()
+    v = np.ascontiguousarray(v, np.float32).copy()
+    r = np.ascontiguousarray(r, np.float32)
+    m = np.ascontiguousarray(m, np.float32)
+    ids = np.ascontiguousarray(ids, np.int32)
+    n = r.shape[0]
+    partner, tc = np.zeros(n, np.int64), np.zeros(n)
+    k = _load().or_collide_step_cellrel(n, int(nc), _p(cell), _p(o), _p(v), _p(r), _p(m), _p(ids), float(e),
+                                        float(dt), _p(partner), _p(tc))
+    if k < 0:
+        raise MemoryError("oracle collide_step_cellrel")
+    return cell, o, v, partner, tc, k
 
 
 def mesh_map(xi, amp):

@@ -68,6 +68,13 @@ static double minimg(double d) {
   return d;
 }
 
+/* Same in a periodic box of length L (L = 1 gives minimg exactly). */
+static double minimg_box(double d, double L) {
+  if (d > 0.5 * L) return d - L;
+  if (d < -0.5 * L) return d + L;
+  return d;
+}
+
 /* Reading of the garbled Eq. collision-detect 2: dx_p = x_1 - x_2 and
  * dv_p = v_1 - v_2. With a = dv.dv, b = dx.dv, c = dx.dx - R^2 the roots of
  * a t^2 + 2 b t + c = 0 are both positive iff c > 0 and b < 0 (this is also the
@@ -75,15 +82,14 @@ static double minimg(double d) {
  * double root carries no normal velocity). The smaller root is written as
  * c / (-b + sqrt(b^2 - a c)), the cancellation-free form of (-b - sqrt(.))/a.
  * The root must satisfy t <= dt (inclusive). */
-double or_contact_time(const double xi[3], const double xj[3], const double vi[3], const double vj[3],
-                       double ri, double rj, double dt) {
-  double dx0 = minimg(xi[0] - xj[0]);
-  double dx1 = minimg(xi[1] - xj[1]);
-  double dx2 = minimg(xi[2] - xj[2]);
+static double contact_time_box(const double xi[3], const double xj[3], const double vi[3], const double vj[3],
+                               double R, double dt, double L) {
+  double dx0 = minimg_box(xi[0] - xj[0], L);
+  double dx1 = minimg_box(xi[1] - xj[1], L);
+  double dx2 = minimg_box(xi[2] - xj[2], L);
   double dv0 = vi[0] - vj[0];
   double dv1 = vi[1] - vj[1];
   double dv2 = vi[2] - vj[2];
-  double R = ri + rj;
   double a = (dv0 * dv0 + dv1 * dv1) + dv2 * dv2;
   double b = (dx0 * dv0 + dx1 * dv1) + dx2 * dv2;
   double c = ((dx0 * dx0 + dx1 * dx1) + dx2 * dx2) - R * R;
@@ -94,6 +100,11 @@ double or_contact_time(const double xi[3], const double xj[3], const double vi[3
   double t = c / (-b + sqrt(disc));
   if (t <= dt) return t;
   return INFINITY;
+}
+
+double or_contact_time(const double xi[3], const double xj[3], const double vi[3], const double vj[3],
+                       double ri, double rj, double dt) {
+  return contact_time_box(xi, xj, vi, vj, ri + rj, dt, 1.0);
 }
 
 static void load3(const double* a, int64_t n, int64_t i, double out[3]) {
@@ -531,4 +542,126 @@ int or_project(int64_t n, const double* x, const double* q, int ne, int degree, 
   free(P.lz);
   free(P.comp);
   return 0;
+}
+
+/* ------------------------------------------------------------------ mixed storage */
+
+int64_t or_collide_step_cellrel(int64_t n, int32_t nc, int32_t* cell, float* o, float* v, const float* r,
+                                const float* m, const int32_t* id, double e, double dt, int64_t* partner,
+                                double* tc) {
+  const double L = (double)nc;
+  /* exact FP64 cell-unit copies: x = c + o, v_c = v nc */
+  double* x = (double*)malloc(sizeof(double) * (size_t)(3 * n > 0 ? 3 * n : 1));
+  double* vc = (double*)malloc(sizeof(double) * (size_t)(3 * n > 0 ? 3 * n : 1));
+  double* vn = (double*)malloc(sizeof(double) * (size_t)(3 * n > 0 ? 3 * n : 1));
+  int64_t cap = n > 16 ? 4 * n : 64;
+  int64_t *ci = NULL, *cj = NULL;
+  double* ct = NULL;
+  if (!x || !vc || !vn) { free(x); free(vc); free(vn); return -1; }
+  for (int64_t i = 0; i < n; ++i) {
+    int32_t cl = cell[i];
+    int32_t c3[3] = {cl % nc, (cl / nc) % nc, cl / (nc * nc)};
+    for (int k = 0; k < 3; ++k) {
+      x[k * n + i] = (double)c3[k] + (double)o[k * n + i];
+      vc[k * n + i] = (double)v[k * n + i] * L;
+    }
+  }
+  /* candidates by brute force over all pairs (plain; the mixed tests use small n) */
+  int64_t cnt;
+  for (;;) {
+    ci = (int64_t*)malloc(sizeof(int64_t) * (size_t)cap);
+    cj = (int64_t*)malloc(sizeof(int64_t) * (size_t)cap);
+    ct = (double*)malloc(sizeof(double) * (size_t)cap);
+    if (!ci || !cj || !ct) { free(ci); free(cj); free(ct); free(x); free(vc); free(vn); return -1; }
+    cnt = 0;
+    for (int64_t i = 0; i < n; ++i) {
+      double xi[3] = {x[i], x[n + i], x[2 * n + i]};
+      double vi[3] = {vc[i], vc[n + i], vc[2 * n + i]};
+      for (int64_t j = i + 1; j < n; ++j) {
+        double xj[3] = {x[j], x[n + j], x[2 * n + j]};
+        double vj[3] = {vc[j], vc[n + j], vc[2 * n + j]};
+        double R = ((double)r[i] + (double)r[j]) * L;
+        double t = contact_time_box(xi, xj, vi, vj, R, dt, L);
+        if (t <= dt) {
+          if (cnt < cap) { ci[cnt] = i; cj[cnt] = j; ct[cnt] = t; }
+          ++cnt;
+        }
+      }
+    }
+    if (cnt <= cap) break;
+    free(ci); free(cj); free(ct);
+    cap = cnt;
+  }
+  int64_t pairs = or_match_greedy(n, id, cnt, ci, cj, ct, partner, tc);
+  free(ci); free(cj); free(ct);
+  if (pairs < 0) { free(x); free(vc); free(vn); return -1; }
+  const float dtn = (float)(dt * L);
+  for (int64_t i = 0; i < n; ++i) {
+    int32_t cl = cell[i];
+    int32_t c3[3] = {cl % nc, (cl / nc) % nc, cl / (nc * nc)};
+    int64_t j = partner[i];
+    if (j < 0) {
+      /* free flight in FP32 cell units with a carry */
+      for (int k = 0; k < 3; ++k) {
+        float on = o[k * n + i] + dtn * v[k * n + i];
+        if (on >= 1.0f) {
+          on = on - 1.0f;
+          c3[k] = c3[k] + 1 == nc ? 0 : c3[k] + 1;
+        } else if (on < 0.0f) {
+          float up = on + 1.0f;
+          if (up == 1.0f) {
+            on = 0.0f;
+          } else {
+            on = up;
+            c3[k] = c3[k] == 0 ? nc - 1 : c3[k] - 1;
+          }
+        }
+        o[k * n + i] = on;
+      }
+    } else {
+      /* FP64 response: physical velocities, cell-unit positions */
+      double t = tc[i];
+      double dx[3], dvc[3], dv[3], s3[3], nr[3];
+      for (int k = 0; k < 3; ++k) {
+        dx[k] = minimg_box(x[k * n + i] - x[k * n + j], L);
+        dvc[k] = vc[k * n + i] - vc[k * n + j];
+        dv[k] = (double)v[k * n + i] - (double)v[k * n + j];
+      }
+      for (int k = 0; k < 3; ++k) s3[k] = dx[k] + t * dvc[k];
+      double sl = sqrt((s3[0] * s3[0] + s3[1] * s3[1]) + s3[2] * s3[2]);
+      for (int k = 0; k < 3; ++k) nr[k] = -s3[k] / sl;
+      double vrn = (dv[0] * nr[0] + dv[1] * nr[1]) + dv[2] * nr[2];
+      double mi = (double)m[i], mj = (double)m[j];
+      double mr = (mi * mj) / (mi + mj);
+      double J = -mr * (1.0 + e) * vrn;
+      double gi = J / mi;
+      for (int k = 0; k < 3; ++k) {
+        double vold = (double)v[k * n + i];
+        double vnew = vold + gi * nr[k];
+        double y = (x[k * n + i] + t * vc[k * n + i]) + (dt - t) * (vnew * L);
+        if (y < 0.0) y += L;
+        else if (y >= L) y -= L;
+        int32_t cq = (int32_t)floor(y);
+        if (cq < 0) cq = 0;
+        if (cq > nc - 1) cq = nc - 1;
+        float oq = (float)(y - (double)cq);
+        if (oq >= 1.0f) {
+          oq = 0.0f;
+          cq = cq + 1 == nc ? 0 : cq + 1;
+        }
+        c3[k] = cq;
+        o[k * n + i] = oq;
+        vn[k * n + i] = vnew;
+      }
+    }
+    cell[i] = (c3[2] * nc + c3[1]) * nc + c3[0];
+  }
+  /* velocities are stored only after every pair has read the old ones */
+  for (int64_t i = 0; i < n; ++i)
+    if (partner[i] >= 0)
+      for (int k = 0; k < 3; ++k) v[k * n + i] = (float)vn[k * n + i];
+  free(x);
+  free(vc);
+  free(vn);
+  return pairs;
 }

@@ -67,6 +67,25 @@ void or_respond_advance(int64_t n, double* x, double* v, const double* m, const 
 int64_t or_collide_step(int64_t n, double* x, double* v, const double* r, const double* m, const int32_t* id,
                         double e, double dt, int method, int64_t* partner, double* tc);
 
+/* ---- mixed-precision storage (FP32 cell-relative state) ----
+ * A position is stored as an integer cell c in [0, nc) per axis (linear cell
+ * (cz*nc + cy)*nc + cx) and an FP32 offset o in [0,1) in cell units; velocities,
+ * radii and masses as FP32. One step of the mixed method, read from the paper's
+ * operator with this storage:
+ *   contact detection: the a-priori test and root of or_contact_time on exact
+ *     FP64 cell-unit values x = c + o, v = v_f nc, R = (r_i + r_j) nc, periodic
+ *     box of nc cells;
+ *   colliding pairs: the response of or_respond_advance in FP64 (velocities in
+ *     physical units, positions in cell units), the new position wrapped into
+ *     [0, nc), then stored as floor and FP32 offset, the velocity as FP32;
+ *   free particles: o' = o + (dt nc)_f v_f in FP32, carried into the next or
+ *     previous cell when o' leaves [0,1).
+ * Arrays are updated in place. Returns the number of pairs (-1 on allocation
+ * failure); partner/tc as in or_collide_step. */
+int64_t or_collide_step_cellrel(int64_t n, int32_t nc, int32_t* cell, float* o, float* v, const float* r,
+                                const float* m, const int32_t* id, double e, double dt, int64_t* partner,
+                                double* tc);
+
 /* Physical position of a logical point xi in [0,1)^3 under the periodic mesh
  * mapping x = xi + amp*(sin 2pi xi_y sin 2pi xi_z, sin 2pi xi_z sin 2pi xi_x,
  * sin 2pi xi_x sin 2pi xi_y) (amp = 0 is the affine Cartesian mesh), and the

@@ -24,6 +24,8 @@ UNITS = {
     "collide.cu": ["-fmad=false"],
     "project.cu": ["-fmad=false"],
     "noalloc.cu": [],
+    "mixed.cu": ["-fmad=false"],
+    "tc_deposit.cu": [],
 }
 
 

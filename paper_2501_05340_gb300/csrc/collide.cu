@@ -472,6 +472,30 @@ __global__ void k_respond(RespondArgs R) {
 
 }  // namespace
 
+cudaError_t pc_match_launch(pc_ctx* ctx, int64_t n) {
+  MatchArgs M;
+  M.n = n;
+  M.cap = ctx->cap;
+  M.cand_j = ctx->cand_j;
+  M.cand_t = ctx->cand_t;
+  M.ncand = ctx->ncand;
+  M.best = ctx->best;
+  M.sid = ctx->sid;
+  M.partner = ctx->partner;
+  M.tcoll = ctx->tcoll;
+  M.work = ctx->work;
+  M.pair_lo = ctx->pair_lo;
+  M.pair_hi = ctx->pair_hi;
+  M.pair_t = ctx->pair_t;
+  M.counters = ctx->counters;
+  const int tm = pc_phase_begin(ctx, PC_PH_MATCH);
+  k_match_first<<<pc_blocks(n, 256), 256, 0, ctx->stream>>>(M);
+  k_match_finish<<<1, kFinishThreads, 0, ctx->stream>>>(M);
+  ctx->launches += 2;
+  pc_phase_end(ctx, tm);
+  return cudaGetLastError();
+}
+
 pc_status pc_collide_impl(pc_ctx* ctx, const pc_particles* in, pc_particles* out, double dt) {
   const int64_t n = in->n;
   cudaStream_t st = ctx->stream;
@@ -521,28 +545,8 @@ pc_status pc_collide_impl(pc_ctx* ctx, const pc_particles* in, pc_particles* out
     ctx->launches += 1;
     pc_phase_end(ctx, ts);
   }
-  {
-    MatchArgs M;
-    M.n = n;
-    M.cap = ctx->cap;
-    M.cand_j = ctx->cand_j;
-    M.cand_t = ctx->cand_t;
-    M.ncand = ctx->ncand;
-    M.best = ctx->best;
-    M.sid = ctx->sid;
-    M.partner = ctx->partner;
-    M.tcoll = ctx->tcoll;
-    M.work = ctx->work;
-    M.pair_lo = ctx->pair_lo;
-    M.pair_hi = ctx->pair_hi;
-    M.pair_t = ctx->pair_t;
-    M.counters = ctx->counters;
-    const int tm = pc_phase_begin(ctx, PC_PH_MATCH);
-    k_match_first<<<pc_blocks(n, 256), 256, 0, st>>>(M);
-    k_match_finish<<<1, kFinishThreads, 0, st>>>(M);
-    ctx->launches += 2;
-    pc_phase_end(ctx, tm);
-  }
+  e = pc_match_launch(ctx, n);
+  if (e != cudaSuccess) goto fail;
   {
     RespondArgs R;
     R.n = n;

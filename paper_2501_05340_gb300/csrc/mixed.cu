@@ -1,0 +1,698 @@
+// Mixed-precision path of the particle operator (arXiv 2501.05340 operator with
+// FP32 cell-relative storage): quantisation, collision step and the per-particle
+// preparation of the tensor-core projection.
+//
+// Compiled with -fmad=false: FP64 and FP32 expressions that define the stored
+// state are evaluated as separate IEEE operations in source order, so the new
+// state is bit-identical to a plain implementation of the same rules.
+#include <math.h>
+#include <string.h>
+
+#include "df32.cuh"
+#include "pc_internal.cuh"
+
+namespace {
+
+constexpr int kMaxCap = 32;
+
+__device__ __forceinline__ int wrapi(int a, int n) {
+  a %= n;
+  return a < 0 ? a + n : a;
+}
+
+__device__ __forceinline__ double minimg_box(double d, double L) {
+  if (d > 0.5 * L) return d - L;
+  if (d < -0.5 * L) return d + L;
+  return d;
+}
+
+__device__ __forceinline__ float minimgf_box(float d, float L) {
+  if (d > 0.5f * L) return d - L;
+  if (d < -0.5f * L) return d + L;
+  return d;
+}
+
+__device__ __forceinline__ double minimg(double d) {
+  if (d > 0.5) return d - 1.0;
+  if (d < -0.5) return d + 1.0;
+  return d;
+}
+
+__device__ __forceinline__ void raise_status(unsigned long long* counters, int code) {
+  atomicMax(&counters[CNT_STATUS], (unsigned long long)code);
+}
+
+__device__ __forceinline__ void cell_coords(int32_t cell, int nc, int c[3]) {
+  c[0] = cell % nc;
+  c[1] = (cell / nc) % nc;
+  c[2] = cell / (nc * nc);
+}
+
+// ------------------------------------------------------------------ quantise
+
+__global__ void k_quantize(int64_t n, int nc, const double* __restrict__ x, const double* __restrict__ v,
+                           const double* __restrict__ r, const double* __restrict__ m, const double* __restrict__ q,
+                           const int32_t* __restrict__ id, int32_t* __restrict__ cell, float* __restrict__ o,
+                           float* __restrict__ vf, float* __restrict__ rf, float* __restrict__ mf,
+                           float* __restrict__ qf, int32_t* __restrict__ ido) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  int c[3];
+  for (int a = 0; a < 3; ++a) {
+    const double s = x[a * n + i] * (double)nc;
+    double fl = floor(s);
+    if (fl < 0.0) fl = 0.0;
+    if (fl > (double)(nc - 1)) fl = (double)(nc - 1);
+    int ci = (int)fl;
+    float oo = (float)(s - fl);
+    if (oo >= 1.0f) {
+      oo = 0.0f;
+      ci = ci + 1 == nc ? 0 : ci + 1;
+    }
+    c[a] = ci;
+    o[a * n + i] = oo;
+    vf[a * n + i] = (float)v[a * n + i];
+  }
+  cell[i] = (c[2] * nc + c[1]) * nc + c[0];
+  rf[i] = (float)r[i];
+  mf[i] = (float)m[i];
+  ido[i] = id[i];
+  if (qf && q)
+    for (int k = 0; k < 4; ++k) qf[k * n + i] = (float)q[k * n + i];
+}
+
+// ------------------------------------------------------------------ keys, gather
+
+__global__ void k_keys_f32(int64_t n, int nc, const int32_t* __restrict__ cell, const float* __restrict__ o,
+                           const float* __restrict__ v, const float* __restrict__ r, const float* __restrict__ m,
+                           int32_t* __restrict__ key, int32_t* __restrict__ slot, int32_t* __restrict__ cnt,
+                           unsigned long long* __restrict__ counters) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  double v2 = 0.0, rr = 0.0;
+  if (i < n) {
+    const int32_t c = cell[i];
+    const int64_t ncell = (int64_t)nc * nc * nc;
+    bool ok = c >= 0 && (int64_t)c < ncell;
+    for (int a = 0; a < 3; ++a) {
+      const float oa = o[a * n + i];
+      ok = ok && oa >= 0.0f && oa < 1.0f && isfinite(v[a * n + i]);
+    }
+    const float ri = r[i], mi = m[i];
+    ok = ok && ri > 0.0f && ri < 0.25f && mi > 0.0f && isfinite(mi);
+    if (!ok) raise_status(counters, PC_EINVAL);
+    const int32_t k = ok ? c : 0;
+    key[i] = k;
+    slot[i] = atomicAdd(&cnt[k], 1);
+    if (ok) {
+      const double v0 = v[i], v1 = v[n + i], vz = v[2 * n + i];
+      v2 = (v0 * v0 + v1 * v1) + vz * vz;
+      rr = ri;
+    }
+  }
+#pragma unroll
+  for (int s = 16; s > 0; s >>= 1) {
+    v2 = fmax(v2, __shfl_xor_sync(0xffffffffu, v2, s));
+    rr = fmax(rr, __shfl_xor_sync(0xffffffffu, rr, s));
+  }
+  if ((threadIdx.x & 31) == 0) {
+    atomicMax(&counters[CNT_VMAX2], (unsigned long long)__double_as_longlong(v2));
+    atomicMax(&counters[CNT_RMAX], (unsigned long long)__double_as_longlong(rr));
+  }
+}
+
+__global__ void k_gather_f32(int64_t n, const int32_t* __restrict__ perm, const int32_t* __restrict__ cell,
+                             const float* __restrict__ o, const float* __restrict__ v, const float* __restrict__ r,
+                             const int32_t* __restrict__ id, int32_t* __restrict__ scell, float* __restrict__ so,
+                             float* __restrict__ sv, float* __restrict__ sr, int32_t* __restrict__ sid) {
+  const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= n) return;
+  const int64_t p = perm[k];
+  scell[k] = cell[p];
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+    so[a * n + k] = o[a * n + p];
+    sv[a * n + k] = v[a * n + p];
+  }
+  sr[k] = r[p];
+  sid[k] = id[p];
+}
+
+// ------------------------------------------------------------------ search
+
+struct SearchF32 {
+  int64_t n;
+  int nc, cap;
+  double dt;
+  const int32_t* scell;
+  const float *so, *sv, *sr;
+  const int32_t* sid;
+  const int32_t* start;
+  int32_t* cand_j;
+  double* cand_t;
+  int32_t* ncand;
+  int32_t* best;
+  unsigned long long* counters;
+};
+
+// Smaller positive root of |dx + t dv| = R in cell units (dx the minimum image in a
+// box of L cells), with the same operations as the FP64 definition; +inf when the
+// pair is not a candidate.
+__device__ double contact_time_cells(const double xi[3], const double xj[3], const double vi[3],
+                                     const double vj[3], double R, double dt, double L) {
+  const double dx0 = minimg_box(xi[0] - xj[0], L);
+  const double dx1 = minimg_box(xi[1] - xj[1], L);
+  const double dx2 = minimg_box(xi[2] - xj[2], L);
+  const double dv0 = vi[0] - vj[0];
+  const double dv1 = vi[1] - vj[1];
+  const double dv2 = vi[2] - vj[2];
+  const double a = (dv0 * dv0 + dv1 * dv1) + dv2 * dv2;
+  const double b = (dx0 * dv0 + dx1 * dv1) + dx2 * dv2;
+  const double c = ((dx0 * dx0 + dx1 * dx1) + dx2 * dx2) - R * R;
+  if (!(b < 0.0)) return CUDART_INF;
+  if (!(c > 0.0)) return CUDART_INF;
+  const double disc = b * b - a * c;
+  if (!(disc > 0.0)) return CUDART_INF;
+  const double t = c / (-b + sqrt(disc));
+  return t <= dt ? t : CUDART_INF;
+}
+
+// Certified FP32 reject test in cell units. Cell differences are exact integers
+// wrapped to the nearest image; offsets are exact FP32, so for candidate pairs
+// (a few cells apart) |dxf - dx| <= 2.4e-7 cells per axis. Velocities in cell
+// units carry 2^-24 relative error. Same bounds as the FP64 path's filter,
+// expressed in cell units.
+__device__ __forceinline__ bool filter_cells(const float dxf[3], const float dvc[3], float Rc, float dt,
+                                             float vmaxc) {
+  const float d2 = dxf[0] * dxf[0] + dxf[1] * dxf[1] + dxf[2] * dxf[2];
+  const float v2 = dvc[0] * dvc[0] + dvc[1] * dvc[1] + dvc[2] * dvc[2];
+  const float vm = sqrtf(v2);
+  const float reach = (Rc + vm * dt) * 1.00001f + 8.0e-7f + 2.5e-7f * vmaxc * dt;
+  if (d2 > reach * reach) return false;
+  const float bf = dxf[0] * dvc[0] + dxf[1] * dvc[1] + dxf[2] * dvc[2];
+  const float bslack = (8.0e-7f + 1.0e-6f * sqrtf(d2)) * (vm + vmaxc);
+  return !(bf > bslack);
+}
+
+__global__ void __launch_bounds__(256) k_search_f32(SearchF32 A) {
+  const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const int64_t n = A.n;
+  const int nc = A.nc;
+  const double L = (double)nc;
+  const float Lf = (float)nc;
+  const double v2max = __longlong_as_double((long long)A.counters[CNT_VMAX2]);
+  const double rmax = __longlong_as_double((long long)A.counters[CNT_RMAX]);
+  const double reach = (2.0 * rmax + 2.0 * sqrt(v2max) * A.dt) * (1.0 + 1e-9) + 1e-12;  // box units
+  double sd = floor(reach * L * (1.0 + 1e-9)) + 1.0;
+  if (sd > L) sd = L;
+  const int s = (int)sd;
+  if (k == 0) {
+    atomicMax(&A.counters[CNT_STENCIL], (unsigned long long)s);
+    if (!(reach < 0.5)) raise_status(A.counters, PC_EINVAL);
+  }
+  int found = 0, solves = 0, cnt = 0;
+  if (k < n) {
+    double lt[kMaxCap];
+    int lj[kMaxCap];
+    int ck[3];
+    cell_coords(A.scell[k], nc, ck);
+    const float ok3[3] = {A.so[k], A.so[n + k], A.so[2 * n + k]};
+    const float vk3[3] = {A.sv[k], A.sv[n + k], A.sv[2 * n + k]};
+    const float rk = A.sr[k];
+    const float dtf = (float)A.dt * 1.000001f;
+    const float vmaxc = (float)(sqrt(v2max) * L) * 1.000001f;
+    const int span = 2 * s + 1;
+    const bool full = span >= nc;
+    const int cnt_ax = full ? nc : span;
+    for (int oz = 0; oz < cnt_ax; ++oz) {
+      const int zc = full ? oz : wrapi(ck[2] - s + oz, nc);
+      for (int oy = 0; oy < cnt_ax; ++oy) {
+        const int yc = full ? oy : wrapi(ck[1] - s + oy, nc);
+        for (int ox = 0; ox < cnt_ax; ++ox) {
+          const int xc = full ? ox : wrapi(ck[0] - s + ox, nc);
+          const int cj[3] = {xc, yc, zc};
+          const int64_t cl = ((int64_t)zc * nc + yc) * nc + xc;
+          const int beg = A.start[cl], end = A.start[cl + 1];
+          for (int j = beg; j < end; ++j) {
+            if (j == k) continue;
+            float dxf[3], dvc[3];
+#pragma unroll
+            for (int a = 0; a < 3; ++a) {
+              int di = ck[a] - cj[a];
+              if (2 * di > nc) di -= nc;
+              else if (2 * di < -nc) di += nc;
+              dxf[a] = minimgf_box((float)di + (ok3[a] - A.so[a * n + j]), Lf);
+              dvc[a] = (vk3[a] - A.sv[a * n + j]) * Lf;
+            }
+            if (!filter_cells(dxf, dvc, (rk + A.sr[j]) * Lf, dtf, vmaxc)) continue;
+            ++solves;
+            double xi[3], xj[3], vi[3], vj[3];
+#pragma unroll
+            for (int a = 0; a < 3; ++a) {
+              xi[a] = (double)ck[a] + (double)ok3[a];
+              xj[a] = (double)cj[a] + (double)A.so[a * n + j];
+              vi[a] = (double)vk3[a] * L;
+              vj[a] = (double)A.sv[a * n + j] * L;
+            }
+            const double R = ((double)rk + (double)A.sr[j]) * L;
+            const double t = contact_time_cells(xi, xj, vi, vj, R, A.dt, L);
+            if (!(t <= A.dt)) continue;
+            ++found;
+            const int jid = A.sid[j];
+            int pos = cnt;
+            while (pos > 0 && (lt[pos - 1] > t || (lt[pos - 1] == t && A.sid[lj[pos - 1]] > jid))) --pos;
+            if (pos >= A.cap) continue;
+            const int last = cnt < A.cap ? cnt : A.cap - 1;
+            for (int q = last; q > pos; --q) {
+              lt[q] = lt[q - 1];
+              lj[q] = lj[q - 1];
+            }
+            lt[pos] = t;
+            lj[pos] = j;
+            if (cnt < A.cap) ++cnt;
+          }
+        }
+      }
+    }
+    for (int q = 0; q < cnt; ++q) {
+      A.cand_j[(int64_t)q * n + k] = lj[q];
+      A.cand_t[(int64_t)q * n + k] = lt[q];
+    }
+    A.ncand[k] = cnt;
+    A.best[k] = cnt > 0 ? lj[0] : -1;
+    if (found > A.cap) raise_status(A.counters, PC_ECAPACITY);
+  }
+  int fsum = found, ssum = solves, fmx = found;
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    fsum += __shfl_xor_sync(0xffffffffu, fsum, o);
+    ssum += __shfl_xor_sync(0xffffffffu, ssum, o);
+    fmx = max(fmx, __shfl_xor_sync(0xffffffffu, fmx, o));
+  }
+  if ((threadIdx.x & 31) == 0) {
+    if (fsum) atomicAdd(&A.counters[CNT_CANDS], (unsigned long long)fsum);
+    if (ssum) atomicAdd(&A.counters[CNT_SOLVES], (unsigned long long)ssum);
+    if (fmx) atomicMax(&A.counters[CNT_MAXCAND], (unsigned long long)fmx);
+  }
+}
+
+// ------------------------------------------------------------------ respond
+
+struct RespondF32 {
+  int64_t n;
+  int nc;
+  double dt, e;
+  const int32_t* scell;
+  const float *so, *sv, *sr;
+  const int32_t* sid;
+  const int32_t* partner;
+  const double* tcoll;
+  const int32_t* perm;
+  const float* m_in;
+  const float* q_in;
+  int32_t* cell_out;
+  float *o_out, *v_out, *r_out, *m_out, *q_out;
+  int32_t* id_out;
+};
+
+// Free particles: o' = o + float(dt nc) v in FP32 with a carry. Colliding pairs:
+// FP64 response (velocities physical, positions in cell units), wrap into [0, nc),
+// stored as floor + FP32 offset, velocity rounded to FP32.
+__global__ void k_respond_f32(RespondF32 R) {
+  const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const int64_t n = R.n;
+  if (k >= n) return;
+  const int nc = R.nc;
+  const double L = (double)nc;
+  const int64_t p = R.perm[k];
+  const int32_t j = R.partner[k];
+  const float mi_f = R.m_in[p];
+  int c[3];
+  cell_coords(R.scell[k], nc, c);
+  float oo[3], vo[3];
+  if (j < 0) {
+    const float dtn = (float)(R.dt * L);
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+      const float va = R.sv[a * n + k];
+      float on = R.so[a * n + k] + dtn * va;
+      if (on >= 1.0f) {
+        on = on - 1.0f;
+        c[a] = c[a] + 1 == nc ? 0 : c[a] + 1;
+      } else if (on < 0.0f) {
+        const float up = on + 1.0f;
+        if (up == 1.0f) {
+          on = 0.0f;
+        } else {
+          on = up;
+          c[a] = c[a] == 0 ? nc - 1 : c[a] - 1;
+        }
+      }
+      oo[a] = on;
+      vo[a] = va;
+    }
+  } else {
+    const double t = R.tcoll[k];
+    int cj[3];
+    cell_coords(R.scell[j], nc, cj);
+    double xi[3], dx[3], dvc[3], dv[3], s3[3], nr[3];
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+      xi[a] = (double)c[a] + (double)R.so[a * n + k];
+      const double xj = (double)cj[a] + (double)R.so[a * n + j];
+      dx[a] = minimg_box(xi[a] - xj, L);
+      dvc[a] = (double)R.sv[a * n + k] * L - (double)R.sv[a * n + j] * L;
+      dv[a] = (double)R.sv[a * n + k] - (double)R.sv[a * n + j];
+    }
+#pragma unroll
+    for (int a = 0; a < 3; ++a) s3[a] = dx[a] + t * dvc[a];
+    const double sl = sqrt((s3[0] * s3[0] + s3[1] * s3[1]) + s3[2] * s3[2]);
+#pragma unroll
+    for (int a = 0; a < 3; ++a) nr[a] = -s3[a] / sl;
+    const double vrn = (dv[0] * nr[0] + dv[1] * nr[1]) + dv[2] * nr[2];
+    const double mi = (double)mi_f, mj = (double)R.m_in[R.perm[j]];
+    const double mr = (mi * mj) / (mi + mj);
+    const double J = -mr * (1.0 + R.e) * vrn;
+    const double gi = J / mi;
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+      const double vold = (double)R.sv[a * n + k];
+      const double vnew = vold + gi * nr[a];
+      double y = (xi[a] + t * (vold * L)) + (R.dt - t) * (vnew * L);
+      if (y < 0.0) y += L;
+      else if (y >= L) y -= L;
+      double fl = floor(y);
+      if (fl < 0.0) fl = 0.0;
+      if (fl > (double)(nc - 1)) fl = (double)(nc - 1);
+      int cq = (int)fl;
+      float oq = (float)(y - fl);
+      if (oq >= 1.0f) {
+        oq = 0.0f;
+        cq = cq + 1 == nc ? 0 : cq + 1;
+      }
+      c[a] = cq;
+      oo[a] = oq;
+      vo[a] = (float)vnew;
+    }
+  }
+  R.cell_out[k] = (c[2] * nc + c[1]) * nc + c[0];
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+    R.o_out[a * n + k] = oo[a];
+    R.v_out[a * n + k] = vo[a];
+  }
+  R.r_out[k] = R.sr[k];
+  R.m_out[k] = mi_f;
+  R.id_out[k] = R.sid[k];
+  if (R.q_out)
+    for (int q = 0; q < 4; ++q) R.q_out[q * n + k] = R.q_in[q * n + p];
+}
+
+// ------------------------------------------------------------------ projection prep
+
+// Element of a cell-relative coordinate: floor((c + o) ne / nc) in df32, the same
+// function for the binning and for the factors.
+__device__ __forceinline__ int elem_of(int c, float o, f2 rnn, int ne, float* t) {
+  const f2 xc = two_sum((float)c, o);  // exact
+  const f2 u = df_mul(xc, rnn);
+  float e = floorf(u.h);
+  if (u.h == e && u.l < 0.0f) e -= 1.0f;
+  int ei = (int)e;
+  float tt = (u.h - e) + u.l;
+  if (ei < 0) {
+    ei = 0;
+    tt = 0.0f;
+  }
+  if (ei > ne - 1) {
+    ei = ne - 1;
+    tt = 1.0f;
+  }
+  *t = tt;
+  return ei;
+}
+
+__global__ void k_elem_keys_f32(int64_t n, int nc, int ne, f2 rnn, const int32_t* __restrict__ cell,
+                                const float* __restrict__ o, int32_t* __restrict__ key, int32_t* __restrict__ slot,
+                                int32_t* __restrict__ cnt, unsigned long long* __restrict__ counters) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  int c[3];
+  const int32_t cl = cell[i];
+  if (!(cl >= 0 && (int64_t)cl < (int64_t)nc * nc * nc)) raise_status(counters, PC_EINVAL);
+  cell_coords(cl < 0 ? 0 : cl, nc, c);
+  int e[3];
+  float t;
+  for (int a = 0; a < 3; ++a) {
+    const float oa = o[a * n + i];
+    if (!(oa >= 0.0f && oa < 1.0f)) raise_status(counters, PC_EINVAL);
+    e[a] = elem_of(min(max(c[a], 0), nc - 1), oa, rnn, ne, &t);
+  }
+  const int k = (e[2] * ne + e[1]) * ne + e[0];
+  key[i] = k;
+  slot[i] = atomicAdd(&cnt[k], 1);
+}
+
+struct PrepF32 {
+  int64_t n;
+  int nc, ne, n1, rho, win;
+  f2 rnn;           // ne / nc
+  float rce;        // cutoff in element units
+  float c2l;        // h^2 / (2 sigma^2) log2(e)
+  double h, rc;
+  float s[64];      // window node offsets o + (eta_i + 1)/2 in element units
+  float wq[16];     // Gauss weights
+  double eta[16];
+  const int32_t* perm;
+  const int32_t* cell;
+  const float* o;
+  const float* q;
+  float4* rec;      // [n][4]
+};
+
+// Per particle (sorted by element): position t_a in its own element's units, the
+// inside-cutoff mask of the 3 (2 rho + 1) n1 window nodes, 1/Z_a with
+// Z_a = sum over inside nodes of w_i exp(-(delta h)^2/(2 sigma^2)), and q.
+// A node whose FP32 distance is within 1e-4 relative of the cutoff is decided in
+// FP64 on the stored position x = (c + o)/nc with the plain definition.
+__global__ void __launch_bounds__(128) k_proj_prep_f32(PrepF32 P) {
+  const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const int64_t n = P.n;
+  if (k >= n) return;
+  const int64_t p = P.perm[k];
+  int c[3];
+  cell_coords(P.cell[p], P.nc, c);
+  float t3[3], iz[3];
+  unsigned mask[3];
+  for (int a = 0; a < 3; ++a) {
+    const float oa = P.o[a * n + p];
+    float t;
+    const int ea = elem_of(c[a], oa, P.rnn, P.ne, &t);
+    float Z = 0.0f;
+    unsigned mk = 0u;
+    for (int w = 0; w < P.win; ++w) {
+      const float d = P.s[w] - t;
+      const float ad = fabsf(d);
+      bool inside;
+      if (fabsf(ad - P.rce) > 1e-4f * P.rce) {
+        inside = ad < P.rce;
+      } else {
+        const int i = w % P.n1, off = w / P.n1 - P.rho;
+        const int ge = wrapi(ea + off, P.ne);
+        const double x = ((double)c[a] + (double)oa) / (double)P.nc;
+        const double X = ((double)ge + 0.5 * (P.eta[i] + 1.0)) * P.h;
+        inside = fabs(minimg(X - x)) <= P.rc;
+      }
+      if (inside) {
+        mk |= 1u << w;
+        Z += P.wq[w % P.n1] * exp2f(-(d * d) * P.c2l);
+      }
+    }
+    t3[a] = t;
+    iz[a] = Z > 0.0f ? 1.0f / Z : 0.0f;
+    mask[a] = mk;
+  }
+  float4* rp = P.rec + 4 * k;
+  const float q0 = P.q[p], q1 = P.q[n + p], q2 = P.q[2 * n + p], q3 = P.q[3 * n + p];
+  rp[0] = make_float4(t3[0], t3[1], t3[2], iz[0]);
+  rp[1] = make_float4(iz[1], iz[2], q0, q1);
+  rp[2] = make_float4(q2, q3, __uint_as_float(mask[0]), __uint_as_float(mask[1]));
+  rp[3] = make_float4(__uint_as_float(mask[2]), 0.0f, 0.0f, 0.0f);
+}
+
+}  // namespace
+
+pc_status pc_quantize_impl(pc_ctx* ctx, const pc_particles* in, pc_particles_f32* out) {
+  const int64_t n = in->n;
+  if (n == 0) return PC_OK;
+  k_quantize<<<pc_blocks(n, 256), 256, 0, ctx->stream>>>(n, ctx->nc, in->x, in->v, in->r, in->m, in->q, in->id,
+                                                          out->cell, out->o, out->v, out->r, out->m, out->q, out->id);
+  ctx->launches += 1;
+  const cudaError_t e = cudaGetLastError();
+  if (e == cudaSuccess) return PC_OK;
+  snprintf(ctx->err, sizeof(ctx->err), "pc_quantize: %s", cudaGetErrorString(e));
+  return PC_ECUDA;
+}
+
+pc_status pc_collide_f32_impl(pc_ctx* ctx, const pc_particles_f32* in, pc_particles_f32* out, double dt) {
+  const int64_t n = in->n;
+  cudaStream_t st = ctx->stream;
+  cudaError_t e = cudaMemsetAsync(ctx->counters, 0, sizeof(unsigned long long) * CNT_N, st);
+  if (e == cudaSuccess && n == 0) return PC_OK;
+  if (e == cudaSuccess) e = cudaMemsetAsync(ctx->cnt, 0, sizeof(int32_t) * (size_t)ctx->ncell, st);
+  if (e != cudaSuccess) goto fail;
+  {
+    const int tb = pc_phase_begin(ctx, PC_PH_BIN);
+    k_keys_f32<<<pc_blocks(n, 256), 256, 0, st>>>(n, ctx->nc, in->cell, in->o, in->v, in->r, in->m, ctx->key,
+                                                   ctx->slot, ctx->cnt, ctx->counters);
+    ctx->launches += 1;
+    e = pc_bin_finish(n, ctx->ncell, ctx->key, ctx->slot, in->id, ctx->cnt, ctx->start, ctx->blocksums, ctx->perm, st,
+                      &ctx->launches);
+    pc_phase_end(ctx, tb);
+  }
+  if (e != cudaSuccess) goto fail;
+  {
+    const int tg = pc_phase_begin(ctx, PC_PH_GATHER);
+    k_gather_f32<<<pc_blocks(n, 256), 256, 0, st>>>(n, ctx->perm, in->cell, in->o, in->v, in->r, in->id,
+                                                     ctx->scell, ctx->sxf, ctx->svf, ctx->srf, ctx->sid);
+    ctx->launches += 1;
+    pc_phase_end(ctx, tg);
+  }
+  {
+    SearchF32 A;
+    A.n = n;
+    A.nc = ctx->nc;
+    A.cap = ctx->cap;
+    A.dt = dt;
+    A.scell = ctx->scell;
+    A.so = ctx->sxf;
+    A.sv = ctx->svf;
+    A.sr = ctx->srf;
+    A.sid = ctx->sid;
+    A.start = ctx->start;
+    A.cand_j = ctx->cand_j;
+    A.cand_t = ctx->cand_t;
+    A.ncand = ctx->ncand;
+    A.best = ctx->best;
+    A.counters = ctx->counters;
+    const int ts = pc_phase_begin(ctx, PC_PH_SEARCH);
+    k_search_f32<<<pc_blocks(n, 256), 256, 0, st>>>(A);
+    ctx->launches += 1;
+    pc_phase_end(ctx, ts);
+  }
+  e = pc_match_launch(ctx, n);
+  if (e != cudaSuccess) goto fail;
+  {
+    RespondF32 R;
+    R.n = n;
+    R.nc = ctx->nc;
+    R.dt = dt;
+    R.e = ctx->cfg.restitution;
+    R.scell = ctx->scell;
+    R.so = ctx->sxf;
+    R.sv = ctx->svf;
+    R.sr = ctx->srf;
+    R.sid = ctx->sid;
+    R.partner = ctx->partner;
+    R.tcoll = ctx->tcoll;
+    R.perm = ctx->perm;
+    R.m_in = in->m;
+    R.q_in = in->q;
+    R.cell_out = out->cell;
+    R.o_out = out->o;
+    R.v_out = out->v;
+    R.r_out = out->r;
+    R.m_out = out->m;
+    R.q_out = in->q ? out->q : nullptr;
+    R.id_out = out->id;
+    const int tr = pc_phase_begin(ctx, PC_PH_RESPOND);
+    k_respond_f32<<<pc_blocks(n, 256), 256, 0, st>>>(R);
+    ctx->launches += 1;
+    pc_phase_end(ctx, tr);
+  }
+  e = cudaGetLastError();
+  if (e == cudaSuccess) return PC_OK;
+fail:
+  snprintf(ctx->err, sizeof(ctx->err), "pc_collide_f32: %s", cudaGetErrorString(e));
+  return PC_ECUDA;
+}
+
+pc_status pc_project_f32_impl(pc_ctx* ctx, const pc_particles_f32* p, float* field, int tc_type) {
+  const int64_t n = p->n;
+  cudaStream_t st = ctx->stream;
+  const int ne = ctx->cfg.ne;
+  const int64_t nel = (int64_t)ne * ne * ne;
+  const double rnn = (double)ne / (double)ctx->nc;
+  const f2 rnnf = {(float)rnn, (float)(rnn - (double)(float)rnn)};
+  cudaError_t e = cudaMemsetAsync(ctx->cnt, 0, sizeof(int32_t) * (size_t)nel, st);
+  if (e != cudaSuccess) goto fail;
+  {
+    const int tb = pc_phase_begin(ctx, PC_PH_PBIN);
+    if (n > 0) {
+      k_elem_keys_f32<<<pc_blocks(n, 256), 256, 0, st>>>(n, ctx->nc, ne, rnnf, p->cell, p->o, ctx->key, ctx->slot,
+                                                          ctx->cnt, ctx->counters);
+      ctx->launches += 1;
+    }
+    e = pc_bin_finish(n, nel, ctx->key, ctx->slot, p->id, ctx->cnt, ctx->start, ctx->blocksums, ctx->perm, st,
+                      &ctx->launches);
+    pc_phase_end(ctx, tb);
+  }
+  if (e != cudaSuccess) goto fail;
+  if (n > 0) {
+    PrepF32 P;
+    memset(&P, 0, sizeof(P));
+    P.n = n;
+    P.nc = ctx->nc;
+    P.ne = ne;
+    P.n1 = ctx->n1;
+    P.rho = ctx->rho;
+    P.win = ctx->win;
+    P.rnn = rnnf;
+    P.h = ctx->h;
+    P.rc = ctx->cfg.cutoff_sigmas * ctx->cfg.sigma;
+    P.rce = (float)(P.rc * ne);
+    P.c2l = (float)(ctx->h * ctx->h / (2.0 * ctx->cfg.sigma * ctx->cfg.sigma) * 1.4426950408889634);
+    for (int w = 0; w < ctx->win; ++w)
+      P.s[w] = (float)((double)(w / ctx->n1 - ctx->rho) + 0.5 * (ctx->eta[w % ctx->n1] + 1.0));
+    for (int i = 0; i < ctx->n1; ++i) {
+      P.wq[i] = (float)ctx->w[i];
+      P.eta[i] = ctx->eta[i];
+    }
+    P.perm = ctx->perm;
+    P.cell = p->cell;
+    P.o = p->o;
+    P.q = p->q;
+    P.rec = (float4*)ctx->fac;
+    const int tf = pc_phase_begin(ctx, PC_PH_FACTORS);
+    k_proj_prep_f32<<<pc_blocks(n, 128), 128, 0, st>>>(P);
+    ctx->launches += 1;
+    pc_phase_end(ctx, tf);
+  }
+  {
+    TcDepositArgs T;
+    memset(&T, 0, sizeof(T));
+    T.n = n;
+    T.ne = ne;
+    T.n1 = ctx->n1;
+    T.rho = ctx->rho;
+    T.tc_type = tc_type;
+    T.c2l = (float)(ctx->h * ctx->h / (2.0 * ctx->cfg.sigma * ctx->cfg.sigma) * 1.4426950408889634);
+    T.rce = (float)(ctx->cfg.cutoff_sigmas * ctx->cfg.sigma * ne);
+    for (int i = 0; i < ctx->n1; ++i) T.s[i] = (float)(0.5 * (ctx->eta[i] + 1.0));
+    T.start = ctx->start;
+    T.rec = (const float4*)ctx->fac;
+    T.field = field;
+    T.counters = ctx->counters;
+    const double sc = 8.0 * (double)ne * ne * ne;
+    T.scale_out = (float)(sc / 4096.0);  // operands scaled by 2^8 (YZ) and 2^4 (A)
+    const int td = pc_phase_begin(ctx, PC_PH_DEPOSIT);
+    int nb = 0;
+    e = pc_tc_deposit_launch(T, st, &nb);
+    ctx->launches += 1;
+    pc_phase_end(ctx, td);
+    if (e != cudaSuccess) goto fail;
+  }
+  e = cudaGetLastError();
+  if (e == cudaSuccess) return PC_OK;
+fail:
+  snprintf(ctx->err, sizeof(ctx->err), "pc_project_f32: %s", cudaGetErrorString(e));
+  return PC_ECUDA;
+}

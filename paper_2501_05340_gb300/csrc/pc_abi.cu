@@ -82,7 +82,7 @@ pc_status fail(pc_ctx* ctx, pc_status s, const char* msg) {
 void free_all(pc_ctx* c) {
   void* ptrs[] = {c->cnt, c->start, c->blocksums, c->key, c->slot, c->perm, c->sx, c->sv, c->sr,
                   c->sid, c->sxf, c->svf, c->srf, c->cand_j, c->cand_t, c->ncand, c->best, c->partner,
-                  c->work, c->tcoll, c->pair_lo, c->pair_hi, c->pair_t, c->counters, c->fac, c->sq};
+                  c->work, c->tcoll, c->pair_lo, c->pair_hi, c->pair_t, c->counters, c->fac, c->sq, c->scell};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   if (c->h_counters) cudaFreeHost(c->h_counters);
@@ -165,6 +165,7 @@ pc_status pc_init(pc_ctx** out, const pc_config* cfg) {
   chk(dalloc(&ctx->best, n));
   chk(dalloc(&ctx->partner, n));
   chk(dalloc(&ctx->work, n));
+  chk(dalloc(&ctx->scell, n));
   chk(dalloc(&ctx->tcoll, n));
   chk(dalloc(&ctx->pair_lo, n / 2 + 1));
   chk(dalloc(&ctx->pair_hi, n / 2 + 1));
@@ -205,6 +206,42 @@ pc_status pc_project(pc_ctx* ctx, const pc_particles* p, double* field) {
   return pc_project_impl(ctx, p, field);
 }
 
+int32_t pc_cells_per_side(const pc_ctx* ctx) { return ctx ? ctx->nc : 0; }
+
+static bool particles_f32_ok(const pc_particles_f32* p, int64_t n_max) {
+  return p && p->n >= 0 && p->n <= n_max && (p->n == 0 || (p->id && p->cell && p->o && p->v && p->r && p->m));
+}
+
+pc_status pc_quantize(pc_ctx* ctx, const pc_particles* in, pc_particles_f32* out) {
+  if (!ctx) return PC_EINVAL;
+  if (!particles_ok(in, ctx->cfg.n_max) || !particles_f32_ok(out, ctx->cfg.n_max) || in->n != out->n)
+    return fail(ctx, PC_EINVAL, "pc_quantize: bad particle arrays");
+  return pc_quantize_impl(ctx, in, out);
+}
+
+pc_status pc_collide_f32(pc_ctx* ctx, const pc_particles_f32* in, pc_particles_f32* out, double dt) {
+  if (!ctx) return PC_EINVAL;
+  if (!particles_f32_ok(in, ctx->cfg.n_max) || !particles_f32_ok(out, ctx->cfg.n_max) || in->n != out->n)
+    return fail(ctx, PC_EINVAL, "pc_collide_f32: bad particle arrays");
+  if (in->n > 0 && (in->cell == out->cell || in->o == out->o || in->v == out->v || in->id == out->id ||
+                    in->r == out->r || in->m == out->m))
+    return fail(ctx, PC_EINVAL, "pc_collide_f32: in and out must be distinct buffers");
+  if (in->n > 0 && in->q && (!out->q || out->q == in->q))
+    return fail(ctx, PC_EINVAL, "pc_collide_f32: out->q must be a distinct buffer when in->q is given");
+  if (!(dt > 0.0 && dt < INFINITY)) return fail(ctx, PC_EINVAL, "pc_collide_f32: dt must be positive and finite");
+  return pc_collide_f32_impl(ctx, in, out, dt);
+}
+
+pc_status pc_project_f32(pc_ctx* ctx, const pc_particles_f32* p, float* field, int32_t tc_type) {
+  if (!ctx) return PC_EINVAL;
+  if (!particles_f32_ok(p, ctx->cfg.n_max) || !field || (p->n > 0 && !p->q) ||
+      (tc_type != PC_TC_F16 && tc_type != PC_TC_BF16))
+    return fail(ctx, PC_EINVAL, "pc_project_f32: bad arguments");
+  if (ctx->n1 > 8 || ctx->win > 32)
+    return fail(ctx, PC_EINVAL, "pc_project_f32: needs N + 1 <= 8 and (2 rho + 1)(N + 1) <= 32");
+  return pc_project_f32_impl(ctx, p, field, tc_type);
+}
+
 pc_status pc_sync(pc_ctx* ctx) {
   if (!ctx) return PC_EINVAL;
   cudaError_t e = cudaStreamSynchronize(ctx->stream);
@@ -218,8 +255,8 @@ pc_status pc_sync(pc_ctx* ctx) {
   if (st) {
     static const char* names[] = {"ok", "invalid particle data (position outside [0,1), radius, mass or velocity)",
                                   "", "", "matching did not converge",
-                                  "candidate list overflow: raise cand_cap"};
-    snprintf(ctx->err, sizeof(ctx->err), "device: %s", st < 6 ? names[st] : "unknown");
+                                  "candidate list overflow: raise cand_cap", "a bounded wait in a kernel expired"};
+    snprintf(ctx->err, sizeof(ctx->err), "device: %s", st < 7 ? names[st] : "unknown");
     const unsigned long long z = 0;
     cudaMemcpy(ctx->counters + CNT_STATUS, &z, sizeof(z), cudaMemcpyHostToDevice);
   }

@@ -49,6 +49,7 @@ struct pc_ctx {
   int32_t* cand_j;
   double* cand_t;
   int32_t *ncand, *best, *partner, *work;
+  int32_t* scell;  // sorted linear cells (mixed path)
   double* tcoll;
   int32_t *pair_lo, *pair_hi;
   double* pair_t;
@@ -99,6 +100,27 @@ void pc_build_exp_table(DfExpTable* tab);
 
 // ---- collide (collide.cu) ----------------------------------------------------
 pc_status pc_collide_impl(pc_ctx* ctx, const pc_particles* in, pc_particles* out, double dt);
+// Matching rounds on the candidate lists left by a search kernel (both paths).
+cudaError_t pc_match_launch(pc_ctx* ctx, int64_t n);
+
+// ---- mixed-precision path (mixed.cu, tc_deposit.cu) --------------------------
+pc_status pc_quantize_impl(pc_ctx* ctx, const pc_particles* in, pc_particles_f32* out);
+pc_status pc_collide_f32_impl(pc_ctx* ctx, const pc_particles_f32* in, pc_particles_f32* out, double dt);
+pc_status pc_project_f32_impl(pc_ctx* ctx, const pc_particles_f32* p, float* field, int tc_type);
+// Tensor-core deposit over the prepared particle records (tc_deposit.cu).
+struct TcDepositArgs {
+  int64_t n;
+  int ne, n1, rho, tc_type;
+  float c2l;        // h^2 / (2 sigma^2) log2(e): exponent factor for exp2 in element units
+  float rce;        // cutoff in element units
+  float scale_out;  // (2/h)^3 / (operand scalings)
+  float s[16];      // (eta_i + 1) / 2
+  const int32_t* start;
+  const float4* rec;  // [n][4]: (t0 t1 t2 iz0) (iz1 iz2 q0 q1) (q2 q3 mask0 mask1) (mask2 - - -)
+  float* field;
+  unsigned long long* counters;
+};
+cudaError_t pc_tc_deposit_launch(const TcDepositArgs& A, cudaStream_t st, int* nblocks);
 
 // ---- project (project.cu) ----------------------------------------------------
 pc_status pc_project_impl(pc_ctx* ctx, const pc_particles* p, double* field);

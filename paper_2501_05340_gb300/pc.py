@@ -16,8 +16,10 @@ from . import build as _build
 
 c_i64, c_i32, c_d, c_p = ctypes.c_int64, ctypes.c_int32, ctypes.c_double, ctypes.c_void_p
 
-PC_OK, PC_EINVAL, PC_ENOMEM, PC_ECUDA, PC_ENOCONVERGE, PC_ECAPACITY = range(6)
-STATUS_NAMES = {0: "PC_OK", 1: "PC_EINVAL", 2: "PC_ENOMEM", 3: "PC_ECUDA", 4: "PC_ENOCONVERGE", 5: "PC_ECAPACITY"}
+PC_OK, PC_EINVAL, PC_ENOMEM, PC_ECUDA, PC_ENOCONVERGE, PC_ECAPACITY, PC_ETIMEOUT = range(7)
+STATUS_NAMES = {0: "PC_OK", 1: "PC_EINVAL", 2: "PC_ENOMEM", 3: "PC_ECUDA", 4: "PC_ENOCONVERGE", 5: "PC_ECAPACITY",
+                6: "PC_ETIMEOUT"}
+PC_TC_F16, PC_TC_BF16 = 0, 1
 
 
 class PcConfig(ctypes.Structure):
@@ -28,6 +30,11 @@ class PcConfig(ctypes.Structure):
 
 class PcParticles(ctypes.Structure):
     _fields_ = [("n", c_i64), ("id", c_p), ("x", c_p), ("v", c_p), ("r", c_p), ("m", c_p), ("q", c_p)]
+
+
+class PcParticlesF32(ctypes.Structure):
+    _fields_ = [("n", c_i64), ("id", c_p), ("cell", c_p), ("o", c_p), ("v", c_p), ("r", c_p), ("m", c_p),
+                ("q", c_p)]
 
 
 class PcStats(ctypes.Structure):
@@ -61,6 +68,13 @@ def library():
         lib.pc_sync.argtypes = [c_p]
         lib.pc_set_timing.argtypes = [c_p, ctypes.c_int]
         lib.pc_get_timing.argtypes = [c_p, c_p, c_p]
+        lib.pc_cells_per_side.argtypes = [c_p]
+        lib.pc_cells_per_side.restype = ctypes.c_int32
+        lib.pc_quantize.argtypes = [c_p, ctypes.POINTER(PcParticles), ctypes.POINTER(PcParticlesF32)]
+        lib.pc_collide_f32.argtypes = [c_p, ctypes.POINTER(PcParticlesF32), ctypes.POINTER(PcParticlesF32), c_d]
+        lib.pc_project_f32.argtypes = [c_p, ctypes.POINTER(PcParticlesF32), c_p, ctypes.c_int32]
+        for f in ("pc_quantize", "pc_collide_f32", "pc_project_f32"):
+            getattr(lib, f).restype = ctypes.c_int
         lib.pc_project_noalloc.argtypes = [ctypes.POINTER(PcConfig), ctypes.POINTER(PcParticles), c_p,
                                             ctypes.c_char_p, c_i64]
         lib.pc_project_noalloc.restype = ctypes.c_int
@@ -130,6 +144,51 @@ class State:
         return out
 
 
+class StateF32:
+    """FP32 cell-relative device particle state of the mixed-precision path."""
+
+    def __init__(self, id, cell, o, v, r, m, q=None):
+        self.id, self.cell, self.o, self.v, self.r, self.m, self.q = id, cell, o, v, r, m, q
+        n = r.shape[0]
+        for name, t, shape, dt in (("id", id, (n,), torch.int32), ("cell", cell, (n,), torch.int32),
+                                   ("o", o, (3, n), torch.float32), ("v", v, (3, n), torch.float32),
+                                   ("r", r, (n,), torch.float32), ("m", m, (n,), torch.float32)):
+            if tuple(t.shape) != shape or t.dtype != dt or not t.is_contiguous() or not t.is_cuda:
+                raise ValueError("StateF32.%s must be a contiguous CUDA %s tensor of shape %s" % (name, dt, shape))
+        if q is not None and (tuple(q.shape) != (4, n) or q.dtype != torch.float32 or not q.is_contiguous()):
+            raise ValueError("StateF32.q must be a contiguous CUDA float32 tensor of shape (4, n)")
+
+    @property
+    def n(self):
+        return self.r.shape[0]
+
+    @staticmethod
+    def empty(n, device="cuda", with_q=True):
+        f = dict(dtype=torch.float32, device=device)
+        i = dict(dtype=torch.int32, device=device)
+        return StateF32(torch.empty(n, **i), torch.empty(n, **i), torch.empty(3, n, **f), torch.empty(3, n, **f),
+                        torch.empty(n, **f), torch.empty(n, **f), torch.empty(4, n, **f) if with_q else None)
+
+    @staticmethod
+    def from_arrays(d, device="cuda", with_q=True):
+        """From numpy arrays id, cell, o[3][n], v[3][n], r, m, q[4][n]."""
+        t = lambda a, dt: torch.as_tensor(np.ascontiguousarray(a)).to(device=device, dtype=dt)
+        return StateF32(t(d["id"], torch.int32), t(d["cell"], torch.int32), t(d["o"], torch.float32),
+                        t(d["v"], torch.float32), t(d["r"], torch.float32), t(d["m"], torch.float32),
+                        t(d["q"], torch.float32) if with_q and "q" in d else None)
+
+    def struct(self):
+        return PcParticlesF32(self.n, _ptr(self.id), _ptr(self.cell), _ptr(self.o), _ptr(self.v), _ptr(self.r),
+                              _ptr(self.m), _ptr(self.q))
+
+    def numpy(self):
+        out = dict(id=self.id.cpu().numpy(), cell=self.cell.cpu().numpy(), o=self.o.cpu().numpy(),
+                   v=self.v.cpu().numpy(), r=self.r.cpu().numpy(), m=self.m.cpu().numpy())
+        if self.q is not None:
+            out["q"] = self.q.cpu().numpy()
+        return out
+
+
 class Context:
     """One operator instance (pc_init). All calls run on ``stream`` (default: torch's current)."""
 
@@ -165,6 +224,31 @@ class Context:
             raise ValueError("field must be contiguous float64 of shape (%d, 4, %d)" % (nel, self.n1 ** 3))
         s = state.struct()
         self._check(library().pc_project(self._h, ctypes.byref(s), _ptr(field)))
+
+    @property
+    def cells_per_side(self):
+        return int(library().pc_cells_per_side(self._h))
+
+    def quantize(self, src, dst):
+        """FP64 State -> FP32 cell-relative StateF32 (same order)."""
+        a, b = src.struct(), dst.struct()
+        self._check(library().pc_quantize(self._h, ctypes.byref(a), ctypes.byref(b)))
+
+    def collide_f32(self, src, dst, dt):
+        a, b = src.struct(), dst.struct()
+        self._check(library().pc_collide_f32(self._h, ctypes.byref(a), ctypes.byref(b), float(dt)))
+
+    def project_f32(self, state, field, tc="f16"):
+        """FP32 field[ne^3, 4, n1^3] <- tensor-core projection (tc = "f16" or "bf16")."""
+        nel = self.ne ** 3
+        if tuple(field.shape) != (nel, 4, self.n1 ** 3) or field.dtype != torch.float32 or not field.is_contiguous():
+            raise ValueError("field must be contiguous float32 of shape (%d, 4, %d)" % (nel, self.n1 ** 3))
+        s = state.struct()
+        t = PC_TC_BF16 if tc == "bf16" else PC_TC_F16
+        self._check(library().pc_project_f32(self._h, ctypes.byref(s), _ptr(field), t))
+
+    def new_field_f32(self):
+        return torch.empty(self.ne ** 3, 4, self.n1 ** 3, dtype=torch.float32, device="cuda")
 
     def new_field(self):
         return torch.empty(self.ne ** 3, 4, self.n1 ** 3, dtype=torch.float64, device="cuda")

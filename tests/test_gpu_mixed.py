@@ -1,0 +1,163 @@
+"""Mixed-precision path (FP32 cell-relative storage, tensor-core projection) through
+the C ABI, against the oracle.
+
+Collisions: pairs, cells, offsets and velocities bit-identical to the oracle's
+cell-relative step. Projection: FP16 split within 1e-5 normwise per component of
+the FP64 oracle field of the stored (dequantized) state; BF16 within 1e-4.
+"""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2501_05340_gb300 import inputs
+from tests.gpu_helpers import by_id, field_err, oracle_pairs
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+if not torch.cuda.is_available():
+    pytest.skip("needs a CUDA GPU", allow_module_level=True)
+
+from paper_2501_05340_gb300 import pc  # noqa: E402
+
+F16_TOL = 1e-5
+BF16_TOL = 1e-4
+
+
+def mixed_state(w, ctx):
+    """FP64 workload -> GPU FP32 cell-relative state via pc_quantize."""
+    s64 = pc.State.from_arrays(w)
+    s32 = pc.StateF32.empty(s64.n)
+    ctx.quantize(s64, s32)
+    ctx.sync()
+    return s32
+
+
+def test_quantize_matches_oracle_rule():
+    w = inputs.draw("mixed_16m", seed=0, n=20000)
+    ctx = pc.Context(w["x"].shape[1], 64, 7, 4e-3, w["e"], pc.reach_of(w["r"], w["v"], w["dt"]))
+    s32 = mixed_state(w, ctx)
+    g = s32.numpy()
+    cell, o = oracle.quantize(w["x"], ctx.cells_per_side)
+    assert np.array_equal(g["cell"], cell) and np.array_equal(g["o"], o)
+    assert np.array_equal(g["v"], w["v"].astype(np.float32))
+    assert np.all((g["o"] >= 0) & (g["o"] < 1))
+
+
+@pytest.mark.parametrize("name,n,dtmul", [("mixed_16m", 3000, 60), ("dense_1m", 2500, 25), ("small_8192", 2000, 1)])
+def test_collide_f32_bit_identical(name, n, dtmul):
+    w = inputs.draw(name, seed=1, n=n)
+    dt = dtmul * w["dt"]
+    ctx = pc.Context(n, w["workload"].ne, w["workload"].degree, w["workload"].sigma, w["e"],
+                     pc.reach_of(w["r"], w["v"], dt))
+    nc = ctx.cells_per_side
+    a = mixed_state(w, ctx)
+    b = pc.StateF32.empty(n)
+    cur = by_id(a.numpy())
+    total = 0
+    for step in range(5):
+        ctx.collide_f32(a, b, dt)
+        ctx.sync()
+        gids, gt = ctx.pairs()
+        cell, o, v, partner, tc, k = oracle.collide_step_cellrel(cur["cell"], cur["o"], cur["v"], cur["r"], cur["m"],
+                                                                 cur["id"], nc, w["e"], dt)
+        oids, ot = oracle_pairs(partner, tc, cur["id"])
+        assert np.array_equal(gids, oids) and np.array_equal(gt, ot)
+        g = by_id(b.numpy())
+        assert np.array_equal(g["cell"], cell), "cells differ"
+        assert np.array_equal(g["o"], o), "offsets differ"
+        assert np.array_equal(g["v"], v), "velocities differ"
+        assert np.array_equal(g["q"], cur["q"]) and np.array_equal(g["m"], cur["m"])
+        cur = dict(cur)
+        cur["cell"], cur["o"], cur["v"] = cell, o, v
+        total += k
+        a, b = b, a
+    assert total > 0
+
+
+def _oracle_field_of(s32np, nc, wl, ne=None):
+    x = oracle.dequantize(s32np["cell"], s32np["o"], nc)
+    return oracle.project(x, s32np["q"].astype(np.float64), ne or wl.ne, wl.degree, wl.sigma, wl.cutoff_sigmas)[0]
+
+
+@pytest.mark.parametrize("tc,tol", [("f16", F16_TOL), ("bf16", BF16_TOL)])
+def test_project_f32_reduced_mesh(tc, tol):
+    """16^3 mesh, degree 7, sigma = 0.016 (3 sigma < h), 20000 particles."""
+    w = inputs.draw("mixed_16m", seed=2, n=20000)
+    ctx = pc.Context(w["x"].shape[1], 16, 7, 0.016, w["e"], pc.reach_of(w["r"], w["v"], w["dt"]))
+    s32 = mixed_state(w, ctx)
+    f = ctx.new_field_f32()
+    ctx.project_f32(s32, f, tc)
+    ctx.sync()
+    F = f.cpu().numpy().astype(np.float64)
+    g = s32.numpy()
+    x = oracle.dequantize(g["cell"], g["o"], ctx.cells_per_side)
+    R, _ = oracle.project(x, g["q"].astype(np.float64), 16, 7, 0.016, 3.0)
+    err = field_err(F, R)
+    print("normwise error per component (%s):" % tc, err)
+    assert np.all(err <= tol), err
+
+
+@pytest.mark.parametrize("n", [1, 17, 300])
+def test_project_f32_small_counts(n):
+    w = inputs.draw("small_8192", seed=3, n=n)
+    wl = w["workload"]
+    ctx = pc.Context(n, wl.ne, wl.degree, wl.sigma, w["e"], pc.reach_of(w["r"], w["v"], w["dt"]))
+    s32 = mixed_state(w, ctx)
+    f = ctx.new_field_f32()
+    ctx.project_f32(s32, f, "f16")
+    ctx.sync()
+    g = s32.numpy()
+    x = oracle.dequantize(g["cell"], g["o"], ctx.cells_per_side)
+    R, _ = oracle.project(x, g["q"].astype(np.float64), wl.ne, wl.degree, wl.sigma, wl.cutoff_sigmas)
+    assert np.all(field_err(f.cpu().numpy().astype(np.float64), R) <= F16_TOL)
+
+
+def test_project_f32_deterministic():
+    w = inputs.draw("mixed_16m", seed=4, n=20000)
+    ctx = pc.Context(w["x"].shape[1], 16, 7, 0.016, w["e"], pc.reach_of(w["r"], w["v"], w["dt"]))
+    s32 = mixed_state(w, ctx)
+    f1, f2 = ctx.new_field_f32(), ctx.new_field_f32()
+    ctx.project_f32(s32, f1)
+    ctx.project_f32(s32, f2)
+    ctx.sync()
+    assert torch.equal(f1, f2)
+
+
+def test_project_f32_full_size_sampled():
+    """16,777,216 spheres on the 64^3 degree-7 mesh: conservation, and sampled elements
+    against the oracle run on the particles that can reach them."""
+    w = inputs.draw("mixed_16m", seed=5)
+    wl = w["workload"]
+    n = w["x"].shape[1]
+    ctx = pc.Context(n, wl.ne, wl.degree, wl.sigma, w["e"], pc.reach_of(w["r"], w["v"], w["dt"]))
+    s32 = mixed_state(w, ctx)
+    f = ctx.new_field_f32()
+    ctx.project_f32(s32, f, "f16")
+    ctx.sync()
+    nc = ctx.cells_per_side
+    cell = s32.cell.cpu().numpy()
+    o = s32.o.cpu().numpy()
+    q = s32.q.cpu().numpy().astype(np.float64)
+    x = oracle.dequantize(cell, o, nc)
+    eta, om = np.polynomial.legendre.leggauss(wl.degree + 1)
+    W = (np.einsum("k,j,i->kji", om, om, om) * (0.5 / wl.ne) ** 3).ravel()
+    tot = (f.double().sum(dim=0) * torch.as_tensor(W, device="cuda")).sum(dim=1).cpu().numpy()
+    assert np.all(np.abs(tot - q.sum(axis=1)) <= 1e-5 * np.abs(q).sum(axis=1))
+    rng = np.random.default_rng(1)
+    elems = rng.choice(wl.ne ** 3, 4, replace=False)
+    e_of = np.minimum((x * wl.ne).astype(np.int64), wl.ne - 1)
+    keep = np.zeros(n, bool)
+    for el in elems:
+        c = [el % wl.ne, (el // wl.ne) % wl.ne, el // wl.ne ** 2]
+        near = np.ones(n, bool)
+        for a in range(3):
+            d = (e_of[a] - c[a] + wl.ne // 2) % wl.ne - wl.ne // 2
+            near &= np.abs(d) <= 1
+        keep |= near
+    R, _ = oracle.project(x[:, keep], q[:, keep], wl.ne, wl.degree, wl.sigma, wl.cutoff_sigmas)
+    F = f[torch.as_tensor(elems, device="cuda")].cpu().numpy().astype(np.float64)
+    scale = f.abs().amax(dim=(0, 2)).cpu().numpy()
+    err = np.abs(F - R[elems]).max(axis=(0, 2)) / scale
+    print("sampled normwise error", err)
+    assert np.all(err <= F16_TOL), err

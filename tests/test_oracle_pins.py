@@ -492,3 +492,57 @@ def test_curved_map_special_points():
     assert np.allclose(X, [0.25, 0.25, 0.02], atol=1e-17)
     X, dj = oracle.mesh_map(np.array([0.3, 0.0, 0.0]), 0.02)
     assert np.allclose(X, [0.3, 0.0, 0.0], atol=1e-17)
+
+
+# ----------------------------------------------------------------- mixed storage
+
+def test_cellrel_step_matches_fp64_on_dequantized_state():
+    """The cell-relative step equals the FP64 step on the dequantized state up to the
+    storage rounding: same pairs, positions within 1e-7 cells, velocities within FP32 rounding."""
+    w = inputs.draw("dense_1m", n=3000, seed=21)
+    nc = 25
+    cell, o = oracle.quantize(w["x"], nc)
+    vf, rf, mf = w["v"].astype(np.float32), w["r"].astype(np.float32), w["m"].astype(np.float32)
+    dt = 40 * w["dt"]
+    c1, o1, v1, p1, tc1, k1 = oracle.collide_step_cellrel(cell, o, vf, rf, mf, w["id"], nc, 0.9, dt)
+    xd = oracle.dequantize(cell, o, nc)
+    x2, v2, p2, tc2, k2 = oracle.collide_step(xd, vf.astype(np.float64), rf.astype(np.float64),
+                                              mf.astype(np.float64), w["id"], 0.9, dt)
+    assert k1 == k2 > 5 and np.array_equal(p1, p2)
+    assert np.allclose(tc1, tc2, rtol=1e-12, atol=0)
+    d = oracle.dequantize(c1, o1, nc) - x2
+    d -= np.round(d)
+    assert np.max(np.abs(d)) * nc < 1e-6
+    assert np.allclose(v1, v2, rtol=1e-6, atol=1e-6)
+
+
+def test_cellrel_free_flight_carry():
+    """Free flight across the upper and lower cell faces and the periodic boundary."""
+    nc = 10
+    cell = np.array([9, 0 + 10 * 5, 5 + 10 * 3], np.int32)  # x-cells 9, 0, 5 (different y-cells)
+    o = np.zeros((3, 3), np.float32)
+    o[0] = [0.99, 0.01, 0.5]
+    o[1] = 0.5
+    o[2] = 0.5
+    v = np.zeros((3, 3), np.float32)
+    v[0] = [1.0, -1.0, 0.0]
+    r = np.full(3, 1e-4, np.float32)
+    m = np.ones(3, np.float32)
+    c1, o1, v1, p, tc, k = oracle.collide_step_cellrel(cell, o, v, r, m, np.arange(3, dtype=np.int32), nc, 1.0, 0.002)
+    assert k == 0
+    assert c1[0] % 10 == 0 and abs(o1[0, 0] - np.float32(np.float32(0.99) + np.float32(0.02) - 1)) < 1e-7
+    assert c1[1] == 9 + 10 * 5 and abs(o1[0, 1] - (np.float32(0.01) - np.float32(0.02) + 1)) < 1e-6
+    assert c1[2] == cell[2] and np.array_equal(o1[:, 2], o[:, 2])
+
+
+def test_cellrel_momentum_conserved_to_storage_rounding():
+    w = inputs.draw("dense_1m", n=2500, seed=22)
+    nc = 25
+    cell, o = oracle.quantize(w["x"], nc)
+    vf, rf, mf = w["v"].astype(np.float32), w["r"].astype(np.float32), w["m"].astype(np.float32)
+    c1, o1, v1, p, tc, k = oracle.collide_step_cellrel(cell, o, vf, rf, mf, w["id"], nc, 0.8, 40 * w["dt"])
+    assert k > 5
+    p0 = (mf.astype(np.float64) * vf).sum(axis=1)
+    p1 = (mf.astype(np.float64) * v1).sum(axis=1)
+    scale = (mf.astype(np.float64) * np.abs(vf)).sum(axis=1)
+    assert np.all(np.abs(p1 - p0) <= 1e-6 * scale)
