@@ -33,6 +33,8 @@ METRIC = "particle-steps/s collide+project (FP64)"
 UNIT = "particle-steps/s"
 # FP64 pipe of a GB300: 152 SMs x 2 FP64 FMA per clock x 2 flop x 2.07 GHz (max SM clock).
 FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12
+# FP32 pipe: 152 SMs x 128 lanes x 2.07 GHz, operations (an FMA counts once) per second.
+FP32_PIPE_TOPS = 152 * 128 * 2.07e9 / 1e12
 # dram bytes per launch of the dominant kernel from the committed ncu capture
 # (profiles/), or None when the kernel changed since that capture.
 DEPOSIT_DRAM_BYTES = None
@@ -47,6 +49,8 @@ def parse():
     ap.add_argument("--workload", default="dense_1m")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-mixed", action="store_true")
+    ap.add_argument("--mixed-steps", type=int, default=5)
     return ap.parse_args()
 
 
@@ -185,24 +189,35 @@ def run_ours(args, ws, rank, local):
     roofline = None
     if dom == "deposit" and dcnt:
         nodes = support_nodes(a.x.cpu().numpy(), wl)
-        flops = 8.0 * nodes  # 4 FMA (one per source component) per (particle, support node)
-        achieved = flops / (dms / dcnt / 1e3) / 1e12
-        roofline = {"kernel": "k_proj_gather", "bound": "alu", "achieved": achieved, "peak": FP64_PEAK_TFLOPS,
-                    "unit": "TFLOP/s", "frac": achieved / FP64_PEAK_TFLOPS,
+        # 4 source components per (particle, support node); each FP64-accurate multiply-add
+        # in double-float costs 12 FP32-pipe operations (4 for the exact product, 8 for the
+        # TwoSum accumulation)
+        ops = 4.0 * 12.0 * nodes
+        achieved = ops / (dms / dcnt / 1e3) / 1e12
+        roofline = {"kernel": "k_proj_deposit", "bound": "alu", "achieved": achieved, "peak": FP32_PIPE_TOPS,
+                    "unit": "Tops/s (FP32 pipe)", "frac": achieved / FP32_PIPE_TOPS,
                     "traffic": DEPOSIT_DRAM_BYTES,
-                    "peak_source": "FP64 pipe: 152 SMs x 2 FMA/clk x 2 flop x 2.07 GHz (derived, recipe unit counts)",
-                    "algorithmic": "8 flop per (particle, Gauss node in its box support): %.4g flop per launch" % flops}
+                    "peak_source": "FP32 pipe: 152 SMs x 128 lanes x 2.07 GHz, one operation per lane per clock "
+                                   "(derived from the recipe's unit counts)",
+                    "algorithmic": "48 FP32 operations per (particle, Gauss node in its box support): %.4g per launch"
+                                   % ops,
+                    "fp64_equivalent_tflops": 8.0 * nodes / (dms / dcnt / 1e3) / 1e12,
+                    "fp64_pipe_peak_tflops": FP64_PEAK_TFLOPS}
     phase_ms = {k: round(v[0] / max(v[1], 1), 4) for k, v in phases.items()}
 
     e2e = None
     if not args.no_e2e:
         e2e = e2e_run(args, ctx, w, n, dt, stream, torch, pc, dist, ws)
 
+    ctx.close()
+    del a, b, field
+    mixed = None
+    if not args.no_mixed:
+        mixed = mixed_run(args, rank, torch, pc, stream)
     cpu = None
     if rank == 0 and not args.no_cpu_baseline:
         cpu = cpu_baseline(w, wl)
     clocks = clk.summary()
-    ctx.close()
     if dist:
         dist.destroy_process_group()
     if rank != 0:
@@ -216,10 +231,125 @@ def run_ours(args, ws, rank, local):
                    "phi": round(w["phi"], 4), "l2": "inputs larger than L2 (state 105 MB + field 226 MB + scratch)",
                    "parallelism": "independent replica per GPU" if ws > 1 else "1 GPU"},
         "phase_ms_per_call": phase_ms, "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
-        "gpu_launches": launches, "clocks": clocks,
+        "gpu_launches": launches, "clocks": clocks, "mixed": mixed,
         "collide_stats": {k: st[k] for k in ("pairs", "candidates", "worklist", "rounds", "fp64_solves",
                                               "max_candidates", "cells_per_side", "stencil")},
     }
+
+
+def mixed_run(args, rank, torch, pc, stream, workload="mixed_16m"):
+    """The mixed-precision path on its own workload (16,777,216 spheres, 64^3 mesh of
+    degree 7): pc_collide_f32 + pc_project_f32 (FP16 split, tensor cores) per step,
+    and the FP64 path timed on the same workload for comparison."""
+    wl = inputs.WORKLOADS[workload]
+    w = inputs.draw(workload, seed=rank)
+    n, dt = w["x"].shape[1], w["dt"]
+    peaks = {}
+    try:
+        peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except (OSError, ValueError):
+        pass
+    out = {"workload": workload, "particles": n, "dt": dt, "unit": UNIT, "tc": "f16"}
+    with torch.cuda.stream(stream):
+        s64 = pc.State.from_arrays(w)
+        ctx = pc.Context(n, wl.ne, wl.degree, wl.sigma, w["e"], pc.reach_of(w["r"], w["v"], dt),
+                         cutoff_sigmas=wl.cutoff_sigmas, stream=stream)
+        a = pc.StateF32.empty(n)
+        b = pc.StateF32.empty(n)
+        ctx.quantize(s64, a)
+        f32 = ctx.new_field_f32()
+    torch.cuda.synchronize()
+    for _ in range(2):
+        ctx.collide_f32(a, b, dt)
+        ctx.project_f32(b, f32)
+        a, b = b, a
+    ctx.sync()
+    ctx.set_timing(True)
+    ctx.timing()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    for _ in range(args.mixed_steps):
+        ctx.collide_f32(a, b, dt)
+        ctx.project_f32(b, f32)
+        a, b = b, a
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    ms = ev0.elapsed_time(ev1) / args.mixed_steps
+    ph = ctx.timing()
+    ctx.set_timing(False)
+    st = ctx.stats()
+    if st["status"] != 0:
+        raise RuntimeError("device status %d in the mixed run" % st["status"])
+    out["ms_per_step"] = ms
+    out["value"] = n / (ms / 1e3)
+    out["phase_ms_per_call"] = {k: round(v[0] / max(v[1], 1), 4) for k, v in ph.items()}
+    dep_ms = ph["deposit"][0] / max(ph["deposit"][1], 1)
+    # tensor work issued: one M=128 N=64 K=16 MMA per 16 kept particles per element
+    pairs = element_pairs(b.numpy(), ctx.cells_per_side, wl)
+    flops = 2.0 * 128 * 64 * 16 * pairs["chunks"]
+    peak = peaks.get("bf16_tflops", 1900.0)
+    out["roofline"] = {"kernel": "k_tc_deposit", "bound": "tensor", "achieved": flops / (dep_ms / 1e3) / 1e12,
+                       "peak": peak, "unit": "TFLOP/s", "frac": flops / (dep_ms / 1e3) / 1e12 / peak,
+                       "peak_source": "MEASURED_PEAKS.json bf16_tflops (fp16 has the same dense rate)",
+                       "algorithmic": "2*128*64*16 flop per MMA, %d MMAs (16 kept particles each) per launch"
+                                      % pairs["chunks"]}
+    out["kept_particle_element_pairs"] = pairs["pairs"]
+    ctx.close()
+    del a, b, f32
+    # FP64 path on the same workload (one step after one warm-up)
+    with torch.cuda.stream(stream):
+        c64 = pc.Context(n, wl.ne, wl.degree, wl.sigma, w["e"], pc.reach_of(w["r"], w["v"], dt),
+                         cutoff_sigmas=wl.cutoff_sigmas, stream=stream)
+        t64 = pc.State.empty(n)
+        f64 = c64.new_field()
+    for rep in range(2):
+        if rep == 1:
+            ev0.record(stream)
+        c64.collide(s64, t64, dt)
+        c64.project(t64, f64)
+        if rep == 1:
+            ev1.record(stream)
+    torch.cuda.synchronize()
+    c64.sync()
+    out["fp64_ms_per_step_same_workload"] = ev0.elapsed_time(ev1)
+    out["speedup_vs_fp64"] = out["fp64_ms_per_step_same_workload"] / ms
+    c64.close()
+    return out
+
+
+def element_pairs(s32, nc, wl):
+    """Kept (particle, element) pairs of the mixed deposit and its MMA count, from the
+    particles' support boxes (every element gets ceil(kept / 16) MMAs)."""
+    cell = s32["cell"].astype(np.int64)
+    c = np.stack([cell % nc, (cell // nc) % nc, cell // (nc * nc)]).astype(np.float64)
+    x = (c + s32["o"].astype(np.float64)) / nc
+    eta, _ = np.polynomial.legendre.leggauss(wl.degree + 1)
+    rc = wl.cutoff_sigmas * wl.sigma
+    ne = wl.ne
+    h = 1.0 / ne
+    lo = np.floor((x - rc) * ne - 1e-9).astype(np.int64)
+    counts = np.zeros(ne ** 3, np.int64)
+    first = (eta[0] + 1) / 2 * h
+    last = (eta[-1] + 1) / 2 * h
+    n = x.shape[1]
+    per_axis = []
+    for a in range(3):
+        es = []
+        for o in range(3):
+            e = lo[a] + o
+            # element e holds a node within rc of x iff its node span [e h + first, e h + last] meets [x - rc, x + rc]
+            ok = (e * h + first <= x[a] + rc) & (e * h + last >= x[a] - rc)
+            es.append((np.mod(e, ne), ok))
+        per_axis.append(es)
+    pairs = 0
+    for ox in range(3):
+        for oy in range(3):
+            for oz in range(3):
+                ok = per_axis[0][ox][1] & per_axis[1][oy][1] & per_axis[2][oz][1]
+                el = (per_axis[2][oz][0] * ne + per_axis[1][oy][0]) * ne + per_axis[0][ox][0]
+                counts += np.bincount(el[ok], minlength=ne ** 3)
+                pairs += int(ok.sum())
+    return {"pairs": pairs, "chunks": int(np.ceil(counts / 16.0).sum())}
 
 
 def e2e_run(args, ctx, w, n, dt, stream, torch, pc, dist, ws):
