@@ -51,6 +51,12 @@ def _load():
         lib.or_collide_step.restype = i64
         lib.or_collide_step_cellrel.argtypes = [i64, i32, P, P, P, P, P, P, d, d, P, P]
         lib.or_collide_step_cellrel.restype = i64
+        lib.or_collide_replay.argtypes = [i64, P, P, P, P, P, d, d]
+        lib.or_collide_replay.restype = i32
+        lib.or_collide_adjoint.argtypes = [i64, P, P, P, P, P, d, d, P, P, P, P]
+        lib.or_collide_adjoint.restype = i32
+        lib.or_project_adjoint.argtypes = [i64, P, P, i32, i32, d, d, i32, P, P, P]
+        lib.or_project_adjoint.restype = i32
         lib.or_mesh_map.argtypes = [P, d, P, P]
         lib.or_mesh_map.restype = None
         lib.or_project.argtypes = [i64, P, P, i32, i32, d, d, i32, d, P, P]
@@ -176,6 +182,42 @@ def collide_step_cellrel(cell, o, v, r, m, ids, nc, e, dt):
     if k < 0:
         raise MemoryError("oracle collide_step_cellrel")
     return cell, o, v, partner, tc, k
+
+
+def collide_replay(x, v, r, m, partner, e, dt):
+    """One step with a fixed matching; returns (x', v'). Raises if a pair lost its root."""
+    x, v = _f64(x).copy(), _f64(v).copy()
+    r, m = _f64(r), _f64(m)
+    partner = np.ascontiguousarray(partner, np.int64)
+    rc = _load().or_collide_replay(r.shape[0], _p(x), _p(v), _p(r), _p(m), _p(partner), float(e), float(dt))
+    if rc != 0:
+        raise ValueError("replay: a recorded pair has no contact in [0, dt]")
+    return x, v
+
+
+def collide_adjoint(x, v, r, m, partner, e, dt, gx_out, gv_out):
+    """Cotangents of the pre-step (x, v) of one replayed step."""
+    x, v, r, m = _f64(x), _f64(v), _f64(r), _f64(m)
+    partner = np.ascontiguousarray(partner, np.int64)
+    gxo, gvo = _f64(gx_out), _f64(gv_out)
+    gx, gv = np.zeros_like(x), np.zeros_like(v)
+    rc = _load().or_collide_adjoint(r.shape[0], _p(x), _p(v), _p(r), _p(m), _p(partner), float(e), float(dt),
+                                    _p(gxo), _p(gvo), _p(gx), _p(gv))
+    if rc != 0:
+        raise ValueError("adjoint: a recorded pair has no contact in [0, dt]")
+    return gx, gv
+
+
+def project_adjoint(x, q, G, ne, degree, sigma, cutoff_sigmas=3.0, cutoff="box"):
+    """(dL/dq [4][n], dL/dx [3][n]) for dL/dfield = G."""
+    x, q, G = _f64(x), _f64(q), _f64(G)
+    n = x.shape[-1]
+    gq, gx = np.zeros((4, n)), np.zeros((3, n))
+    rc = _load().or_project_adjoint(n, _p(x), _p(q), ne, degree, float(sigma), float(cutoff_sigmas),
+                                    0 if cutoff == "box" else 1, _p(G), _p(gq), _p(gx))
+    if rc:
+        raise ValueError("or_project_adjoint failed")
+    return gq, gx
 
 
 def mesh_map(xi, amp):

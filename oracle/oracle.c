@@ -665,3 +665,188 @@ int64_t or_collide_step_cellrel(int64_t n, int32_t nc, int32_t* cell, float* o, 
   free(vn);
   return pairs;
 }
+
+/* ------------------------------------------------------------------ adjoint */
+
+int or_collide_replay(int64_t n, double* x, double* v, const double* r, const double* m, const int64_t* partner,
+                      double e, double dt) {
+  double* tc = (double*)malloc(sizeof(double) * (size_t)(n > 0 ? n : 1));
+  if (!tc) return -2;
+  int bad = 0;
+  for (int64_t i = 0; i < n; ++i) {
+    tc[i] = INFINITY;
+    int64_t j = partner[i];
+    if (j < 0) continue;
+    double xi[3], xj[3], vi[3], vj[3];
+    load3(x, n, i, xi);
+    load3(x, n, j, xj);
+    load3(v, n, i, vi);
+    load3(v, n, j, vj);
+    double t = or_contact_time(xi, xj, vi, vj, r[i], r[j], dt);
+    if (!(t <= dt)) bad = 1;
+    tc[i] = t;
+  }
+  if (!bad) or_respond_advance(n, x, v, m, partner, tc, e, dt);
+  free(tc);
+  return bad ? -1 : 0;
+}
+
+static double dot3(const double a[3], const double b[3]) { return (a[0] * b[0] + a[1] * b[1]) + a[2] * b[2]; }
+
+int or_collide_adjoint(int64_t n, const double* x, const double* v, const double* r, const double* m,
+                       const int64_t* partner, double e, double dt, const double* gx_out, const double* gv_out,
+                       double* gx_in, double* gv_in) {
+  /* free flight: x' = x + dt v, v' = v */
+  for (int64_t i = 0; i < n; ++i)
+    for (int k = 0; k < 3; ++k) {
+      gx_in[k * n + i] = gx_out[k * n + i];
+      gv_in[k * n + i] = gv_out[k * n + i] + dt * gx_out[k * n + i];
+    }
+  for (int64_t i = 0; i < n; ++i) {
+    int64_t j = partner[i];
+    if (j < 0 || j < i) continue; /* each pair once, from its lower index */
+    double xi[3], xj[3], vi[3], vj[3];
+    load3(x, n, i, xi);
+    load3(x, n, j, xj);
+    load3(v, n, i, vi);
+    load3(v, n, j, vj);
+    double t = or_contact_time(xi, xj, vi, vj, r[i], r[j], dt);
+    if (!(t <= dt)) return -1;
+    /* forward intermediates */
+    double dx[3], dv[3], s[3], nrm[3], vin[3], vjn[3];
+    for (int k = 0; k < 3; ++k) {
+      dx[k] = minimg(xi[k] - xj[k]);
+      dv[k] = vi[k] - vj[k];
+      s[k] = dx[k] + t * dv[k];
+    }
+    double sl = sqrt(dot3(s, s));
+    for (int k = 0; k < 3; ++k) nrm[k] = -s[k] / sl;
+    double vrn = dot3(dv, nrm);
+    double mr = (m[i] * m[j]) / (m[i] + m[j]);
+    double J = -mr * (1.0 + e) * vrn;
+    for (int k = 0; k < 3; ++k) {
+      vin[k] = vi[k] + (J / m[i]) * nrm[k];
+      vjn[k] = vj[k] - (J / m[j]) * nrm[k];
+    }
+    double Xi[3], Xj[3], Vi[3], Vj[3];
+    for (int k = 0; k < 3; ++k) {
+      Xi[k] = gx_out[k * n + i];
+      Xj[k] = gx_out[k * n + j];
+      Vi[k] = gv_out[k * n + i];
+      Vj[k] = gv_out[k * n + j];
+    }
+    /* reverse sweep; the free-flight initialisation above is replaced for i and j */
+    double gxi[3], gxj[3], gvi[3], gvj[3], gdx[3] = {0, 0, 0}, gdv[3] = {0, 0, 0}, gn[3] = {0, 0, 0};
+    double gt = 0.0, gJ = 0.0;
+    double Vit[3], Vjt[3];
+    for (int k = 0; k < 3; ++k) {
+      /* x_i' = x_i + t v_i + (dt - t) v_i' */
+      gxi[k] = Xi[k];
+      gvi[k] = t * Xi[k];
+      Vit[k] = Vi[k] + (dt - t) * Xi[k];
+      gt += Xi[k] * (vi[k] - vin[k]);
+      gxj[k] = Xj[k];
+      gvj[k] = t * Xj[k];
+      Vjt[k] = Vj[k] + (dt - t) * Xj[k];
+      gt += Xj[k] * (vj[k] - vjn[k]);
+    }
+    /* v_i' = v_i + (J/m_i) n, v_j' = v_j - (J/m_j) n */
+    for (int k = 0; k < 3; ++k) {
+      gvi[k] += Vit[k];
+      gvj[k] += Vjt[k];
+      gn[k] += (J / m[i]) * Vit[k] - (J / m[j]) * Vjt[k];
+    }
+    gJ = dot3(Vit, nrm) / m[i] - dot3(Vjt, nrm) / m[j];
+    /* J = -m_r (1 + e) v_rn, v_rn = dv . n */
+    double gvrn = -mr * (1.0 + e) * gJ;
+    for (int k = 0; k < 3; ++k) {
+      gdv[k] += gvrn * nrm[k];
+      gn[k] += gvrn * dv[k];
+    }
+    /* n = -s/|s|: gs = -(gn - nh (nh . gn))/|s| with nh = s/|s| */
+    double nh[3] = {s[0] / sl, s[1] / sl, s[2] / sl};
+    double pg = dot3(nh, gn);
+    double gs[3];
+    for (int k = 0; k < 3; ++k) gs[k] = -(gn[k] - nh[k] * pg) / sl;
+    /* s = dx + t dv */
+    for (int k = 0; k < 3; ++k) {
+      gdx[k] += gs[k];
+      gdv[k] += t * gs[k];
+    }
+    gt += dot3(gs, dv);
+    /* t from |dx + t dv| = R: dt/d(dx) = -s/(s.dv), dt/d(dv) = -t s/(s.dv) */
+    double sdv = dot3(s, dv);
+    for (int k = 0; k < 3; ++k) {
+      gdx[k] += gt * (-s[k] / sdv);
+      gdv[k] += gt * (-t * s[k] / sdv);
+    }
+    for (int k = 0; k < 3; ++k) {
+      gx_in[k * n + i] = gxi[k] + gdx[k];
+      gx_in[k * n + j] = gxj[k] - gdx[k];
+      gv_in[k * n + i] = gvi[k] + gdv[k];
+      gv_in[k * n + j] = gvj[k] - gdv[k];
+    }
+  }
+  return 0;
+}
+
+int or_project_adjoint(int64_t n, const double* x, const double* q, int ne, int degree, double sigma,
+                       double cutoff_sigmas, int cutoff_kind, const double* G, double* gq, double* gx) {
+  if (n < 0 || ne < 1 || degree < 0 || degree > 15 || !(sigma > 0.0)) return 1;
+  int n1 = degree + 1;
+  double eta[16], w[16];
+  if (or_gauss_legendre(n1, eta, w)) return 1;
+  int64_t nodes = (int64_t)n1 * n1 * n1;
+  double h = 1.0 / ne, hh = 0.5 * h, rc = cutoff_sigmas * sigma, s2 = sigma * sigma;
+  int* lx = (int*)malloc(sizeof(int) * (size_t)(ne * n1));
+  int* ly = (int*)malloc(sizeof(int) * (size_t)(ne * n1));
+  int* lz = (int*)malloc(sizeof(int) * (size_t)(ne * n1));
+  if (!lx || !ly || !lz) { free(lx); free(ly); free(lz); return 2; }
+  for (int64_t p = 0; p < n; ++p) {
+    double xp[3] = {x[p], x[n + p], x[2 * n + p]};
+    int nx = near_nodes(xp[0], rc, ne, n1, eta, lx);
+    int ny = near_nodes(xp[1], rc, ne, n1, eta, ly);
+    int nz = near_nodes(xp[2], rc, ne, n1, eta, lz);
+    /* Z = sum W K, Z1 = sum W K d, S0 = sum a K, S1 = sum a K d, with a = sum_c G_c q_c */
+    double Z = 0, Z1[3] = {0, 0, 0}, S0 = 0, S1[3] = {0, 0, 0}, GK[4] = {0, 0, 0, 0};
+    for (int pass = 0; pass < 2; ++pass)
+      for (int c3 = 0; c3 < nz; ++c3)
+        for (int b3 = 0; b3 < ny; ++b3)
+          for (int a3 = 0; a3 < nx; ++a3) {
+            int gx_ = lx[a3], gy = ly[b3], gz = lz[c3];
+            int ex = gx_ / n1, i = gx_ % n1, ey = gy / n1, j = gy % n1, ez = gz / n1, k = gz % n1;
+            double X[3] = {(ex + 0.5 * (eta[i] + 1.0)) * h, (ey + 0.5 * (eta[j] + 1.0)) * h,
+                           (ez + 0.5 * (eta[k] + 1.0)) * h};
+            double d[3] = {minimg(X[0] - xp[0]), minimg(X[1] - xp[1]), minimg(X[2] - xp[2])};
+            double d2s = (d[0] * d[0] + d[1] * d[1]) + d[2] * d[2];
+            if (cutoff_kind == 0) {
+              if (!(fabs(d[0]) <= rc && fabs(d[1]) <= rc && fabs(d[2]) <= rc)) continue;
+            } else if (!(d2s <= rc * rc)) {
+              continue;
+            }
+            double K = exp(-d2s / (2.0 * s2));
+            if (pass == 0) {
+              double W = w[i] * w[j] * w[k] * hh * hh * hh;
+              Z += W * K;
+              for (int a = 0; a < 3; ++a) Z1[a] += W * K * d[a];
+            } else {
+              int64_t e = ((int64_t)ez * ne + ey) * ne + ex;
+              int64_t base = e * 4 * nodes + ((int64_t)k * n1 + j) * n1 + i;
+              double a = 0;
+              for (int c = 0; c < 4; ++c) {
+                double g = G[base + (int64_t)c * nodes];
+                a += g * q[(int64_t)c * n + p];
+                GK[c] += g * K;
+              }
+              S0 += a * K;
+              for (int aa = 0; aa < 3; ++aa) S1[aa] += a * K * d[aa];
+            }
+          }
+    for (int c = 0; c < 4; ++c) gq[(int64_t)c * n + p] = Z > 0 ? GK[c] / Z : 0.0;
+    for (int a = 0; a < 3; ++a) gx[(int64_t)a * n + p] = Z > 0 ? (S1[a] / Z - S0 * Z1[a] / (Z * Z)) / s2 : 0.0;
+  }
+  free(lx);
+  free(ly);
+  free(lz);
+  return 0;
+}

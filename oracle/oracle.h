@@ -86,6 +86,28 @@ int64_t or_collide_step_cellrel(int64_t n, int32_t nc, int32_t* cell, float* o, 
                                 const float* m, const int32_t* id, double e, double dt, int64_t* partner,
                                 double* tc);
 
+/* ---- adjoint (not in the paper; gradients of the operator with the pair set held fixed) ----
+ * Replay: one step with a given matching (partner[i] = index or -1), contact times
+ * recomputed by or_contact_time's formula; returns -1 if a given pair has no root
+ * in [0, dt] any more. x, v updated in place as or_respond_advance. */
+int or_collide_replay(int64_t n, double* x, double* v, const double* r, const double* m, const int64_t* partner,
+                      double e, double dt);
+
+/* Vector-Jacobian product of one replayed step: given the cotangents gx_out, gv_out
+ * of the new state, returns gx_in, gv_in of the pre-step state (x, v). The
+ * contact time enters through the implicit function theorem on |dx + t dv| = R;
+ * the periodic wrap has derivative 1. Returns -1 on a pair without a root. */
+int or_collide_adjoint(int64_t n, const double* x, const double* v, const double* r, const double* m,
+                       const int64_t* partner, double e, double dt, const double* gx_out, const double* gv_out,
+                       double* gx_in, double* gv_in);
+
+/* Vector-Jacobian product of or_project (affine mesh): given G = dL/dfield,
+ * gq[c][p] = sum_g G[g][c] K_pg / Z_p and gx[a][p] = dL/dx_p (the kernel's
+ * Gaussian derivative K (X - x)/sigma^2 inside the cutoff, Z_p differentiated
+ * too; the cutoff itself is held fixed). */
+int or_project_adjoint(int64_t n, const double* x, const double* q, int ne, int degree, double sigma,
+                       double cutoff_sigmas, int cutoff_kind, const double* G, double* gq, double* gx);
+
 /* Physical position of a logical point xi in [0,1)^3 under the periodic mesh
  * mapping x = xi + amp*(sin 2pi xi_y sin 2pi xi_z, sin 2pi xi_z sin 2pi xi_x,
  * sin 2pi xi_x sin 2pi xi_y) (amp = 0 is the affine Cartesian mesh), and the
