@@ -38,6 +38,7 @@ typedef enum {
   PC_ENOCONVERGE = 4,  /* the matching rounds reached their cap (cannot happen for valid input) */
   PC_ECAPACITY = 5,    /* a capacity was exceeded (candidate partners per particle, fixed scratch) */
   PC_ETIMEOUT = 6,     /* a bounded wait inside a kernel expired (the kernel stopped cleanly) */
+  PC_EREPLAY = 7,      /* a given pair has no contact within the step any more (replay / adjoint) */
 } pc_status;
 
 typedef struct pc_ctx pc_ctx;
@@ -137,6 +138,37 @@ pc_status pc_collide(pc_ctx* ctx, const pc_particles* in, pc_particles* out, dou
  * p->q must be non-NULL. field: device [ne^3][4][(N+1)^3] doubles, overwritten.
  * Accuracy: within 1e-12 of the exact sum, normwise per component. */
 pc_status pc_project(pc_ctx* ctx, const pc_particles* p, double* field);
+
+/* ---- differentiation (no counterpart in the paper) ----
+ * The gradient of a rollout is taken with each step's pair set held fixed. The
+ * calls below work on particle arrays in one fixed order (for example by id), not
+ * on the cell-sorted order that pc_collide writes. */
+
+/* Scatter the pairs of the last pc_collide into partner[id] (device, n_ids
+ * entries): the partner's id, or -1. Ids must lie in [0, n_ids). */
+pc_status pc_pairs_to_partner(pc_ctx* ctx, int32_t* partner, int64_t n_ids);
+
+/* One step with a given pair set (partner[p] = index of p's partner in the same
+ * arrays, or -1): contact times from the formula of pc_collide, the same response
+ * and advance, no search and no reordering; `out` in the order of `in` (r, m, id,
+ * q copied when out's pointers differ from in's). Bit-identical to pc_collide for
+ * the pair set pc_collide chose. A pair without a root in [0, dt] is recorded as
+ * PC_EREPLAY (reported by pc_sync). */
+pc_status pc_collide_replay(pc_ctx* ctx, const pc_particles* in, pc_particles* out, const int32_t* partner,
+                            double dt);
+
+/* Vector-Jacobian product of pc_collide_replay at the pre-step state `in`: given
+ * device cotangents gx_out, gv_out [3][n] of the new positions and velocities,
+ * writes gx_in, gv_in [3][n] of the old ones. The contact time is differentiated
+ * through |dx + t dv| = r_i + r_j (implicit function theorem), the wrap has
+ * derivative 1. */
+pc_status pc_collide_adjoint(pc_ctx* ctx, const pc_particles* in, const int32_t* partner, double dt,
+                             const double* gx_out, const double* gv_out, double* gx_in, double* gv_in);
+
+/* Vector-Jacobian product of pc_project: given G = dL/dfield (device, field
+ * layout), writes gq[4][n] = dL/dq and gx[3][n] = dL/dx (the Gaussian and the
+ * normalisation Z_p differentiated, the cutoff held fixed), in the order of p. FP64. */
+pc_status pc_project_adjoint(pc_ctx* ctx, const pc_particles* p, const double* G, double* gq, double* gx);
 
 /* ---- mixed-precision path ---- */
 

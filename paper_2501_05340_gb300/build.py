@@ -26,6 +26,7 @@ UNITS = {
     "noalloc.cu": [],
     "mixed.cu": ["-fmad=false"],
     "tc_deposit.cu": [],
+    "adjoint.cu": ["-fmad=false"],
 }
 
 

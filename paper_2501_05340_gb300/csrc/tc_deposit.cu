@@ -159,7 +159,6 @@ __global__ void __launch_bounds__(kThreads) k_tc_deposit(TcDepositArgs A) {
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int n1 = A.n1, ne = A.ne, rho = A.rho, span = 2 * rho + 1, nrange = span * span * span;
   const int nodes = n1 * n1 * n1;
-  const int64_t n = A.n;
   const int64_t nel = (int64_t)ne * ne * ne;
 
   for (int i = tid; i < kStages * 4096 / 16; i += kThreads) reinterpret_cast<uint4*>(&S.a[0][0])[i] = make_uint4(0, 0, 0, 0);

@@ -16,9 +16,9 @@ from . import build as _build
 
 c_i64, c_i32, c_d, c_p = ctypes.c_int64, ctypes.c_int32, ctypes.c_double, ctypes.c_void_p
 
-PC_OK, PC_EINVAL, PC_ENOMEM, PC_ECUDA, PC_ENOCONVERGE, PC_ECAPACITY, PC_ETIMEOUT = range(7)
+PC_OK, PC_EINVAL, PC_ENOMEM, PC_ECUDA, PC_ENOCONVERGE, PC_ECAPACITY, PC_ETIMEOUT, PC_EREPLAY = range(8)
 STATUS_NAMES = {0: "PC_OK", 1: "PC_EINVAL", 2: "PC_ENOMEM", 3: "PC_ECUDA", 4: "PC_ENOCONVERGE", 5: "PC_ECAPACITY",
-                6: "PC_ETIMEOUT"}
+                6: "PC_ETIMEOUT", 7: "PC_EREPLAY"}
 PC_TC_F16, PC_TC_BF16 = 0, 1
 
 
@@ -68,6 +68,12 @@ def library():
         lib.pc_sync.argtypes = [c_p]
         lib.pc_set_timing.argtypes = [c_p, ctypes.c_int]
         lib.pc_get_timing.argtypes = [c_p, c_p, c_p]
+        lib.pc_pairs_to_partner.argtypes = [c_p, c_p, c_i64]
+        lib.pc_collide_replay.argtypes = [c_p, ctypes.POINTER(PcParticles), ctypes.POINTER(PcParticles), c_p, c_d]
+        lib.pc_collide_adjoint.argtypes = [c_p, ctypes.POINTER(PcParticles), c_p, c_d, c_p, c_p, c_p, c_p]
+        lib.pc_project_adjoint.argtypes = [c_p, ctypes.POINTER(PcParticles), c_p, c_p, c_p]
+        for f in ("pc_pairs_to_partner", "pc_collide_replay", "pc_collide_adjoint", "pc_project_adjoint"):
+            getattr(lib, f).restype = ctypes.c_int
         lib.pc_cells_per_side.argtypes = [c_p]
         lib.pc_cells_per_side.restype = ctypes.c_int32
         lib.pc_quantize.argtypes = [c_p, ctypes.POINTER(PcParticles), ctypes.POINTER(PcParticlesF32)]
@@ -224,6 +230,27 @@ class Context:
             raise ValueError("field must be contiguous float64 of shape (%d, 4, %d)" % (nel, self.n1 ** 3))
         s = state.struct()
         self._check(library().pc_project(self._h, ctypes.byref(s), _ptr(field)))
+
+    def partner_by_id(self, n_ids, out=None):
+        """Device int32 [n_ids]: the partner id of each id in the last collide, or -1."""
+        if out is None:
+            out = torch.empty(n_ids, dtype=torch.int32, device="cuda")
+        self._check(library().pc_pairs_to_partner(self._h, _ptr(out), int(n_ids)))
+        return out
+
+    def collide_replay(self, src, dst, partner, dt):
+        """One step with a fixed pair set (partner: int32 [n], index in the same order)."""
+        a, b = src.struct(), dst.struct()
+        self._check(library().pc_collide_replay(self._h, ctypes.byref(a), ctypes.byref(b), _ptr(partner), float(dt)))
+
+    def collide_adjoint(self, pre, partner, dt, gx_out, gv_out, gx_in, gv_in):
+        a = pre.struct()
+        self._check(library().pc_collide_adjoint(self._h, ctypes.byref(a), _ptr(partner), float(dt), _ptr(gx_out),
+                                                 _ptr(gv_out), _ptr(gx_in), _ptr(gv_in)))
+
+    def project_adjoint(self, state, G, gq, gx):
+        a = state.struct()
+        self._check(library().pc_project_adjoint(self._h, ctypes.byref(a), _ptr(G), _ptr(gq), _ptr(gx)))
 
     @property
     def cells_per_side(self):
