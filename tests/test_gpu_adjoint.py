@@ -178,12 +178,15 @@ def test_rollout_gradient_matches_finite_differences():
         # central differences carry an O(h^2) truncation error that is large when a
         # perturbed particle is in a nearly grazing pair (t ~ sqrt of the discriminant):
         # such a direction is as unusable as one that crosses a cutoff, and is redrawn
-        if abs(fd - fd2) > 1e-6 * abs(fd):
+        if abs(fd - fd2) > 1e-5 * abs(fd):
             curved += 1
             replaced += 1
             continue
-        print("direction %d: FD(h) %.12e FD(h/2) %.12e adjoint %.12e" % (accepted, fd, fd2, ad))
-        assert abs(fd - ad) <= 1e-6 * abs(ad), (fd, fd2, ad)
+        # in the asymptotic regime the O(h^2) term cancels in (4 FD(h/2) - FD(h)) / 3
+        rich = (4 * fd2 - fd) / 3
+        print("direction %d: FD(h) %.12e Richardson %.12e adjoint %.12e" % (accepted, fd, rich, ad))
+        assert abs(fd - ad) <= 2e-5 * abs(ad), (fd, fd2, ad)
+        assert abs(rich - ad) <= 1e-7 * abs(ad), (fd, fd2, rich, ad)
         accepted += 1
     print("directions replaced: %d (%d strongly curved)" % (replaced, curved))
     assert accepted == 8, "directions replaced: %d" % replaced
