@@ -56,6 +56,8 @@ typedef struct {
                            Larger actual reaches stay exact (more cells are searched). (> 0) */
   int32_t cand_cap;     /* candidate partners kept per particle and step (1..32; 0 = 16) */
   void* stream;         /* cudaStream_t for all work (NULL = legacy default stream) */
+  double amp;           /* curved-mesh amplitude a of x = xi + a (sin 2pi xi_y sin 2pi xi_z, cyclic);
+                           0 = affine. Used by pc_project_curved_f32 (needs cutoff_kind 1), 0 <= a < 0.04 */
 } pc_config;
 
 /* Device SoA particle state (FP64). */
@@ -201,6 +203,18 @@ pc_status pc_collide_f32(pc_ctx* ctx, const pc_particles_f32* in, pc_particles_f
  * [ne^3][4][(N+1)^3], overwritten. Requires N + 1 <= 8 and (2 rho + 1)(N + 1) <= 32,
  * rho = ceil(cutoff_sigmas sigma ne). */
 pc_status pc_project_f32(pc_ctx* ctx, const pc_particles_f32* p, float* field, int32_t tc_type);
+
+/* Projection on the curved periodic mesh x = Phi(xi) = xi + amp (sin 2pi xi_y sin 2pi xi_z,
+ * sin 2pi xi_z sin 2pi xi_x, sin 2pi xi_x sin 2pi xi_y) with the non-separable
+ * physical-space Gaussian and a spherical cutoff (cfg.cutoff_kind = 1):
+ * field[g][c] = sum_p q[c][p] K(X_g - x_p) / Z_p, X_g = Phi(xi_g) at the Gauss nodes,
+ * Z_p = sum_g W_g K(X_g - x_p), W_g = w_i w_j w_k (h/2)^3 det DPhi(xi_g). Particles are
+ * located in logical space by Newton's method on Phi(xi) = x (Sec. 3.2,
+ * localisation). FP32 factors and accumulation; distances from double-float
+ * positions; cutoff decisions within 1e-4 relative of the cutoff made in FP64.
+ * field: device FP32 [ne^3][4][(N+1)^3], overwritten. Deterministic (gather per
+ * element). Requires cfg.amp > 0 or = 0, 2 pi sqrt(3) amp < 0.5. */
+pc_status pc_project_curved_f32(pc_ctx* ctx, const pc_particles_f32* p, float* field);
 
 /* Copy the pairs of the last pc_collide to HOST memory: ids[2k], ids[2k+1] (smaller
  * id first) and t[k], sorted by the smaller id. Writes min(cap, count) pairs and

@@ -27,6 +27,7 @@ UNITS = {
     "mixed.cu": ["-fmad=false"],
     "tc_deposit.cu": [],
     "adjoint.cu": ["-fmad=false"],
+    "curved.cu": ["-fmad=false"],
 }
 
 

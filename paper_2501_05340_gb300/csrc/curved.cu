@@ -1,0 +1,447 @@
+// Projection on the curved periodic mesh (arXiv 2501.05340 deposition, Sec. 2.3 /
+// 4.2, with a non-separable Gaussian shape function in physical space):
+//   x = Phi(xi) = xi + amp (sin 2pi xi_y sin 2pi xi_z, sin 2pi xi_z sin 2pi xi_x, sin 2pi xi_x sin 2pi xi_y),
+//   field[g][c] = sum_p q[c][p] K(X_g - x_p) / Z_p, Z_p = sum_g W_g K(X_g - x_p),
+//   W_g = w_i w_j w_k (h/2)^3 det DPhi(xi_g), K(d) = exp(-|d|^2/(2 sigma^2)) for |d| <= rc.
+// Steps: Newton's method on Phi(xi) = x locates every particle in logical space
+// (the localisation of Sec. 3.2) and bins it by logical element; per particle Z_p
+// over the logical box that bounds the physical ball of radius rc (|Phi(a) - Phi(b)|
+// >= (1 - L)|a - b| with L = 2 pi sqrt(3) amp); per element a gather over the
+// particles of the 2 rho + 1 logical neighbours, culled by the element's bounding
+// box. FP32 factors and accumulation; positions as double-float so that node to
+// particle distances keep their precision; cutoff decisions within 2e-4 relative
+// of the cutoff are made in FP64 with the plain definition. Compiled with -fmad=false.
+#include <math.h>
+#include <string.h>
+
+#include "df32.cuh"
+#include "pc_internal.cuh"
+
+namespace {
+
+__device__ __forceinline__ int wrapi(int a, int n) {
+  a %= n;
+  return a < 0 ? a + n : a;
+}
+
+__device__ __forceinline__ float minimgf(float d) {
+  if (d > 0.5f) return d - 1.0f;
+  if (d < -0.5f) return d + 1.0f;
+  return d;
+}
+
+__device__ __forceinline__ double minimg(double d) {
+  if (d > 0.5) return d - 1.0;
+  if (d < -0.5) return d + 1.0;
+  return d;
+}
+
+__device__ __forceinline__ void raise_status(unsigned long long* counters, int code) {
+  atomicMax(&counters[CNT_STATUS], (unsigned long long)code);
+}
+
+// Position (c + o)/nc of a cell-relative coordinate as double-float.
+__device__ __forceinline__ f2 pos_df(int c, float o, f2 inv_nc) { return df_mul(two_sum((float)c, o), inv_nc); }
+
+struct LocArgs {
+  int64_t n;
+  int nc, ne;
+  float amp;
+  f2 inv_nc;
+  const int32_t* cell;
+  const float* o;
+  float* xi;  // [3][n], input order
+  int32_t *key, *slot, *cnt;
+  unsigned long long* counters;
+};
+
+// Newton's method on Phi(xi) = x (residual taken in the periodic minimum image),
+// 8 iterations from xi = x; the map's perturbation has Lipschitz constant < 0.5,
+// so the iteration contracts quadratically.
+__global__ void k_curved_locate(LocArgs A) {
+  const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const int64_t n = A.n;
+  if (p >= n) return;
+  const int32_t cl = A.cell[p];
+  const int nc = A.nc;
+  if (!(cl >= 0 && (int64_t)cl < (int64_t)nc * nc * nc)) raise_status(A.counters, PC_EINVAL);
+  const int32_t cs = cl < 0 ? 0 : cl;
+  const int c3[3] = {cs % nc, (cs / nc) % nc, cs / (nc * nc)};
+  float x[3], xi[3];
+  for (int a = 0; a < 3; ++a) {
+    const float oa = A.o[a * n + p];
+    if (!(oa >= 0.0f && oa < 1.0f)) raise_status(A.counters, PC_EINVAL);
+    const f2 xd = pos_df(c3[a], oa, A.inv_nc);
+    x[a] = xd.h;
+    xi[a] = xd.h;
+  }
+  const float g = 6.283185307179586f * A.amp;
+  for (int it = 0; it < 8; ++it) {
+    float s[3], c[3];
+    for (int a = 0; a < 3; ++a) sincospif(2.0f * xi[a], &s[a], &c[a]);
+    const float F0 = minimgf(xi[0] + A.amp * s[1] * s[2] - x[0]);
+    const float F1 = minimgf(xi[1] + A.amp * s[2] * s[0] - x[1]);
+    const float F2 = minimgf(xi[2] + A.amp * s[0] * s[1] - x[2]);
+    // J = I + g [[0, c1 s2, s1 c2], [c0 s2, 0, s0 c2], [c0 s1, s0 c1, 0]]
+    const float a01 = g * c[1] * s[2], a02 = g * s[1] * c[2];
+    const float a10 = g * c[0] * s[2], a12 = g * s[0] * c[2];
+    const float a20 = g * c[0] * s[1], a21 = g * s[0] * c[1];
+    const float det = 1.0f * (1.0f - a12 * a21) - a01 * (a10 - a12 * a20) + a02 * (a10 * a21 - a20);
+    const float d0 = (F0 * (1.0f - a12 * a21) - a01 * (F1 - a12 * F2) + a02 * (F1 * a21 - F2)) / det;
+    const float d1 = ((F1 - a12 * F2) - F0 * (a10 - a12 * a20) + a02 * (a10 * F2 - a20 * F1)) / det;
+    const float d2 = ((F2 - a21 * F1) - a01 * (a10 * F2 - a20 * F1) + F0 * (a10 * a21 - a20)) / det;
+    xi[0] -= d0;
+    xi[1] -= d1;
+    xi[2] -= d2;
+  }
+  int e[3];
+  for (int a = 0; a < 3; ++a) {
+    float w = xi[a] - floorf(xi[a]);
+    if (w >= 1.0f) w = 0.0f;
+    xi[a] = w;
+    int ea = (int)(w * (float)A.ne);
+    e[a] = ea < 0 ? 0 : (ea >= A.ne ? A.ne - 1 : ea);
+    A.xi[a * n + p] = w;
+  }
+  const int k = (e[2] * A.ne + e[1]) * A.ne + e[0];
+  A.key[p] = k;
+  A.slot[p] = atomicAdd(&A.cnt[k], 1);
+}
+
+struct CPrepArgs {
+  int64_t n;
+  int nc, ne, n1, rho;
+  float amp, rcl, rc2f, c2l, hf;
+  f2 inv_nc, h;
+  double hd, rc;
+  float s[16], wq[16];
+  double eta[16];
+  const int32_t* perm;
+  const int32_t* cell;
+  const float* o;
+  const float* xi;
+  const float* q;
+  float4* rec;  // [n][3]: (x0h x0l x1h x1l) (x2h x2l 1/Z q0) (q1 q2 q3 -)
+};
+
+// Inside-cutoff decision for a node: float distance squared r2 against rc^2, and the
+// plain FP64 definition within 2e-4 relative of the edge (x_p = (c + o)/nc).
+__device__ __forceinline__ bool inside_cut(float r2, float rc2f, const int c3[3], const float o3[3], int nc,
+                                           const double xig[3], float amp, double rc) {
+  if (r2 < rc2f * 0.9998f) return true;
+  if (r2 > rc2f * 1.0002f) return false;
+  const double tp = 6.283185307179586476925286766559;
+  double s[3];
+  for (int a = 0; a < 3; ++a) s[a] = sin(tp * xig[a]);
+  const double X[3] = {xig[0] + (double)amp * s[1] * s[2], xig[1] + (double)amp * s[2] * s[0],
+                       xig[2] + (double)amp * s[0] * s[1]};
+  double d[3];
+  for (int a = 0; a < 3; ++a) d[a] = minimg(X[a] - ((double)c3[a] + (double)o3[a]) / (double)nc);
+  const double d2s = (d[0] * d[0] + d[1] * d[1]) + d[2] * d[2];
+  return d2s <= rc * rc;
+}
+
+__global__ void __launch_bounds__(128) k_curved_prep(CPrepArgs A) {
+  const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const int64_t n = A.n;
+  if (k >= n) return;
+  const int64_t p = A.perm[k];
+  const int nc = A.nc, ne = A.ne, n1 = A.n1;
+  const int32_t cl = A.cell[p] < 0 ? 0 : A.cell[p];
+  const int c3[3] = {cl % nc, (cl / nc) % nc, cl / (nc * nc)};
+  float o3[3], xip[3];
+  f2 x[3];
+  int ea[3];
+  for (int a = 0; a < 3; ++a) {
+    o3[a] = A.o[a * n + p];
+    x[a] = pos_df(c3[a], o3[a], A.inv_nc);
+    xip[a] = A.xi[a * n + p];
+    int e = (int)(xip[a] * (float)ne);
+    ea[a] = e < 0 ? 0 : (e >= ne ? ne - 1 : e);
+  }
+  // 1-D logical candidates per axis: the window's nodes within rcl of xi_p
+  const int win = (2 * A.rho + 1) * n1;
+  int nl[3] = {0, 0, 0};
+  int lw[3][64];
+  for (int a = 0; a < 3; ++a)
+    for (int w = 0; w < win; ++w) {
+      const int o = w / n1 - A.rho, i = w % n1;
+      const float xg = ((float)(ea[a] + o) + A.s[i]) * A.hf;
+      if (fabsf(xg - xip[a]) <= A.rcl) lw[a][nl[a]++] = w;
+    }
+  const float g = 6.283185307179586f * A.amp;
+  float Z = 0.0f;
+  for (int kz = 0; kz < nl[2]; ++kz)
+    for (int ky = 0; ky < nl[1]; ++ky)
+      for (int kx = 0; kx < nl[0]; ++kx) {
+        const int w3[3] = {lw[0][kx], lw[1][ky], lw[2][kz]};
+        float sn[3], cs[3];
+        double xig[3];
+        float dist[3];
+        for (int a = 0; a < 3; ++a) {
+          const int o = w3[a] / n1 - A.rho, i = w3[a] % n1;
+          const f2 xg = df_mul(two_sum((float)(ea[a] + o), A.s[i]), A.h);  // logical node coordinate
+          sincospif(2.0f * xg.h, &sn[a], &cs[a]);
+          xig[a] = ((double)wrapi(ea[a] + o, ne) + 0.5 * (A.eta[i] + 1.0)) * A.hd;
+          const f2 dd = df_add(xg, df_neg(x[a]));
+          dist[a] = dd.h + dd.l;
+        }
+        const float dx = minimgf(dist[0] + A.amp * sn[1] * sn[2]);
+        const float dy = minimgf(dist[1] + A.amp * sn[2] * sn[0]);
+        const float dz = minimgf(dist[2] + A.amp * sn[0] * sn[1]);
+        const float r2 = dx * dx + dy * dy + dz * dz;
+        if (!inside_cut(r2, A.rc2f, c3, o3, nc, xig, A.amp, A.rc)) continue;
+        const float a01 = g * cs[1] * sn[2], a02 = g * sn[1] * cs[2];
+        const float a10 = g * cs[0] * sn[2], a12 = g * sn[0] * cs[2];
+        const float a20 = g * cs[0] * sn[1], a21 = g * sn[0] * cs[1];
+        const float det = 1.0f * (1.0f - a12 * a21) - a01 * (a10 - a12 * a20) + a02 * (a10 * a21 - a20);
+        const float W = A.wq[w3[0] % n1] * A.wq[w3[1] % n1] * A.wq[w3[2] % n1] * det;
+        Z += W * exp2f(-r2 * A.c2l);
+      }
+  const float hh = 0.5f * A.hf;
+  Z *= hh * hh * hh;
+  const float iz = Z > 0.0f ? 1.0f / Z : 0.0f;
+  float4* rp = A.rec + 3 * k;
+  rp[0] = make_float4(x[0].h, x[0].l, x[1].h, x[1].l);
+  rp[1] = make_float4(x[2].h, x[2].l, iz, A.q[p]);
+  rp[2] = make_float4(A.q[n + p], A.q[2 * n + p], A.q[3 * n + p], 0.0f);
+}
+
+struct CDepArgs {
+  int64_t n;
+  int nc, ne, n1, rho;
+  float amp, rc2f, rcf, c2l;
+  f2 h;
+  double hd, rc;
+  float s[16];
+  double eta[16];
+  const int32_t* start;
+  const int32_t* perm;  // for the FP64 edge decisions (stored cell + offset)
+  const int32_t* cell;
+  const float* o;
+  const float4* rec;
+  float* field;
+};
+
+// One CTA per element, one thread per node. Particles of the neighbouring logical
+// elements are staged in batches (one per thread) with a bounding-box test; every
+// node then adds q_c K / Z of the staged particles that pass.
+__global__ void k_curved_deposit(CDepArgs A) {
+  extern __shared__ float4 sm4[];
+  const int nodes = blockDim.x;  // n1^3
+  float4* st = sm4;                                      // [nodes][3]
+  int* keep = (int*)(sm4 + 3 * nodes);                   // [nodes]
+  __shared__ float bbox[6];
+  __shared__ int pre[126], rbeg[126];
+  const int t = threadIdx.x;
+  const int n1 = A.n1, ne = A.ne, rho = A.rho, span = 2 * rho + 1, nrange = span * span * span;
+  const int e = blockIdx.x;
+  const int ex = e % ne, ey = (e / ne) % ne, ez = e / (ne * ne);
+  const int i = t % n1, j = (t / n1) % n1, k = t / (n1 * n1);
+  const int el[3] = {ex, ey, ez}, li[3] = {i, j, k};
+  f2 X[3];
+  float sn[3];
+  double xig[3];
+  for (int a = 0; a < 3; ++a) {
+    const f2 xg = df_mul(two_sum((float)el[a], A.s[li[a]]), A.h);
+    float cs;
+    sincospif(2.0f * xg.h, &sn[a], &cs);
+    X[a] = xg;
+    xig[a] = ((double)el[a] + 0.5 * (A.eta[li[a]] + 1.0)) * A.hd;
+  }
+  const float pert[3] = {A.amp * sn[1] * sn[2], A.amp * sn[2] * sn[0], A.amp * sn[0] * sn[1]};
+  // bounding box of the element's physical nodes
+  __shared__ float coords[3][1024];
+  for (int a = 0; a < 3; ++a) coords[a][t] = X[a].h + pert[a];
+  __syncthreads();
+  if (t == 0) {
+    for (int a = 0; a < 3; ++a) {
+      float lo = 1e30f, hi = -1e30f;
+      for (int g = 0; g < nodes; ++g) {
+        lo = fminf(lo, coords[a][g]);
+        hi = fmaxf(hi, coords[a][g]);
+      }
+      bbox[a] = lo;
+      bbox[3 + a] = hi;
+    }
+    int s = 0;
+    for (int r = 0; r < nrange; ++r) {
+      const int dx = r % span - rho, dy = (r / span) % span - rho, dz = r / (span * span) - rho;
+      const int nb = (wrapi(ez + dz, ne) * ne + wrapi(ey + dy, ne)) * ne + wrapi(ex + dx, ne);
+      const int b0 = A.start[nb], b1 = A.start[nb + 1];
+      pre[r] = s;
+      rbeg[r] = b0;
+      s += b1 - b0;
+    }
+    pre[nrange] = s;
+  }
+  __syncthreads();
+  const float cen[3] = {0.5f * (bbox[0] + bbox[3]), 0.5f * (bbox[1] + bbox[4]), 0.5f * (bbox[2] + bbox[5])};
+  const float hw[3] = {0.5f * (bbox[3] - bbox[0]), 0.5f * (bbox[4] - bbox[1]), 0.5f * (bbox[5] - bbox[2])};
+  const float cut = A.rcf * 1.0002f + 1e-6f;
+  const int total = pre[nrange];
+  float acc[4] = {0.0f, 0.0f, 0.0f, 0.0f};
+  for (int base = 0; base < total; base += nodes) {
+    const int idx = base + t;
+    int kp = 0;
+    if (idx < total) {
+      int r = 0;
+      while (pre[r + 1] <= idx) ++r;
+      const int jj = rbeg[r] + (idx - pre[r]);
+      const float4 r0 = A.rec[3 * (int64_t)jj], r1 = A.rec[3 * (int64_t)jj + 1], r2 = A.rec[3 * (int64_t)jj + 2];
+      st[3 * t] = r0;
+      st[3 * t + 1] = r1;
+      st[3 * t + 2] = r2;
+      const float xp[3] = {r0.x, r0.z, r1.x};
+      float d2 = 0.0f;
+      for (int a = 0; a < 3; ++a) {
+        const float ex_ = fmaxf(fabsf(minimgf(xp[a] - cen[a])) - hw[a], 0.0f);
+        d2 += ex_ * ex_;
+      }
+      kp = d2 <= cut * cut ? jj + 1 : 0;
+    }
+    keep[t] = kp;
+    __syncthreads();
+    const int cntb = min(nodes, total - base);
+    for (int q = 0; q < cntb; ++q) {
+      const int kk = keep[q];
+      if (!kk) continue;
+      const float4 r0 = st[3 * q], r1 = st[3 * q + 1], r2 = st[3 * q + 2];
+      const f2 xp[3] = {{r0.x, r0.y}, {r0.z, r0.w}, {r1.x, r1.y}};
+      float d[3];
+      for (int a = 0; a < 3; ++a) {
+        const f2 dd = df_add(X[a], df_neg(xp[a]));
+        d[a] = minimgf((dd.h + dd.l) + pert[a]);
+      }
+      const float r2s = d[0] * d[0] + d[1] * d[1] + d[2] * d[2];
+      if (r2s > A.rc2f * 1.0002f) continue;
+      if (r2s >= A.rc2f * 0.9998f) {
+        const int64_t pj = A.perm[kk - 1];
+        const int32_t cl = A.cell[pj] < 0 ? 0 : A.cell[pj];
+        const int nc = A.nc;
+        const int c3[3] = {cl % nc, (cl / nc) % nc, cl / (nc * nc)};
+        const float o3[3] = {A.o[pj], A.o[A.n + pj], A.o[2 * A.n + pj]};
+        if (!inside_cut(r2s, A.rc2f, c3, o3, nc, xig, A.amp, A.rc)) continue;
+      }
+      const float K = exp2f(-r2s * A.c2l) * r1.z;
+      acc[0] += r1.w * K;
+      acc[1] += r2.x * K;
+      acc[2] += r2.y * K;
+      acc[3] += r2.z * K;
+    }
+    __syncthreads();
+  }
+  float* out = A.field + (int64_t)e * 4 * nodes;
+  for (int c = 0; c < 4; ++c) out[c * nodes + t] = acc[c];
+}
+
+}  // namespace
+
+pc_status pc_project_curved_f32_impl(pc_ctx* ctx, const pc_particles_f32* p, float* field) {
+  const int64_t n = p->n;
+  cudaStream_t st = ctx->stream;
+  const int ne = ctx->cfg.ne;
+  const int64_t nel = (int64_t)ne * ne * ne;
+  const double inv = 1.0 / (double)ctx->nc;
+  const f2 inv_nc = {(float)inv, (float)(inv - (double)(float)inv)};
+  const f2 hdf = {(float)ctx->h, (float)(ctx->h - (double)(float)ctx->h)};
+  const double rc = ctx->cfg.cutoff_sigmas * ctx->cfg.sigma;
+  cudaError_t e = cudaMemsetAsync(ctx->cnt, 0, sizeof(int32_t) * (size_t)nel, st);
+  if (e != cudaSuccess) goto fail;
+  {
+    const int tb = pc_phase_begin(ctx, PC_PH_PBIN);
+    if (n > 0) {
+      LocArgs L;
+      L.n = n;
+      L.nc = ctx->nc;
+      L.ne = ne;
+      L.amp = (float)ctx->cfg.amp;
+      L.inv_nc = inv_nc;
+      L.cell = p->cell;
+      L.o = p->o;
+      L.xi = ctx->sxf;
+      L.key = ctx->key;
+      L.slot = ctx->slot;
+      L.cnt = ctx->cnt;
+      L.counters = ctx->counters;
+      k_curved_locate<<<pc_blocks(n, 256), 256, 0, st>>>(L);
+      ctx->launches += 1;
+    }
+    e = pc_bin_finish(n, nel, ctx->key, ctx->slot, p->id, ctx->cnt, ctx->start, ctx->blocksums, ctx->perm, st,
+                      &ctx->launches);
+    pc_phase_end(ctx, tb);
+  }
+  if (e != cudaSuccess) goto fail;
+  if (n > 0) {
+    CPrepArgs P;
+    memset(&P, 0, sizeof(P));
+    P.n = n;
+    P.nc = ctx->nc;
+    P.ne = ne;
+    P.n1 = ctx->n1;
+    P.rho = ctx->rho;
+    P.amp = (float)ctx->cfg.amp;
+    const double lip = 6.283185307179586 * 1.7320508075688772 * ctx->cfg.amp;
+    P.rcl = (float)(rc / (1.0 - lip) * 1.001 + 1e-6);
+    P.rc2f = (float)(rc * rc);
+    P.c2l = (float)(1.4426950408889634 / (2.0 * ctx->cfg.sigma * ctx->cfg.sigma));
+    P.hf = (float)ctx->h;
+    P.inv_nc = inv_nc;
+    P.h = hdf;
+    P.hd = ctx->h;
+    P.rc = rc;
+    for (int i = 0; i < ctx->n1; ++i) {
+      const double si = 0.5 * (ctx->eta[i] + 1.0);
+      P.s[i] = (float)si;
+      P.wq[i] = (float)ctx->w[i];
+      P.eta[i] = ctx->eta[i];
+    }
+    P.perm = ctx->perm;
+    P.cell = p->cell;
+    P.o = p->o;
+    P.xi = ctx->sxf;
+    P.q = p->q;
+    P.rec = (float4*)ctx->fac;
+    const int tf = pc_phase_begin(ctx, PC_PH_FACTORS);
+    k_curved_prep<<<pc_blocks(n, 128), 128, 0, st>>>(P);
+    ctx->launches += 1;
+    pc_phase_end(ctx, tf);
+  }
+  {
+    CDepArgs D;
+    memset(&D, 0, sizeof(D));
+    D.n = n;
+    D.nc = ctx->nc;
+    D.ne = ne;
+    D.n1 = ctx->n1;
+    D.rho = ctx->rho;
+    D.amp = (float)ctx->cfg.amp;
+    D.rc2f = (float)(rc * rc);
+    D.rcf = (float)rc;
+    D.c2l = (float)(1.4426950408889634 / (2.0 * ctx->cfg.sigma * ctx->cfg.sigma));
+    D.h = hdf;
+    D.hd = ctx->h;
+    D.rc = rc;
+    for (int i = 0; i < ctx->n1; ++i) {
+      D.s[i] = (float)(0.5 * (ctx->eta[i] + 1.0));
+      D.eta[i] = ctx->eta[i];
+    }
+    D.start = ctx->start;
+    D.perm = ctx->perm;
+    D.cell = p->cell;
+    D.o = p->o;
+    D.rec = (const float4*)ctx->fac;
+    D.field = field;
+    const int nodes = ctx->n1 * ctx->n1 * ctx->n1;
+    const size_t smem = (size_t)nodes * (3 * sizeof(float4) + sizeof(int));
+    const int td = pc_phase_begin(ctx, PC_PH_DEPOSIT);
+    k_curved_deposit<<<(unsigned)nel, nodes, smem, st>>>(D);
+    ctx->launches += 1;
+    pc_phase_end(ctx, td);
+  }
+  e = cudaGetLastError();
+  if (e == cudaSuccess) return PC_OK;
+fail:
+  snprintf(ctx->err, sizeof(ctx->err), "pc_project_curved_f32: %s", cudaGetErrorString(e));
+  return PC_ECUDA;
+}

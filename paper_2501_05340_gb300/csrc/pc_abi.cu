@@ -109,10 +109,15 @@ pc_status pc_init(pc_ctx** out, const pc_config* cfg) {
   if (c.ne < 3 || c.ne > 1024 || c.degree < 0 || c.degree > 15) return PC_EINVAL;
   if (!(c.sigma > 0.0) || !(c.cutoff_sigmas > 0.0) || !(c.restitution >= 0.0 && c.restitution <= 1.0))
     return PC_EINVAL;
-  if (c.cutoff_kind != 0) return PC_EINVAL;  // the sphere cutoff is served by the curved-mesh path
+  if (c.cutoff_kind != 0 && c.cutoff_kind != 1) return PC_EINVAL;
   if (!(c.reach_hint > 0.0) || c.cand_cap < 0 || c.cand_cap > 32) return PC_EINVAL;
+  if (!(c.amp >= 0.0 && c.amp < 0.04)) return PC_EINVAL;
   const double rc = c.cutoff_sigmas * c.sigma;
-  const int rho = (int)ceil(rc * c.ne * (1.0 + 1e-12));
+  // the sphere cutoff serves the curved mesh: in logical space the physical ball of
+  // radius rc lies within rc / (1 - L) per axis, L = 2 pi sqrt(3) amp
+  const double lip = 6.283185307179586 * 1.7320508075688772 * c.amp;
+  const int rho = c.cutoff_kind == 0 ? (int)ceil(rc * c.ne * (1.0 + 1e-12))
+                                     : (int)ceil(rc / (1.0 - lip) * c.ne * (1.001) + 1e-9);
   if (rho < 1 || rho > 2 || 2 * rho + 1 > c.ne || !(rc < 0.5)) return PC_EINVAL;
   if ((2 * rho + 1) * (c.degree + 1) > 64) return PC_EINVAL;
 
@@ -201,6 +206,7 @@ pc_status pc_collide(pc_ctx* ctx, const pc_particles* in, pc_particles* out, dou
 
 pc_status pc_project(pc_ctx* ctx, const pc_particles* p, double* field) {
   if (!ctx) return PC_EINVAL;
+  if (ctx->cfg.cutoff_kind != 0) return fail(ctx, PC_EINVAL, "pc_project: needs the box cutoff (cutoff_kind 0)");
   if (!particles_ok(p, ctx->cfg.n_max) || !field || (p->n > 0 && !p->q))
     return fail(ctx, PC_EINVAL, "pc_project: bad arguments");
   return pc_project_impl(ctx, p, field);
@@ -239,7 +245,19 @@ pc_status pc_project_f32(pc_ctx* ctx, const pc_particles_f32* p, float* field, i
     return fail(ctx, PC_EINVAL, "pc_project_f32: bad arguments");
   if (ctx->n1 > 8 || ctx->win > 32)
     return fail(ctx, PC_EINVAL, "pc_project_f32: needs N + 1 <= 8 and (2 rho + 1)(N + 1) <= 32");
+  if (ctx->cfg.cutoff_kind != 0) return fail(ctx, PC_EINVAL, "pc_project_f32: needs the box cutoff");
   return pc_project_f32_impl(ctx, p, field, tc_type);
+}
+
+pc_status pc_project_curved_f32(pc_ctx* ctx, const pc_particles_f32* p, float* field) {
+  if (!ctx) return PC_EINVAL;
+  if (!particles_f32_ok(p, ctx->cfg.n_max) || !field || (p->n > 0 && !p->q))
+    return fail(ctx, PC_EINVAL, "pc_project_curved_f32: bad arguments");
+  if (ctx->cfg.cutoff_kind != 1)
+    return fail(ctx, PC_EINVAL, "pc_project_curved_f32: needs the sphere cutoff (cutoff_kind 1)");
+  if (ctx->n1 * ctx->n1 * ctx->n1 > 1024)
+    return fail(ctx, PC_EINVAL, "pc_project_curved_f32: needs (N + 1)^3 <= 1024");
+  return pc_project_curved_f32_impl(ctx, p, field);
 }
 
 pc_status pc_sync(pc_ctx* ctx) {

@@ -25,7 +25,7 @@ PC_TC_F16, PC_TC_BF16 = 0, 1
 class PcConfig(ctypes.Structure):
     _fields_ = [("n_max", c_i64), ("ne", c_i32), ("degree", c_i32), ("sigma", c_d), ("cutoff_sigmas", c_d),
                 ("cutoff_kind", c_i32), ("restitution", c_d), ("reach_hint", c_d), ("cand_cap", c_i32),
-                ("stream", c_p)]
+                ("stream", c_p), ("amp", c_d)]
 
 
 class PcParticles(ctypes.Structure):
@@ -68,6 +68,8 @@ def library():
         lib.pc_sync.argtypes = [c_p]
         lib.pc_set_timing.argtypes = [c_p, ctypes.c_int]
         lib.pc_get_timing.argtypes = [c_p, c_p, c_p]
+        lib.pc_project_curved_f32.argtypes = [c_p, ctypes.POINTER(PcParticlesF32), c_p]
+        lib.pc_project_curved_f32.restype = ctypes.c_int
         lib.pc_pairs_to_partner.argtypes = [c_p, c_p, c_i64]
         lib.pc_collide_replay.argtypes = [c_p, ctypes.POINTER(PcParticles), ctypes.POINTER(PcParticles), c_p, c_d]
         lib.pc_collide_adjoint.argtypes = [c_p, ctypes.POINTER(PcParticles), c_p, c_d, c_p, c_p, c_p, c_p]
@@ -199,13 +201,14 @@ class Context:
     """One operator instance (pc_init). All calls run on ``stream`` (default: torch's current)."""
 
     def __init__(self, n_max, ne, degree, sigma, restitution, reach_hint, cutoff_sigmas=3.0, cand_cap=16,
-                 stream=None):
+                 stream=None, cutoff="box", amp=0.0):
         lib = library()
         if stream is None:
             stream = torch.cuda.current_stream()
         self.stream = stream
-        self.cfg = PcConfig(int(n_max), int(ne), int(degree), float(sigma), float(cutoff_sigmas), 0,
-                            float(restitution), float(reach_hint), int(cand_cap), c_p(stream.cuda_stream))
+        self.cfg = PcConfig(int(n_max), int(ne), int(degree), float(sigma), float(cutoff_sigmas),
+                            0 if cutoff == "box" else 1, float(restitution), float(reach_hint), int(cand_cap),
+                            c_p(stream.cuda_stream), float(amp))
         h = c_p()
         st = lib.pc_init(ctypes.byref(h), ctypes.byref(self.cfg))
         if st != PC_OK:
@@ -274,6 +277,14 @@ class Context:
         t = PC_TC_BF16 if tc == "bf16" else PC_TC_F16
         self._check(library().pc_project_f32(self._h, ctypes.byref(s), _ptr(field), t))
 
+    def project_curved_f32(self, state, field):
+        """FP32 field <- projection on the curved mesh (context made with cutoff="sphere", amp > 0)."""
+        nel = self.ne ** 3
+        if tuple(field.shape) != (nel, 4, self.n1 ** 3) or field.dtype != torch.float32 or not field.is_contiguous():
+            raise ValueError("field must be contiguous float32 of shape (%d, 4, %d)" % (nel, self.n1 ** 3))
+        s = state.struct()
+        self._check(library().pc_project_curved_f32(self._h, ctypes.byref(s), _ptr(field)))
+
     def new_field_f32(self):
         return torch.empty(self.ne ** 3, 4, self.n1 ** 3, dtype=torch.float32, device="cuda")
 
@@ -332,7 +343,7 @@ def project_noalloc(state, field, ne, degree, sigma, cutoff_sigmas=3.0, stream=N
     if stream is None:
         stream = torch.cuda.current_stream()
     cfg = PcConfig(0, int(ne), int(degree), float(sigma), float(cutoff_sigmas), 0, 0.0, 0.0, 0,
-                   c_p(stream.cuda_stream))
+                   c_p(stream.cuda_stream), 0.0)
     s = state.struct()
     msg = ctypes.create_string_buffer(256)
     st = library().pc_project_noalloc(ctypes.byref(cfg), ctypes.byref(s), _ptr(field), msg, 256)
