@@ -25,29 +25,9 @@
 
 namespace {
 
-constexpr int kThreads = 128;
-constexpr int kStages = 4;
 constexpr int kChunk = 16;
-constexpr int kListMax = 2048;
-constexpr uint32_t kTmemCols = 64;
 constexpr long kSpinLimit = 1L << 26;
 
-struct __align__(1024) TcSmem {
-  uint8_t a[kStages][4096];
-  uint8_t b[kStages][2048];
-  float pf[kStages][kChunk][28];  // kx[8] ky[8] kz[8] q[4] per staged particle
-  float comb[64][33];
-  int list[kListMax];
-  int lmeta[kListMax];
-  int pre[128];
-  int rbeg[128];
-  int wcount[4];
-  unsigned long long mbar_stage[kStages];
-  unsigned long long mbar_done;
-  uint32_t tmem_base;
-  int nlist;
-  int failed;
-};
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
 
@@ -152,26 +132,364 @@ __device__ __forceinline__ int wrapi(int a, int n) {
   return a < 0 ? a + n : a;
 }
 
+constexpr int kProducers = 8;                           // producer warps, one TMEM accumulator each
+constexpr int kEpiWarps = 4;                            // one per TMEM lane quarter
+constexpr int kThreads2 = 32 * (kProducers + kEpiWarps + 1);
+constexpr int kRing = 2;                                // operand slots per producer
+constexpr int kList = 64;                               // kept-particle ring (>= kChunk + 32)
+constexpr int kQ = 16;                                  // finished-element queue (>= 2 kProducers)
+
+struct __align__(1024) TcSmem2 {
+  uint8_t a[kProducers][kRing][4096];
+  uint8_t b[kProducers][kRing][2048];
+  float pf[kProducers][kChunk][28];
+  int list[kProducers][kList];
+  int lmeta[kProducers][kList];
+  float comb[64][33];
+  int pre[kProducers][128];
+  int rbeg[kProducers][128];
+  int meta[kProducers][kRing][4];  // element, accumulate flag, last-chunk flag
+  unsigned long long full[kProducers][kRing];
+  unsigned long long empty[kProducers][kRing];
+  unsigned long long acc_full[kProducers];
+  unsigned long long acc_empty[kProducers];  // 2 arrivals: epilogue quarters 0 and 1
+  unsigned long long comb_full;              // 2 arrivals: epilogue quarters 2 and 3
+  unsigned long long comb_empty;             // 2 arrivals: epilogue quarters 0 and 1
+  unsigned long long fin;
+  int qe[kQ];
+  int qb[kQ];
+  int q_tail;
+  int prod_total[kProducers];
+  int failed;
+  uint32_t tmem_base;
+};
+
+__device__ __forceinline__ int vload(const int* p) { return *(const volatile int*)p; }
+__device__ __forceinline__ void vstore(int* p, int v) { *(volatile int*)p = v; }
+
+__device__ __forceinline__ bool mbar_try(unsigned long long* bar, uint32_t parity) {
+  uint32_t done;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+      "selp.u32 %0, 1, 0, p;\n\t}\n"
+      : "=r"(done)
+      : "r"(smem_u32(bar)), "r"(parity)
+      : "memory");
+  return done != 0;
+}
+
+__device__ __forceinline__ void mbar_arrive(unsigned long long* bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
+
+__device__ __forceinline__ void fail_now(TcSmem2& S, unsigned long long* counters) {
+  vstore(&S.failed, 1);
+  atomicMax(counters, (unsigned long long)PC_ETIMEOUT);
+}
+
+// Producer warp w: owns elements blockIdx.x * kProducers + w + k * gridDim.x * kProducers.
+// Per element: neighbour ranges, ordered warp-level compaction of the particles
+// whose support reaches the element, then per 16 kept particles: factors (lane
+// parallel), the operand rows (3 per lane) into its ring slot, and a release
+// arrival on the slot's full barrier for the MMA thread.
 template <int kBf16>
-__global__ void __launch_bounds__(kThreads) k_tc_deposit(TcDepositArgs A) {
-  extern __shared__ uint8_t smraw[];
-  TcSmem& S = *reinterpret_cast<TcSmem*>(smraw + ((1024 - (smem_u32(smraw) & 1023)) & 1023));
-  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+__device__ void tc_producer(TcSmem2& S, const TcDepositArgs& A, int w, int lane) {
   const int n1 = A.n1, ne = A.ne, rho = A.rho, span = 2 * rho + 1, nrange = span * span * span;
   const int nodes = n1 * n1 * n1;
   const int64_t nel = (int64_t)ne * ne * ne;
+  int chunk = 0;
+  for (int64_t e = (int64_t)blockIdx.x * kProducers + w; e < nel; e += (int64_t)gridDim.x * kProducers) {
+    if (vload(&S.failed)) break;
+    const int ex = (int)(e % ne), ey = (int)((e / ne) % ne), ez = (int)(e / ((int64_t)ne * ne));
+    for (int r = lane; r < nrange; r += 32) {
+      const int dx = r % span - rho, dy = (r / span) % span - rho, dz = r / (span * span) - rho;
+      const int nb = (wrapi(ez + dz, ne) * ne + wrapi(ey + dy, ne)) * ne + wrapi(ex + dx, ne);
+      const int b0 = A.start[nb], b1 = A.start[nb + 1];
+      S.rbeg[w][r] = b0;
+      S.pre[w][r + 1] = b1 - b0;
+    }
+    __syncwarp();
+    if (lane == 0) {
+      S.pre[w][0] = 0;
+      for (int r = 1; r <= nrange; ++r) S.pre[w][r] += S.pre[w][r - 1];
+    }
+    __syncwarp();
+    const int total = S.pre[w][nrange];
+    int nmma = 0;
+    int scan = 0;
+    int head = 0, tail = 0;  // kept-particle ring: [head, tail)
+    for (;;) {
+      // refill until the ring holds more than one chunk or the neighbourhood is exhausted,
+      // so that "last chunk of the element" is known exactly
+      while (scan < total && tail - head <= kChunk) {
+        const int idx = scan + lane;
+        bool keep = false;
+        int j = 0, meta = 0;
+        if (idx < total) {
+          int r = 0;
+          while (S.pre[w][r + 1] <= idx) ++r;
+          j = S.rbeg[w][r] + (idx - S.pre[w][r]);
+          const int d3[3] = {r % span - rho, (r / span) % span - rho, r / (span * span) - rho};
+          const float4 r2 = A.rec[4 * (int64_t)j + 2];
+          const float4 r3 = A.rec[4 * (int64_t)j + 3];
+          const unsigned mk[3] = {__float_as_uint(r2.z), __float_as_uint(r2.w), __float_as_uint(r3.x)};
+          keep = true;
+#pragma unroll
+          for (int a = 0; a < 3; ++a) {
+            const int wo = rho - d3[a];
+            keep = keep && ((mk[a] >> (wo * n1)) & ((1u << n1) - 1u)) != 0u;
+            meta |= wo << (4 * a);
+          }
+        }
+        const unsigned bal = __ballot_sync(0xffffffffu, keep);
+        if (keep) {
+          const int pos = (tail + __popc(bal & ((1u << lane) - 1u))) & (kList - 1);
+          S.list[w][pos] = j;
+          S.lmeta[w][pos] = meta;
+        }
+        tail += __popc(bal);
+        scan += 32;
+      }
+      __syncwarp();
+      const int avail = tail - head;
+      if (avail == 0) break;
+      const int take = avail < kChunk ? avail : kChunk;
+      const bool last = avail <= kChunk;  // the refill stopped short only because the scan is done
+      const int slot = chunk % kRing;
+      if (chunk >= kRing) {
+        const uint32_t par = (uint32_t)((chunk / kRing - 1) & 1);
+        long it = 0;
+        while (!mbar_try(&S.empty[w][slot], par)) {
+          if (++it > kSpinLimit || vload(&S.failed)) {
+            if (lane == 0) fail_now(S, A.counters + CNT_STATUS);
+            return;
+          }
+        }
+      }
+      // factors: lane -> particle p = lane & 15, values 12 h .. 12 h + 11 of (kx[8] ky[8] kz[8])
+      {
+        const int p = lane & 15, hlf = lane >> 4;
+        float* pf = S.pf[w][p];
+        if (p < take) {
+          const int64_t j = S.list[w][(head + p) & (kList - 1)];
+          const int meta = S.lmeta[w][(head + p) & (kList - 1)];
+          const float4 r0 = A.rec[4 * j], r1 = A.rec[4 * j + 1], r2 = A.rec[4 * j + 2], r3 = A.rec[4 * j + 3];
+          const float t3[3] = {r0.x, r0.y, r0.z}, iz[3] = {r0.w, r1.x, r1.y};
+          const unsigned mk[3] = {__float_as_uint(r2.z), __float_as_uint(r2.w), __float_as_uint(r3.x)};
+#pragma unroll
+          for (int u = 0; u < 12; ++u) {
+            const int v = 12 * hlf + u, a = v >> 3, i = v & 7;
+            float f = 0.0f;
+            if (i < n1) {
+              const int wo = (meta >> (4 * a)) & 15;
+              if ((mk[a] >> (wo * n1 + i)) & 1u) {
+                const float d = (float)(wo - rho) + A.s[i] - t3[a];
+                f = exp2f(-(d * d) * A.c2l) * iz[a];
+              }
+            }
+            pf[v] = f;
+          }
+          if (hlf == 0) {
+            pf[24] = r1.z;
+            pf[25] = r1.w;
+            pf[26] = r2.x;
+            pf[27] = r2.y;
+          }
+        } else {
+#pragma unroll
+          for (int u = 0; u < 12; ++u) pf[12 * hlf + u] = 0.0f;
+          if (hlf == 0) pf[24] = pf[25] = pf[26] = pf[27] = 0.0f;
+        }
+      }
+      __syncwarp();
+      // operand rows: 0..63 YZ (A operand, hi + lo), 64..95 q kx (B operand, hi + lo)
+#pragma unroll
+      for (int rr = 0; rr < 3; ++rr) {
+        const int row = lane + 32 * rr;
+        float v[16];
+        if (row < 64) {
+          if (row < n1 * n1) {
+            const int jj = row % n1, kk = row / n1;
+#pragma unroll
+            for (int p = 0; p < kChunk; ++p) v[p] = S.pf[w][p][8 + jj] * S.pf[w][p][16 + kk] * 256.0f;
+            store_row<kBf16>(S.a[w][slot], row, 64, v);
+          }
+        } else {
+          const int ci = row - 64;
+          if (ci < 4 * n1) {
+            const int c = ci / n1, i = ci % n1;
+#pragma unroll
+            for (int p = 0; p < kChunk; ++p) v[p] = S.pf[w][p][24 + c] * S.pf[w][p][i] * 16.0f;
+            store_row<kBf16>(S.b[w][slot], ci, 32, v);
+          }
+        }
+      }
+      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+      __syncwarp();
+      if (lane == 0) {
+        S.meta[w][slot][0] = (int)e;
+        S.meta[w][slot][1] = nmma > 0 ? 1 : 0;
+        S.meta[w][slot][2] = last ? 1 : 0;
+        mbar_arrive(&S.full[w][slot]);
+      }
+      head += take;
+      ++nmma;
+      ++chunk;
+      if (last) break;
+    }
+    if (nmma == 0) {
+      float* out = A.field + e * 4 * nodes;
+      for (int a = lane; a < 4 * nodes; a += 32) out[a] = 0.0f;
+    }
+  }
+  __syncwarp();
+  if (lane == 0) {
+    __threadfence_block();
+    vstore(&S.prod_total[w], chunk);
+  }
+}
 
-  for (int i = tid; i < kStages * 4096 / 16; i += kThreads) reinterpret_cast<uint4*>(&S.a[0][0])[i] = make_uint4(0, 0, 0, 0);
-  for (int i = tid; i < kStages * 2048 / 16; i += kThreads) reinterpret_cast<uint4*>(&S.b[0][0])[i] = make_uint4(0, 0, 0, 0);
+// The MMA thread: serves the producers' rings in turn; before the first chunk of a
+// producer's element it waits (without blocking the others) for the epilogue to
+// have emptied that producer's accumulator; after an element's last chunk it commits
+// the accumulator and queues (element, producer) for the epilogue.
+__device__ void tc_mma(TcSmem2& S, const TcDepositArgs& A, uint32_t tmem, uint32_t idesc) {
+  int used[kProducers], eng[kProducers];
+  for (int w = 0; w < kProducers; ++w) used[w] = eng[w] = 0;
+  int qt = 0;
+  long idle = 0;
+  for (;;) {
+    if (vload(&S.failed)) break;
+    bool all_done = true, progress = false;
+    for (int w = 0; w < kProducers; ++w) {
+      const int tot = vload(&S.prod_total[w]);
+      if (tot >= 0 && eng[w] >= tot) continue;
+      all_done = false;
+      const int c = eng[w], slot = c % kRing;
+      if (!mbar_try(&S.full[w][slot], (uint32_t)((c / kRing) & 1))) continue;
+      const int e = S.meta[w][slot][0], acc = S.meta[w][slot][1], last = S.meta[w][slot][2];
+      if (!acc) {
+        if (used[w] >= 1 && !mbar_try(&S.acc_empty[w], (uint32_t)((used[w] - 1) & 1))) continue;
+        ++used[w];
+      }
+      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+      mma_issue(tmem + 64u * w, make_desc(smem_u32(S.a[w][slot]), 128, 256), make_desc(smem_u32(S.b[w][slot]), 128, 256),
+                idesc, (uint32_t)acc);
+      mma_commit(&S.empty[w][slot]);
+      if (last) {
+        mma_commit(&S.acc_full[w]);
+        S.qe[qt % kQ] = e;
+        S.qb[qt % kQ] = w;
+        __threadfence_block();
+        vstore(&S.q_tail, ++qt);
+      }
+      ++eng[w];
+      progress = true;
+    }
+    if (all_done) break;
+    if (progress) {
+      idle = 0;
+    } else if (++idle > kSpinLimit) {
+      fail_now(S, A.counters + CNT_STATUS);
+      break;
+    }
+  }
+  // every MMA issued so far has completed once this commit arrives
+  mma_commit(&S.fin);
+  (void)mbar_wait(&S.fin, 0);
+  S.qe[qt % kQ] = -1;
+  S.qb[qt % kQ] = 0;
+  __threadfence_block();
+  vstore(&S.q_tail, ++qt);
+}
+
+// Epilogue warp for TMEM lane quarter q: drains the finished-element queue in order.
+__device__ void tc_epilogue(TcSmem2& S, const TcDepositArgs& A, uint32_t tmem, int q, int lane) {
+  const int n1 = A.n1, nodes = n1 * n1 * n1;
+  int seen[kProducers];
+  for (int w = 0; w < kProducers; ++w) seen[w] = 0;
+  for (int k = 0;; ++k) {
+    long it = 0;
+    while (vload(&S.q_tail) <= k) {
+      if (++it > kSpinLimit || vload(&S.failed)) {
+        if (lane == 0 && q == 0 && !vload(&S.failed)) fail_now(S, A.counters + CNT_STATUS);
+        return;
+      }
+    }
+    const int e = vload(&S.qe[k % kQ]), w = vload(&S.qb[k % kQ]);
+    if (e < 0) return;
+    if (!mbar_wait(&S.acc_full[w], (uint32_t)(seen[w] & 1))) {
+      if (lane == 0) fail_now(S, A.counters + CNT_STATUS);
+      return;
+    }
+    ++seen[w];
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    float r[64];
+    tmem_ld64(tmem + 64u * w + ((uint32_t)(32 * q) << 16), r);
+    const int jk = 32 * (q & 1) + lane;
+    if (q >= 2) {
+      // rows 64..127 (YZ lo): add the two column halves into comb for quarters 0 and 1
+      if (k >= 1 && !mbar_wait(&S.comb_empty, (uint32_t)((k - 1) & 1))) {
+        if (lane == 0) fail_now(S, A.counters + CNT_STATUS);
+        return;
+      }
+#pragma unroll
+      for (int ci = 0; ci < 32; ++ci) S.comb[jk][ci] = r[ci] + r[32 + ci];
+      asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+      __syncwarp();
+      if (lane == 0) mbar_arrive(&S.comb_full);
+    } else {
+      if (!mbar_wait(&S.comb_full, (uint32_t)(k & 1))) {
+        if (lane == 0) fail_now(S, A.counters + CNT_STATUS);
+        return;
+      }
+      if (jk < n1 * n1) {
+        float* out = A.field + (int64_t)e * 4 * nodes;
+        for (int ci = 0; ci < 4 * n1; ++ci) {
+          const int c = ci / n1, i = ci % n1;
+          out[c * nodes + jk * n1 + i] = ((r[ci] + r[32 + ci]) + S.comb[jk][ci]) * A.scale_out;
+        }
+      }
+      asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+      __syncwarp();
+      if (lane == 0) {
+        mbar_arrive(&S.comb_empty);
+        // quarters 2 and 3 finished their loads before comb_full; 0 and 1 arrive here
+        mbar_arrive(&S.acc_empty[w]);
+      }
+    }
+  }
+}
+
+template <int kBf16>
+__global__ void __launch_bounds__(kThreads2, 1) k_tc_deposit(TcDepositArgs A) {
+  extern __shared__ uint8_t smraw[];
+  TcSmem2& S = *reinterpret_cast<TcSmem2*>(smraw + ((1024 - (smem_u32(smraw) & 1023)) & 1023));
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  for (int i = tid; i < kProducers * kRing * 4096 / 16; i += kThreads2)
+    reinterpret_cast<uint4*>(&S.a[0][0][0])[i] = make_uint4(0, 0, 0, 0);
+  for (int i = tid; i < kProducers * kRing * 2048 / 16; i += kThreads2)
+    reinterpret_cast<uint4*>(&S.b[0][0][0])[i] = make_uint4(0, 0, 0, 0);
   if (tid == 0) {
-    for (int s = 0; s < kStages; ++s)
-      asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&S.mbar_stage[s])));
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&S.mbar_done)));
+    for (int w = 0; w < kProducers; ++w) {
+      for (int s = 0; s < kRing; ++s) {
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&S.full[w][s])));
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&S.empty[w][s])));
+      }
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&S.acc_full[w])));
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], 2;" ::"r"(smem_u32(&S.acc_empty[w])));
+      S.prod_total[w] = -1;
+    }
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&S.fin)));
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 2;" ::"r"(smem_u32(&S.comb_full)));
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 2;" ::"r"(smem_u32(&S.comb_empty)));
+    S.q_tail = 0;
     S.failed = 0;
   }
   if (warp == 0) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&S.tmem_base)),
-                 "r"(kTmemCols));
+                 "r"(64u * kProducers));
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
   }
   asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
@@ -180,212 +498,41 @@ __global__ void __launch_bounds__(kThreads) k_tc_deposit(TcDepositArgs A) {
   __syncthreads();
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
   const uint32_t tmem = S.tmem_base;
-  // kind::f16, D = F32, A/B = F16 (0) or BF16 (1), both K-major, N = 64, M = 128
   const uint32_t fmt = kBf16 ? 1u : 0u;
   const uint32_t idesc = (1u << 4) | (fmt << 7) | (fmt << 10) | (8u << 17) | (8u << 24);
-  long chunk_counter = 0;
-  uint32_t done_count = 0;
-
-  for (int64_t e = blockIdx.x; e < nel; e += gridDim.x) {
-    if (S.failed) break;
-    const int ex = (int)(e % ne), ey = (int)((e / ne) % ne), ez = (int)(e / ((int64_t)ne * ne));
-    if (tid == 0) {
-      int s = 0;
-      for (int r = 0; r < nrange; ++r) {
-        const int dx = r % span - rho, dy = (r / span) % span - rho, dz = r / (span * span) - rho;
-        const int nb = (wrapi(ez + dz, ne) * ne + wrapi(ey + dy, ne)) * ne + wrapi(ex + dx, ne);
-        const int b0 = A.start[nb], b1 = A.start[nb + 1];
-        S.pre[r] = s;
-        S.rbeg[r] = b0;
-        s += b1 - b0;
-      }
-      S.pre[nrange] = s;
-    }
-    __syncthreads();
-    const int total = S.pre[nrange];
-    int nmma = 0;
-    int scan = 0;
-    while (scan < total && !S.failed) {
-      // ---- ordered compaction of the particles whose support reaches this element
-      if (tid == 0) S.nlist = 0;
-      __syncthreads();
-      while (scan < total) {
-        const int idx = scan + tid;
-        bool keep = false;
-        int j = 0, meta = 0;
-        if (idx < total) {
-          int r = 0;
-          while (S.pre[r + 1] <= idx) ++r;
-          j = S.rbeg[r] + (idx - S.pre[r]);
-          const int d3[3] = {r % span - rho, (r / span) % span - rho, r / (span * span) - rho};
-          const float4 r2 = A.rec[4 * (int64_t)j + 2];
-          const float4 r3 = A.rec[4 * (int64_t)j + 3];
-          const unsigned mk[3] = {__float_as_uint(r2.z), __float_as_uint(r2.w), __float_as_uint(r3.x)};
-          keep = true;
-#pragma unroll
-          for (int a = 0; a < 3; ++a) {
-            const int wo = rho - d3[a];  // this element's slot in the particle's window
-            keep = keep && ((mk[a] >> (wo * n1)) & ((1u << n1) - 1u)) != 0u;
-            meta |= wo << (4 * a);
-          }
-        }
-        const unsigned bal = __ballot_sync(0xffffffffu, keep);
-        if (lane == 0) S.wcount[warp] = __popc(bal);
-        __syncthreads();
-        int base = S.nlist;
-        for (int w = 0; w < warp; ++w) base += S.wcount[w];
-        const int added = S.wcount[0] + S.wcount[1] + S.wcount[2] + S.wcount[3];
-        if (keep) {
-          const int pos = base + __popc(bal & ((1u << lane) - 1u));
-          S.list[pos] = j;
-          S.lmeta[pos] = meta;
-        }
-        __syncthreads();
-        if (tid == 0) S.nlist += added;
-        scan += kThreads;
-        __syncthreads();
-        if (S.nlist + kThreads > kListMax) break;
-      }
-      const int nl = S.nlist;
-      // ---- chunks of 16 kept particles: stage factors, build operands, one MMA
-      for (int c0 = 0; c0 < nl; c0 += kChunk) {
-        const int s = (int)(chunk_counter % kStages);
-        if (chunk_counter >= kStages) {
-          const uint32_t par = (uint32_t)((chunk_counter / kStages - 1) & 1);
-          if (!mbar_wait(&S.mbar_stage[s], par)) {
-            atomicMax(&A.counters[CNT_STATUS], (unsigned long long)PC_ETIMEOUT);
-            S.failed = 1;
-          }
-        }
-        __syncthreads();
-        if (S.failed) break;
-        {
-          const int p = tid >> 3, i = tid & 7;
-          float f3[3] = {0.0f, 0.0f, 0.0f}, qv = 0.0f;
-          if (c0 + p < nl && i < n1) {
-            const int64_t j = S.list[c0 + p];
-            const int meta = S.lmeta[c0 + p];
-            const float4 r0 = A.rec[4 * j], r1 = A.rec[4 * j + 1], r2 = A.rec[4 * j + 2], r3 = A.rec[4 * j + 3];
-            const float t3[3] = {r0.x, r0.y, r0.z}, iz[3] = {r0.w, r1.x, r1.y};
-            const unsigned mk[3] = {__float_as_uint(r2.z), __float_as_uint(r2.w), __float_as_uint(r3.x)};
-            const float q4[4] = {r1.z, r1.w, r2.x, r2.y};
-#pragma unroll
-            for (int a = 0; a < 3; ++a) {
-              const int wo = (meta >> (4 * a)) & 15;
-              const int w = wo * n1 + i;
-              if ((mk[a] >> w) & 1u) {
-                const float d = (float)(wo - rho) + A.s[i] - t3[a];
-                f3[a] = exp2f(-(d * d) * A.c2l) * iz[a];
-              }
-            }
-            if (i < 4) qv = q4[i];
-          }
-          float* pf = S.pf[s][p];
-          pf[i] = f3[0];
-          pf[8 + i] = f3[1];
-          pf[16 + i] = f3[2];
-          if (i < 4) pf[24 + i] = qv;
-        }
-        __syncthreads();
-        if (tid < 64) {
-          const int jk = tid;
-          if (jk < n1 * n1) {
-            const int jj = jk % n1, kk = jk / n1;
-            float v[16];
-#pragma unroll
-            for (int p = 0; p < kChunk; ++p) v[p] = S.pf[s][p][8 + jj] * S.pf[s][p][16 + kk] * 256.0f;
-            store_row<kBf16>(S.a[s], jk, 64, v);
-          }
-        } else if (tid < 96) {
-          const int ci = tid - 64;
-          if (ci < 4 * n1) {
-            const int c = ci / n1, i = ci % n1;
-            float v[16];
-#pragma unroll
-            for (int p = 0; p < kChunk; ++p) v[p] = S.pf[s][p][24 + c] * S.pf[s][p][i] * 16.0f;
-            store_row<kBf16>(S.b[s], ci, 32, v);
-          }
-        }
-        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-        __syncthreads();
-        if (tid == 0) {
-          asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-          mma_issue(tmem, make_desc(smem_u32(S.a[s]), 128, 256), make_desc(smem_u32(S.b[s]), 128, 256), idesc,
-                    nmma > 0 ? 1u : 0u);
-          mma_commit(&S.mbar_stage[s]);
-        }
-        ++nmma;
-        ++chunk_counter;
-      }
-    }
-    if (S.failed) break;
-    float* out = A.field + e * 4 * nodes;
-    if (nmma == 0) {
-      for (int a = tid; a < 4 * nodes; a += kThreads) out[a] = 0.0f;
-      __syncthreads();
-      continue;
-    }
-    // ---- epilogue: wait for the element's MMAs, add the four quadrants
-    if (tid == 0) mma_commit(&S.mbar_done);
-    if (!mbar_wait(&S.mbar_done, done_count & 1)) {
-      atomicMax(&A.counters[CNT_STATUS], (unsigned long long)PC_ETIMEOUT);
-      S.failed = 1;
-    }
-    ++done_count;
-    __syncthreads();
-    if (S.failed) break;
-    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-    float r[64];
-    tmem_ld64(tmem + ((uint32_t)(32 * warp) << 16), r);
-    const int jk = 32 * (warp & 1) + lane;
-    if (warp >= 2) {
-#pragma unroll
-      for (int ci = 0; ci < 32; ++ci) S.comb[jk][ci] = r[ci] + r[32 + ci];
-    }
-    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
-    __syncthreads();
-    if (warp < 2 && jk < n1 * n1) {
-      for (int ci = 0; ci < 4 * n1; ++ci) {
-        const int c = ci / n1, i = ci % n1;
-        out[c * nodes + jk * n1 + i] = ((r[ci] + r[32 + ci]) + S.comb[jk][ci]) * A.scale_out;
-      }
-    }
-    __syncthreads();
+  if (warp < kProducers) {
+    tc_producer<kBf16>(S, A, warp, lane);
+  } else if (warp < kProducers + kEpiWarps) {
+    tc_epilogue(S, A, tmem, warp - kProducers, lane);
+  } else if (lane == 0) {
+    tc_mma(S, A, tmem, idesc);
   }
-  // ---- teardown: no MMA may be in flight when the tensor memory is freed
-  if (S.failed) {
-    if (tid == 0) mma_commit(&S.mbar_done);
-    (void)mbar_wait(&S.mbar_done, done_count & 1);
-  }
+  __syncwarp();
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
   __syncthreads();
-  if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kTmemCols));
+  if (warp == 0)
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(64u * kProducers));
 }
 
 }  // namespace
 
 cudaError_t pc_tc_deposit_launch(const TcDepositArgs& A, cudaStream_t st, int* nblocks) {
-  const size_t smem = sizeof(TcSmem) + 1024;
+  const size_t smem = sizeof(TcSmem2) + 1024;
   const int64_t nel = (int64_t)A.ne * A.ne * A.ne;
-  int dev = 0, sms = 0, per = 0;
+  int dev = 0, sms = 0;
   PC_CUDA_TRY(cudaGetDevice(&dev));
   PC_CUDA_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
-  if (A.tc_type == PC_TC_BF16) {
-    PC_CUDA_TRY(cudaFuncSetAttribute(k_tc_deposit<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    PC_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_tc_deposit<1>, kThreads, smem));
-  } else {
-    PC_CUDA_TRY(cudaFuncSetAttribute(k_tc_deposit<0>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    PC_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_tc_deposit<0>, kThreads, smem));
-  }
-  if (per < 1) per = 1;
-  if (per > 4) per = 4;  // 4 x 64 tensor-memory columns per SM at most
-  int64_t grid = (int64_t)sms * per;
-  if (grid > nel) grid = nel;
+  // one persistent CTA per SM: it holds all 512 tensor-memory columns
+  int64_t grid = (nel + kProducers - 1) / kProducers;
+  if (grid > sms) grid = sms;
   if (grid < 1) grid = 1;
   *nblocks = (int)grid;
-  if (A.tc_type == PC_TC_BF16)
-    k_tc_deposit<1><<<(unsigned)grid, kThreads, smem, st>>>(A);
-  else
-    k_tc_deposit<0><<<(unsigned)grid, kThreads, smem, st>>>(A);
+  if (A.tc_type == PC_TC_BF16) {
+    PC_CUDA_TRY(cudaFuncSetAttribute(k_tc_deposit<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    k_tc_deposit<1><<<(unsigned)grid, kThreads2, smem, st>>>(A);
+  } else {
+    PC_CUDA_TRY(cudaFuncSetAttribute(k_tc_deposit<0>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    k_tc_deposit<0><<<(unsigned)grid, kThreads2, smem, st>>>(A);
+  }
   return cudaGetLastError();
 }
