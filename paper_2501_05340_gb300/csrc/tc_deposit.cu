@@ -143,7 +143,7 @@ struct __align__(1024) TcSmem2 {
   uint8_t a[kProducers][kRing][4096];
   uint8_t b[kProducers][kRing][2048];
   float pf[kProducers][kChunk][28];
-  int list[kProducers][kList];
+  float4 lrec[kProducers][kList][4];  // the kept particles' records
   int lmeta[kProducers][kList];
   float comb[64][33];
   int pre[kProducers][128];
@@ -219,37 +219,53 @@ __device__ void tc_producer(TcSmem2& S, const TcDepositArgs& A, int w, int lane)
     int nmma = 0;
     int scan = 0;
     int head = 0, tail = 0;  // kept-particle ring: [head, tail)
+    // candidate batch [scan, scan + 32) loaded one batch ahead, so that its global
+    // load latency overlaps the previous chunk's work
+    float4 c0r, c1r, c2r, c3r;
+    int cmeta = 0;
+    bool cvalid = false;
+    auto load_batch = [&](int base) {
+      const int idx = base + lane;
+      cvalid = idx < total;
+      if (cvalid) {
+        int r = 0;
+        while (S.pre[w][r + 1] <= idx) ++r;
+        const int64_t j = S.rbeg[w][r] + (idx - S.pre[w][r]);
+        const int d3[3] = {r % span - rho, (r / span) % span - rho, r / (span * span) - rho};
+        cmeta = (rho - d3[0]) | ((rho - d3[1]) << 4) | ((rho - d3[2]) << 8);
+        c0r = A.rec[4 * j];
+        c1r = A.rec[4 * j + 1];
+        c2r = A.rec[4 * j + 2];
+        c3r = A.rec[4 * j + 3];
+      }
+    };
+    if (total > 0) load_batch(0);
     for (;;) {
       // refill until the ring holds more than one chunk or the neighbourhood is exhausted,
       // so that "last chunk of the element" is known exactly
       while (scan < total && tail - head <= kChunk) {
-        const int idx = scan + lane;
         bool keep = false;
-        int j = 0, meta = 0;
-        if (idx < total) {
-          int r = 0;
-          while (S.pre[w][r + 1] <= idx) ++r;
-          j = S.rbeg[w][r] + (idx - S.pre[w][r]);
-          const int d3[3] = {r % span - rho, (r / span) % span - rho, r / (span * span) - rho};
-          const float4 r2 = A.rec[4 * (int64_t)j + 2];
-          const float4 r3 = A.rec[4 * (int64_t)j + 3];
-          const unsigned mk[3] = {__float_as_uint(r2.z), __float_as_uint(r2.w), __float_as_uint(r3.x)};
+        if (cvalid) {
+          const unsigned mk[3] = {__float_as_uint(c2r.z), __float_as_uint(c2r.w), __float_as_uint(c3r.x)};
           keep = true;
 #pragma unroll
           for (int a = 0; a < 3; ++a) {
-            const int wo = rho - d3[a];
+            const int wo = (cmeta >> (4 * a)) & 15;
             keep = keep && ((mk[a] >> (wo * n1)) & ((1u << n1) - 1u)) != 0u;
-            meta |= wo << (4 * a);
           }
         }
         const unsigned bal = __ballot_sync(0xffffffffu, keep);
         if (keep) {
           const int pos = (tail + __popc(bal & ((1u << lane) - 1u))) & (kList - 1);
-          S.list[w][pos] = j;
-          S.lmeta[w][pos] = meta;
+          S.lrec[w][pos][0] = c0r;
+          S.lrec[w][pos][1] = c1r;
+          S.lrec[w][pos][2] = c2r;
+          S.lrec[w][pos][3] = c3r;
+          S.lmeta[w][pos] = cmeta;
         }
         tail += __popc(bal);
         scan += 32;
+        if (scan < total) load_batch(scan);
       }
       __syncwarp();
       const int avail = tail - head;
@@ -272,9 +288,9 @@ __device__ void tc_producer(TcSmem2& S, const TcDepositArgs& A, int w, int lane)
         const int p = lane & 15, hlf = lane >> 4;
         float* pf = S.pf[w][p];
         if (p < take) {
-          const int64_t j = S.list[w][(head + p) & (kList - 1)];
-          const int meta = S.lmeta[w][(head + p) & (kList - 1)];
-          const float4 r0 = A.rec[4 * j], r1 = A.rec[4 * j + 1], r2 = A.rec[4 * j + 2], r3 = A.rec[4 * j + 3];
+          const int pos = (head + p) & (kList - 1);
+          const int meta = S.lmeta[w][pos];
+          const float4 r0 = S.lrec[w][pos][0], r1 = S.lrec[w][pos][1], r2 = S.lrec[w][pos][2], r3 = S.lrec[w][pos][3];
           const float t3[3] = {r0.x, r0.y, r0.z}, iz[3] = {r0.w, r1.x, r1.y};
           const unsigned mk[3] = {__float_as_uint(r2.z), __float_as_uint(r2.w), __float_as_uint(r3.x)};
 #pragma unroll
