@@ -13,10 +13,15 @@
 //
 // Operands live in shared memory in the K-major layout without swizzle: core
 // matrices of 8 rows x 16 bytes, (row/8) * 256 + (k/8) * 128 + (row%8) * 16 + (k%8) * 2.
-// One elected thread issues tcgen05.mma and tcgen05.commit; the commit arrives on
-// the stage's mbarrier when the tensor core has read the stage. Every wait on an
-// mbarrier is bounded: on expiry the kernel records PC_ETIMEOUT, stops issuing,
-// waits (bounded) for its MMAs and frees its tensor memory.
+// Each of the 8 producer warps owns one 64-column accumulator in tensor memory and
+// builds, for one element at a time, the operand tiles of 16 kept particles; its
+// lane 0 issues the tcgen05.mma and a tcgen05.commit that arrives on the slot's
+// mbarrier when the tensor core has read it (commits track the issuing thread's own
+// MMAs, so producers need no common issuer). After an element's last chunk the
+// producer queues (element, producer); 4 epilogue warps, one per TMEM lane quarter,
+// drain the queue. Every wait is bounded in wall-clock time: on expiry the kernel
+// records PC_ETIMEOUT, stops issuing, waits (bounded) for its MMAs and frees its
+// tensor memory.
 #include <cuda_bf16.h>
 #include <cuda_fp16.h>
 #include <stdint.h>
@@ -26,7 +31,6 @@
 namespace {
 
 constexpr int kChunk = 16;
-constexpr long kSpinLimit = 1L << 26;
 
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
@@ -43,22 +47,6 @@ __device__ __forceinline__ uint64_t make_desc(uint32_t saddr, uint32_t lbo, uint
   d |= (uint64_t)((sbo >> 4) & 0x3FFF) << 32;
   d |= (uint64_t)1 << 46;
   return d;
-}
-
-__device__ __forceinline__ bool mbar_wait(unsigned long long* bar, uint32_t parity) {
-  const uint32_t a = smem_u32(bar);
-  for (long it = 0; it < kSpinLimit; ++it) {
-    uint32_t done;
-    asm volatile(
-        "{\n\t.reg .pred p;\n\t"
-        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
-        "selp.u32 %0, 1, 0, p;\n\t}\n"
-        : "=r"(done)
-        : "r"(a), "r"(parity)
-        : "memory");
-    if (done) return true;
-  }
-  return false;
 }
 
 __device__ __forceinline__ void mma_commit(unsigned long long* bar) {
@@ -132,40 +120,53 @@ __device__ __forceinline__ int wrapi(int a, int n) {
   return a < 0 ? a + n : a;
 }
 
-constexpr int kProducers = 8;                           // producer warps, one TMEM accumulator each
-constexpr int kEpiWarps = 4;                            // one per TMEM lane quarter
-constexpr int kThreads2 = 32 * (kProducers + kEpiWarps + 1);
-constexpr int kRing = 2;                                // operand slots per producer
-constexpr int kList = 64;                               // kept-particle ring (>= kChunk + 32)
-constexpr int kQ = 16;                                  // finished-element queue (>= 2 kProducers)
+constexpr int kProducers = 8;                       // producer warps, one TMEM accumulator each
+constexpr int kEpiWarps = 4;                        // one per TMEM lane quarter
+constexpr int kThreads = 32 * (kProducers + kEpiWarps);
+constexpr int kRing = 2;                            // operand slots per producer
+constexpr int kList = 64;                           // kept-particle ring (>= kChunk + 32)
+constexpr int kQ = 32;                              // finished-element queue (>= 2 kProducers)
+constexpr int kMaxRanges = 125;                     // (2 rho + 1)^3 neighbour cells, rho <= 2
+constexpr int kPf = 20;                             // words per factor row: 16 particles + pad
+constexpr unsigned long long kWaitNs = 2000000000;  // a wait without progress for 2 s fails
 
-struct __align__(1024) TcSmem2 {
+// Per-producer factor rows are [v][p] with v = 8 a + i (axis a, node i) and 24 + c
+// (charge c); the row pitch of 20 words keeps both the lane-per-particle stores and
+// the float4 row reads free of bank conflicts. Kept records are stored as four
+// planes of float4 so that consecutive ring positions hit consecutive banks.
+struct __align__(1024) TcSmem {
   uint8_t a[kProducers][kRing][4096];
   uint8_t b[kProducers][kRing][2048];
-  float pf[kProducers][kChunk][28];
-  float4 lrec[kProducers][kList][4];  // the kept particles' records
+  float pf[kProducers][28][kPf];
+  float4 lrec[kProducers][4][kList];
   int lmeta[kProducers][kList];
   float comb[64][33];
-  int pre[kProducers][128];
-  int rbeg[kProducers][128];
-  int meta[kProducers][kRing][4];  // element, accumulate flag, last-chunk flag
-  unsigned long long full[kProducers][kRing];
-  unsigned long long empty[kProducers][kRing];
-  unsigned long long acc_full[kProducers];
-  unsigned long long acc_empty[kProducers];  // 2 arrivals: epilogue quarters 0 and 1
-  unsigned long long comb_full;              // 2 arrivals: epilogue quarters 2 and 3
-  unsigned long long comb_empty;             // 2 arrivals: epilogue quarters 0 and 1
-  unsigned long long fin;
+  int pre[kProducers][kMaxRanges + 1];
+  int rbeg[kProducers][kMaxRanges];
+  int rmeta[kProducers][kMaxRanges];
+  unsigned long long empty[kProducers][kRing];  // tcgen05.commit: the slot has been read
+  unsigned long long acc_full[kProducers];      // tcgen05.commit: the element's MMAs are done
+  unsigned long long acc_empty[kProducers];     // 2 arrivals: epilogue quarters 0 and 1
+  unsigned long long fin[kProducers];           // tcgen05.commit at producer exit
+  unsigned long long qfull[kQ];                 // queue entry written
+  unsigned long long comb_full;                 // 2 arrivals: epilogue quarters 2 and 3
+  unsigned long long comb_empty;                // 2 arrivals: epilogue quarters 0 and 1
   int qe[kQ];
   int qb[kQ];
-  int q_tail;
-  int prod_total[kProducers];
+  int q_head;
+  int progress[kProducers];
   int failed;
   uint32_t tmem_base;
 };
 
 __device__ __forceinline__ int vload(const int* p) { return *(const volatile int*)p; }
 __device__ __forceinline__ void vstore(int* p, int v) { *(volatile int*)p = v; }
+
+__device__ __forceinline__ unsigned long long gtime() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
 
 __device__ __forceinline__ bool mbar_try(unsigned long long* bar, uint32_t parity) {
   uint32_t done;
@@ -183,44 +184,82 @@ __device__ __forceinline__ void mbar_arrive(unsigned long long* bar) {
   asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
 }
 
-__device__ __forceinline__ void fail_now(TcSmem2& S, unsigned long long* counters) {
+// Waits for the phase of the given parity. Returns false once the block has failed,
+// or after kWaitNs without completion.
+__device__ bool mbar_wait(unsigned long long* bar, uint32_t parity, const int* failed) {
+  if (mbar_try(bar, parity)) return true;
+  const unsigned long long t0 = gtime();
+  for (unsigned it = 1;; ++it) {
+    if (mbar_try(bar, parity)) return true;
+    if ((it & 63u) == 0u && (vload(failed) || gtime() - t0 > kWaitNs)) return false;
+  }
+}
+
+__device__ __forceinline__ void fail_now(TcSmem& S, unsigned long long* counters) {
   vstore(&S.failed, 1);
   atomicMax(counters, (unsigned long long)PC_ETIMEOUT);
 }
 
+// Queue push by a producer's lane 0: (element, producer) or the exit sentinel e = -1.
+__device__ __forceinline__ void queue_push(TcSmem& S, int e, int w) {
+  const int k = atomicAdd(&S.q_head, 1);
+  S.qe[k % kQ] = e;
+  S.qb[k % kQ] = w;
+  mbar_arrive(&S.qfull[k % kQ]);  // release: the entry is visible to the waiter
+}
+
 // Producer warp w: owns elements blockIdx.x * kProducers + w + k * gridDim.x * kProducers.
-// Per element: neighbour ranges, ordered warp-level compaction of the particles
-// whose support reaches the element, then per 16 kept particles: factors (lane
-// parallel), the operand rows (3 per lane) into its ring slot, and a release
-// arrival on the slot's full barrier for the MMA thread.
+// Per element: the (2 rho + 1)^3 neighbour cell ranges and their prefix sum, ordered
+// warp-level compaction of the particles whose support reaches the element, then per
+// 16 kept particles: factors (lane parallel), the operand rows (3 per lane) into a
+// ring slot, and one tcgen05.mma into the producer's own accumulator, issued by
+// lane 0. Accumulation order inside an element is the kept order, so the deposit is
+// deterministic.
 template <int kBf16>
-__device__ void tc_producer(TcSmem2& S, const TcDepositArgs& A, int w, int lane) {
+__device__ void tc_producer(TcSmem& S, const TcDepositArgs& A, uint32_t tmem, uint32_t idesc, int w, int lane) {
   const int n1 = A.n1, ne = A.ne, rho = A.rho, span = 2 * rho + 1, nrange = span * span * span;
   const int nodes = n1 * n1 * n1;
   const int64_t nel = (int64_t)ne * ne * ne;
-  int chunk = 0;
-  for (int64_t e = (int64_t)blockIdx.x * kProducers + w; e < nel; e += (int64_t)gridDim.x * kProducers) {
-    if (vload(&S.failed)) break;
+  int top = 1;
+  while (2 * top < nrange) top *= 2;
+  // factor slots of this lane: particle p, nodes 4 hh .. 4 hh + 3 of each axis
+  const int p = lane & 15, hh = lane >> 4;
+  const unsigned lanemask = (((1u << n1) - 1u) >> (4 * hh)) & 15u;
+  float sv[4];
+#pragma unroll
+  for (int ii = 0; ii < 4; ++ii) sv[ii] = (4 * hh + ii < n1) ? A.s[4 * hh + ii] : 0.0f;
+  const float c2l = A.c2l;
+  const uint32_t acc = tmem + 64u * (uint32_t)w;
+  int chunk = 0, used = 0;
+  bool ok = true;
+  for (int64_t e = (int64_t)blockIdx.x * kProducers + w; ok && e < nel; e += (int64_t)gridDim.x * kProducers) {
+    if (__any_sync(0xffffffffu, vload(&S.failed))) break;
     const int ex = (int)(e % ne), ey = (int)((e / ne) % ne), ez = (int)(e / ((int64_t)ne * ne));
-    for (int r = lane; r < nrange; r += 32) {
-      const int dx = r % span - rho, dy = (r / span) % span - rho, dz = r / (span * span) - rho;
-      const int nb = (wrapi(ez + dz, ne) * ne + wrapi(ey + dy, ne)) * ne + wrapi(ex + dx, ne);
-      const int b0 = A.start[nb], b1 = A.start[nb + 1];
-      S.rbeg[w][r] = b0;
-      S.pre[w][r + 1] = b1 - b0;
+    int total = 0;
+    for (int r0 = 0; r0 < nrange; r0 += 32) {
+      const int r = r0 + lane;
+      int cnt = 0;
+      if (r < nrange) {
+        const int dx = r % span - rho, dy = (r / span) % span - rho, dz = r / (span * span) - rho;
+        const int nb = (wrapi(ez + dz, ne) * ne + wrapi(ey + dy, ne)) * ne + wrapi(ex + dx, ne);
+        const int b0 = A.start[nb];
+        cnt = A.start[nb + 1] - b0;
+        S.rbeg[w][r] = b0;
+        S.rmeta[w][r] = (rho - dx) | ((rho - dy) << 4) | ((rho - dz) << 8);
+      }
+      int x = cnt;
+#pragma unroll
+      for (int o = 1; o < 32; o <<= 1) {
+        const int y = __shfl_up_sync(0xffffffffu, x, o);
+        if (lane >= o) x += y;
+      }
+      if (r < nrange) S.pre[w][r + 1] = total + x;
+      total += __shfl_sync(0xffffffffu, x, 31);
     }
+    if (lane == 0) S.pre[w][0] = 0;
     __syncwarp();
-    if (lane == 0) {
-      S.pre[w][0] = 0;
-      for (int r = 1; r <= nrange; ++r) S.pre[w][r] += S.pre[w][r - 1];
-    }
-    __syncwarp();
-    const int total = S.pre[w][nrange];
-    int nmma = 0;
-    int scan = 0;
-    int head = 0, tail = 0;  // kept-particle ring: [head, tail)
-    // candidate batch [scan, scan + 32) loaded one batch ahead, so that its global
-    // load latency overlaps the previous chunk's work
+    int nmma = 0, scan = 0, head = 0, tail = 0;  // kept-particle ring: [head, tail)
+    // candidate batch [scan, scan + 32), loaded one batch ahead
     float4 c0r, c1r, c2r, c3r;
     int cmeta = 0;
     bool cvalid = false;
@@ -229,10 +268,10 @@ __device__ void tc_producer(TcSmem2& S, const TcDepositArgs& A, int w, int lane)
       cvalid = idx < total;
       if (cvalid) {
         int r = 0;
-        while (S.pre[w][r + 1] <= idx) ++r;
-        const int64_t j = S.rbeg[w][r] + (idx - S.pre[w][r]);
-        const int d3[3] = {r % span - rho, (r / span) % span - rho, r / (span * span) - rho};
-        cmeta = (rho - d3[0]) | ((rho - d3[1]) << 4) | ((rho - d3[2]) << 8);
+        for (int stp = top; stp > 0; stp >>= 1)
+          if (r + stp < nrange && S.pre[w][r + stp] <= idx) r += stp;
+        cmeta = S.rmeta[w][r];
+        const int64_t j = (int64_t)S.rbeg[w][r] + (idx - S.pre[w][r]);
         c0r = A.rec[4 * j];
         c1r = A.rec[4 * j + 1];
         c2r = A.rec[4 * j + 2];
@@ -241,8 +280,8 @@ __device__ void tc_producer(TcSmem2& S, const TcDepositArgs& A, int w, int lane)
     };
     if (total > 0) load_batch(0);
     for (;;) {
-      // refill until the ring holds more than one chunk or the neighbourhood is exhausted,
-      // so that "last chunk of the element" is known exactly
+      // refill until the ring holds more than one chunk or the neighbourhood is
+      // exhausted, so that "last chunk of the element" is known exactly
       while (scan < total && tail - head <= kChunk) {
         bool keep = false;
         if (cvalid) {
@@ -257,10 +296,10 @@ __device__ void tc_producer(TcSmem2& S, const TcDepositArgs& A, int w, int lane)
         const unsigned bal = __ballot_sync(0xffffffffu, keep);
         if (keep) {
           const int pos = (tail + __popc(bal & ((1u << lane) - 1u))) & (kList - 1);
-          S.lrec[w][pos][0] = c0r;
-          S.lrec[w][pos][1] = c1r;
-          S.lrec[w][pos][2] = c2r;
-          S.lrec[w][pos][3] = c3r;
+          S.lrec[w][0][pos] = c0r;
+          S.lrec[w][1][pos] = c1r;
+          S.lrec[w][2][pos] = c2r;
+          S.lrec[w][3][pos] = c3r;
           S.lmeta[w][pos] = cmeta;
         }
         tail += __popc(bal);
@@ -272,181 +311,167 @@ __device__ void tc_producer(TcSmem2& S, const TcDepositArgs& A, int w, int lane)
       if (avail == 0) break;
       const int take = avail < kChunk ? avail : kChunk;
       const bool last = avail <= kChunk;  // the refill stopped short only because the scan is done
-      const int slot = chunk % kRing;
-      if (chunk >= kRing) {
-        const uint32_t par = (uint32_t)((chunk / kRing - 1) & 1);
-        long it = 0;
-        while (!mbar_try(&S.empty[w][slot], par)) {
-          if (++it > kSpinLimit || vload(&S.failed)) {
-            if (lane == 0) fail_now(S, A.counters + CNT_STATUS);
-            return;
-          }
-        }
-      }
-      // factors: lane -> particle p = lane & 15, values 12 h .. 12 h + 11 of (kx[8] ky[8] kz[8])
+      // factors into pf: lane -> particle p, nodes 4 hh + ii; kx scaled by 2^4, kz by 2^8
       {
-        const int p = lane & 15, hlf = lane >> 4;
-        float* pf = S.pf[w][p];
+        float f[3][4] = {};
+        float qv[2] = {0.0f, 0.0f};
         if (p < take) {
           const int pos = (head + p) & (kList - 1);
           const int meta = S.lmeta[w][pos];
-          const float4 r0 = S.lrec[w][pos][0], r1 = S.lrec[w][pos][1], r2 = S.lrec[w][pos][2], r3 = S.lrec[w][pos][3];
-          const float t3[3] = {r0.x, r0.y, r0.z}, iz[3] = {r0.w, r1.x, r1.y};
+          const float4 r0 = S.lrec[w][0][pos], r1 = S.lrec[w][1][pos], r2 = S.lrec[w][2][pos], r3 = S.lrec[w][3][pos];
+          const float t3[3] = {r0.x, r0.y, r0.z};
+          const float iz[3] = {r0.w * 16.0f, r1.x, r1.y * 256.0f};
           const unsigned mk[3] = {__float_as_uint(r2.z), __float_as_uint(r2.w), __float_as_uint(r3.x)};
 #pragma unroll
-          for (int u = 0; u < 12; ++u) {
-            const int v = 12 * hlf + u, a = v >> 3, i = v & 7;
-            float f = 0.0f;
-            if (i < n1) {
-              const int wo = (meta >> (4 * a)) & 15;
-              if ((mk[a] >> (wo * n1 + i)) & 1u) {
-                const float d = (float)(wo - rho) + A.s[i] - t3[a];
-                f = exp2f(-(d * d) * A.c2l) * iz[a];
-              }
-            }
-            pf[v] = f;
-          }
-          if (hlf == 0) {
-            pf[24] = r1.z;
-            pf[25] = r1.w;
-            pf[26] = r2.x;
-            pf[27] = r2.y;
-          }
-        } else {
+          for (int a = 0; a < 3; ++a) {
+            const int wo = (meta >> (4 * a)) & 15;
+            const int sh = wo * n1 + 4 * hh;
+            const unsigned bits = (sh < 32 ? (mk[a] >> sh) : 0u) & lanemask;
+            const float base = (float)(wo - rho) - t3[a];
 #pragma unroll
-          for (int u = 0; u < 12; ++u) pf[12 * hlf + u] = 0.0f;
-          if (hlf == 0) pf[24] = pf[25] = pf[26] = pf[27] = 0.0f;
+            for (int ii = 0; ii < 4; ++ii) {
+              const float d = base + sv[ii];
+              const float g = exp2f(-(d * d) * c2l) * iz[a];
+              f[a][ii] = ((bits >> ii) & 1u) ? g : 0.0f;
+            }
+          }
+          qv[0] = hh ? r2.x : r1.z;
+          qv[1] = hh ? r2.y : r1.w;
         }
+        float* pf = &S.pf[w][0][0];
+#pragma unroll
+        for (int a = 0; a < 3; ++a)
+#pragma unroll
+          for (int ii = 0; ii < 4; ++ii) pf[(8 * a + 4 * hh + ii) * kPf + p] = f[a][ii];
+        pf[(24 + 2 * hh) * kPf + p] = qv[0];
+        pf[(25 + 2 * hh) * kPf + p] = qv[1];
+      }
+      const int slot = chunk % kRing;
+      const bool free_slot =
+          chunk < kRing || mbar_wait(&S.empty[w][slot], (uint32_t)((chunk / kRing - 1) & 1), &S.failed);
+      if (!__all_sync(0xffffffffu, free_slot)) {
+        if (lane == 0) fail_now(S, A.counters + CNT_STATUS);
+        ok = false;
+        break;
       }
       __syncwarp();
-      // operand rows: 0..63 YZ (A operand, hi + lo), 64..95 q kx (B operand, hi + lo)
+      // operand rows: lane and lane + 32 of YZ (A operand), lane of q kx (B operand)
 #pragma unroll
       for (int rr = 0; rr < 3; ++rr) {
         const int row = lane + 32 * rr;
-        float v[16];
-        if (row < 64) {
-          if (row < n1 * n1) {
-            const int jj = row % n1, kk = row / n1;
+        const bool is_a = rr < 2;
+        const int nrows = is_a ? n1 * n1 : 4 * n1;
+        const int lr = is_a ? row : lane;
+        if (lr < nrows) {
+          const int u0 = is_a ? 8 + lr % n1 : 24 + lr / n1;  // ky_j  or q_c
+          const int u1 = is_a ? 16 + lr / n1 : lr % n1;      // kz_k  or kx_i
+          const float4* x0 = reinterpret_cast<const float4*>(&S.pf[w][u0][0]);
+          const float4* x1 = reinterpret_cast<const float4*>(&S.pf[w][u1][0]);
+          float v[16];
 #pragma unroll
-            for (int p = 0; p < kChunk; ++p) v[p] = S.pf[w][p][8 + jj] * S.pf[w][p][16 + kk] * 256.0f;
-            store_row<kBf16>(S.a[w][slot], row, 64, v);
+          for (int t = 0; t < 4; ++t) {
+            const float4 g = x0[t], h = x1[t];
+            v[4 * t] = g.x * h.x;
+            v[4 * t + 1] = g.y * h.y;
+            v[4 * t + 2] = g.z * h.z;
+            v[4 * t + 3] = g.w * h.w;
           }
-        } else {
-          const int ci = row - 64;
-          if (ci < 4 * n1) {
-            const int c = ci / n1, i = ci % n1;
-#pragma unroll
-            for (int p = 0; p < kChunk; ++p) v[p] = S.pf[w][p][24 + c] * S.pf[w][p][i] * 16.0f;
-            store_row<kBf16>(S.b[w][slot], ci, 32, v);
-          }
+          if (is_a)
+            store_row<kBf16>(S.a[w][slot], lr, 64, v);
+          else
+            store_row<kBf16>(S.b[w][slot], lr, 32, v);
         }
       }
       asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
       __syncwarp();
       if (lane == 0) {
-        S.meta[w][slot][0] = (int)e;
-        S.meta[w][slot][1] = nmma > 0 ? 1 : 0;
-        S.meta[w][slot][2] = last ? 1 : 0;
-        mbar_arrive(&S.full[w][slot]);
+        bool go = true;
+        if (nmma == 0 && used > 0)  // the epilogue has read this accumulator's previous element
+          go = mbar_wait(&S.acc_empty[w], (uint32_t)((used - 1) & 1), &S.failed);
+        if (go) {
+          asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+          mma_issue(acc, make_desc(smem_u32(S.a[w][slot]), 128, 256), make_desc(smem_u32(S.b[w][slot]), 128, 256),
+                    idesc, nmma > 0 ? 1u : 0u);
+          mma_commit(&S.empty[w][slot]);
+          if (last) {
+            mma_commit(&S.acc_full[w]);
+            queue_push(S, (int)e, w);
+          }
+          vstore(&S.progress[w], chunk + 1);
+        } else {
+          fail_now(S, A.counters + CNT_STATUS);
+        }
       }
+      if (__shfl_sync(0xffffffffu, vload(&S.failed), 0)) {
+        ok = false;
+        break;
+      }
+      if (nmma == 0) ++used;
       head += take;
       ++nmma;
       ++chunk;
       if (last) break;
     }
-    if (nmma == 0) {
+    if (ok && nmma == 0) {
       float* out = A.field + e * 4 * nodes;
-      for (int a = lane; a < 4 * nodes; a += 32) out[a] = 0.0f;
+      for (int k = lane; k < 4 * nodes; k += 32) out[k] = 0.0f;
     }
   }
   __syncwarp();
   if (lane == 0) {
-    __threadfence_block();
-    vstore(&S.prod_total[w], chunk);
+    // every MMA this thread issued has completed once this commit arrives
+    mma_commit(&S.fin[w]);
+    int never = 0;
+    (void)mbar_wait(&S.fin[w], 0, &never);
+    queue_push(S, -1, w);
   }
 }
 
-// The MMA thread: serves the producers' rings in turn; before the first chunk of a
-// producer's element it waits (without blocking the others) for the epilogue to
-// have emptied that producer's accumulator; after an element's last chunk it commits
-// the accumulator and queues (element, producer) for the epilogue.
-__device__ void tc_mma(TcSmem2& S, const TcDepositArgs& A, uint32_t tmem, uint32_t idesc) {
-  int used[kProducers], eng[kProducers];
-  for (int w = 0; w < kProducers; ++w) used[w] = eng[w] = 0;
-  int qt = 0;
-  long idle = 0;
-  for (;;) {
-    if (vload(&S.failed)) break;
-    bool all_done = true, progress = false;
-    for (int w = 0; w < kProducers; ++w) {
-      const int tot = vload(&S.prod_total[w]);
-      if (tot >= 0 && eng[w] >= tot) continue;
-      all_done = false;
-      const int c = eng[w], slot = c % kRing;
-      if (!mbar_try(&S.full[w][slot], (uint32_t)((c / kRing) & 1))) continue;
-      const int e = S.meta[w][slot][0], acc = S.meta[w][slot][1], last = S.meta[w][slot][2];
-      if (!acc) {
-        if (used[w] >= 1 && !mbar_try(&S.acc_empty[w], (uint32_t)((used[w] - 1) & 1))) continue;
-        ++used[w];
-      }
-      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-      mma_issue(tmem + 64u * w, make_desc(smem_u32(S.a[w][slot]), 128, 256), make_desc(smem_u32(S.b[w][slot]), 128, 256),
-                idesc, (uint32_t)acc);
-      mma_commit(&S.empty[w][slot]);
-      if (last) {
-        mma_commit(&S.acc_full[w]);
-        S.qe[qt % kQ] = e;
-        S.qb[qt % kQ] = w;
-        __threadfence_block();
-        vstore(&S.q_tail, ++qt);
-      }
-      ++eng[w];
-      progress = true;
-    }
-    if (all_done) break;
-    if (progress) {
-      idle = 0;
-    } else if (++idle > kSpinLimit) {
-      fail_now(S, A.counters + CNT_STATUS);
-      break;
-    }
-  }
-  // every MMA issued so far has completed once this commit arrives
-  mma_commit(&S.fin);
-  (void)mbar_wait(&S.fin, 0);
-  S.qe[qt % kQ] = -1;
-  S.qb[qt % kQ] = 0;
-  __threadfence_block();
-  vstore(&S.q_tail, ++qt);
-}
-
-// Epilogue warp for TMEM lane quarter q: drains the finished-element queue in order.
-__device__ void tc_epilogue(TcSmem2& S, const TcDepositArgs& A, uint32_t tmem, int q, int lane) {
+// Epilogue warp for TMEM lane quarter q: drains the finished-element queue in
+// order until every producer has sent its exit sentinel.
+__device__ void tc_epilogue(TcSmem& S, const TcDepositArgs& A, uint32_t tmem, int q, int lane) {
   const int n1 = A.n1, nodes = n1 * n1 * n1;
-  int seen[kProducers];
-  for (int w = 0; w < kProducers; ++w) seen[w] = 0;
-  for (int k = 0;; ++k) {
-    long it = 0;
-    while (vload(&S.q_tail) <= k) {
-      if (++it > kSpinLimit || vload(&S.failed)) {
-        if (lane == 0 && q == 0 && !vload(&S.failed)) fail_now(S, A.counters + CNT_STATUS);
-        return;
+  unsigned seen = 0u;  // bit w: parity of the next acc_full phase of producer w
+  int exited = 0;
+  for (int k = 0; exited < kProducers; ++k) {
+    // the next entry may be a whole element away: time out only without producer progress
+    {
+      unsigned long long t0 = gtime();
+      int last_sum = -1;
+      for (unsigned it = 0; !mbar_try(&S.qfull[k % kQ], (uint32_t)((k / kQ) & 1)); ++it) {
+        if ((it & 63u) != 63u) continue;
+        if (vload(&S.failed)) return;
+        const unsigned long long now = gtime();
+        if (now - t0 > kWaitNs) {
+          int sum = 0;
+          for (int w = 0; w < kProducers; ++w) sum += vload(&S.progress[w]);
+          if (sum == last_sum) {
+            if (lane == 0 && q == 0) fail_now(S, A.counters + CNT_STATUS);
+            return;
+          }
+          last_sum = sum;
+          t0 = now;
+        }
       }
     }
     const int e = vload(&S.qe[k % kQ]), w = vload(&S.qb[k % kQ]);
-    if (e < 0) return;
-    if (!mbar_wait(&S.acc_full[w], (uint32_t)(seen[w] & 1))) {
+    if (e < 0) {
+      ++exited;
+      continue;
+    }
+    if (!mbar_wait(&S.acc_full[w], (seen >> w) & 1u, &S.failed)) {
       if (lane == 0) fail_now(S, A.counters + CNT_STATUS);
       return;
     }
-    ++seen[w];
+    seen ^= 1u << w;
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
     float r[64];
     tmem_ld64(tmem + 64u * w + ((uint32_t)(32 * q) << 16), r);
     const int jk = 32 * (q & 1) + lane;
+    const int m = k - exited;  // index of this element among the drained ones
     if (q >= 2) {
       // rows 64..127 (YZ lo): add the two column halves into comb for quarters 0 and 1
-      if (k >= 1 && !mbar_wait(&S.comb_empty, (uint32_t)((k - 1) & 1))) {
+      if (m >= 1 && !mbar_wait(&S.comb_empty, (uint32_t)((m - 1) & 1), &S.failed)) {
         if (lane == 0) fail_now(S, A.counters + CNT_STATUS);
         return;
       }
@@ -456,15 +481,18 @@ __device__ void tc_epilogue(TcSmem2& S, const TcDepositArgs& A, uint32_t tmem, i
       __syncwarp();
       if (lane == 0) mbar_arrive(&S.comb_full);
     } else {
-      if (!mbar_wait(&S.comb_full, (uint32_t)(k & 1))) {
+      if (!mbar_wait(&S.comb_full, (uint32_t)(m & 1), &S.failed)) {
         if (lane == 0) fail_now(S, A.counters + CNT_STATUS);
         return;
       }
       if (jk < n1 * n1) {
         float* out = A.field + (int64_t)e * 4 * nodes;
-        for (int ci = 0; ci < 4 * n1; ++ci) {
-          const int c = ci / n1, i = ci % n1;
-          out[c * nodes + jk * n1 + i] = ((r[ci] + r[32 + ci]) + S.comb[jk][ci]) * A.scale_out;
+#pragma unroll
+        for (int ci = 0; ci < 32; ++ci) {
+          if (ci < 4 * n1) {
+            const int c = ci / n1, i = ci - c * n1;
+            out[c * nodes + jk * n1 + i] = ((r[ci] + r[32 + ci]) + S.comb[jk][ci]) * A.scale_out;
+          }
         }
       }
       asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
@@ -479,28 +507,27 @@ __device__ void tc_epilogue(TcSmem2& S, const TcDepositArgs& A, uint32_t tmem, i
 }
 
 template <int kBf16>
-__global__ void __launch_bounds__(kThreads2, 1) k_tc_deposit(TcDepositArgs A) {
+__global__ void __launch_bounds__(kThreads, 1) k_tc_deposit(TcDepositArgs A) {
   extern __shared__ uint8_t smraw[];
-  TcSmem2& S = *reinterpret_cast<TcSmem2*>(smraw + ((1024 - (smem_u32(smraw) & 1023)) & 1023));
+  TcSmem& S = *reinterpret_cast<TcSmem*>(smraw + ((1024 - (smem_u32(smraw) & 1023)) & 1023));
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-  for (int i = tid; i < kProducers * kRing * 4096 / 16; i += kThreads2)
+  for (int i = tid; i < kProducers * kRing * 4096 / 16; i += kThreads)
     reinterpret_cast<uint4*>(&S.a[0][0][0])[i] = make_uint4(0, 0, 0, 0);
-  for (int i = tid; i < kProducers * kRing * 2048 / 16; i += kThreads2)
+  for (int i = tid; i < kProducers * kRing * 2048 / 16; i += kThreads)
     reinterpret_cast<uint4*>(&S.b[0][0][0])[i] = make_uint4(0, 0, 0, 0);
   if (tid == 0) {
     for (int w = 0; w < kProducers; ++w) {
-      for (int s = 0; s < kRing; ++s) {
-        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&S.full[w][s])));
+      for (int s = 0; s < kRing; ++s)
         asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&S.empty[w][s])));
-      }
       asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&S.acc_full[w])));
       asm volatile("mbarrier.init.shared::cta.b64 [%0], 2;" ::"r"(smem_u32(&S.acc_empty[w])));
-      S.prod_total[w] = -1;
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&S.fin[w])));
+      S.progress[w] = 0;
     }
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&S.fin)));
+    for (int k = 0; k < kQ; ++k) asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&S.qfull[k])));
     asm volatile("mbarrier.init.shared::cta.b64 [%0], 2;" ::"r"(smem_u32(&S.comb_full)));
     asm volatile("mbarrier.init.shared::cta.b64 [%0], 2;" ::"r"(smem_u32(&S.comb_empty)));
-    S.q_tail = 0;
+    S.q_head = 0;
     S.failed = 0;
   }
   if (warp == 0) {
@@ -516,13 +543,10 @@ __global__ void __launch_bounds__(kThreads2, 1) k_tc_deposit(TcDepositArgs A) {
   const uint32_t tmem = S.tmem_base;
   const uint32_t fmt = kBf16 ? 1u : 0u;
   const uint32_t idesc = (1u << 4) | (fmt << 7) | (fmt << 10) | (8u << 17) | (8u << 24);
-  if (warp < kProducers) {
-    tc_producer<kBf16>(S, A, warp, lane);
-  } else if (warp < kProducers + kEpiWarps) {
+  if (warp < kProducers)
+    tc_producer<kBf16>(S, A, tmem, idesc, warp, lane);
+  else
     tc_epilogue(S, A, tmem, warp - kProducers, lane);
-  } else if (lane == 0) {
-    tc_mma(S, A, tmem, idesc);
-  }
   __syncwarp();
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
   __syncthreads();
@@ -533,7 +557,7 @@ __global__ void __launch_bounds__(kThreads2, 1) k_tc_deposit(TcDepositArgs A) {
 }  // namespace
 
 cudaError_t pc_tc_deposit_launch(const TcDepositArgs& A, cudaStream_t st, int* nblocks) {
-  const size_t smem = sizeof(TcSmem2) + 1024;
+  const size_t smem = sizeof(TcSmem) + 1024;
   const int64_t nel = (int64_t)A.ne * A.ne * A.ne;
   int dev = 0, sms = 0;
   PC_CUDA_TRY(cudaGetDevice(&dev));
@@ -545,10 +569,10 @@ cudaError_t pc_tc_deposit_launch(const TcDepositArgs& A, cudaStream_t st, int* n
   *nblocks = (int)grid;
   if (A.tc_type == PC_TC_BF16) {
     PC_CUDA_TRY(cudaFuncSetAttribute(k_tc_deposit<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    k_tc_deposit<1><<<(unsigned)grid, kThreads2, smem, st>>>(A);
+    k_tc_deposit<1><<<(unsigned)grid, kThreads, smem, st>>>(A);
   } else {
     PC_CUDA_TRY(cudaFuncSetAttribute(k_tc_deposit<0>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    k_tc_deposit<0><<<(unsigned)grid, kThreads2, smem, st>>>(A);
+    k_tc_deposit<0><<<(unsigned)grid, kThreads, smem, st>>>(A);
   }
   return cudaGetLastError();
 }
