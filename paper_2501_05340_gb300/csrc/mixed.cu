@@ -470,8 +470,8 @@ struct PrepF32 {
 
 // Per particle (sorted by element): position t_a in its own element's units, the
 // inside-cutoff mask of the 3 (2 rho + 1) n1 window nodes, 1/Z_a with
-// Z_a = sum over inside nodes of w_i exp(-(delta h)^2/(2 sigma^2)), and q.
-// A node whose FP32 distance is within 1e-4 relative of the cutoff is decided in
+// Z_a = sum over inside nodes of w_i exp(-(delta h)^2/(2 sigma^2)), q, and per axis
+// which of the 2 rho + 1 window elements hold an inside node. A node whose FP32 distance is within 1e-4 relative of the cutoff is decided in
 // FP64 on the stored position x = (c + o)/nc with the plain definition.
 __global__ void __launch_bounds__(128) k_proj_prep_f32(PrepF32 P) {
   const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -515,7 +515,13 @@ __global__ void __launch_bounds__(128) k_proj_prep_f32(PrepF32 P) {
   rp[0] = make_float4(t3[0], t3[1], t3[2], iz[0]);
   rp[1] = make_float4(iz[1], iz[2], q0, q1);
   rp[2] = make_float4(q2, q3, __uint_as_float(mask[0]), __uint_as_float(mask[1]));
-  rp[3] = make_float4(__uint_as_float(mask[2]), 0.0f, 0.0f, 0.0f);
+  // reach bits: bit 8 a + wo set when window block wo of axis a holds an inside node
+  unsigned reach = 0u;
+  const unsigned nmask = (1u << P.n1) - 1u;
+  for (int a = 0; a < 3; ++a)
+    for (int wo = 0; wo < 2 * P.rho + 1; ++wo)
+      if ((mask[a] >> (wo * P.n1)) & nmask) reach |= 1u << (8 * a + wo);
+  rp[3] = make_float4(__uint_as_float(mask[2]), __uint_as_float(reach), 0.0f, 0.0f);
 }
 
 }  // namespace

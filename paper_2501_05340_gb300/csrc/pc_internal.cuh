@@ -117,7 +117,7 @@ struct TcDepositArgs {
   float scale_out;  // (2/h)^3 / (operand scalings)
   float s[16];      // (eta_i + 1) / 2
   const int32_t* start;
-  const float4* rec;  // [n][4]: (t0 t1 t2 iz0) (iz1 iz2 q0 q1) (q2 q3 mask0 mask1) (mask2 - - -)
+  const float4* rec;  // [n][4]: (t0 t1 t2 iz0) (iz1 iz2 q0 q1) (q2 q3 mask0 mask1) (mask2 reach - -)
   float* field;
   unsigned long long* counters;
 };
