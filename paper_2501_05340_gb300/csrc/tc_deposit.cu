@@ -168,6 +168,21 @@ __device__ __forceinline__ bool mbar_try(unsigned long long* bar, uint32_t parit
   return done != 0;
 }
 
+// As mbar_try, but a thread whose phase is not complete sleeps in hardware until it
+// completes or about kSuspendNs have passed, instead of spinning on the issue slots.
+constexpr uint32_t kSuspendNs = 200000;
+__device__ __forceinline__ bool mbar_try_sleep(unsigned long long* bar, uint32_t parity) {
+  uint32_t done;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n\t"
+      "selp.u32 %0, 1, 0, p;\n\t}\n"
+      : "=r"(done)
+      : "r"(smem_u32(bar)), "r"(parity), "r"(kSuspendNs)
+      : "memory");
+  return done != 0;
+}
+
 __device__ __forceinline__ void mbar_arrive(unsigned long long* bar) {
   asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
 }
@@ -177,9 +192,9 @@ __device__ __forceinline__ void mbar_arrive(unsigned long long* bar) {
 __device__ bool mbar_wait(unsigned long long* bar, uint32_t parity, const int* failed) {
   if (mbar_try(bar, parity)) return true;
   const unsigned long long t0 = gtime();
-  for (unsigned it = 1;; ++it) {
-    if (mbar_try(bar, parity)) return true;
-    if ((it & 63u) == 0u && (vload(failed) || gtime() - t0 > kWaitNs)) return false;
+  for (;;) {
+    if (mbar_try_sleep(bar, parity)) return true;
+    if (vload(failed) || gtime() - t0 > kWaitNs) return false;
   }
 }
 
@@ -190,9 +205,8 @@ __device__ bool mbar_wait_progress(TcSmem& S, unsigned long long* bar, uint32_t 
   if (mbar_try(bar, parity)) return true;
   unsigned long long t0 = gtime();
   int last_sum = -1;
-  for (unsigned it = 1;; ++it) {
-    if (mbar_try(bar, parity)) return true;
-    if ((it & 63u) != 0u) continue;
+  for (;;) {
+    if (mbar_try_sleep(bar, parity)) return true;
     if (vload(&S.failed)) return false;
     const unsigned long long now = gtime();
     if (now - t0 > kWaitNs) {
@@ -236,6 +250,9 @@ __device__ void tc_scanner(TcSmem& S, const TcDepositArgs& A, int k, int lane) {
 #pragma unroll
   for (int ii = 0; ii < 4; ++ii) sv[ii] = (4 * hh + ii < n1) ? A.s[4 * hh + ii] : 0.0f;
   const float c2l = A.c2l;
+  // B operand row of this lane: q_c kx_i, rows of the factor tile 24 + c and i
+  const bool brow = lane < 4 * n1;
+  const int bc = lane / n1, bq = (24 + bc) * kPf, bx = (lane - bc * n1) * kPf;
   int chunk = 0, prog = 0;
   bool ok = true;
   for (int64_t e = (int64_t)blockIdx.x * kPairs + k; ok && e < nel; e += (int64_t)gridDim.x * kPairs) {
@@ -367,11 +384,9 @@ __device__ void tc_scanner(TcSmem& S, const TcDepositArgs& A, int k, int lane) {
         break;
       }
       __syncwarp();
-      // B operand row of this lane: q_c kx_i
-      if (lane < 4 * n1) {
-        const int c = lane / n1, i = lane - c * n1;
-        const float4* x0 = reinterpret_cast<const float4*>(&S.pf[k][slot][24 + c][0]);
-        const float4* x1 = reinterpret_cast<const float4*>(&S.pf[k][slot][i][0]);
+      if (brow) {
+        const float4* x0 = reinterpret_cast<const float4*>(&S.pf[k][slot][0][0] + bq);
+        const float4* x1 = reinterpret_cast<const float4*>(&S.pf[k][slot][0][0] + bx);
         float v[16];
 #pragma unroll
         for (int t = 0; t < 4; ++t) {
@@ -420,6 +435,15 @@ template <int kBf16>
 __device__ void tc_builder(TcSmem& S, const TcDepositArgs& A, uint32_t tmem, uint32_t idesc, int k, int lane) {
   const int n1 = A.n1;
   const uint32_t acc = tmem + 64u * (uint32_t)k;
+  // A operand rows of this lane: jk = lane + 32 rr -> factor tile rows 8 + j and 16 + k
+  int ry[2], rz[2];
+#pragma unroll
+  for (int rr = 0; rr < 2; ++rr) {
+    const int row = lane + 32 * rr, kk = row / n1;
+    ry[rr] = (8 + row - kk * n1) * kPf;
+    rz[rr] = (16 + kk) * kPf;
+  }
+  const int nrow = n1 * n1;
   int used = 0;
   for (int c = 0;; ++c) {
     const int slot = c % kRing;
@@ -434,10 +458,9 @@ __device__ void tc_builder(TcSmem& S, const TcDepositArgs& A, uint32_t tmem, uin
 #pragma unroll
     for (int rr = 0; rr < 2; ++rr) {
       const int row = lane + 32 * rr;
-      if (row < n1 * n1) {
-        const int j = row % n1, kk = row / n1;
-        const float4* x0 = reinterpret_cast<const float4*>(&S.pf[k][slot][8 + j][0]);
-        const float4* x1 = reinterpret_cast<const float4*>(&S.pf[k][slot][16 + kk][0]);
+      if (row < nrow) {
+        const float4* x0 = reinterpret_cast<const float4*>(&S.pf[k][slot][0][0] + ry[rr]);
+        const float4* x1 = reinterpret_cast<const float4*>(&S.pf[k][slot][0][0] + rz[rr]);
         float v[16];
 #pragma unroll
         for (int t = 0; t < 4; ++t) {
