@@ -327,6 +327,263 @@ __global__ void k_proj_deposit(DepositArgs G) {
   }
 }
 
+// ---- blocked deposit, n1 <= 8 -------------------------------------------------
+// An element's deposit is the contraction D[jk][ci] = sum_p YZ_p[jk] A_p[ci] with
+// YZ = ky_j kz_k and A = q_c kx_i (df32), jk = k n1 + j, ci = c n1 + i. One CTA per
+// element and one warp per 2 x 2 block of (j, k) node lines; lane (b, g) of a warp
+// owns (j, k) = (2 wj + (b & 1), 2 wk + (b >> 1)), b = lane >> 3, and the TC columns
+// ci = g TC .. g TC + TC - 1, g = lane & 7, as df32 accumulators in registers. A
+// warp runs only over the staged particles whose y and z support meets its lines:
+// outside the support the factors are exact zeros, so the skipped terms change no
+// sum. Every sum runs in candidate order (canonical), so the result is deterministic.
+template <int N1>
+struct BlkShape {
+  static constexpr int NB = (N1 + 1) / 2;                            // blocks per side
+  static constexpr int NW = NB * NB;                                 // warps per CTA
+  static constexpr int TC = (4 * N1 + 7) / 8;                        // columns per lane
+  static constexpr int TCP = TC == 3 ? 4 : TC;                       // padded column group
+  static constexpr int CPW = NW == 1 ? 32 : (NW == 4 ? 8 : (NW == 9 ? 4 : 2));  // candidates staged per warp
+  static constexpr int CB = NW * CPW;                                // candidates per batch
+  static constexpr int RAW = 3 * N1 + 4;                             // factor slices and sources
+  static constexpr int YZP = (N1 * N1 + 1) & ~1;                     // YZ, padded to 16 bytes
+  static constexpr int PER = YZP + 8 * TCP;                          // staged df32 values per particle
+  static constexpr int MINB = NW == 1 ? 16 : (NW == 4 ? 8 : (NW == 9 ? 4 : 3));
+  static constexpr size_t SMEM = (size_t)(2 * CB * PER + CB * RAW) * sizeof(float2) + (size_t)(4 * CB + 376) * sizeof(int);
+};
+
+struct BlkArgs {
+  int64_t n;
+  int ne, rho, win;
+  const int32_t* start;
+  const float2* fac;
+  const float2* sq;
+  double* field;
+};
+
+// acc += a b for df32 a, b: product with its FMA error terms, TwoSum on the high
+// parts, all errors gathered in the low part.
+__device__ __forceinline__ void df_fma_acc(f2& acc, float2 a, float2 b) {
+  const float p = a.x * b.x;
+  float e = fmaf(a.x, b.x, -p);
+  e = fmaf(a.x, b.y, e);
+  e = fmaf(a.y, b.x, e);
+  const float s = acc.h + p;
+  const float bb = s - acc.h;
+  const float err = (acc.h - (s - bb)) + (p - bb);
+  acc.h = s;
+  acc.l = acc.l + (err + e);
+}
+
+template <int N1>
+__global__ void __launch_bounds__(32 * BlkShape<N1>::NW, BlkShape<N1>::MINB) k_proj_deposit_blk(BlkArgs G) {
+  using B = BlkShape<N1>;
+  constexpr int TC = B::TC, TCP = B::TCP, CPW = B::CPW, CB = B::CB, RAW = B::RAW, PER = B::PER, YZP = B::YZP;
+  constexpr int NODES = N1 * N1 * N1;
+  extern __shared__ float4 smb4[];
+  float2* stage = reinterpret_cast<float2*>(smb4);  // [2][CB][PER]: YZ then A groups
+  float2* raw = stage + 2 * CB * PER;               // [CB][RAW]
+  int* box = reinterpret_cast<int*>(raw + CB * RAW);  // [2][CB]: y and z support lines, -1 if not kept
+  int* cj = box + 2 * CB;                           // [CB] particle index (sorted order), -1 past the end
+  int* cw = cj + CB;                                // [CB] factor window offsets of the 3 axes
+  int* pre = cw + CB;                               // [126] prefix of the neighbour range sizes
+  int* rbeg = pre + 126;                            // [125]
+  int* rmeta = rbeg + 125;                          // [125]
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int64_t n = G.n;
+  const int ne = G.ne, rho = G.rho, span = 2 * rho + 1, nrange = span * span * span, win = G.win;
+  const int e = blockIdx.x;
+  const int ex = e % ne, ey = (e / ne) % ne, ez = e / (ne * ne);
+  if (warp == 0) {
+    int tot = 0;
+    for (int r0 = 0; r0 < nrange; r0 += 32) {
+      const int r = r0 + lane;
+      int cnt = 0;
+      if (r < nrange) {
+        const int dx = r % span - rho, dy = (r / span) % span - rho, dz = r / (span * span) - rho;
+        const int nb = (wrapi(ez + dz, ne) * ne + wrapi(ey + dy, ne)) * ne + wrapi(ex + dx, ne);
+        const int b0 = G.start[nb];
+        cnt = G.start[nb + 1] - b0;
+        rbeg[r] = b0;
+        rmeta[r] = ((rho - dx) * N1) | (((rho - dy) * N1) << 8) | (((rho - dz) * N1) << 16);
+      }
+      int x = cnt;
+#pragma unroll
+      for (int o = 1; o < 32; o <<= 1) {
+        const int y = __shfl_up_sync(0xffffffffu, x, o);
+        if (lane >= o) x += y;
+      }
+      if (r < nrange) pre[r + 1] = tot + x;
+      tot += __shfl_sync(0xffffffffu, x, 31);
+    }
+    if (lane == 0) pre[0] = 0;
+  }
+  __syncthreads();
+  const int total = pre[nrange];
+  const int nbatch = (total + CB - 1) / CB;
+  int top = 1;
+  while (2 * top < nrange) top *= 2;
+
+  const int wj = warp % B::NB, wk = warp / B::NB;
+  const int bq = lane >> 3, g = lane & 7;
+  const int j = 2 * wj + (bq & 1), k = 2 * wk + (bq >> 1);
+  const bool jk_ok = j < N1 && k < N1;
+  const int jk = jk_ok ? k * N1 + j : 0;
+  const int y0 = 2 * wj, z0 = 2 * wk;
+
+  // staging of batch b into buffer buf by this warp: its CPW candidates
+  auto stage_batch = [&](int b, int buf) {
+    if (lane < CPW) {
+      const int c = warp * CPW + lane;
+      const int idx = b * CB + c;
+      int jj = -1, wm = 0;
+      if (idx < total) {
+        int r = 0;
+        for (int stp = top; stp > 0; stp >>= 1)
+          if (r + stp < nrange && pre[r + stp] <= idx) r += stp;
+        jj = rbeg[r] + (idx - pre[r]);
+        wm = rmeta[r];
+      }
+      cj[c] = jj;
+      cw[c] = wm;
+    }
+    __syncwarp();
+    for (int t = lane; t < CPW * RAW; t += 32) {
+      const int pl = t / RAW, rr = t - pl * RAW;
+      const int c = warp * CPW + pl;
+      const int jj = cj[c];
+      float2 v = make_float2(0.0f, 0.0f);
+      if (jj >= 0) {
+        if (rr < 3 * N1) {
+          const int a = rr / N1, i = rr - a * N1;
+          const int wo = (cw[c] >> (8 * a)) & 255;
+          v = G.fac[((int64_t)a * win + wo + i) * n + jj];
+        } else {
+          v = G.sq[(int64_t)(rr - 3 * N1) * n + jj];
+        }
+      }
+      raw[c * RAW + rr] = v;
+    }
+    __syncwarp();
+    if (lane < CPW) {
+      const int c = warp * CPW + lane;
+      const float2* f = raw + c * RAW;
+      int lo[3] = {N1, N1, N1}, hi[3] = {-1, -1, -1};
+#pragma unroll
+      for (int a = 0; a < 3; ++a)
+#pragma unroll
+        for (int i = 0; i < N1; ++i)
+          if (f[a * N1 + i].x != 0.0f) {
+            lo[a] = min(lo[a], i);
+            hi[a] = i;
+          }
+      const bool kept = hi[0] >= 0 && hi[1] >= 0 && hi[2] >= 0;
+      box[buf * CB + c] = kept ? (lo[1] | (hi[1] << 8) | (lo[2] << 16) | (hi[2] << 24)) : -1;
+    }
+    float2* sp = stage + (size_t)(buf * CB + warp * CPW) * PER;
+    for (int t = lane; t < CPW * PER; t += 32) {
+      const int pl = t / PER, rr = t - pl * PER;
+      const float2* f = raw + (warp * CPW + pl) * RAW;
+      f2 v = {0.0f, 0.0f};
+      if (rr < N1 * N1) {
+        const int kk = rr / N1, jj = rr - kk * N1;
+        const float2 fy = f[N1 + jj], fz = f[2 * N1 + kk];
+        v = df_mul({fy.x, fy.y}, {fz.x, fz.y});
+      } else if (rr >= YZP) {
+        const int s = rr - YZP, gg = s / TCP, t2 = s - gg * TCP;
+        const int ci = gg * TC + t2;
+        if (t2 < TC && ci < 4 * N1) {
+          const int c = ci / N1, i = ci - c * N1;
+          const float2 fx = f[i], qv = f[3 * N1 + c];
+          v = df_mul({qv.x, qv.y}, {fx.x, fx.y});
+        }
+      }
+      sp[t] = make_float2(v.h, v.l);
+    }
+  };
+
+  f2 acc[TC];
+#pragma unroll
+  for (int t = 0; t < TC; ++t) acc[t] = {0.0f, 0.0f};
+  auto gemm_batch = [&](int buf) {
+    const float2* sb = stage + (size_t)buf * CB * PER;
+    const int* bx = box + buf * CB;
+#pragma unroll
+    for (int base = 0; base < CB; base += 32) {
+      const int c = base + lane;
+      bool rel = false;
+      if (c < CB) {
+        const int w = bx[c];
+        if (w >= 0) {
+          const int ylo = w & 255, yhi = (w >> 8) & 255, zlo = (w >> 16) & 255, zhi = (w >> 24) & 255;
+          rel = ylo <= y0 + 1 && yhi >= y0 && zlo <= z0 + 1 && zhi >= z0;
+        }
+      }
+      unsigned m = __ballot_sync(0xffffffffu, rel);
+      while (m) {
+        const int q = base + __ffs(m) - 1;
+        m &= m - 1;
+        const float2* pq = sb + (size_t)q * PER;
+        const float2 bv = pq[jk];
+        float2 av[TCP];
+        if constexpr (TCP == 1) {
+          av[0] = pq[YZP + g];
+        } else {
+#pragma unroll
+          for (int u = 0; u < TCP / 2; ++u) {
+            const float4 v4 = reinterpret_cast<const float4*>(pq + YZP + g * TCP)[u];
+            av[2 * u] = make_float2(v4.x, v4.y);
+            av[2 * u + 1] = make_float2(v4.z, v4.w);
+          }
+        }
+#pragma unroll
+        for (int t = 0; t < TC; ++t) df_fma_acc(acc[t], av[t], bv);
+      }
+    }
+  };
+
+  if (nbatch > 0) stage_batch(0, 0);
+  __syncthreads();
+  for (int b = 0; b < nbatch; ++b) {
+    if (b + 1 < nbatch) stage_batch(b + 1, (b + 1) & 1);
+    gemm_batch(b & 1);
+    __syncthreads();
+  }
+  if (jk_ok) {
+    double* out = G.field + (int64_t)e * 4 * NODES;
+#pragma unroll
+    for (int t = 0; t < TC; ++t) {
+      const int ci = g * TC + t;
+      if (ci < 4 * N1) {
+        const int c = ci / N1, i = ci - c * N1;
+        out[c * NODES + jk * N1 + i] = (double)acc[t].h + (double)acc[t].l;
+      }
+    }
+  }
+}
+
+template <int N1>
+cudaError_t launch_blk(const BlkArgs& G, int64_t nel, cudaStream_t st) {
+  using B = BlkShape<N1>;
+  cudaError_t e = cudaFuncSetAttribute(k_proj_deposit_blk<N1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)B::SMEM);
+  if (e != cudaSuccess) return e;
+  k_proj_deposit_blk<N1><<<(unsigned)nel, 32 * B::NW, B::SMEM, st>>>(G);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_blk_n1(int n1, const BlkArgs& G, int64_t nel, cudaStream_t st) {
+  switch (n1) {
+    case 1: return launch_blk<1>(G, nel, st);
+    case 2: return launch_blk<2>(G, nel, st);
+    case 3: return launch_blk<3>(G, nel, st);
+    case 4: return launch_blk<4>(G, nel, st);
+    case 5: return launch_blk<5>(G, nel, st);
+    case 6: return launch_blk<6>(G, nel, st);
+    case 7: return launch_blk<7>(G, nel, st);
+    case 8: return launch_blk<8>(G, nel, st);
+    default: return cudaErrorInvalidValue;
+  }
+}
+
 }  // namespace
 
 static void deposit_shape(int n1, int* nwarps, int* batch, size_t* smem) {
@@ -418,12 +675,29 @@ pc_status pc_project_impl(pc_ctx* ctx, const pc_particles* p, double* field) {
     G.fac = ctx->fac;
     G.sq = ctx->sq;
     G.field = field;
-    e = cudaFuncSetAttribute(k_proj_deposit, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) goto fail;
-    const int td = pc_phase_begin(ctx, PC_PH_DEPOSIT);
-    k_proj_deposit<<<(unsigned)nel, 32 * G.nwarps, smem, st>>>(G);
-    ctx->launches += 1;
-    pc_phase_end(ctx, td);
+    if (ctx->n1 <= 8) {
+      BlkArgs K;
+      K.n = n;
+      K.ne = ne;
+      K.rho = ctx->rho;
+      K.win = ctx->win;
+      K.start = ctx->start;
+      K.fac = ctx->fac;
+      K.sq = ctx->sq;
+      K.field = field;
+      const int td = pc_phase_begin(ctx, PC_PH_DEPOSIT);
+      e = launch_blk_n1(ctx->n1, K, nel, st);
+      ctx->launches += 1;
+      pc_phase_end(ctx, td);
+      if (e != cudaSuccess) goto fail;
+    } else {
+      e = cudaFuncSetAttribute(k_proj_deposit, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+      if (e != cudaSuccess) goto fail;
+      const int td = pc_phase_begin(ctx, PC_PH_DEPOSIT);
+      k_proj_deposit<<<(unsigned)nel, 32 * G.nwarps, smem, st>>>(G);
+      ctx->launches += 1;
+      pc_phase_end(ctx, td);
+    }
   }
   e = cudaGetLastError();
   if (e == cudaSuccess) return PC_OK;
