@@ -335,20 +335,23 @@ __global__ void k_proj_deposit(DepositArgs G) {
 // ci = g TC .. g TC + TC - 1, g = lane & 7, as df32 accumulators in registers. A
 // warp runs only over the staged particles whose y and z support meets its lines:
 // outside the support the factors are exact zeros, so the skipped terms change no
-// sum. Every sum runs in candidate order (canonical), so the result is deterministic.
+// sum. Candidates come in batches of 32, staged lane-per-candidate by one warp in
+// turn into a double buffer; every sum runs in candidate order (canonical), so the
+// result is deterministic.
 template <int N1>
 struct BlkShape {
-  static constexpr int NB = (N1 + 1) / 2;                            // blocks per side
-  static constexpr int NW = NB * NB;                                 // warps per CTA
-  static constexpr int TC = (4 * N1 + 7) / 8;                        // columns per lane
-  static constexpr int TCP = TC == 3 ? 4 : TC;                       // padded column group
-  static constexpr int CPW = NW == 1 ? 32 : (NW == 4 ? 8 : (NW == 9 ? 4 : 2));  // candidates staged per warp
-  static constexpr int CB = NW * CPW;                                // candidates per batch
-  static constexpr int RAW = 3 * N1 + 4;                             // factor slices and sources
-  static constexpr int YZP = (N1 * N1 + 1) & ~1;                     // YZ, padded to 16 bytes
-  static constexpr int PER = YZP + 8 * TCP;                          // staged df32 values per particle
-  static constexpr int MINB = NW == 1 ? 16 : (NW == 4 ? 8 : (NW == 9 ? 4 : 3));
-  static constexpr size_t SMEM = (size_t)(2 * CB * PER + CB * RAW) * sizeof(float2) + (size_t)(4 * CB + 376) * sizeof(int);
+  static constexpr int NB = (N1 + 1) / 2;          // blocks per side
+  static constexpr int NW = NB * NB;               // warps per CTA
+  static constexpr int TC = (4 * N1 + 7) / 8;      // columns per lane
+  static constexpr int TCP = TC == 3 ? 4 : TC;     // padded column group
+  static constexpr int YZP = (N1 * N1 + 1) & ~1;   // YZ entries, padded to 16 bytes
+  // staged df32 values per particle: YZ, then A as [TCP / 2][8 groups][2] (groups of
+  // one column when TCP = 1); the row pitch in 16-byte units is odd, so that the
+  // stager's per-lane row stores do not collide in the banks
+  static constexpr int PER0 = YZP + 8 * TCP;
+  static constexpr int PER = (PER0 / 2) % 2 == 1 ? PER0 : PER0 + 2;
+  static constexpr int MINB = NW == 1 ? 16 : (NW == 4 ? 8 : (NW == 9 ? 4 : 2));
+  static constexpr size_t SMEM = (size_t)(2 * 32 * PER) * sizeof(float2) + (size_t)(2 * 32 + 376) * sizeof(int);
 };
 
 struct BlkArgs {
@@ -374,20 +377,40 @@ __device__ __forceinline__ void df_fma_acc(f2& acc, float2 a, float2 b) {
   acc.l = acc.l + (err + e);
 }
 
+__device__ __forceinline__ float2 df_mul2(float2 a, float2 b) {
+  const f2 v = df_mul({a.x, a.y}, {b.x, b.y});
+  return make_float2(v.h, v.l);
+}
+
+// Offset of A column (group g, slot t) in a staged row.
+template <int N1>
+__host__ __device__ constexpr int a_off(int g, int t) {
+  using B = BlkShape<N1>;
+  return B::TCP == 1 ? B::YZP + g : B::YZP + ((t >> 1) * 8 + g) * 2 + (t & 1);
+}
+
+// Column ci held at entry x of the A part of a staged row (inverse of a_off), or -1
+// for padding.
+template <int N1>
+__host__ __device__ constexpr int a_col(int x) {
+  using B = BlkShape<N1>;
+  const int g = B::TCP == 1 ? x : (B::TCP == 2 ? x / 2 : (x / 2) % 8);
+  const int t = B::TCP == 1 ? 0 : (B::TCP == 2 ? x % 2 : 2 * ((x / 2) / 8) + x % 2);
+  const int ci = g * B::TC + t;
+  return (t < B::TC && ci < 4 * N1) ? ci : -1;
+}
+
 template <int N1>
 __global__ void __launch_bounds__(32 * BlkShape<N1>::NW, BlkShape<N1>::MINB) k_proj_deposit_blk(BlkArgs G) {
   using B = BlkShape<N1>;
-  constexpr int TC = B::TC, TCP = B::TCP, CPW = B::CPW, CB = B::CB, RAW = B::RAW, PER = B::PER, YZP = B::YZP;
+  constexpr int NW = B::NW, TC = B::TC, TCP = B::TCP, PER = B::PER, YZP = B::YZP;
   constexpr int NODES = N1 * N1 * N1;
   extern __shared__ float4 smb4[];
-  float2* stage = reinterpret_cast<float2*>(smb4);  // [2][CB][PER]: YZ then A groups
-  float2* raw = stage + 2 * CB * PER;               // [CB][RAW]
-  int* box = reinterpret_cast<int*>(raw + CB * RAW);  // [2][CB]: y and z support lines, -1 if not kept
-  int* cj = box + 2 * CB;                           // [CB] particle index (sorted order), -1 past the end
-  int* cw = cj + CB;                                // [CB] factor window offsets of the 3 axes
-  int* pre = cw + CB;                               // [126] prefix of the neighbour range sizes
-  int* rbeg = pre + 126;                            // [125]
-  int* rmeta = rbeg + 125;                          // [125]
+  float2* stage = reinterpret_cast<float2*>(smb4);          // [2][32][PER]
+  int* box = reinterpret_cast<int*>(stage + 2 * 32 * PER);  // [2][32]: y, z support lines; -1 if not kept
+  int* pre = box + 2 * 32;                                  // [126] prefix of the neighbour range sizes
+  int* rbeg = pre + 126;                                    // [125]
+  int* rmeta = rbeg + 125;                                  // [125]
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int64_t n = G.n;
   const int ne = G.ne, rho = G.rho, span = 2 * rho + 1, nrange = span * span * span, win = G.win;
@@ -419,132 +442,122 @@ __global__ void __launch_bounds__(32 * BlkShape<N1>::NW, BlkShape<N1>::MINB) k_p
   }
   __syncthreads();
   const int total = pre[nrange];
-  const int nbatch = (total + CB - 1) / CB;
+  const int nbatch = (total + 31) / 32;
   int top = 1;
   while (2 * top < nrange) top *= 2;
 
+  // staging of batch b into buffer buf by the calling warp, lane = candidate
+  auto stage_batch = [&](int b, int buf) {
+    const int idx = b * 32 + lane;
+    int64_t jj = 0;
+    int wm = 0;
+    const bool valid = idx < total;
+    if (valid) {
+      int r = 0;
+      for (int stp = top; stp > 0; stp >>= 1)
+        if (r + stp < nrange && pre[r + stp] <= idx) r += stp;
+      jj = rbeg[r] + (idx - pre[r]);
+      wm = rmeta[r];
+    }
+    float4* row = reinterpret_cast<float4*>(stage + (size_t)(buf * 32 + lane) * PER);
+    int ylo = N1, yhi = -1, zlo = N1, zhi = -1;
+    {
+      float2 fy[N1], fz[N1];
+      const float2* py = G.fac + ((int64_t)win + ((wm >> 8) & 255)) * n + jj;
+      const float2* pz = G.fac + ((int64_t)2 * win + ((wm >> 16) & 255)) * n + jj;
+#pragma unroll
+      for (int i = 0; i < N1; ++i) {
+        fy[i] = valid ? py[(int64_t)i * n] : make_float2(0.0f, 0.0f);
+        fz[i] = valid ? pz[(int64_t)i * n] : make_float2(0.0f, 0.0f);
+      }
+#pragma unroll
+      for (int i = 0; i < N1; ++i) {
+        if (fy[i].x != 0.0f) {
+          ylo = min(ylo, i);
+          yhi = i;
+        }
+        if (fz[i].x != 0.0f) {
+          zlo = min(zlo, i);
+          zhi = i;
+        }
+      }
+#pragma unroll
+      for (int u = 0; u < YZP / 2; ++u) {
+        float2 v[2];
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+          const int q = 2 * u + h;
+          v[h] = q < N1 * N1 ? df_mul2(fy[q % N1], fz[q / N1]) : make_float2(0.0f, 0.0f);
+        }
+        row[u] = make_float4(v[0].x, v[0].y, v[1].x, v[1].y);
+      }
+    }
+    bool xany = false;
+    {
+      float2 fx[N1], qv[4];
+      const float2* px = G.fac + (int64_t)(wm & 255) * n + jj;
+#pragma unroll
+      for (int i = 0; i < N1; ++i) {
+        fx[i] = valid ? px[(int64_t)i * n] : make_float2(0.0f, 0.0f);
+        xany = xany || fx[i].x != 0.0f;
+      }
+#pragma unroll
+      for (int c = 0; c < 4; ++c) qv[c] = valid ? G.sq[(int64_t)c * n + jj] : make_float2(0.0f, 0.0f);
+#pragma unroll
+      for (int u = 0; u < 4 * TCP; ++u) {
+        float2 v[2];
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+          const int ci = a_col<N1>(2 * u + h);
+          v[h] = ci >= 0 ? df_mul2(qv[ci / N1], fx[ci % N1]) : make_float2(0.0f, 0.0f);
+        }
+        row[YZP / 2 + u] = make_float4(v[0].x, v[0].y, v[1].x, v[1].y);
+      }
+    }
+    box[buf * 32 + lane] = (yhi >= 0 && zhi >= 0 && xany) ? (ylo | (yhi << 8) | (zlo << 16) | (zhi << 24)) : -1;
+  };
+
+  // this lane's outputs and their staged-row offsets
   const int wj = warp % B::NB, wk = warp / B::NB;
   const int bq = lane >> 3, g = lane & 7;
   const int j = 2 * wj + (bq & 1), k = 2 * wk + (bq >> 1);
   const bool jk_ok = j < N1 && k < N1;
   const int jk = jk_ok ? k * N1 + j : 0;
   const int y0 = 2 * wj, z0 = 2 * wk;
-
-  // staging of batch b into buffer buf by this warp: its CPW candidates
-  auto stage_batch = [&](int b, int buf) {
-    if (lane < CPW) {
-      const int c = warp * CPW + lane;
-      const int idx = b * CB + c;
-      int jj = -1, wm = 0;
-      if (idx < total) {
-        int r = 0;
-        for (int stp = top; stp > 0; stp >>= 1)
-          if (r + stp < nrange && pre[r + stp] <= idx) r += stp;
-        jj = rbeg[r] + (idx - pre[r]);
-        wm = rmeta[r];
-      }
-      cj[c] = jj;
-      cw[c] = wm;
-    }
-    __syncwarp();
-    for (int t = lane; t < CPW * RAW; t += 32) {
-      const int pl = t / RAW, rr = t - pl * RAW;
-      const int c = warp * CPW + pl;
-      const int jj = cj[c];
-      float2 v = make_float2(0.0f, 0.0f);
-      if (jj >= 0) {
-        if (rr < 3 * N1) {
-          const int a = rr / N1, i = rr - a * N1;
-          const int wo = (cw[c] >> (8 * a)) & 255;
-          v = G.fac[((int64_t)a * win + wo + i) * n + jj];
-        } else {
-          v = G.sq[(int64_t)(rr - 3 * N1) * n + jj];
-        }
-      }
-      raw[c * RAW + rr] = v;
-    }
-    __syncwarp();
-    if (lane < CPW) {
-      const int c = warp * CPW + lane;
-      const float2* f = raw + c * RAW;
-      int lo[3] = {N1, N1, N1}, hi[3] = {-1, -1, -1};
-#pragma unroll
-      for (int a = 0; a < 3; ++a)
-#pragma unroll
-        for (int i = 0; i < N1; ++i)
-          if (f[a * N1 + i].x != 0.0f) {
-            lo[a] = min(lo[a], i);
-            hi[a] = i;
-          }
-      const bool kept = hi[0] >= 0 && hi[1] >= 0 && hi[2] >= 0;
-      box[buf * CB + c] = kept ? (lo[1] | (hi[1] << 8) | (lo[2] << 16) | (hi[2] << 24)) : -1;
-    }
-    float2* sp = stage + (size_t)(buf * CB + warp * CPW) * PER;
-    for (int t = lane; t < CPW * PER; t += 32) {
-      const int pl = t / PER, rr = t - pl * PER;
-      const float2* f = raw + (warp * CPW + pl) * RAW;
-      f2 v = {0.0f, 0.0f};
-      if (rr < N1 * N1) {
-        const int kk = rr / N1, jj = rr - kk * N1;
-        const float2 fy = f[N1 + jj], fz = f[2 * N1 + kk];
-        v = df_mul({fy.x, fy.y}, {fz.x, fz.y});
-      } else if (rr >= YZP) {
-        const int s = rr - YZP, gg = s / TCP, t2 = s - gg * TCP;
-        const int ci = gg * TC + t2;
-        if (t2 < TC && ci < 4 * N1) {
-          const int c = ci / N1, i = ci - c * N1;
-          const float2 fx = f[i], qv = f[3 * N1 + c];
-          v = df_mul({qv.x, qv.y}, {fx.x, fx.y});
-        }
-      }
-      sp[t] = make_float2(v.h, v.l);
-    }
-  };
-
   f2 acc[TC];
 #pragma unroll
   for (int t = 0; t < TC; ++t) acc[t] = {0.0f, 0.0f};
   auto gemm_batch = [&](int buf) {
-    const float2* sb = stage + (size_t)buf * CB * PER;
-    const int* bx = box + buf * CB;
+    const float2* sb = stage + (size_t)buf * 32 * PER;
+    const int w = box[buf * 32 + lane];
+    const int ylo = w & 255, yhi = (w >> 8) & 255, zlo = (w >> 16) & 255, zhi = (w >> 24) & 255;
+    const bool rel = w >= 0 && ylo <= y0 + 1 && yhi >= y0 && zlo <= z0 + 1 && zhi >= z0;
+    unsigned m = __ballot_sync(0xffffffffu, rel);
+    while (m) {
+      const int q = __ffs(m) - 1;
+      m &= m - 1;
+      const float2* pq = sb + q * PER;
+      const float2 bv = pq[jk];
+      float2 av[TCP];
+      if constexpr (TCP == 1) {
+        av[0] = pq[YZP + g];
+      } else {
 #pragma unroll
-    for (int base = 0; base < CB; base += 32) {
-      const int c = base + lane;
-      bool rel = false;
-      if (c < CB) {
-        const int w = bx[c];
-        if (w >= 0) {
-          const int ylo = w & 255, yhi = (w >> 8) & 255, zlo = (w >> 16) & 255, zhi = (w >> 24) & 255;
-          rel = ylo <= y0 + 1 && yhi >= y0 && zlo <= z0 + 1 && zhi >= z0;
+        for (int u = 0; u < TCP / 2; ++u) {
+          const float4 v4 = *reinterpret_cast<const float4*>(pq + a_off<N1>(g, 2 * u));
+          av[2 * u] = make_float2(v4.x, v4.y);
+          av[2 * u + 1] = make_float2(v4.z, v4.w);
         }
       }
-      unsigned m = __ballot_sync(0xffffffffu, rel);
-      while (m) {
-        const int q = base + __ffs(m) - 1;
-        m &= m - 1;
-        const float2* pq = sb + (size_t)q * PER;
-        const float2 bv = pq[jk];
-        float2 av[TCP];
-        if constexpr (TCP == 1) {
-          av[0] = pq[YZP + g];
-        } else {
 #pragma unroll
-          for (int u = 0; u < TCP / 2; ++u) {
-            const float4 v4 = reinterpret_cast<const float4*>(pq + YZP + g * TCP)[u];
-            av[2 * u] = make_float2(v4.x, v4.y);
-            av[2 * u + 1] = make_float2(v4.z, v4.w);
-          }
-        }
-#pragma unroll
-        for (int t = 0; t < TC; ++t) df_fma_acc(acc[t], av[t], bv);
-      }
+      for (int t = 0; t < TC; ++t) df_fma_acc(acc[t], av[t], bv);
     }
   };
 
-  if (nbatch > 0) stage_batch(0, 0);
+  if (nbatch > 0 && warp == 0) stage_batch(0, 0);
   __syncthreads();
   for (int b = 0; b < nbatch; ++b) {
-    if (b + 1 < nbatch) stage_batch(b + 1, (b + 1) & 1);
+    if (b + 1 < nbatch && warp == (b + 1) % NW) stage_batch(b + 1, (b + 1) & 1);
     gemm_batch(b & 1);
     __syncthreads();
   }
