@@ -18,6 +18,8 @@
 
 #include <string.h>
 
+#include <type_traits>
+
 #include "df32.cuh"
 #include "pc_internal.cuh"
 
@@ -335,9 +337,9 @@ __global__ void k_proj_deposit(DepositArgs G) {
 // ci = g TC .. g TC + TC - 1, g = lane & 7, as df32 accumulators in registers. A
 // warp runs only over the staged particles whose y and z support meets its lines:
 // outside the support the factors are exact zeros, so the skipped terms change no
-// sum. Candidates come in batches of 32, staged lane-per-candidate by one warp in
-// turn into a double buffer; every sum runs in candidate order (canonical), so the
-// result is deterministic.
+// sum. Candidates come in batches of 32 (in a fixed permuted order that spreads
+// each batch over the neighbourhood), staged lane-per-candidate into a double
+// buffer; every sum runs in that order, so the result is deterministic.
 template <int N1>
 struct BlkShape {
   static constexpr int NB = (N1 + 1) / 2;          // blocks per side
@@ -375,6 +377,23 @@ __device__ __forceinline__ void df_fma_acc(f2& acc, float2 a, float2 b) {
   const float err = (acc.h - (s - bb)) + (p - bb);
   acc.h = s;
   acc.l = acc.l + (err + e);
+}
+
+// Two accumulators at once on the packed FP32x2 pipe instructions: (H, L) += (ah, al) b
+// with H, L, ah, al pairs of high and low parts and b one df32 value; the same
+// operations as df_fma_acc, lane by lane.
+__device__ __forceinline__ float2 neg2(float2 a) { return make_float2(-a.x, -a.y); }
+__device__ __forceinline__ void df_fma_acc2(float2& H, float2& L, float2 ah, float2 al, float2 b) {
+  const float2 bh = make_float2(b.x, b.x), bl = make_float2(b.y, b.y);
+  const float2 p = __fmul2_rn(ah, bh);
+  float2 e = __ffma2_rn(ah, bh, neg2(p));
+  e = __ffma2_rn(ah, bl, e);
+  e = __ffma2_rn(al, bh, e);
+  const float2 s = __fadd2_rn(H, p);
+  const float2 bb = __fadd2_rn(s, neg2(H));
+  const float2 err = __fadd2_rn(__fadd2_rn(H, neg2(__fadd2_rn(s, neg2(bb)))), __fadd2_rn(p, neg2(bb)));
+  H = s;
+  L = __fadd2_rn(L, __fadd2_rn(err, e));
 }
 
 __device__ __forceinline__ float2 df_mul2(float2 a, float2 b) {
@@ -445,76 +464,127 @@ __global__ void __launch_bounds__(32 * BlkShape<N1>::NW, BlkShape<N1>::MINB) k_p
   const int nbatch = (total + 31) / 32;
   int top = 1;
   while (2 * top < nrange) top *= 2;
-
-  // staging of batch b into buffer buf by the calling warp, lane = candidate
-  auto stage_batch = [&](int b, int buf) {
-    const int idx = b * 32 + lane;
-    int64_t jj = 0;
-    int wm = 0;
-    const bool valid = idx < total;
-    if (valid) {
-      int r = 0;
-      for (int stp = top; stp > 0; stp >>= 1)
-        if (r + stp < nrange && pre[r + stp] <= idx) r += stp;
-      jj = rbeg[r] + (idx - pre[r]);
-      wm = rmeta[r];
+  // Candidates are taken in blocks of 8 whose order is a multiplicative permutation
+  // blk -> blk mix mod nfull (mix coprime to nfull, near nfull / golden ratio), so that
+  // a batch mixes four distant blocks of the neighbourhood and the warps' shares of a
+  // batch stay even; the trailing partial block keeps its place.
+  const int nfull = total >> 3;
+  int mix = 1;
+  if (nfull > 2) {
+    mix = (int)(0.6180339887 * nfull) | 1;
+    for (;; mix += 2) {
+      int a = nfull, c = mix;
+      while (c) {
+        const int t = a % c;
+        a = c;
+        c = t;
+      }
+      if (a == 1) break;
     }
+  }
+
+  // Staging of batch b into buffer buf, lane = candidate, in three parts that go to
+  // three different warps: part 0 and 1 the YZ products of the lower and upper k half,
+  // part 2 the A products and the support box.
+  auto cand = [&](int b, int64_t& jj, int& wm) -> bool {
+    int idx = b * 32 + lane;
+    jj = 0;
+    wm = 0;
+    if (idx >= total) return false;
+    if ((idx >> 3) < nfull) idx = (int)(((int64_t)(idx >> 3) * mix) % nfull) * 8 + (idx & 7);
+    int r = 0;
+    for (int stp = top; stp > 0; stp >>= 1)
+      if (r + stp < nrange && pre[r + stp] <= idx) r += stp;
+    jj = rbeg[r] + (idx - pre[r]);
+    wm = rmeta[r];
+    return true;
+  };
+  auto stage_yz = [&](int b, int buf, auto half) {
+    constexpr int H = decltype(half)::value;
+    constexpr int KH = (N1 + 1) / 2;                       // k lines in the lower half
+    constexpr int U0 = H == 0 ? 0 : (KH * N1) / 2;         // float4 range of this half
+    constexpr int U1 = H == 0 ? (KH * N1) / 2 : YZP / 2;
+    int64_t jj;
+    int wm;
+    const bool valid = cand(b, jj, wm);
+    float4* row = reinterpret_cast<float4*>(stage + (size_t)(buf * 32 + lane) * PER);
+    float2 fy[N1], fz[N1];
+    const float2* py = G.fac + ((int64_t)win + ((wm >> 8) & 255)) * n + jj;
+    const float2* pz = G.fac + ((int64_t)2 * win + ((wm >> 16) & 255)) * n + jj;
+#pragma unroll
+    for (int i = 0; i < N1; ++i) {
+      fy[i] = valid ? py[(int64_t)i * n] : make_float2(0.0f, 0.0f);
+      const bool need = (2 * U0) / N1 <= i && i <= (2 * U1 - 1) / N1;
+      fz[i] = (valid && need) ? pz[(int64_t)i * n] : make_float2(0.0f, 0.0f);
+    }
+#pragma unroll
+    for (int u = U0; u < U1; ++u) {
+      float2 v[2];
+#pragma unroll
+      for (int h = 0; h < 2; ++h) {
+        const int q = 2 * u + h;
+        v[h] = q < N1 * N1 ? df_mul2(fy[q % N1], fz[q / N1]) : make_float2(0.0f, 0.0f);
+      }
+      row[u] = make_float4(v[0].x, v[0].y, v[1].x, v[1].y);
+    }
+  };
+  auto stage_a = [&](int b, int buf) {
+    int64_t jj;
+    int wm;
+    const bool valid = cand(b, jj, wm);
     float4* row = reinterpret_cast<float4*>(stage + (size_t)(buf * 32 + lane) * PER);
     int ylo = N1, yhi = -1, zlo = N1, zhi = -1;
     {
-      float2 fy[N1], fz[N1];
-      const float2* py = G.fac + ((int64_t)win + ((wm >> 8) & 255)) * n + jj;
-      const float2* pz = G.fac + ((int64_t)2 * win + ((wm >> 16) & 255)) * n + jj;
+      const float* py = reinterpret_cast<const float*>(G.fac + ((int64_t)win + ((wm >> 8) & 255)) * n + jj);
+      const float* pz = reinterpret_cast<const float*>(G.fac + ((int64_t)2 * win + ((wm >> 16) & 255)) * n + jj);
 #pragma unroll
       for (int i = 0; i < N1; ++i) {
-        fy[i] = valid ? py[(int64_t)i * n] : make_float2(0.0f, 0.0f);
-        fz[i] = valid ? pz[(int64_t)i * n] : make_float2(0.0f, 0.0f);
-      }
-#pragma unroll
-      for (int i = 0; i < N1; ++i) {
-        if (fy[i].x != 0.0f) {
+        const float y = valid ? py[2 * (int64_t)i * n] : 0.0f;
+        const float z = valid ? pz[2 * (int64_t)i * n] : 0.0f;
+        if (y != 0.0f) {
           ylo = min(ylo, i);
           yhi = i;
         }
-        if (fz[i].x != 0.0f) {
+        if (z != 0.0f) {
           zlo = min(zlo, i);
           zhi = i;
         }
       }
-#pragma unroll
-      for (int u = 0; u < YZP / 2; ++u) {
-        float2 v[2];
-#pragma unroll
-        for (int h = 0; h < 2; ++h) {
-          const int q = 2 * u + h;
-          v[h] = q < N1 * N1 ? df_mul2(fy[q % N1], fz[q / N1]) : make_float2(0.0f, 0.0f);
-        }
-        row[u] = make_float4(v[0].x, v[0].y, v[1].x, v[1].y);
-      }
     }
+    float2 fx[N1], qv[4];
     bool xany = false;
-    {
-      float2 fx[N1], qv[4];
-      const float2* px = G.fac + (int64_t)(wm & 255) * n + jj;
+    const float2* px = G.fac + (int64_t)(wm & 255) * n + jj;
 #pragma unroll
-      for (int i = 0; i < N1; ++i) {
-        fx[i] = valid ? px[(int64_t)i * n] : make_float2(0.0f, 0.0f);
-        xany = xany || fx[i].x != 0.0f;
+    for (int i = 0; i < N1; ++i) {
+      fx[i] = valid ? px[(int64_t)i * n] : make_float2(0.0f, 0.0f);
+      xany = xany || fx[i].x != 0.0f;
+    }
+#pragma unroll
+    for (int c = 0; c < 4; ++c) qv[c] = valid ? G.sq[(int64_t)c * n + jj] : make_float2(0.0f, 0.0f);
+#pragma unroll
+    for (int u = 0; u < 4 * TCP; ++u) {
+      float2 v[2];
+#pragma unroll
+      for (int h = 0; h < 2; ++h) {
+        const int ci = a_col<N1>(2 * u + h);
+        v[h] = ci >= 0 ? df_mul2(qv[ci / N1], fx[ci % N1]) : make_float2(0.0f, 0.0f);
       }
-#pragma unroll
-      for (int c = 0; c < 4; ++c) qv[c] = valid ? G.sq[(int64_t)c * n + jj] : make_float2(0.0f, 0.0f);
-#pragma unroll
-      for (int u = 0; u < 4 * TCP; ++u) {
-        float2 v[2];
-#pragma unroll
-        for (int h = 0; h < 2; ++h) {
-          const int ci = a_col<N1>(2 * u + h);
-          v[h] = ci >= 0 ? df_mul2(qv[ci / N1], fx[ci % N1]) : make_float2(0.0f, 0.0f);
-        }
-        row[YZP / 2 + u] = make_float4(v[0].x, v[0].y, v[1].x, v[1].y);
-      }
+      // column pairs of a group as (h0, h1, l0, l1) for the packed accumulators
+      row[YZP / 2 + u] = TCP == 1 ? make_float4(v[0].x, v[0].y, v[1].x, v[1].y)
+                                  : make_float4(v[0].x, v[1].x, v[0].y, v[1].y);
     }
     box[buf * 32 + lane] = (yhi >= 0 && zhi >= 0 && xany) ? (ylo | (yhi << 8) | (zlo << 16) | (zhi << 24)) : -1;
+  };
+  // the parts of batch b go to warps 3 b, 3 b + 1, 3 b + 2 (mod NW)
+  auto stage_parts = [&](int b) {
+    const int buf = b & 1;
+#pragma unroll
+    for (int part = 0; part < 3; ++part) {
+      if (warp != (3 * b + part) % NW) continue;
+      if (part == 0) stage_yz(b, buf, std::integral_constant<int, 0>());
+      if (part == 1) stage_yz(b, buf, std::integral_constant<int, 1>());
+      if (part == 2) stage_a(b, buf);
+    }
   };
 
   // this lane's outputs and their staged-row offsets
@@ -524,9 +594,12 @@ __global__ void __launch_bounds__(32 * BlkShape<N1>::NW, BlkShape<N1>::MINB) k_p
   const bool jk_ok = j < N1 && k < N1;
   const int jk = jk_ok ? k * N1 + j : 0;
   const int y0 = 2 * wj, z0 = 2 * wk;
-  f2 acc[TC];
+  // columns 2u, 2u + 1 of this lane in packed pairs (H, L); an odd last column in acc1
+  constexpr int NP = TC / 2;
+  float2 AH[NP > 0 ? NP : 1], AL[NP > 0 ? NP : 1];
 #pragma unroll
-  for (int t = 0; t < TC; ++t) acc[t] = {0.0f, 0.0f};
+  for (int u = 0; u < (NP > 0 ? NP : 1); ++u) AH[u] = AL[u] = make_float2(0.0f, 0.0f);
+  f2 acc1 = {0.0f, 0.0f};
   auto gemm_batch = [&](int buf) {
     const float2* sb = stage + (size_t)buf * 32 * PER;
     const int w = box[buf * 32 + lane];
@@ -538,26 +611,25 @@ __global__ void __launch_bounds__(32 * BlkShape<N1>::NW, BlkShape<N1>::MINB) k_p
       m &= m - 1;
       const float2* pq = sb + q * PER;
       const float2 bv = pq[jk];
-      float2 av[TCP];
       if constexpr (TCP == 1) {
-        av[0] = pq[YZP + g];
+        df_fma_acc(acc1, pq[YZP + g], bv);
       } else {
 #pragma unroll
         for (int u = 0; u < TCP / 2; ++u) {
           const float4 v4 = *reinterpret_cast<const float4*>(pq + a_off<N1>(g, 2 * u));
-          av[2 * u] = make_float2(v4.x, v4.y);
-          av[2 * u + 1] = make_float2(v4.z, v4.w);
+          if (2 * u + 1 < TC)
+            df_fma_acc2(AH[u], AL[u], make_float2(v4.x, v4.y), make_float2(v4.z, v4.w), bv);
+          else if (2 * u < TC)
+            df_fma_acc(acc1, make_float2(v4.x, v4.z), bv);
         }
       }
-#pragma unroll
-      for (int t = 0; t < TC; ++t) df_fma_acc(acc[t], av[t], bv);
     }
   };
 
-  if (nbatch > 0 && warp == 0) stage_batch(0, 0);
+  if (nbatch > 0) stage_parts(0);
   __syncthreads();
   for (int b = 0; b < nbatch; ++b) {
-    if (b + 1 < nbatch && warp == (b + 1) % NW) stage_batch(b + 1, (b + 1) & 1);
+    if (b + 1 < nbatch) stage_parts(b + 1);
     gemm_batch(b & 1);
     __syncthreads();
   }
@@ -568,7 +640,15 @@ __global__ void __launch_bounds__(32 * BlkShape<N1>::NW, BlkShape<N1>::MINB) k_p
       const int ci = g * TC + t;
       if (ci < 4 * N1) {
         const int c = ci / N1, i = ci - c * N1;
-        out[c * NODES + jk * N1 + i] = (double)acc[t].h + (double)acc[t].l;
+        float h, l;
+        if (TCP == 1 || t >= 2 * NP) {
+          h = acc1.h;
+          l = acc1.l;
+        } else {
+          h = (t & 1) ? AH[t / 2].y : AH[t / 2].x;
+          l = (t & 1) ? AL[t / 2].y : AL[t / 2].x;
+        }
+        out[c * NODES + jk * N1 + i] = (double)h + (double)l;
       }
     }
   }
