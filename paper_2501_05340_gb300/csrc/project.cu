@@ -353,7 +353,7 @@ struct BlkShape {
   static constexpr int PER0 = YZP + 8 * TCP;
   static constexpr int PER = (PER0 / 2) % 2 == 1 ? PER0 : PER0 + 2;
   static constexpr int MINB = NW == 1 ? 16 : (NW == 4 ? 8 : (NW == 9 ? 4 : 2));
-  static constexpr size_t SMEM = (size_t)(2 * 32 * PER) * sizeof(float2) + (size_t)(2 * 32 + 376) * sizeof(int);
+  static constexpr size_t SMEM = (size_t)(2 * 32 * PER + PER) * sizeof(float2) + (size_t)(2 * 32 + 376) * sizeof(int);
 };
 
 struct BlkArgs {
@@ -426,7 +426,8 @@ __global__ void __launch_bounds__(32 * BlkShape<N1>::NW, BlkShape<N1>::MINB) k_p
   constexpr int NODES = N1 * N1 * N1;
   extern __shared__ float4 smb4[];
   float2* stage = reinterpret_cast<float2*>(smb4);          // [2][32][PER]
-  int* box = reinterpret_cast<int*>(stage + 2 * 32 * PER);  // [2][32]: y, z support lines; -1 if not kept
+  float2* zrow = stage + 2 * 32 * PER;                      // [PER] zeros: the partner of an odd last particle
+  int* box = reinterpret_cast<int*>(zrow + PER);            // [2][32]: y, z support lines; -1 if not kept
   int* pre = box + 2 * 32;                                  // [126] prefix of the neighbour range sizes
   int* rbeg = pre + 126;                                    // [125]
   int* rmeta = rbeg + 125;                                  // [125]
@@ -435,6 +436,7 @@ __global__ void __launch_bounds__(32 * BlkShape<N1>::NW, BlkShape<N1>::MINB) k_p
   const int ne = G.ne, rho = G.rho, span = 2 * rho + 1, nrange = span * span * span, win = G.win;
   const int e = blockIdx.x;
   const int ex = e % ne, ey = (e / ne) % ne, ez = e / (ne * ne);
+  for (int t = threadIdx.x; t < PER; t += blockDim.x) zrow[t] = make_float2(0.0f, 0.0f);
   if (warp == 0) {
     int tot = 0;
     for (int r0 = 0; r0 < nrange; r0 += 32) {
@@ -606,10 +608,17 @@ __global__ void __launch_bounds__(32 * BlkShape<N1>::NW, BlkShape<N1>::MINB) k_p
     const int ylo = w & 255, yhi = (w >> 8) & 255, zlo = (w >> 16) & 255, zhi = (w >> 24) & 255;
     const bool rel = w >= 0 && ylo <= y0 + 1 && yhi >= y0 && zlo <= z0 + 1 && zhi >= z0;
     unsigned m = __ballot_sync(0xffffffffu, rel);
+    // two particles per pass; an odd last one is paired with the zero row, whose
+    // terms leave the accumulators bit for bit unchanged
     while (m) {
-      const int q = __ffs(m) - 1;
+      const float2* pr[2];
+      pr[0] = sb + (__ffs(m) - 1) * PER;
       m &= m - 1;
-      const float2* pq = sb + q * PER;
+      pr[1] = m ? sb + (__ffs(m) - 1) * PER : zrow;
+      m &= m - 1;
+#pragma unroll
+      for (int h = 0; h < 2; ++h) {
+      const float2* pq = pr[h];
       const float2 bv = pq[jk];
       if constexpr (TCP == 1) {
         df_fma_acc(acc1, pq[YZP + g], bv);
@@ -622,6 +631,7 @@ __global__ void __launch_bounds__(32 * BlkShape<N1>::NW, BlkShape<N1>::MINB) k_p
           else if (2 * u < TC)
             df_fma_acc(acc1, make_float2(v4.x, v4.z), bv);
         }
+      }
       }
     }
   };
