@@ -35,9 +35,11 @@ UNIT = "particle-steps/s"
 FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12
 # FP32 pipe: 152 SMs x 128 lanes x 2.07 GHz, operations (an FMA counts once) per second.
 FP32_PIPE_TOPS = 152 * 128 * 2.07e9 / 1e12
-# dram bytes per launch of the dominant kernel from the committed ncu capture
-# (profiles/), or None when the kernel changed since that capture.
-DEPOSIT_DRAM_BYTES = None
+# DRAM bytes (read + write) per launch of the dominant kernels at the bench workloads, from
+# the committed ncu captures (profiles/k_proj_deposit_blk_fp64.md, profiles/k_tc_deposit_mixed.md);
+# None once a kernel has changed since its capture.
+DEPOSIT_DRAM_BYTES = 753.9e6   # k_proj_deposit_blk<6>, dense_1m
+TC_DEPOSIT_DRAM_BYTES = 3.44e9  # k_tc_deposit<0>, mixed_16m
 
 
 def parse():
@@ -194,9 +196,9 @@ def run_ours(args, ws, rank, local):
         # TwoSum accumulation)
         ops = 4.0 * 12.0 * nodes
         achieved = ops / (dms / dcnt / 1e3) / 1e12
-        roofline = {"kernel": "k_proj_deposit", "bound": "alu", "achieved": achieved, "peak": FP32_PIPE_TOPS,
+        roofline = {"kernel": "k_proj_deposit_blk" if wl.degree + 1 <= 8 else "k_proj_deposit", "bound": "alu", "achieved": achieved, "peak": FP32_PIPE_TOPS,
                     "unit": "Tops/s (FP32 pipe)", "frac": achieved / FP32_PIPE_TOPS,
-                    "traffic": DEPOSIT_DRAM_BYTES,
+                    "traffic": DEPOSIT_DRAM_BYTES if wl.name == "dense_1m" else None,
                     "peak_source": "FP32 pipe: 152 SMs x 128 lanes x 2.07 GHz, one operation per lane per clock "
                                    "(derived from the recipe's unit counts)",
                     "algorithmic": "48 FP32 operations per (particle, Gauss node in its box support): %.4g per launch"
@@ -290,6 +292,7 @@ def mixed_run(args, rank, torch, pc, stream, workload="mixed_16m"):
     peak = peaks.get("bf16_tflops", 1900.0)
     out["roofline"] = {"kernel": "k_tc_deposit", "bound": "tensor", "achieved": flops / (dep_ms / 1e3) / 1e12,
                        "peak": peak, "unit": "TFLOP/s", "frac": flops / (dep_ms / 1e3) / 1e12 / peak,
+                       "traffic": TC_DEPOSIT_DRAM_BYTES if wl.name == "mixed_16m" else None,
                        "peak_source": "MEASURED_PEAKS.json bf16_tflops (fp16 has the same dense rate)",
                        "algorithmic": "2*128*64*16 flop per MMA, %d MMAs (16 kept particles each) per launch"
                                       % pairs["chunks"]}
