@@ -194,6 +194,32 @@ pc_status pc_quantize(pc_ctx* ctx, const pc_particles* in, pc_particles_f32* out
  * implementation of these rules. */
 pc_status pc_collide_f32(pc_ctx* ctx, const pc_particles_f32* in, pc_particles_f32* out, double dt);
 
+/* One mixed step with a given pair set (partner[p] = index of p's partner in the
+ * same arrays, or -1), in the order of `in`: the contact time of pc_collide_f32's
+ * search (FP64, cell units, from p's side), then the same free flight and response
+ * (arXiv 2501.05340 Sec. 2.4 with the stored-state rules of pc_collide_f32), so
+ * bit-identical to pc_collide_f32 for the pair set it chose. out's cell, o and v
+ * must be distinct from in's; r, m, id, q are copied when out's pointers differ
+ * from in's. A pair without a root in [0, dt] is recorded as PC_EREPLAY and both
+ * particles fly free. Not in the paper: the forward pass of FP32 rollouts. */
+pc_status pc_collide_replay_f32(pc_ctx* ctx, const pc_particles_f32* in, pc_particles_f32* out, const int32_t* partner,
+                                double dt);
+
+/* Vector-Jacobian product of pc_collide_replay_f32 at the pre-step state `in`, in
+ * FP32 and physical units (x = (cell + o) / nc): given device cotangents gx_out,
+ * gv_out [3][n] of the new positions and velocities, writes gx_in, gv_in [3][n]
+ * (distinct buffers) of the old ones. The storage rounding is taken as the
+ * identity; the contact time is the forward step's FP64 root, differentiated
+ * through |dx + t dv| = r_i + r_j in FP32. Not in the paper. */
+pc_status pc_collide_adjoint_f32(pc_ctx* ctx, const pc_particles_f32* in, const int32_t* partner, double dt,
+                                 const float* gx_out, const float* gv_out, float* gx_in, float* gv_in);
+
+/* Vector-Jacobian product of pc_project_f32 in FP32 (box cutoff): given
+ * G = dL/dfield (device FP32, field layout [ne^3][4][n1^3]), writes gq[4][n] =
+ * dL/dq and gx[3][n] = dL/dx (physical units) in the order of p, with the inside-
+ * cutoff decisions of the forward pass held fixed. Not in the paper. */
+pc_status pc_project_adjoint_f32(pc_ctx* ctx, const pc_particles_f32* p, const float* G, float* gq, float* gx);
+
 /* Projection of p->q (as pc_project) on the tensor cores: per element the
  * separable deposit is the dense contraction D[jk][c i] = sum_p (ky_j kz_k)(q_c kx_i),
  * each factor split into high and low parts of tc_type (FP16 or BF16), the three

@@ -314,15 +314,81 @@ struct RespondF32 {
   int32_t* id_out;
 };
 
-// Free particles: o' = o + float(dt nc) v in FP32 with a carry. Colliding pairs:
-// FP64 response (velocities physical, positions in cell units), wrap into [0, nc),
-// stored as floor + FP32 offset, velocity rounded to FP32.
+// Free flight of one axis: o' = o + float(dt nc) v in FP32 with a carry into the
+// neighbouring cell (periodic).
+__device__ __forceinline__ float advance_free_axis(float o, float va, float dtn, int nc, int* c) {
+  float on = o + dtn * va;
+  if (on >= 1.0f) {
+    on = on - 1.0f;
+    *c = *c + 1 == nc ? 0 : *c + 1;
+  } else if (on < 0.0f) {
+    const float up = on + 1.0f;
+    if (up == 1.0f) {
+      on = 0.0f;
+    } else {
+      on = up;
+      *c = *c == 0 ? nc - 1 : *c - 1;
+    }
+  }
+  return on;
+}
+
+// Response of particle i of a colliding pair (i, j) at contact time t, in cell
+// units: FP64 response from the stored values, new position wrapped into [0, nc)
+// and stored as floor + FP32 offset (carried when it rounds to 1), velocity
+// rounded to FP32. c[] holds i's cell on entry and its new cell on exit.
+__device__ __forceinline__ void respond_pair_f32(int c[3], const int cj[3], const float oi[3], const float oj[3],
+                                                 const float vi[3], const float vj[3], float mi_f, float mj_f,
+                                                 double t, double dt, double e, int nc, float oo[3], float vo[3]) {
+  const double L = (double)nc;
+  double xi[3], dx[3], dvc[3], dv[3], s3[3], nr[3];
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+    xi[a] = (double)c[a] + (double)oi[a];
+    const double xj = (double)cj[a] + (double)oj[a];
+    dx[a] = minimg_box(xi[a] - xj, L);
+    dvc[a] = (double)vi[a] * L - (double)vj[a] * L;
+    dv[a] = (double)vi[a] - (double)vj[a];
+  }
+#pragma unroll
+  for (int a = 0; a < 3; ++a) s3[a] = dx[a] + t * dvc[a];
+  const double sl = sqrt((s3[0] * s3[0] + s3[1] * s3[1]) + s3[2] * s3[2]);
+#pragma unroll
+  for (int a = 0; a < 3; ++a) nr[a] = -s3[a] / sl;
+  const double vrn = (dv[0] * nr[0] + dv[1] * nr[1]) + dv[2] * nr[2];
+  const double mi = (double)mi_f, mj = (double)mj_f;
+  const double mr = (mi * mj) / (mi + mj);
+  const double J = -mr * (1.0 + e) * vrn;
+  const double gi = J / mi;
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+    const double vold = (double)vi[a];
+    const double vnew = vold + gi * nr[a];
+    double y = (xi[a] + t * (vold * L)) + (dt - t) * (vnew * L);
+    if (y < 0.0) y += L;
+    else if (y >= L) y -= L;
+    double fl = floor(y);
+    if (fl < 0.0) fl = 0.0;
+    if (fl > (double)(nc - 1)) fl = (double)(nc - 1);
+    int cq = (int)fl;
+    float oq = (float)(y - fl);
+    if (oq >= 1.0f) {
+      oq = 0.0f;
+      cq = cq + 1 == nc ? 0 : cq + 1;
+    }
+    c[a] = cq;
+    oo[a] = oq;
+    vo[a] = (float)vnew;
+  }
+}
+
+// Free particles: advance_free_axis on each axis. Colliding pairs: respond_pair_f32
+// at the contact time found by the search.
 __global__ void k_respond_f32(RespondF32 R) {
   const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   const int64_t n = R.n;
   if (k >= n) return;
   const int nc = R.nc;
-  const double L = (double)nc;
   const int64_t p = R.perm[k];
   const int32_t j = R.partner[k];
   const float mi_f = R.m_in[p];
@@ -330,69 +396,18 @@ __global__ void k_respond_f32(RespondF32 R) {
   cell_coords(R.scell[k], nc, c);
   float oo[3], vo[3];
   if (j < 0) {
-    const float dtn = (float)(R.dt * L);
+    const float dtn = (float)(R.dt * (double)nc);
 #pragma unroll
     for (int a = 0; a < 3; ++a) {
-      const float va = R.sv[a * n + k];
-      float on = R.so[a * n + k] + dtn * va;
-      if (on >= 1.0f) {
-        on = on - 1.0f;
-        c[a] = c[a] + 1 == nc ? 0 : c[a] + 1;
-      } else if (on < 0.0f) {
-        const float up = on + 1.0f;
-        if (up == 1.0f) {
-          on = 0.0f;
-        } else {
-          on = up;
-          c[a] = c[a] == 0 ? nc - 1 : c[a] - 1;
-        }
-      }
-      oo[a] = on;
-      vo[a] = va;
+      vo[a] = R.sv[a * n + k];
+      oo[a] = advance_free_axis(R.so[a * n + k], vo[a], dtn, nc, &c[a]);
     }
   } else {
-    const double t = R.tcoll[k];
     int cj[3];
     cell_coords(R.scell[j], nc, cj);
-    double xi[3], dx[3], dvc[3], dv[3], s3[3], nr[3];
-#pragma unroll
-    for (int a = 0; a < 3; ++a) {
-      xi[a] = (double)c[a] + (double)R.so[a * n + k];
-      const double xj = (double)cj[a] + (double)R.so[a * n + j];
-      dx[a] = minimg_box(xi[a] - xj, L);
-      dvc[a] = (double)R.sv[a * n + k] * L - (double)R.sv[a * n + j] * L;
-      dv[a] = (double)R.sv[a * n + k] - (double)R.sv[a * n + j];
-    }
-#pragma unroll
-    for (int a = 0; a < 3; ++a) s3[a] = dx[a] + t * dvc[a];
-    const double sl = sqrt((s3[0] * s3[0] + s3[1] * s3[1]) + s3[2] * s3[2]);
-#pragma unroll
-    for (int a = 0; a < 3; ++a) nr[a] = -s3[a] / sl;
-    const double vrn = (dv[0] * nr[0] + dv[1] * nr[1]) + dv[2] * nr[2];
-    const double mi = (double)mi_f, mj = (double)R.m_in[R.perm[j]];
-    const double mr = (mi * mj) / (mi + mj);
-    const double J = -mr * (1.0 + R.e) * vrn;
-    const double gi = J / mi;
-#pragma unroll
-    for (int a = 0; a < 3; ++a) {
-      const double vold = (double)R.sv[a * n + k];
-      const double vnew = vold + gi * nr[a];
-      double y = (xi[a] + t * (vold * L)) + (R.dt - t) * (vnew * L);
-      if (y < 0.0) y += L;
-      else if (y >= L) y -= L;
-      double fl = floor(y);
-      if (fl < 0.0) fl = 0.0;
-      if (fl > (double)(nc - 1)) fl = (double)(nc - 1);
-      int cq = (int)fl;
-      float oq = (float)(y - fl);
-      if (oq >= 1.0f) {
-        oq = 0.0f;
-        cq = cq + 1 == nc ? 0 : cq + 1;
-      }
-      c[a] = cq;
-      oo[a] = oq;
-      vo[a] = (float)vnew;
-    }
+    const float oi[3] = {R.so[k], R.so[n + k], R.so[2 * n + k]}, oj[3] = {R.so[j], R.so[n + j], R.so[2 * n + j]};
+    const float vi[3] = {R.sv[k], R.sv[n + k], R.sv[2 * n + k]}, vj[3] = {R.sv[j], R.sv[n + j], R.sv[2 * n + j]};
+    respond_pair_f32(c, cj, oi, oj, vi, vj, mi_f, R.m_in[R.perm[j]], R.tcoll[k], R.dt, R.e, nc, oo, vo);
   }
   R.cell_out[k] = (c[2] * nc + c[1]) * nc + c[0];
 #pragma unroll
@@ -522,6 +537,316 @@ __global__ void __launch_bounds__(128) k_proj_prep_f32(PrepF32 P) {
     for (int wo = 0; wo < 2 * P.rho + 1; ++wo)
       if ((mask[a] >> (wo * P.n1)) & nmask) reach |= 1u << (8 * a + wo);
   rp[3] = make_float4(__uint_as_float(mask[2]), __uint_as_float(reach), 0.0f, 0.0f);
+}
+
+// ------------------------------------------------------------------ FP32 rollouts
+
+struct ReplayF32 {
+  int64_t n;
+  int nc;
+  double dt, e;
+  const int32_t* cell;
+  const float *o, *v, *r, *m, *q;
+  const int32_t* id;
+  const int32_t* partner;
+  int32_t* cell_out;
+  float *o_out, *v_out, *r_out, *m_out, *q_out;
+  int32_t* id_out;
+  unsigned long long* counters;
+};
+
+// Contact time of the pair (i, j) from i's side, with the arguments the search
+// forms: exact FP64 positions in cell units, v nc, (r_i + r_j) nc.
+__device__ __forceinline__ double pair_time_cells(const int ci[3], const int cj[3], const float oi[3],
+                                                  const float oj[3], const float vi[3], const float vj[3], float ri,
+                                                  float rj, double dt, int nc) {
+  const double L = (double)nc;
+  double xi[3], xj[3], vci[3], vcj[3];
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+    xi[a] = (double)ci[a] + (double)oi[a];
+    xj[a] = (double)cj[a] + (double)oj[a];
+    vci[a] = (double)vi[a] * L;
+    vcj[a] = (double)vj[a] * L;
+  }
+  return contact_time_cells(xi, xj, vci, vcj, ((double)ri + (double)rj) * L, dt, L);
+}
+
+// One mixed step with a given pair set, in the order of the arrays (partner[i] =
+// index of i's partner, or -1): the contact time of the search, then the same
+// free flight and response as k_respond_f32, hence bit-identical to
+// pc_collide_f32 for the pair set it chose.
+__global__ void k_replay_f32(ReplayF32 R) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const int64_t n = R.n;
+  if (i >= n) return;
+  const int nc = R.nc;
+  const int32_t j = R.partner[i];
+  int c[3];
+  cell_coords(R.cell[i], nc, c);
+  const float oi[3] = {R.o[i], R.o[n + i], R.o[2 * n + i]};
+  const float vi[3] = {R.v[i], R.v[n + i], R.v[2 * n + i]};
+  float oo[3], vo[3];
+  bool free_flight = j < 0;
+  if (!free_flight) {
+    int cj[3];
+    cell_coords(R.cell[j], nc, cj);
+    const float oj[3] = {R.o[j], R.o[n + j], R.o[2 * n + j]};
+    const float vj[3] = {R.v[j], R.v[n + j], R.v[2 * n + j]};
+    const double t = pair_time_cells(c, cj, oi, oj, vi, vj, R.r[i], R.r[j], R.dt, nc);
+    if (t <= R.dt) {
+      respond_pair_f32(c, cj, oi, oj, vi, vj, R.m[i], R.m[j], t, R.dt, R.e, nc, oo, vo);
+    } else {
+      raise_status(R.counters, PC_EREPLAY);
+      free_flight = true;
+    }
+  }
+  if (free_flight) {
+    const float dtn = (float)(R.dt * (double)nc);
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+      vo[a] = vi[a];
+      oo[a] = advance_free_axis(oi[a], vi[a], dtn, nc, &c[a]);
+    }
+  }
+  R.cell_out[i] = (c[2] * nc + c[1]) * nc + c[0];
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+    R.o_out[a * n + i] = oo[a];
+    R.v_out[a * n + i] = vo[a];
+  }
+  if (R.r_out) R.r_out[i] = R.r[i];
+  if (R.m_out) R.m_out[i] = R.m[i];
+  if (R.id_out) R.id_out[i] = R.id[i];
+  if (R.q_out)
+    for (int q = 0; q < 4; ++q) R.q_out[q * n + i] = R.q[q * n + i];
+}
+
+struct AdjF32 {
+  int64_t n;
+  int nc;
+  double dt, e;
+  const int32_t* cell;
+  const float *o, *v, *r, *m;
+  const int32_t* partner;
+  const float *gxo, *gvo;
+  float *gxi, *gvi;
+  unsigned long long* counters;
+};
+
+// Vector-Jacobian product of the mixed step in FP32, physical units, the pair set
+// fixed and the storage rounding taken as the identity. The contact time is the
+// FP64 root of the forward step (the value the step used); every derivative is
+// evaluated in FP32: t through |dx + t dv| = R (implicit function theorem),
+// n = -s/|s|, J = -m_r (1+e) dv.n, v' = v + (J/m) n, x' = x + t v + (dt - t) v'.
+__global__ void k_collide_adjoint_f32(AdjF32 A) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const int64_t n = A.n;
+  if (i >= n) return;
+  const int32_t j = A.partner[i];
+  const float dtf = (float)A.dt;
+  if (j < 0) {
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+      const float X = A.gxo[a * n + i];
+      A.gxi[a * n + i] = X;
+      A.gvi[a * n + i] = A.gvo[a * n + i] + dtf * X;
+    }
+    return;
+  }
+  const int nc = A.nc;
+  int ci[3], cj[3];
+  cell_coords(A.cell[i], nc, ci);
+  cell_coords(A.cell[j], nc, cj);
+  const float oi[3] = {A.o[i], A.o[n + i], A.o[2 * n + i]}, oj[3] = {A.o[j], A.o[n + j], A.o[2 * n + j]};
+  const float vi[3] = {A.v[i], A.v[n + i], A.v[2 * n + i]}, vj[3] = {A.v[j], A.v[n + j], A.v[2 * n + j]};
+  const double t64 = pair_time_cells(ci, cj, oi, oj, vi, vj, A.r[i], A.r[j], A.dt, nc);
+  if (!(t64 <= A.dt)) {
+    raise_status(A.counters, PC_EREPLAY);
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+      A.gxi[a * n + i] = 0.0f;
+      A.gvi[a * n + i] = 0.0f;
+    }
+    return;
+  }
+  const float t = (float)t64, inv_nc = 1.0f / (float)nc, Lf = (float)nc;
+  const float mi = A.m[i], mj = A.m[j];
+  float dx[3], dv[3], s[3], nr[3], vin[3], vjn[3];
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+    // cell difference wrapped to the nearest image, then the exact offset difference
+    int di = ci[a] - cj[a];
+    if (2 * di > nc) di -= nc;
+    else if (2 * di < -nc) di += nc;
+    dx[a] = minimgf_box((float)di + (oi[a] - oj[a]), Lf) * inv_nc;
+    dv[a] = vi[a] - vj[a];
+    s[a] = dx[a] + t * dv[a];
+  }
+  const float sl = sqrtf((s[0] * s[0] + s[1] * s[1]) + s[2] * s[2]);
+#pragma unroll
+  for (int a = 0; a < 3; ++a) nr[a] = -s[a] / sl;
+  const float vrn = (dv[0] * nr[0] + dv[1] * nr[1]) + dv[2] * nr[2];
+  const float mr = (mi * mj) / (mi + mj);
+  const float J = -mr * (1.0f + (float)A.e) * vrn;
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+    vin[a] = vi[a] + (J / mi) * nr[a];
+    vjn[a] = vj[a] - (J / mj) * nr[a];
+  }
+  float Vit[3], Vjt[3], gn[3] = {0.0f, 0.0f, 0.0f}, gdv[3] = {0.0f, 0.0f, 0.0f}, gdx[3] = {0.0f, 0.0f, 0.0f},
+        gvi_own[3];
+  float gt = 0.0f;
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+    const float Xi = A.gxo[a * n + i], Xj = A.gxo[a * n + j];
+    gvi_own[a] = t * Xi;
+    Vit[a] = A.gvo[a * n + i] + (dtf - t) * Xi;
+    Vjt[a] = A.gvo[a * n + j] + (dtf - t) * Xj;
+    gt += Xi * (vi[a] - vin[a]) + Xj * (vj[a] - vjn[a]);
+  }
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+    gvi_own[a] += Vit[a];
+    gn[a] += (J / mi) * Vit[a] - (J / mj) * Vjt[a];
+  }
+  const float gJ = ((Vit[0] * nr[0] + Vit[1] * nr[1]) + Vit[2] * nr[2]) / mi -
+                   ((Vjt[0] * nr[0] + Vjt[1] * nr[1]) + Vjt[2] * nr[2]) / mj;
+  const float gvrn = -mr * (1.0f + (float)A.e) * gJ;
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+    gdv[a] += gvrn * nr[a];
+    gn[a] += gvrn * dv[a];
+  }
+  const float nh[3] = {s[0] / sl, s[1] / sl, s[2] / sl};
+  const float pg = (nh[0] * gn[0] + nh[1] * gn[1]) + nh[2] * gn[2];
+  float gs[3];
+#pragma unroll
+  for (int a = 0; a < 3; ++a) gs[a] = -(gn[a] - nh[a] * pg) / sl;
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+    gdx[a] += gs[a];
+    gdv[a] += t * gs[a];
+  }
+  gt += (gs[0] * dv[0] + gs[1] * dv[1]) + gs[2] * dv[2];
+  const float sdv = (s[0] * dv[0] + s[1] * dv[1]) + s[2] * dv[2];
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+    gdx[a] += gt * (-s[a] / sdv);
+    gdv[a] += gt * (-t * s[a] / sdv);
+  }
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+    A.gxi[a * n + i] = A.gxo[a * n + i] + gdx[a];
+    A.gvi[a * n + i] = gvi_own[a] + gdv[a];
+  }
+}
+
+struct ProjAdjF32 {
+  int64_t n;
+  int nc, ne, n1, rho, win;
+  f2 rnn;             // ne / nc
+  float rce, c2l;     // cutoff in element units; h^2 / (2 sigma^2) log2(e)
+  float scale;        // (2/h)^3
+  float hs2;          // h / sigma^2
+  double h, rc;
+  float s[64];        // window node offsets in element units
+  float wq[16];
+  double eta[16];
+  const int32_t* cell;
+  const float *o, *q, *G;
+  float *gq, *gx;
+};
+
+// Vector-Jacobian product of pc_project_f32 in FP32, one warp per particle: the
+// window factors and the inside-cutoff decisions of the forward preparation, Z_a,
+// the weighted mean offsets mu_a, then a sweep over the support box reading G:
+//   gq_c = (2/h)^3 sum_g G_gc khat, gx_a = (2/h)^3 h / sigma^2 sum_g a_g khat (d_a - mu_a),
+// with d in element units, a_g = sum_c G_gc q_c and khat = kx ky kz / (Zx Zy Zz).
+__global__ void __launch_bounds__(128) k_project_adjoint_f32(ProjAdjF32 A) {
+  __shared__ float kf[4][3][64];
+  __shared__ float dd[4][3][64];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int64_t p = (int64_t)blockIdx.x * 4 + warp;
+  if (p >= A.n) return;
+  const int64_t n = A.n;
+  const int n1 = A.n1, ne = A.ne, nc = A.nc, win = A.win, nodes = n1 * n1 * n1;
+  int c[3], ea[3];
+  float t3[3];
+  cell_coords(A.cell[p], nc, c);
+#pragma unroll
+  for (int a = 0; a < 3; ++a) ea[a] = elem_of(c[a], A.o[a * n + p], A.rnn, ne, &t3[a]);
+  for (int u = lane; u < 3 * win; u += 32) {
+    const int a = u / win, w = u - a * win;
+    const float d = A.s[w] - t3[a];
+    const float ad = fabsf(d);
+    bool inside;
+    if (fabsf(ad - A.rce) > 1e-4f * A.rce) {
+      inside = ad < A.rce;
+    } else {
+      const int i = w % n1, off = w / n1 - A.rho;
+      const int ge = wrapi(ea[a] + off, ne);
+      const double x = ((double)c[a] + (double)A.o[a * n + p]) / (double)nc;
+      const double X = ((double)ge + 0.5 * (A.eta[i] + 1.0)) * A.h;
+      inside = fabs(minimg(X - x)) <= A.rc;
+    }
+    kf[warp][a][w] = inside ? exp2f(-(d * d) * A.c2l) : 0.0f;
+    dd[warp][a][w] = d;
+  }
+  __syncwarp();
+  float Z[3], mu[3];
+  int lo[3], cnt[3];
+  for (int a = 0; a < 3; ++a) {
+    float z = 0.0f, z1 = 0.0f;
+    int l = -1, hgh = -2;
+    for (int w = 0; w < win; ++w) {
+      const float k = kf[warp][a][w];
+      if (k != 0.0f) {
+        if (l < 0) l = w;
+        hgh = w;
+      }
+      z += A.wq[w % n1] * k;
+      z1 += A.wq[w % n1] * k * dd[warp][a][w];
+    }
+    Z[a] = z;
+    mu[a] = z > 0.0f ? z1 / z : 0.0f;
+    lo[a] = l < 0 ? 0 : l;
+    cnt[a] = hgh >= l ? hgh - l + 1 : 0;
+  }
+  const float q0 = A.q[p], q1 = A.q[n + p], q2 = A.q[2 * n + p], q3 = A.q[3 * n + p];
+  float aq[4] = {0.0f, 0.0f, 0.0f, 0.0f}, ax[3] = {0.0f, 0.0f, 0.0f};
+  const int nbox = cnt[0] * cnt[1] * cnt[2];
+  for (int u = lane; u < nbox; u += 32) {
+    const int wx = lo[0] + u % cnt[0];
+    const int wy = lo[1] + (u / cnt[0]) % cnt[1];
+    const int wz = lo[2] + u / (cnt[0] * cnt[1]);
+    const float kx = kf[warp][0][wx], ky = kf[warp][1][wy], kz = kf[warp][2][wz];
+    if (kx == 0.0f || ky == 0.0f || kz == 0.0f) continue;
+    const int gex = wrapi(ea[0] + wx / n1 - A.rho, ne), gey = wrapi(ea[1] + wy / n1 - A.rho, ne),
+              gez = wrapi(ea[2] + wz / n1 - A.rho, ne);
+    const int64_t e = ((int64_t)gez * ne + gey) * ne + gex;
+    const int64_t g = e * 4 * nodes + ((int64_t)(wz % n1) * n1 + (wy % n1)) * n1 + (wx % n1);
+    const float G0 = A.G[g], G1 = A.G[g + nodes], G2 = A.G[g + 2 * nodes], G3 = A.G[g + 3 * nodes];
+    const float kh = (kx * ky) * kz;
+    aq[0] += G0 * kh;
+    aq[1] += G1 * kh;
+    aq[2] += G2 * kh;
+    aq[3] += G3 * kh;
+    const float akh = (((G0 * q0 + G1 * q1) + G2 * q2) + G3 * q3) * kh;
+    ax[0] += akh * (dd[warp][0][wx] - mu[0]);
+    ax[1] += akh * (dd[warp][1][wy] - mu[1]);
+    ax[2] += akh * (dd[warp][2][wz] - mu[2]);
+  }
+  for (int o = 16; o > 0; o >>= 1) {
+    for (int k = 0; k < 4; ++k) aq[k] += __shfl_xor_sync(0xffffffffu, aq[k], o);
+    for (int a = 0; a < 3; ++a) ax[a] += __shfl_xor_sync(0xffffffffu, ax[a], o);
+  }
+  if (lane == 0) {
+    const float zz = (Z[0] * Z[1]) * Z[2];
+    const float f = zz > 0.0f ? A.scale / zz : 0.0f;
+    for (int k = 0; k < 4; ++k) A.gq[k * n + p] = aq[k] * f;
+    for (int a = 0; a < 3; ++a) A.gx[a * n + p] = ax[a] * f * A.hs2;
+  }
 }
 
 }  // namespace
@@ -700,5 +1025,108 @@ pc_status pc_project_f32_impl(pc_ctx* ctx, const pc_particles_f32* p, float* fie
   if (e == cudaSuccess) return PC_OK;
 fail:
   snprintf(ctx->err, sizeof(ctx->err), "pc_project_f32: %s", cudaGetErrorString(e));
+  return PC_ECUDA;
+}
+
+pc_status pc_collide_replay_f32_impl(pc_ctx* ctx, const pc_particles_f32* in, pc_particles_f32* out,
+                                     const int32_t* partner, double dt) {
+  const int64_t n = in->n;
+  if (n == 0) return PC_OK;
+  ReplayF32 R;
+  R.n = n;
+  R.nc = ctx->nc;
+  R.dt = dt;
+  R.e = ctx->cfg.restitution;
+  R.cell = in->cell;
+  R.o = in->o;
+  R.v = in->v;
+  R.r = in->r;
+  R.m = in->m;
+  R.q = in->q;
+  R.id = in->id;
+  R.partner = partner;
+  R.cell_out = out->cell;
+  R.o_out = out->o;
+  R.v_out = out->v;
+  R.r_out = (out->r && out->r != in->r) ? out->r : nullptr;
+  R.m_out = (out->m && out->m != in->m) ? out->m : nullptr;
+  R.id_out = (out->id && in->id && out->id != in->id) ? out->id : nullptr;
+  R.q_out = (out->q && in->q && out->q != in->q) ? out->q : nullptr;
+  R.counters = ctx->counters;
+  k_replay_f32<<<pc_blocks(n, 256), 256, 0, ctx->stream>>>(R);
+  ctx->launches += 1;
+  const cudaError_t e = cudaGetLastError();
+  if (e == cudaSuccess) return PC_OK;
+  snprintf(ctx->err, sizeof(ctx->err), "pc_collide_replay_f32: %s", cudaGetErrorString(e));
+  return PC_ECUDA;
+}
+
+pc_status pc_collide_adjoint_f32_impl(pc_ctx* ctx, const pc_particles_f32* in, const int32_t* partner, double dt,
+                                      const float* gx_out, const float* gv_out, float* gx_in, float* gv_in) {
+  const int64_t n = in->n;
+  if (n == 0) return PC_OK;
+  AdjF32 A;
+  A.n = n;
+  A.nc = ctx->nc;
+  A.dt = dt;
+  A.e = ctx->cfg.restitution;
+  A.cell = in->cell;
+  A.o = in->o;
+  A.v = in->v;
+  A.r = in->r;
+  A.m = in->m;
+  A.partner = partner;
+  A.gxo = gx_out;
+  A.gvo = gv_out;
+  A.gxi = gx_in;
+  A.gvi = gv_in;
+  A.counters = ctx->counters;
+  k_collide_adjoint_f32<<<pc_blocks(n, 256), 256, 0, ctx->stream>>>(A);
+  ctx->launches += 1;
+  const cudaError_t e = cudaGetLastError();
+  if (e == cudaSuccess) return PC_OK;
+  snprintf(ctx->err, sizeof(ctx->err), "pc_collide_adjoint_f32: %s", cudaGetErrorString(e));
+  return PC_ECUDA;
+}
+
+pc_status pc_project_adjoint_f32_impl(pc_ctx* ctx, const pc_particles_f32* p, const float* G, float* gq,
+                                      float* gx) {
+  const int64_t n = p->n;
+  if (n == 0) return PC_OK;
+  const int ne = ctx->cfg.ne;
+  const double rnn = (double)ne / (double)ctx->nc;
+  ProjAdjF32 A;
+  memset(&A, 0, sizeof(A));
+  A.n = n;
+  A.nc = ctx->nc;
+  A.ne = ne;
+  A.n1 = ctx->n1;
+  A.rho = ctx->rho;
+  A.win = ctx->win;
+  A.rnn = {(float)rnn, (float)(rnn - (double)(float)rnn)};
+  A.h = ctx->h;
+  A.rc = ctx->cfg.cutoff_sigmas * ctx->cfg.sigma;
+  A.rce = (float)(A.rc * ne);
+  A.c2l = (float)(ctx->h * ctx->h / (2.0 * ctx->cfg.sigma * ctx->cfg.sigma) * 1.4426950408889634);
+  const double s2h = 2.0 / ctx->h;
+  A.scale = (float)(s2h * s2h * s2h);
+  A.hs2 = (float)(ctx->h / (ctx->cfg.sigma * ctx->cfg.sigma));
+  for (int w = 0; w < ctx->win; ++w)
+    A.s[w] = (float)((double)(w / ctx->n1 - ctx->rho) + 0.5 * (ctx->eta[w % ctx->n1] + 1.0));
+  for (int i = 0; i < ctx->n1; ++i) {
+    A.wq[i] = (float)ctx->w[i];
+    A.eta[i] = ctx->eta[i];
+  }
+  A.cell = p->cell;
+  A.o = p->o;
+  A.q = p->q;
+  A.G = G;
+  A.gq = gq;
+  A.gx = gx;
+  k_project_adjoint_f32<<<(unsigned)((n + 3) / 4), 128, 0, ctx->stream>>>(A);
+  ctx->launches += 1;
+  const cudaError_t e = cudaGetLastError();
+  if (e == cudaSuccess) return PC_OK;
+  snprintf(ctx->err, sizeof(ctx->err), "pc_project_adjoint_f32: %s", cudaGetErrorString(e));
   return PC_ECUDA;
 }

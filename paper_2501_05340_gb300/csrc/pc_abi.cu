@@ -249,6 +249,40 @@ pc_status pc_project_f32(pc_ctx* ctx, const pc_particles_f32* p, float* field, i
   return pc_project_f32_impl(ctx, p, field, tc_type);
 }
 
+pc_status pc_collide_replay_f32(pc_ctx* ctx, const pc_particles_f32* in, pc_particles_f32* out, const int32_t* partner,
+                                double dt) {
+  if (!ctx) return PC_EINVAL;
+  if (!particles_f32_ok(in, ctx->cfg.n_max) || !particles_f32_ok(out, ctx->cfg.n_max) || in->n != out->n ||
+      (in->n > 0 && !partner))
+    return fail(ctx, PC_EINVAL, "pc_collide_replay_f32: bad arguments");
+  if (in->n > 0 && (in->cell == out->cell || in->o == out->o || in->v == out->v))
+    return fail(ctx, PC_EINVAL, "pc_collide_replay_f32: in and out cell, o, v must be distinct buffers");
+  if (!(dt > 0.0 && dt < INFINITY))
+    return fail(ctx, PC_EINVAL, "pc_collide_replay_f32: dt must be positive and finite");
+  return pc_collide_replay_f32_impl(ctx, in, out, partner, dt);
+}
+
+pc_status pc_collide_adjoint_f32(pc_ctx* ctx, const pc_particles_f32* in, const int32_t* partner, double dt,
+                                 const float* gx_out, const float* gv_out, float* gx_in, float* gv_in) {
+  if (!ctx) return PC_EINVAL;
+  if (!particles_f32_ok(in, ctx->cfg.n_max) ||
+      (in->n > 0 && (!partner || !gx_out || !gv_out || !gx_in || !gv_in)))
+    return fail(ctx, PC_EINVAL, "pc_collide_adjoint_f32: bad arguments");
+  if (in->n > 0 && (gx_in == gx_out || gv_in == gv_out || gx_in == gv_out || gv_in == gx_out))
+    return fail(ctx, PC_EINVAL, "pc_collide_adjoint_f32: input and output cotangents must be distinct buffers");
+  if (!(dt > 0.0 && dt < INFINITY))
+    return fail(ctx, PC_EINVAL, "pc_collide_adjoint_f32: dt must be positive and finite");
+  return pc_collide_adjoint_f32_impl(ctx, in, partner, dt, gx_out, gv_out, gx_in, gv_in);
+}
+
+pc_status pc_project_adjoint_f32(pc_ctx* ctx, const pc_particles_f32* p, const float* G, float* gq, float* gx) {
+  if (!ctx) return PC_EINVAL;
+  if (!particles_f32_ok(p, ctx->cfg.n_max) || (p->n > 0 && (!p->q || !G || !gq || !gx)))
+    return fail(ctx, PC_EINVAL, "pc_project_adjoint_f32: bad arguments");
+  if (ctx->cfg.cutoff_kind != 0) return fail(ctx, PC_EINVAL, "pc_project_adjoint_f32: needs the box cutoff");
+  return pc_project_adjoint_f32_impl(ctx, p, G, gq, gx);
+}
+
 pc_status pc_project_curved_f32(pc_ctx* ctx, const pc_particles_f32* p, float* field) {
   if (!ctx) return PC_EINVAL;
   if (!particles_f32_ok(p, ctx->cfg.n_max) || !field || (p->n > 0 && !p->q))

@@ -107,6 +107,12 @@ cudaError_t pc_match_launch(pc_ctx* ctx, int64_t n);
 pc_status pc_quantize_impl(pc_ctx* ctx, const pc_particles* in, pc_particles_f32* out);
 pc_status pc_collide_f32_impl(pc_ctx* ctx, const pc_particles_f32* in, pc_particles_f32* out, double dt);
 pc_status pc_project_f32_impl(pc_ctx* ctx, const pc_particles_f32* p, float* field, int tc_type);
+pc_status pc_collide_replay_f32_impl(pc_ctx* ctx, const pc_particles_f32* in, pc_particles_f32* out,
+                                     const int32_t* partner, double dt);
+pc_status pc_collide_adjoint_f32_impl(pc_ctx* ctx, const pc_particles_f32* in, const int32_t* partner, double dt,
+                                      const float* gx_out, const float* gv_out, float* gx_in, float* gv_in);
+pc_status pc_project_adjoint_f32_impl(pc_ctx* ctx, const pc_particles_f32* p, const float* G, float* gq,
+                                      float* gx);
 pc_status pc_project_curved_f32_impl(pc_ctx* ctx, const pc_particles_f32* p, float* field);
 // Tensor-core deposit over the prepared particle records (tc_deposit.cu).
 struct TcDepositArgs {

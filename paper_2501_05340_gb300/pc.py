@@ -81,7 +81,12 @@ def library():
         lib.pc_quantize.argtypes = [c_p, ctypes.POINTER(PcParticles), ctypes.POINTER(PcParticlesF32)]
         lib.pc_collide_f32.argtypes = [c_p, ctypes.POINTER(PcParticlesF32), ctypes.POINTER(PcParticlesF32), c_d]
         lib.pc_project_f32.argtypes = [c_p, ctypes.POINTER(PcParticlesF32), c_p, ctypes.c_int32]
-        for f in ("pc_quantize", "pc_collide_f32", "pc_project_f32"):
+        lib.pc_collide_replay_f32.argtypes = [c_p, ctypes.POINTER(PcParticlesF32), ctypes.POINTER(PcParticlesF32),
+                                              c_p, c_d]
+        lib.pc_collide_adjoint_f32.argtypes = [c_p, ctypes.POINTER(PcParticlesF32), c_p, c_d, c_p, c_p, c_p, c_p]
+        lib.pc_project_adjoint_f32.argtypes = [c_p, ctypes.POINTER(PcParticlesF32), c_p, c_p, c_p]
+        for f in ("pc_quantize", "pc_collide_f32", "pc_project_f32", "pc_collide_replay_f32", "pc_collide_adjoint_f32",
+                  "pc_project_adjoint_f32"):
             getattr(lib, f).restype = ctypes.c_int
         lib.pc_project_noalloc.argtypes = [ctypes.POINTER(PcConfig), ctypes.POINTER(PcParticles), c_p,
                                             ctypes.c_char_p, c_i64]
@@ -267,6 +272,21 @@ class Context:
     def collide_f32(self, src, dst, dt):
         a, b = src.struct(), dst.struct()
         self._check(library().pc_collide_f32(self._h, ctypes.byref(a), ctypes.byref(b), float(dt)))
+
+    def collide_replay_f32(self, src, dst, partner, dt):
+        """One mixed step with a fixed pair set (partner: int32 [n], index in the same order)."""
+        a, b = src.struct(), dst.struct()
+        self._check(library().pc_collide_replay_f32(self._h, ctypes.byref(a), ctypes.byref(b), _ptr(partner),
+                                                    float(dt)))
+
+    def collide_adjoint_f32(self, pre, partner, dt, gx_out, gv_out, gx_in, gv_in):
+        a = pre.struct()
+        self._check(library().pc_collide_adjoint_f32(self._h, ctypes.byref(a), _ptr(partner), float(dt),
+                                                     _ptr(gx_out), _ptr(gv_out), _ptr(gx_in), _ptr(gv_in)))
+
+    def project_adjoint_f32(self, state, G, gq, gx):
+        a = state.struct()
+        self._check(library().pc_project_adjoint_f32(self._h, ctypes.byref(a), _ptr(G), _ptr(gq), _ptr(gx)))
 
     def project_f32(self, state, field, tc="f16"):
         """FP32 field[ne^3, 4, n1^3] <- tensor-core projection (tc = "f16" or "bf16")."""
