@@ -124,14 +124,60 @@ def test_project_f32_deterministic():
     assert torch.equal(f1, f2)
 
 
-def test_project_f32_full_size_sampled():
-    """16,777,216 spheres on the 64^3 degree-7 mesh: conservation, and sampled elements
-    against the oracle run on the particles that can reach them."""
+@pytest.fixture(scope="module")
+def full16():
+    """The mixed workload at its full size (16,777,216 spheres), quantised on the GPU."""
     w = inputs.draw("mixed_16m", seed=5)
     wl = w["workload"]
     n = w["x"].shape[1]
     ctx = pc.Context(n, wl.ne, wl.degree, wl.sigma, w["e"], pc.reach_of(w["r"], w["v"], w["dt"]))
-    s32 = mixed_state(w, ctx)
+    return w, ctx, mixed_state(w, ctx)
+
+
+def test_collide_f32_full_size_sampled(full16):
+    """One step at 16,777,216 spheres. For 8 random sub-cubes of half-side 0.06 the oracle
+    runs the mixed-storage step (brute-force candidates) on the ~29,000 particles of the
+    cube; every particle in the cube's core (half-side 0.03) must have the same partner
+    and the same new cell, offsets and velocity. The 0.03 margin is ~7 collision reaches:
+    a difference caused by the cube's boundary would need a chain of 7 blocking
+    collisions to reach the core."""
+    w, ctx, s32 = full16
+    n, dt, nc = w["x"].shape[1], w["dt"], ctx.cells_per_side
+    b = pc.StateF32.empty(n)
+    ctx.collide_f32(s32, b, dt)
+    ctx.sync()
+    gids, _ = ctx.pairs()
+    gpart = np.full(n, -1, np.int64)
+    gpart[gids[:, 0]], gpart[gids[:, 1]] = gids[:, 1], gids[:, 0]
+    a = s32.numpy()  # quantised in id order
+    g = by_id(b.numpy())
+    x = oracle.dequantize(a["cell"], a["o"], nc)
+    rng = np.random.default_rng(3)
+    compared = pairs = 0
+    for _ in range(8):
+        c = rng.random(3)
+        d = np.abs((x - c[:, None] + 0.5) % 1.0 - 0.5)
+        sub = np.nonzero((d <= 0.06).all(axis=0))[0]
+        core = (d[:, sub] <= 0.03).all(axis=0)
+        cell, o, v, partner, tc, k = oracle.collide_step_cellrel(a["cell"][sub], a["o"][:, sub], a["v"][:, sub],
+                                                                 a["r"][sub], a["m"][sub], a["id"][sub], nc, w["e"], dt)
+        opart = np.where(partner >= 0, sub[np.maximum(partner, 0)], -1)
+        ids = sub[core]
+        assert np.array_equal(gpart[ids], opart[core])
+        assert np.array_equal(g["cell"][ids], cell[core])
+        assert np.array_equal(g["o"][:, ids], o[:, core]) and np.array_equal(g["v"][:, ids], v[:, core])
+        compared += len(ids)
+        pairs += int((opart[core] >= 0).sum())
+    print("full-size collide: %d core particles compared, %d of them in pairs" % (compared, pairs))
+    assert pairs > 100
+
+
+def test_project_f32_full_size_sampled(full16):
+    """16,777,216 spheres on the 64^3 degree-7 mesh: conservation, and sampled elements
+    against the oracle run on the particles that can reach them."""
+    w, ctx, s32 = full16
+    wl = w["workload"]
+    n = w["x"].shape[1]
     f = ctx.new_field_f32()
     ctx.project_f32(s32, f, "f16")
     ctx.sync()
