@@ -189,62 +189,100 @@ __device__ __forceinline__ int stencil_radius(const unsigned long long* counters
   return (int)s;
 }
 
-__device__ __forceinline__ void consider(const SearchArgs& A, int64_t k, int64_t j, const double xi[3],
-                                         const double vi[3], double ri, const float xf[3], const float vf[3],
-                                         float rf, float dtf, float vmaxf, double* lt, int* lj, int& cnt,
-                                         int& found, int& solves) {
+constexpr int kQCap = 1024;  // filter survivors queued per block
+constexpr int kMine = 8;     // survivors queued per particle (further ones are solved in place)
+
+// Exact FP64 contact time of the pair (k, j) of the sorted arrays.
+__device__ __forceinline__ double solve_pair(const SearchArgs& A, int64_t k, int64_t j) {
   const int64_t n = A.n;
-  float dxf[3], dvf[3];
-#pragma unroll
-  for (int a = 0; a < 3; ++a) {
-    dxf[a] = minimgf(xf[a] - A.sxf[a * n + j]);
-    dvf[a] = vf[a] - A.svf[a * n + j];
-  }
-  if (!filter_keep(dxf, dvf, rf + A.srf[j], dtf, vmaxf)) return;
-  ++solves;
+  const double xi[3] = {A.sx[k], A.sx[n + k], A.sx[2 * n + k]};
+  const double vi[3] = {A.sv[k], A.sv[n + k], A.sv[2 * n + k]};
   const double xj[3] = {A.sx[j], A.sx[n + j], A.sx[2 * n + j]};
   const double vj[3] = {A.sv[j], A.sv[n + j], A.sv[2 * n + j]};
-  const double t = contact_time_exact(xi, xj, vi, vj, ri + A.sr[j], A.dt);
-  if (!(t <= A.dt)) return;
-  ++found;
-  const int jid = A.sid[j];
-  // insertion into the list sorted by (t, id), keeping the cap best
+  return contact_time_exact(xi, xj, vi, vj, A.sr[k] + A.sr[j], A.dt);
+}
+
+// Insertion into a list sorted by (t, id), keeping the cap first.
+__device__ __forceinline__ void insert_sorted(double* lt, int* lj, int& cnt, int cap, double t, int j,
+                                              const int32_t* sid) {
+  const int jid = sid[j];
   int pos = cnt;
-  while (pos > 0 && (lt[pos - 1] > t || (lt[pos - 1] == t && A.sid[lj[pos - 1]] > jid))) --pos;
-  if (pos >= A.cap) return;
-  int last = cnt < A.cap ? cnt : A.cap - 1;
+  while (pos > 0 && (lt[pos - 1] > t || (lt[pos - 1] == t && sid[lj[pos - 1]] > jid))) --pos;
+  if (pos >= cap) return;
+  const int last = cnt < cap ? cnt : cap - 1;
   for (int q = last; q > pos; --q) {
     lt[q] = lt[q - 1];
     lj[q] = lj[q - 1];
   }
   lt[pos] = t;
-  lj[pos] = (int)j;
-  if (cnt < A.cap) ++cnt;
+  lj[pos] = j;
+  if (cnt < cap) ++cnt;
 }
 
+// Thread per particle (sorted by cell). The certified FP32 filter runs over the
+// stencil (each row of cells along x as one range when it does not wrap); its
+// survivors are queued per block and solved in FP64 by all of the block's threads
+// together, then each particle inserts its own roots into its list sorted by
+// (t, id). On this GPU an FP64 instruction takes a warp 64 pipe cycles whatever
+// the number of active lanes, so solving a block's survivors densely instead of in
+// each diverged warp removes most of the FP64 time. The insertion does not depend
+// on the order of the roots.
 __global__ void __launch_bounds__(256) k_search(SearchArgs A) {
   const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   const int64_t n = A.n;
-  double reach;
-  const int s = stencil_radius(A.counters, A.nc, A.dt, &reach);
-  if (k == 0) {
-    atomicMax(&A.counters[CNT_STENCIL], (unsigned long long)s);
-    if (!(reach < 0.5)) raise_status(A.counters, PC_EINVAL);
+  // stencil radius and speed bound from the step's maxima, once per block
+  __shared__ int s_sh;
+  __shared__ float vmaxf_sh;
+  __shared__ int q_cnt;
+  __shared__ int q_own[kQCap], q_j[kQCap];
+  __shared__ double q_t[kQCap];
+  if (threadIdx.x == 0) {
+    double reach;
+    s_sh = stencil_radius(A.counters, A.nc, A.dt, &reach);
+    vmaxf_sh = (float)sqrt(__longlong_as_double((long long)A.counters[CNT_VMAX2])) * 1.000001f;
+    q_cnt = 0;
+    if (blockIdx.x == 0) {
+      atomicMax(&A.counters[CNT_STENCIL], (unsigned long long)s_sh);
+      if (!(reach < 0.5)) raise_status(A.counters, PC_EINVAL);
+    }
   }
+  __syncthreads();
+  const int s = s_sh;
   int found = 0, solves = 0, cnt = 0;
+  double lt[kMaxCap];
+  int lj[kMaxCap];
+  int mine[kMine];
+  int nmine = 0;
   if (k < n) {
-    double lt[kMaxCap];
-    int lj[kMaxCap];
-    const double xi[3] = {A.sx[k], A.sx[n + k], A.sx[2 * n + k]};
-    const double vi[3] = {A.sv[k], A.sv[n + k], A.sv[2 * n + k]};
-    const double ri = A.sr[k];
     const float xf[3] = {A.sxf[k], A.sxf[n + k], A.sxf[2 * n + k]};
     const float vf[3] = {A.svf[k], A.svf[n + k], A.svf[2 * n + k]};
     const float rf = A.srf[k];
     const float dtf = (float)A.dt * 1.000001f;
-    const float vmaxf = (float)sqrt(__longlong_as_double((long long)A.counters[CNT_VMAX2])) * 1.000001f;
+    const float vmaxf = vmaxf_sh;
     const int nc = A.nc;
-    const int cx = cell_of(xi[0], nc), cy = cell_of(xi[1], nc), cz = cell_of(xi[2], nc);
+    const int cx = cell_of(A.sx[k], nc), cy = cell_of(A.sx[n + k], nc), cz = cell_of(A.sx[2 * n + k], nc);
+    auto visit = [&](int64_t j) {
+      float dxf[3], dvf[3];
+#pragma unroll
+      for (int a = 0; a < 3; ++a) {
+        dxf[a] = minimgf(xf[a] - A.sxf[a * n + j]);
+        dvf[a] = vf[a] - A.svf[a * n + j];
+      }
+      if (!filter_keep(dxf, dvf, rf + A.srf[j], dtf, vmaxf)) return;
+      const int slot = nmine < kMine ? atomicAdd(&q_cnt, 1) : kQCap;
+      if (slot < kQCap) {
+        q_own[slot] = threadIdx.x;
+        q_j[slot] = (int)j;
+        mine[nmine++] = slot;
+      } else {
+        ++solves;
+        const double t = solve_pair(A, k, j);
+        if (t <= A.dt) {
+          ++found;
+          insert_sorted(lt, lj, cnt, A.cap, t, (int)j, A.sid);
+        }
+      }
+    };
     const int span = 2 * s + 1;
     const bool full = span >= nc;  // the stencil covers the whole axis: visit every cell once
     const int cnt_ax = full ? nc : span;
@@ -256,15 +294,32 @@ __global__ void __launch_bounds__(256) k_search(SearchArgs A) {
         if (!full && cx - s >= 0 && cx + s < nc) {
           const int beg = A.start[row + cx - s], end = A.start[row + cx + s + 1];
           for (int j = beg; j < end; ++j)
-            if (j != k) consider(A, k, j, xi, vi, ri, xf, vf, rf, dtf, vmaxf, lt, lj, cnt, found, solves);
+            if (j != k) visit(j);
         } else {
           for (int ox = 0; ox < cnt_ax; ++ox) {
             const int xc = full ? ox : wrapi(cx - s + ox, nc);
             const int beg = A.start[row + xc], end = A.start[row + xc + 1];
             for (int j = beg; j < end; ++j)
-              if (j != k) consider(A, k, j, xi, vi, ri, xf, vf, rf, dtf, vmaxf, lt, lj, cnt, found, solves);
+              if (j != k) visit(j);
           }
         }
+      }
+    }
+  }
+  __syncthreads();
+  const int total = q_cnt < kQCap ? q_cnt : kQCap;
+  const int64_t kb = (int64_t)blockIdx.x * blockDim.x;
+  for (int e = threadIdx.x; e < total; e += blockDim.x) {
+    q_t[e] = solve_pair(A, kb + q_own[e], q_j[e]);
+    ++solves;
+  }
+  __syncthreads();
+  if (k < n) {
+    for (int i = 0; i < nmine; ++i) {
+      const double t = q_t[mine[i]];
+      if (t <= A.dt) {
+        ++found;
+        insert_sorted(lt, lj, cnt, A.cap, t, q_j[mine[i]], A.sid);
       }
     }
     for (int q = 0; q < cnt; ++q) {

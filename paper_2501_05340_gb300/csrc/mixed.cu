@@ -193,22 +193,36 @@ __device__ __forceinline__ bool filter_cells(const float dxf[3], const float dvc
   return !(bf > bslack);
 }
 
-__global__ void __launch_bounds__(256) k_search_f32(SearchF32 A) {
+// Thread per particle (sorted by cell). The stencil is taken row by row; a row of
+// 2 s + 1 cells along x that does not wrap is one contiguous range of the sorted
+// arrays, walked with the x cell advanced at the cell starts. Each candidate goes
+// through the certified FP32 filter, survivors through the exact FP64 root in cell
+// units, and roots in [0, dt] into the particle's list sorted by (t, id).
+__global__ void __launch_bounds__(256, 3) k_search_f32(SearchF32 A) {
   const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   const int64_t n = A.n;
   const int nc = A.nc;
   const double L = (double)nc;
   const float Lf = (float)nc;
-  const double v2max = __longlong_as_double((long long)A.counters[CNT_VMAX2]);
-  const double rmax = __longlong_as_double((long long)A.counters[CNT_RMAX]);
-  const double reach = (2.0 * rmax + 2.0 * sqrt(v2max) * A.dt) * (1.0 + 1e-9) + 1e-12;  // box units
-  double sd = floor(reach * L * (1.0 + 1e-9)) + 1.0;
-  if (sd > L) sd = L;
-  const int s = (int)sd;
-  if (k == 0) {
-    atomicMax(&A.counters[CNT_STENCIL], (unsigned long long)s);
-    if (!(reach < 0.5)) raise_status(A.counters, PC_EINVAL);
+  // stencil radius and speed bound from the step's maxima, once per block (FP64 is
+  // 1/64 of the FP32 rate on this GPU)
+  __shared__ int s_sh;
+  __shared__ float vmaxc_sh;
+  if (threadIdx.x == 0) {
+    const double v2max = __longlong_as_double((long long)A.counters[CNT_VMAX2]);
+    const double rmax = __longlong_as_double((long long)A.counters[CNT_RMAX]);
+    const double reach = (2.0 * rmax + 2.0 * sqrt(v2max) * A.dt) * (1.0 + 1e-9) + 1e-12;  // box units
+    double sd = floor(reach * L * (1.0 + 1e-9)) + 1.0;
+    if (sd > L) sd = L;
+    s_sh = (int)sd;
+    vmaxc_sh = (float)(sqrt(v2max) * L) * 1.000001f;
+    if (blockIdx.x == 0) {
+      atomicMax(&A.counters[CNT_STENCIL], (unsigned long long)s_sh);
+      if (!(reach < 0.5)) raise_status(A.counters, PC_EINVAL);
+    }
   }
+  __syncthreads();
+  const int s = s_sh;
   int found = 0, solves = 0, cnt = 0;
   if (k < n) {
     double lt[kMaxCap];
@@ -219,56 +233,70 @@ __global__ void __launch_bounds__(256) k_search_f32(SearchF32 A) {
     const float vk3[3] = {A.sv[k], A.sv[n + k], A.sv[2 * n + k]};
     const float rk = A.sr[k];
     const float dtf = (float)A.dt * 1.000001f;
-    const float vmaxc = (float)(sqrt(v2max) * L) * 1.000001f;
+    const float vmaxc = vmaxc_sh;
+    // candidate j in cell (xc, yc, zc)
+    auto visit = [&](int j, int xc, int yc, int zc) {
+      const int cj[3] = {xc, yc, zc};
+      float dxf[3], dvc[3];
+#pragma unroll
+      for (int a = 0; a < 3; ++a) {
+        int di = ck[a] - cj[a];
+        if (2 * di > nc) di -= nc;
+        else if (2 * di < -nc) di += nc;
+        dxf[a] = minimgf_box((float)di + (ok3[a] - A.so[a * n + j]), Lf);
+        dvc[a] = (vk3[a] - A.sv[a * n + j]) * Lf;
+      }
+      if (!filter_cells(dxf, dvc, (rk + A.sr[j]) * Lf, dtf, vmaxc)) return;
+      ++solves;
+      double xi[3], xj[3], vi[3], vj[3];
+#pragma unroll
+      for (int a = 0; a < 3; ++a) {
+        xi[a] = (double)ck[a] + (double)ok3[a];
+        xj[a] = (double)cj[a] + (double)A.so[a * n + j];
+        vi[a] = (double)vk3[a] * L;
+        vj[a] = (double)A.sv[a * n + j] * L;
+      }
+      const double R = ((double)rk + (double)A.sr[j]) * L;
+      const double t = contact_time_cells(xi, xj, vi, vj, R, A.dt, L);
+      if (!(t <= A.dt)) return;
+      ++found;
+      const int jid = A.sid[j];
+      int pos = cnt;
+      while (pos > 0 && (lt[pos - 1] > t || (lt[pos - 1] == t && A.sid[lj[pos - 1]] > jid))) --pos;
+      if (pos >= A.cap) return;
+      const int last = cnt < A.cap ? cnt : A.cap - 1;
+      for (int q = last; q > pos; --q) {
+        lt[q] = lt[q - 1];
+        lj[q] = lj[q - 1];
+      }
+      lt[pos] = t;
+      lj[pos] = j;
+      if (cnt < A.cap) ++cnt;
+    };
     const int span = 2 * s + 1;
     const bool full = span >= nc;
     const int cnt_ax = full ? nc : span;
+    const bool row_range = !full && ck[0] - s >= 0 && ck[0] + s < nc;
     for (int oz = 0; oz < cnt_ax; ++oz) {
       const int zc = full ? oz : wrapi(ck[2] - s + oz, nc);
       for (int oy = 0; oy < cnt_ax; ++oy) {
         const int yc = full ? oy : wrapi(ck[1] - s + oy, nc);
-        for (int ox = 0; ox < cnt_ax; ++ox) {
-          const int xc = full ? ox : wrapi(ck[0] - s + ox, nc);
-          const int cj[3] = {xc, yc, zc};
-          const int64_t cl = ((int64_t)zc * nc + yc) * nc + xc;
-          const int beg = A.start[cl], end = A.start[cl + 1];
-          for (int j = beg; j < end; ++j) {
-            if (j == k) continue;
-            float dxf[3], dvc[3];
-#pragma unroll
-            for (int a = 0; a < 3; ++a) {
-              int di = ck[a] - cj[a];
-              if (2 * di > nc) di -= nc;
-              else if (2 * di < -nc) di += nc;
-              dxf[a] = minimgf_box((float)di + (ok3[a] - A.so[a * n + j]), Lf);
-              dvc[a] = (vk3[a] - A.sv[a * n + j]) * Lf;
-            }
-            if (!filter_cells(dxf, dvc, (rk + A.sr[j]) * Lf, dtf, vmaxc)) continue;
-            ++solves;
-            double xi[3], xj[3], vi[3], vj[3];
-#pragma unroll
-            for (int a = 0; a < 3; ++a) {
-              xi[a] = (double)ck[a] + (double)ok3[a];
-              xj[a] = (double)cj[a] + (double)A.so[a * n + j];
-              vi[a] = (double)vk3[a] * L;
-              vj[a] = (double)A.sv[a * n + j] * L;
-            }
-            const double R = ((double)rk + (double)A.sr[j]) * L;
-            const double t = contact_time_cells(xi, xj, vi, vj, R, A.dt, L);
-            if (!(t <= A.dt)) continue;
-            ++found;
-            const int jid = A.sid[j];
-            int pos = cnt;
-            while (pos > 0 && (lt[pos - 1] > t || (lt[pos - 1] == t && A.sid[lj[pos - 1]] > jid))) --pos;
-            if (pos >= A.cap) continue;
-            const int last = cnt < A.cap ? cnt : A.cap - 1;
-            for (int q = last; q > pos; --q) {
-              lt[q] = lt[q - 1];
-              lj[q] = lj[q - 1];
-            }
-            lt[pos] = t;
-            lj[pos] = j;
-            if (cnt < A.cap) ++cnt;
+        const int64_t row = ((int64_t)zc * nc + yc) * nc;
+        if (row_range) {
+          int xc = ck[0] - s;
+          int next = A.start[row + xc + 1];
+          const int end = A.start[row + ck[0] + s + 1];
+          for (int j = A.start[row + xc]; j < end; ++j) {
+            while (j >= next) next = A.start[row + (++xc) + 1];
+            if (j != k) visit(j, xc, yc, zc);
+          }
+        } else {
+          for (int ox = 0; ox < cnt_ax; ++ox) {
+            const int xc = full ? ox : wrapi(ck[0] - s + ox, nc);
+            const int64_t cl = row + xc;
+            const int beg = A.start[cl], end = A.start[cl + 1];
+            for (int j = beg; j < end; ++j)
+              if (j != k) visit(j, xc, yc, zc);
           }
         }
       }
