@@ -193,22 +193,66 @@ __device__ __forceinline__ bool filter_cells(const float dxf[3], const float dvc
   return !(bf > bslack);
 }
 
+constexpr int kPend = 8;  // filter survivors deferred per particle (further ones are solved in place)
+
+// FP64 root of the pair (k, j) in cell units, with the arguments the step defines.
+__device__ __forceinline__ double solve_cells(const SearchF32& A, int64_t k, int64_t j) {
+  const int64_t n = A.n;
+  const int nc = A.nc;
+  const double L = (double)nc;
+  int ck[3], cj[3];
+  cell_coords(A.scell[k], nc, ck);
+  cell_coords(A.scell[j], nc, cj);
+  double xi[3], xj[3], vi[3], vj[3];
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+    xi[a] = (double)ck[a] + (double)A.so[a * n + k];
+    xj[a] = (double)cj[a] + (double)A.so[a * n + j];
+    vi[a] = (double)A.sv[a * n + k] * L;
+    vj[a] = (double)A.sv[a * n + j] * L;
+  }
+  return contact_time_cells(xi, xj, vi, vj, ((double)A.sr[k] + (double)A.sr[j]) * L, A.dt, L);
+}
+
+// Insertion into a list sorted by (t, id), keeping the cap first.
+__device__ __forceinline__ void insert_sorted(double* lt, int* lj, int& cnt, int cap, double t, int j,
+                                              const int32_t* sid) {
+  const int jid = sid[j];
+  int pos = cnt;
+  while (pos > 0 && (lt[pos - 1] > t || (lt[pos - 1] == t && sid[lj[pos - 1]] > jid))) --pos;
+  if (pos >= cap) return;
+  const int last = cnt < cap ? cnt : cap - 1;
+  for (int q = last; q > pos; --q) {
+    lt[q] = lt[q - 1];
+    lj[q] = lj[q - 1];
+  }
+  lt[pos] = t;
+  lj[pos] = j;
+  if (cnt < cap) ++cnt;
+}
+
 // Thread per particle (sorted by cell). The stencil is taken row by row; a row of
 // 2 s + 1 cells along x that does not wrap is one contiguous range of the sorted
 // arrays, walked with the x cell advanced at the cell starts. Each candidate goes
-// through the certified FP32 filter, survivors through the exact FP64 root in cell
-// units, and roots in [0, dt] into the particle's list sorted by (t, id).
+// through the certified FP32 filter. The survivors are solved exactly in FP64
+// after the warp's filter loops, by the warp's lanes together: on this GPU an FP64
+// instruction takes a warp 64 pipe cycles whatever the number of active lanes, so
+// a warp's few survivors cost one pass instead of one per survivor. Roots in
+// [0, dt] go into the particle's list sorted by (t, id), independent of order.
 __global__ void __launch_bounds__(256, 3) k_search_f32(SearchF32 A) {
   const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   const int64_t n = A.n;
   const int nc = A.nc;
-  const double L = (double)nc;
   const float Lf = (float)nc;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   // stencil radius and speed bound from the step's maxima, once per block (FP64 is
   // 1/64 of the FP32 rate on this GPU)
   __shared__ int s_sh;
-  __shared__ float vmaxc_sh;
+  __shared__ float vmaxc_sh, rmaxc_sh;
+  __shared__ int q_own[8][32 * kPend], q_j[8][32 * kPend];
+  __shared__ double q_t[8][32 * kPend];
   if (threadIdx.x == 0) {
+    const double L = (double)nc;
     const double v2max = __longlong_as_double((long long)A.counters[CNT_VMAX2]);
     const double rmax = __longlong_as_double((long long)A.counters[CNT_RMAX]);
     const double reach = (2.0 * rmax + 2.0 * sqrt(v2max) * A.dt) * (1.0 + 1e-9) + 1e-12;  // box units
@@ -216,6 +260,7 @@ __global__ void __launch_bounds__(256, 3) k_search_f32(SearchF32 A) {
     if (sd > L) sd = L;
     s_sh = (int)sd;
     vmaxc_sh = (float)(sqrt(v2max) * L) * 1.000001f;
+    rmaxc_sh = (float)(rmax * L) * 1.000001f;
     if (blockIdx.x == 0) {
       atomicMax(&A.counters[CNT_STENCIL], (unsigned long long)s_sh);
       if (!(reach < 0.5)) raise_status(A.counters, PC_EINVAL);
@@ -224,9 +269,11 @@ __global__ void __launch_bounds__(256, 3) k_search_f32(SearchF32 A) {
   __syncthreads();
   const int s = s_sh;
   int found = 0, solves = 0, cnt = 0;
+  double lt[kMaxCap];
+  int lj[kMaxCap];
+  int pend[kPend];
+  int npend = 0;
   if (k < n) {
-    double lt[kMaxCap];
-    int lj[kMaxCap];
     int ck[3];
     cell_coords(A.scell[k], nc, ck);
     const float ok3[3] = {A.so[k], A.so[n + k], A.so[2 * n + k]};
@@ -234,6 +281,12 @@ __global__ void __launch_bounds__(256, 3) k_search_f32(SearchF32 A) {
     const float rk = A.sr[k];
     const float dtf = (float)A.dt * 1.000001f;
     const float vmaxc = vmaxc_sh;
+    // A reach no pair of this particle exceeds in filter_cells: (r_k + r_max) nc and
+    // (|v_k| nc + vmaxc) for the radius sum and the speed, with margins. Beyond it
+    // filter_cells rejects, so those candidates skip their velocity and radius loads.
+    const float vkc = sqrtf(vk3[0] * vk3[0] + vk3[1] * vk3[1] + vk3[2] * vk3[2]) * Lf * 1.000001f;
+    const float rhi = ((rk * Lf + rmaxc_sh) + (vkc + vmaxc) * dtf) * 1.00002f + 8.0e-7f + 2.5e-7f * vmaxc * dtf;
+    const float rl2 = rhi * rhi * 1.0001f;
     // candidate j in cell (xc, yc, zc)
     auto visit = [&](int j, int xc, int yc, int zc) {
       const int cj[3] = {xc, yc, zc};
@@ -244,34 +297,21 @@ __global__ void __launch_bounds__(256, 3) k_search_f32(SearchF32 A) {
         if (2 * di > nc) di -= nc;
         else if (2 * di < -nc) di += nc;
         dxf[a] = minimgf_box((float)di + (ok3[a] - A.so[a * n + j]), Lf);
-        dvc[a] = (vk3[a] - A.sv[a * n + j]) * Lf;
       }
-      if (!filter_cells(dxf, dvc, (rk + A.sr[j]) * Lf, dtf, vmaxc)) return;
-      ++solves;
-      double xi[3], xj[3], vi[3], vj[3];
+      if (dxf[0] * dxf[0] + dxf[1] * dxf[1] + dxf[2] * dxf[2] > rl2) return;
 #pragma unroll
-      for (int a = 0; a < 3; ++a) {
-        xi[a] = (double)ck[a] + (double)ok3[a];
-        xj[a] = (double)cj[a] + (double)A.so[a * n + j];
-        vi[a] = (double)vk3[a] * L;
-        vj[a] = (double)A.sv[a * n + j] * L;
+      for (int a = 0; a < 3; ++a) dvc[a] = (vk3[a] - A.sv[a * n + j]) * Lf;
+      if (!filter_cells(dxf, dvc, (rk + A.sr[j]) * Lf, dtf, vmaxc)) return;
+      if (npend < kPend) {
+        pend[npend++] = j;
+      } else {
+        ++solves;
+        const double t = solve_cells(A, k, j);
+        if (t <= A.dt) {
+          ++found;
+          insert_sorted(lt, lj, cnt, A.cap, t, j, A.sid);
+        }
       }
-      const double R = ((double)rk + (double)A.sr[j]) * L;
-      const double t = contact_time_cells(xi, xj, vi, vj, R, A.dt, L);
-      if (!(t <= A.dt)) return;
-      ++found;
-      const int jid = A.sid[j];
-      int pos = cnt;
-      while (pos > 0 && (lt[pos - 1] > t || (lt[pos - 1] == t && A.sid[lj[pos - 1]] > jid))) --pos;
-      if (pos >= A.cap) return;
-      const int last = cnt < A.cap ? cnt : A.cap - 1;
-      for (int q = last; q > pos; --q) {
-        lt[q] = lt[q - 1];
-        lj[q] = lj[q - 1];
-      }
-      lt[pos] = t;
-      lj[pos] = j;
-      if (cnt < A.cap) ++cnt;
     };
     const int span = 2 * s + 1;
     const bool full = span >= nc;
@@ -299,6 +339,35 @@ __global__ void __launch_bounds__(256, 3) k_search_f32(SearchF32 A) {
               if (j != k) visit(j, xc, yc, zc);
           }
         }
+      }
+    }
+  }
+  // the warp's deferred survivors, solved by its lanes together
+  int off = npend;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const int y = __shfl_up_sync(0xffffffffu, off, o);
+    if (lane >= o) off += y;
+  }
+  const int wtotal = __shfl_sync(0xffffffffu, off, 31);
+  off -= npend;
+  for (int i = 0; i < npend; ++i) {
+    q_own[warp][off + i] = lane;
+    q_j[warp][off + i] = pend[i];
+  }
+  __syncwarp();
+  const int64_t kw = (int64_t)blockIdx.x * blockDim.x + 32 * warp;
+  for (int e = lane; e < wtotal; e += 32) {
+    q_t[warp][e] = solve_cells(A, kw + q_own[warp][e], q_j[warp][e]);
+    ++solves;
+  }
+  __syncwarp();
+  if (k < n) {
+    for (int i = 0; i < npend; ++i) {
+      const double t = q_t[warp][off + i];
+      if (t <= A.dt) {
+        ++found;
+        insert_sorted(lt, lj, cnt, A.cap, t, pend[i], A.sid);
       }
     }
     for (int q = 0; q < cnt; ++q) {
