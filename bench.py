@@ -124,6 +124,16 @@ class ClockSampler:
                 "reasons": reasons, "samples": len(rows)}
 
 
+def max_over_ranks(x, dist, device="cuda"):
+    """The maximum of x over the ranks of the process group (x itself without one)."""
+    if not dist:
+        return x
+    import torch
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
 def run_ours(args, ws, rank, local):
     import torch
 
@@ -178,11 +188,7 @@ def run_ours(args, ws, rank, local):
     launches = st["kernel_launches"] - l0
     if st["status"] != 0:
         raise RuntimeError("device status %d during the timed region" % st["status"])
-    t_max = ms
-    if dist:
-        t = torch.tensor([ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        t_max = float(t.item())
+    t_max = max_over_ranks(ms, dist)
     value = n * args.steps * ws / (t_max / 1e3)
 
     # dominant kernel and its roofline
@@ -385,11 +391,7 @@ def e2e_run(args, ctx, w, n, dt, stream, torch, pc, dist, ws):
     for _ in range(args.steps):
         step()
     stream.synchronize()
-    el = time.perf_counter() - t0
-    if dist:
-        t = torch.tensor([el], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        el = float(t.item())
+    el = max_over_ranks(time.perf_counter() - t0, dist)
     return {"value": n * args.steps * ws / el, "unit": UNIT, "h2d_bytes_per_step": int(h2d),
             "d2h_bytes_per_step": int(d2h)}
 
