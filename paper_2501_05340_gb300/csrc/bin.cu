@@ -91,22 +91,84 @@ __global__ void k_bin_scatter(int64_t n, const int32_t* __restrict__ key, const 
   if (i < n) perm[start[key[i]] + slot[i]] = (int32_t)i;
 }
 
-// Insertion sort of each bin's entries by particle id (bins hold a few particles).
-__global__ void k_bin_order(int64_t nbins, const int32_t* __restrict__ start, const int32_t* __restrict__ id,
-                            int32_t* __restrict__ perm) {
-  int64_t b = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (b >= nbins) return;
-  const int beg = start[b], end = start[b + 1];
-  if (end - beg < 2) return;
-  for (int a = beg + 1; a < end; ++a) {
-    const int32_t p = perm[a];
-    const int32_t pid = id[p];
-    int c = a - 1;
-    while (c >= beg && id[perm[c]] > pid) {
-      perm[c + 1] = perm[c];
-      --c;
+constexpr int kSmallBin = 16;   // a bin of at most this many is sorted by one lane
+constexpr int kWarpBin = 256;   // a larger bin up to this many is ranked by the warp (8 per lane)
+
+// Each bin's entries ordered by particle id (ids are distinct). A warp takes 32
+// consecutive bins: every lane sorts its own bin when it holds at most kSmallBin
+// entries (in registers), then the warp ranks each larger bin together: every
+// entry counts the entries of its bin with a smaller id and is written to that
+// position. Bins beyond kWarpBin are sorted by insertion by one lane.
+__global__ void __launch_bounds__(256) k_bin_order(int64_t nbins, const int32_t* __restrict__ start,
+                                                   const int32_t* __restrict__ id, int32_t* __restrict__ perm) {
+  const int64_t b = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const int lane = threadIdx.x & 31;
+  int beg = 0, m = 0;
+  if (b < nbins) {
+    beg = start[b];
+    m = start[b + 1] - beg;
+  }
+  if (m >= 2 && m <= kSmallBin) {
+    int32_t p[kSmallBin], key[kSmallBin];
+#pragma unroll
+    for (int a = 0; a < kSmallBin; ++a)
+      if (a < m) {
+        p[a] = perm[beg + a];
+        key[a] = id[p[a]];
+      }
+#pragma unroll
+    for (int a = 0; a < kSmallBin; ++a) {
+      if (a >= m) break;
+      int r = 0;
+#pragma unroll
+      for (int c = 0; c < kSmallBin; ++c)
+        if (c < m && key[c] < key[a]) ++r;
+      perm[beg + r] = p[a];
     }
-    perm[c + 1] = p;
+  }
+  unsigned big = __ballot_sync(0xffffffffu, m > kSmallBin);
+  while (big) {
+    const int src = __ffs(big) - 1;
+    big &= big - 1;
+    const int bb = __shfl_sync(0xffffffffu, beg, src), bm = __shfl_sync(0xffffffffu, m, src);
+    if (bm <= kWarpBin) {
+      int32_t p[kWarpBin / 32], key[kWarpBin / 32];
+#pragma unroll
+      for (int u = 0; u < kWarpBin / 32; ++u) {
+        const int a = lane + 32 * u;
+        p[u] = a < bm ? perm[bb + a] : 0;
+        key[u] = a < bm ? id[p[u]] : 0x7fffffff;
+      }
+      int rank[kWarpBin / 32];
+#pragma unroll
+      for (int u = 0; u < kWarpBin / 32; ++u) rank[u] = 0;
+#pragma unroll
+      for (int u2 = 0; u2 < kWarpBin / 32; ++u2) {
+        if (32 * u2 >= bm) break;
+        for (int sft = 0; sft < 32; ++sft) {
+          const int other = __shfl_sync(0xffffffffu, key[u2], sft);
+#pragma unroll
+          for (int u = 0; u < kWarpBin / 32; ++u) rank[u] += other < key[u] ? 1 : 0;
+        }
+      }
+      __syncwarp();
+#pragma unroll
+      for (int u = 0; u < kWarpBin / 32; ++u)
+        if (lane + 32 * u < bm) perm[bb + rank[u]] = p[u];
+      __syncwarp();
+    } else if (lane == 0) {
+      for (int a = bb + 1; a < bb + bm; ++a) {
+        const int32_t q = perm[a];
+        const int32_t qid = id[q];
+        int c = a - 1;
+        while (c >= bb && id[perm[c]] > qid) {
+          perm[c + 1] = perm[c];
+          --c;
+        }
+        perm[c + 1] = q;
+      }
+    }
+    __syncwarp();
   }
 }
 
