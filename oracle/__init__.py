@@ -61,6 +61,9 @@ def _load():
         lib.or_mesh_map.restype = None
         lib.or_project.argtypes = [i64, P, P, i32, i32, d, d, i32, d, P, P]
         lib.or_project.restype = i32
+        for f in (lib.or_project_idw, lib.or_project_dirac):
+            f.argtypes = [i64, P, P, i32, i32, P]
+            f.restype = i32
         _lib = lib
     return _lib
 
@@ -218,6 +221,30 @@ def project_adjoint(x, q, G, ne, degree, sigma, cutoff_sigmas=3.0, cutoff="box")
     if rc:
         raise ValueError("or_project_adjoint failed")
     return gq, gx
+
+
+def project_idw(x, q, ne, degree):
+    """Field [ne^3][4][n1^3] of the linear corner-node (IDW) deposition."""
+    x, q = _f64(x), _f64(q)
+    n = x.shape[-1]
+    n1 = degree + 1
+    field = np.zeros((ne ** 3, 4, n1 ** 3))
+    rc = _load().or_project_idw(n, _p(x), _p(q), ne, degree, _p(field))
+    if rc:
+        raise ValueError("or_project_idw failed (%d)" % rc)
+    return field
+
+
+def project_dirac(x, q, ne, degree):
+    """Field [ne^3][4][n1^3] of the nearest-node (Dirac) deposition."""
+    x, q = _f64(x), _f64(q)
+    n = x.shape[-1]
+    n1 = degree + 1
+    field = np.zeros((ne ** 3, 4, n1 ** 3))
+    rc = _load().or_project_dirac(n, _p(x), _p(q), ne, degree, _p(field))
+    if rc:
+        raise ValueError("or_project_dirac failed (%d)" % rc)
+    return field
 
 
 def mesh_map(xi, amp):

@@ -850,3 +850,126 @@ int or_project_adjoint(int64_t n, const double* x, const double* q, int ne, int 
   free(lz);
   return 0;
 }
+
+/* ------------------------------------------------------------------ corner-node and Dirac deposition */
+
+/* Trilinear weight of corner (dx, dy, dz) in {0,1}^3 of an element at reference
+ * position xi in [-1,1]^3: prod_d (1 + s_d xi_d) / 2 with s_d = -1 for d = 0 and
+ * +1 for d = 1, i.e. 1 at its own corner, 0 at the others. */
+static double corner_weight(int dx, int dy, int dz, const double xi[3]) {
+  const double a = dx ? 0.5 * (1.0 + xi[0]) : 0.5 * (1.0 - xi[0]);
+  const double b = dy ? 0.5 * (1.0 + xi[1]) : 0.5 * (1.0 - xi[1]);
+  const double c = dz ? 0.5 * (1.0 + xi[2]) : 0.5 * (1.0 - xi[2]);
+  return a * b * c;
+}
+
+/* Element of a coordinate in [0,1) and the reference coordinate 2 (x ne - e) - 1. */
+static int elem_ref(double y, int ne, double* xi) {
+  int e = (int)floor(y * ne);
+  if (e < 0) e = 0;
+  if (e > ne - 1) e = ne - 1;
+  *xi = 2.0 * (y * ne - e) - 1.0;
+  return e;
+}
+
+static int64_t corner_node(int ex, int ey, int ez, int dx, int dy, int dz, int ne) {
+  return ((int64_t)((ez + dz) % ne) * ne + (ey + dy) % ne) * ne + (ex + dx) % ne;
+}
+
+int or_project_idw(int64_t n, const double* x, const double* q, int ne, int degree, double* field) {
+  if (n < 0 || ne < 1 || degree < 0 || degree > 15 || !field || (n > 0 && (!x || !q))) return 1;
+  const int n1 = degree + 1, nodes = n1 * n1 * n1;
+  const int64_t nel = (int64_t)ne * ne * ne;
+  double eta[16], w[16];
+  if (or_gauss_legendre(n1, eta, w)) return 1;
+  const double h = 1.0 / ne, jac = 0.125 * h * h * h;
+  double* S = (double*)calloc((size_t)(8 * nel + 2 * nel), sizeof(double)); /* [4][nel] sums + [4][nel] comp + V, Vc */
+  if (!S) return 4;
+  double* Sc = S + 4 * nel;
+  double* V = S + 8 * nel;
+  double* Vc = V + nel;
+  /* node volumes: the quadrature of each corner's trilinear hat over the elements around it */
+  for (int ez = 0; ez < ne; ++ez)
+    for (int ey = 0; ey < ne; ++ey)
+      for (int ex = 0; ex < ne; ++ex)
+        for (int d = 0; d < 8; ++d)
+          for (int k = 0; k < n1; ++k)
+            for (int j = 0; j < n1; ++j)
+              for (int i = 0; i < n1; ++i) {
+                const double xg[3] = {eta[i], eta[j], eta[k]};
+                const int64_t N = corner_node(ex, ey, ez, d & 1, (d >> 1) & 1, d >> 2, ne);
+                neu_add(&V[N], &Vc[N], w[i] * w[j] * w[k] * jac * corner_weight(d & 1, (d >> 1) & 1, d >> 2, xg));
+              }
+  /* node sums of the sources */
+  for (int64_t p = 0; p < n; ++p) {
+    double xi[3];
+    const int ex = elem_ref(x[p], ne, &xi[0]), ey = elem_ref(x[n + p], ne, &xi[1]), ez = elem_ref(x[2 * n + p], ne, &xi[2]);
+    for (int d = 0; d < 8; ++d) {
+      const int64_t N = corner_node(ex, ey, ez, d & 1, (d >> 1) & 1, d >> 2, ne);
+      const double wt = corner_weight(d & 1, (d >> 1) & 1, d >> 2, xi);
+      for (int c = 0; c < 4; ++c) neu_add(&S[c * nel + N], &Sc[c * nel + N], q[c * n + p] * wt);
+    }
+  }
+  /* field at the Gauss nodes: trilinear interpolation of the corner densities */
+  for (int ez = 0; ez < ne; ++ez)
+    for (int ey = 0; ey < ne; ++ey)
+      for (int ex = 0; ex < ne; ++ex) {
+        const int64_t e = ((int64_t)ez * ne + ey) * ne + ex;
+        for (int k = 0; k < n1; ++k)
+          for (int j = 0; j < n1; ++j)
+            for (int i = 0; i < n1; ++i) {
+              const double xg[3] = {eta[i], eta[j], eta[k]};
+              for (int c = 0; c < 4; ++c) {
+                double s = 0.0, sc = 0.0;
+                for (int d = 0; d < 8; ++d) {
+                  const int64_t N = corner_node(ex, ey, ez, d & 1, (d >> 1) & 1, d >> 2, ne);
+                  const double dens = (S[c * nel + N] + Sc[c * nel + N]) / (V[N] + Vc[N]);
+                  neu_add(&s, &sc, corner_weight(d & 1, (d >> 1) & 1, d >> 2, xg) * dens);
+                }
+                field[(e * 4 + c) * nodes + ((int64_t)k * n1 + j) * n1 + i] = s + sc;
+              }
+            }
+      }
+  free(S);
+  return 0;
+}
+
+int or_project_dirac(int64_t n, const double* x, const double* q, int ne, int degree, double* field) {
+  if (n < 0 || ne < 1 || degree < 0 || degree > 15 || !field || (n > 0 && (!x || !q))) return 1;
+  const int n1 = degree + 1, nodes = n1 * n1 * n1;
+  const int64_t nel = (int64_t)ne * ne * ne;
+  double eta[16], w[16];
+  if (or_gauss_legendre(n1, eta, w)) return 1;
+  const double h = 1.0 / ne, jac = 0.125 * h * h * h;
+  double* cmp = (double*)calloc((size_t)(nel * 4 * nodes), sizeof(double));
+  if (!cmp) return 4;
+  memset(field, 0, sizeof(double) * (size_t)(nel * 4 * nodes));
+  for (int64_t p = 0; p < n; ++p) {
+    int e3[3], i3[3];
+    for (int a = 0; a < 3; ++a) {
+      double xi;
+      e3[a] = elem_ref(x[a * n + p], ne, &xi);
+      /* nearest Gauss node along the axis; the lower index on a tie */
+      int best = 0;
+      for (int i = 1; i < n1; ++i)
+        if (fabs(eta[i] - xi) < fabs(eta[best] - xi)) best = i;
+      i3[a] = best;
+    }
+    const int64_t e = ((int64_t)e3[2] * ne + e3[1]) * ne + e3[0];
+    const int g = (i3[2] * n1 + i3[1]) * n1 + i3[0];
+    for (int c = 0; c < 4; ++c) {
+      const int64_t o = (e * 4 + c) * nodes + g;
+      neu_add(&field[o], &cmp[o], q[c * n + p]);
+    }
+  }
+  for (int64_t e = 0; e < nel; ++e)
+    for (int c = 0; c < 4; ++c)
+      for (int k = 0; k < n1; ++k)
+        for (int j = 0; j < n1; ++j)
+          for (int i = 0; i < n1; ++i) {
+            const int64_t o = (e * 4 + c) * nodes + ((int64_t)k * n1 + j) * n1 + i;
+            field[o] = (field[o] + cmp[o]) / (w[i] * w[j] * w[k] * jac);
+          }
+  free(cmp);
+  return 0;
+}

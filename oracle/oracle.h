@@ -125,6 +125,22 @@ void or_mesh_map(const double xi[3], double amp, double X[3], double* detJ);
 int or_project(int64_t n, const double* x, const double* q, int ne, int degree, double sigma, double cutoff_sigmas,
                int cutoff_kind, double amp, double* field, double* Z);
 
+/* Linear corner-node deposition (Sec. 2.3, the deposition operator P in its linear
+ * inverse-distance-weighting form; Sec. 4.2, unique periodic corner-node ids) on
+ * the affine mesh: a particle at reference position xi of its element adds
+ * q_c w_n(xi) to each of the element's 8 corner nodes, w_n(xi) = prod_d
+ * (1 + s_d xi_d)/2 (s_d = -1/+1 for the lower/upper corner); node n carries the
+ * density S_n / V_n with V_n = sum over the elements around n of the quadrature
+ * sum_g W_g w_n(xi_g) (its Jacobian-weighted volume); the field at the Gauss
+ * nodes of an element is the trilinear interpolation of its corner densities,
+ * so sum_g W_g F_gc = sum_p q_pc. Neumaier sums. Returns 0 on success. */
+int or_project_idw(int64_t n, const double* x, const double* q, int ne, int degree, double* field);
+
+/* Dirac deposition (Sec. 4.2): the whole source of a particle goes to the Gauss
+ * node of its element nearest in reference coordinates (per axis; the lower index
+ * on a tie), as the density q / W_g. Returns 0 on success. */
+int or_project_dirac(int64_t n, const double* x, const double* q, int ne, int degree, double* field);
+
 #ifdef __cplusplus
 }
 #endif
