@@ -52,6 +52,7 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-mixed", action="store_true")
+    ap.add_argument("--no-operators", action="store_true")
     ap.add_argument("--mixed-steps", type=int, default=5)
     return ap.parse_args()
 
@@ -217,6 +218,10 @@ def run_ours(args, ws, rank, local):
     if not args.no_e2e:
         e2e = e2e_run(args, ctx, w, n, dt, stream, torch, pc, dist, ws)
 
+    operators = None
+    if not args.no_operators:
+        operators = operators_run(args, ctx, a, wl, stream, torch)
+
     ctx.close()
     del a, b, field
     mixed = None
@@ -239,7 +244,7 @@ def run_ours(args, ws, rank, local):
                    "phi": round(w["phi"], 4), "l2": "inputs larger than L2 (state 105 MB + field 226 MB + scratch)",
                    "parallelism": "independent replica per GPU" if ws > 1 else "1 GPU"},
         "phase_ms_per_call": phase_ms, "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
-        "gpu_launches": launches, "clocks": clocks, "mixed": mixed,
+        "gpu_launches": launches, "clocks": clocks, "mixed": mixed, "operators": operators,
         "collide_stats": {k: st[k] for k in ("pairs", "candidates", "worklist", "rounds", "fp64_solves",
                                               "max_candidates", "cells_per_side", "stencil")},
     }
@@ -394,6 +399,47 @@ def e2e_run(args, ctx, w, n, dt, stream, torch, pc, dist, ws):
     el = max_over_ranks(time.perf_counter() - t0, dist)
     return {"value": n * args.steps * ws / el, "unit": UNIT, "h2d_bytes_per_step": int(h2d),
             "d2h_bytes_per_step": int(d2h)}
+
+
+def operators_run(args, ctx, state, wl, stream, torch):
+    """The corner-node (IDW) and nearest-DOF (Dirac) depositions of the same state, each
+    timed alone over --steps calls after --warmup (CUDA events on the library's stream),
+    with the achieved HBM bandwidth of their deposit kernels: algorithmic bytes per call
+    = particles x (perm 4 + x 24 + q 32 B) + the field written once (+ the 8 x 4 corner
+    sums and node densities written and read once for IDW) / the deposit phase's mean
+    duration."""
+    peak = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))["hbm_gbs"]
+    n, nel, nodes = state.n, wl.ne ** 3, (wl.degree + 1) ** 3
+    field = ctx.new_field()
+    out = {"workload": args.workload, "peak_hbm_gbs": peak, "peak_source": "MEASURED_PEAKS.json hbm_gbs"}
+    # IDW also writes and reads its df32 corner sums (32 x 8 B per element) and node
+    # densities (4 x 8 B per node) once
+    for kind, extra in (("idw", 2 * (32 + 4) * 8 * nel), ("dirac", 0)):
+        call = getattr(ctx, "project_" + kind)
+        for _ in range(max(3, args.warmup)):
+            call(state, field)
+        ctx.sync()
+        ctx.set_timing(True)
+        ctx.timing()
+        ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        ev0.record(stream)
+        for _ in range(args.steps):
+            call(state, field)
+        ev1.record(stream)
+        torch.cuda.synchronize()
+        ms = ev0.elapsed_time(ev1) / args.steps
+        ph = ctx.timing()
+        ctx.set_timing(False)
+        if ctx.stats()["status"] != 0:
+            raise RuntimeError("device status during the %s deposition" % kind)
+        dep = ph["deposit"][0] / max(ph["deposit"][1], 1)
+        algo = n * 60 + 4 * nodes * 8 * nel + extra
+        out[kind] = {"ms_per_call": round(ms, 4), "particles_per_s": n / (ms / 1e3),
+                     "phase_ms_per_call": {k: round(v[0] / max(v[1], 1), 4) for k, v in ph.items() if v[1]},
+                     "deposit_algorithmic_bytes": algo, "deposit_hbm_gbs": algo / (dep / 1e3) / 1e9,
+                     "deposit_frac": algo / (dep / 1e3) / 1e9 / peak}
+    return out
 
 
 def cpu_sample(w, wl, frac_project=16):

@@ -141,6 +141,30 @@ pc_status pc_collide(pc_ctx* ctx, const pc_particles* in, pc_particles* out, dou
  * Accuracy: within 1e-12 of the exact sum, normwise per component. */
 pc_status pc_project(pc_ctx* ctx, const pc_particles* p, double* field);
 
+/* Linear corner-node deposition (Sec. 2.3: the C0 linear form of inverse distance
+ * weighting onto the corner nodes of the host element; Sec. 4.2: corner nodes with
+ * unique periodic ids, deposition radius one element) on the affine mesh. A
+ * particle at reference position xi in [-1,1]^3 of its element (xi_a = 2 (x_a ne -
+ * e_a) - 1) gives q[c][p] w_d(xi) to corner d of the element, w_d(xi) =
+ * prod_a (1 -/+ xi_a)/2 for the lower / upper corner along axis a. Node n holds the
+ * density S_n / V_n, S_n its sum over all particles, V_n = the sum over the 8
+ * elements around it of sum_g W_g w_n(xi_g) (= h^3 here). The field at the Gauss
+ * nodes of an element is the trilinear interpolation of its 8 corner densities, so
+ * sum_g W_g field[g][c] = sum_p q[c][p]. p->q must be non-NULL; positions in
+ * [0,1)^3 (else PC_EINVAL from pc_sync). field: device [ne^3][4][(N+1)^3] doubles,
+ * overwritten. FP64, deterministic (particles summed by element, then id).
+ * Accuracy: within 1e-12 of the exact sums, normwise per component. */
+pc_status pc_project_idw(pc_ctx* ctx, const pc_particles* p, double* field);
+
+/* Nearest-DOF (Dirac delta) deposition (Sec. 4.2): the whole source of a particle
+ * goes to the Gauss node of its element nearest to it, which is the per-axis nearest
+ * node in reference coordinates (the lower index on an exact tie), as the density
+ * q[c][p] / W_g, W_g = w_i w_j w_k (h/2)^3; the nearest node of the own element is
+ * also the nearest of the whole mesh. Arguments and layout as pc_project_idw. FP64,
+ * deterministic; a particle within rounding of a midpoint between two nodes may
+ * choose either. */
+pc_status pc_project_dirac(pc_ctx* ctx, const pc_particles* p, double* field);
+
 /* ---- differentiation (no counterpart in the paper) ----
  * The gradient of a rollout is taken with each step's pair set held fixed. The
  * calls below work on particle arrays in one fixed order (for example by id), not

@@ -28,6 +28,7 @@ UNITS = {
     "tc_deposit.cu": [],
     "adjoint.cu": ["-fmad=false"],
     "curved.cu": ["-fmad=false"],
+    "nodal.cu": ["-fmad=false"],
 }
 
 

@@ -172,6 +172,71 @@ __global__ void __launch_bounds__(256) k_bin_order(int64_t nbins, const int32_t*
   }
 }
 
+// The same ordering with one warp per bin, for bins that hold tens of entries on
+// average (mesh elements): a bin of at most 32 (64) entries is ranked from one (two)
+// register tiles, a larger one as in k_bin_order.
+__global__ void __launch_bounds__(256) k_bin_order_warp(int64_t nbins, const int32_t* __restrict__ start,
+                                                        const int32_t* __restrict__ id, int32_t* __restrict__ perm) {
+  const int64_t b = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
+  if (b >= nbins) return;  // warp-uniform
+  const int beg = start[b], bm = start[b + 1] - beg;
+  if (bm < 2) return;
+  if (bm <= 64) {
+    const int32_t p0 = lane < bm ? perm[beg + lane] : 0, p1 = lane + 32 < bm ? perm[beg + 32 + lane] : 0;
+    const int32_t k0 = lane < bm ? id[p0] : 0x7fffffff, k1 = lane + 32 < bm ? id[p1] : 0x7fffffff;
+    int r0 = 0, r1 = 0;
+    const int m0 = min(bm, 32);
+    for (int sft = 0; sft < m0; ++sft) {
+      const int other = __shfl_sync(0xffffffffu, k0, sft);
+      r0 += other < k0;
+      r1 += other < k1;
+    }
+    if (bm > 32)
+      for (int sft = 0; sft < bm - 32; ++sft) {
+        const int other = __shfl_sync(0xffffffffu, k1, sft);
+        r0 += other < k0;
+        r1 += other < k1;
+      }
+    __syncwarp();
+    if (lane < bm) perm[beg + r0] = p0;
+    if (lane + 32 < bm) perm[beg + r1] = p1;
+  } else if (bm <= kWarpBin) {
+    int32_t p[kWarpBin / 32], key[kWarpBin / 32], rank[kWarpBin / 32];
+#pragma unroll
+    for (int u = 0; u < kWarpBin / 32; ++u) {
+      const int a = lane + 32 * u;
+      p[u] = a < bm ? perm[beg + a] : 0;
+      key[u] = a < bm ? id[p[u]] : 0x7fffffff;
+      rank[u] = 0;
+    }
+#pragma unroll
+    for (int u2 = 0; u2 < kWarpBin / 32; ++u2) {
+      if (32 * u2 >= bm) break;
+      for (int sft = 0; sft < 32; ++sft) {
+        const int other = __shfl_sync(0xffffffffu, key[u2], sft);
+#pragma unroll
+        for (int u = 0; u < kWarpBin / 32; ++u) rank[u] += other < key[u] ? 1 : 0;
+      }
+    }
+    __syncwarp();
+#pragma unroll
+    for (int u = 0; u < kWarpBin / 32; ++u)
+      if (lane + 32 * u < bm) perm[beg + rank[u]] = p[u];
+  } else if (lane == 0) {
+    for (int a = beg + 1; a < beg + bm; ++a) {
+      const int32_t q = perm[a];
+      const int32_t qid = id[q];
+      int c = a - 1;
+      while (c >= beg && id[perm[c]] > qid) {
+        perm[c + 1] = perm[c];
+        --c;
+      }
+      perm[c + 1] = q;
+    }
+  }
+}
+
 }  // namespace
 
 cudaError_t pc_exclusive_scan(const int32_t* in, int32_t* out, int64_t n, int32_t* blocksums, cudaStream_t s,
@@ -191,7 +256,10 @@ cudaError_t pc_bin_finish(int64_t n, int64_t nbins, const int32_t* key, const in
   PC_CUDA_TRY(pc_exclusive_scan(cnt, start, nbins, blocksums, s, launches));
   if (n > 0) {
     k_bin_scatter<<<pc_blocks(n, 256), 256, 0, s>>>(n, key, slot, start, perm);
-    k_bin_order<<<pc_blocks(nbins, 256), 256, 0, s>>>(nbins, start, id, perm);
+    if (n >= 8 * nbins)
+      k_bin_order_warp<<<pc_blocks(32 * nbins, 256), 256, 0, s>>>(nbins, start, id, perm);
+    else
+      k_bin_order<<<pc_blocks(nbins, 256), 256, 0, s>>>(nbins, start, id, perm);
     *launches += 2;
   }
   return cudaGetLastError();

@@ -82,7 +82,7 @@ pc_status fail(pc_ctx* ctx, pc_status s, const char* msg) {
 void free_all(pc_ctx* c) {
   void* ptrs[] = {c->cnt, c->start, c->blocksums, c->key, c->slot, c->perm, c->sx, c->sv, c->sr,
                   c->sid, c->sxf, c->svf, c->srf, c->cand_j, c->cand_t, c->ncand, c->best, c->partner,
-                  c->work, c->tcoll, c->pair_lo, c->pair_hi, c->pair_t, c->counters, c->fac, c->sq, c->scell};
+                  c->work, c->tcoll, c->pair_lo, c->pair_hi, c->pair_t, c->counters, c->fac, c->sq, c->scell, c->corner};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   if (c->h_counters) cudaFreeHost(c->h_counters);
@@ -178,6 +178,7 @@ pc_status pc_init(pc_ctx** out, const pc_config* cfg) {
   chk(dalloc(&ctx->counters, CNT_N));
   chk(dalloc(&ctx->fac, (int64_t)3 * ctx->win * n));
   chk(dalloc(&ctx->sq, 4 * n));
+  chk(dalloc(&ctx->corner, 36 * nel));
   if (e == cudaSuccess) e = cudaMallocHost((void**)&ctx->h_counters, sizeof(unsigned long long) * CNT_N);
   if (e == cudaSuccess) e = cudaMemset(ctx->counters, 0, sizeof(unsigned long long) * CNT_N);
   if (e != cudaSuccess) {
@@ -210,6 +211,20 @@ pc_status pc_project(pc_ctx* ctx, const pc_particles* p, double* field) {
   if (!particles_ok(p, ctx->cfg.n_max) || !field || (p->n > 0 && !p->q))
     return fail(ctx, PC_EINVAL, "pc_project: bad arguments");
   return pc_project_impl(ctx, p, field);
+}
+
+pc_status pc_project_idw(pc_ctx* ctx, const pc_particles* p, double* field) {
+  if (!ctx) return PC_EINVAL;
+  if (!particles_ok(p, ctx->cfg.n_max) || !field || (p->n > 0 && !p->q))
+    return fail(ctx, PC_EINVAL, "pc_project_idw: bad arguments");
+  return pc_project_idw_impl(ctx, p, field);
+}
+
+pc_status pc_project_dirac(pc_ctx* ctx, const pc_particles* p, double* field) {
+  if (!ctx) return PC_EINVAL;
+  if (!particles_ok(p, ctx->cfg.n_max) || !field || (p->n > 0 && !p->q))
+    return fail(ctx, PC_EINVAL, "pc_project_dirac: bad arguments");
+  return pc_project_dirac_impl(ctx, p, field);
 }
 
 int32_t pc_cells_per_side(const pc_ctx* ctx) { return ctx ? ctx->nc : 0; }

@@ -59,6 +59,7 @@ struct pc_ctx {
   float2* fac;  // [3][win][n_max] normalised 1-D kernel factors (df32), sorted order
   float2* sq;   // [4][n_max] sources times (2/h)^3 (df32), sorted order
   DfExpTable exp_tab;
+  double* corner;  // 36 ne^3 doubles: pc_project_idw's df32 corner sums [ne^3][8][4] and node densities [ne^3][4]
   // Legendre-Gauss nodes and weights (passed to the kernels as arguments)
   double eta[16], w[16];
   // per-phase timers (pc_set_timing) and the launch counter
@@ -131,6 +132,14 @@ cudaError_t pc_tc_deposit_launch(const TcDepositArgs& A, cudaStream_t st, int* n
 
 // ---- project (project.cu) ----------------------------------------------------
 pc_status pc_project_impl(pc_ctx* ctx, const pc_particles* p, double* field);
+// Particles binned by mesh element: ctx->start[e] .. ctx->start[e + 1] index
+// ctx->perm, which lists the input indices of element e's particles in id order.
+// Positions outside [0,1) raise PC_EINVAL in the device status.
+cudaError_t pc_elem_bin(pc_ctx* ctx, int64_t n, const double* x, const int32_t* id);
+
+// ---- corner-node and nearest-DOF depositions (nodal.cu) -----------------------
+pc_status pc_project_idw_impl(pc_ctx* ctx, const pc_particles* p, double* field);
+pc_status pc_project_dirac_impl(pc_ctx* ctx, const pc_particles* p, double* field);
 
 #define PC_CUDA_TRY(expr)                          \
   do {                                             \

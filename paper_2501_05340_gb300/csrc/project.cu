@@ -710,23 +710,28 @@ static void deposit_shape(int n1, int* nwarps, int* batch, size_t* smem) {
   *smem = (4 * nodes + 8 * (per_p + raw_p)) * sizeof(float2) + 8 * 5 * sizeof(int) + fixed;
 }
 
+cudaError_t pc_elem_bin(pc_ctx* ctx, int64_t n, const double* x, const int32_t* id) {
+  cudaStream_t st = ctx->stream;
+  const int ne = ctx->cfg.ne;
+  const int64_t nel = (int64_t)ne * ne * ne;
+  PC_CUDA_TRY(cudaMemsetAsync(ctx->cnt, 0, sizeof(int32_t) * (size_t)nel, st));
+  const int tb = pc_phase_begin(ctx, PC_PH_PBIN);
+  if (n > 0) {
+    k_elem_keys<<<pc_blocks(n, 256), 256, 0, st>>>(n, x, ne, ctx->key, ctx->slot, ctx->cnt, ctx->counters);
+    ctx->launches += 1;
+  }
+  const cudaError_t e = pc_bin_finish(n, nel, ctx->key, ctx->slot, id, ctx->cnt, ctx->start, ctx->blocksums,
+                                      ctx->perm, st, &ctx->launches);
+  pc_phase_end(ctx, tb);
+  return e;
+}
+
 pc_status pc_project_impl(pc_ctx* ctx, const pc_particles* p, double* field) {
   const int64_t n = p->n;
   cudaStream_t st = ctx->stream;
   const int ne = ctx->cfg.ne;
   const int64_t nel = (int64_t)ne * ne * ne;
-  cudaError_t e = cudaMemsetAsync(ctx->cnt, 0, sizeof(int32_t) * (size_t)nel, st);
-  if (e != cudaSuccess) goto fail;
-  {
-    const int tb = pc_phase_begin(ctx, PC_PH_PBIN);
-    if (n > 0) {
-      k_elem_keys<<<pc_blocks(n, 256), 256, 0, st>>>(n, p->x, ne, ctx->key, ctx->slot, ctx->cnt, ctx->counters);
-      ctx->launches += 1;
-    }
-    e = pc_bin_finish(n, nel, ctx->key, ctx->slot, p->id, ctx->cnt, ctx->start, ctx->blocksums, ctx->perm, st,
-                      &ctx->launches);
-    pc_phase_end(ctx, tb);
-  }
+  cudaError_t e = pc_elem_bin(ctx, n, p->x, p->id);
   if (e != cudaSuccess) goto fail;
   if (n > 0) {
     FactorArgs F;

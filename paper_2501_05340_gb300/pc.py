@@ -63,6 +63,9 @@ def library():
         lib.pc_init.argtypes = [ctypes.POINTER(c_p), ctypes.POINTER(PcConfig)]
         lib.pc_collide.argtypes = [c_p, ctypes.POINTER(PcParticles), ctypes.POINTER(PcParticles), c_d]
         lib.pc_project.argtypes = [c_p, ctypes.POINTER(PcParticles), c_p]
+        for f in (lib.pc_project_idw, lib.pc_project_dirac):
+            f.argtypes = [c_p, ctypes.POINTER(PcParticles), c_p]
+            f.restype = ctypes.c_int
         lib.pc_get_pairs.argtypes = [c_p, c_p, c_p, c_i64, ctypes.POINTER(c_i64)]
         lib.pc_get_stats.argtypes = [c_p, ctypes.POINTER(PcStats)]
         lib.pc_sync.argtypes = [c_p]
@@ -238,6 +241,23 @@ class Context:
             raise ValueError("field must be contiguous float64 of shape (%d, 4, %d)" % (nel, self.n1 ** 3))
         s = state.struct()
         self._check(library().pc_project(self._h, ctypes.byref(s), _ptr(field)))
+
+    def project_idw(self, state, field):
+        """field <- the linear corner-node (IDW) deposition of state.q at state.x."""
+        self._check_field(field)
+        s = state.struct()
+        self._check(library().pc_project_idw(self._h, ctypes.byref(s), _ptr(field)))
+
+    def project_dirac(self, state, field):
+        """field <- the nearest-DOF (Dirac) deposition of state.q at state.x."""
+        self._check_field(field)
+        s = state.struct()
+        self._check(library().pc_project_dirac(self._h, ctypes.byref(s), _ptr(field)))
+
+    def _check_field(self, field):
+        nel = self.ne ** 3
+        if tuple(field.shape) != (nel, 4, self.n1 ** 3) or field.dtype != torch.float64 or not field.is_contiguous():
+            raise ValueError("field must be contiguous float64 of shape (%d, 4, %d)" % (nel, self.n1 ** 3))
 
     def partner_by_id(self, n_ids, out=None):
         """Device int32 [n_ids]: the partner id of each id in the last collide, or -1."""
