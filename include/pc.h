@@ -152,8 +152,11 @@ pc_status pc_project(pc_ctx* ctx, const pc_particles* p, double* field);
  * nodes of an element is the trilinear interpolation of its 8 corner densities, so
  * sum_g W_g field[g][c] = sum_p q[c][p]. p->q must be non-NULL; positions in
  * [0,1)^3 (else PC_EINVAL from pc_sync). field: device [ne^3][4][(N+1)^3] doubles,
- * overwritten. FP64, deterministic (particles summed by element, then id).
- * Accuracy: within 1e-12 of the exact sums, normwise per component. */
+ * overwritten. FP64-accurate (double-float sums and products, one FP64 FMA per
+ * output), deterministic (particles summed by element, then id). Sources are
+ * taken to 46 significant bits; magnitudes below 2^-126 count as zero, from
+ * 2^128 on as infinite. Accuracy: within 1e-12 of the exact sums, normwise per
+ * component. */
 pc_status pc_project_idw(pc_ctx* ctx, const pc_particles* p, double* field);
 
 /* Nearest-DOF (Dirac delta) deposition (Sec. 4.2): the whole source of a particle
