@@ -61,6 +61,8 @@ def _load():
         lib.or_mesh_map.restype = None
         lib.or_project.argtypes = [i64, P, P, i32, i32, d, d, i32, d, P, P]
         lib.or_project.restype = i32
+        lib.or_respond_advance_rot.argtypes = [i64, P, P, P, P, P, P, P, P, d, d, d]
+        lib.or_respond_advance_rot.restype = None
         for f in (lib.or_project_idw, lib.or_project_dirac):
             f.argtypes = [i64, P, P, i32, i32, P]
             f.restype = i32
@@ -133,6 +135,26 @@ def respond_advance(x, v, m, partner, tc, e, dt):
     tc = _f64(tc)
     _load().or_respond_advance(m.shape[0], _p(x), _p(v), _p(m), _p(partner), _p(tc), float(e), float(dt))
     return x, v
+
+
+def respond_advance_rot(x, v, w, r, m, ids, partner, tc, e, mu, dt):
+    """Response with friction and rotation + free flight + wrap; returns new (x, v, w)."""
+    x, v, w = _f64(x).copy(), _f64(v).copy(), _f64(w).copy()
+    r, m = _f64(r), _f64(m)
+    ids = np.ascontiguousarray(ids, np.int32)
+    partner = np.ascontiguousarray(partner, np.int64)
+    tc = _f64(tc)
+    _load().or_respond_advance_rot(m.shape[0], _p(x), _p(v), _p(w), _p(r), _p(m), _p(ids), _p(partner), _p(tc),
+                                   float(e), float(mu), float(dt))
+    return x, v, w
+
+
+def collide_step_rot(x, v, w, r, m, ids, e, mu, dt, method="cells"):
+    """One collision step with friction and rotation: the pairs of collide_step (they do
+    not depend on w), then respond_advance_rot. Returns (x', v', w', partner, tc, npairs)."""
+    _, _, partner, tc, k = collide_step(x, v, r, m, ids, e, dt, method)
+    x1, v1, w1 = respond_advance_rot(x, v, w, r, m, ids, partner, tc, e, mu, dt)
+    return x1, v1, w1, partner, tc, k
 
 
 def collide_step(x, v, r, m, ids, e, dt, method="cells"):

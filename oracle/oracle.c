@@ -370,6 +370,91 @@ void or_respond_advance(int64_t n, double* x, double* v, const double* m, const 
   free(vn);
 }
 
+/* Response with Coulomb friction and rotation (Sec. 2.4: the jump relations of
+ * linear and angular momentum, J = J_n n + J_t t, J_n = -m_r (1+e) v_r.n, the
+ * contact-point velocity v_c = v_r + r_1 w_1 x n + r_2 w_2 x n, its tangential part
+ * v_rt = v_c - (v_c.n) n, J_t = max(mu J_n, -(2/7)(1+e) m_r |v_rt|), t = v_rt/|v_rt|),
+ * from each particle's own side (it is particle 1, its partner particle 2, n from 1
+ * to 2). Readings: I = (2/5) m r^2 (solid sphere; the paper does not state I); the
+ * two rotational terms of v_c are added in the order of the particles' ids (lower
+ * first), so both sides see the same bits up to sign; |v_rt| = 0 gives no tangential
+ * impulse; I (w' - w) = r (n x J) = r J_t (n x t). Positions as or_respond_advance. */
+static void cross3(const double a[3], const double b[3], double c[3]) {
+  c[0] = a[1] * b[2] - a[2] * b[1];
+  c[1] = a[2] * b[0] - a[0] * b[2];
+  c[2] = a[0] * b[1] - a[1] * b[0];
+}
+
+void or_respond_advance_rot(int64_t n, double* x, double* v, double* w, const double* r, const double* m,
+                            const int32_t* id, const int64_t* partner, const double* tc, double e, double mu,
+                            double dt) {
+  double* xn = (double*)malloc(sizeof(double) * (size_t)(9 * n > 0 ? 9 * n : 1));
+  if (!xn) return;
+  double* vn = xn + 3 * n;
+  double* wn = xn + 6 * n;
+  for (int64_t i = 0; i < n; ++i) {
+    int64_t j = partner[i];
+    if (j < 0) {
+      for (int k = 0; k < 3; ++k) {
+        vn[k * n + i] = v[k * n + i];
+        wn[k * n + i] = w[k * n + i];
+        xn[k * n + i] = x[k * n + i] + dt * v[k * n + i];
+      }
+      continue;
+    }
+    const double t = tc[i];
+    double dx[3], dv[3], s[3], nrm[3];
+    for (int k = 0; k < 3; ++k) {
+      dx[k] = minimg(x[k * n + i] - x[k * n + j]);
+      dv[k] = v[k * n + i] - v[k * n + j];
+    }
+    for (int k = 0; k < 3; ++k) s[k] = dx[k] + t * dv[k];
+    const double sl = sqrt((s[0] * s[0] + s[1] * s[1]) + s[2] * s[2]);
+    for (int k = 0; k < 3; ++k) nrm[k] = -s[k] / sl;
+    const double vrn = (dv[0] * nrm[0] + dv[1] * nrm[1]) + dv[2] * nrm[2];
+    const double mr = (m[i] * m[j]) / (m[i] + m[j]);
+    const double Jn = -mr * (1.0 + e) * vrn;
+    /* contact-point velocity, rotational terms in id order */
+    const int64_t lo = id[i] < id[j] ? i : j, hi = id[i] < id[j] ? j : i;
+    double wl[3], wh[3], cl[3], ch[3], vc[3];
+    for (int k = 0; k < 3; ++k) {
+      wl[k] = w[k * n + lo];
+      wh[k] = w[k * n + hi];
+    }
+    cross3(wl, nrm, cl);
+    cross3(wh, nrm, ch);
+    for (int k = 0; k < 3; ++k) vc[k] = (dv[k] + r[lo] * cl[k]) + r[hi] * ch[k];
+    const double vcn = (vc[0] * nrm[0] + vc[1] * nrm[1]) + vc[2] * nrm[2];
+    double vt[3];
+    for (int k = 0; k < 3; ++k) vt[k] = vc[k] - vcn * nrm[k];
+    const double vtl = sqrt((vt[0] * vt[0] + vt[1] * vt[1]) + vt[2] * vt[2]);
+    double Jt = 0.0, tv[3] = {0.0, 0.0, 0.0};
+    if (vtl > 0.0) {
+      const double slide = mu * Jn, stick = -(2.0 / 7.0) * (1.0 + e) * mr * vtl;
+      Jt = slide > stick ? slide : stick;
+      for (int k = 0; k < 3; ++k) tv[k] = vt[k] / vtl;
+    }
+    const double gn = Jn / m[i], gt = Jt / m[i];
+    double nt[3];
+    cross3(nrm, tv, nt);
+    const double inertia = 0.4 * m[i] * r[i] * r[i];
+    const double gw = (r[i] * Jt) / inertia;
+    for (int k = 0; k < 3; ++k) {
+      const double vold = v[k * n + i];
+      const double vnew = (vold + gn * nrm[k]) + gt * tv[k];
+      vn[k * n + i] = vnew;
+      wn[k * n + i] = w[k * n + i] + gw * nt[k];
+      xn[k * n + i] = (x[k * n + i] + t * vold) + (dt - t) * vnew;
+    }
+  }
+  for (int64_t a = 0; a < 3 * n; ++a) {
+    v[a] = vn[a];
+    w[a] = wn[a];
+    x[a] = wrap01(xn[a]);
+  }
+  free(xn);
+}
+
 int64_t or_collide_step(int64_t n, double* x, double* v, const double* r, const double* m, const int32_t* id,
                         double e, double dt, int method, int64_t* partner, double* tc) {
   int64_t cap = n > 16 ? 4 * n : 64;

@@ -61,6 +61,14 @@ int64_t or_match_rounds(int64_t n, const int32_t* id, int64_t ncand, const int64
 void or_respond_advance(int64_t n, double* x, double* v, const double* m, const int64_t* partner,
                         const double* tc, double e, double dt);
 
+/* Response with Coulomb friction and rotation (Sec. 2.4): the jump relations of
+ * linear and angular momentum with J = J_n n + J_t t, J_t = max(mu J_n,
+ * -(2/7)(1+e) m_r |v_rt|) from the tangential contact-point velocity v_rt; moment
+ * of inertia (2/5) m r^2. w[3][n] angular velocities, updated in place with x, v. */
+void or_respond_advance_rot(int64_t n, double* x, double* v, double* w, const double* r, const double* m,
+                            const int32_t* id, const int64_t* partner, const double* tc, double e, double mu,
+                            double dt);
+
 /* One whole collision step: candidates, greedy matching, response, advance.
  * partner/tc (length n) receive the matching. method: 0 cell list, 1 brute
  * force. Returns the number of pairs, or -1 on allocation failure. */
