@@ -220,7 +220,7 @@ def run_ours(args, ws, rank, local):
 
     operators = None
     if not args.no_operators:
-        operators = operators_run(args, ctx, a, wl, stream, torch)
+        operators = operators_run(args, ctx, a, wl, stream, torch, pc, dt)
 
     ctx.close()
     del a, b, field
@@ -401,13 +401,14 @@ def e2e_run(args, ctx, w, n, dt, stream, torch, pc, dist, ws):
             "d2h_bytes_per_step": int(d2h)}
 
 
-def operators_run(args, ctx, state, wl, stream, torch):
+def operators_run(args, ctx, state, wl, stream, torch, pc, args_dt):
     """The corner-node (IDW) and nearest-DOF (Dirac) depositions of the same state, each
     timed alone over --steps calls after --warmup (CUDA events on the library's stream),
     with the achieved HBM bandwidth of their deposit kernels: algorithmic bytes per call
     = particles x (perm 4 + x 24 + q 32 B) + the field written once (+ the 8 x 4 corner
     sums and node densities written and read once for IDW) / the deposit phase's mean
-    duration."""
+    duration. Also the collision step with friction and rotation next to the
+    frictionless one."""
     peak = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))["hbm_gbs"]
     n, nel, nodes = state.n, wl.ne ** 3, (wl.degree + 1) ** 3
     field = ctx.new_field()
@@ -439,6 +440,36 @@ def operators_run(args, ctx, state, wl, stream, torch):
                      "phase_ms_per_call": {k: round(v[0] / max(v[1], 1), 4) for k, v in ph.items() if v[1]},
                      "deposit_algorithmic_bytes": algo, "deposit_hbm_gbs": algo / (dep / 1e3) / 1e9,
                      "deposit_frac": algo / (dep / 1e3) / 1e9 / peak}
+    # the collision step with Coulomb friction and rotation (mu = 0.3, N(0, 50^2) spins)
+    # next to the frictionless step, both from the same state into a scratch state
+    dst = pc.State.empty(n)
+    gen = torch.Generator(device="cuda").manual_seed(0)
+    w_in = 50.0 * torch.randn(3, n, dtype=torch.float64, device="cuda", generator=gen)
+    w_out = torch.empty_like(w_in)
+    dt = args_dt
+    res = {}
+    for kind, call in (("collide", lambda: ctx.collide(state, dst, dt)),
+                       ("collide_rot", lambda: ctx.collide_rot(state, dst, w_in, w_out, 0.3, dt))):
+        for _ in range(max(3, args.warmup)):
+            call()
+        ctx.sync()
+        ctx.set_timing(True)
+        ctx.timing()
+        ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        ev0.record(stream)
+        for _ in range(args.steps):
+            call()
+        ev1.record(stream)
+        torch.cuda.synchronize()
+        ph = ctx.timing()
+        ctx.set_timing(False)
+        if ctx.stats()["status"] != 0:
+            raise RuntimeError("device status during the %s step" % kind)
+        res[kind] = {"ms_per_call": round(ev0.elapsed_time(ev1) / args.steps, 4),
+                     "respond_ms": round(ph["respond"][0] / max(ph["respond"][1], 1), 4)}
+    out["friction"] = dict(res["collide_rot"], mu=0.3, frictionless_ms_per_call=res["collide"]["ms_per_call"],
+                           frictionless_respond_ms=res["collide"]["respond_ms"])
     return out
 
 

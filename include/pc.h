@@ -133,6 +133,22 @@ pc_status pc_init(pc_ctx** ctx, const pc_config* cfg);
  * so pairs, times, x' and v' are bit-identical to a plain IEEE implementation. */
 pc_status pc_collide(pc_ctx* ctx, const pc_particles* in, pc_particles* out, double dt);
 
+/* One collision step with Coulomb friction and rotation (Sec. 2.4 jump relations of
+ * linear and angular momentum): the pairs of pc_collide (they do not depend on the
+ * spin), then for each pair, from each particle's own side (it is particle 1, n from
+ * it to its partner): J = J_n n + J_t t, J_n = -m_r (1+e) v_r.n; contact-point
+ * velocity v_c = v_r + r_1 w_1 x n + r_2 w_2 x n (the two rotational terms added
+ * lower id first); v_rt = v_c - (v_c.n) n; J_t = max(mu J_n, -(2/7)(1+e) m_r |v_rt|)
+ * (sliding, else sticking), t = v_rt / |v_rt| (no tangential impulse when |v_rt| =
+ * 0); v' = v + J/m, w' = w + r (n x J) / I with I = (2/5) m r^2 (solid spheres);
+ * x' = x + t v + (dt - t) v'. w_in: device angular velocities [3][n] in the order of
+ * `in`; w_out: [3][n] in the order of `out` (cell-sorted like the other outputs);
+ * distinct buffers. mu >= 0 (mu = 0 leaves w unchanged and gives pc_collide's
+ * velocities). FP64 in a fixed operation order without fused multiply-add: bit-
+ * identical to the plain IEEE implementation. Other arguments as pc_collide. */
+pc_status pc_collide_rot(pc_ctx* ctx, const pc_particles* in, pc_particles* out, const double* w_in, double* w_out,
+                         double mu, double dt);
+
 /* Projection (Sec. 2.3, 4.2 with a Gaussian shape function): for every Gauss node
  * X_g, field[g][c] = sum_p q[c][p] K(X_g - x_p) / Z_p, Z_p = sum_g W_g K(X_g - x_p),
  * W_g = w_i w_j w_k (h/2)^3, K(d) = exp(-|d|^2/(2 sigma^2)) inside the cutoff and 0

@@ -205,6 +205,22 @@ pc_status pc_collide(pc_ctx* ctx, const pc_particles* in, pc_particles* out, dou
   return pc_collide_impl(ctx, in, out, dt);
 }
 
+pc_status pc_collide_rot(pc_ctx* ctx, const pc_particles* in, pc_particles* out, const double* w_in, double* w_out,
+                         double mu, double dt) {
+  if (!ctx) return PC_EINVAL;
+  if (!particles_ok(in, ctx->cfg.n_max) || !particles_ok(out, ctx->cfg.n_max) || in->n != out->n)
+    return fail(ctx, PC_EINVAL, "pc_collide_rot: bad particle arrays");
+  if (in->n > 0 && (in->x == out->x || in->v == out->v || in->id == out->id || in->r == out->r || in->m == out->m))
+    return fail(ctx, PC_EINVAL, "pc_collide_rot: in and out must be distinct buffers");
+  if (in->n > 0 && in->q && (!out->q || out->q == in->q))
+    return fail(ctx, PC_EINVAL, "pc_collide_rot: out->q must be a distinct buffer when in->q is given");
+  if (in->n > 0 && (!w_in || !w_out || w_in == w_out))
+    return fail(ctx, PC_EINVAL, "pc_collide_rot: w_in and w_out must be distinct non-NULL buffers");
+  if (!(mu >= 0.0 && mu < INFINITY)) return fail(ctx, PC_EINVAL, "pc_collide_rot: mu must be finite and >= 0");
+  if (!(dt > 0.0 && dt < INFINITY)) return fail(ctx, PC_EINVAL, "pc_collide_rot: dt must be positive and finite");
+  return pc_collide_impl(ctx, in, out, dt, w_in, w_out, mu);
+}
+
 pc_status pc_project(pc_ctx* ctx, const pc_particles* p, double* field) {
   if (!ctx) return PC_EINVAL;
   if (ctx->cfg.cutoff_kind != 0) return fail(ctx, PC_EINVAL, "pc_project: needs the box cutoff (cutoff_kind 0)");

@@ -100,7 +100,10 @@ void pc_gauss_rule(int n1, double* x, double* w);
 void pc_build_exp_table(DfExpTable* tab);
 
 // ---- collide (collide.cu) ----------------------------------------------------
-pc_status pc_collide_impl(pc_ctx* ctx, const pc_particles* in, pc_particles* out, double dt);
+// w_in / w_out: angular velocities [3][n] (input / output order) for the response with
+// friction and rotation; NULL for the frictionless response.
+pc_status pc_collide_impl(pc_ctx* ctx, const pc_particles* in, pc_particles* out, double dt,
+                          const double* w_in = nullptr, double* w_out = nullptr, double mu = 0.0);
 // Matching rounds on the candidate lists left by a search kernel (both paths).
 cudaError_t pc_match_launch(pc_ctx* ctx, int64_t n);
 

@@ -63,6 +63,9 @@ def library():
         lib.pc_init.argtypes = [ctypes.POINTER(c_p), ctypes.POINTER(PcConfig)]
         lib.pc_collide.argtypes = [c_p, ctypes.POINTER(PcParticles), ctypes.POINTER(PcParticles), c_d]
         lib.pc_project.argtypes = [c_p, ctypes.POINTER(PcParticles), c_p]
+        lib.pc_collide_rot.argtypes = [c_p, ctypes.POINTER(PcParticles), ctypes.POINTER(PcParticles), c_p, c_p, c_d,
+                                       c_d]
+        lib.pc_collide_rot.restype = ctypes.c_int
         for f in (lib.pc_project_idw, lib.pc_project_dirac):
             f.argtypes = [c_p, ctypes.POINTER(PcParticles), c_p]
             f.restype = ctypes.c_int
@@ -241,6 +244,16 @@ class Context:
             raise ValueError("field must be contiguous float64 of shape (%d, 4, %d)" % (nel, self.n1 ** 3))
         s = state.struct()
         self._check(library().pc_project(self._h, ctypes.byref(s), _ptr(field)))
+
+    def collide_rot(self, src, dst, w_in, w_out, mu, dt):
+        """One step with Coulomb friction mu and rotation: dst (cell-sorted) and w_out
+        (angular velocities [3][n] float64 in dst's order) from src and w_in (src's order)."""
+        for w in (w_in, w_out):
+            if tuple(w.shape) != (3, src.n) or w.dtype != torch.float64 or not w.is_contiguous():
+                raise ValueError("angular velocities must be contiguous float64 of shape (3, n)")
+        a, b = src.struct(), dst.struct()
+        self._check(library().pc_collide_rot(self._h, ctypes.byref(a), ctypes.byref(b), _ptr(w_in), _ptr(w_out),
+                                             float(mu), float(dt)))
 
     def project_idw(self, state, field):
         """field <- the linear corner-node (IDW) deposition of state.q at state.x."""
