@@ -63,6 +63,10 @@ def _load():
         lib.or_project.restype = i32
         lib.or_respond_advance_rot.argtypes = [i64, P, P, P, P, P, P, P, P, d, d, d]
         lib.or_respond_advance_rot.restype = None
+        lib.or_eval_field.argtypes = [i64, P, P, i32, i32, i32, P]
+        lib.or_eval_field.restype = i32
+        lib.or_drag_sources.argtypes = [i64, P, P, P, d, P]
+        lib.or_drag_sources.restype = None
         for f in (lib.or_project_idw, lib.or_project_dirac):
             f.argtypes = [i64, P, P, i32, i32, P]
             f.restype = i32
@@ -267,6 +271,26 @@ def project_dirac(x, q, ne, degree):
     if rc:
         raise ValueError("or_project_dirac failed (%d)" % rc)
     return field
+
+
+def eval_field(x, field, ne, degree):
+    """DG solution at the particles: out [nvar][n] from field [ne^3][nvar][n1^3]."""
+    x, field = _f64(x), _f64(field)
+    n = x.shape[-1]
+    nvar = field.shape[1]
+    out = np.zeros((nvar, n))
+    rc = _load().or_eval_field(n, _p(x), _p(field), ne, degree, nvar, _p(out))
+    if rc:
+        raise ValueError("or_eval_field failed (%d)" % rc)
+    return out
+
+
+def drag_sources(v, r, fluid, mu_f):
+    """Sources q [4][n] = (-F, -F.v) of the drag force from fluid [4][n] = (rho, u)."""
+    v, r, fluid = _f64(v), _f64(r), _f64(fluid)
+    q = np.zeros((4, r.shape[0]))
+    _load().or_drag_sources(r.shape[0], _p(v), _p(r), _p(fluid), float(mu_f), _p(q))
+    return q
 
 
 def mesh_map(xi, amp):

@@ -12,6 +12,10 @@
  *   or_match_*             Sec. 4.3 (one collision per particle per step)
  *   or_respond_advance     Sec. 2.4 (J_n = -m_r (1+e) v_r.n, frictionless), Sec. 3.3 update
  *   or_project             Sec. 2.3 / 4.2 (deposition operator P, Gaussian shape function)
+ *   or_project_idw/_dirac  Sec. 2.3 / 4.2 (corner-node and nearest-DOF deposition)
+ *   or_respond_advance_rot Sec. 2.4 (friction and rotation)
+ *   or_eval_field          Sec. 3.2 (field evaluation: the DG solution at the particles)
+ *   or_drag_sources        Sec. 2.2 / 2.3 (drag force and its momentum and energy sources)
  * Readings where the paper is silent or garbled are listed at each function.
  */
 #include "oracle.h"
@@ -1057,4 +1061,61 @@ int or_project_dirac(int64_t n, const double* x, const double* q, int ne, int de
           }
   free(cmp);
   return 0;
+}
+
+/* ------------------------------------------------------------------ field at particles, drag sources */
+
+/* Lagrange basis polynomial i of the nodes eta[0..n1) at xi: prod_{m != i} (xi - eta_m) / (eta_i - eta_m). */
+static double lagrange(int n1, const double* eta, int i, double xi) {
+  double num = 1.0, den = 1.0;
+  for (int m = 0; m < n1; ++m) {
+    if (m == i) continue;
+    num *= xi - eta[m];
+    den *= eta[i] - eta[m];
+  }
+  return num / den;
+}
+
+int or_eval_field(int64_t n, const double* x, const double* field, int ne, int degree, int nvar, double* out) {
+  if (n < 0 || ne < 1 || degree < 0 || degree > 15 || nvar < 1 || (n > 0 && (!x || !field || !out))) return 1;
+  const int n1 = degree + 1, nodes = n1 * n1 * n1;
+  double eta[16], w[16];
+  if (or_gauss_legendre(n1, eta, w)) return 1;
+  for (int64_t p = 0; p < n; ++p) {
+    double xi[3];
+    const int ex = elem_ref(x[p], ne, &xi[0]), ey = elem_ref(x[n + p], ne, &xi[1]), ez = elem_ref(x[2 * n + p], ne, &xi[2]);
+    const int64_t e = ((int64_t)ez * ne + ey) * ne + ex;
+    double lx[16], ly[16], lz[16];
+    for (int i = 0; i < n1; ++i) {
+      lx[i] = lagrange(n1, eta, i, xi[0]);
+      ly[i] = lagrange(n1, eta, i, xi[1]);
+      lz[i] = lagrange(n1, eta, i, xi[2]);
+    }
+    for (int c = 0; c < nvar; ++c) {
+      const double* U = field + (e * nvar + c) * nodes;
+      double s = 0.0, sc = 0.0;
+      for (int k = 0; k < n1; ++k)
+        for (int j = 0; j < n1; ++j)
+          for (int i = 0; i < n1; ++i) neu_add(&s, &sc, U[(k * n1 + j) * n1 + i] * (lx[i] * ly[j] * lz[k]));
+      out[c * n + p] = s + sc;
+    }
+  }
+  return 0;
+}
+
+void or_drag_sources(int64_t n, const double* v, const double* r, const double* fluid, double mu_f, double* q) {
+  const double pi = 3.14159265358979323846;
+  for (int64_t p = 0; p < n; ++p) {
+    const double d = 2.0 * r[p];
+    const double rho = fluid[p];
+    double rel[3], F[3];
+    for (int k = 0; k < 3; ++k) rel[k] = fluid[(k + 1) * n + p] - v[k * n + p];
+    const double speed = sqrt((rel[0] * rel[0] + rel[1] * rel[1]) + rel[2] * rel[2]);
+    const double re = rho * speed * d / mu_f;
+    const double fd = 1.0 + 0.15 * pow(re, 0.687);
+    const double coef = 3.0 * pi * mu_f * d * fd;
+    for (int k = 0; k < 3; ++k) F[k] = coef * rel[k];
+    for (int k = 0; k < 3; ++k) q[k * n + p] = -F[k];
+    q[3 * n + p] = -((F[0] * v[p] + F[1] * v[n + p]) + F[2] * v[2 * n + p]);
+  }
 }

@@ -149,6 +149,19 @@ int or_project_idw(int64_t n, const double* x, const double* q, int ne, int degr
  * on a tie), as the density q / W_g. Returns 0 on success. */
 int or_project_dirac(int64_t n, const double* x, const double* q, int ne, int degree, double* field);
 
+/* The DG solution at the particles (Sec. 3.2, field evaluation): for each particle
+ * in element e at reference position xi, out[c][p] = sum_{ijk} U[e][c][k][j][i]
+ * l_i(xi_1) l_j(xi_2) l_k(xi_3), l the Lagrange basis of the Legendre-Gauss nodes;
+ * field [ne^3][nvar][(N+1)^3]. Neumaier sums. Returns 0 on success. */
+int or_eval_field(int64_t n, const double* x, const double* field, int ne, int degree, int nvar, double* out);
+
+/* Momentum and energy sources of the drag force (Sec. 2.2 particle momentum
+ * equation, Sec. 2.3 source terms): F = 3 pi mu_f d f_D (u_f - v_p), d = 2r, with the
+ * Schiller-Naumann factor f_D = 1 + 0.15 Re^0.687, Re = rho_f |u_f - v_p| d / mu_f
+ * (the paper's Loth correlation is not printed); q = (-F, -F.v_p) [4][n].
+ * fluid [4][n] = (rho_f, u_f) at the particles. */
+void or_drag_sources(int64_t n, const double* v, const double* r, const double* fluid, double mu_f, double* q);
+
 #ifdef __cplusplus
 }
 #endif
