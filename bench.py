@@ -470,6 +470,31 @@ def operators_run(args, ctx, state, wl, stream, torch, pc, args_dt):
                      "respond_ms": round(ph["respond"][0] / max(ph["respond"][1], 1), 4)}
     out["friction"] = dict(res["collide_rot"], mu=0.3, frictionless_ms_per_call=res["collide"]["ms_per_call"],
                            frictionless_respond_ms=res["collide"]["respond_ms"])
+    # fluid -> particle coupling: a 4-variable field (rho, u) evaluated at every particle,
+    # then the drag sources (the inputs of the projection in a two-way coupled step)
+    fl = torch.randn(nel, 4, nodes, dtype=torch.float64, device="cuda", generator=gen)
+    fluid = torch.empty(4, n, dtype=torch.float64, device="cuda")
+    qd = torch.empty(4, n, dtype=torch.float64, device="cuda")
+    for _ in range(max(3, args.warmup)):
+        ctx.eval_field(state, fl, fluid)
+        ctx.drag_sources(state, fluid, 1.8e-5, qd)
+    ctx.sync()
+    evs = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+    torch.cuda.synchronize()
+    t_eval = t_drag = 0.0
+    for _ in range(args.steps):
+        evs[0].record(stream)
+        ctx.eval_field(state, fl, fluid)
+        evs[1].record(stream)
+        ctx.drag_sources(state, fluid, 1.8e-5, qd)
+        evs[2].record(stream)
+        torch.cuda.synchronize()
+        t_eval += evs[0].elapsed_time(evs[1])
+        t_drag += evs[1].elapsed_time(evs[2])
+    if ctx.stats()["status"] != 0:
+        raise RuntimeError("device status during the field evaluation")
+    out["coupling"] = {"eval_field_ms_per_call": round(t_eval / args.steps, 4), "nvar": 4,
+                       "drag_sources_ms_per_call": round(t_drag / args.steps, 4)}
     return out
 
 

@@ -29,6 +29,7 @@ UNITS = {
     "adjoint.cu": ["-fmad=false"],
     "curved.cu": ["-fmad=false"],
     "nodal.cu": ["-fmad=false"],
+    "coupling.cu": ["-fmad=false"],
 }
 
 

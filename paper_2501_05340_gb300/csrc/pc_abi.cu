@@ -229,6 +229,21 @@ pc_status pc_project(pc_ctx* ctx, const pc_particles* p, double* field) {
   return pc_project_impl(ctx, p, field);
 }
 
+pc_status pc_eval_field(pc_ctx* ctx, const pc_particles* p, const double* field, int32_t nvar, double* out) {
+  if (!ctx) return PC_EINVAL;
+  if (!particles_ok(p, ctx->cfg.n_max) || nvar < 1 || nvar > 16 || (p->n > 0 && (!field || !out)))
+    return fail(ctx, PC_EINVAL, "pc_eval_field: bad arguments");
+  return pc_eval_field_impl(ctx, p, field, nvar, out);
+}
+
+pc_status pc_drag_sources(pc_ctx* ctx, const pc_particles* p, const double* fluid, double mu_f, double* q) {
+  if (!ctx) return PC_EINVAL;
+  if (!particles_ok(p, ctx->cfg.n_max) || (p->n > 0 && (!fluid || !q)))
+    return fail(ctx, PC_EINVAL, "pc_drag_sources: bad arguments");
+  if (!(mu_f > 0.0 && mu_f < INFINITY)) return fail(ctx, PC_EINVAL, "pc_drag_sources: mu_f must be positive");
+  return pc_drag_sources_impl(ctx, p, fluid, mu_f, q);
+}
+
 pc_status pc_project_idw(pc_ctx* ctx, const pc_particles* p, double* field) {
   if (!ctx) return PC_EINVAL;
   if (!particles_ok(p, ctx->cfg.n_max) || !field || (p->n > 0 && !p->q))

@@ -140,6 +140,10 @@ pc_status pc_project_impl(pc_ctx* ctx, const pc_particles* p, double* field);
 // Positions outside [0,1) raise PC_EINVAL in the device status.
 cudaError_t pc_elem_bin(pc_ctx* ctx, int64_t n, const double* x, const int32_t* id);
 
+// ---- fluid -> particle coupling (coupling.cu) ----------------------------------
+pc_status pc_eval_field_impl(pc_ctx* ctx, const pc_particles* p, const double* field, int nvar, double* out);
+pc_status pc_drag_sources_impl(pc_ctx* ctx, const pc_particles* p, const double* fluid, double mu_f, double* q);
+
 // ---- corner-node and nearest-DOF depositions (nodal.cu) -----------------------
 pc_status pc_project_idw_impl(pc_ctx* ctx, const pc_particles* p, double* field);
 pc_status pc_project_dirac_impl(pc_ctx* ctx, const pc_particles* p, double* field);

@@ -66,6 +66,10 @@ def library():
         lib.pc_collide_rot.argtypes = [c_p, ctypes.POINTER(PcParticles), ctypes.POINTER(PcParticles), c_p, c_p, c_d,
                                        c_d]
         lib.pc_collide_rot.restype = ctypes.c_int
+        lib.pc_eval_field.argtypes = [c_p, ctypes.POINTER(PcParticles), c_p, c_i32, c_p]
+        lib.pc_eval_field.restype = ctypes.c_int
+        lib.pc_drag_sources.argtypes = [c_p, ctypes.POINTER(PcParticles), c_p, c_d, c_p]
+        lib.pc_drag_sources.restype = ctypes.c_int
         for f in (lib.pc_project_idw, lib.pc_project_dirac):
             f.argtypes = [c_p, ctypes.POINTER(PcParticles), c_p]
             f.restype = ctypes.c_int
@@ -254,6 +258,28 @@ class Context:
         a, b = src.struct(), dst.struct()
         self._check(library().pc_collide_rot(self._h, ctypes.byref(a), ctypes.byref(b), _ptr(w_in), _ptr(w_out),
                                              float(mu), float(dt)))
+
+    def eval_field(self, state, field, out=None):
+        """The DG polynomial of field [ne^3, nvar, n1^3] (float64, CUDA) at the particles:
+        out [nvar, n] in state's order."""
+        nel = self.ne ** 3
+        if field.dim() != 3 or tuple(field.shape[::2]) != (nel, self.n1 ** 3) or field.dtype != torch.float64 \
+                or not field.is_contiguous():
+            raise ValueError("field must be contiguous float64 of shape (%d, nvar, %d)" % (nel, self.n1 ** 3))
+        nvar = field.shape[1]
+        if out is None:
+            out = torch.empty(nvar, state.n, dtype=torch.float64, device="cuda")
+        s = state.struct()
+        self._check(library().pc_eval_field(self._h, ctypes.byref(s), _ptr(field), int(nvar), _ptr(out)))
+        return out
+
+    def drag_sources(self, state, fluid, mu_f, q=None):
+        """Drag sources q [4, n] = (-F, -F.v) from fluid [4, n] = (rho, u) at the particles."""
+        if q is None:
+            q = torch.empty(4, state.n, dtype=torch.float64, device="cuda")
+        s = state.struct()
+        self._check(library().pc_drag_sources(self._h, ctypes.byref(s), _ptr(fluid), float(mu_f), _ptr(q)))
+        return q
 
     def project_idw(self, state, field):
         """field <- the linear corner-node (IDW) deposition of state.q at state.x."""
