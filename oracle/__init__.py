@@ -67,6 +67,8 @@ def _load():
         lib.or_eval_field.restype = i32
         lib.or_drag_sources.argtypes = [i64, P, P, P, d, P]
         lib.or_drag_sources.restype = None
+        lib.or_collide_step_sfc.argtypes = [i64, P, P, P, P, P, d, d, i64, P, P]
+        lib.or_collide_step_sfc.restype = i64
         for f in (lib.or_project_idw, lib.or_project_dirac):
             f.argtypes = [i64, P, P, i32, i32, P]
             f.restype = i32
@@ -159,6 +161,21 @@ def collide_step_rot(x, v, w, r, m, ids, e, mu, dt, method="cells"):
     _, _, partner, tc, k = collide_step(x, v, r, m, ids, e, dt, method)
     x1, v1, w1 = respond_advance_rot(x, v, w, r, m, ids, partner, tc, e, mu, dt)
     return x1, v1, w1, partner, tc, k
+
+
+def collide_step_sfc(x, v, r, m, ids, e, dt, ncell):
+    """One collision step with first-found pair selection along the Morton curve over
+    ncell^3 cells; returns (x', v', partner, tc, npairs)."""
+    x, v = _f64(x).copy(), _f64(v).copy()
+    r, m = _f64(r), _f64(m)
+    ids = np.ascontiguousarray(ids, np.int32)
+    n = r.shape[0]
+    partner, tc = np.zeros(n, np.int64), np.zeros(n)
+    k = _load().or_collide_step_sfc(n, _p(x), _p(v), _p(r), _p(m), _p(ids), float(e), float(dt), int(ncell),
+                                    _p(partner), _p(tc))
+    if k < 0:
+        raise MemoryError("oracle collide")
+    return x, v, partner, tc, k
 
 
 def collide_step(x, v, r, m, ids, e, dt, method="cells"):

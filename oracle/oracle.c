@@ -459,6 +459,121 @@ void or_respond_advance_rot(int64_t n, double* x, double* v, double* w, const do
   free(xn);
 }
 
+/* ---------------------------------------------------------- first-found pair selection */
+
+/* Morton (Z-order) code of a cell: bit b of cx, cy, cz goes to bit 3b, 3b+1, 3b+2. */
+static uint64_t morton3(uint64_t cx, uint64_t cy, uint64_t cz) {
+  uint64_t code = 0;
+  for (int b = 0; b < 21; ++b)
+    code |= (((cx >> b) & 1u) << (3 * b)) | (((cy >> b) & 1u) << (3 * b + 1)) | (((cz >> b) & 1u) << (3 * b + 2));
+  return code;
+}
+
+typedef struct {
+  uint64_t key;
+  int64_t idx;
+} keyed_t;
+
+static int cmp_keyed(const void* a, const void* b) {
+  const keyed_t* x = (const keyed_t*)a;
+  const keyed_t* y = (const keyed_t*)b;
+  return x->key < y->key ? -1 : (x->key > y->key ? 1 : 0);
+}
+
+int64_t or_collide_step_sfc(int64_t n, double* x, double* v, const double* r, const double* m, const int32_t* id,
+                            double e, double dt, int64_t ncell, int64_t* partner, double* tc) {
+  int64_t cap = n > 16 ? 4 * n : 64;
+  int64_t* ci = NULL;
+  int64_t* cj = NULL;
+  double* ct = NULL;
+  int64_t nc = 0;
+  for (;;) {
+    ci = (int64_t*)malloc(sizeof(int64_t) * (size_t)cap);
+    cj = (int64_t*)malloc(sizeof(int64_t) * (size_t)cap);
+    ct = (double*)malloc(sizeof(double) * (size_t)cap);
+    if (!ci || !cj || !ct) { free(ci); free(cj); free(ct); return -1; }
+    nc = or_candidates_cells(n, x, v, r, dt, cap, ci, cj, ct);
+    if (nc < 0) { free(ci); free(cj); free(ct); return -1; }
+    if (nc <= cap) break;
+    free(ci); free(cj); free(ct);
+    cap = nc;
+  }
+  /* rank of every particle along the curve: (Morton code of its cell, id) */
+  uint64_t* key = (uint64_t*)malloc(sizeof(uint64_t) * (size_t)(n > 0 ? n : 1));
+  keyed_t* order = (keyed_t*)malloc(sizeof(keyed_t) * (size_t)(n > 0 ? n : 1));
+  /* every particle's candidates, ordered by the partner's rank */
+  keyed_t* adj = (keyed_t*)malloc(sizeof(keyed_t) * (size_t)(2 * nc > 0 ? 2 * nc : 1));
+  double* adjt = (double*)malloc(sizeof(double) * (size_t)(2 * nc > 0 ? 2 * nc : 1));
+  int64_t* off = (int64_t*)calloc((size_t)n + 1, sizeof(int64_t));
+  if (!key || !order || !adj || !adjt || !off) {
+    free(ci); free(cj); free(ct); free(key); free(order); free(adj); free(adjt); free(off);
+    return -1;
+  }
+  for (int64_t i = 0; i < n; ++i) {
+    const uint64_t code = morton3((uint64_t)cell_of(x[i], ncell), (uint64_t)cell_of(x[n + i], ncell),
+                                  (uint64_t)cell_of(x[2 * n + i], ncell));
+    key[i] = (code << 32) | (uint32_t)id[i];
+    order[i].key = key[i];
+    order[i].idx = i;
+    partner[i] = -1;
+    tc[i] = INFINITY;
+  }
+  qsort(order, (size_t)n, sizeof(keyed_t), cmp_keyed);
+  for (int64_t k = 0; k < nc; ++k) {
+    off[ci[k] + 1]++;
+    off[cj[k] + 1]++;
+  }
+  for (int64_t i = 0; i < n; ++i) off[i + 1] += off[i];
+  {
+    int64_t* fill = (int64_t*)calloc((size_t)(n > 0 ? n : 1), sizeof(int64_t));
+    if (!fill) { free(ci); free(cj); free(ct); free(key); free(order); free(adj); free(adjt); free(off); return -1; }
+    for (int64_t k = 0; k < nc; ++k) {
+      const int64_t a = ci[k], b = cj[k];
+      int64_t pa = off[a] + fill[a]++, pb = off[b] + fill[b]++;
+      adj[pa].key = key[b];
+      adj[pa].idx = b;
+      adjt[pa] = ct[k];
+      adj[pb].key = key[a];
+      adj[pb].idx = a;
+      adjt[pb] = ct[k];
+    }
+    free(fill);
+  }
+  /* sort each particle's candidates by partner rank, carrying the contact times */
+  for (int64_t i = 0; i < n; ++i) {
+    for (int64_t a = off[i] + 1; a < off[i + 1]; ++a) {
+      const keyed_t kk = adj[a];
+      const double tt = adjt[a];
+      int64_t b = a - 1;
+      while (b >= off[i] && adj[b].key > kk.key) {
+        adj[b + 1] = adj[b];
+        adjt[b + 1] = adjt[b];
+        --b;
+      }
+      adj[b + 1] = kk;
+      adjt[b + 1] = tt;
+    }
+  }
+  /* visit the particles along the curve; each free one takes its first free candidate */
+  int64_t pairs = 0;
+  for (int64_t q = 0; q < n; ++q) {
+    const int64_t i = order[q].idx;
+    if (partner[i] >= 0) continue;
+    for (int64_t a = off[i]; a < off[i + 1]; ++a) {
+      const int64_t j = adj[a].idx;
+      if (partner[j] >= 0) continue;
+      partner[i] = j;
+      partner[j] = i;
+      tc[i] = tc[j] = adjt[a];
+      ++pairs;
+      break;
+    }
+  }
+  free(ci); free(cj); free(ct); free(key); free(order); free(adj); free(adjt); free(off);
+  or_respond_advance(n, x, v, m, partner, tc, e, dt);
+  return pairs;
+}
+
 int64_t or_collide_step(int64_t n, double* x, double* v, const double* r, const double* m, const int32_t* id,
                         double e, double dt, int method, int64_t* partner, double* tc) {
   int64_t cap = n > 16 ? 4 * n : 64;

@@ -75,6 +75,17 @@ void or_respond_advance_rot(int64_t n, double* x, double* v, double* w, const do
 int64_t or_collide_step(int64_t n, double* x, double* v, const double* r, const double* m, const int32_t* id,
                         double e, double dt, int method, int64_t* partner, double* tc);
 
+/* One collision step with the paper's first-found pair selection (Sec. 4.3: the
+ * particles are visited in the order of the space-filling curve, each free particle
+ * checks its possible partners in that order and the first valid collision with a
+ * free partner is committed at once). Reading: the curve is the Morton (Z-order)
+ * curve over the uniform grid of ncell^3 collision cells (bit b of the cell's x, y, z
+ * index to bit 3b, 3b+1, 3b+2), particles within a cell by id; the candidates are
+ * those of or_candidates_cells. Then or_respond_advance. Returns the number of
+ * pairs, or -1 on allocation failure. */
+int64_t or_collide_step_sfc(int64_t n, double* x, double* v, const double* r, const double* m, const int32_t* id,
+                            double e, double dt, int64_t ncell, int64_t* partner, double* tc);
+
 /* ---- mixed-precision storage (FP32 cell-relative state) ----
  * A position is stored as an integer cell c in [0, nc) per axis (linear cell
  * (cz*nc + cy)*nc + cx) and an FP32 offset o in [0,1) in cell units; velocities,
