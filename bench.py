@@ -448,8 +448,14 @@ def operators_run(args, ctx, state, wl, stream, torch, pc, args_dt):
     w_out = torch.empty_like(w_in)
     dt = args_dt
     res = {}
+    def sfc_collide():
+        ctx.set_pair_policy("sfc_first")
+        ctx.collide(state, dst, dt)
+        ctx.set_pair_policy("earliest")
+
     for kind, call in (("collide", lambda: ctx.collide(state, dst, dt)),
-                       ("collide_rot", lambda: ctx.collide_rot(state, dst, w_in, w_out, 0.3, dt))):
+                       ("collide_rot", lambda: ctx.collide_rot(state, dst, w_in, w_out, 0.3, dt)),
+                       ("collide_sfc", sfc_collide)):
         for _ in range(max(3, args.warmup)):
             call()
         ctx.sync()
@@ -470,6 +476,8 @@ def operators_run(args, ctx, state, wl, stream, torch, pc, args_dt):
                      "respond_ms": round(ph["respond"][0] / max(ph["respond"][1], 1), 4)}
     out["friction"] = dict(res["collide_rot"], mu=0.3, frictionless_ms_per_call=res["collide"]["ms_per_call"],
                            frictionless_respond_ms=res["collide"]["respond_ms"])
+    out["sfc_first_pairs"] = {"ms_per_call": res["collide_sfc"]["ms_per_call"],
+                              "earliest_contact_ms_per_call": res["collide"]["ms_per_call"]}
     # fluid -> particle coupling: a 4-variable field (rho, u) evaluated at every particle,
     # then the drag sources (the inputs of the projection in a two-way coupled step)
     fl = torch.randn(nel, 4, nodes, dtype=torch.float64, device="cuda", generator=gen)

@@ -115,6 +115,17 @@ typedef enum {
   PC_NPHASE = 8
 } pc_phase;
 
+/* Pair selection of pc_collide / pc_collide_rot (Sec. 4.3: at most one collision per
+ * particle per step). PC_PAIRS_EARLIEST (the default): earliest contact first, ties
+ * to the smaller id pair. PC_PAIRS_SFC_FIRST: the paper's first-found order, with the
+ * particles visited along a space-filling curve and each free particle taking the
+ * first free partner of a valid collision in that order; the curve is the Morton
+ * (Z-order) curve over the collision cells (bit b of the cell's x, y, z index to bit
+ * 3b, 3b+1, 3b+2), particles within a cell by id, so the result depends on the cell
+ * grid (pc_cells_per_side). Either matching is computed in parallel and is unique. */
+typedef enum { PC_PAIRS_EARLIEST = 0, PC_PAIRS_SFC_FIRST = 1 } pc_pair_policy;
+pc_status pc_set_pair_policy(pc_ctx* ctx, int32_t policy);
+
 /* Create a context: validates cfg, builds the Gauss tables, chooses the collision
  * cells (side >= reach_hint, at least 3 per side) and allocates all scratch on
  * the current CUDA device. *ctx is NULL on failure. */

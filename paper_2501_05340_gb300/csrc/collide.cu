@@ -219,6 +219,44 @@ __device__ __forceinline__ void insert_sorted(double* lt, int* lj, int& cnt, int
   if (cnt < cap) ++cnt;
 }
 
+// Morton (Z-order) code of a cell with coordinates below 1024: bit b of cx, cy, cz to
+// bit 3b, 3b+1, 3b+2.
+__device__ __forceinline__ uint32_t spread3(uint32_t v) {
+  v &= 0x3FFu;
+  v = (v | (v << 16)) & 0x030000FFu;
+  v = (v | (v << 8)) & 0x0300F00Fu;
+  v = (v | (v << 4)) & 0x030C30C3u;
+  v = (v | (v << 2)) & 0x09249249u;
+  return v;
+}
+
+// Rank key of sorted particle j along the curve of the first-found pair selection:
+// (Morton code of its cell, id).
+__device__ __forceinline__ unsigned long long sfc_key(const double* __restrict__ sx, const int32_t* __restrict__ sid,
+                                                      int64_t n, int nc, int64_t j) {
+  const uint32_t code = spread3((uint32_t)cell_of(sx[j], nc)) | (spread3((uint32_t)cell_of(sx[n + j], nc)) << 1) |
+                        (spread3((uint32_t)cell_of(sx[2 * n + j], nc)) << 2);
+  return ((unsigned long long)code << 32) | (uint32_t)sid[j];
+}
+
+// Insertion into a list sorted by the partner's rank key (first-found selection).
+__device__ __forceinline__ void insert_by_key(double* lt, int* lj, unsigned long long* lk, int& cnt, int cap,
+                                              double t, int j, unsigned long long key) {
+  int pos = cnt;
+  while (pos > 0 && lk[pos - 1] > key) --pos;
+  if (pos >= cap) return;
+  const int last = cnt < cap ? cnt : cap - 1;
+  for (int q = last; q > pos; --q) {
+    lt[q] = lt[q - 1];
+    lj[q] = lj[q - 1];
+    lk[q] = lk[q - 1];
+  }
+  lt[pos] = t;
+  lj[pos] = j;
+  lk[pos] = key;
+  if (cnt < cap) ++cnt;
+}
+
 // Thread per particle (sorted by cell). The certified FP32 filter runs over the
 // stencil (each row of cells along x as one range when it does not wrap); its
 // survivors are queued per block and solved in FP64 by all of the block's threads
@@ -226,7 +264,10 @@ __device__ __forceinline__ void insert_sorted(double* lt, int* lj, int& cnt, int
 // (t, id). On this GPU an FP64 instruction takes a warp 64 pipe cycles whatever
 // the number of active lanes, so solving a block's survivors densely instead of in
 // each diverged warp removes most of the FP64 time. The insertion does not depend
-// on the order of the roots.
+// on the order of the roots. kSfc: the lists are sorted by the partner's rank key
+// instead (the paper's first-found selection; the matching then takes, for every
+// particle, its first free candidate in that order).
+template <bool kSfc>
 __global__ void __launch_bounds__(256) k_search(SearchArgs A) {
   const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   const int64_t n = A.n;
@@ -251,6 +292,7 @@ __global__ void __launch_bounds__(256) k_search(SearchArgs A) {
   int found = 0, solves = 0, cnt = 0;
   double lt[kMaxCap];
   int lj[kMaxCap];
+  unsigned long long lk[kSfc ? kMaxCap : 1];
   int mine[kMine];
   int nmine = 0;
   if (k < n) {
@@ -279,7 +321,10 @@ __global__ void __launch_bounds__(256) k_search(SearchArgs A) {
         const double t = solve_pair(A, k, j);
         if (t <= A.dt) {
           ++found;
-          insert_sorted(lt, lj, cnt, A.cap, t, (int)j, A.sid);
+          if constexpr (kSfc)
+            insert_by_key(lt, lj, lk, cnt, A.cap, t, (int)j, sfc_key(A.sx, A.sid, n, nc, j));
+          else
+            insert_sorted(lt, lj, cnt, A.cap, t, (int)j, A.sid);
         }
       }
     };
@@ -319,7 +364,10 @@ __global__ void __launch_bounds__(256) k_search(SearchArgs A) {
       const double t = q_t[mine[i]];
       if (t <= A.dt) {
         ++found;
-        insert_sorted(lt, lj, cnt, A.cap, t, q_j[mine[i]], A.sid);
+        if constexpr (kSfc)
+          insert_by_key(lt, lj, lk, cnt, A.cap, t, q_j[mine[i]], sfc_key(A.sx, A.sid, n, A.nc, q_j[mine[i]]));
+        else
+          insert_sorted(lt, lj, cnt, A.cap, t, q_j[mine[i]], A.sid);
       }
     }
     for (int q = 0; q < cnt; ++q) {
@@ -699,7 +747,10 @@ pc_status pc_collide_impl(pc_ctx* ctx, const pc_particles* in, pc_particles* out
     A.best = ctx->best;
     A.counters = ctx->counters;
     const int ts = pc_phase_begin(ctx, PC_PH_SEARCH);
-    k_search<<<pc_blocks(n, 256), 256, 0, st>>>(A);
+    if (ctx->pair_policy == PC_PAIRS_SFC_FIRST)
+      k_search<true><<<pc_blocks(n, 256), 256, 0, st>>>(A);
+    else
+      k_search<false><<<pc_blocks(n, 256), 256, 0, st>>>(A);
     ctx->launches += 1;
     pc_phase_end(ctx, ts);
   }

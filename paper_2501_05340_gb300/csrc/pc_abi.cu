@@ -258,6 +258,14 @@ pc_status pc_project_dirac(pc_ctx* ctx, const pc_particles* p, double* field) {
   return pc_project_dirac_impl(ctx, p, field);
 }
 
+pc_status pc_set_pair_policy(pc_ctx* ctx, int32_t policy) {
+  if (!ctx) return PC_EINVAL;
+  if (policy != PC_PAIRS_EARLIEST && policy != PC_PAIRS_SFC_FIRST)
+    return fail(ctx, PC_EINVAL, "pc_set_pair_policy: unknown policy");
+  ctx->pair_policy = policy;
+  return PC_OK;
+}
+
 int32_t pc_cells_per_side(const pc_ctx* ctx) { return ctx ? ctx->nc : 0; }
 
 static bool particles_f32_ok(const pc_particles_f32* p, int64_t n_max) {

@@ -59,6 +59,7 @@ struct pc_ctx {
   float2* fac;  // [3][win][n_max] normalised 1-D kernel factors (df32), sorted order
   float2* sq;   // [4][n_max] sources times (2/h)^3 (df32), sorted order
   DfExpTable exp_tab;
+  int pair_policy;  // PC_PAIRS_EARLIEST or PC_PAIRS_SFC_FIRST (pc_set_pair_policy)
   double* corner;  // 36 ne^3 doubles: pc_project_idw's df32 corner sums [ne^3][8][4] and node densities [ne^3][4]
   // Legendre-Gauss nodes and weights (passed to the kernels as arguments)
   double eta[16], w[16];

@@ -70,6 +70,8 @@ def library():
         lib.pc_eval_field.restype = ctypes.c_int
         lib.pc_drag_sources.argtypes = [c_p, ctypes.POINTER(PcParticles), c_p, c_d, c_p]
         lib.pc_drag_sources.restype = ctypes.c_int
+        lib.pc_set_pair_policy.argtypes = [c_p, c_i32]
+        lib.pc_set_pair_policy.restype = ctypes.c_int
         for f in (lib.pc_project_idw, lib.pc_project_dirac):
             f.argtypes = [c_p, ctypes.POINTER(PcParticles), c_p]
             f.restype = ctypes.c_int
@@ -248,6 +250,11 @@ class Context:
             raise ValueError("field must be contiguous float64 of shape (%d, 4, %d)" % (nel, self.n1 ** 3))
         s = state.struct()
         self._check(library().pc_project(self._h, ctypes.byref(s), _ptr(field)))
+
+    def set_pair_policy(self, policy):
+        """Pair selection of collide / collide_rot: "earliest" or "sfc_first"."""
+        code = {"earliest": 0, "sfc_first": 1}[policy]
+        self._check(library().pc_set_pair_policy(self._h, code))
 
     def collide_rot(self, src, dst, w_in, w_out, mu, dt):
         """One step with Coulomb friction mu and rotation: dst (cell-sorted) and w_out
