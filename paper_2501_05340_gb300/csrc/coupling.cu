@@ -70,31 +70,6 @@ __device__ __forceinline__ f2 split_f64(double v) {
   return fast_two_sum(h, u23_scaled((unsigned)(u >> 6) & 0x7FFFFFu) * __uint_as_float(sign | sc));
 }
 
-__device__ __forceinline__ double df_to_f64(f2 a) {
-  const unsigned hb = __float_as_uint(a.h), lb = __float_as_uint(a.l);
-  const unsigned long long sgn = (unsigned long long)(hb >> 31) << 63;
-  const int eh = (int)((hb >> 23) & 0xFF);
-  if (eh == 0) return __longlong_as_double((long long)sgn);
-  if (eh == 0xFF)
-    return __longlong_as_double((long long)(sgn | 0x7FF0000000000000ull | ((hb & 0x7FFFFFu) ? (1ull << 51) : 0ull)));
-  unsigned long long S = (unsigned long long)((hb & 0x7FFFFFu) | 0x800000u) << 29;
-  if (lb & 0x7FFFFFFFu) {
-    const int el = (int)((lb >> 23) & 0xFF);
-    const unsigned ml = (lb & 0x7FFFFFu) | (el ? 0x800000u : 0u);
-    const int k = min((el ? el : 1) - eh + 29, 5);
-    const unsigned long long L = k >= 0 ? ((unsigned long long)ml << k) : (k > -32 ? (unsigned long long)(ml >> -k) : 0ull);
-    S = ((hb ^ lb) >> 31) ? S - L : S + L;
-  }
-  int e = eh;
-  if (S >> 53) {
-    S >>= 1;
-    ++e;
-  } else if (!(S >> 52)) {
-    S <<= 1;
-    --e;
-  }
-  return __longlong_as_double((long long)(sgn | ((unsigned long long)(e + 896) << 52) | (S & (kOne52 - 1))));
-}
 
 __device__ __forceinline__ void df_acc_mul(f2& acc, f2 a, f2 b) {
   f2 p = two_prod(a.h, b.h);

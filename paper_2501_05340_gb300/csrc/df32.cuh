@@ -79,6 +79,36 @@ __device__ __forceinline__ f2 df_from_double(double d) {
 
 __device__ __forceinline__ double df_to_double(f2 a) { return (double)a.h + (double)a.l; }
 
+// A normalised df32 pair (|l| <= ulp(h)/2) as the double h + l, truncated to 53 bits,
+// by integer operations only (no conversion or FP64 instruction, which on GB300 run at
+// the FP64 rate even when a branch around them is never taken): a subnormal h gives a
+// signed zero, an infinite or NaN h the double infinity or NaN.
+__device__ __forceinline__ double df_to_f64(f2 a) {
+  const unsigned hb = __float_as_uint(a.h), lb = __float_as_uint(a.l);
+  const unsigned long long sgn = (unsigned long long)(hb >> 31) << 63;
+  const int eh = (int)((hb >> 23) & 0xFF);
+  if (eh == 0) return __longlong_as_double((long long)sgn);
+  if (eh == 0xFF)
+    return __longlong_as_double((long long)(sgn | 0x7FF0000000000000ull | ((hb & 0x7FFFFFu) ? (1ull << 51) : 0ull)));
+  unsigned long long S = (unsigned long long)((hb & 0x7FFFFFu) | 0x800000u) << 29;  // unit 2^(eh - 179)
+  if (lb & 0x7FFFFFFFu) {
+    const int el = (int)((lb >> 23) & 0xFF);
+    const unsigned ml = (lb & 0x7FFFFFu) | (el ? 0x800000u : 0u);
+    const int k = min((el ? el : 1) - eh + 29, 5);  // l = ml 2^(el - 150) = ml 2^k units (k <= 5 when normalised)
+    const unsigned long long L = k >= 0 ? ((unsigned long long)ml << k) : (k > -32 ? (unsigned long long)(ml >> -k) : 0ull);
+    S = ((hb ^ lb) >> 31) ? S - L : S + L;
+  }
+  int e = eh;
+  if (S >> 53) {
+    S >>= 1;
+    ++e;
+  } else if (!(S >> 52)) {
+    S <<= 1;
+    --e;
+  }
+  return __longlong_as_double((long long)(sgn | ((unsigned long long)(e + 896) << 52) | (S & ((1ull << 52) - 1))));
+}
+
 // Constants of exp2(j/64) and the split of ln(2)/64, computed on the host in
 // double precision and passed to the kernels.
 struct DfExpTable {
