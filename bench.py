@@ -35,8 +35,8 @@ UNIT = "particle-steps/s"
 FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12
 # FP32 pipe: 152 SMs x 128 lanes x 2.07 GHz, operations (an FMA counts once) per second.
 FP32_PIPE_TOPS = 152 * 128 * 2.07e9 / 1e12
-# DRAM bytes (read + write) per launch of the dominant kernels at the bench workloads, from
-# the committed ncu captures (profiles/k_proj_deposit_blk_fp64.md, profiles/k_tc_deposit_mixed.md);
+# DRAM bytes (read + write) per launch of the dominant kernels at the bench workloads, from one
+# ncu capture of each (dram__bytes_read.sum + dram__bytes_write.sum, summarised under profiles/);
 # None once a kernel has changed since its capture.
 DEPOSIT_DRAM_BYTES = 753.9e6   # k_proj_deposit_blk<6>, dense_1m
 TC_DEPOSIT_DRAM_BYTES = 3.44e9  # k_tc_deposit<0>, mixed_16m
