@@ -268,7 +268,7 @@ __device__ __forceinline__ void insert_by_key(double* lt, int* lj, unsigned long
 // instead (the paper's first-found selection; the matching then takes, for every
 // particle, its first free candidate in that order).
 template <bool kSfc>
-__global__ void __launch_bounds__(256) k_search(SearchArgs A) {
+__global__ void __launch_bounds__(256, 3) k_search(SearchArgs A) {
   const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   const int64_t n = A.n;
   // stencil radius and speed bound from the step's maxima, once per block
@@ -522,58 +522,81 @@ struct RespondArgs {
 // Frictionless hard-sphere response (Sec. 2.4) from the particle's own side:
 // s = dx + t dv (from partner to self), n = -s/|s|, v_r.n, m_r = m_i m_j/(m_i + m_j),
 // J = -m_r (1 + e) v_r.n, v' = v + (J/m_i) n, x' = x + t v + (dt - t) v' (Sec. 3.3).
-__global__ void k_respond(RespondArgs R) {
-  const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+__device__ __forceinline__ void pair_response(const RespondArgs& R, int64_t k, int32_t j, double mi, double xo[3],
+                                              double vo[3]) {
   const int64_t n = R.n;
-  if (k >= n) return;
-  const int64_t p = R.perm[k];
-  const int32_t j = R.partner[k];
-  const double mi = R.m_in[p];
-  double xo[3], vo[3];
   const double xi[3] = {R.sx[k], R.sx[n + k], R.sx[2 * n + k]};
   const double vi[3] = {R.sv[k], R.sv[n + k], R.sv[2 * n + k]};
-  if (j < 0) {
-#pragma unroll
-    for (int a = 0; a < 3; ++a) {
-      vo[a] = vi[a];
-      xo[a] = xi[a] + R.dt * vi[a];
-    }
-  } else {
-    const double t = R.tcoll[k];
-    const double mj = R.m_in[R.perm[j]];
-    double dx[3], dv[3], s[3], nr[3];
-#pragma unroll
-    for (int a = 0; a < 3; ++a) {
-      dx[a] = minimg(xi[a] - R.sx[a * n + j]);
-      dv[a] = vi[a] - R.sv[a * n + j];
-    }
-#pragma unroll
-    for (int a = 0; a < 3; ++a) s[a] = dx[a] + t * dv[a];
-    const double sl = sqrt((s[0] * s[0] + s[1] * s[1]) + s[2] * s[2]);
-#pragma unroll
-    for (int a = 0; a < 3; ++a) nr[a] = -s[a] / sl;
-    const double vrn = (dv[0] * nr[0] + dv[1] * nr[1]) + dv[2] * nr[2];
-    const double mr = (mi * mj) / (mi + mj);
-    const double J = -mr * (1.0 + R.e) * vrn;
-    const double gi = J / mi;
-#pragma unroll
-    for (int a = 0; a < 3; ++a) {
-      const double vnew = vi[a] + gi * nr[a];
-      vo[a] = vnew;
-      xo[a] = (xi[a] + t * vi[a]) + (R.dt - t) * vnew;
-    }
-  }
+  const double t = R.tcoll[k];
+  const double mj = R.m_in[R.perm[j]];
+  double dx[3], dv[3], s[3], nr[3];
 #pragma unroll
   for (int a = 0; a < 3; ++a) {
-    R.x_out[a * n + k] = wrap01(xo[a]);
-    R.v_out[a * n + k] = vo[a];
+    dx[a] = minimg(xi[a] - R.sx[a * n + j]);
+    dv[a] = vi[a] - R.sv[a * n + j];
   }
-  R.r_out[k] = R.sr[k];
-  R.m_out[k] = mi;
-  R.id_out[k] = R.sid[k];
-  if (R.q_out) {
 #pragma unroll
-    for (int c = 0; c < 4; ++c) R.q_out[c * n + k] = R.q_in[c * n + p];
+  for (int a = 0; a < 3; ++a) s[a] = dx[a] + t * dv[a];
+  const double sl = sqrt((s[0] * s[0] + s[1] * s[1]) + s[2] * s[2]);
+#pragma unroll
+  for (int a = 0; a < 3; ++a) nr[a] = -s[a] / sl;
+  const double vrn = (dv[0] * nr[0] + dv[1] * nr[1]) + dv[2] * nr[2];
+  const double mr = (mi * mj) / (mi + mj);
+  const double J = -mr * (1.0 + R.e) * vrn;
+  const double gi = J / mi;
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+    const double vnew = vi[a] + gi * nr[a];
+    vo[a] = vnew;
+    xo[a] = (xi[a] + t * vi[a]) + (R.dt - t) * vnew;
+  }
+}
+
+// One thread per particle for free flight and the copies; the block's colliding
+// particles are queued and their responses computed by the block's first threads
+// together: on this GPU an FP64 instruction takes a warp the same pipe time whatever
+// the number of active lanes, so the few colliding lanes of every warp would
+// otherwise cost each warp the whole FP64 response.
+__global__ void __launch_bounds__(256) k_respond(RespondArgs R) {
+  __shared__ int q_cnt;
+  __shared__ int q_k[256];
+  if (threadIdx.x == 0) q_cnt = 0;
+  __syncthreads();
+  const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const int64_t n = R.n;
+  if (k < n) {
+    const int64_t p = R.perm[k];
+    const int32_t j = R.partner[k];
+    const double mi = R.m_in[p];
+    if (j < 0) {
+#pragma unroll
+      for (int a = 0; a < 3; ++a) {
+        const double vi = R.sv[a * n + k];
+        R.x_out[a * n + k] = wrap01(R.sx[a * n + k] + R.dt * vi);
+        R.v_out[a * n + k] = vi;
+      }
+    } else {
+      q_k[atomicAdd(&q_cnt, 1)] = threadIdx.x;
+    }
+    R.r_out[k] = R.sr[k];
+    R.m_out[k] = mi;
+    R.id_out[k] = R.sid[k];
+    if (R.q_out) {
+#pragma unroll
+      for (int c = 0; c < 4; ++c) R.q_out[c * n + k] = R.q_in[c * n + p];
+    }
+  }
+  __syncthreads();
+  const int nq = q_cnt;
+  for (int e = threadIdx.x; e < nq; e += blockDim.x) {
+    const int64_t kk = (int64_t)blockIdx.x * blockDim.x + q_k[e];
+    double xo[3], vo[3];
+    pair_response(R, kk, R.partner[kk], R.m_in[R.perm[kk]], xo, vo);
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+      R.x_out[a * n + kk] = wrap01(xo[a]);
+      R.v_out[a * n + kk] = vo[a];
+    }
   }
 }
 
