@@ -606,95 +606,117 @@ __device__ __forceinline__ void cross3(const double a[3], const double b[3], dou
   c[2] = a[0] * b[1] - a[1] * b[0];
 }
 
+// The response with friction and rotation of sorted particle k with partner j (see
+// k_respond_rot).
+__device__ __forceinline__ void pair_response_rot(const RespondArgs& R, int64_t k, int32_t j, double xo[3],
+                                                  double vo[3], double wo[3]) {
+  const int64_t n = R.n;
+  const int64_t p = R.perm[k];
+  const double mi = R.m_in[p];
+  const double xi[3] = {R.sx[k], R.sx[n + k], R.sx[2 * n + k]};
+  const double vi[3] = {R.sv[k], R.sv[n + k], R.sv[2 * n + k]};
+  const double wi[3] = {R.w_in[p], R.w_in[n + p], R.w_in[2 * n + p]};
+  const double t = R.tcoll[k];
+  const int64_t pj = R.perm[j];
+  const double mj = R.m_in[pj];
+  double dx[3], dv[3], s[3], nr[3];
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+    dx[a] = minimg(xi[a] - R.sx[a * n + j]);
+    dv[a] = vi[a] - R.sv[a * n + j];
+  }
+#pragma unroll
+  for (int a = 0; a < 3; ++a) s[a] = dx[a] + t * dv[a];
+  const double sl = sqrt((s[0] * s[0] + s[1] * s[1]) + s[2] * s[2]);
+#pragma unroll
+  for (int a = 0; a < 3; ++a) nr[a] = -s[a] / sl;
+  const double vrn = (dv[0] * nr[0] + dv[1] * nr[1]) + dv[2] * nr[2];
+  const double mr = (mi * mj) / (mi + mj);
+  const double Jn = -mr * (1.0 + R.e) * vrn;
+  const double wj[3] = {R.w_in[pj], R.w_in[n + pj], R.w_in[2 * n + pj]};
+  const double ri = R.sr[k], rj = R.sr[j];
+  const bool self_lo = R.sid[k] < R.sid[j];
+  double cl[3], ch[3], vc[3];
+  cross3(self_lo ? wi : wj, nr, cl);
+  cross3(self_lo ? wj : wi, nr, ch);
+  const double rl = self_lo ? ri : rj, rh = self_lo ? rj : ri;
+#pragma unroll
+  for (int a = 0; a < 3; ++a) vc[a] = (dv[a] + rl * cl[a]) + rh * ch[a];
+  const double vcn = (vc[0] * nr[0] + vc[1] * nr[1]) + vc[2] * nr[2];
+  double vt[3];
+#pragma unroll
+  for (int a = 0; a < 3; ++a) vt[a] = vc[a] - vcn * nr[a];
+  const double vtl = sqrt((vt[0] * vt[0] + vt[1] * vt[1]) + vt[2] * vt[2]);
+  double Jt = 0.0, tv[3] = {0.0, 0.0, 0.0};
+  if (vtl > 0.0) {
+    const double slide = R.mu * Jn, stick = -(2.0 / 7.0) * (1.0 + R.e) * mr * vtl;
+    Jt = slide > stick ? slide : stick;
+#pragma unroll
+    for (int a = 0; a < 3; ++a) tv[a] = vt[a] / vtl;
+  }
+  const double gn = Jn / mi, gt = Jt / mi;
+  double nt[3];
+  cross3(nr, tv, nt);
+  const double inertia = 0.4 * mi * ri * ri;
+  const double gw = (ri * Jt) / inertia;
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+    const double vnew = (vi[a] + gn * nr[a]) + gt * tv[a];
+    vo[a] = vnew;
+    wo[a] = wi[a] + gw * nt[a];
+    xo[a] = (xi[a] + t * vi[a]) + (R.dt - t) * vnew;
+  }
+}
+
 // Response with Coulomb friction and rotation (Sec. 2.4) from the particle's own side
 // (it is particle 1, n from it to its partner): J = J_n n + J_t t, J_n = -m_r (1+e) v_r.n,
 // contact-point velocity v_c = v_r + r_1 w_1 x n + r_2 w_2 x n with the two rotational
 // terms added in id order (lower first, so both sides see the same bits up to sign),
 // v_rt = v_c - (v_c.n) n, J_t = max(mu J_n, -(2/7)(1+e) m_r |v_rt|), t = v_rt/|v_rt| (no
 // tangential impulse when |v_rt| = 0); v' = v + (J_n/m) n + (J_t/m) t and
-// w' = w + (r J_t / I)(n x t) with I = (2/5) m r^2; x' = x + t v + (dt - t) v'.
-__global__ void k_respond_rot(RespondArgs R) {
+// w' = w + (r J_t / I)(n x t) with I = (2/5) m r^2; x' = x + t v + (dt - t) v'. The
+// colliding particles of a block are computed densely, as in k_respond.
+__global__ void __launch_bounds__(256) k_respond_rot(RespondArgs R) {
+  __shared__ int q_cnt;
+  __shared__ int q_k[256];
+  if (threadIdx.x == 0) q_cnt = 0;
+  __syncthreads();
   const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   const int64_t n = R.n;
-  if (k >= n) return;
-  const int64_t p = R.perm[k];
-  const int32_t j = R.partner[k];
-  const double mi = R.m_in[p];
-  double xo[3], vo[3], wo[3];
-  const double xi[3] = {R.sx[k], R.sx[n + k], R.sx[2 * n + k]};
-  const double vi[3] = {R.sv[k], R.sv[n + k], R.sv[2 * n + k]};
-  const double wi[3] = {R.w_in[p], R.w_in[n + p], R.w_in[2 * n + p]};
-  if (j < 0) {
+  if (k < n) {
+    const int64_t p = R.perm[k];
+    const int32_t j = R.partner[k];
+    if (j < 0) {
 #pragma unroll
-    for (int a = 0; a < 3; ++a) {
-      vo[a] = vi[a];
-      wo[a] = wi[a];
-      xo[a] = xi[a] + R.dt * vi[a];
+      for (int a = 0; a < 3; ++a) {
+        const double vi = R.sv[a * n + k];
+        R.x_out[a * n + k] = wrap01(R.sx[a * n + k] + R.dt * vi);
+        R.v_out[a * n + k] = vi;
+        R.w_out[a * n + k] = R.w_in[a * n + p];
+      }
+    } else {
+      q_k[atomicAdd(&q_cnt, 1)] = threadIdx.x;
     }
-  } else {
-    const double t = R.tcoll[k];
-    const int64_t pj = R.perm[j];
-    const double mj = R.m_in[pj];
-    double dx[3], dv[3], s[3], nr[3];
+    R.r_out[k] = R.sr[k];
+    R.m_out[k] = R.m_in[p];
+    R.id_out[k] = R.sid[k];
+    if (R.q_out) {
 #pragma unroll
-    for (int a = 0; a < 3; ++a) {
-      dx[a] = minimg(xi[a] - R.sx[a * n + j]);
-      dv[a] = vi[a] - R.sv[a * n + j];
-    }
-#pragma unroll
-    for (int a = 0; a < 3; ++a) s[a] = dx[a] + t * dv[a];
-    const double sl = sqrt((s[0] * s[0] + s[1] * s[1]) + s[2] * s[2]);
-#pragma unroll
-    for (int a = 0; a < 3; ++a) nr[a] = -s[a] / sl;
-    const double vrn = (dv[0] * nr[0] + dv[1] * nr[1]) + dv[2] * nr[2];
-    const double mr = (mi * mj) / (mi + mj);
-    const double Jn = -mr * (1.0 + R.e) * vrn;
-    const double wj[3] = {R.w_in[pj], R.w_in[n + pj], R.w_in[2 * n + pj]};
-    const double ri = R.sr[k], rj = R.sr[j];
-    const bool self_lo = R.sid[k] < R.sid[j];
-    double cl[3], ch[3], vc[3];
-    cross3(self_lo ? wi : wj, nr, cl);
-    cross3(self_lo ? wj : wi, nr, ch);
-    const double rl = self_lo ? ri : rj, rh = self_lo ? rj : ri;
-#pragma unroll
-    for (int a = 0; a < 3; ++a) vc[a] = (dv[a] + rl * cl[a]) + rh * ch[a];
-    const double vcn = (vc[0] * nr[0] + vc[1] * nr[1]) + vc[2] * nr[2];
-    double vt[3];
-#pragma unroll
-    for (int a = 0; a < 3; ++a) vt[a] = vc[a] - vcn * nr[a];
-    const double vtl = sqrt((vt[0] * vt[0] + vt[1] * vt[1]) + vt[2] * vt[2]);
-    double Jt = 0.0, tv[3] = {0.0, 0.0, 0.0};
-    if (vtl > 0.0) {
-      const double slide = R.mu * Jn, stick = -(2.0 / 7.0) * (1.0 + R.e) * mr * vtl;
-      Jt = slide > stick ? slide : stick;
-#pragma unroll
-      for (int a = 0; a < 3; ++a) tv[a] = vt[a] / vtl;
-    }
-    const double gn = Jn / mi, gt = Jt / mi;
-    double nt[3];
-    cross3(nr, tv, nt);
-    const double inertia = 0.4 * mi * ri * ri;
-    const double gw = (ri * Jt) / inertia;
-#pragma unroll
-    for (int a = 0; a < 3; ++a) {
-      const double vnew = (vi[a] + gn * nr[a]) + gt * tv[a];
-      vo[a] = vnew;
-      wo[a] = wi[a] + gw * nt[a];
-      xo[a] = (xi[a] + t * vi[a]) + (R.dt - t) * vnew;
+      for (int c = 0; c < 4; ++c) R.q_out[c * n + k] = R.q_in[c * n + p];
     }
   }
+  __syncthreads();
+  const int nq = q_cnt;
+  for (int e = threadIdx.x; e < nq; e += blockDim.x) {
+    const int64_t kk = (int64_t)blockIdx.x * blockDim.x + q_k[e];
+    double xo[3], vo[3], wo[3];
+    pair_response_rot(R, kk, R.partner[kk], xo, vo, wo);
 #pragma unroll
-  for (int a = 0; a < 3; ++a) {
-    R.x_out[a * n + k] = wrap01(xo[a]);
-    R.v_out[a * n + k] = vo[a];
-    R.w_out[a * n + k] = wo[a];
-  }
-  R.r_out[k] = R.sr[k];
-  R.m_out[k] = mi;
-  R.id_out[k] = R.sid[k];
-  if (R.q_out) {
-#pragma unroll
-    for (int c = 0; c < 4; ++c) R.q_out[c * n + k] = R.q_in[c * n + p];
+    for (int a = 0; a < 3; ++a) {
+      R.x_out[a * n + kk] = wrap01(xo[a]);
+      R.v_out[a * n + kk] = vo[a];
+      R.w_out[a * n + kk] = wo[a];
+    }
   }
 }
 

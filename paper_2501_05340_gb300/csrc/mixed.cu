@@ -480,43 +480,61 @@ __device__ __forceinline__ void respond_pair_f32(int c[3], const int cj[3], cons
 }
 
 // Free particles: advance_free_axis on each axis. Colliding pairs: respond_pair_f32
-// at the contact time found by the search.
-__global__ void k_respond_f32(RespondF32 R) {
+// at the contact time found by the search, queued per block and computed by the
+// block's first threads together (its FP64 instructions would otherwise cost every
+// warp with a colliding lane the whole response).
+__global__ void __launch_bounds__(256) k_respond_f32(RespondF32 R) {
+  __shared__ int q_cnt;
+  __shared__ int q_k[256];
+  if (threadIdx.x == 0) q_cnt = 0;
+  __syncthreads();
   const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   const int64_t n = R.n;
-  if (k >= n) return;
   const int nc = R.nc;
-  const int64_t p = R.perm[k];
-  const int32_t j = R.partner[k];
-  const float mi_f = R.m_in[p];
-  int c[3];
-  cell_coords(R.scell[k], nc, c);
-  float oo[3], vo[3];
-  if (j < 0) {
-    const float dtn = (float)(R.dt * (double)nc);
+  if (k < n) {
+    const int64_t p = R.perm[k];
+    const int32_t j = R.partner[k];
+    const float mi_f = R.m_in[p];
+    if (j < 0) {
+      int c[3];
+      cell_coords(R.scell[k], nc, c);
+      const float dtn = (float)(R.dt * (double)nc);
+#pragma unroll
+      for (int a = 0; a < 3; ++a) {
+        const float v = R.sv[a * n + k];
+        R.o_out[a * n + k] = advance_free_axis(R.so[a * n + k], v, dtn, nc, &c[a]);
+        R.v_out[a * n + k] = v;
+      }
+      R.cell_out[k] = (c[2] * nc + c[1]) * nc + c[0];
+    } else {
+      q_k[atomicAdd(&q_cnt, 1)] = threadIdx.x;
+    }
+    R.r_out[k] = R.sr[k];
+    R.m_out[k] = mi_f;
+    R.id_out[k] = R.sid[k];
+    if (R.q_out)
+      for (int q = 0; q < 4; ++q) R.q_out[q * n + k] = R.q_in[q * n + p];
+  }
+  __syncthreads();
+  const int nq = q_cnt;
+  for (int e = threadIdx.x; e < nq; e += blockDim.x) {
+    const int64_t kk = (int64_t)blockIdx.x * blockDim.x + q_k[e];
+    const int32_t j = R.partner[kk];
+    int c[3], cj[3];
+    cell_coords(R.scell[kk], nc, c);
+    cell_coords(R.scell[j], nc, cj);
+    const float oi[3] = {R.so[kk], R.so[n + kk], R.so[2 * n + kk]}, oj[3] = {R.so[j], R.so[n + j], R.so[2 * n + j]};
+    const float vi[3] = {R.sv[kk], R.sv[n + kk], R.sv[2 * n + kk]}, vj[3] = {R.sv[j], R.sv[n + j], R.sv[2 * n + j]};
+    float oo[3], vo[3];
+    respond_pair_f32(c, cj, oi, oj, vi, vj, R.m_in[R.perm[kk]], R.m_in[R.perm[j]], R.tcoll[kk], R.dt, R.e, nc, oo,
+                     vo);
+    R.cell_out[kk] = (c[2] * nc + c[1]) * nc + c[0];
 #pragma unroll
     for (int a = 0; a < 3; ++a) {
-      vo[a] = R.sv[a * n + k];
-      oo[a] = advance_free_axis(R.so[a * n + k], vo[a], dtn, nc, &c[a]);
+      R.o_out[a * n + kk] = oo[a];
+      R.v_out[a * n + kk] = vo[a];
     }
-  } else {
-    int cj[3];
-    cell_coords(R.scell[j], nc, cj);
-    const float oi[3] = {R.so[k], R.so[n + k], R.so[2 * n + k]}, oj[3] = {R.so[j], R.so[n + j], R.so[2 * n + j]};
-    const float vi[3] = {R.sv[k], R.sv[n + k], R.sv[2 * n + k]}, vj[3] = {R.sv[j], R.sv[n + j], R.sv[2 * n + j]};
-    respond_pair_f32(c, cj, oi, oj, vi, vj, mi_f, R.m_in[R.perm[j]], R.tcoll[k], R.dt, R.e, nc, oo, vo);
   }
-  R.cell_out[k] = (c[2] * nc + c[1]) * nc + c[0];
-#pragma unroll
-  for (int a = 0; a < 3; ++a) {
-    R.o_out[a * n + k] = oo[a];
-    R.v_out[a * n + k] = vo[a];
-  }
-  R.r_out[k] = R.sr[k];
-  R.m_out[k] = mi_f;
-  R.id_out[k] = R.sid[k];
-  if (R.q_out)
-    for (int q = 0; q < 4; ++q) R.q_out[q * n + k] = R.q_in[q * n + p];
 }
 
 // ------------------------------------------------------------------ projection prep
