@@ -53,6 +53,7 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-mixed", action="store_true")
     ap.add_argument("--no-operators", action="store_true")
+    ap.add_argument("--no-adjoint", action="store_true")
     ap.add_argument("--mixed-steps", type=int, default=5)
     return ap.parse_args()
 
@@ -224,6 +225,9 @@ def run_ours(args, ws, rank, local):
 
     ctx.close()
     del a, b, field
+    adjoint = None
+    if not args.no_adjoint and args.workload == "dense_1m":
+        adjoint = adjoint_run(args, w, wl, stream, torch, pc)
     mixed = None
     if not args.no_mixed:
         mixed = mixed_run(args, rank, torch, pc, stream)
@@ -244,7 +248,7 @@ def run_ours(args, ws, rank, local):
                    "phi": round(w["phi"], 4), "l2": "inputs larger than L2 (state 105 MB + field 226 MB + scratch)",
                    "parallelism": "independent replica per GPU" if ws > 1 else "1 GPU"},
         "phase_ms_per_call": phase_ms, "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
-        "gpu_launches": launches, "clocks": clocks, "mixed": mixed, "operators": operators,
+        "gpu_launches": launches, "clocks": clocks, "mixed": mixed, "operators": operators, "adjoint": adjoint,
         "collide_stats": {k: st[k] for k in ("pairs", "candidates", "worklist", "rounds", "fp64_solves",
                                               "max_candidates", "cells_per_side", "stencil")},
     }
@@ -421,6 +425,57 @@ def e2e_run(args, ctx, w, n, dt, stream, torch, pc, dist, ws):
         raise RuntimeError("the downloaded field differs from the device field")
     return {"value": n * args.steps * ws / el, "unit": UNIT, "h2d_bytes_per_step": int(h2d),
             "d2h_bytes_per_step": int(d2h), "overlap": "copies on separate streams, double-buffered"}
+
+
+def adjoint_run(args, w, wl, stream, torch, pc, steps=50, every=10):
+    """The differentiable rollout of the dense workload: loss 0.5 ||P(S_50(x, v), q) - T||^2
+    with T the projection of a 1 % perturbed copy, forward (pair sets recorded,
+    checkpoints every 10 steps) and backward (replays and step adjoints), FP64 (Rollout)
+    and FP32 on the mixed path (Rollout32). Times include the library's host syncs."""
+    from paper_2501_05340_gb300 import autograd
+
+    n, dt = w["x"].shape[1], w["dt"]
+    T = lambda a, dtp=torch.float64: torch.as_tensor(np.ascontiguousarray(a)).to("cuda", dtp)
+    rng = np.random.default_rng(11)
+    xp = w["x"] + 0.01 * wl.sigma * rng.normal(size=w["x"].shape)
+    xp -= np.floor(xp)
+    pert = dict(w, x=xp, v=w["v"] * (1 + 0.01 * rng.normal(size=w["v"].shape)),
+                q=w["q"] * (1 + 0.01 * rng.normal(size=w["q"].shape)))
+    out = {"workload": args.workload, "steps": steps, "checkpoint_every": every}
+    with torch.cuda.stream(stream):
+        ctx = pc.Context(n, wl.ne, wl.degree, wl.sigma, w["e"], pc.reach_of(w["r"], w["v"], dt) * 1.5,
+                         stream=stream)
+        r, m, ids = T(w["r"]), T(w["m"]), T(w["id"], torch.int32)
+        for kind in ("fp64", "fp32"):
+            if kind == "fp64":
+                target = ctx.new_field()
+                ctx.project(pc.State.from_arrays(pert), target)
+                fn = autograd.rollout_loss
+            else:
+                p32 = pc.StateF32.empty(n)
+                ctx.quantize(pc.State.from_arrays(pert), p32)
+                target = ctx.new_field_f32()
+                ctx.project_f32(p32, target)
+                fn = autograd.rollout_loss_f32
+            times = []
+            for _ in range(2):  # the first pass warms up
+                x0, v0, q = (T(w[k]).requires_grad_(True) for k in ("x", "v", "q"))
+                torch.cuda.synchronize()
+                t0 = time.perf_counter()
+                loss = fn(x0, v0, q, r, m, ids, target, ctx, dt, steps, every)
+                torch.cuda.synchronize()
+                t1 = time.perf_counter()
+                loss.backward()
+                torch.cuda.synchronize()
+                t2 = time.perf_counter()
+                times.append((t1 - t0, t2 - t1))
+            if ctx.stats()["status"] != 0:
+                raise RuntimeError("device status during the %s rollout" % kind)
+            fwd, bwd = times[-1]
+            out[kind] = {"forward_ms": round(1e3 * fwd, 2), "backward_ms": round(1e3 * bwd, 2),
+                         "particle_steps_per_s": n * steps / (fwd + bwd)}
+        ctx.close()
+    return out
 
 
 def operators_run(args, ctx, state, wl, stream, torch, pc, args_dt):

@@ -83,59 +83,80 @@ struct ReplayArgs {
   unsigned long long* counters;
 };
 
-__global__ void k_replay(ReplayArgs A) {
-  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+// The replayed pair step of particle i (partner j): contact time, response, advance;
+// a pair without a root in [0, dt] is recorded as PC_EREPLAY and flies free.
+__device__ __forceinline__ void replay_pair(const ReplayArgs& A, int64_t i, int32_t j) {
   const int64_t n = A.n;
-  if (i >= n) return;
-  const int32_t j = A.partner[i];
   const double xi[3] = {A.x[i], A.x[n + i], A.x[2 * n + i]};
   const double vi[3] = {A.v[i], A.v[n + i], A.v[2 * n + i]};
   double xo[3], vo[3];
-  if (j < 0) {
+  const double xj[3] = {A.x[j], A.x[n + j], A.x[2 * n + j]};
+  const double vj[3] = {A.v[j], A.v[n + j], A.v[2 * n + j]};
+  const double t = pair_time(xi, xj, vi, vj, A.r[i] + A.r[j], A.dt);
+  if (!(t <= A.dt)) {
+    atomicMax(&A.counters[CNT_STATUS], (unsigned long long)PC_EREPLAY);
     for (int a = 0; a < 3; ++a) {
       vo[a] = vi[a];
       xo[a] = xi[a] + A.dt * vi[a];
     }
   } else {
-    const double xj[3] = {A.x[j], A.x[n + j], A.x[2 * n + j]};
-    const double vj[3] = {A.v[j], A.v[n + j], A.v[2 * n + j]};
-    const double t = pair_time(xi, xj, vi, vj, A.r[i] + A.r[j], A.dt);
-    if (!(t <= A.dt)) {
-      atomicMax(&A.counters[CNT_STATUS], (unsigned long long)PC_EREPLAY);
-      for (int a = 0; a < 3; ++a) {
-        vo[a] = vi[a];
-        xo[a] = xi[a] + A.dt * vi[a];
-      }
-    } else {
-      double dx[3], dv[3], s[3], nr[3];
-      for (int a = 0; a < 3; ++a) {
-        dx[a] = minimg(xi[a] - xj[a]);
-        dv[a] = vi[a] - vj[a];
-      }
-      for (int a = 0; a < 3; ++a) s[a] = dx[a] + t * dv[a];
-      const double sl = sqrt((s[0] * s[0] + s[1] * s[1]) + s[2] * s[2]);
-      for (int a = 0; a < 3; ++a) nr[a] = -s[a] / sl;
-      const double vrn = (dv[0] * nr[0] + dv[1] * nr[1]) + dv[2] * nr[2];
-      const double mi = A.m[i], mj = A.m[j];
-      const double mr = (mi * mj) / (mi + mj);
-      const double J = -mr * (1.0 + A.e) * vrn;
-      const double gi = J / mi;
-      for (int a = 0; a < 3; ++a) {
-        const double vnew = vi[a] + gi * nr[a];
-        vo[a] = vnew;
-        xo[a] = (xi[a] + t * vi[a]) + (A.dt - t) * vnew;
-      }
+    double dx[3], dv[3], s[3], nr[3];
+    for (int a = 0; a < 3; ++a) {
+      dx[a] = minimg(xi[a] - xj[a]);
+      dv[a] = vi[a] - vj[a];
+    }
+    for (int a = 0; a < 3; ++a) s[a] = dx[a] + t * dv[a];
+    const double sl = sqrt((s[0] * s[0] + s[1] * s[1]) + s[2] * s[2]);
+    for (int a = 0; a < 3; ++a) nr[a] = -s[a] / sl;
+    const double vrn = (dv[0] * nr[0] + dv[1] * nr[1]) + dv[2] * nr[2];
+    const double mi = A.m[i], mj = A.m[j];
+    const double mr = (mi * mj) / (mi + mj);
+    const double J = -mr * (1.0 + A.e) * vrn;
+    const double gi = J / mi;
+    for (int a = 0; a < 3; ++a) {
+      const double vnew = vi[a] + gi * nr[a];
+      vo[a] = vnew;
+      xo[a] = (xi[a] + t * vi[a]) + (A.dt - t) * vnew;
     }
   }
   for (int a = 0; a < 3; ++a) {
     A.xo[a * n + i] = wrap01(xo[a]);
     A.vo[a * n + i] = vo[a];
   }
-  if (A.ro) A.ro[i] = A.r[i];
-  if (A.mo) A.mo[i] = A.m[i];
-  if (A.ido) A.ido[i] = A.id[i];
-  if (A.qo)
-    for (int c = 0; c < 4; ++c) A.qo[c * n + i] = A.q[c * n + i];
+}
+
+// One thread per particle for free flight and the copies; the block's colliding
+// particles are queued and replayed by the block's first threads together (an FP64
+// instruction takes a warp the same pipe time whatever the number of active lanes).
+__global__ void __launch_bounds__(256) k_replay(ReplayArgs A) {
+  __shared__ int q_cnt;
+  __shared__ int q_i[256];
+  if (threadIdx.x == 0) q_cnt = 0;
+  __syncthreads();
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const int64_t n = A.n;
+  if (i < n) {
+    if (A.partner[i] < 0) {
+      for (int a = 0; a < 3; ++a) {
+        const double vi = A.v[a * n + i];
+        A.xo[a * n + i] = wrap01(A.x[a * n + i] + A.dt * vi);
+        A.vo[a * n + i] = vi;
+      }
+    } else {
+      q_i[atomicAdd(&q_cnt, 1)] = threadIdx.x;
+    }
+    if (A.ro) A.ro[i] = A.r[i];
+    if (A.mo) A.mo[i] = A.m[i];
+    if (A.ido) A.ido[i] = A.id[i];
+    if (A.qo)
+      for (int c = 0; c < 4; ++c) A.qo[c * n + i] = A.q[c * n + i];
+  }
+  __syncthreads();
+  const int nq = q_cnt;
+  for (int e = threadIdx.x; e < nq; e += blockDim.x) {
+    const int64_t ii = (int64_t)blockIdx.x * blockDim.x + q_i[e];
+    replay_pair(A, ii, A.partner[ii]);
+  }
 }
 
 struct AdjArgs {
@@ -151,18 +172,8 @@ struct AdjArgs {
 // Reverse sweep of one pair's response, from particle i's side; writes i's cotangents.
 // Forward: t from |dx + t dv| = R, s = dx + t dv, n = -s/|s|, J = -m_r (1+e) dv.n,
 // v_i' = v_i + (J/m_i) n, v_j' = v_j - (J/m_j) n, x_k' = x_k + t v_k + (dt - t) v_k'.
-__global__ void k_collide_adjoint(AdjArgs A) {
-  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+__device__ __forceinline__ void adjoint_pair(const AdjArgs& A, int64_t i, int32_t j) {
   const int64_t n = A.n;
-  if (i >= n) return;
-  const int32_t j = A.partner[i];
-  if (j < 0) {
-    for (int a = 0; a < 3; ++a) {
-      A.gxi[a * n + i] = A.gxo[a * n + i];
-      A.gvi[a * n + i] = A.gvo[a * n + i] + A.dt * A.gxo[a * n + i];
-    }
-    return;
-  }
   const double xi[3] = {A.x[i], A.x[n + i], A.x[2 * n + i]};
   const double vi[3] = {A.v[i], A.v[n + i], A.v[2 * n + i]};
   const double xj[3] = {A.x[j], A.x[n + j], A.x[2 * n + j]};
@@ -228,6 +239,33 @@ __global__ void k_collide_adjoint(AdjArgs A) {
   for (int a = 0; a < 3; ++a) {
     A.gxi[a * n + i] = A.gxo[a * n + i] + gdx[a];
     A.gvi[a * n + i] = gvi_own[a] + gdv[a];
+  }
+}
+
+// One thread per particle for the free ones; the block's colliding particles are
+// queued and swept by the block's first threads together, as in k_replay.
+__global__ void __launch_bounds__(256) k_collide_adjoint(AdjArgs A) {
+  __shared__ int q_cnt;
+  __shared__ int q_i[256];
+  if (threadIdx.x == 0) q_cnt = 0;
+  __syncthreads();
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const int64_t n = A.n;
+  if (i < n) {
+    if (A.partner[i] < 0) {
+      for (int a = 0; a < 3; ++a) {
+        A.gxi[a * n + i] = A.gxo[a * n + i];
+        A.gvi[a * n + i] = A.gvo[a * n + i] + A.dt * A.gxo[a * n + i];
+      }
+    } else {
+      q_i[atomicAdd(&q_cnt, 1)] = threadIdx.x;
+    }
+  }
+  __syncthreads();
+  const int nq = q_cnt;
+  for (int e = threadIdx.x; e < nq; e += blockDim.x) {
+    const int64_t ii = (int64_t)blockIdx.x * blockDim.x + q_i[e];
+    adjoint_pair(A, ii, A.partner[ii]);
   }
 }
 

@@ -691,32 +691,25 @@ __device__ __forceinline__ double pair_time_cells(const int ci[3], const int cj[
 // index of i's partner, or -1): the contact time of the search, then the same
 // free flight and response as k_respond_f32, hence bit-identical to
 // pc_collide_f32 for the pair set it chose.
-__global__ void k_replay_f32(ReplayF32 R) {
-  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+// The replayed pair step of particle i (partner j >= 0); a pair without a root in
+// [0, dt] is recorded as PC_EREPLAY and flies free.
+__device__ __forceinline__ void replay_pair_f32(const ReplayF32& R, int64_t i, int32_t j) {
   const int64_t n = R.n;
-  if (i >= n) return;
   const int nc = R.nc;
-  const int32_t j = R.partner[i];
   int c[3];
   cell_coords(R.cell[i], nc, c);
   const float oi[3] = {R.o[i], R.o[n + i], R.o[2 * n + i]};
   const float vi[3] = {R.v[i], R.v[n + i], R.v[2 * n + i]};
   float oo[3], vo[3];
-  bool free_flight = j < 0;
-  if (!free_flight) {
-    int cj[3];
-    cell_coords(R.cell[j], nc, cj);
-    const float oj[3] = {R.o[j], R.o[n + j], R.o[2 * n + j]};
-    const float vj[3] = {R.v[j], R.v[n + j], R.v[2 * n + j]};
-    const double t = pair_time_cells(c, cj, oi, oj, vi, vj, R.r[i], R.r[j], R.dt, nc);
-    if (t <= R.dt) {
-      respond_pair_f32(c, cj, oi, oj, vi, vj, R.m[i], R.m[j], t, R.dt, R.e, nc, oo, vo);
-    } else {
-      raise_status(R.counters, PC_EREPLAY);
-      free_flight = true;
-    }
-  }
-  if (free_flight) {
+  int cj[3];
+  cell_coords(R.cell[j], nc, cj);
+  const float oj[3] = {R.o[j], R.o[n + j], R.o[2 * n + j]};
+  const float vj[3] = {R.v[j], R.v[n + j], R.v[2 * n + j]};
+  const double t = pair_time_cells(c, cj, oi, oj, vi, vj, R.r[i], R.r[j], R.dt, nc);
+  if (t <= R.dt) {
+    respond_pair_f32(c, cj, oi, oj, vi, vj, R.m[i], R.m[j], t, R.dt, R.e, nc, oo, vo);
+  } else {
+    raise_status(R.counters, PC_EREPLAY);
     const float dtn = (float)(R.dt * (double)nc);
 #pragma unroll
     for (int a = 0; a < 3; ++a) {
@@ -730,11 +723,48 @@ __global__ void k_replay_f32(ReplayF32 R) {
     R.o_out[a * n + i] = oo[a];
     R.v_out[a * n + i] = vo[a];
   }
-  if (R.r_out) R.r_out[i] = R.r[i];
-  if (R.m_out) R.m_out[i] = R.m[i];
-  if (R.id_out) R.id_out[i] = R.id[i];
-  if (R.q_out)
-    for (int q = 0; q < 4; ++q) R.q_out[q * n + i] = R.q[q * n + i];
+}
+
+// One mixed step with a given pair set, in the order of the arrays (partner[i] =
+// index of i's partner, or -1): the contact time of the search, then the same
+// free flight and response as k_respond_f32, hence bit-identical to
+// pc_collide_f32 for the pair set it chose. The block's colliding particles are
+// replayed by its first threads together, as in k_respond_f32.
+__global__ void __launch_bounds__(256) k_replay_f32(ReplayF32 R) {
+  __shared__ int q_cnt;
+  __shared__ int q_i[256];
+  if (threadIdx.x == 0) q_cnt = 0;
+  __syncthreads();
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const int64_t n = R.n;
+  const int nc = R.nc;
+  if (i < n) {
+    if (R.partner[i] < 0) {
+      int c[3];
+      cell_coords(R.cell[i], nc, c);
+      const float dtn = (float)(R.dt * (double)nc);
+#pragma unroll
+      for (int a = 0; a < 3; ++a) {
+        const float vi = R.v[a * n + i];
+        R.o_out[a * n + i] = advance_free_axis(R.o[a * n + i], vi, dtn, nc, &c[a]);
+        R.v_out[a * n + i] = vi;
+      }
+      R.cell_out[i] = (c[2] * nc + c[1]) * nc + c[0];
+    } else {
+      q_i[atomicAdd(&q_cnt, 1)] = threadIdx.x;
+    }
+    if (R.r_out) R.r_out[i] = R.r[i];
+    if (R.m_out) R.m_out[i] = R.m[i];
+    if (R.id_out) R.id_out[i] = R.id[i];
+    if (R.q_out)
+      for (int q = 0; q < 4; ++q) R.q_out[q * n + i] = R.q[q * n + i];
+  }
+  __syncthreads();
+  const int nq = q_cnt;
+  for (int e = threadIdx.x; e < nq; e += blockDim.x) {
+    const int64_t ii = (int64_t)blockIdx.x * blockDim.x + q_i[e];
+    replay_pair_f32(R, ii, R.partner[ii]);
+  }
 }
 
 struct AdjF32 {
@@ -754,21 +784,9 @@ struct AdjF32 {
 // FP64 root of the forward step (the value the step used); every derivative is
 // evaluated in FP32: t through |dx + t dv| = R (implicit function theorem),
 // n = -s/|s|, J = -m_r (1+e) dv.n, v' = v + (J/m) n, x' = x + t v + (dt - t) v'.
-__global__ void k_collide_adjoint_f32(AdjF32 A) {
-  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+__device__ __forceinline__ void adjoint_pair_f32(const AdjF32& A, int64_t i, int32_t j) {
   const int64_t n = A.n;
-  if (i >= n) return;
-  const int32_t j = A.partner[i];
   const float dtf = (float)A.dt;
-  if (j < 0) {
-#pragma unroll
-    for (int a = 0; a < 3; ++a) {
-      const float X = A.gxo[a * n + i];
-      A.gxi[a * n + i] = X;
-      A.gvi[a * n + i] = A.gvo[a * n + i] + dtf * X;
-    }
-    return;
-  }
   const int nc = A.nc;
   int ci[3], cj[3];
   cell_coords(A.cell[i], nc, ci);
@@ -854,6 +872,36 @@ __global__ void k_collide_adjoint_f32(AdjF32 A) {
   for (int a = 0; a < 3; ++a) {
     A.gxi[a * n + i] = A.gxo[a * n + i] + gdx[a];
     A.gvi[a * n + i] = gvi_own[a] + gdv[a];
+  }
+}
+
+// One thread per particle for the free ones; the block's colliding particles are
+// swept by its first threads together, as in k_replay_f32.
+__global__ void __launch_bounds__(256) k_collide_adjoint_f32(AdjF32 A) {
+  __shared__ int q_cnt;
+  __shared__ int q_i[256];
+  if (threadIdx.x == 0) q_cnt = 0;
+  __syncthreads();
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const int64_t n = A.n;
+  const float dtf = (float)A.dt;
+  if (i < n) {
+    if (A.partner[i] < 0) {
+#pragma unroll
+      for (int a = 0; a < 3; ++a) {
+        const float X = A.gxo[a * n + i];
+        A.gxi[a * n + i] = X;
+        A.gvi[a * n + i] = A.gvo[a * n + i] + dtf * X;
+      }
+    } else {
+      q_i[atomicAdd(&q_cnt, 1)] = threadIdx.x;
+    }
+  }
+  __syncthreads();
+  const int nq = q_cnt;
+  for (int e = threadIdx.x; e < nq; e += blockDim.x) {
+    const int64_t ii = (int64_t)blockIdx.x * blockDim.x + q_i[e];
+    adjoint_pair_f32(A, ii, A.partner[ii]);
   }
 }
 
