@@ -316,7 +316,10 @@ __global__ void __launch_bounds__(256, 3) k_search(SearchArgs A) {
         q_own[slot] = threadIdx.x;
         q_j[slot] = (int)j;
         mine[nmine++] = slot;
-      } else {
+      }
+      // an overflowing survivor is solved on the spot; the warp-uniform test keeps the
+      // FP64 solve from being issued predicated off on every candidate
+      if (__any_sync(__activemask(), slot >= kQCap) && slot >= kQCap) {
         ++solves;
         const double t = solve_pair(A, k, j);
         if (t <= A.dt) {

@@ -302,9 +302,11 @@ __global__ void __launch_bounds__(256, 3) k_search_f32(SearchF32 A) {
 #pragma unroll
       for (int a = 0; a < 3; ++a) dvc[a] = (vk3[a] - A.sv[a * n + j]) * Lf;
       if (!filter_cells(dxf, dvc, (rk + A.sr[j]) * Lf, dtf, vmaxc)) return;
-      if (npend < kPend) {
-        pend[npend++] = j;
-      } else {
+      const bool over = npend >= kPend;
+      if (!over) pend[npend++] = j;
+      // an overflowing survivor is solved on the spot; the warp-uniform test keeps the
+      // FP64 solve from being issued predicated off on every candidate
+      if (__any_sync(__activemask(), over) && over) {
         ++solves;
         const double t = solve_cells(A, k, j);
         if (t <= A.dt) {
