@@ -54,6 +54,7 @@ def parse():
     ap.add_argument("--no-mixed", action="store_true")
     ap.add_argument("--no-operators", action="store_true")
     ap.add_argument("--no-adjoint", action="store_true")
+    ap.add_argument("--curved", action="store_true", help="also time the 67M-particle curved-mesh workload")
     ap.add_argument("--mixed-steps", type=int, default=5)
     return ap.parse_args()
 
@@ -228,6 +229,9 @@ def run_ours(args, ws, rank, local):
     adjoint = None
     if not args.no_adjoint and args.workload == "dense_1m":
         adjoint = adjoint_run(args, w, wl, stream, torch, pc)
+    curved = None
+    if args.curved:
+        curved = curved_run(args, rank, torch, pc, stream)
     mixed = None
     if not args.no_mixed:
         mixed = mixed_run(args, rank, torch, pc, stream)
@@ -248,7 +252,7 @@ def run_ours(args, ws, rank, local):
                    "phi": round(w["phi"], 4), "l2": "inputs larger than L2 (state 105 MB + field 226 MB + scratch)",
                    "parallelism": "independent replica per GPU" if ws > 1 else "1 GPU"},
         "phase_ms_per_call": phase_ms, "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
-        "gpu_launches": launches, "clocks": clocks, "mixed": mixed, "operators": operators, "adjoint": adjoint,
+        "gpu_launches": launches, "clocks": clocks, "mixed": mixed, "operators": operators, "adjoint": adjoint, "curved": curved,
         "collide_stats": {k: st[k] for k in ("pairs", "candidates", "worklist", "rounds", "fp64_solves",
                                               "max_candidates", "cells_per_side", "stencil")},
     }
@@ -425,6 +429,53 @@ def e2e_run(args, ctx, w, n, dt, stream, torch, pc, dist, ws):
         raise RuntimeError("the downloaded field differs from the device field")
     return {"value": n * args.steps * ws / el, "unit": UNIT, "h2d_bytes_per_step": int(h2d),
             "d2h_bytes_per_step": int(d2h), "overlap": "copies on separate streams, double-buffered"}
+
+
+def curved_run(args, rank, torch, pc, stream, workload="curved_67m"):
+    """The curved-mesh workload: 67,108,864 spheres on the 128^3 degree-3 mesh curved by
+    the sine map, per step pc_collide_f32 + pc_project_curved_f32 (FP32 storage, spherical
+    cutoff, Jacobian weights, Newton localisation). Not in the default run: drawing the
+    state takes minutes on the host."""
+    wl = inputs.WORKLOADS[workload]
+    w = inputs.draw(workload, seed=rank)
+    n, dt = w["x"].shape[1], w["dt"]
+    out = {"workload": workload, "particles": n, "dt": dt, "unit": UNIT, "phi": round(w["phi"], 4)}
+    with torch.cuda.stream(stream):
+        ctx = pc.Context(n, wl.ne, wl.degree, wl.sigma, w["e"], pc.reach_of(w["r"], w["v"], dt),
+                         cutoff_sigmas=wl.cutoff_sigmas, cutoff="sphere", amp=wl.amp, stream=stream)
+        a, b = pc.StateF32.empty(n), pc.StateF32.empty(n)
+        ctx.quantize(pc.State.from_arrays(w), a)
+        field = ctx.new_field_f32()
+    del w
+    torch.cuda.synchronize()
+
+    def step(src, dst):
+        ctx.collide_f32(src, dst, dt)
+        ctx.project_curved_f32(dst, field)
+
+    for _ in range(args.warmup):
+        step(a, b)
+        a, b = b, a
+    ctx.sync()
+    ctx.set_timing(True)
+    ctx.timing()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    ev0.record(stream)
+    for _ in range(args.mixed_steps):
+        step(a, b)
+        a, b = b, a
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    ms = ev0.elapsed_time(ev1) / args.mixed_steps
+    ph = ctx.timing()
+    ctx.set_timing(False)
+    if ctx.stats()["status"] != 0:
+        raise RuntimeError("device status during the curved run")
+    out.update({"ms_per_step": ms, "value": n / (ms / 1e3),
+                "phase_ms_per_call": {k: round(v[0] / max(v[1], 1), 4) for k, v in ph.items() if v[1]}})
+    ctx.close()
+    return out
 
 
 def adjoint_run(args, w, wl, stream, torch, pc, steps=50, every=10):
