@@ -32,7 +32,8 @@ _lib = None
 def build(force=False):
     if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
         tmp = _LIB + ".tmp%d" % os.getpid()
-        subprocess.check_call(["gcc", "-O2", "-ffp-contract=off", "-fPIC", "-shared", "-o", tmp, _SRC, "-lm"])
+        subprocess.check_call(["gcc", "-O2", "-ffp-contract=off", "-fPIC", "-shared", "-pthread", "-o", tmp, _SRC,
+                               "-lm"])
         os.replace(tmp, _LIB)
     return _LIB
 
@@ -48,6 +49,7 @@ def _load():
         lib.pcgen_fixed_speed.argtypes = [i64, u64, u64, d, P]
         lib.pcgen_diameters.argtypes = [i64, u64, i32, d, d, d, d, P]
         lib.pcgen_rsa.argtypes = [i64, u64, P, P, i64, P]
+        lib.pcgen_rsa_sequential.argtypes = [i64, u64, P, P, i64, P]
         _lib = lib
     return _lib
 

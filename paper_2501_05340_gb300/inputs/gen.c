@@ -15,12 +15,17 @@
  * were drawn. A uniform hash grid with cell side >= the largest diameter keeps
  * each test to the 27 neighbouring cells.
  *
- * Build: cc -O2 -ffp-contract=off -fPIC -shared gen.c -lm
+ * Large packings are placed by speculative batches with the same result as the
+ * one-by-one process (see pcgen_rsa).
+ *
+ * Build: cc -O2 -ffp-contract=off -fPIC -shared -pthread gen.c -lm
  */
 #include <math.h>
+#include <pthread.h>
 #include <stdint.h>
 #include <stdlib.h>
 #include <string.h>
+#include <unistd.h>
 
 static uint64_t sm64_next(uint64_t* s) {
   uint64_t z = (*s += 0x9E3779B97F4A7C15ull);
@@ -144,7 +149,8 @@ static int64_t wrap_step(int64_t a, int64_t d, int64_t ng) {
   return a < 0 ? a + ng : (a >= ng ? a - ng : a);
 }
 
-int pcgen_rsa(int64_t n, uint64_t seed, const double* r, double* x, int64_t max_reject, int64_t* rejects_out) {
+static int rsa_sequential(int64_t n, uint64_t seed, const double* r, double* x, int64_t max_reject,
+                          int64_t* rejects_out) {
   if (n < 0 || !r || !x) return 1;
   if (n == 0) return 0;
   double rmax = 0.0;
@@ -232,4 +238,209 @@ int pcgen_rsa(int64_t n, uint64_t seed, const double* r, double* x, int64_t max_
   free(node);
   if (rejects_out) *rejects_out = rejects;
   return 0;
+}
+
+/* ---------------------------------------------------------- batched placement
+ *
+ * The candidate centres come from the stream in a fixed order whatever the
+ * outcomes, and the sphere a candidate is tried for is the next one still to be
+ * placed. A batch of B candidates is therefore drawn at once; worker threads
+ * test them, read-only, against the spheres placed before the batch, with the
+ * largest radius any of them can be tried for (r_hi = max of the next B radii),
+ * and keep for each candidate the spheres that overlap it at that radius (its
+ * only possible conflicts with the old spheres: fl(r_i + r_q) <= fl(r_hi + r_q)).
+ * The main thread then takes the candidates in order with the one-by-one rule:
+ * the exact test against that short list and against the spheres placed earlier
+ * in the same batch. The placements, and the count of rejected candidates, are
+ * those of the one-by-one process. */
+enum { kBatch = 8192, kList = 6 };
+
+typedef struct {
+  double c[3];
+  int64_t q[kList];
+  int nq;  /* kList + 1: more than kList conflicts, test against all old spheres */
+} rsa_cand;
+
+typedef struct {
+  int64_t ng;
+  const int64_t* head;
+  const rsa_node* node;
+  rsa_cand* cand;
+  int64_t ncand;
+  double r_hi;
+  int nthreads;
+} rsa_pool;
+
+typedef struct {
+  rsa_pool* pool;
+  int tid;
+} rsa_worker_arg;
+
+static int overlaps(double px, double py, double pz, double ri, const rsa_node* q) {
+  const double ddx = minimg(px - q->x), ddy = minimg(py - q->y), ddz = minimg(pz - q->z);
+  const double rr = ri + q->r;
+  return ddx * ddx + ddy * ddy + ddz * ddz <= rr * rr;
+}
+
+static void conflicts(const rsa_pool* P, rsa_cand* k) {
+  const int64_t ng = P->ng;
+  const double px = k->c[0], py = k->c[1], pz = k->c[2];
+  const int64_t cx = cell_index(px, ng), cy = cell_index(py, ng), cz = cell_index(pz, ng);
+  k->nq = 0;
+  for (int64_t dz = -1; dz <= 1; ++dz)
+    for (int64_t dy = -1; dy <= 1; ++dy)
+      for (int64_t dx = -1; dx <= 1; ++dx) {
+        const int64_t cell = (wrap_step(cz, dz, ng) * ng + wrap_step(cy, dy, ng)) * ng + wrap_step(cx, dx, ng);
+        for (int64_t j = P->head[cell]; j >= 0; j = P->node[j].next)
+          if (overlaps(px, py, pz, P->r_hi, &P->node[j])) {
+            if (k->nq == kList) {
+              k->nq = kList + 1;
+              return;
+            }
+            k->q[k->nq++] = j;
+          }
+      }
+}
+
+/* Conflict lists of the candidates k = tid, tid + nthreads, ... of the batch. */
+static void* rsa_worker(void* p) {
+  rsa_worker_arg* a = (rsa_worker_arg*)p;
+  const rsa_pool* P = a->pool;
+  for (int64_t k = a->tid; k < P->ncand; k += P->nthreads) conflicts(P, &P->cand[k]);
+  return NULL;
+}
+
+/* Exact one-by-one test of candidate k for radius ri: its conflict list (or all
+ * old spheres when the list overflowed) and the spheres placed since the batch
+ * began (indices >= first_new, at the heads of the cell lists of the cells marked
+ * in `touched`). */
+static int accepted(const rsa_pool* P, const rsa_cand* k, double ri, int64_t first_new, const uint64_t* touched) {
+  const int64_t ng = P->ng;
+  const double px = k->c[0], py = k->c[1], pz = k->c[2];
+  const int64_t cx = cell_index(px, ng), cy = cell_index(py, ng), cz = cell_index(pz, ng);
+  if (k->nq <= kList) {
+    for (int t = 0; t < k->nq; ++t)
+      if (overlaps(px, py, pz, ri, &P->node[k->q[t]])) return 0;
+  }
+  for (int64_t dz = -1; dz <= 1; ++dz)
+    for (int64_t dy = -1; dy <= 1; ++dy)
+      for (int64_t dx = -1; dx <= 1; ++dx) {
+        const int64_t cell = (wrap_step(cz, dz, ng) * ng + wrap_step(cy, dy, ng)) * ng + wrap_step(cx, dx, ng);
+        if (k->nq <= kList && !((touched[cell >> 6] >> (cell & 63)) & 1u)) continue;
+        for (int64_t j = P->head[cell]; j >= 0; j = P->node[j].next) {
+          if (j < first_new && k->nq <= kList) break; /* the old spheres were covered by the list */
+          if (overlaps(px, py, pz, ri, &P->node[j])) return 0;
+        }
+      }
+  return 1;
+}
+
+static int rsa_batched(int64_t n, uint64_t seed, const double* r, double* x, int64_t max_reject, int64_t* rejects_out,
+                       int nthreads) {
+  double rmax = 0.0;
+  for (int64_t i = 0; i < n; ++i) {
+    if (!(r[i] > 0.0) || r[i] >= 0.25) return 1;
+    if (r[i] > rmax) rmax = r[i];
+  }
+  int64_t ng = (int64_t)floor(1.0 / (2.0 * rmax * (1.0 + 1e-9)));
+  if (ng < 1) ng = 1;
+  while (ng > 1 && ng * ng * ng > ((int64_t)1 << 30)) --ng;
+  if (ng < 3) return rsa_sequential(n, seed, r, x, max_reject, rejects_out);
+  const int64_t ncell = ng * ng * ng;
+  int64_t* head = (int64_t*)malloc(sizeof(int64_t) * (size_t)ncell);
+  rsa_node* node = (rsa_node*)malloc(sizeof(rsa_node) * (size_t)n);
+  rsa_cand* cand = (rsa_cand*)malloc(sizeof(rsa_cand) * kBatch);
+  pthread_t* th = (pthread_t*)malloc(sizeof(pthread_t) * (size_t)nthreads);
+  rsa_worker_arg* wa = (rsa_worker_arg*)malloc(sizeof(rsa_worker_arg) * (size_t)nthreads);
+  uint64_t* touched = (uint64_t*)calloc((size_t)((ncell + 63) / 64), sizeof(uint64_t));
+  int64_t* placed_cell = (int64_t*)malloc(sizeof(int64_t) * kBatch);
+  if (!head || !node || !cand || !th || !wa || !touched || !placed_cell) {
+    free(head); free(node); free(cand); free(th); free(wa); free(touched); free(placed_cell);
+    return 4;
+  }
+  for (int64_t c = 0; c < ncell; ++c) head[c] = -1;
+  rsa_pool P;
+  P.ng = ng;
+  P.head = head;
+  P.node = node;
+  P.cand = cand;
+  P.ncand = 0;
+  P.r_hi = 0.0;
+  P.nthreads = nthreads;
+  int rc = 0;
+  uint64_t s = stream_state(seed, 1);
+  int64_t rejects = 0, i = 0;
+  while (rc == 0 && i < n) {
+    /* draw a batch; the radius bound covers every sphere it can be tried for */
+    const int64_t nb = kBatch;
+    double r_hi = 0.0;
+    for (int64_t t = i; t < n && t < i + nb; ++t)
+      if (r[t] > r_hi) r_hi = r[t];
+    for (int64_t k = 0; k < nb; ++k) {
+      cand[k].c[0] = u01(&s);
+      cand[k].c[1] = u01(&s);
+      cand[k].c[2] = u01(&s);
+    }
+    P.ncand = nb;
+    P.r_hi = r_hi;
+    /* the conflict lists, one slice per thread; a slice whose thread could not be
+       started is done here */
+    int ok[64];
+    for (int t = 1; t < nthreads; ++t) {
+      wa[t].pool = &P;
+      wa[t].tid = t;
+      ok[t] = pthread_create(&th[t], NULL, rsa_worker, &wa[t]) == 0;
+    }
+    wa[0].pool = &P;
+    wa[0].tid = 0;
+    rsa_worker(&wa[0]);
+    for (int t = 1; t < nthreads; ++t) {
+      if (ok[t])
+        pthread_join(th[t], NULL);
+      else
+        rsa_worker(&wa[t]);
+    }
+    const int64_t first_new = i;
+    int64_t nplaced = 0;
+    for (int64_t k = 0; k < nb && i < n; ++k) {
+      if (accepted(&P, &cand[k], r[i], first_new, touched)) {
+        const double px = cand[k].c[0], py = cand[k].c[1], pz = cand[k].c[2];
+        x[i] = px; x[n + i] = py; x[2 * n + i] = pz;
+        const int64_t c = (cell_index(pz, ng) * ng + cell_index(py, ng)) * ng + cell_index(px, ng);
+        node[i].x = px;
+        node[i].y = py;
+        node[i].z = pz;
+        node[i].r = r[i];
+        node[i].next = head[c];
+        head[c] = i;
+        touched[c >> 6] |= (uint64_t)1 << (c & 63);
+        placed_cell[nplaced++] = c;
+        ++i;
+      } else if (++rejects > max_reject) {
+        rc = 3;
+        break;
+      }
+    }
+    for (int64_t t = 0; t < nplaced; ++t) touched[placed_cell[t] >> 6] = 0;
+  }
+  free(head); free(node); free(cand); free(th); free(wa); free(touched); free(placed_cell);
+  if (rejects_out) *rejects_out = rejects;
+  return rc;
+}
+
+int pcgen_rsa(int64_t n, uint64_t seed, const double* r, double* x, int64_t max_reject, int64_t* rejects_out) {
+  if (n < 0 || !r || !x) return 1;
+  if (n == 0) return 0;
+  long cores = sysconf(_SC_NPROCESSORS_ONLN);
+  const char* env = getenv("PCGEN_THREADS");
+  if (env && atoi(env) > 0) cores = atoi(env);
+  const int nthreads = (int)(cores < 1 ? 1 : (cores > 64 ? 64 : cores));
+  if (n < (1 << 18) || nthreads < 2) return rsa_sequential(n, seed, r, x, max_reject, rejects_out);
+  return rsa_batched(n, seed, r, x, max_reject, rejects_out, nthreads);
+}
+
+/* The one-by-one process, for tests of the batched placement. */
+int pcgen_rsa_sequential(int64_t n, uint64_t seed, const double* r, double* x, int64_t max_reject,
+                         int64_t* rejects_out) {
+  return rsa_sequential(n, seed, r, x, max_reject, rejects_out);
 }
