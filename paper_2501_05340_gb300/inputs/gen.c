@@ -257,8 +257,8 @@ enum { kBatch = 8192, kList = 6 };
 
 typedef struct {
   double c[3];
-  int64_t q[kList];
-  int nq;  /* kList + 1: more than kList conflicts, test against all old spheres */
+  double d2[kList], rq[kList];  /* squared minimum-image distance and radius of each possible conflict */
+  int nq;                       /* kList + 1: more than kList conflicts, test against all old spheres */
 } rsa_cand;
 
 typedef struct {
@@ -276,10 +276,14 @@ typedef struct {
   int tid;
 } rsa_worker_arg;
 
-static int overlaps(double px, double py, double pz, double ri, const rsa_node* q) {
+static double dist2(double px, double py, double pz, const rsa_node* q) {
   const double ddx = minimg(px - q->x), ddy = minimg(py - q->y), ddz = minimg(pz - q->z);
+  return ddx * ddx + ddy * ddy + ddz * ddz;
+}
+
+static int overlaps(double px, double py, double pz, double ri, const rsa_node* q) {
   const double rr = ri + q->r;
-  return ddx * ddx + ddy * ddy + ddz * ddz <= rr * rr;
+  return dist2(px, py, pz, q) <= rr * rr;
 }
 
 static void conflicts(const rsa_pool* P, rsa_cand* k) {
@@ -291,14 +295,18 @@ static void conflicts(const rsa_pool* P, rsa_cand* k) {
     for (int64_t dy = -1; dy <= 1; ++dy)
       for (int64_t dx = -1; dx <= 1; ++dx) {
         const int64_t cell = (wrap_step(cz, dz, ng) * ng + wrap_step(cy, dy, ng)) * ng + wrap_step(cx, dx, ng);
-        for (int64_t j = P->head[cell]; j >= 0; j = P->node[j].next)
-          if (overlaps(px, py, pz, P->r_hi, &P->node[j])) {
+        for (int64_t j = P->head[cell]; j >= 0; j = P->node[j].next) {
+          const rsa_node* q = &P->node[j];
+          const double d2 = dist2(px, py, pz, q), rr = P->r_hi + q->r;
+          if (d2 <= rr * rr) {
             if (k->nq == kList) {
               k->nq = kList + 1;
               return;
             }
-            k->q[k->nq++] = j;
+            k->d2[k->nq] = d2;
+            k->rq[k->nq++] = q->r;
           }
+        }
       }
 }
 
@@ -319,8 +327,10 @@ static int accepted(const rsa_pool* P, const rsa_cand* k, double ri, int64_t fir
   const double px = k->c[0], py = k->c[1], pz = k->c[2];
   const int64_t cx = cell_index(px, ng), cy = cell_index(py, ng), cz = cell_index(pz, ng);
   if (k->nq <= kList) {
-    for (int t = 0; t < k->nq; ++t)
-      if (overlaps(px, py, pz, ri, &P->node[k->q[t]])) return 0;
+    for (int t = 0; t < k->nq; ++t) {
+      const double rr = ri + k->rq[t];
+      if (k->d2[t] <= rr * rr) return 0;
+    }
   }
   for (int64_t dz = -1; dz <= 1; ++dz)
     for (int64_t dy = -1; dy <= 1; ++dy)
