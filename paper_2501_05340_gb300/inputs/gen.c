@@ -248,11 +248,19 @@ static int rsa_sequential(int64_t n, uint64_t seed, const double* r, double* x, 
  * test them, read-only, against the spheres placed before the batch, with the
  * largest radius any of them can be tried for (r_hi = max of the next B radii),
  * and keep for each candidate the spheres that overlap it at that radius (its
- * only possible conflicts with the old spheres: fl(r_i + r_q) <= fl(r_hi + r_q)).
- * The main thread then takes the candidates in order with the one-by-one rule:
- * the exact test against that short list and against the spheres placed earlier
- * in the same batch. The placements, and the count of rejected candidates, are
- * those of the one-by-one process. */
+ * only possible conflicts with the old spheres: fl(r_i + r_q) <= fl(r_hi + r_q)),
+ * with their squared distances. The main thread then takes the candidates in
+ * order with the one-by-one rule: the exact test against that short list and
+ * against the spheres placed earlier in the same batch. The placements, and the
+ * count of rejected candidates, are those of the one-by-one process.
+ *
+ * The spheres are held in two grids: those up to r_cut (1.5 times the mean
+ * radius) in a fine grid of cell side >= 2 r_cut, the larger ones in a coarse
+ * grid of cell side >= 2 r_max, so that a wide size distribution does not make
+ * every search walk the long cell lists of a grid sized by its largest sphere. A
+ * search for radius R visits the fine cells within R + r_cut and the coarse cells
+ * within R + r_max of the candidate; which spheres are visited does not change
+ * the outcome of the exact test. */
 enum { kBatch = 8192, kList = 6 };
 
 typedef struct {
@@ -262,8 +270,15 @@ typedef struct {
 } rsa_cand;
 
 typedef struct {
-  int64_t ng;
-  const int64_t* head;
+  int64_t ng;     /* cells per side */
+  double r_in;    /* the largest radius held (r_cut or r_max) */
+  int64_t* head;  /* first sphere of each cell, -1 when empty */
+  uint64_t* touched; /* cells that received a sphere in the current batch */
+} rsa_grid;
+
+typedef struct {
+  rsa_grid g[2];  /* fine, coarse */
+  int ngrid;
   const rsa_node* node;
   rsa_cand* cand;
   int64_t ncand;
@@ -286,28 +301,72 @@ static int overlaps(double px, double py, double pz, double ri, const rsa_node* 
   return dist2(px, py, pz, q) <= rr * rr;
 }
 
+/* Cells of grid g to visit around p for a search radius R: offsets -s..s per axis
+ * (every cell once when 2 s + 1 covers the axis). Two points closer than D along an
+ * axis lie in cells at most floor(D ng) + 1 apart; the 1e-12 covers the rounding of
+ * the products x ng that place them in cells. */
+typedef struct {
+  int64_t lo, cnt, c0[3];
+} rsa_span;
+
+static rsa_span grid_span(const rsa_grid* g, double px, double py, double pz, double R) {
+  rsa_span sp;
+  const int64_t ng = g->ng;
+  int64_t s = (int64_t)floor((R + g->r_in) * (double)ng + 1e-12) + 1;
+  if (2 * s + 1 >= ng) {
+    sp.lo = 0;
+    sp.cnt = ng;
+    sp.c0[0] = sp.c0[1] = sp.c0[2] = -1; /* absolute cells 0 .. ng - 1 */
+  } else {
+    sp.lo = -s;
+    sp.cnt = 2 * s + 1;
+    sp.c0[0] = cell_index(px, ng);
+    sp.c0[1] = cell_index(py, ng);
+    sp.c0[2] = cell_index(pz, ng);
+  }
+  return sp;
+}
+
+static int64_t span_cell(const rsa_grid* g, const rsa_span* sp, int64_t oz, int64_t oy, int64_t ox) {
+  const int64_t ng = g->ng;
+  int64_t a[3];
+  const int64_t o[3] = {ox, oy, oz};
+  for (int d = 0; d < 3; ++d) {
+    if (sp->c0[d] < 0) {
+      a[d] = o[d];
+    } else {
+      /* |lo + o| <= s < ng / 2: one wrap at most */
+      const int64_t v = sp->c0[d] + sp->lo + o[d];
+      a[d] = v < 0 ? v + ng : (v >= ng ? v - ng : v);
+    }
+  }
+  return (a[2] * ng + a[1]) * ng + a[0];
+}
+
 static void conflicts(const rsa_pool* P, rsa_cand* k) {
-  const int64_t ng = P->ng;
   const double px = k->c[0], py = k->c[1], pz = k->c[2];
-  const int64_t cx = cell_index(px, ng), cy = cell_index(py, ng), cz = cell_index(pz, ng);
   k->nq = 0;
-  for (int64_t dz = -1; dz <= 1; ++dz)
-    for (int64_t dy = -1; dy <= 1; ++dy)
-      for (int64_t dx = -1; dx <= 1; ++dx) {
-        const int64_t cell = (wrap_step(cz, dz, ng) * ng + wrap_step(cy, dy, ng)) * ng + wrap_step(cx, dx, ng);
-        for (int64_t j = P->head[cell]; j >= 0; j = P->node[j].next) {
-          const rsa_node* q = &P->node[j];
-          const double d2 = dist2(px, py, pz, q), rr = P->r_hi + q->r;
-          if (d2 <= rr * rr) {
-            if (k->nq == kList) {
-              k->nq = kList + 1;
-              return;
+  for (int gi = 0; gi < P->ngrid; ++gi) {
+    const rsa_grid* g = &P->g[gi];
+    const rsa_span sp = grid_span(g, px, py, pz, P->r_hi);
+    for (int64_t oz = 0; oz < sp.cnt; ++oz)
+      for (int64_t oy = 0; oy < sp.cnt; ++oy)
+        for (int64_t ox = 0; ox < sp.cnt; ++ox) {
+          const int64_t cell = span_cell(g, &sp, oz, oy, ox);
+          for (int64_t j = g->head[cell]; j >= 0; j = P->node[j].next) {
+            const rsa_node* q = &P->node[j];
+            const double d2 = dist2(px, py, pz, q), rr = P->r_hi + q->r;
+            if (d2 <= rr * rr) {
+              if (k->nq == kList) {
+                k->nq = kList + 1;
+                return;
+              }
+              k->d2[k->nq] = d2;
+              k->rq[k->nq++] = q->r;
             }
-            k->d2[k->nq] = d2;
-            k->rq[k->nq++] = q->r;
           }
         }
-      }
+  }
 }
 
 /* Conflict lists of the candidates k = tid, tid + nthreads, ... of the batch. */
@@ -320,62 +379,82 @@ static void* rsa_worker(void* p) {
 
 /* Exact one-by-one test of candidate k for radius ri: its conflict list (or all
  * old spheres when the list overflowed) and the spheres placed since the batch
- * began (indices >= first_new, at the heads of the cell lists of the cells marked
- * in `touched`). */
-static int accepted(const rsa_pool* P, const rsa_cand* k, double ri, int64_t first_new, const uint64_t* touched) {
-  const int64_t ng = P->ng;
+ * began (indices >= first_new, at the heads of the lists of the touched cells). */
+static int accepted(const rsa_pool* P, const rsa_cand* k, double ri, int64_t first_new) {
   const double px = k->c[0], py = k->c[1], pz = k->c[2];
-  const int64_t cx = cell_index(px, ng), cy = cell_index(py, ng), cz = cell_index(pz, ng);
-  if (k->nq <= kList) {
+  const int listed = k->nq <= kList;
+  if (listed) {
     for (int t = 0; t < k->nq; ++t) {
       const double rr = ri + k->rq[t];
       if (k->d2[t] <= rr * rr) return 0;
     }
   }
-  for (int64_t dz = -1; dz <= 1; ++dz)
-    for (int64_t dy = -1; dy <= 1; ++dy)
-      for (int64_t dx = -1; dx <= 1; ++dx) {
-        const int64_t cell = (wrap_step(cz, dz, ng) * ng + wrap_step(cy, dy, ng)) * ng + wrap_step(cx, dx, ng);
-        if (k->nq <= kList && !((touched[cell >> 6] >> (cell & 63)) & 1u)) continue;
-        for (int64_t j = P->head[cell]; j >= 0; j = P->node[j].next) {
-          if (j < first_new && k->nq <= kList) break; /* the old spheres were covered by the list */
-          if (overlaps(px, py, pz, ri, &P->node[j])) return 0;
+  for (int gi = 0; gi < P->ngrid; ++gi) {
+    const rsa_grid* g = &P->g[gi];
+    const rsa_span sp = grid_span(g, px, py, pz, ri);
+    for (int64_t oz = 0; oz < sp.cnt; ++oz)
+      for (int64_t oy = 0; oy < sp.cnt; ++oy)
+        for (int64_t ox = 0; ox < sp.cnt; ++ox) {
+          const int64_t cell = span_cell(g, &sp, oz, oy, ox);
+          if (listed && !((g->touched[cell >> 6] >> (cell & 63)) & 1u)) continue;
+          for (int64_t j = g->head[cell]; j >= 0; j = P->node[j].next) {
+            if (j < first_new && listed) break; /* the old spheres were covered by the list */
+            if (overlaps(px, py, pz, ri, &P->node[j])) return 0;
+          }
         }
-      }
+  }
+  return 1;
+}
+
+static int grid_init(rsa_grid* g, double r_in) {
+  int64_t ng = (int64_t)floor(1.0 / (2.0 * r_in * (1.0 + 1e-9)));
+  if (ng < 1) ng = 1;
+  while (ng > 1 && ng * ng * ng > ((int64_t)1 << 28)) --ng;
+  const int64_t ncell = ng * ng * ng;
+  g->ng = ng;
+  g->r_in = r_in;
+  g->head = (int64_t*)malloc(sizeof(int64_t) * (size_t)ncell);
+  g->touched = (uint64_t*)calloc((size_t)((ncell + 63) / 64), sizeof(uint64_t));
+  if (!g->head || !g->touched) return 0;
+  for (int64_t c = 0; c < ncell; ++c) g->head[c] = -1;
   return 1;
 }
 
 static int rsa_batched(int64_t n, uint64_t seed, const double* r, double* x, int64_t max_reject, int64_t* rejects_out,
                        int nthreads) {
-  double rmax = 0.0;
+  double rmax = 0.0, rsum = 0.0;
   for (int64_t i = 0; i < n; ++i) {
     if (!(r[i] > 0.0) || r[i] >= 0.25) return 1;
     if (r[i] > rmax) rmax = r[i];
+    rsum += r[i];
   }
-  int64_t ng = (int64_t)floor(1.0 / (2.0 * rmax * (1.0 + 1e-9)));
-  if (ng < 1) ng = 1;
-  while (ng > 1 && ng * ng * ng > ((int64_t)1 << 30)) --ng;
-  if (ng < 3) return rsa_sequential(n, seed, r, x, max_reject, rejects_out);
-  const int64_t ncell = ng * ng * ng;
-  int64_t* head = (int64_t*)malloc(sizeof(int64_t) * (size_t)ncell);
+  /* two grids only when a grid sized by the largest sphere would hold many spheres
+     per cell; the fine cells hold at least the volume of one sphere per particle */
+  double r_cut = 1.5 * rsum / (double)n;
+  const double half_side = 0.5 * cbrt(1.0 / (double)n);
+  if (r_cut < half_side) r_cut = half_side;
+  const double coarse_cells = pow(floor(1.0 / (2.0 * rmax * (1.0 + 1e-9))), 3.0);
+  if (r_cut > rmax || (double)n < 8.0 * coarse_cells) r_cut = rmax;
+  rsa_pool P;
+  memset(&P, 0, sizeof(P));
+  P.ngrid = r_cut < rmax ? 2 : 1;
   rsa_node* node = (rsa_node*)malloc(sizeof(rsa_node) * (size_t)n);
   rsa_cand* cand = (rsa_cand*)malloc(sizeof(rsa_cand) * kBatch);
   pthread_t* th = (pthread_t*)malloc(sizeof(pthread_t) * (size_t)nthreads);
   rsa_worker_arg* wa = (rsa_worker_arg*)malloc(sizeof(rsa_worker_arg) * (size_t)nthreads);
-  uint64_t* touched = (uint64_t*)calloc((size_t)((ncell + 63) / 64), sizeof(uint64_t));
-  int64_t* placed_cell = (int64_t*)malloc(sizeof(int64_t) * kBatch);
-  if (!head || !node || !cand || !th || !wa || !touched || !placed_cell) {
-    free(head); free(node); free(cand); free(th); free(wa); free(touched); free(placed_cell);
+  int64_t* placed = (int64_t*)malloc(sizeof(int64_t) * 2 * kBatch); /* (grid, cell) of the batch's spheres */
+  int ok_alloc = node && cand && th && wa && placed && grid_init(&P.g[0], r_cut);
+  if (ok_alloc && P.ngrid == 2) ok_alloc = grid_init(&P.g[1], rmax);
+  if (!ok_alloc) {
+    for (int gi = 0; gi < 2; ++gi) {
+      free(P.g[gi].head);
+      free(P.g[gi].touched);
+    }
+    free(node); free(cand); free(th); free(wa); free(placed);
     return 4;
   }
-  for (int64_t c = 0; c < ncell; ++c) head[c] = -1;
-  rsa_pool P;
-  P.ng = ng;
-  P.head = head;
   P.node = node;
   P.cand = cand;
-  P.ncand = 0;
-  P.r_hi = 0.0;
   P.nthreads = nthreads;
   int rc = 0;
   uint64_t s = stream_state(seed, 1);
@@ -413,27 +492,36 @@ static int rsa_batched(int64_t n, uint64_t seed, const double* r, double* x, int
     const int64_t first_new = i;
     int64_t nplaced = 0;
     for (int64_t k = 0; k < nb && i < n; ++k) {
-      if (accepted(&P, &cand[k], r[i], first_new, touched)) {
+      if (accepted(&P, &cand[k], r[i], first_new)) {
         const double px = cand[k].c[0], py = cand[k].c[1], pz = cand[k].c[2];
         x[i] = px; x[n + i] = py; x[2 * n + i] = pz;
+        const int gi = (P.ngrid == 2 && r[i] > r_cut) ? 1 : 0;
+        rsa_grid* g = &P.g[gi];
+        const int64_t ng = g->ng;
         const int64_t c = (cell_index(pz, ng) * ng + cell_index(py, ng)) * ng + cell_index(px, ng);
         node[i].x = px;
         node[i].y = py;
         node[i].z = pz;
         node[i].r = r[i];
-        node[i].next = head[c];
-        head[c] = i;
-        touched[c >> 6] |= (uint64_t)1 << (c & 63);
-        placed_cell[nplaced++] = c;
+        node[i].next = g->head[c];
+        g->head[c] = i;
+        g->touched[c >> 6] |= (uint64_t)1 << (c & 63);
+        placed[2 * nplaced] = gi;
+        placed[2 * nplaced + 1] = c;
+        ++nplaced;
         ++i;
       } else if (++rejects > max_reject) {
         rc = 3;
         break;
       }
     }
-    for (int64_t t = 0; t < nplaced; ++t) touched[placed_cell[t] >> 6] = 0;
+    for (int64_t t = 0; t < nplaced; ++t) P.g[placed[2 * t]].touched[placed[2 * t + 1] >> 6] = 0;
   }
-  free(head); free(node); free(cand); free(th); free(wa); free(touched); free(placed_cell);
+  for (int gi = 0; gi < 2; ++gi) {
+    free(P.g[gi].head);
+    free(P.g[gi].touched);
+  }
+  free(node); free(cand); free(th); free(wa); free(placed);
   if (rejects_out) *rejects_out = rejects;
   return rc;
 }
