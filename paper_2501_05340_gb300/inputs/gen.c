@@ -533,7 +533,10 @@ int pcgen_rsa(int64_t n, uint64_t seed, const double* r, double* x, int64_t max_
   const char* env = getenv("PCGEN_THREADS");
   if (env && atoi(env) > 0) cores = atoi(env);
   const int nthreads = (int)(cores < 1 ? 1 : (cores > 64 ? 64 : cores));
-  if (n < (1 << 18) || nthreads < 2) return rsa_sequential(n, seed, r, x, max_reject, rejects_out);
+  /* PCGEN_MIN_BATCHED lowers the size from which the batched placement runs (tests) */
+  const char* mb = getenv("PCGEN_MIN_BATCHED");
+  const int64_t min_batched = (mb && atoll(mb) > 0) ? atoll(mb) : ((int64_t)1 << 18);
+  if (n < min_batched || nthreads < 2) return rsa_sequential(n, seed, r, x, max_reject, rejects_out);
   return rsa_batched(n, seed, r, x, max_reject, rejects_out, nthreads);
 }
 

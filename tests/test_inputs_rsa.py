@@ -40,3 +40,30 @@ def test_batched_stops_like_one_by_one(monkeypatch):
     b = _place("pcgen_rsa_sequential", "small_8192", 300000, 3, 1000)
     assert a[0] == b[0] == 3 and a[2] == b[2] == 1001
     assert np.array_equal(a[1], b[1])
+
+
+def test_batched_two_grids_equal_one_by_one(monkeypatch):
+    """A very wide lognormal size law (median d = 1e-3, log-sigma 1.0, 60,000 spheres):
+    the largest sphere sets a coarse grid of a few thousand cells, so the batched
+    placement holds the spheres up to 1.5x the mean radius in a fine grid (searched
+    several cells deep) and the rest in the coarse one; the packing is still the
+    one-by-one packing."""
+    lib = inputs._load()
+    n = 60000
+    d = np.zeros(n)
+    assert lib.pcgen_diameters(n, 11, 2, 1e-3, 1.0, 0.0, 0.0, inputs._p(d)) == 0
+    r = 0.5 * d
+    coarse_cells = np.floor(1.0 / (2 * r.max() * (1 + 1e-9))) ** 3
+    assert n >= 8 * coarse_cells  # the two-grid mode of the batched placement
+    out = []
+    for fn in ("pcgen_rsa", "pcgen_rsa_sequential"):
+        if fn == "pcgen_rsa":
+            monkeypatch.setenv("PCGEN_THREADS", "6")
+            monkeypatch.setenv("PCGEN_MIN_BATCHED", "1000")
+        x = np.zeros((3, n))
+        rej = np.zeros(1, np.int64)
+        rc = getattr(lib, fn)(n, 11, inputs._p(r), inputs._p(x), 50 * n, inputs._p(rej))
+        out.append((rc, x, int(rej[0])))
+    assert out[0][0] == out[1][0] == 0
+    assert out[0][2] == out[1][2]
+    assert np.array_equal(out[0][1], out[1][1])
