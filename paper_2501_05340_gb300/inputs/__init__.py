@@ -10,7 +10,9 @@ Workloads are named by what they are, with their sizes:
 * ``small_8192``   8192 monodisperse spheres d=0.02, 8^3 mesh N=3, sigma=0.02, dt=2e-3, e=0.9
 * ``dense_1m``     1,048,576 spheres d~U[0.006,0.008], 32^3 mesh N=5, sigma=0.01, e=0.9
 * ``mixed_16m``    16,777,216 spheres d lognormal(2.2e-3, 0.2) clipped [1e-3,4e-3], 64^3 mesh N=7, sigma=4e-3, e=0.85
-* ``curved_67m``   67,108,864 spheres d lognormal(1.6e-3, 0.25), 128^3 curved mesh N=3, sigma=3e-3, e=0.9
+* ``curved_67m``   67,108,864 spheres d lognormal(1.6e-3, 0.25), 128^3 curved mesh N=3, sigma=3e-3, e=0.9,
+                   placed largest first: in drawn order the largest spheres (3-4x the median) come
+                   up when the box is already near phi = 0.19 and find almost no free space left
 
 Every workload can be drawn at a reduced particle count (``n=``) with the same
 diameter law; the mesh and kernel are kept, the time step follows the same rule.
@@ -73,6 +75,7 @@ class Workload:
     cutoff: str = "box"   # "box" (separable) or "sphere"
     amp: float = 0.0      # curved-mesh amplitude (0 = affine)
     dt: float = 0.0       # 0: dt = 0.99 * 0.25 * d_min / max|v|, 3 significant figures, rounded down
+    place: str = "drawn"  # placement order: "drawn" (index order) or "largest_first" (ties by index)
 
 
 WORKLOADS = {
@@ -80,7 +83,7 @@ WORKLOADS = {
     "dense_1m": Workload("dense_1m", 1 << 20, 1, (0.006, 0.008, 0, 0), 0.9, 50, 32, 5, 0.01),
     "mixed_16m": Workload("mixed_16m", 1 << 24, 2, (2.2e-3, 0.2, 1e-3, 4e-3), 0.85, 20, 64, 7, 4e-3),
     "curved_67m": Workload("curved_67m", 1 << 26, 2, (1.6e-3, 0.25, 0.0, 0.0), 0.9, 10, 128, 3, 3e-3,
-                           cutoff="sphere", amp=0.02),
+                           cutoff="sphere", amp=0.02, place="largest_first"),
 }
 
 
@@ -105,11 +108,23 @@ def draw(workload, seed=0, n=None, max_reject=None):
     if lib.pcgen_diameters(n, seed, w.dkind, *[float(a) for a in w.dparams], _p(d)):
         raise ValueError("bad diameter law")
     r = 0.5 * d
-    x = np.zeros((3, n))
+    if w.place == "drawn":
+        perm = None
+    elif w.place == "largest_first":
+        perm = np.argsort(-r, kind="stable")
+    else:
+        raise ValueError("unknown placement order %r" % (w.place,))
+    rp = r if perm is None else np.ascontiguousarray(r[perm])
+    xp = np.zeros((3, n))
     rej = np.zeros(1, np.int64)
-    rc = lib.pcgen_rsa(n, seed, _p(r), _p(x), int(max_reject or 50 * n + 1000), _p(rej))
+    rc = lib.pcgen_rsa(n, seed, _p(rp), _p(xp), int(max_reject or 50 * n + 1000), _p(rej))
     if rc:
         raise RuntimeError("random sequential addition failed (code %d)" % rc)
+    if perm is None:
+        x = xp
+    else:
+        x = np.empty_like(xp)
+        x[:, perm] = xp
     v = np.zeros((3, n))
     lib.pcgen_normal(3 * n, seed, 3, 1.0, _p(v))
     q = np.zeros((4, n))

@@ -67,3 +67,44 @@ def test_batched_two_grids_equal_one_by_one(monkeypatch):
     assert out[0][0] == out[1][0] == 0
     assert out[0][2] == out[1][2]
     assert np.array_equal(out[0][1], out[1][1])
+
+
+def test_largest_first_placement_is_a_packing_of_the_drawn_sizes():
+    """The curved-mesh workload places its spheres largest first (ties by index), each
+    keeping its drawn diameter and index: at a reduced count the result holds the same
+    diameters as the drawn law, no two spheres overlap in the periodic box, and the
+    positions are those of the one-by-one placement of the sorted radii."""
+    n = 20000
+    w = inputs.draw("curved_67m", seed=5, n=n)
+    lib = inputs._load()
+    wl = inputs.WORKLOADS["curved_67m"]
+    d = np.zeros(n)
+    assert lib.pcgen_diameters(n, 5, wl.dkind, *[float(a) for a in wl.dparams], inputs._p(d)) == 0
+    assert np.array_equal(w["r"], 0.5 * d)
+    order = sorted(range(n), key=lambda i: (-d[i], i))
+    rs = np.ascontiguousarray(0.5 * d[order])
+    xs = np.zeros((3, n))
+    rej = np.zeros(1, np.int64)
+    assert lib.pcgen_rsa_sequential(n, 5, inputs._p(rs), inputs._p(xs), 50 * n, inputs._p(rej)) == 0
+    assert np.array_equal(w["x"][:, order], xs) and w["rejects"] == int(rej[0])
+    # no overlaps: cell list with cells no smaller than the largest diameter
+    x, r = w["x"], w["r"]
+    nc = int(1.0 / (2 * r.max()))
+    c = np.floor(x * nc).astype(np.int64) % nc
+    key = (c[2] * nc + c[1]) * nc + c[0]
+    cells = {}
+    for i, k in enumerate(key):
+        cells.setdefault(k, []).append(i)
+    worst = np.inf
+    for i in range(n):
+        for dz in (-1, 0, 1):
+            for dy in (-1, 0, 1):
+                for dx in (-1, 0, 1):
+                    k = (((c[2, i] + dz) % nc) * nc + (c[1, i] + dy) % nc) * nc + (c[0, i] + dx) % nc
+                    for j in cells.get(k, ()):
+                        if j <= i:
+                            continue
+                        dd = x[:, j] - x[:, i]
+                        dd -= np.round(dd)
+                        worst = min(worst, np.sqrt(dd @ dd) - r[i] - r[j])
+    assert worst >= 0.0, worst
