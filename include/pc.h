@@ -317,7 +317,8 @@ pc_status pc_project_curved_f32(pc_ctx* ctx, const pc_particles_f32* p, float* f
 
 /* Copy the pairs of the last pc_collide to HOST memory: ids[2k], ids[2k+1] (smaller
  * id first) and t[k], sorted by the smaller id. Writes min(cap, count) pairs and
- * the count to *npairs. Waits for the stream. */
+ * the count to *npairs. Waits for the stream. PC_ECAPACITY if the device pair count
+ * exceeds the pair buffers (n_max / 2 + 1; only after an earlier failed step). */
 pc_status pc_get_pairs(pc_ctx* ctx, int32_t* ids, double* t, int64_t cap, int64_t* npairs);
 
 /* Counters of the last pc_collide into HOST memory; returns the device status.

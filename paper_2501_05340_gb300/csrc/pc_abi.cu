@@ -359,10 +359,17 @@ pc_status pc_sync(pc_ctx* ctx) {
   e = cudaMemcpy(&st, ctx->counters + CNT_STATUS, sizeof(st), cudaMemcpyDeviceToHost);
   if (e != cudaSuccess) return PC_ECUDA;
   if (st) {
-    static const char* names[] = {"ok", "invalid particle data (position outside [0,1), radius, mass or velocity)",
-                                  "", "", "matching did not converge",
-                                  "candidate list overflow: raise cand_cap", "a bounded wait in a kernel expired"};
-    snprintf(ctx->err, sizeof(ctx->err), "device: %s", st < 7 ? names[st] : "unknown");
+    // indexed by pc_status; PC_ENOMEM and PC_ECUDA are host-side codes and never raised on the GPU
+    static const char* names[] = {"ok",
+                                  "invalid particle data (position outside [0,1), radius, mass or velocity)",
+                                  "out of memory",
+                                  "CUDA error",
+                                  "matching did not converge",
+                                  "candidate list overflow: raise cand_cap",
+                                  "a bounded wait in a kernel expired",
+                                  "a given pair has no contact within the step (replay / adjoint)"};
+    const unsigned long long nnames = sizeof(names) / sizeof(names[0]);
+    snprintf(ctx->err, sizeof(ctx->err), "device: %s", st < nnames ? names[st] : "unknown");
     const unsigned long long z = 0;
     cudaMemcpy(ctx->counters + CNT_STATUS, &z, sizeof(z), cudaMemcpyHostToDevice);
   }
@@ -395,6 +402,8 @@ pc_status pc_get_pairs(pc_ctx* ctx, int32_t* ids, double* t, int64_t cap, int64_
   if (cudaStreamSynchronize(ctx->stream) != cudaSuccess ||
       cudaMemcpy(&np, ctx->counters + CNT_PAIRS, sizeof(np), cudaMemcpyDeviceToHost) != cudaSuccess)
     return fail(ctx, PC_ECUDA, "pc_get_pairs: CUDA error");
+  if (np > (unsigned long long)(ctx->cfg.n_max / 2 + 1))
+    return fail(ctx, PC_ECAPACITY, "pc_get_pairs: pair count exceeds the pair buffers");
   std::vector<int32_t> lo(np), hi(np);
   std::vector<double> tt(np);
   if (np && (cudaMemcpy(lo.data(), ctx->pair_lo, 4 * np, cudaMemcpyDeviceToHost) != cudaSuccess ||
