@@ -118,6 +118,20 @@ def _ptr(t):
     return c_p(t.data_ptr()) if t is not None else c_p(0)
 
 
+def _dev(t, name, dtype, shape, device=None):
+    """Check that t is a contiguous CUDA tensor of dtype and shape (None matches any
+    extent) on the given CUDA device index; the library reads and writes it through a
+    raw device pointer with that layout. Returns t."""
+    ok = (isinstance(t, torch.Tensor) and t.is_cuda and t.dtype == dtype and t.is_contiguous() and
+          t.dim() == len(shape) and all(want is None or got == want for got, want in zip(t.shape, shape)) and
+          (device is None or t.device.index == device))
+    if not ok:
+        dims = ", ".join("*" if d is None else str(d) for d in shape)
+        where = "" if device is None else " on cuda:%d" % device
+        raise ValueError("%s must be a contiguous CUDA %s tensor of shape (%s)%s" % (name, dtype, dims, where))
+    return t
+
+
 class State:
     """FP64 device particle state (SoA torch tensors)."""
 
@@ -129,12 +143,18 @@ class State:
                                    ("id", id, (n,), torch.int32)):
             if tuple(t.shape) != shape or t.dtype != dt or not t.is_contiguous() or not t.is_cuda:
                 raise ValueError("State.%s must be a contiguous CUDA %s tensor of shape %s" % (name, dt, shape))
-        if q is not None and (tuple(q.shape) != (4, n) or q.dtype != torch.float64 or not q.is_contiguous()):
-            raise ValueError("State.q must be a contiguous CUDA float64 tensor of shape (4, n)")
+        if q is not None:
+            _dev(q, "State.q", torch.float64, (4, n))
+        if len({t.device for t in (x, v, r, m, id, q) if t is not None}) != 1:
+            raise ValueError("State tensors must be on one CUDA device")
 
     @property
     def n(self):
         return self.r.shape[0]
+
+    @property
+    def device(self):
+        return self.r.device.index
 
     @staticmethod
     def empty(n, device="cuda", with_q=True):
@@ -180,12 +200,18 @@ class StateF32:
                                    ("r", r, (n,), torch.float32), ("m", m, (n,), torch.float32)):
             if tuple(t.shape) != shape or t.dtype != dt or not t.is_contiguous() or not t.is_cuda:
                 raise ValueError("StateF32.%s must be a contiguous CUDA %s tensor of shape %s" % (name, dt, shape))
-        if q is not None and (tuple(q.shape) != (4, n) or q.dtype != torch.float32 or not q.is_contiguous()):
-            raise ValueError("StateF32.q must be a contiguous CUDA float32 tensor of shape (4, n)")
+        if q is not None:
+            _dev(q, "StateF32.q", torch.float32, (4, n))
+        if len({t.device for t in (id, cell, o, v, r, m, q) if t is not None}) != 1:
+            raise ValueError("StateF32 tensors must be on one CUDA device")
 
     @property
     def n(self):
         return self.r.shape[0]
+
+    @property
+    def device(self):
+        return self.r.device.index
 
     @staticmethod
     def empty(n, device="cuda", with_q=True):
@@ -233,22 +259,34 @@ class Context:
         self._h = h
         self.n1 = degree + 1
         self.ne = ne
+        self.device = torch.cuda.current_device()
 
     def _check(self, st):
         if st != PC_OK:
             raise PcError(st, library().pc_last_error(self._h).decode())
 
+    def _on(self, *states):
+        """Structs of the states, after checking that they live on the context's device."""
+        for s in states:
+            if s.device != self.device:
+                raise ValueError("particle state on cuda:%s, context on cuda:%d" % (s.device, self.device))
+        return [s.struct() for s in states]
+
+    def _t(self, t, name, dtype, shape):
+        return _dev(t, name, dtype, shape, self.device)
+
+    def _field_shape(self, nvar=4):
+        return (self.ne ** 3, nvar, self.n1 ** 3)
+
     def collide(self, src, dst, dt):
         """One collision step src -> dst (distinct states, same n)."""
-        a, b = src.struct(), dst.struct()
+        a, b = self._on(src, dst)
         self._check(library().pc_collide(self._h, ctypes.byref(a), ctypes.byref(b), float(dt)))
 
     def project(self, state, field):
         """field[ne^3, 4, n1^3] (float64, CUDA) <- projection of state.q at state.x."""
-        nel = self.ne ** 3
-        if tuple(field.shape) != (nel, 4, self.n1 ** 3) or field.dtype != torch.float64 or not field.is_contiguous():
-            raise ValueError("field must be contiguous float64 of shape (%d, 4, %d)" % (nel, self.n1 ** 3))
-        s = state.struct()
+        self._t(field, "field", torch.float64, self._field_shape())
+        (s,) = self._on(state)
         self._check(library().pc_project(self._h, ctypes.byref(s), _ptr(field)))
 
     def set_pair_policy(self, policy):
@@ -259,71 +297,73 @@ class Context:
     def collide_rot(self, src, dst, w_in, w_out, mu, dt):
         """One step with Coulomb friction mu and rotation: dst (cell-sorted) and w_out
         (angular velocities [3][n] float64 in dst's order) from src and w_in (src's order)."""
-        for w in (w_in, w_out):
-            if tuple(w.shape) != (3, src.n) or w.dtype != torch.float64 or not w.is_contiguous():
-                raise ValueError("angular velocities must be contiguous float64 of shape (3, n)")
-        a, b = src.struct(), dst.struct()
+        self._t(w_in, "w_in", torch.float64, (3, src.n))
+        self._t(w_out, "w_out", torch.float64, (3, src.n))
+        a, b = self._on(src, dst)
         self._check(library().pc_collide_rot(self._h, ctypes.byref(a), ctypes.byref(b), _ptr(w_in), _ptr(w_out),
                                              float(mu), float(dt)))
 
     def eval_field(self, state, field, out=None):
         """The DG polynomial of field [ne^3, nvar, n1^3] (float64, CUDA) at the particles:
         out [nvar, n] in state's order."""
-        nel = self.ne ** 3
-        if field.dim() != 3 or tuple(field.shape[::2]) != (nel, self.n1 ** 3) or field.dtype != torch.float64 \
-                or not field.is_contiguous():
-            raise ValueError("field must be contiguous float64 of shape (%d, nvar, %d)" % (nel, self.n1 ** 3))
+        self._t(field, "field", torch.float64, self._field_shape(None))
         nvar = field.shape[1]
         if out is None:
-            out = torch.empty(nvar, state.n, dtype=torch.float64, device="cuda")
-        s = state.struct()
+            out = torch.empty(nvar, state.n, dtype=torch.float64, device=field.device)
+        self._t(out, "out", torch.float64, (nvar, state.n))
+        (s,) = self._on(state)
         self._check(library().pc_eval_field(self._h, ctypes.byref(s), _ptr(field), int(nvar), _ptr(out)))
         return out
 
     def drag_sources(self, state, fluid, mu_f, q=None):
         """Drag sources q [4, n] = (-F, -F.v) from fluid [4, n] = (rho, u) at the particles."""
+        self._t(fluid, "fluid", torch.float64, (4, state.n))
         if q is None:
-            q = torch.empty(4, state.n, dtype=torch.float64, device="cuda")
-        s = state.struct()
+            q = torch.empty(4, state.n, dtype=torch.float64, device=fluid.device)
+        self._t(q, "q", torch.float64, (4, state.n))
+        (s,) = self._on(state)
         self._check(library().pc_drag_sources(self._h, ctypes.byref(s), _ptr(fluid), float(mu_f), _ptr(q)))
         return q
 
     def project_idw(self, state, field):
         """field <- the linear corner-node (IDW) deposition of state.q at state.x."""
-        self._check_field(field)
-        s = state.struct()
+        self._t(field, "field", torch.float64, self._field_shape())
+        (s,) = self._on(state)
         self._check(library().pc_project_idw(self._h, ctypes.byref(s), _ptr(field)))
 
     def project_dirac(self, state, field):
         """field <- the nearest-DOF (Dirac) deposition of state.q at state.x."""
-        self._check_field(field)
-        s = state.struct()
+        self._t(field, "field", torch.float64, self._field_shape())
+        (s,) = self._on(state)
         self._check(library().pc_project_dirac(self._h, ctypes.byref(s), _ptr(field)))
-
-    def _check_field(self, field):
-        nel = self.ne ** 3
-        if tuple(field.shape) != (nel, 4, self.n1 ** 3) or field.dtype != torch.float64 or not field.is_contiguous():
-            raise ValueError("field must be contiguous float64 of shape (%d, 4, %d)" % (nel, self.n1 ** 3))
 
     def partner_by_id(self, n_ids, out=None):
         """Device int32 [n_ids]: the partner id of each id in the last collide, or -1."""
         if out is None:
-            out = torch.empty(n_ids, dtype=torch.int32, device="cuda")
+            out = torch.empty(n_ids, dtype=torch.int32, device="cuda:%d" % self.device)
+        self._t(out, "out", torch.int32, (n_ids,))
         self._check(library().pc_pairs_to_partner(self._h, _ptr(out), int(n_ids)))
         return out
 
     def collide_replay(self, src, dst, partner, dt):
         """One step with a fixed pair set (partner: int32 [n], index in the same order)."""
-        a, b = src.struct(), dst.struct()
+        self._t(partner, "partner", torch.int32, (src.n,))
+        a, b = self._on(src, dst)
         self._check(library().pc_collide_replay(self._h, ctypes.byref(a), ctypes.byref(b), _ptr(partner), float(dt)))
 
     def collide_adjoint(self, pre, partner, dt, gx_out, gv_out, gx_in, gv_in):
-        a = pre.struct()
+        self._t(partner, "partner", torch.int32, (pre.n,))
+        for name, g in (("gx_out", gx_out), ("gv_out", gv_out), ("gx_in", gx_in), ("gv_in", gv_in)):
+            self._t(g, name, torch.float64, (3, pre.n))
+        (a,) = self._on(pre)
         self._check(library().pc_collide_adjoint(self._h, ctypes.byref(a), _ptr(partner), float(dt), _ptr(gx_out),
                                                  _ptr(gv_out), _ptr(gx_in), _ptr(gv_in)))
 
     def project_adjoint(self, state, G, gq, gx):
-        a = state.struct()
+        self._t(G, "G", torch.float64, self._field_shape())
+        self._t(gq, "gq", torch.float64, (4, state.n))
+        self._t(gx, "gx", torch.float64, (3, state.n))
+        (a,) = self._on(state)
         self._check(library().pc_project_adjoint(self._h, ctypes.byref(a), _ptr(G), _ptr(gq), _ptr(gx)))
 
     @property
@@ -332,50 +372,53 @@ class Context:
 
     def quantize(self, src, dst):
         """FP64 State -> FP32 cell-relative StateF32 (same order)."""
-        a, b = src.struct(), dst.struct()
+        a, b = self._on(src, dst)
         self._check(library().pc_quantize(self._h, ctypes.byref(a), ctypes.byref(b)))
 
     def collide_f32(self, src, dst, dt):
-        a, b = src.struct(), dst.struct()
+        a, b = self._on(src, dst)
         self._check(library().pc_collide_f32(self._h, ctypes.byref(a), ctypes.byref(b), float(dt)))
 
     def collide_replay_f32(self, src, dst, partner, dt):
         """One mixed step with a fixed pair set (partner: int32 [n], index in the same order)."""
-        a, b = src.struct(), dst.struct()
+        self._t(partner, "partner", torch.int32, (src.n,))
+        a, b = self._on(src, dst)
         self._check(library().pc_collide_replay_f32(self._h, ctypes.byref(a), ctypes.byref(b), _ptr(partner),
                                                     float(dt)))
 
     def collide_adjoint_f32(self, pre, partner, dt, gx_out, gv_out, gx_in, gv_in):
-        a = pre.struct()
+        self._t(partner, "partner", torch.int32, (pre.n,))
+        for name, g in (("gx_out", gx_out), ("gv_out", gv_out), ("gx_in", gx_in), ("gv_in", gv_in)):
+            self._t(g, name, torch.float32, (3, pre.n))
+        (a,) = self._on(pre)
         self._check(library().pc_collide_adjoint_f32(self._h, ctypes.byref(a), _ptr(partner), float(dt),
                                                      _ptr(gx_out), _ptr(gv_out), _ptr(gx_in), _ptr(gv_in)))
 
     def project_adjoint_f32(self, state, G, gq, gx):
-        a = state.struct()
+        self._t(G, "G", torch.float32, self._field_shape())
+        self._t(gq, "gq", torch.float32, (4, state.n))
+        self._t(gx, "gx", torch.float32, (3, state.n))
+        (a,) = self._on(state)
         self._check(library().pc_project_adjoint_f32(self._h, ctypes.byref(a), _ptr(G), _ptr(gq), _ptr(gx)))
 
     def project_f32(self, state, field, tc="f16"):
         """FP32 field[ne^3, 4, n1^3] <- tensor-core projection (tc = "f16" or "bf16")."""
-        nel = self.ne ** 3
-        if tuple(field.shape) != (nel, 4, self.n1 ** 3) or field.dtype != torch.float32 or not field.is_contiguous():
-            raise ValueError("field must be contiguous float32 of shape (%d, 4, %d)" % (nel, self.n1 ** 3))
-        s = state.struct()
+        self._t(field, "field", torch.float32, self._field_shape())
+        (s,) = self._on(state)
         t = PC_TC_BF16 if tc == "bf16" else PC_TC_F16
         self._check(library().pc_project_f32(self._h, ctypes.byref(s), _ptr(field), t))
 
     def project_curved_f32(self, state, field):
         """FP32 field <- projection on the curved mesh (context made with cutoff="sphere", amp > 0)."""
-        nel = self.ne ** 3
-        if tuple(field.shape) != (nel, 4, self.n1 ** 3) or field.dtype != torch.float32 or not field.is_contiguous():
-            raise ValueError("field must be contiguous float32 of shape (%d, 4, %d)" % (nel, self.n1 ** 3))
-        s = state.struct()
+        self._t(field, "field", torch.float32, self._field_shape())
+        (s,) = self._on(state)
         self._check(library().pc_project_curved_f32(self._h, ctypes.byref(s), _ptr(field)))
 
     def new_field_f32(self):
-        return torch.empty(self.ne ** 3, 4, self.n1 ** 3, dtype=torch.float32, device="cuda")
+        return torch.empty(self._field_shape(), dtype=torch.float32, device="cuda:%d" % self.device)
 
     def new_field(self):
-        return torch.empty(self.ne ** 3, 4, self.n1 ** 3, dtype=torch.float64, device="cuda")
+        return torch.empty(self._field_shape(), dtype=torch.float64, device="cuda:%d" % self.device)
 
     def pairs(self):
         """Pairs of the last collide: (ids[k, 2] smaller first, t[k]) sorted by the smaller id."""
@@ -430,6 +473,7 @@ def project_noalloc(state, field, ne, degree, sigma, cutoff_sigmas=3.0, stream=N
         stream = torch.cuda.current_stream()
     cfg = PcConfig(0, int(ne), int(degree), float(sigma), float(cutoff_sigmas), 0, 0.0, 0.0, 0,
                    c_p(stream.cuda_stream), 0.0)
+    _dev(field, "field", torch.float64, (ne ** 3, 4, (degree + 1) ** 3), state.device)
     s = state.struct()
     msg = ctypes.create_string_buffer(256)
     st = library().pc_project_noalloc(ctypes.byref(cfg), ctypes.byref(s), _ptr(field), msg, 256)

@@ -46,3 +46,27 @@ def test_argument_validation_without_gpu():
     assert lib.pc_collide(None, None, None, 1e-3) == pc.PC_EINVAL
     assert lib.pc_project(None, None, None) == pc.PC_EINVAL
     lib.pc_destroy(None)
+
+
+def test_binding_rejects_host_and_misshaped_tensors():
+    """The binding hands raw device pointers to the library, so it refuses host tensors,
+    other dtypes, non-contiguous views and wrong shapes before any call (the library
+    cannot tell a host pointer from a device one)."""
+    torch = pytest.importorskip("torch")
+    from paper_2501_05340_gb300 import pc
+    host = torch.zeros(3, 5, dtype=torch.float64)
+    with pytest.raises(ValueError, match="CUDA"):
+        pc._dev(host, "w_in", torch.float64, (3, 5))
+    n = 5
+    f64 = lambda *s: torch.zeros(*s, dtype=torch.float64)
+    with pytest.raises(ValueError, match="State.x"):
+        pc.State(f64(3, n), f64(3, n), f64(n), f64(n), torch.zeros(n, dtype=torch.int32))
+    with pytest.raises(ValueError, match="StateF32.id"):
+        pc.StateF32(torch.zeros(n, dtype=torch.int32), torch.zeros(n, dtype=torch.int32),
+                    torch.zeros(3, n), torch.zeros(3, n), torch.zeros(n), torch.zeros(n))
+    # the shape test itself, on a tensor that passes every other check but residence
+    t = f64(4, n).t()
+    assert not t.is_contiguous()
+    for bad, shape in ((f64(4, n), (3, n)), (f64(4, n), (4, n, 1)), (t, (n, 4))):
+        with pytest.raises(ValueError):
+            pc._dev(bad, "q", torch.float64, shape)

@@ -46,7 +46,7 @@ def test_noalloc_matches_project_twice():
 def test_noalloc_rejects_oversized_problem():
     n = 200000  # about 476 bytes per particle on a 32^3 mesh of degree 5: beyond 32 MiB
     a = pc.State.empty(n)
-    f = torch.empty(1, dtype=torch.float64, device="cuda")
+    f = torch.empty(32 ** 3, 4, 6 ** 3, dtype=torch.float64, device="cuda")
     with pytest.raises(pc.PcError) as ei:
         pc.project_noalloc(a, f, 32, 5, 0.01, 3.0)
     assert ei.value.status == pc.PC_ECAPACITY
