@@ -25,6 +25,20 @@ def test_replay_equals_search_step_bitwise():
     assert np.array_equal(x1, x2) and np.array_equal(v1, v2)
 
 
+def test_replay_counts_contact_at_the_end_of_the_step():
+    """Contact exactly at t = dt counts (the inclusive bound of the search step): two
+    spheres of radius 1/32 head-on at unit speed, 1/8 apart, meet at t = 1/32 exactly in
+    binary arithmetic; with dt = 1/32 the replay of that pair succeeds and equals the
+    search step bit for bit."""
+    x = np.array([[0.25, 0.375], [0.5, 0.5], [0.5, 0.5]])
+    v = np.array([[1.0, -1.0], [0.0, 0.0], [0.0, 0.0]])
+    r, m, ids, dt = np.full(2, 0.03125), np.array([1.0, 2.0]), np.arange(2, dtype=np.int32), 0.03125
+    x1, v1, partner, tc, k = oracle.collide_step(x, v, r, m, ids, 0.7, dt)
+    assert k == 1 and tc[0] == dt
+    x2, v2 = oracle.collide_replay(x, v, r, m, np.array([1, 0]), 0.7, dt)
+    assert np.array_equal(x2, x1) and np.array_equal(v2, v1)
+
+
 def _torch_replay(x, v, r, m, partner, e, dt):
     """Plain torch float64 restatement of one step with a fixed matching (test only)."""
     n = x.shape[1]

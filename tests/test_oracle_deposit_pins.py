@@ -154,3 +154,25 @@ def test_dirac_source_on_a_gauss_node():
     assert np.allclose(F[e, :, g], q[:, 0] / W[g], rtol=1e-14)
     F[e, :, g] = 0
     assert not F.any()
+
+
+@pytest.mark.parametrize("degree", [1, 3, 5, 7])
+def test_dirac_tie_goes_to_the_lower_node(degree):
+    """Reading of the nearest-DOF deposition: a source exactly halfway between two nodes of
+    an axis goes to the lower one. With an even node count the element centre (reference
+    coordinate exactly 0) is halfway between the two middle nodes on every axis (the rule's
+    nodes are symmetric bit for bit, checked first): the whole source lands on node
+    (a, a, a), a = n1/2 - 1, of that element, as q / (w_a^3 (h/2)^3), and nowhere else."""
+    ne, n1 = 3, degree + 1
+    eta, w = oracle.gauss_legendre(n1)
+    a = n1 // 2 - 1
+    assert eta[a] == -eta[a + 1]
+    x = np.full((3, 1), 0.5)  # centre of element (1, 1, 1)
+    q = np.array([[2.0], [-1.0], [0.5], [3.0]])
+    F = oracle.project_dirac(x, q, ne, degree)
+    e = (1 * ne + 1) * ne + 1
+    g = (a * n1 + a) * n1 + a
+    h = 1.0 / ne
+    expect = np.zeros_like(F)
+    expect[e, :, g] = q[:, 0] / (w[a] ** 3 * (h / 2) ** 3)
+    assert np.allclose(F, expect, rtol=1e-14, atol=0)

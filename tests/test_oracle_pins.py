@@ -191,6 +191,40 @@ def test_cell_list_equals_bruteforce_adversarial():
             assert np.array_equal(u, z)
 
 
+def test_cell_list_reaches_fast_head_on_pairs():
+    """Sec. 4.3 reach: two spheres can meet within dt from up to 2 r_max + 2 v_max dt apart.
+    Small spheres (the velocity term dominates the reach) in head-on pairs at the
+    fastest speed, their centres 0.17-0.19 apart along x, y, z and diagonals, with dt = 0.1
+    (reach 0.202), among slow background spheres: the cell list finds what brute force
+    finds, every fast pair included. Cells sized with half the velocity term miss pairs."""
+    rng = np.random.default_rng(11)
+    r0, vmax, dt = 1e-3, 1.0, 0.1
+    nb = 300
+    xs, vs, fast = [rng.random((3, nb))], [rng.normal(0, 0.01, (3, nb))], []
+    dirs = [(1, 0, 0), (0, 1, 0), (0, 0, 1), (1, 1, 0), (1, -1, 1), (0, 1, -1)]
+    for k in range(24):
+        u = np.array(dirs[k % len(dirs)], float)
+        u /= np.linalg.norm(u)
+        d = rng.uniform(0.17, 0.19)
+        c = rng.random(3)
+        a, b = c - 0.5 * d * u, c + 0.5 * d * u
+        xs.append(np.stack([a, b], 1))
+        vs.append(np.stack([vmax * u, -vmax * u], 1))
+        fast.append((nb + 2 * k, nb + 2 * k + 1))
+    x = np.concatenate(xs, 1)
+    x -= np.floor(x)
+    x[x >= 1.0] = 0.0
+    v = np.concatenate(vs, 1)
+    n = x.shape[1]
+    r = np.full(n, r0)
+    a = oracle.candidates(x, v, r, dt, "cells")
+    b = oracle.candidates(x, v, r, dt, "bruteforce")
+    for u_, z in zip(a, b):
+        assert np.array_equal(u_, z)
+    found = set(zip(a[0].tolist(), a[1].tolist()))
+    assert all(p in found for p in fast), [p for p in fast if p not in found]
+
+
 # ----------------------------------------------------------------- matching
 
 def _is_greedy(n, ids, ci, cj, ct, partner):
