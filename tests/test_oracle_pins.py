@@ -569,6 +569,41 @@ def test_cellrel_free_flight_carry():
     assert c1[2] == cell[2] and np.array_equal(o1[:, 2], o[:, 2])
 
 
+def test_cellrel_tiny_negative_offset_stays_in_the_cell():
+    """Free flight to an offset of -2^-30 cells: adding one cell rounds to exactly 1.0 in
+    FP32, so the offset is set to 0 in the same cell (an offset of 1.0 would leave [0, 1));
+    the stored position is within FP32 rounding of the exact one."""
+    nc = 10
+    cell = np.array([3 + 10 * (4 + 10 * 5)], np.int32)
+    o = np.full((3, 1), 0.5, np.float32)
+    o[0, 0] = 2.0 ** -30
+    v = np.zeros((3, 1), np.float32)
+    v[0, 0] = -(2.0 ** -29)
+    c1, o1, v1, p, tc, k = oracle.collide_step_cellrel(cell, o, v, np.full(1, 1e-3, np.float32),
+                                                       np.ones(1, np.float32), np.zeros(1, np.int32), nc, 1.0, 0.1)
+    assert k == 0 and c1[0] == cell[0] and o1[0, 0] == 0.0
+    assert np.all((o1 >= 0.0) & (o1 < 1.0))
+
+
+def test_cellrel_collision_across_the_lower_face():
+    """A pair that collides near x = 0: after the exchange (e = 1, equal masses) the
+    struck sphere leaves through the lower face and wraps to cell nc - 1 of the
+    periodic box; equal to the FP64 step on the dequantized state."""
+    nc = 10
+    x = np.array([[0.03, 0.045], [0.5, 0.5], [0.5, 0.5]])
+    cell, o = oracle.quantize(x, nc)
+    v = np.array([[0.0, -2.0], [0.0, 0.0], [0.0, 0.0]], np.float32)
+    r, m, ids, dt = np.full(2, 0.002, np.float32), np.ones(2, np.float32), np.arange(2, dtype=np.int32), 0.03
+    c1, o1, v1, p1, tc1, k1 = oracle.collide_step_cellrel(cell, o, v, r, m, ids, nc, 1.0, dt)
+    x2, v2, p2, tc2, k2 = oracle.collide_step(oracle.dequantize(cell, o, nc), v.astype(np.float64),
+                                              r.astype(np.float64), m.astype(np.float64), ids, 1.0, dt)
+    assert k1 == k2 == 1 and np.array_equal(p1, p2)
+    assert c1[0] % nc == nc - 1 and abs(x2[0, 0] - 0.981) < 1e-6
+    d = oracle.dequantize(c1, o1, nc) - x2
+    d -= np.round(d)
+    assert np.max(np.abs(d)) * nc < 1e-6
+
+
 def test_cellrel_momentum_conserved_to_storage_rounding():
     w = inputs.draw("dense_1m", n=2500, seed=22)
     nc = 25

@@ -30,11 +30,16 @@ def _ranks(x, ids, ncell):
     return rank
 
 
-@pytest.mark.parametrize("seed,ncell,mult", [(0, 12, 10), (1, 7, 20), (2, 20, 10)])
-def test_first_found_characterisation(seed, ncell, mult):
+@pytest.mark.parametrize("seed,ncell,mult,shuffle", [(0, 12, 10, False), (1, 7, 20, False), (2, 20, 10, False),
+                                                  (3, 7, 20, True)])
+def test_first_found_characterisation(seed, ncell, mult, shuffle):
+    """shuffle: ids are a random permutation of the indices, so that order by id and
+    order by index differ inside a cell."""
     d = inputs.draw("small_8192", seed=seed, n=3000)
     dt = mult * d["dt"]
     x, v, r, m, ids = d["x"], d["v"], d["r"], d["m"], d["id"]
+    if shuffle:
+        ids = np.random.default_rng(seed).permutation(len(ids)).astype(np.int32)
     x1, v1, partner, tc, k = oracle.collide_step_sfc(x, v, r, m, ids, 0.9, dt, ncell)
     ci, cj, ct = oracle.candidates(x, v, r, dt)
     assert k > 30 and len(ci) > k
