@@ -75,6 +75,55 @@ def test_collide_f32_bit_identical(name, n, dtmul):
     assert total > 0
 
 
+def _ctx_10_cells(n):
+    """A context whose collision grid has 10 cells per side (reach hint 0.095)."""
+    ctx = pc.Context(n, 8, 3, 0.02, 1.0, 0.095)
+    assert ctx.cells_per_side == 10
+    return ctx
+
+
+def test_collide_f32_tiny_negative_offset_stays_in_the_cell():
+    """Free flight to an offset of -2^-30 cells (dt nc = 1, v = -2^-29): adding one cell
+    rounds to 1.0 in FP32, so the offset becomes 0 in the same cell, as in the oracle."""
+    ctx = _ctx_10_cells(4)
+    d = dict(id=np.arange(4, dtype=np.int32), cell=np.array([3 + 10 * (4 + 10 * 5), 1, 222, 777], np.int32),
+             o=np.full((3, 4), 0.5, np.float32), v=np.zeros((3, 4), np.float32), r=np.full(4, 1e-3, np.float32),
+             m=np.ones(4, np.float32), q=np.zeros((4, 4), np.float32))
+    d["o"][0, 0] = 2.0 ** -30
+    d["v"][0, 0] = -(2.0 ** -29)
+    a, b = pc.StateF32.from_arrays(d), pc.StateF32.empty(4)
+    ctx.collide_f32(a, b, 0.1)
+    ctx.sync()
+    c1, o1, v1, partner, tc, k = oracle.collide_step_cellrel(d["cell"], d["o"], d["v"], d["r"], d["m"], d["id"], 10,
+                                                             1.0, 0.1)
+    g = by_id(b.numpy())
+    assert k == 0 and c1[0] == d["cell"][0] and o1[0, 0] == 0.0
+    assert np.array_equal(g["cell"], c1) and np.array_equal(g["o"], o1) and np.array_equal(g["v"], v1)
+
+
+def test_collide_f32_pair_wraps_through_the_lower_face():
+    """A pair colliding near x = 0 (e = 1, equal masses): the struck sphere leaves through
+    the lower face and wraps to cell 9 of 10; pair, cells, offsets and velocities
+    bit-identical to the oracle's cell-relative step."""
+    ctx = _ctx_10_cells(2)
+    w = dict(x=np.array([[0.03, 0.045], [0.5, 0.5], [0.5, 0.5]]), v=np.array([[0.0, -2.0], [0.0, 0.0], [0.0, 0.0]]),
+             r=np.full(2, 0.002), m=np.ones(2), id=np.arange(2, dtype=np.int32), q=np.zeros((4, 2)))
+    a = mixed_state(w, ctx)
+    b = pc.StateF32.empty(2)
+    cur = by_id(a.numpy())
+    ctx.collide_f32(a, b, 0.03)
+    ctx.sync()
+    gids, gt = ctx.pairs()
+    c1, o1, v1, partner, tc, k = oracle.collide_step_cellrel(cur["cell"], cur["o"], cur["v"], cur["r"], cur["m"],
+                                                             cur["id"], 10, 1.0, 0.03)
+    oids, ot = oracle_pairs(partner, tc, cur["id"])
+    assert k == 1 and c1[0] % 10 == 9
+    assert np.array_equal(gids, oids) and np.array_equal(gt, ot)
+    g = by_id(b.numpy())
+    for key, ref in (("cell", c1), ("o", o1), ("v", v1)):
+        assert np.array_equal(g[key], ref), key
+
+
 def _oracle_field_of(s32np, nc, wl, ne=None):
     x = oracle.dequantize(s32np["cell"], s32np["o"], nc)
     return oracle.project(x, s32np["q"].astype(np.float64), ne or wl.ne, wl.degree, wl.sigma, wl.cutoff_sigmas)[0]
