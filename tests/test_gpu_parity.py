@@ -119,6 +119,21 @@ def test_pair_across_periodic_corner():
     assert k == 1
 
 
+def test_free_flight_wraps_tiny_negative_positions_to_zero():
+    """Free flight across x = 0 by less than half an ulp of 1: y - floor(y) rounds to 1.0,
+    which the wrap maps to 0.0 (as in the oracle), so every coordinate stays in [0, 1);
+    one ordinary wrap across x = 1 beside it."""
+    x = np.array([[0.0, 0.9995, 1e-17], [0.2, 0.5, 0.7], [0.3, 0.5, 0.1]])
+    v = np.array([[-1e-20, 0.002, -1e-16], [0.0, 0.0, 0.0], [0.0, 0.0, 0.0]])
+    d = dict(x=x, v=v, r=np.full(3, 1e-3), m=np.ones(3), id=np.array([2, 0, 1], np.int32), q=np.ones((4, 3)))
+    a, b = pc.State.from_arrays(d), pc.State.empty(3)
+    ctx = pc.Context(3, 8, 3, 0.02, 0.9, pc.reach_of(d["r"], v, 0.5))
+    nxt, k = compare_collide_step(ctx, a, b, by_id(dict(d)), 0.5, 0.9)
+    g = b.numpy()
+    assert k == 0 and np.all((g["x"] >= 0.0) & (g["x"] < 1.0))
+    assert nxt["x"][0, 1] == 0.0 and nxt["x"][0, 2] == 0.0  # ids 1 and 2
+
+
 def test_clustered_cells():
     """Many particles in few cells (high occupancy, many candidates per particle)."""
     w = inputs.draw("dense_1m", seed=5, n=3000)
