@@ -72,6 +72,40 @@ def test_dense_full_size_step_bit_identical_and_differs_from_earliest():
     assert not np.array_equal(sfc_pairs, earliest)
 
 
+@pytest.mark.parametrize("policy", ["sfc_first", "earliest"])
+def test_rollout_with_permuted_ids(policy):
+    """Ids a random permutation of the indices, so that order by id and order by index
+    differ inside every cell (the curve rank, the per-cell order and the tie-breaks use
+    ids): 5 steps of 4000 spheres at 10x the time step, pairs, times, x and v bit-identical
+    to the oracle's step of the same policy."""
+    w = inputs.draw("small_8192", seed=5, n=4000)
+    dt = 10 * w["dt"]
+    ctx = _ctx(w, 4000, dt)
+    ctx.set_pair_policy(policy)
+    ids = np.random.default_rng(5).permutation(4000).astype(np.int32)
+    cur = by_id({"x": w["x"], "v": w["v"], "r": w["r"], "m": w["m"], "id": ids})
+    total = 0
+    for _ in range(5):
+        src = pc.State.from_arrays(cur, with_q=False)
+        dst = pc.State.empty(src.n, with_q=False)
+        ctx.collide(src, dst, dt)
+        ctx.sync()
+        gids, gt = ctx.pairs()
+        if policy == "sfc_first":
+            x1, v1, partner, tc, k = oracle.collide_step_sfc(cur["x"], cur["v"], cur["r"], cur["m"], cur["id"],
+                                                             w["e"], dt, ctx.cells_per_side)
+        else:
+            x1, v1, partner, tc, k = oracle.collide_step(cur["x"], cur["v"], cur["r"], cur["m"], cur["id"], w["e"], dt)
+        oids, ot = oracle_pairs(partner, tc, cur["id"])
+        assert np.array_equal(gids, oids) and np.array_equal(gt, ot)
+        g = by_id(dst.numpy())
+        assert np.array_equal(g["x"], x1) and np.array_equal(g["v"], v1)
+        cur = dict(cur)
+        cur["x"], cur["v"] = x1, v1
+        total += k
+    assert total > 100
+
+
 def test_unknown_policy_is_rejected():
     w = inputs.draw("small_8192", seed=2, n=100)
     ctx = _ctx(w, 100, w["dt"])
