@@ -83,7 +83,7 @@ def test_rollout_with_permuted_ids(policy):
     ctx = _ctx(w, 4000, dt)
     ctx.set_pair_policy(policy)
     ids = np.random.default_rng(5).permutation(4000).astype(np.int32)
-    cur = by_id({"x": w["x"], "v": w["v"], "r": w["r"], "m": w["m"], "id": ids})
+    cur = {"x": w["x"], "v": w["v"], "r": w["r"], "m": w["m"], "id": ids}  # index order, ids permuted
     total = 0
     for _ in range(5):
         src = pc.State.from_arrays(cur, with_q=False)
@@ -98,8 +98,8 @@ def test_rollout_with_permuted_ids(policy):
             x1, v1, partner, tc, k = oracle.collide_step(cur["x"], cur["v"], cur["r"], cur["m"], cur["id"], w["e"], dt)
         oids, ot = oracle_pairs(partner, tc, cur["id"])
         assert np.array_equal(gids, oids) and np.array_equal(gt, ot)
-        g = by_id(dst.numpy())
-        assert np.array_equal(g["x"], x1) and np.array_equal(g["v"], v1)
+        g, o = by_id(dst.numpy()), by_id({"x": x1, "v": v1, "id": cur["id"]})
+        assert np.array_equal(g["x"], o["x"]) and np.array_equal(g["v"], o["v"])
         cur = dict(cur)
         cur["x"], cur["v"] = x1, v1
         total += k
