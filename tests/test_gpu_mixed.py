@@ -75,6 +75,38 @@ def test_collide_f32_bit_identical(name, n, dtmul):
     assert total > 0
 
 
+def test_collide_f32_permuted_ids():
+    """Ids a random permutation of the indices, the state kept in index order (order by
+    id and by index differ inside every cell): 4 steps of 3000 spheres of the mixed law,
+    pairs, times, cells, offsets and velocities bit-identical, compared by id."""
+    w = inputs.draw("mixed_16m", seed=4, n=3000)
+    w["id"] = np.random.default_rng(4).permutation(3000).astype(np.int32)
+    dt = 60 * w["dt"]
+    ctx = pc.Context(3000, w["workload"].ne, w["workload"].degree, w["workload"].sigma, w["e"],
+                     pc.reach_of(w["r"], w["v"], dt))
+    nc = ctx.cells_per_side
+    a = mixed_state(w, ctx)
+    b = pc.StateF32.empty(3000)
+    cur = a.numpy()
+    total = 0
+    for _ in range(4):
+        ctx.collide_f32(a, b, dt)
+        ctx.sync()
+        gids, gt = ctx.pairs()
+        cell, o, v, partner, tc, k = oracle.collide_step_cellrel(cur["cell"], cur["o"], cur["v"], cur["r"], cur["m"],
+                                                                 cur["id"], nc, w["e"], dt)
+        oids, ot = oracle_pairs(partner, tc, cur["id"])
+        assert np.array_equal(gids, oids) and np.array_equal(gt, ot)
+        g, ref = by_id(b.numpy()), by_id(dict(cell=cell, o=o, v=v, id=cur["id"]))
+        for key in ("cell", "o", "v"):
+            assert np.array_equal(g[key], ref[key]), key
+        cur = dict(cur)
+        cur["cell"], cur["o"], cur["v"] = cell, o, v
+        total += k
+        a, b = b, a
+    assert total > 0
+
+
 def _ctx_10_cells(n):
     """A context whose collision grid has 10 cells per side (reach hint 0.095)."""
     ctx = pc.Context(n, 8, 3, 0.02, 1.0, 0.095)
