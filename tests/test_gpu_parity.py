@@ -64,6 +64,26 @@ def test_small_rollout_bit_identical():
     assert total > 1000
 
 
+@pytest.mark.parametrize("e", [0.0, 1.0])
+def test_restitution_limits_rollout(e):
+    """Perfectly inelastic (e = 0: the pair leaves with equal normal velocities) and
+    elastic (e = 1) collisions: 20 steps of 4000 spheres at 5x the time step, every step
+    bit-identical."""
+    w = dict(inputs.draw("small_8192", seed=8, n=4000))
+    w["e"] = e
+    dt = 5 * w["dt"]
+    a = pc.State.from_arrays(w)
+    b = pc.State.empty(a.n)
+    ctx = make_ctx(w, a.n, dt)
+    cur = {k: w[k] for k in ("x", "v", "r", "m", "id", "q")}
+    total = 0
+    for _ in range(20):
+        cur, k = compare_collide_step(ctx, a, b, cur, dt, e)
+        total += k
+        a, b = b, a
+    assert total > 100
+
+
 def test_dense_full_size_steps_bit_identical():
     """1,048,576 spheres (phi ~0.19) at the full size: 3 steps, every pair and bit."""
     w = inputs.draw("dense_1m", seed=1)
