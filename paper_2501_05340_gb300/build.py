@@ -6,6 +6,7 @@ FP64 contact solve and response; double-float arithmetic that places every FMA
 explicitly); the others with the default contraction.
 """
 import os
+import shutil
 import subprocess
 import sys
 
@@ -53,15 +54,26 @@ def up_to_date():
 
 
 def build(force=False, verbose=False, extra=()):
-    """Build libpc.so if any source is newer; returns its path. Raises on failure."""
+    """Build libpc.so if any source is newer; returns its path. Raises on failure.
+
+    Each process compiles into its own object folder and replaces the library
+    atomically, so processes that build at the same time do not mix objects."""
     if not force and up_to_date():
         return LIB
-    os.makedirs(BUILD, exist_ok=True)
+    objdir = os.path.join(BUILD, "p%d" % os.getpid())
+    os.makedirs(objdir, exist_ok=True)
+    try:
+        return _compile_and_link(objdir, verbose, extra)
+    finally:
+        shutil.rmtree(objdir, ignore_errors=True)
+
+
+def _compile_and_link(objdir, verbose, extra):
     nvcc = _nvcc()
     procs = []
     objs = []
     for unit, flags in UNITS.items():
-        obj = os.path.join(BUILD, unit.replace(".cu", ".o"))
+        obj = os.path.join(objdir, unit.replace(".cu", ".o"))
         cmd = [nvcc] + ARCH + COMMON + list(flags) + list(extra) + ["-c", os.path.join(CSRC, unit), "-o", obj]
         if verbose:
             print(" ".join(cmd))
