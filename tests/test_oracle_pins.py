@@ -534,14 +534,17 @@ def test_quantize_carries_an_offset_that_rounds_to_one():
     """Quantisation rule of the FP32 cell-relative storage: an offset s - floor(s) that
     rounds to 1.0 in FP32 is stored as offset 0 in the next cell, wrapping from n_c - 1 to
     0 (on a power-of-two grid s = x n_c is exact, so the offset 1 - 2^-40 reaches the
-    cast); dequantising gives x back within FP32 rounding of one cell."""
+    cast); dequantising gives a position in [0, 1) within FP32 rounding of one cell of x
+    (modulo the periodic wrap)."""
     nc = 8
     x = np.array([[(3 + 1 - 2.0 ** -40) / nc, (nc - 2.0 ** -40) / nc, 0.5625], [0.5] * 3, [0.5] * 3])
     assert list(np.floor(x[0] * nc)) == [3.0, 7.0, 4.0]
     cell, o = oracle.quantize(x, nc)
     assert list(cell % nc) == [4, 0, 4] and list(o[0]) == [0.0, 0.0, 0.5]
     assert np.all((o >= 0.0) & (o < 1.0))
-    d = oracle.dequantize(cell, o, nc) - x
+    xd = oracle.dequantize(cell, o, nc)
+    assert np.all((xd >= 0.0) & (xd < 1.0))  # in the box itself, not only modulo 1
+    d = xd - x
     d -= np.round(d)
     assert np.abs(d).max() * nc <= 2.0 ** -24
 
