@@ -70,3 +70,23 @@ def test_binding_rejects_host_and_misshaped_tensors():
     for bad, shape in ((f64(4, n), (3, n)), (f64(4, n), (4, n, 1)), (t, (n, 4))):
         with pytest.raises(ValueError):
             pc._dev(bad, "q", torch.float64, shape)
+
+
+def test_every_entry_point_rejects_a_null_context():
+    """Every function the header declares has its argument types set in the binding and
+    refuses a NULL context (or configuration) with PC_EINVAL before any CUDA call; the
+    three non-status functions return their documented values."""
+    from paper_2501_05340_gb300 import pc
+    lib = pc.library()
+    names = _declared()
+    special = {"pc_cells_per_side": 0, "pc_last_error": b"null context", "pc_destroy": None}
+    for name in sorted(names):
+        f = getattr(lib, name)
+        assert f.argtypes is not None, "%s has no argtypes in the binding" % name
+        args = [0.0 if t is ctypes.c_double else 0 if t in (ctypes.c_int, ctypes.c_int32, ctypes.c_int64) else None
+                for t in f.argtypes]
+        got = f(*args)
+        if name in special:
+            assert got == special[name], name
+        else:
+            assert got == pc.PC_EINVAL, (name, got)
