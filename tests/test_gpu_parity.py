@@ -3,6 +3,8 @@
 Collisions: pair sets, contact times, positions and velocities bit-identical.
 Projection: fields within 1e-12 normwise per component (max |F - F_ref| / max |F_ref|).
 """
+import ctypes
+
 import numpy as np
 import pytest
 
@@ -152,6 +154,24 @@ def test_free_flight_wraps_tiny_negative_positions_to_zero():
     g = b.numpy()
     assert k == 0 and np.all((g["x"] >= 0.0) & (g["x"] < 1.0))
     assert nxt["x"][0, 1] == 0.0 and nxt["x"][0, 2] == 0.0  # ids 1 and 2
+
+
+def test_get_pairs_copies_a_prefix_and_reports_the_count():
+    """pc_get_pairs with a capacity below the pair count writes the first pairs of the
+    sorted list and still reports the full count."""
+    w = inputs.draw("small_8192", seed=9, n=3000)
+    dt = 10 * w["dt"]
+    ctx = make_ctx(w, 3000, dt)
+    a, b = pc.State.from_arrays(w), pc.State.empty(3000)
+    ctx.collide(a, b, dt)
+    ctx.sync()
+    ids, t = ctx.pairs()
+    assert len(ids) > 10
+    part_ids, part_t, cnt = np.zeros(10, np.int32), np.zeros(5), ctypes.c_int64()
+    st = pc.library().pc_get_pairs(ctx._h, part_ids.ctypes.data_as(ctypes.c_void_p),
+                                   part_t.ctypes.data_as(ctypes.c_void_p), 5, ctypes.byref(cnt))
+    assert st == pc.PC_OK and cnt.value == len(ids)
+    assert np.array_equal(part_ids.reshape(5, 2), ids[:5]) and np.array_equal(part_t, t[:5])
 
 
 def test_clustered_cells():
