@@ -136,3 +136,20 @@ def test_free_particles_keep_spin_and_fly():
     ref = d["x"] + 1e-3 * d["v"]
     ref -= np.floor(ref)
     assert np.allclose(x1, ref, rtol=0, atol=1e-15)
+
+
+def test_head_on_without_spin_has_no_tangential_impulse():
+    """A head-on collision of non-spinning spheres: the contact-point velocity is exactly
+    normal (|v_rt| = 0), so friction adds no tangential impulse whatever mu: the response
+    is the frictionless one bit for bit and the spins stay zero (no 0/0 direction)."""
+    x = np.array([[0.5, 0.504], [0.5, 0.5], [0.5, 0.5]])
+    v = np.array([[1.0, -1.0], [0.0, 0.0], [0.0, 0.0]])
+    r, m, ids = np.full(2, 0.001), np.array([1.0, 3.0]), np.arange(2, dtype=np.int32)
+    dt = 0.01
+    t = oracle.contact_time(x[:, 0], x[:, 1], v[:, 0], v[:, 1], r[0], r[1], dt)
+    assert 0 < t <= dt
+    partner, tc = np.array([1, 0]), np.array([t, t])
+    x0, v0 = oracle.respond_advance(x, v, m, partner, tc, 0.9, dt)
+    x1, v1, w1 = oracle.respond_advance_rot(x, v, np.zeros((3, 2)), r, m, ids, partner, tc, 0.9, 0.3, dt)
+    assert np.all(np.isfinite(v1)) and np.array_equal(v1, v0) and np.array_equal(x1, x0)
+    assert not w1.any()

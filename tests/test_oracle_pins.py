@@ -51,6 +51,10 @@ def test_contact_time_inclusive_dt_and_rejections():
     assert math.isinf(oracle.contact_time(xi, xj, [0, 1, 0], [0, 1, 0], 0.03125, 0.03125, 1.0))  # no relative motion
     # grazing: the closest approach is exactly R -> double root, no collision
     assert math.isinf(oracle.contact_time([0.5, 0.5, 0.5], [0.5, 0.75, 0.5], [0, 0, 0], [1, 0, 0], 0.125, 0.125, 10.0))
+    # grazing while approaching (b < 0): offset exactly R across the line of motion, binary-exact
+    # values, so b^2 - a c is exactly 0: a double root, no collision
+    assert math.isinf(oracle.contact_time([0.375, 0.5625, 0.5], [0.5, 0.5, 0.5], [1, 0, 0], [0, 0, 0], 0.03125,
+                                          0.03125, 1.0))
 
 
 def test_contact_time_across_periodic_face():
@@ -225,6 +229,42 @@ def test_cell_list_reaches_fast_head_on_pairs():
     assert all(p in found for p in fast), [p for p in fast if p not in found]
 
 
+def test_cell_list_at_the_reach_limit():
+    """A head-on pair 0.20005 apart with reach 2 r + 2 v dt = 0.20008 (dt = 0.09904): the
+    grid has 4 cells per side (1 / reach = 4.998); the pair meets within the step and the
+    cell list finds it, as brute force does. A grid sized from a reach only 0.1 % smaller
+    has 5 cells per side and puts the two spheres 2 cells apart."""
+    x = np.array([[0.19995, 0.40], [0.5, 0.5], [0.5, 0.5]])
+    v = np.array([[1.0, -1.0], [0.0, 0.0], [0.0, 0.0]])
+    r, dt = np.full(2, 1e-3), 0.09904
+    reach = 2 * 1e-3 + 2 * 1.0 * dt
+    assert int(1.0 / reach) == 4 and int(1.0 / (0.999 * reach)) == 5
+    a = oracle.candidates(x, v, r, dt, "cells")
+    b = oracle.candidates(x, v, r, dt, "bruteforce")
+    assert len(a[0]) == 1 and (a[0][0], a[1][0]) == (0, 1)
+    for u, z in zip(a, b):
+        assert np.array_equal(u, z)
+
+
+@pytest.mark.parametrize("target_reach", [0.45, 0.8])
+def test_cell_list_with_fewer_than_three_cells(target_reach):
+    """A reach above 1/3 leaves fewer than 3 cells per side, where the 27-cell stencil
+    would visit a cell more than once: the candidates still equal brute force, each pair
+    once."""
+    rng = np.random.default_rng(int(target_reach * 100))
+    n = 500
+    x = rng.random((3, n))
+    v = rng.normal(size=(3, n))
+    r = np.full(n, 0.015)
+    vmax = float(np.sqrt((v * v).sum(0)).max())
+    dt = (target_reach - 0.03) / (2 * vmax)
+    a = oracle.candidates(x, v, r, dt, "cells")
+    b = oracle.candidates(x, v, r, dt, "bruteforce")
+    assert len(a[0]) > 5
+    for u, z in zip(a, b):
+        assert np.array_equal(u, z)
+
+
 # ----------------------------------------------------------------- matching
 
 def _is_greedy(n, ids, ci, cj, ct, partner):
@@ -282,6 +322,18 @@ def test_matching_chains():
     assert list(p) == [1, 0, -1]
     p, t, k = oracle.match(np.array([5, 1, 0], np.int32), [0, 1], [1, 2], [1e-3, 1e-3], 3)
     assert list(p) == [-1, 2, 1]
+
+
+def test_matching_rounds_one_pair_per_round():
+    """A path 0-1-2-3-4-5 whose contact times grow along it: each round of mutual earliest
+    picks commits exactly one pair ((0,1), then (2,3), then (4,5)), and the rounds must go
+    on until no free particle has a free candidate; the result equals the greedy matching."""
+    ids = np.arange(6, dtype=np.int32)
+    ci, cj, ct = [0, 1, 2, 3, 4], [1, 2, 3, 4, 5], [1e-3, 2e-3, 3e-3, 4e-3, 5e-3]
+    pg, tg, kg = oracle.match(ids, ci, cj, ct, 6)
+    pr, tr, kr, rounds = oracle.match(ids, ci, cj, ct, 6, method="rounds")
+    assert list(pg) == [1, 0, 3, 2, 5, 4] and kg == 3
+    assert np.array_equal(pr, pg) and np.array_equal(tr, tg) and kr == 3 and rounds == 3
 
 
 # ----------------------------------------------------------------- response
@@ -513,6 +565,80 @@ def test_curved_projection_affine_limit_and_conservation():
                                 oracle.mesh_map(xi, 0.02)[1]
     tot = np.einsum("ecg,eg->c", Fc, Wg)
     assert np.all(np.abs(tot - w["q"].sum(axis=1)) <= 1e-12 * np.abs(w["q"]).sum(axis=1))
+
+
+@pytest.mark.parametrize("cutoff", ["box", "sphere"])
+def test_cutoff_is_inclusive_at_exactly_rc(cutoff):
+    """Reading: the cutoff is inclusive (<= 3 sigma, box or sphere). A particle on the x
+    line of a Gauss node with x - X exactly -r_c in FP64 (and equal y, z): that node takes
+    the weight exp(-r_c^2 / (2 sigma^2)) / Z in the forward projection, and in the adjoint a
+    unit dL/dfield at that node gives dL/dq_0 = K / Z."""
+    ne, degree, sigma, cs = 4, 3, 0.02, 3.0
+    n1 = degree + 1
+    rc = cs * sigma
+    eta, _ = oracle.gauss_legendre(n1)
+    h = 1.0 / ne
+    i, j, k = 1, 2, 1
+    X = [(1 + 0.5 * (eta[a] + 1.0)) * h for a in (i, j, k)]  # node (i, j, k) of element (1, 1, 1)
+    xp0 = X[0] - rc
+    for step in range(64):
+        if X[0] - xp0 == rc:
+            break
+        xp0 = np.nextafter(xp0, -np.inf if X[0] - xp0 < rc else np.inf)
+    assert X[0] - xp0 == rc
+    x = np.array([[xp0], [X[1]], [X[2]]])
+    q = np.array([[1.0], [2.0], [3.0], [4.0]])
+    F, Z = oracle.project(x, q, ne, degree, sigma, cs, cutoff=cutoff)
+    e, g = (1 * ne + 1) * ne + 1, (k * n1 + j) * n1 + i
+    K = math.exp(-(rc * rc) * (1.0 / (2.0 * sigma * sigma)))
+    assert K > 0 and Z[0] > 0
+    assert np.allclose(F[e, :, g], q[:, 0] * K / Z[0], rtol=1e-13, atol=0)
+    G = np.zeros_like(F)
+    G[e, 0, g] = 1.0
+    gq, _ = oracle.project_adjoint(x, q, G, ne, degree, sigma, cs, cutoff=cutoff)
+    assert gq[0, 0] == pytest.approx(K / Z[0], rel=1e-13)
+
+
+def test_curved_projection_equals_an_all_node_brute_force():
+    """Curved mesh (amp = 0.02, sphere cutoff): the projection equals a brute force over
+    every node of the mesh (physical node positions from the mapping, weights with det J,
+    Z summed over all nodes), so no node whose physical distance is within r_c is missed
+    by the logical-coordinate scan."""
+    ne, degree, sigma, cs, amp = 6, 2, 0.02, 3.0, 0.02
+    n1 = degree + 1
+    rng = np.random.default_rng(17)
+    n = 40
+    x, q = rng.random((3, n)), rng.normal(size=(4, n))
+    F, _ = oracle.project(x, q, ne, degree, sigma, cs, cutoff="sphere", amp=amp)
+    eta, om = np.polynomial.legendre.leggauss(n1)
+    h = 1.0 / ne
+    Xg = np.zeros((ne ** 3, n1 ** 3, 3))
+    Wg = np.zeros((ne ** 3, n1 ** 3))
+    for ez in range(ne):
+        for ey in range(ne):
+            for ex in range(ne):
+                e = (ez * ne + ey) * ne + ex
+                for kk in range(n1):
+                    for jj in range(n1):
+                        for ii in range(n1):
+                            xi = np.array([(ex + 0.5 * (eta[ii] + 1)) * h, (ey + 0.5 * (eta[jj] + 1)) * h,
+                                           (ez + 0.5 * (eta[kk] + 1)) * h])
+                            Xp, dj = oracle.mesh_map(xi, amp)
+                            g = (kk * n1 + jj) * n1 + ii
+                            Xg[e, g] = Xp
+                            Wg[e, g] = om[ii] * om[jj] * om[kk] * (h / 2) ** 3 * dj
+    R = np.zeros_like(F)
+    rc = cs * sigma
+    for p in range(n):
+        d = Xg - x[:, p]
+        d -= np.round(d)
+        d2 = (d * d).sum(-1)
+        K = np.where(d2 <= rc * rc, np.exp(-d2 / (2 * sigma * sigma)), 0.0)
+        Zp = (Wg * K).sum()
+        if Zp > 0:
+            R += q[:, p][None, :, None] * (K / Zp)[:, None, :]
+    err = np.abs(F - R).max(axis=(0, 2)) / np.abs(R).max(axis=(0, 2))
+    assert np.all(err <= 1e-12), err
 
 
 def test_curved_map_special_points():
