@@ -88,6 +88,18 @@ def test_rollout_with_permuted_ids():
     assert total > 100
 
 
+def test_head_on_without_spin_has_no_tangential_impulse():
+    """A head-on pair of non-spinning spheres with mu = 0.3: the tangential contact
+    velocity is exactly zero, so there is no tangential impulse (no 0/0 direction); bit-
+    identical to the oracle, finite, and the spins stay zero."""
+    w = dict(x=np.array([[0.5, 0.504], [0.5, 0.5], [0.5, 0.5]]), v=np.array([[1.0, -1.0], [0.0, 0.0], [0.0, 0.0]]),
+             r=np.full(2, 0.001), m=np.array([1.0, 3.0]), id=np.arange(2, dtype=np.int32), e=0.9)
+    ctx = pc.Context(2, 8, 3, 0.02, 0.9, pc.reach_of(w["r"], w["v"], 0.01))
+    cur = {k: w[k] for k in ("x", "v", "r", "m", "id")}
+    nxt, spins, k = _step(ctx, cur, np.zeros((3, 2)), 0.3, 0.01, 0.9)
+    assert k == 1 and np.all(np.isfinite(nxt["v"])) and not spins.any()
+
+
 def test_dense_full_size_step_bit_identical():
     """1,048,576 spheres of the dense workload, mu = 0.2, one step: every pair and bit."""
     w = inputs.draw("dense_1m", seed=2)

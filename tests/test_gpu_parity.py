@@ -174,6 +174,22 @@ def test_get_pairs_copies_a_prefix_and_reports_the_count():
     assert np.array_equal(part_ids.reshape(5, 2), ids[:5]) and np.array_equal(part_t, t[:5])
 
 
+def test_grazing_double_root_is_not_a_collision():
+    """A sphere passing another at exactly R while approaching (binary-exact values, so
+    b^2 - a c is exactly 0): a double root, no collision; beside it a head-on pair that
+    does collide. Pairs, times, x and v bit-identical to the oracle."""
+    x = np.array([[0.375, 0.5, 0.125, 0.1875], [0.5625, 0.5, 0.125, 0.125], [0.5, 0.5, 0.875, 0.875]])
+    v = np.array([[1.0, 0.0, 0.5, -0.5], [0.0, 0.0, 0.0, 0.0], [0.0, 0.0, 0.0, 0.0]])
+    d = dict(x=x, v=v, r=np.array([0.03125, 0.03125, 0.0078125, 0.0078125]), m=np.array([1.0, 2.0, 1.0, 1.5]),
+             id=np.arange(4, dtype=np.int32), q=np.ones((4, 4)))
+    a, b = pc.State.from_arrays(d), pc.State.empty(4)
+    ctx = pc.Context(4, 8, 3, 0.02, 0.9, pc.reach_of(d["r"], v, 0.2))
+    _, k = compare_collide_step(ctx, a, b, by_id(dict(d)), 0.2, 0.9)
+    assert k == 1
+    ids, t = ctx.pairs()
+    assert ids.tolist() == [[2, 3]] and t[0] == 0.046875
+
+
 def test_clustered_cells():
     """Many particles in few cells (high occupancy, many candidates per particle)."""
     w = inputs.draw("dense_1m", seed=5, n=3000)
