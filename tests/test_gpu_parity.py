@@ -190,6 +190,43 @@ def test_grazing_double_root_is_not_a_collision():
     assert ids.tolist() == [[2, 3]] and t[0] == 0.046875
 
 
+def test_chain_matched_one_pair_per_round():
+    """Six spheres in a row, each faster to the right than its right neighbour, with gaps
+    growing along the row: contact times grow along the chain, so the matching rounds
+    commit one pair per round ((0,1), then (2,3), then (4,5)); bit-identical to the oracle."""
+    gaps = [0.010, 0.012, 0.014, 0.016, 0.018]
+    r0 = 0.01
+    xs = [0.2]
+    for g in gaps:
+        xs.append(xs[-1] + 2 * r0 + g)
+    n = 6
+    x = np.array([xs, [0.5] * n, [0.5] * n])
+    v = np.array([[-0.5 * i for i in range(n)], [0.0] * n, [0.0] * n])
+    d = dict(x=x, v=v, r=np.full(n, r0), m=np.ones(n), id=np.arange(n, dtype=np.int32), q=np.ones((4, n)))
+    a, b = pc.State.from_arrays(d), pc.State.empty(n)
+    ctx = pc.Context(n, 8, 3, 0.02, 0.9, pc.reach_of(d["r"], v, 0.05))
+    _, k = compare_collide_step(ctx, a, b, by_id(dict(d)), 0.05, 0.9)
+    assert k == 3
+    assert ctx.pairs()[0].tolist() == [[0, 1], [2, 3], [4, 5]]
+
+
+@pytest.mark.parametrize("target_reach", [0.45, 0.8])
+def test_reach_spanning_the_box(target_reach):
+    """A step whose reach exceeds a third of the box: the grid keeps 3 cells per side and
+    the stencil covers every cell once; pairs, times, x and v bit-identical to the oracle."""
+    rng = np.random.default_rng(int(target_reach * 100))
+    n = 500
+    d = dict(x=rng.random((3, n)), v=rng.normal(size=(3, n)), r=np.full(n, 0.015), m=rng.uniform(0.5, 2.0, n),
+             id=np.arange(n, dtype=np.int32), q=rng.normal(size=(4, n)))
+    vmax = float(np.sqrt((d["v"] ** 2).sum(0)).max())
+    dt = (target_reach - 0.03) / (2 * vmax)
+    a, b = pc.State.from_arrays(d), pc.State.empty(n)
+    ctx = pc.Context(n, 8, 3, 0.02, 0.9, pc.reach_of(d["r"], d["v"], dt))
+    assert ctx.cells_per_side == 3
+    _, k = compare_collide_step(ctx, a, b, by_id(dict(d)), dt, 0.9)
+    assert k > 5
+
+
 def test_clustered_cells():
     """Many particles in few cells (high occupancy, many candidates per particle)."""
     w = inputs.draw("dense_1m", seed=5, n=3000)
