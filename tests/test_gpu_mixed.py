@@ -107,6 +107,33 @@ def test_collide_f32_permuted_ids():
     assert total > 0
 
 
+@pytest.mark.parametrize("target_reach", [0.45, 0.8])
+def test_collide_f32_reach_spanning_the_box(target_reach):
+    """Mixed path with a reach above a third of the box: 3 cells per side, the stencil
+    covers every cell once; pairs, times, cells, offsets and velocities bit-identical."""
+    rng = np.random.default_rng(int(target_reach * 100) + 1)
+    n = 500
+    w = dict(x=rng.random((3, n)), v=rng.normal(size=(3, n)), r=np.full(n, 0.015), m=rng.uniform(0.5, 2.0, n),
+             id=np.arange(n, dtype=np.int32), q=rng.normal(size=(4, n)))
+    vmax = float(np.sqrt((w["v"] ** 2).sum(0)).max())
+    dt = (target_reach - 0.03) / (2 * vmax)
+    ctx = pc.Context(n, 8, 3, 0.02, 0.9, pc.reach_of(w["r"], w["v"], dt))
+    assert ctx.cells_per_side == 3
+    a = mixed_state(w, ctx)
+    b = pc.StateF32.empty(n)
+    cur = by_id(a.numpy())
+    ctx.collide_f32(a, b, dt)
+    ctx.sync()
+    gids, gt = ctx.pairs()
+    cell, o, v, partner, tc, k = oracle.collide_step_cellrel(cur["cell"], cur["o"], cur["v"], cur["r"], cur["m"],
+                                                             cur["id"], 3, 0.9, dt)
+    oids, ot = oracle_pairs(partner, tc, cur["id"])
+    assert k > 5 and np.array_equal(gids, oids) and np.array_equal(gt, ot)
+    g = by_id(b.numpy())
+    for key, ref in (("cell", cell), ("o", o), ("v", v)):
+        assert np.array_equal(g[key], ref), key
+
+
 def _ctx_10_cells(n):
     """A context whose collision grid has 10 cells per side (reach hint 0.095)."""
     ctx = pc.Context(n, 8, 3, 0.02, 1.0, 0.095)
