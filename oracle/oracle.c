@@ -81,8 +81,8 @@ static double minimg_box(double d, double L) {
 
 /* Reading of the garbled Eq. collision-detect 2: dx_p = x_1 - x_2 and
  * dv_p = v_1 - v_2. With a = dv.dv, b = dx.dv, c = dx.dx - R^2 the roots of
- * a t^2 + 2 b t + c = 0 are both positive iff c > 0 and b < 0 (this is also the
- * "particles approach" rule), real and distinct iff b^2 - a c > 0 (a grazing
+ * a t^2 + 2 b t + c = 0 are both positive iff c > 0 and b < 0 (b < 0 also says the
+ * pair is closing in), real and distinct iff b^2 - a c > 0 (a grazing
  * double root carries no normal velocity). The smaller root is written as
  * c / (-b + sqrt(b^2 - a c)), the cancellation-free form of (-b - sqrt(.))/a.
  * The root must satisfy t <= dt (inclusive). */
@@ -326,8 +326,8 @@ static double wrap01(double y) {
 
 /* Frictionless hard-sphere response. With s = dx + t dv the contact vector
  * (from particle j to particle i, dx = minimg(x_i - x_j), dv = v_i - v_j),
- * n = -s/|s| is the unit normal from i to j (Sec. 2.4: "from particle 1 to
- * particle 2"). v_r = v_i - v_j, m_r = m_i m_j/(m_i + m_j),
+ * n = -s/|s| is the unit normal from i to j (Sec. 2.4 points the normal from the
+ * first sphere of the pair to the second). v_r = v_i - v_j, m_r = m_i m_j/(m_i + m_j),
  * J = -m_r (1 + e) (v_r . n), v_i' = v_i + (J/m_i) n, v_j' = v_j - (J/m_j) n.
  * Reading of the garbled position update of Sec. 3.3: the particle moves with
  * its old velocity to the contact point and with its new one for the rest of
