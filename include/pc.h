@@ -168,8 +168,9 @@ pc_status pc_collide_rot(pc_ctx* ctx, const pc_particles* in, pc_particles* out,
  * Accuracy: within 1e-12 of the exact sum, normwise per component. */
 pc_status pc_project(pc_ctx* ctx, const pc_particles* p, double* field);
 
-/* Linear corner-node deposition (Sec. 2.3: the C0 linear form of inverse distance
- * weighting onto the corner nodes of the host element; Sec. 4.2: corner nodes with
+/* Linear corner-node deposition (Sec. 2.3: the continuous, linear variant of inverse
+ * distance weighting, each source spread over the 8 vertices of the element that
+ * contains it; Sec. 4.2: corner nodes with
  * unique periodic ids, deposition radius one element) on the affine mesh. A
  * particle at reference position xi in [-1,1]^3 of its element (xi_a = 2 (x_a ne -
  * e_a) - 1) gives q[c][p] w_d(xi) to corner d of the element, w_d(xi) =

@@ -1,7 +1,6 @@
 /*
  * CPU oracle for the particle collision and projection operator of
- * Schwarz, Kopper, de Staercke, Beck, "Efficient computation of particle-fluid and
- * particle-particle interactions in compressible flow" (arXiv 2501.05340).
+ * arXiv 2501.05340 (Schwarz, Kopper, de Staercke, Beck).
  *
  * TEST INFRASTRUCTURE ONLY. Plain, slow, FP64 C code that states what the GPU
  * path must compute. Only the tests, the smoke check and the benchmark's CPU
