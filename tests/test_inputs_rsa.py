@@ -108,3 +108,49 @@ def test_largest_first_placement_is_a_packing_of_the_drawn_sizes():
                         dd -= np.round(dd)
                         worst = min(worst, np.sqrt(dd @ dd) - r[i] - r[j])
     assert worst >= 0.0, worst
+
+
+def _min_gap(x, r):
+    """Smallest surface gap over all pairs in the periodic unit cube (cell list, vectorised)."""
+    n = x.shape[1]
+    nc = max(1, int(1.0 / (2 * r.max() * (1 + 1e-9))))
+    c = np.floor(x * nc).astype(np.int64) % nc
+    key = (c[2] * nc + c[1]) * nc + c[0]
+    order = np.argsort(key, kind="stable")
+    ks = key[order]
+    starts = np.searchsorted(ks, np.arange(nc ** 3))
+    ends = np.searchsorted(ks, np.arange(nc ** 3), side="right")
+    worst = np.inf
+    for i in range(n):
+        for dz in (-1, 0, 1):
+            for dy in (-1, 0, 1):
+                for dx in (-1, 0, 1):
+                    k = (((c[2, i] + dz) % nc) * nc + (c[1, i] + dy) % nc) * nc + (c[0, i] + dx) % nc
+                    js = order[starts[k]:ends[k]]
+                    js = js[js > i]
+                    if len(js):
+                        d = x[:, js] - x[:, i:i + 1]
+                        d -= np.round(d)
+                        gap = np.sqrt((d * d).sum(0)) - r[i] - r[js]
+                        worst = min(worst, float(gap.min()))
+    return worst
+
+
+@pytest.mark.parametrize("name,n", [("small_8192", 8192), ("dense_1m", 20000), ("mixed_16m", 20000),
+                                    ("curved_67m", 20000)])
+def test_every_workload_draw_is_a_valid_state(name, n):
+    """Each workload's draw (at a reduced count where the full one is large): positions in
+    [0, 1), no two spheres overlapping or touching in the periodic cube, ids 0..n-1,
+    m = pi d^3 / 6, the time-step rule, and the reported volume fraction."""
+    w = inputs.draw(name, seed=1, n=n)
+    x, r = w["x"], w["r"]
+    assert x.shape == (3, n) and w["v"].shape == (3, n) and w["q"].shape == (4, n)
+    assert np.all((x >= 0.0) & (x < 1.0))
+    assert np.array_equal(w["id"], np.arange(n, dtype=np.int32))
+    assert np.allclose(w["m"], np.pi / 6 * (2 * r) ** 3, rtol=1e-15, atol=0)
+    assert _min_gap(x, r) > 0.0
+    assert abs(w["phi"] - float((np.pi / 6 * (2 * r) ** 3).sum())) <= 1e-12
+    wl = w["workload"]
+    if wl.dt == 0:
+        assert w["dt"] == inputs.dt_rule(2 * r, w["v"])
+        assert w["dt"] <= 0.99 * 0.25 * (2 * r).min() / np.sqrt((w["v"] ** 2).sum(0)).max()
