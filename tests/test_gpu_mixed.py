@@ -183,6 +183,33 @@ def test_collide_f32_pair_wraps_through_the_lower_face():
         assert np.array_equal(g[key], ref), key
 
 
+def test_collide_f32_collided_offset_that_rounds_to_one_is_carried():
+    """A head-on pair (e = 1) with dt chosen so that the struck sphere ends 1e-9 cells below
+    the face x = 4 cells: its FP32 offset rounds to 1.0 and is stored as offset 0 of cell 4;
+    pair, cells, offsets and velocities bit-identical to the oracle."""
+    ctx = _ctx_10_cells(2)
+    w = dict(x=np.array([[0.30, 0.36], [0.55, 0.55], [0.45, 0.45]]), v=np.array([[1.0, -1.0], [0.0, 0.0], [0.0, 0.0]]),
+             r=np.full(2, 0.01), m=np.ones(2), id=np.arange(2, dtype=np.int32), q=np.zeros((4, 2)))
+    a = mixed_state(w, ctx)
+    cur = by_id(a.numpy())
+    xd = oracle.dequantize(cur["cell"], cur["o"], 10) * 10
+    R = (float(cur["r"][0]) + float(cur["r"][1])) * 10
+    t = (xd[0, 1] - xd[0, 0] - R) / 20.0
+    dt = t + (4.0 - 1e-9 - (xd[0, 1] - t * 10)) / 10
+    b = pc.StateF32.empty(2)
+    ctx.collide_f32(a, b, dt)
+    ctx.sync()
+    gids, gt = ctx.pairs()
+    c1, o1, v1, partner, tc, k = oracle.collide_step_cellrel(cur["cell"], cur["o"], cur["v"], cur["r"], cur["m"],
+                                                             cur["id"], 10, 1.0, dt)
+    oids, ot = oracle_pairs(partner, tc, cur["id"])
+    assert k == 1 and c1[1] % 10 == 4 and o1[0, 1] == 0.0
+    assert np.array_equal(gids, oids) and np.array_equal(gt, ot)
+    g = by_id(b.numpy())
+    for key, ref in (("cell", c1), ("o", o1), ("v", v1)):
+        assert np.array_equal(g[key], ref), key
+
+
 def _oracle_field_of(s32np, nc, wl, ne=None):
     x = oracle.dequantize(s32np["cell"], s32np["o"], nc)
     return oracle.project(x, s32np["q"].astype(np.float64), ne or wl.ne, wl.degree, wl.sigma, wl.cutoff_sigmas)[0]

@@ -749,6 +749,31 @@ def test_cellrel_collision_across_the_lower_face():
     assert np.max(np.abs(d)) * nc < 1e-6
 
 
+def test_cellrel_collided_offset_that_rounds_to_one_is_carried():
+    """A head-on pair (e = 1, equal masses) with dt chosen so that the struck sphere ends
+    1e-9 cells below the face x = 4 cells: its offset rounds to 1.0 in FP32 and must be
+    stored as offset 0 of cell 4 (every offset stays in [0, 1)); the position equals the
+    FP64 step on the dequantized state."""
+    nc = 10
+    x = np.array([[0.30, 0.36], [0.55, 0.55], [0.45, 0.45]])
+    cell, o = oracle.quantize(x, nc)
+    v = np.array([[1.0, -1.0], [0.0, 0.0], [0.0, 0.0]], np.float32)
+    r, m, ids = np.full(2, 0.01, np.float32), np.ones(2, np.float32), np.arange(2, dtype=np.int32)
+    xd = oracle.dequantize(cell, o, nc) * nc                     # cell units
+    R = (float(r[0]) + float(r[1])) * nc
+    t = (xd[0, 1] - xd[0, 0] - R) / (2.0 * nc)                   # closing speed 2 nc cells per unit time
+    dt = t + (4.0 - 1e-9 - (xd[0, 1] - t * nc)) / nc             # sphere 1 leaves at +1 after the exchange
+    c1, o1, v1, p, tc, k = oracle.collide_step_cellrel(cell, o, v, r, m, ids, nc, 1.0, dt)
+    assert k == 1 and np.all((o1 >= 0.0) & (o1 < 1.0))
+    assert c1[1] % nc == 4 and o1[0, 1] == 0.0
+    x2, _, _, _, _ = oracle.collide_step(oracle.dequantize(cell, o, nc), v.astype(np.float64), r.astype(np.float64),
+                                         m.astype(np.float64), ids, 1.0, dt)
+    assert abs(x2[0, 1] * nc - (4.0 - 1e-9)) < 1e-10
+    d = oracle.dequantize(c1, o1, nc) - x2
+    d -= np.round(d)
+    assert np.max(np.abs(d)) * nc < 1e-6
+
+
 def test_cellrel_momentum_conserved_to_storage_rounding():
     w = inputs.draw("dense_1m", n=2500, seed=22)
     nc = 25
