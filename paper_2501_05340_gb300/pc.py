@@ -1,8 +1,8 @@
 """Python binding of the pc C ABI (``include/pc.h``): argument marshalling only.
 
 Every step of the operator runs in the CUDA library ``libpc.so``; there is no
-CPU fallback. Importing this module builds the library if it is missing or
-stale (nvcc, sm_103a) and raises if that fails.
+CPU fallback. The first call that needs the library builds it if it is missing
+or stale (nvcc, sm_103a) and loads it; a failed build or load raises.
 
 Particle state lives in torch CUDA tensors (SoA, float64): ``x[3, n]``,
 ``v[3, n]``, ``r[n]``, ``m[n]``, ``q[4, n]`` and ``id[n]`` (int32).
