@@ -336,6 +336,29 @@ def test_matching_rounds_one_pair_per_round():
     assert np.array_equal(pr, pg) and np.array_equal(tr, tg) and kr == 3 and rounds == 3
 
 
+@pytest.mark.parametrize("method", ["cells", "bruteforce"])
+def test_step_with_more_candidates_than_the_first_buffer(method):
+    """40 spheres contracting towards one point: all 780 pairs are candidates, more than the
+    4 n entries the step first allocates, so it must grow its candidate buffers and use every
+    candidate: its pairs are the greedy matching of the full brute-force candidate list, and
+    the first-found step's pairs form a maximal matching of the same list."""
+    rng = np.random.default_rng(23)
+    n = 40
+    c = np.array([0.5, 0.5, 0.5])
+    x = c[:, None] + rng.uniform(-0.05, 0.05, (3, n))
+    v = -(x - c[:, None]) / 0.1
+    r, m, ids, dt = np.full(n, 0.002), rng.uniform(0.5, 2.0, n), np.arange(n, dtype=np.int32), 0.1
+    ci, cj, ct = oracle.candidates(x, v, r, dt, "bruteforce")
+    assert len(ci) > 4 * n
+    pg, tg, kg = oracle.match(ids, ci, cj, ct, n)
+    _, _, p, t, k = oracle.collide_step(x, v, r, m, ids, 0.9, dt, method)
+    assert k == kg == n // 2 and np.array_equal(p, pg) and np.array_equal(t, tg)
+    _, _, ps, ts, ks = oracle.collide_step_sfc(x, v, r, m, ids, 0.9, dt, 4)
+    assert ks == n // 2 and all(ps[ps[i]] == i for i in range(n))
+    for a, b in zip(ci, cj):
+        assert ps[a] >= 0 or ps[b] >= 0
+
+
 # ----------------------------------------------------------------- response
 
 def _pair_state(rng, e_same_mass=True):
