@@ -52,8 +52,13 @@ typedef struct {
   double cutoff_sigmas; /* kernel cutoff radius in units of sigma (> 0); 3 in the paper's workloads */
   int32_t cutoff_kind;  /* 0: box |d_axis| <= cutoff on every axis (separable); 1: sphere |d| <= cutoff */
   double restitution;   /* normal restitution coefficient e in [0, 1] (Sec. 2.4) */
-  double reach_hint;    /* expected largest 2 r_max + 2 v_max dt; sizes the collision cells.
-                           Larger actual reaches stay exact (more cells are searched). (> 0) */
+  double reach_hint;    /* expected largest reach 2 r_max + 2 v_max dt of a step; sizes the
+                           collision cells (side >= reach_hint). 0 < reach_hint < 0.5.
+                           A step whose actual reach exceeds the hint stays exact (more
+                           cells are searched) as long as it stays below 0.5 box lengths,
+                           where the periodic minimum image is the only image that can
+                           collide; a step with a reach >= 0.5 is refused on the GPU
+                           (PC_EINVAL from the next pc_sync, outputs undefined). */
   int32_t cand_cap;     /* candidate partners kept per particle and step (1..32; 0 = 16) */
   void* stream;         /* cudaStream_t for all work (NULL = legacy default stream) */
   double amp;           /* curved-mesh amplitude a of x = xi + a (sin 2pi xi_y sin 2pi xi_z, cyclic);

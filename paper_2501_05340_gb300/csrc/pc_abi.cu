@@ -110,7 +110,9 @@ pc_status pc_init(pc_ctx** out, const pc_config* cfg) {
   if (!(c.sigma > 0.0) || !(c.cutoff_sigmas > 0.0) || !(c.restitution >= 0.0 && c.restitution <= 1.0))
     return PC_EINVAL;
   if (c.cutoff_kind != 0 && c.cutoff_kind != 1) return PC_EINVAL;
-  if (!(c.reach_hint > 0.0) || c.cand_cap < 0 || c.cand_cap > 32) return PC_EINVAL;
+  // the periodic minimum image names one partner image only while the reach stays
+  // below half the box; the search kernels check the actual reach of each step too
+  if (!(c.reach_hint > 0.0 && c.reach_hint < 0.5) || c.cand_cap < 0 || c.cand_cap > 32) return PC_EINVAL;
   if (!(c.amp >= 0.0 && c.amp < 0.04)) return PC_EINVAL;
   const double rc = c.cutoff_sigmas * c.sigma;
   // the sphere cutoff serves the curved mesh: in logical space the physical ball of

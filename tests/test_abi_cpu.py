@@ -35,7 +35,8 @@ def test_argument_validation_without_gpu():
     h = ctypes.c_void_p()
     assert lib.pc_init(ctypes.byref(h), None) == pc.PC_EINVAL
     bad = [dict(n_max=0), dict(ne=2), dict(degree=16), dict(sigma=0.0), dict(restitution=1.5),
-           dict(reach_hint=0.0), dict(cand_cap=33), dict(sigma=0.2)]  # sigma=0.2: cutoff beyond half the box
+           dict(reach_hint=0.0), dict(reach_hint=0.5), dict(reach_hint=0.8), dict(cand_cap=33),
+           dict(sigma=0.2)]  # sigma=0.2: cutoff beyond half the box; reach >= 0.5: minimum image not unique
     for b in bad:
         kw = dict(n_max=100, ne=8, degree=3, sigma=0.02, cutoff_sigmas=3.0, cutoff_kind=0, restitution=0.9,
                   reach_hint=0.04, cand_cap=16, stream=None)

@@ -107,17 +107,18 @@ def test_collide_f32_permuted_ids():
     assert total > 0
 
 
-@pytest.mark.parametrize("target_reach", [0.45, 0.8])
+@pytest.mark.parametrize("target_reach", [0.45, 0.49])
 def test_collide_f32_reach_spanning_the_box(target_reach):
-    """Mixed path with a reach above a third of the box: 3 cells per side, the stencil
-    covers every cell once; pairs, times, cells, offsets and velocities bit-identical."""
+    """Mixed path with a reach above a third of the box (below half of it): 3 cells per
+    side, the stencil covers every cell once; pairs, times, cells, offsets and velocities
+    bit-identical."""
     rng = np.random.default_rng(int(target_reach * 100) + 1)
     n = 500
     w = dict(x=rng.random((3, n)), v=rng.normal(size=(3, n)), r=np.full(n, 0.015), m=rng.uniform(0.5, 2.0, n),
              id=np.arange(n, dtype=np.int32), q=rng.normal(size=(4, n)))
     vmax = float(np.sqrt((w["v"] ** 2).sum(0)).max())
     dt = (target_reach - 0.03) / (2 * vmax)
-    ctx = pc.Context(n, 8, 3, 0.02, 0.9, pc.reach_of(w["r"], w["v"], dt))
+    ctx = pc.Context(n, 8, 3, 0.02, 0.9, pc.reach_of(w["r"], w["v"], dt, margin=1.0))
     assert ctx.cells_per_side == 3
     a = mixed_state(w, ctx)
     b = pc.StateF32.empty(n)
@@ -132,6 +133,24 @@ def test_collide_f32_reach_spanning_the_box(target_reach):
     g = by_id(b.numpy())
     for key, ref in (("cell", cell), ("o", o), ("v", v)):
         assert np.array_equal(g[key], ref), key
+
+
+def test_collide_f32_reach_of_half_the_box_is_refused():
+    """A mixed step whose actual reach is 0.8 box lengths under a hint of 0.3: refused on
+    the GPU (PC_EINVAL from pc_sync), as the FP64 path refuses it."""
+    rng = np.random.default_rng(81)
+    n = 500
+    w = dict(x=rng.random((3, n)), v=rng.normal(size=(3, n)), r=np.full(n, 0.015), m=rng.uniform(0.5, 2.0, n),
+             id=np.arange(n, dtype=np.int32), q=rng.normal(size=(4, n)))
+    vmax = float(np.sqrt((w["v"] ** 2).sum(0)).max())
+    dt = (0.8 - 0.03) / (2 * vmax)
+    ctx = pc.Context(n, 8, 3, 0.02, 0.9, 0.3)
+    a = mixed_state(w, ctx)
+    b = pc.StateF32.empty(n)
+    ctx.collide_f32(a, b, dt)
+    with pytest.raises(pc.PcError, match="PC_EINVAL"):
+        ctx.sync()
+    ctx.sync()
 
 
 def _ctx_10_cells(n):

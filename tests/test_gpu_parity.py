@@ -210,9 +210,10 @@ def test_chain_matched_one_pair_per_round():
     assert ctx.pairs()[0].tolist() == [[0, 1], [2, 3], [4, 5]]
 
 
-@pytest.mark.parametrize("target_reach", [0.45, 0.8])
+@pytest.mark.parametrize("target_reach", [0.45, 0.49])
 def test_reach_spanning_the_box(target_reach):
-    """A step whose reach exceeds a third of the box: the grid keeps 3 cells per side and
+    """A step whose reach exceeds a third of the box (but stays below half of it, where the
+    minimum image is the only image that can collide): the grid keeps 3 cells per side and
     the stencil covers every cell once; pairs, times, x and v bit-identical to the oracle."""
     rng = np.random.default_rng(int(target_reach * 100))
     n = 500
@@ -221,10 +222,30 @@ def test_reach_spanning_the_box(target_reach):
     vmax = float(np.sqrt((d["v"] ** 2).sum(0)).max())
     dt = (target_reach - 0.03) / (2 * vmax)
     a, b = pc.State.from_arrays(d), pc.State.empty(n)
-    ctx = pc.Context(n, 8, 3, 0.02, 0.9, pc.reach_of(d["r"], d["v"], dt))
+    ctx = pc.Context(n, 8, 3, 0.02, 0.9, pc.reach_of(d["r"], d["v"], dt, margin=1.0))
     assert ctx.cells_per_side == 3
     _, k = compare_collide_step(ctx, a, b, by_id(dict(d)), dt, 0.9)
     assert k > 5
+
+
+def test_reach_of_half_the_box_is_refused():
+    """A reach of half the box or more: pc_init refuses such a hint on the host, and a step
+    whose actual reach reaches 0.5 under a smaller hint is refused on the GPU (PC_EINVAL
+    from pc_sync), since another periodic image than the minimum one could then collide."""
+    with pytest.raises(pc.PcError, match="PC_EINVAL"):
+        pc.Context(10, 8, 3, 0.02, 0.9, 0.5)
+    rng = np.random.default_rng(80)
+    n = 500
+    d = dict(x=rng.random((3, n)), v=rng.normal(size=(3, n)), r=np.full(n, 0.015), m=rng.uniform(0.5, 2.0, n),
+             id=np.arange(n, dtype=np.int32), q=rng.normal(size=(4, n)))
+    vmax = float(np.sqrt((d["v"] ** 2).sum(0)).max())
+    dt = (0.8 - 0.03) / (2 * vmax)
+    a, b = pc.State.from_arrays(d), pc.State.empty(n)
+    ctx = pc.Context(n, 8, 3, 0.02, 0.9, 0.3)
+    ctx.collide(a, b, dt)
+    with pytest.raises(pc.PcError, match="PC_EINVAL"):
+        ctx.sync()
+    ctx.sync()  # the status is cleared once reported
 
 
 def test_clustered_cells():
