@@ -368,7 +368,9 @@ pc_status pc_get_timing(pc_ctx* ctx, double* ms, int64_t* count);
  *
  * The first call on each device looks up the array's device address
  * (cudaGetSymbolAddress) with that device current; make that first call before
- * any stream capture. The work is queued on cfg->stream and the call returns
+ * any stream capture. The address is kept per device together with the id of
+ * the context it belongs to; after a cudaDeviceReset the next call finds a new
+ * context and looks the address up again (so, again, before any capture). The work is queued on cfg->stream and the call returns
  * without waiting; checks made on the GPU (positions outside [0,1)) are not
  * reported. All calls share the one array, which keeps the previous call's
  * contents (what must start at zero is cleared by each call): calls that overlap

@@ -7,6 +7,8 @@
 #include <math.h>
 #include <string.h>
 
+#include <cuda.h>
+
 #include <mutex>
 
 #include "pc_internal.cuh"
@@ -19,10 +21,40 @@ constexpr size_t kNoallocBytes = (size_t)PC_NOALLOC_SCRATCH_BYTES;
 static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoallocBytes];
 
 // Device address of g_noalloc_scratch per device. In host code the array's name
-// is only a host-side stand-in, so the address is looked up once per device.
+// is only a host-side stand-in, so the address is looked up once per device and
+// context: a cudaDeviceReset destroys the context that held the array, and the
+// next call sees a context with another id and looks the address up again.
 constexpr int kMaxDevices = 64;
 void* g_scratch_addr[kMaxDevices];
+unsigned long long g_scratch_ctx[kMaxDevices];
 std::mutex g_scratch_mu;
+
+// Driver entry points for the current context's unique id (no link to libcuda:
+// the runtime hands out the driver's functions).
+typedef CUresult (*ctx_get_current_fn)(CUcontext*);
+typedef CUresult (*ctx_get_id_fn)(CUcontext, unsigned long long*);
+ctx_get_current_fn g_ctx_current;
+ctx_get_id_fn g_ctx_id;
+
+// Unique id of the calling thread's current context, 0 if there is none or the
+// driver cannot tell.
+unsigned long long current_context_id() {
+  if (!g_ctx_current || !g_ctx_id) {
+    void* a = nullptr;
+    void* b = nullptr;
+    cudaDriverEntryPointQueryResult qa, qb;
+    if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &a, 12000, cudaEnableDefault, &qa) != cudaSuccess ||
+        cudaGetDriverEntryPointByVersion("cuCtxGetId", &b, 12000, cudaEnableDefault, &qb) != cudaSuccess ||
+        qa != cudaDriverEntryPointSuccess || qb != cudaDriverEntryPointSuccess)
+      return 0;
+    g_ctx_current = (ctx_get_current_fn)a;
+    g_ctx_id = (ctx_get_id_fn)b;
+  }
+  CUcontext cu = nullptr;
+  unsigned long long id = 0;
+  if (g_ctx_current(&cu) != CUDA_SUCCESS || !cu || g_ctx_id(cu, &id) != CUDA_SUCCESS) return 0;
+  return id;
+}
 
 size_t align256(size_t b) { return (b + 255) & ~(size_t)255; }
 
@@ -40,6 +72,11 @@ extern "C" pc_status pc_project_noalloc(const pc_config* cfg, const pc_particles
   put_msg(msg, msg_len, "no error");
   if (!cfg || !p || !field || p->n < 0 || (p->n > 0 && (!p->x || !p->q || !p->id))) {
     put_msg(msg, msg_len, "pc_project_noalloc: bad arguments");
+    return PC_EINVAL;
+  }
+  // particle indices and bin slots are int32 on the device
+  if (p->n >= ((int64_t)1 << 31)) {
+    put_msg(msg, msg_len, "pc_project_noalloc: more than 2^31 - 1 particles");
     return PC_EINVAL;
   }
   const pc_config& c = *cfg;
@@ -98,7 +135,8 @@ extern "C" pc_status pc_project_noalloc(const pc_config* cfg, const pc_particles
   unsigned char* base = nullptr;
   {
     std::lock_guard<std::mutex> lock(g_scratch_mu);
-    if (!g_scratch_addr[dev]) {
+    const unsigned long long cid = current_context_id();
+    if (!g_scratch_addr[dev] || cid == 0 || cid != g_scratch_ctx[dev]) {
       void* a = nullptr;
       const cudaError_t e = cudaGetSymbolAddress(&a, g_noalloc_scratch);
       if (e != cudaSuccess || !a) {
@@ -106,6 +144,8 @@ extern "C" pc_status pc_project_noalloc(const pc_config* cfg, const pc_particles
         return PC_ECUDA;
       }
       g_scratch_addr[dev] = a;
+      // the lookup makes the device's primary context current if none was
+      g_scratch_ctx[dev] = current_context_id();
     }
     base = (unsigned char*)g_scratch_addr[dev];
   }

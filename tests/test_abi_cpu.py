@@ -49,6 +49,20 @@ def test_argument_validation_without_gpu():
     lib.pc_destroy(None)
 
 
+def test_noalloc_rejects_more_than_int32_particles_without_gpu():
+    """pc_project_noalloc refuses n >= 2^31 (int32 indices on the device) before it
+    sizes its scratch or touches the GPU (the pointers are never dereferenced)."""
+    from paper_2501_05340_gb300 import pc
+    lib = pc.library()
+    cfg = pc.PcConfig(n_max=0, ne=8, degree=3, sigma=0.02, cutoff_sigmas=3.0, cutoff_kind=0, restitution=0.0,
+                      reach_hint=0.0, cand_cap=0, stream=None)
+    fake = ctypes.c_void_p(256)
+    p = pc.PcParticles(1 << 31, fake, fake, fake, fake, fake, fake)
+    msg = ctypes.create_string_buffer(128)
+    assert lib.pc_project_noalloc(ctypes.byref(cfg), ctypes.byref(p), fake, msg, 128) == pc.PC_EINVAL
+    assert b"2^31" in msg.value
+
+
 def test_binding_rejects_host_and_misshaped_tensors():
     """The binding hands raw device pointers to the library, so it refuses host tensors,
     other dtypes, non-contiguous views and wrong shapes before any call (the library

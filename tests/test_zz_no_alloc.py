@@ -1,9 +1,12 @@
 """pc_project_noalloc, the projection for callers that may not allocate device
 memory (its scratch is a fixed array inside the library), against pc_project on
-two calls in a row with different inputs. Collected last on purpose."""
+two calls in a row with different inputs, and the smaller case against the
+oracle too; free device memory is unchanged across its calls. Collected last on
+purpose."""
 import numpy as np
 import pytest
 
+import oracle
 from paper_2501_05340_gb300 import inputs
 from tests.gpu_helpers import field_err
 
@@ -41,6 +44,26 @@ def test_noalloc_matches_project_twice():
         got = f.cpu().numpy()
         assert np.all(np.isfinite(got))
         assert np.all(field_err(got, ref) <= FIELD_TOL), name
+        if name == "small_8192":
+            R, _ = oracle.project(w["x"], w["q"], wl.ne, wl.degree, wl.sigma, wl.cutoff_sigmas)
+            assert np.all(field_err(got, R) <= FIELD_TOL), "oracle"
+
+
+def test_noalloc_allocates_nothing():
+    """After a first call (which may load the library's kernels onto the device), further
+    calls leave the device's free memory unchanged: the scratch is the fixed array."""
+    w = inputs.draw("dense_1m", seed=2, n=20000)
+    wl = w["workload"]
+    a = pc.State.from_arrays(w)
+    f = torch.empty((wl.ne ** 3, 4, (wl.degree + 1) ** 3), dtype=torch.float64, device="cuda")
+    pc.project_noalloc(a, f, wl.ne, wl.degree, wl.sigma, wl.cutoff_sigmas)
+    torch.cuda.synchronize()
+    free0, _ = torch.cuda.mem_get_info()
+    for _ in range(2):
+        pc.project_noalloc(a, f, wl.ne, wl.degree, wl.sigma, wl.cutoff_sigmas)
+    torch.cuda.synchronize()
+    free1, _ = torch.cuda.mem_get_info()
+    assert free1 == free0
 
 
 def test_noalloc_rejects_oversized_problem():
