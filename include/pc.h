@@ -362,7 +362,7 @@ pc_status pc_get_timing(pc_ctx* ctx, double* ms, int64_t* count);
  * inputs (p: device SoA, p->q required) and the output (field: device
  * [ne^3][4][(N+1)^3] doubles, overwritten); cfg supplies ne, degree, sigma,
  * cutoff_sigmas, cutoff_kind (0) and stream; the other fields are ignored.
- * About 12 + 24 (2 rho + 1)(N+1) + 32 bytes per particle plus 8 ne^3 bytes must
+ * About 16 + 24 (2 rho + 1)(N+1) + 64 bytes per particle plus 8 ne^3 bytes must
  * fit in the array (rho = ceil(cutoff_sigmas sigma ne)); larger problems return
  * PC_ECAPACITY with the required size in msg.
  *

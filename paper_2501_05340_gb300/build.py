@@ -1,9 +1,10 @@
 """Compile the CUDA library ``libpc.so`` in-tree for sm_103a (GB300).
 
 Each translation unit is compiled in parallel with its own flags, then linked:
-``collide.cu`` and ``project.cu`` without implicit fused multiply-add (bit-exact
-FP64 contact solve and response; double-float arithmetic that places every FMA
-explicitly); the others with the default contraction.
+``collide.cu``, ``project.cu``, ``fx_deposit.cu`` and the other units that carry
+double-float or bit-exact arithmetic without implicit fused multiply-add (bit-exact
+FP64 contact solve and response; double-float arithmetic and exact digit splits
+that place every FMA explicitly); the others with the default contraction.
 """
 import os
 import shutil
@@ -27,6 +28,7 @@ UNITS = {
     "noalloc.cu": [],
     "mixed.cu": ["-fmad=false"],
     "tc_deposit.cu": [],
+    "fx_deposit.cu": ["-fmad=false"],
     "adjoint.cu": ["-fmad=false"],
     "curved.cu": ["-fmad=false"],
     "nodal.cu": ["-fmad=false"],

@@ -113,10 +113,15 @@ extern "C" pc_status pc_project_noalloc(const pc_config* cfg, const pc_particles
   off = align256(off + sizeof(int32_t) * (size_t)n);
   const size_t o_perm = off;
   off = align256(off + sizeof(int32_t) * (size_t)n);
+  const int rs = (3 * win + 4 + 1) & ~1;
   const size_t o_fac = off;
-  off = align256(off + sizeof(float2) * (size_t)3 * win * (size_t)n);
+  off = align256(off + sizeof(float2) * (size_t)rs * (size_t)n);
   const size_t o_sq = off;
   off = align256(off + sizeof(float2) * (size_t)4 * (size_t)n);
+  const size_t o_reach = off;
+  off = align256(off + sizeof(int32_t) * (size_t)n);
+  const size_t o_fxmax = off;
+  off = align256(off + sizeof(unsigned) * 8);
   if (off > kNoallocBytes) {
     char text[200];
     snprintf(text, sizeof(text),
@@ -169,8 +174,11 @@ extern "C" pc_status pc_project_noalloc(const pc_config* cfg, const pc_particles
   ctx.key = (int32_t*)(base + o_key);
   ctx.slot = (int32_t*)(base + o_slot);
   ctx.perm = (int32_t*)(base + o_perm);
+  ctx.rs = rs;
   ctx.fac = (float2*)(base + o_fac);
   ctx.sq = (float2*)(base + o_sq);
+  ctx.reach = (int32_t*)(base + o_reach);
+  ctx.fxmax = (unsigned*)(base + o_fxmax);
   // the array keeps the previous call's contents: clear the status counters
   if (cudaMemsetAsync(ctx.counters, 0, sizeof(unsigned long long) * CNT_N, ctx.stream) != cudaSuccess) {
     put_msg(msg, msg_len, "pc_project_noalloc: cudaMemsetAsync failed");

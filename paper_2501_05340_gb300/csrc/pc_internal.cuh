@@ -58,6 +58,11 @@ struct pc_ctx {
   // projection scratch
   float2* fac;  // [3][win][n_max] normalised 1-D kernel factors (df32), sorted order
   float2* sq;   // [4][n_max] sources times (2/h)^3 (df32), sorted order
+  // for n1 <= 8 fac holds records instead: [n_max][rs], rs = 3 win + 4 rounded up to
+  // even (the window factors of the 3 axes, then the sources), for the tensor-core deposit
+  int rs;
+  int32_t* reach;   // [n_max] per-axis reach bits of the records
+  unsigned* fxmax;  // [8]: largest factor and largest |source c| (float bits)
   DfExpTable exp_tab;
   int pair_policy;  // PC_PAIRS_EARLIEST or PC_PAIRS_SFC_FIRST (pc_set_pair_policy)
   double* corner;  // 36 ne^3 doubles: pc_project_idw's df32 corner sums [ne^3][8][4] and node densities [ne^3][4]
@@ -133,6 +138,11 @@ struct TcDepositArgs {
   unsigned long long* counters;
 };
 cudaError_t pc_tc_deposit_launch(const TcDepositArgs& A, cudaStream_t st, int* nblocks);
+
+// FP64-accurate tensor-core deposit over the records of k_proj_factors (fx_deposit.cu).
+cudaError_t pc_fx_deposit_launch(int n1, int ne, int rho, int win, int rs, const int32_t* start, const float2* rec,
+                                 const int32_t* reach, const unsigned* fxmax, double* field,
+                                 unsigned long long* counters, cudaStream_t st);
 
 // ---- project (project.cu) ----------------------------------------------------
 pc_status pc_project_impl(pc_ctx* ctx, const pc_particles* p, double* field);

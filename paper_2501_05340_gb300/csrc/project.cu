@@ -8,10 +8,14 @@
 // Pipeline: element key + counting sort of particles by element (bin.cu), then
 //   factors  per particle and axis: the normalised 1-D factors on the nodes of the
 //            2 rho + 1 elements around its own element (rho = ceil(cutoff ne)),
-//   gather   one CTA per element: every warp takes particles of the neighbouring
-//            elements in turn and adds q_c kx ky kz onto the nodes inside the
-//            particle's support box, in a private shared-memory accumulator; the
-//            warps' accumulators are summed in a fixed order at the end.
+//            in double-float; for N + 1 <= 8 written as one record per particle
+//            with its per-axis reach bits and the largest factor and sources,
+//   deposit  N + 1 <= 8: the per-element contraction on the tensor cores by exact
+//            fixed-point digits (fx_deposit.cu); above: one CTA per element, every
+//            warp takes particles of the neighbouring elements in turn and adds
+//            q_c kx ky kz onto the nodes inside the particle's support box, in a
+//            private shared-memory accumulator; the warps' accumulators are summed
+//            in a fixed order at the end.
 // No atomics: the result is deterministic for a given particle order, and the
 // order is canonical (by element, then id).
 #include <math.h>
@@ -73,6 +77,15 @@ struct FactorArgs {
   const double* q;
   float2* fac;  // [3][win][n] normalised 1-D factors k_a / Z_a (df32)
   float2* sq;   // [4][n] sources times (2/h)^3 (df32)
+  // record layout (tensor-core deposit), used instead of fac / sq when rec is set:
+  // rec[k][rs] = the 3 win factors (axis-major), then the 4 sources; reach[k] bit
+  // 8 a + w set when axis a has a non-zero factor in window element w; fxmax[0] the
+  // largest factor and fxmax[1 + c] the largest |source c| (bits of non-negative
+  // floats, atomically maximised)
+  float2* rec;
+  int rs;
+  int32_t* reach;
+  unsigned* fxmax;
 };
 
 // fac[a][w][k] = k_a(X_w - x_a) / Z_a over the window nodes w of the particle's
@@ -85,50 +98,75 @@ struct FactorArgs {
 __global__ void __launch_bounds__(128) k_proj_factors(FactorArgs F) {
   const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   const int64_t n = F.n;
-  if (k >= n) return;
-  const int64_t p = F.perm[k];
-  for (int a = 0; a < 3; ++a) {
-    const double xa = F.x[a * n + p];
-    const int ea = cell_of(xa, F.ne);
-    const f2 t = df_from_double(xa * (double)F.ne - (double)ea);
-    f2 Z = {0.0f, 0.0f};
-    for (int w = 0; w < F.win; ++w) {
-      const int i = w % F.n1;
-      const f2 dl = df_add(F.sw[w], df_neg(t));
-      const float ad = fabsf(dl.h);
-      bool inside;
-      if (fabsf(ad - F.rce) > 1e-5f * F.rce) {
-        inside = ad < F.rce;
-      } else {
-        const int o = w / F.n1 - F.rho;
-        const int ge = wrapi(ea + o, F.ne);
-        const double X = ((double)ge + 0.5 * (F.eta[i] + 1.0)) * F.h;
-        inside = fabs(minimg(X - xa)) <= F.rc;
+  const bool recs = F.rec != nullptr;
+  float fmax = 0.0f, qmax[4] = {0.0f, 0.0f, 0.0f, 0.0f};
+  if (k < n) {
+    const int64_t p = F.perm[k];
+    float2* rk = recs ? F.rec + k * F.rs : nullptr;
+    auto slot = [&](int a, int w) -> float2* {
+      return recs ? rk + a * F.win + w : &F.fac[((int64_t)a * F.win + w) * n + k];
+    };
+    int reach = 0;
+    for (int a = 0; a < 3; ++a) {
+      const double xa = F.x[a * n + p];
+      const int ea = cell_of(xa, F.ne);
+      const f2 t = df_from_double(xa * (double)F.ne - (double)ea);
+      f2 Z = {0.0f, 0.0f};
+      for (int w = 0; w < F.win; ++w) {
+        const int i = w % F.n1;
+        const f2 dl = df_add(F.sw[w], df_neg(t));
+        const float ad = fabsf(dl.h);
+        bool inside;
+        if (fabsf(ad - F.rce) > 1e-5f * F.rce) {
+          inside = ad < F.rce;
+        } else {
+          const int o = w / F.n1 - F.rho;
+          const int ge = wrapi(ea + o, F.ne);
+          const double X = ((double)ge + 0.5 * (F.eta[i] + 1.0)) * F.h;
+          inside = fabs(minimg(X - xa)) <= F.rc;
+        }
+        f2 f = {0.0f, 0.0f};
+        if (inside) {
+          f2 d2 = two_prod(dl.h, dl.h);
+          d2.l = fmaf(2.0f * dl.h, dl.l, d2.l);
+          d2 = fast_two_sum(d2.h, d2.l);
+          f = df_exp_neg(df_neg(df_mul(d2, F.c2)), F.tab);
+          Z = df_add(Z, df_mul(f, F.wq[i]));
+        }
+        *slot(a, w) = make_float2(f.h, f.l);
       }
-      f2 f = {0.0f, 0.0f};
-      if (inside) {
-        f2 d2 = two_prod(dl.h, dl.h);
-        d2.l = fmaf(2.0f * dl.h, dl.l, d2.l);
-        d2 = fast_two_sum(d2.h, d2.l);
-        f = df_exp_neg(df_neg(df_mul(d2, F.c2)), F.tab);
-        Z = df_add(Z, df_mul(f, F.wq[i]));
+      const f2 rz = df_recip(Z);
+      for (int w = 0; w < F.win; ++w) {
+        float2* sl = slot(a, w);
+        const float2 v = *sl;
+        if (v.x != 0.0f) {
+          const f2 r = df_mul({v.x, v.y}, rz);
+          *sl = make_float2(r.h, r.l);
+          fmax = fmaxf(fmax, fabsf(r.h));
+          reach |= 1 << (8 * a + w / F.n1);
+        }
       }
-      F.fac[((int64_t)a * F.win + w) * n + k] = make_float2(f.h, f.l);
     }
-    const f2 rz = df_recip(Z);
-    for (int w = 0; w < F.win; ++w) {
-      float2* slot = &F.fac[((int64_t)a * F.win + w) * n + k];
-      const float2 v = *slot;
-      if (v.x != 0.0f) {
-        const f2 r = df_mul({v.x, v.y}, rz);
-        *slot = make_float2(r.h, r.l);
-      }
-    }
-  }
 #pragma unroll
-  for (int c = 0; c < 4; ++c) {
-    const f2 qs = df_mul(df_from_double(F.q[c * n + p]), F.scale);
-    F.sq[c * n + k] = make_float2(qs.h, qs.l);
+    for (int c = 0; c < 4; ++c) {
+      const f2 qs = df_mul(df_from_double(F.q[c * n + p]), F.scale);
+      if (recs)
+        rk[3 * F.win + c] = make_float2(qs.h, qs.l);
+      else
+        F.sq[c * n + k] = make_float2(qs.h, qs.l);
+      qmax[c] = fabsf(qs.h);
+    }
+    if (recs) F.reach[k] = reach;
+  }
+  if (recs) {
+    // block-free maximum: warp reduction of the float bits, one atomic per warp
+    unsigned v = __reduce_max_sync(0xffffffffu, __float_as_uint(fmax));
+    if ((threadIdx.x & 31) == 0) atomicMax(&F.fxmax[0], v);
+#pragma unroll
+    for (int c = 0; c < 4; ++c) {
+      v = __reduce_max_sync(0xffffffffu, __float_as_uint(qmax[c]));
+      if ((threadIdx.x & 31) == 0) atomicMax(&F.fxmax[1 + c], v);
+    }
   }
 }
 
@@ -329,364 +367,6 @@ __global__ void k_proj_deposit(DepositArgs G) {
   }
 }
 
-// ---- blocked deposit, n1 <= 8 -------------------------------------------------
-// An element's deposit is the contraction D[jk][ci] = sum_p YZ_p[jk] A_p[ci] with
-// YZ = ky_j kz_k and A = q_c kx_i (df32), jk = k n1 + j, ci = c n1 + i. One CTA per
-// element and one warp per 2 x 2 block of (j, k) node lines; lane (b, g) of a warp
-// owns (j, k) = (2 wj + (b & 1), 2 wk + (b >> 1)), b = lane >> 3, and the TC columns
-// ci = g TC .. g TC + TC - 1, g = lane & 7, as df32 accumulators in registers. A
-// warp runs only over the staged particles whose y and z support meets its lines:
-// outside the support the factors are exact zeros, so the skipped terms change no
-// sum. Candidates come in batches of 32 (in a fixed permuted order that spreads
-// each batch over the neighbourhood), staged lane-per-candidate into a double
-// buffer; every sum runs in that order, so the result is deterministic.
-template <int N1>
-struct BlkShape {
-  static constexpr int NB = (N1 + 1) / 2;          // blocks per side
-  static constexpr int NW = NB * NB;               // warps per CTA
-  static constexpr int TC = (4 * N1 + 7) / 8;      // columns per lane
-  static constexpr int TCP = TC == 3 ? 4 : TC;     // padded column group
-  static constexpr int YZP = (N1 * N1 + 1) & ~1;   // YZ entries, padded to 16 bytes
-  // staged df32 values per particle: YZ, then A as [TCP / 2][8 groups][2] (groups of
-  // one column when TCP = 1); the row pitch in 16-byte units is odd, so that the
-  // stager's per-lane row stores do not collide in the banks
-  static constexpr int PER0 = YZP + 8 * TCP;
-  static constexpr int PER = (PER0 / 2) % 2 == 1 ? PER0 : PER0 + 2;
-  static constexpr int MINB = NW == 1 ? 16 : (NW == 4 ? 8 : (NW == 9 ? 4 : 2));
-  static constexpr size_t SMEM = (size_t)(2 * 32 * PER + PER) * sizeof(float2) + (size_t)(2 * 32 + 376) * sizeof(int);
-};
-
-struct BlkArgs {
-  int64_t n;
-  int ne, rho, win;
-  const int32_t* start;
-  const float2* fac;
-  const float2* sq;
-  double* field;
-};
-
-// acc += a b for df32 a, b: product with its FMA error terms, TwoSum on the high
-// parts, all errors gathered in the low part.
-__device__ __forceinline__ void df_fma_acc(f2& acc, float2 a, float2 b) {
-  const float p = a.x * b.x;
-  float e = fmaf(a.x, b.x, -p);
-  e = fmaf(a.x, b.y, e);
-  e = fmaf(a.y, b.x, e);
-  const float s = acc.h + p;
-  const float bb = s - acc.h;
-  const float err = (acc.h - (s - bb)) + (p - bb);
-  acc.h = s;
-  acc.l = acc.l + (err + e);
-}
-
-// Two accumulators at once on the packed FP32x2 pipe instructions: (H, L) += (ah, al) b
-// with H, L, ah, al pairs of high and low parts and b one df32 value; the same
-// operations as df_fma_acc, lane by lane.
-__device__ __forceinline__ float2 neg2(float2 a) { return make_float2(-a.x, -a.y); }
-__device__ __forceinline__ void df_fma_acc2(float2& H, float2& L, float2 ah, float2 al, float2 b) {
-  const float2 bh = make_float2(b.x, b.x), bl = make_float2(b.y, b.y);
-  const float2 p = __fmul2_rn(ah, bh);
-  float2 e = __ffma2_rn(ah, bh, neg2(p));
-  e = __ffma2_rn(ah, bl, e);
-  e = __ffma2_rn(al, bh, e);
-  const float2 s = __fadd2_rn(H, p);
-  const float2 bb = __fadd2_rn(s, neg2(H));
-  const float2 err = __fadd2_rn(__fadd2_rn(H, neg2(__fadd2_rn(s, neg2(bb)))), __fadd2_rn(p, neg2(bb)));
-  H = s;
-  L = __fadd2_rn(L, __fadd2_rn(err, e));
-}
-
-__device__ __forceinline__ float2 df_mul2(float2 a, float2 b) {
-  const f2 v = df_mul({a.x, a.y}, {b.x, b.y});
-  return make_float2(v.h, v.l);
-}
-
-// Offset of A column (group g, slot t) in a staged row.
-template <int N1>
-__host__ __device__ constexpr int a_off(int g, int t) {
-  using B = BlkShape<N1>;
-  return B::TCP == 1 ? B::YZP + g : B::YZP + ((t >> 1) * 8 + g) * 2 + (t & 1);
-}
-
-// Column ci held at entry x of the A part of a staged row (inverse of a_off), or -1
-// for padding.
-template <int N1>
-__host__ __device__ constexpr int a_col(int x) {
-  using B = BlkShape<N1>;
-  const int g = B::TCP == 1 ? x : (B::TCP == 2 ? x / 2 : (x / 2) % 8);
-  const int t = B::TCP == 1 ? 0 : (B::TCP == 2 ? x % 2 : 2 * ((x / 2) / 8) + x % 2);
-  const int ci = g * B::TC + t;
-  return (t < B::TC && ci < 4 * N1) ? ci : -1;
-}
-
-template <int N1>
-__global__ void __launch_bounds__(32 * BlkShape<N1>::NW, BlkShape<N1>::MINB) k_proj_deposit_blk(BlkArgs G) {
-  using B = BlkShape<N1>;
-  constexpr int NW = B::NW, TC = B::TC, TCP = B::TCP, PER = B::PER, YZP = B::YZP;
-  constexpr int NODES = N1 * N1 * N1;
-  extern __shared__ float4 smb4[];
-  float2* stage = reinterpret_cast<float2*>(smb4);          // [2][32][PER]
-  float2* zrow = stage + 2 * 32 * PER;                      // [PER] zeros: the partner of an odd last particle
-  int* box = reinterpret_cast<int*>(zrow + PER);            // [2][32]: y, z support lines; -1 if not kept
-  int* pre = box + 2 * 32;                                  // [126] prefix of the neighbour range sizes
-  int* rbeg = pre + 126;                                    // [125]
-  int* rmeta = rbeg + 125;                                  // [125]
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int64_t n = G.n;
-  const int ne = G.ne, rho = G.rho, span = 2 * rho + 1, nrange = span * span * span, win = G.win;
-  const int e = blockIdx.x;
-  const int ex = e % ne, ey = (e / ne) % ne, ez = e / (ne * ne);
-  for (int t = threadIdx.x; t < PER; t += blockDim.x) zrow[t] = make_float2(0.0f, 0.0f);
-  if (warp == 0) {
-    int tot = 0;
-    for (int r0 = 0; r0 < nrange; r0 += 32) {
-      const int r = r0 + lane;
-      int cnt = 0;
-      if (r < nrange) {
-        const int dx = r % span - rho, dy = (r / span) % span - rho, dz = r / (span * span) - rho;
-        const int nb = (wrapi(ez + dz, ne) * ne + wrapi(ey + dy, ne)) * ne + wrapi(ex + dx, ne);
-        const int b0 = G.start[nb];
-        cnt = G.start[nb + 1] - b0;
-        rbeg[r] = b0;
-        rmeta[r] = ((rho - dx) * N1) | (((rho - dy) * N1) << 8) | (((rho - dz) * N1) << 16);
-      }
-      int x = cnt;
-#pragma unroll
-      for (int o = 1; o < 32; o <<= 1) {
-        const int y = __shfl_up_sync(0xffffffffu, x, o);
-        if (lane >= o) x += y;
-      }
-      if (r < nrange) pre[r + 1] = tot + x;
-      tot += __shfl_sync(0xffffffffu, x, 31);
-    }
-    if (lane == 0) pre[0] = 0;
-  }
-  __syncthreads();
-  const int total = pre[nrange];
-  const int nbatch = (total + 31) / 32;
-  int top = 1;
-  while (2 * top < nrange) top *= 2;
-  // Candidates are taken in blocks of 8 whose order is a multiplicative permutation
-  // blk -> blk mix mod nfull (mix coprime to nfull, near nfull / golden ratio), so that
-  // a batch mixes four distant blocks of the neighbourhood and the warps' shares of a
-  // batch stay even; the trailing partial block keeps its place.
-  const int nfull = total >> 3;
-  int mix = 1;
-  if (nfull > 2) {
-    mix = (int)(0.6180339887 * nfull) | 1;
-    for (;; mix += 2) {
-      int a = nfull, c = mix;
-      while (c) {
-        const int t = a % c;
-        a = c;
-        c = t;
-      }
-      if (a == 1) break;
-    }
-  }
-
-  // Staging of batch b into buffer buf, lane = candidate, in three parts that go to
-  // three different warps: part 0 and 1 the YZ products of the lower and upper k half,
-  // part 2 the A products and the support box.
-  auto cand = [&](int b, int64_t& jj, int& wm) -> bool {
-    int idx = b * 32 + lane;
-    jj = 0;
-    wm = 0;
-    if (idx >= total) return false;
-    if ((idx >> 3) < nfull) idx = (int)(((int64_t)(idx >> 3) * mix) % nfull) * 8 + (idx & 7);
-    int r = 0;
-    for (int stp = top; stp > 0; stp >>= 1)
-      if (r + stp < nrange && pre[r + stp] <= idx) r += stp;
-    jj = rbeg[r] + (idx - pre[r]);
-    wm = rmeta[r];
-    return true;
-  };
-  auto stage_yz = [&](int b, int buf, auto half) {
-    constexpr int H = decltype(half)::value;
-    constexpr int KH = (N1 + 1) / 2;                       // k lines in the lower half
-    constexpr int U0 = H == 0 ? 0 : (KH * N1) / 2;         // float4 range of this half
-    constexpr int U1 = H == 0 ? (KH * N1) / 2 : YZP / 2;
-    int64_t jj;
-    int wm;
-    const bool valid = cand(b, jj, wm);
-    float4* row = reinterpret_cast<float4*>(stage + (size_t)(buf * 32 + lane) * PER);
-    float2 fy[N1], fz[N1];
-    const float2* py = G.fac + ((int64_t)win + ((wm >> 8) & 255)) * n + jj;
-    const float2* pz = G.fac + ((int64_t)2 * win + ((wm >> 16) & 255)) * n + jj;
-#pragma unroll
-    for (int i = 0; i < N1; ++i) {
-      fy[i] = valid ? py[(int64_t)i * n] : make_float2(0.0f, 0.0f);
-      const bool need = (2 * U0) / N1 <= i && i <= (2 * U1 - 1) / N1;
-      fz[i] = (valid && need) ? pz[(int64_t)i * n] : make_float2(0.0f, 0.0f);
-    }
-#pragma unroll
-    for (int u = U0; u < U1; ++u) {
-      float2 v[2];
-#pragma unroll
-      for (int h = 0; h < 2; ++h) {
-        const int q = 2 * u + h;
-        v[h] = q < N1 * N1 ? df_mul2(fy[q % N1], fz[q / N1]) : make_float2(0.0f, 0.0f);
-      }
-      row[u] = make_float4(v[0].x, v[0].y, v[1].x, v[1].y);
-    }
-  };
-  auto stage_a = [&](int b, int buf) {
-    int64_t jj;
-    int wm;
-    const bool valid = cand(b, jj, wm);
-    float4* row = reinterpret_cast<float4*>(stage + (size_t)(buf * 32 + lane) * PER);
-    int ylo = N1, yhi = -1, zlo = N1, zhi = -1;
-    {
-      const float* py = reinterpret_cast<const float*>(G.fac + ((int64_t)win + ((wm >> 8) & 255)) * n + jj);
-      const float* pz = reinterpret_cast<const float*>(G.fac + ((int64_t)2 * win + ((wm >> 16) & 255)) * n + jj);
-#pragma unroll
-      for (int i = 0; i < N1; ++i) {
-        const float y = valid ? py[2 * (int64_t)i * n] : 0.0f;
-        const float z = valid ? pz[2 * (int64_t)i * n] : 0.0f;
-        if (y != 0.0f) {
-          ylo = min(ylo, i);
-          yhi = i;
-        }
-        if (z != 0.0f) {
-          zlo = min(zlo, i);
-          zhi = i;
-        }
-      }
-    }
-    float2 fx[N1], qv[4];
-    bool xany = false;
-    const float2* px = G.fac + (int64_t)(wm & 255) * n + jj;
-#pragma unroll
-    for (int i = 0; i < N1; ++i) {
-      fx[i] = valid ? px[(int64_t)i * n] : make_float2(0.0f, 0.0f);
-      xany = xany || fx[i].x != 0.0f;
-    }
-#pragma unroll
-    for (int c = 0; c < 4; ++c) qv[c] = valid ? G.sq[(int64_t)c * n + jj] : make_float2(0.0f, 0.0f);
-#pragma unroll
-    for (int u = 0; u < 4 * TCP; ++u) {
-      float2 v[2];
-#pragma unroll
-      for (int h = 0; h < 2; ++h) {
-        const int ci = a_col<N1>(2 * u + h);
-        v[h] = ci >= 0 ? df_mul2(qv[ci / N1], fx[ci % N1]) : make_float2(0.0f, 0.0f);
-      }
-      // column pairs of a group as (h0, h1, l0, l1) for the packed accumulators
-      row[YZP / 2 + u] = TCP == 1 ? make_float4(v[0].x, v[0].y, v[1].x, v[1].y)
-                                  : make_float4(v[0].x, v[1].x, v[0].y, v[1].y);
-    }
-    box[buf * 32 + lane] = (yhi >= 0 && zhi >= 0 && xany) ? (ylo | (yhi << 8) | (zlo << 16) | (zhi << 24)) : -1;
-  };
-  // the parts of batch b go to warps 3 b, 3 b + 1, 3 b + 2 (mod NW)
-  auto stage_parts = [&](int b) {
-    const int buf = b & 1;
-#pragma unroll
-    for (int part = 0; part < 3; ++part) {
-      if (warp != (3 * b + part) % NW) continue;
-      if (part == 0) stage_yz(b, buf, std::integral_constant<int, 0>());
-      if (part == 1) stage_yz(b, buf, std::integral_constant<int, 1>());
-      if (part == 2) stage_a(b, buf);
-    }
-  };
-
-  // this lane's outputs and their staged-row offsets
-  const int wj = warp % B::NB, wk = warp / B::NB;
-  const int bq = lane >> 3, g = lane & 7;
-  const int j = 2 * wj + (bq & 1), k = 2 * wk + (bq >> 1);
-  const bool jk_ok = j < N1 && k < N1;
-  const int jk = jk_ok ? k * N1 + j : 0;
-  const int y0 = 2 * wj, z0 = 2 * wk;
-  // columns 2u, 2u + 1 of this lane in packed pairs (H, L); an odd last column in acc1
-  constexpr int NP = TC / 2;
-  float2 AH[NP > 0 ? NP : 1], AL[NP > 0 ? NP : 1];
-#pragma unroll
-  for (int u = 0; u < (NP > 0 ? NP : 1); ++u) AH[u] = AL[u] = make_float2(0.0f, 0.0f);
-  f2 acc1 = {0.0f, 0.0f};
-  auto gemm_batch = [&](int buf) {
-    const float2* sb = stage + (size_t)buf * 32 * PER;
-    const int w = box[buf * 32 + lane];
-    const int ylo = w & 255, yhi = (w >> 8) & 255, zlo = (w >> 16) & 255, zhi = (w >> 24) & 255;
-    const bool rel = w >= 0 && ylo <= y0 + 1 && yhi >= y0 && zlo <= z0 + 1 && zhi >= z0;
-    unsigned m = __ballot_sync(0xffffffffu, rel);
-    // two particles per pass; an odd last one is paired with the zero row, whose
-    // terms leave the accumulators bit for bit unchanged
-    while (m) {
-      const float2* pr[2];
-      pr[0] = sb + (__ffs(m) - 1) * PER;
-      m &= m - 1;
-      pr[1] = m ? sb + (__ffs(m) - 1) * PER : zrow;
-      m &= m - 1;
-#pragma unroll
-      for (int h = 0; h < 2; ++h) {
-      const float2* pq = pr[h];
-      const float2 bv = pq[jk];
-      if constexpr (TCP == 1) {
-        df_fma_acc(acc1, pq[YZP + g], bv);
-      } else {
-#pragma unroll
-        for (int u = 0; u < TCP / 2; ++u) {
-          const float4 v4 = *reinterpret_cast<const float4*>(pq + a_off<N1>(g, 2 * u));
-          if (2 * u + 1 < TC)
-            df_fma_acc2(AH[u], AL[u], make_float2(v4.x, v4.y), make_float2(v4.z, v4.w), bv);
-          else if (2 * u < TC)
-            df_fma_acc(acc1, make_float2(v4.x, v4.z), bv);
-        }
-      }
-      }
-    }
-  };
-
-  if (nbatch > 0) stage_parts(0);
-  __syncthreads();
-  for (int b = 0; b < nbatch; ++b) {
-    if (b + 1 < nbatch) stage_parts(b + 1);
-    gemm_batch(b & 1);
-    __syncthreads();
-  }
-  if (jk_ok) {
-    double* out = G.field + (int64_t)e * 4 * NODES;
-#pragma unroll
-    for (int t = 0; t < TC; ++t) {
-      const int ci = g * TC + t;
-      if (ci < 4 * N1) {
-        const int c = ci / N1, i = ci - c * N1;
-        float h, l;
-        if (TCP == 1 || t >= 2 * NP) {
-          h = acc1.h;
-          l = acc1.l;
-        } else {
-          h = (t & 1) ? AH[t / 2].y : AH[t / 2].x;
-          l = (t & 1) ? AL[t / 2].y : AL[t / 2].x;
-        }
-        out[c * NODES + jk * N1 + i] = (double)h + (double)l;
-      }
-    }
-  }
-}
-
-template <int N1>
-cudaError_t launch_blk(const BlkArgs& G, int64_t nel, cudaStream_t st) {
-  using B = BlkShape<N1>;
-  cudaError_t e = cudaFuncSetAttribute(k_proj_deposit_blk<N1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)B::SMEM);
-  if (e != cudaSuccess) return e;
-  k_proj_deposit_blk<N1><<<(unsigned)nel, 32 * B::NW, B::SMEM, st>>>(G);
-  return cudaGetLastError();
-}
-
-cudaError_t launch_blk_n1(int n1, const BlkArgs& G, int64_t nel, cudaStream_t st) {
-  switch (n1) {
-    case 1: return launch_blk<1>(G, nel, st);
-    case 2: return launch_blk<2>(G, nel, st);
-    case 3: return launch_blk<3>(G, nel, st);
-    case 4: return launch_blk<4>(G, nel, st);
-    case 5: return launch_blk<5>(G, nel, st);
-    case 6: return launch_blk<6>(G, nel, st);
-    case 7: return launch_blk<7>(G, nel, st);
-    case 8: return launch_blk<8>(G, nel, st);
-    default: return cudaErrorInvalidValue;
-  }
-}
-
 }  // namespace
 
 static void deposit_shape(int n1, int* nwarps, int* batch, size_t* smem) {
@@ -762,6 +442,14 @@ pc_status pc_project_impl(pc_ctx* ctx, const pc_particles* p, double* field) {
     F.q = p->q;
     F.fac = ctx->fac;
     F.sq = ctx->sq;
+    if (ctx->n1 <= 8) {
+      F.rec = ctx->fac;
+      F.rs = ctx->rs;
+      F.reach = ctx->reach;
+      F.fxmax = ctx->fxmax;
+      e = cudaMemsetAsync(ctx->fxmax, 0, sizeof(unsigned) * 8, st);
+      if (e != cudaSuccess) goto fail;
+    }
     const int tf = pc_phase_begin(ctx, PC_PH_FACTORS);
     k_proj_factors<<<pc_blocks(n, 128), 128, 0, st>>>(F);
     ctx->launches += 1;
@@ -784,17 +472,13 @@ pc_status pc_project_impl(pc_ctx* ctx, const pc_particles* p, double* field) {
     G.sq = ctx->sq;
     G.field = field;
     if (ctx->n1 <= 8) {
-      BlkArgs K;
-      K.n = n;
-      K.ne = ne;
-      K.rho = ctx->rho;
-      K.win = ctx->win;
-      K.start = ctx->start;
-      K.fac = ctx->fac;
-      K.sq = ctx->sq;
-      K.field = field;
+      if (n == 0) {  // no records: every element's deposit is zero
+        e = cudaMemsetAsync(ctx->fxmax, 0, sizeof(unsigned) * 8, st);
+        if (e != cudaSuccess) goto fail;
+      }
       const int td = pc_phase_begin(ctx, PC_PH_DEPOSIT);
-      e = launch_blk_n1(ctx->n1, K, nel, st);
+      e = pc_fx_deposit_launch(ctx->n1, ne, ctx->rho, ctx->win, ctx->rs, ctx->start, ctx->fac, ctx->reach, ctx->fxmax,
+                               field, ctx->counters, st);
       ctx->launches += 1;
       pc_phase_end(ctx, td);
       if (e != cudaSuccess) goto fail;

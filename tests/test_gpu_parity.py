@@ -377,6 +377,44 @@ def test_project_dense_sampled_elements(name, n):
     assert np.all(err <= FIELD_TOL), err
 
 
+@pytest.mark.parametrize("degree,ne,sigma", [(0, 6, 0.03), (1, 6, 0.03), (2, 6, 0.03), (3, 6, 0.03), (4, 6, 0.03),
+                                               (5, 6, 0.03), (6, 6, 0.03), (7, 6, 0.03), (5, 8, 0.05), (7, 8, 0.05)])
+def test_project_every_degree(degree, ne, sigma):
+    """Full field against the oracle for N + 1 = 1..8 Gauss nodes per axis (every shape of
+    the tensor-core deposit), and with a support spanning 2 elements on each side
+    (sigma 0.05 on 8 elements per side)."""
+    w = inputs.draw("small_8192", seed=12 + degree, n=2500)
+    a = pc.State.from_arrays(w)
+    ctx = pc.Context(a.n, ne, degree, sigma, w["e"], 0.05)
+    f = ctx.new_field()
+    ctx.project(a, f)
+    ctx.sync()
+    R, _ = oracle.project(w["x"], w["q"], ne, degree, sigma, 3.0)
+    assert np.all(field_err(f.cpu().numpy(), R) <= FIELD_TOL)
+
+
+def test_project_crowded_element_in_segments():
+    """6000 particles inside one element's neighbourhood (an element keeps more than 2048
+    of them, so its deposit is accumulated in several segments) and a few far away:
+    the full field against the oracle, and conservation."""
+    rng = np.random.default_rng(21)
+    n = 6000
+    x = 0.5 + 0.05 * (rng.random((3, n)) - 0.5)
+    x[:, :40] = rng.random((3, 40))
+    d = dict(x=x, v=np.zeros((3, n)), r=np.full(n, 1e-4), m=np.ones(n), id=np.arange(n, dtype=np.int32),
+             q=rng.normal(size=(4, n)))
+    a = pc.State.from_arrays(d)
+    ctx = pc.Context(n, 8, 3, 0.02, 0.9, 0.05)
+    f = ctx.new_field()
+    ctx.project(a, f)
+    ctx.sync()
+    F = f.cpu().numpy()
+    R, _ = oracle.project(x, d["q"], 8, 3, 0.02, 3.0)
+    assert np.all(field_err(F, R) <= FIELD_TOL)
+    tot = np.einsum("ecg,g->c", F, quad_weights(8, 3))
+    assert np.all(np.abs(tot - d["q"].sum(axis=1)) <= 1e-12 * np.abs(d["q"]).sum(axis=1))
+
+
 @pytest.mark.parametrize("cs", [1.0, 6.0])
 def test_project_other_cutoffs(cs):
     """Cutoff 1 sigma (most nodes near the edge) and 6 sigma (exp down to -18)."""

@@ -67,7 +67,7 @@ def test_noalloc_allocates_nothing():
 
 
 def test_noalloc_rejects_oversized_problem():
-    n = 200000  # about 476 bytes per particle on a 32^3 mesh of degree 5: beyond 32 MiB
+    n = 200000  # about 512 bytes per particle on a 32^3 mesh of degree 5: beyond 32 MiB
     a = pc.State.empty(n)
     f = torch.empty(32 ** 3, 4, 6 ** 3, dtype=torch.float64, device="cuda")
     with pytest.raises(pc.PcError) as ei:
