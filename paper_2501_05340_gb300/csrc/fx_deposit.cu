@@ -7,23 +7,24 @@
 // a dense contraction over the particles p whose support reaches the element. The
 // factors are double-float (about 48 bits). Each product value v (YZ or A) is
 // scaled by a power of two common to all particles (|v| < 1/2) and written as
-//   v = sum_{d=0..7} s_d 2^(-6 (d+1)) + r,   s_d integers, |r| <= 2^-49,
-// with |s_d| <= 32 except |s_4| <= 128, so every digit is exact in FP16. The tensor
-// core multiplies digit matrices and sums the products in FP32; the cells that
-// carry the leading bits (below) take at most two products of digits 0..3 (each
-// at most 2^10 in magnitude) per particle, so their sums over at most 2048
-// particles stay below 2^23 and are exact, whatever the order. The deposit is
-//   D = 2^(EY + EA) sum_{a,b} 2^(-6 (a + b + 2)) sum_p Y_a[p] A_b[p].
+//   v = sum_{d=0..5} s_d 2^(-8 (d+1)) + r,   s_d integers, |r| <= 2^-49,
+// with |s_d| <= 128 except |s_3| <= 512, so every digit is exact in FP16. The
+// tensor core multiplies digit matrices and sums the products in FP32. The cells
+// whose weight is within 2^-16 of the leading one (r + b <= 2 below) take at most
+// two products of digits 0..2 (each at most 2^14 in magnitude) per particle, so
+// their sums stay below 2^24 and are exact, whatever the order, for up to 1024
+// particles (512 when two products meet in one cell); the other cells weigh 2^-24
+// or less of the leading one, where FP32 rounding stays below 2^-46 of the result.
+// The deposit is
+//   D = 2^(EY + EA) sum_{a,b} 2^(-8 (a + b + 2)) sum_p Y_a[p] A_b[p].
 //
 // Tensor layout: the A operand (M = 128 rows) of MMA group g holds the YZ digits
 // a = R g .. R g + R - 1 (R = floor(128 / n1^2) digit blocks of n1^2 rows); the B
 // operand holds the A digits b = 0..7 (blocks of CP >= 4 n1 rows) and MMA group g
 // writes the accumulator columns from R g CP on. Accumulator cell (r, b) (row block
 // r, column block b) then sums Y_(Rg+r) A_(b-Rg) over all groups g: every product
-// in a cell has the weight 2^(-6 (r + b + 2)). Cells with r + b <= 3 carry the
-// leading 24 bits and hold exact integers; the others are below 2^-48 of the
-// result's scale, where FP32 rounding does not matter. The epilogue adds the cells
-// with their weights in double-float arithmetic and writes FP64.
+// in a cell has the weight 2^(-8 (r + b + 2)). The epilogue adds the cells with
+// their weights in double-float arithmetic and writes FP64.
 //
 // Warp roles of the persistent CTA (one per SM, all 512 tensor-memory columns as
 // two 256-column accumulators so that one element drains while the next
@@ -32,8 +33,8 @@
 // reach bits) and stage their factors; 8 builder warps turn a staged batch into
 // the digit operands; one MMA warp issues the MMAs of each batch in batch order
 // (so the result does not depend on scheduling) and hands finished elements to 4
-// epilogue warps (one per tensor-memory lane quarter). An element with more than
-// 2048 kept particles is deposited in segments that are added in FP64. Every wait
+// epilogue warps (one per tensor-memory lane quarter). An element with more kept
+// particles than one segment holds is deposited in segments added in FP64. Every wait
 // is bounded in wall-clock time: on expiry the kernel records PC_ETIMEOUT, stops
 // issuing, waits (bounded) for its MMAs and frees its tensor memory.
 #include <cuda_fp16.h>
@@ -43,8 +44,9 @@
 
 namespace {
 
-constexpr int kS = 8;                                 // digits per value
-constexpr int kSegMax = 2048;                         // kept particles per accumulation segment
+constexpr int kS = 6;                                 // digits per value
+constexpr float kBase = 256.0f;                       // digit radix (8 bits)
+constexpr float kInvBase = 1.0f / 256.0f;
 constexpr int kGather = 6;                            // gather warps
 constexpr int kBuild = 8;                             // builder warps
 constexpr int kEpi = 4;                               // epilogue warps
@@ -77,6 +79,9 @@ struct FxShape {
   static constexpr int NF = 6;                             // staged-factor slots
   static constexpr int NS0 = (int)((kSmemMax - 1024 - FIXED - NF * FSLOT) / STAGE);
   static constexpr int NS = NS0 > 4 ? 4 : NS0;             // operand stages
+  // kept particles per accumulation segment: the exact cells hold one digit product
+  // per particle when R >= 3 and two when R = 2
+  static constexpr int SEG = R >= 3 ? 1024 : 512;
   __host__ __device__ static constexpr int ncol(int g) { return rup(CP * (kS - R * g), 16); }
   __host__ __device__ static constexpr int col0(int g) { return R * g * CP; }
 };
@@ -162,7 +167,7 @@ struct FxCtl {
   unsigned long long qfull[kQ], qempty[kQ];
   unsigned long long fin;
   int fmeta[8][4];   // element (-1 ends the stream), kept count, first batch, last batch
-  int opmeta[4][4];
+  __align__(16) int opmeta[4][4];
   int qe[kQ], qslot[kQ], qseg[kQ];
   int failed;
   int progress;
@@ -171,20 +176,31 @@ struct FxCtl {
 };
 
 // Waits for the phase of the given parity. Returns false once the block has failed,
-// or after kWaitNs in which no gather warp reported progress.
-__device__ bool fx_wait(FxCtl& C, unsigned long long* bar, uint32_t parity) {
+// or after kWaitNs in which no gather warp reported progress. With backoff the warp
+// sleeps between polls (for waits that usually last microseconds), so that idle
+// warps leave the issue slots and the shared-memory pipe to the working ones.
+__device__ bool fx_wait(FxCtl& C, unsigned long long* bar, uint32_t parity, bool backoff = false) {
   if (mbar_try(bar, parity)) return true;
   unsigned long long t0 = gtime();
   int last = -1;
-  for (;;) {
-    if (mbar_try_sleep(bar, parity)) return true;
-    if (vload(&C.failed)) return false;
-    const unsigned long long now = gtime();
-    if (now - t0 > kWaitNs) {
-      const int p = vload(&C.progress);
-      if (p == last) return false;
-      last = p;
-      t0 = now;
+  unsigned ns = 64;
+  for (int it = 1;; ++it) {
+    if (backoff) {
+      __nanosleep(ns);
+      if (ns < 1024) ns *= 2;
+      if (mbar_try(bar, parity)) return true;
+    } else if (mbar_try_sleep(bar, parity)) {
+      return true;
+    }
+    if ((it & 15) == 0) {
+      if (vload(&C.failed)) return false;
+      const unsigned long long now = gtime();
+      if (now - t0 > kWaitNs) {
+        const int p = vload(&C.progress);
+        if (p == last) return false;
+        last = p;
+        t0 = now;
+      }
     }
   }
 }
@@ -271,7 +287,7 @@ __device__ void fx_gather(const FxSmem<N1>& M, const FxArgs& A, int w, int lane)
     for (int b = (int)((w - q % kGather + kGather) % kGather); b < nb; b += kGather) {
       const int64_t qq = q + b;
       const int fs = (int)(qq % B::NF);
-      if (qq >= B::NF && !fx_wait(C, &C.f_empty[fs], (uint32_t)(((qq / B::NF) - 1) & 1))) {
+      if (qq >= B::NF && !fx_wait(C, &C.f_empty[fs], (uint32_t)(((qq / B::NF) - 1) & 1), true)) {
         if (lane == 0) fail_now(C, A.counters);
         ok = false;
         break;
@@ -331,7 +347,7 @@ __device__ void fx_gather(const FxSmem<N1>& M, const FxArgs& A, int w, int lane)
   // end of the stream: the warp that owns batch q writes the end marker
   if (ok && q % kGather == w) {
     const int fs = (int)(q % B::NF);
-    const bool free_slot = q < B::NF || fx_wait(C, &C.f_empty[fs], (uint32_t)(((q / B::NF) - 1) & 1));
+    const bool free_slot = q < B::NF || fx_wait(C, &C.f_empty[fs], (uint32_t)(((q / B::NF) - 1) & 1), true);
     if (lane == 0) {
       if (!free_slot) fail_now(C, A.counters);
       C.fmeta[fs][0] = -1;
@@ -342,9 +358,9 @@ __device__ void fx_gather(const FxSmem<N1>& M, const FxArgs& A, int w, int lane)
 
 // Digits of a value v = y + w (|v| < 1/2, y the high and w the low part of a
 // double-float product, |w| <= 3 2^-24 |y|): s_d = rint of the remainder scaled by
-// 64^(d+1). The first four come from y alone, exactly (y holds 24 bits); then w
-// joins the remainder, whose rounding there is below 2^-48 of v's scale. |s_4| <=
-// 128, the others <= 32; the remainder after eight digits is below 2^-49.
+// 256^(d+1). The first three come from y alone, exactly (y holds 24 bits); then w
+// joins the remainder, whose rounding there is below 2^-47 of v's scale. |s_3| <=
+// 512, the others <= 128; the remainder after six digits is below 2^-49.
 
 // Builder warp bi: digit operands of every batch, in batch order.
 template <int N1>
@@ -372,8 +388,9 @@ __device__ void fx_build(const FxSmem<N1>& M, const FxArgs& A, int bi, int lane)
         const int t = isA ? it : it - B::NA;
         const int row = 8 * (t >> 5) + (t & 7), o = (t >> 3) & 3;
         if (o >= nok || row >= (isA ? B::JK : B::CI)) continue;
-        // the 8 values of this row for particles 8 o .. 8 o + 7
-        float vy[8], vw[8];
+        // the 8 values of this row for particles 8 o .. 8 o + 7, as 4 pairs of
+        // neighbouring particles on the packed FP32x2 instructions
+        float2 vy[4], vw[4];
         const float2* f0;
         const float2* f1;
         if (isA) {
@@ -384,40 +401,35 @@ __device__ void fx_build(const FxSmem<N1>& M, const FxArgs& A, int bi, int lane)
           f1 = fst + (row % N1) * kFRow + 8 * o;           // kx_i
         }
 #pragma unroll
-        for (int u = 0; u < 8; u += 2) {
-          const float4 a4 = *reinterpret_cast<const float4*>(f0 + u);
-          const float4 b4 = *reinterpret_cast<const float4*>(f1 + u);
+        for (int u = 0; u < 4; ++u) {
+          const float4 a4 = *reinterpret_cast<const float4*>(f0 + 2 * u);
+          const float4 b4 = *reinterpret_cast<const float4*>(f1 + 2 * u);
           // double-float products (a.h + a.l)(b.h + b.l) as an unevaluated high + low pair
-          float p = a4.x * b4.x;
-          float l = fmaf(a4.x, b4.x, -p);
-          l = fmaf(a4.x, b4.y, l);
+          const float2 ah = make_float2(a4.x, a4.z), al = make_float2(a4.y, a4.w);
+          const float2 bh = make_float2(b4.x, b4.z), bl = make_float2(b4.y, b4.w);
+          const float2 p = __fmul2_rn(ah, bh);
+          float2 l = __ffma2_rn(ah, bh, make_float2(-p.x, -p.y));
+          l = __ffma2_rn(ah, bl, l);
           vy[u] = p;
-          vw[u] = fmaf(a4.y, b4.x, l);
-          p = a4.z * b4.z;
-          l = fmaf(a4.z, b4.z, -p);
-          l = fmaf(a4.z, b4.w, l);
-          vy[u + 1] = p;
-          vw[u + 1] = fmaf(a4.w, b4.z, l);
+          vw[u] = __ffma2_rn(al, bh, l);
         }
-        // digits, one per particle and step (see the note above); the first four from the
-        // high parts alone, then the low parts join
-        const float Mg = 12582912.0f;  // 1.5 * 2^23: adding it rounds to an integer
+        // digits, one per particle and step (see the note above); the first three from
+        // the high parts alone, then the low parts join
+        const float2 Mg = make_float2(12582912.0f, 12582912.0f);  // 1.5 * 2^23: adding it rounds to an integer
+        const float2 nMg = make_float2(-12582912.0f, -12582912.0f);
+        const float2 base2 = make_float2(kBase, kBase);
+        const float2 b32 = make_float2(4294967296.0f, 4294967296.0f);
 #pragma unroll
-        for (int u = 0; u < 8; ++u) vy[u] *= 64.0f;
+        for (int u = 0; u < 4; ++u) vy[u] = __fmul2_rn(vy[u], base2);
 #pragma unroll
         for (int k = 0; k < kS; ++k) {
-          float dg[8];
-#pragma unroll
-          for (int u = 0; u < 8; ++u) {
-            if (k == 4) vy[u] = fmaf(vw[u], 1073741824.0f, vy[u]);
-            const float t = vy[u] + Mg;
-            dg[u] = t - Mg;
-            vy[u] = (vy[u] - dg[u]) * 64.0f;
-          }
           uint32_t h[4];
 #pragma unroll
           for (int u = 0; u < 4; ++u) {
-            const __half2 v = __floats2half2_rn(dg[2 * u], dg[2 * u + 1]);
+            if (k == 3) vy[u] = __ffma2_rn(vw[u], b32, vy[u]);
+            const float2 dg = __fadd2_rn(__fadd2_rn(vy[u], Mg), nMg);
+            vy[u] = __fmul2_rn(__fadd2_rn(vy[u], make_float2(-dg.x, -dg.y)), base2);
+            const __half2 v = __floats2half2_rn(dg.x, dg.y);
             h[u] = *reinterpret_cast<const uint32_t*>(&v);
           }
           int off;
@@ -463,14 +475,28 @@ __device__ void fx_mma(const FxSmem<N1>& M, const FxArgs& A, uint32_t tmem, int 
   if (lane == 0) {
     int slot = 0, uses[2] = {0, 0}, t = 0, seg = 0, kept = 0;
     bool started = false, failed = false;
+    // descriptors of stage 0; stage s differs only in the start address field
+    const uint32_t sa0 = smem_u32(M.stage);
+    uint64_t da0[B::G][2], db0[2];
+    uint32_t idesc[B::G];
+#pragma unroll
+    for (int g = 0; g < B::G; ++g) {
+      idesc[g] = (1u << 4) | ((uint32_t)(B::ncol(g) >> 3) << 17) | (8u << 24);
+#pragma unroll
+      for (int h = 0; h < 2; ++h) da0[g][h] = make_desc(sa0 + g * B::ATILE + 256 * h, 128, 512);
+    }
+#pragma unroll
+    for (int h = 0; h < 2; ++h) db0[h] = make_desc(sa0 + B::G * B::ATILE + 256 * h, 128, 512);
     for (int64_t q = 0;; ++q) {
       const int os = (int)(q % B::NS);
-      if (!fx_wait(C, &C.op_full[os], (uint32_t)((q / B::NS) & 1))) {
+      const uint32_t par = (uint32_t)((q / B::NS) & 1);
+      if (!mbar_try(&C.op_full[os], par) && !fx_wait(C, &C.op_full[os], par)) {
         if (!vload(&C.failed)) fail_now(C, A.counters);
         failed = true;
         break;
       }
-      const int e = C.opmeta[os][0], nk = C.opmeta[os][1], first = C.opmeta[os][2], last = C.opmeta[os][3];
+      const int4 mt = *reinterpret_cast<const int4*>(C.opmeta[os]);
+      const int e = mt.x, nk = mt.y, first = mt.z, last = mt.w;
       if (e < 0) break;
       if (first) {
         seg = 0;
@@ -478,7 +504,7 @@ __device__ void fx_mma(const FxSmem<N1>& M, const FxArgs& A, uint32_t tmem, int 
         started = false;
       }
       if (nk > 0) {
-        if (started && kept + nk > kSegMax) {  // close the segment: its cells stay exact
+        if (started && kept + nk > B::SEG) {  // close the segment: its exact cells stay exact
           mma_commit(&C.acc_full[slot]);
           if (!queue_push(C, t++, e, slot, seg++)) {
             failed = true;
@@ -495,17 +521,14 @@ __device__ void fx_mma(const FxSmem<N1>& M, const FxArgs& A, uint32_t tmem, int 
         }
         if (!started) ++uses[slot];
         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-        const uint32_t sa = smem_u32(M.stage + (size_t)os * B::STAGE);
+        const uint64_t so = (uint64_t)((os * B::STAGE) >> 4);
         const uint32_t d0 = tmem + 256u * (uint32_t)slot;
-        const int nh = nk > 16 ? 2 : 1;
-        for (int h = 0; h < nh; ++h) {
 #pragma unroll
-          for (int g = 0; g < B::G; ++g) {
-            const uint32_t idesc = (1u << 4) | ((uint32_t)(B::ncol(g) >> 3) << 17) | (8u << 24);
-            const uint64_t da = make_desc(sa + g * B::ATILE + 256 * h, 128, 512);
-            const uint64_t db = make_desc(sa + B::G * B::ATILE + 256 * h, 128, 512);
-            mma_f16(d0 + (uint32_t)B::col0(g), da, db, idesc, (started || h > 0 || g > 0) ? 1u : 0u);
-          }
+        for (int g = 0; g < B::G; ++g)
+          mma_f16(d0 + (uint32_t)B::col0(g), da0[g][0] + so, db0[0] + so, idesc[g], (started || g > 0) ? 1u : 0u);
+        if (nk > 16) {
+#pragma unroll
+          for (int g = 0; g < B::G; ++g) mma_f16(d0 + (uint32_t)B::col0(g), da0[g][1] + so, db0[1] + so, idesc[g], 1u);
         }
         started = true;
         kept += nk;
@@ -544,10 +567,10 @@ __device__ __forceinline__ void tmem_ld8(uint32_t taddr, uint32_t u[8]) {
       : "r"(taddr));
 }
 
-// df32 a + b / 64 for an FP32 a and a df32 b.
+// df32 a + b / 256 for an FP32 a and a df32 b.
 __device__ __forceinline__ f2 horner_step(float a, f2 b) {
-  const f2 s = two_sum(a, b.h * 0.015625f);
-  return fast_two_sum(s.h, s.l + b.l * 0.015625f);
+  const f2 s = two_sum(a, b.h * kInvBase);
+  return fast_two_sum(s.h, s.l + b.l * kInvBase);
 }
 
 // Epilogue warp eq (tensor-memory lanes 32 (warp % 4) ..): drains the queue in order.
@@ -562,7 +585,7 @@ __device__ void fx_epilogue(const FxSmem<N1>& M, const FxArgs& A, uint32_t tmem,
   const bool rvalid = r < B::R;
   int seen[2] = {0, 0};
   for (int t = 0;; ++t) {
-    if (!fx_wait(C, &C.qfull[t % kQ], (uint32_t)((t / kQ) & 1))) {
+    if (!fx_wait(C, &C.qfull[t % kQ], (uint32_t)((t / kQ) & 1), true)) {
       if (lane == 0 && eq == 0 && !vload(&C.failed)) fail_now(C, A.counters);
       return;
     }
@@ -571,7 +594,7 @@ __device__ void fx_epilogue(const FxSmem<N1>& M, const FxArgs& A, uint32_t tmem,
     if (lane == 0) mbar_arrive(&C.qempty[t % kQ]);
     if (e < 0) return;
     if (slot >= 0) {
-      if (!fx_wait(C, &C.acc_full[slot], (uint32_t)(seen[slot] & 1))) {
+      if (!fx_wait(C, &C.acc_full[slot], (uint32_t)(seen[slot] & 1), true)) {
         if (lane == 0 && !vload(&C.failed)) fail_now(C, A.counters);
         return;
       }
@@ -580,26 +603,17 @@ __device__ void fx_epilogue(const FxSmem<N1>& M, const FxArgs& A, uint32_t tmem,
       const uint32_t ta = tmem + 256u * (uint32_t)slot + ((uint32_t)(32 * quarter) << 16);
 #pragma unroll 1
       for (int cb = 0; cb < B::CP / 8; ++cb) {
-        f2 P[8];
-        uint32_t u[4][8];
+        uint32_t u[kS][8];
 #pragma unroll
-        for (int b = 0; b < 4; ++b) tmem_ld8(ta + (uint32_t)((b + 4) * B::CP + 8 * cb), u[b]);
-        asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-#pragma unroll
-        for (int x = 0; x < 8; ++x) {
-          P[x] = {__uint_as_float(u[3][x]), 0.0f};
-#pragma unroll
-          for (int b = 2; b >= 0; --b) P[x] = horner_step(__uint_as_float(u[b][x]), P[x]);
-        }
-#pragma unroll
-        for (int b = 0; b < 4; ++b) tmem_ld8(ta + (uint32_t)(b * B::CP + 8 * cb), u[b]);
+        for (int b = 0; b < kS; ++b) tmem_ld8(ta + (uint32_t)(b * B::CP + 8 * cb), u[b]);
         asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 #pragma unroll
         for (int x = 0; x < 8; ++x) {
           const int ci = 8 * cb + x;
+          f2 P = {__uint_as_float(u[kS - 1][x]), 0.0f};
 #pragma unroll
-          for (int b = 3; b >= 0; --b) P[x] = horner_step(__uint_as_float(u[b][x]), P[x]);
-          if (rvalid && ci < B::CI) M.comb[(size_t)row * B::CI + ci] = make_float2(P[x].h, P[x].l);
+          for (int b = kS - 2; b >= 0; --b) P = horner_step(__uint_as_float(u[b][x]), P);
+          if (rvalid && ci < B::CI) M.comb[(size_t)row * B::CI + ci] = make_float2(P.h, P.l);
         }
       }
       asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
@@ -607,8 +621,11 @@ __device__ void fx_epilogue(const FxSmem<N1>& M, const FxArgs& A, uint32_t tmem,
       if (lane == 0) mbar_arrive(&C.acc_empty[slot]);
       asm volatile("bar.sync 1, %0;" ::"n"(32 * kEpi) : "memory");
     }
-    // outputs: field[e][c][jk][i] = 2^(ey + ec - 12) sum_r 2^(-6 r) P_r[jk][c i]
+    // outputs: field[e][c][jk][i] = 2^(ey + ec - 16) sum_r 2^(-8 r) P_r[jk][c i]
     double* out = A.field + (int64_t)e * 4 * NODES;
+    double sc[4];
+#pragma unroll
+    for (int c = 0; c < 4; ++c) sc[c] = ldexp(1.0, C.ey + C.ec[c] - 16);
     for (int o = eq * 32 + lane; o < 4 * NODES; o += 32 * kEpi) {
       const int c = o / NODES, rem = o - c * NODES, ojk = rem / N1, i = rem - ojk * N1;
       double val = 0.0;
@@ -618,9 +635,9 @@ __device__ void fx_epilogue(const FxSmem<N1>& M, const FxArgs& A, uint32_t tmem,
 #pragma unroll
         for (int rr = B::R - 1; rr >= 0; --rr) {
           const float2 v = M.comb[(size_t)(rr * B::JK + ojk) * B::CI + ci];
-          Q = df_add({v.x, v.y}, {Q.h * 0.015625f, Q.l * 0.015625f});
+          Q = df_add({v.x, v.y}, {Q.h * kInvBase, Q.l * kInvBase});
         }
-        val = ldexp((double)Q.h + (double)Q.l, C.ey + C.ec[c] - 12);
+        val = ((double)Q.h + (double)Q.l) * sc[c];
       }
       if (seg == 0)
         out[o] = val;

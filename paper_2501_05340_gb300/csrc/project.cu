@@ -77,7 +77,7 @@ struct FactorArgs {
   const double* q;
   float2* fac;  // [3][win][n] normalised 1-D factors k_a / Z_a (df32)
   float2* sq;   // [4][n] sources times (2/h)^3 (df32)
-  // record layout (tensor-core deposit), used instead of fac / sq when rec is set:
+  // record layout (tensor-core deposit, k_proj_records):
   // rec[k][rs] = the 3 win factors (axis-major), then the 4 sources; reach[k] bit
   // 8 a + w set when axis a has a non-zero factor in window element w; fxmax[0] the
   // largest factor and fxmax[1 + c] the largest |source c| (bits of non-negative
@@ -95,78 +95,145 @@ struct FactorArgs {
 // then everything runs in df32. A node whose df32 distance is within 1e-5
 // relative of the cutoff is re-decided with the FP64 expression of the plain
 // definition, so both sides include exactly the same nodes.
-__global__ void __launch_bounds__(128) k_proj_factors(FactorArgs F) {
+// Unnormalised factor k_a of window node w for a particle at element-relative
+// position t (df32) in element ea of its axis, coordinate xa (for the FP64
+// re-decision near the cutoff).
+__device__ __forceinline__ f2 window_factor(const FactorArgs& F, f2 t, int ea, double xa, int w) {
+  const int i = w % F.n1;
+  const f2 dl = df_add(F.sw[w], df_neg(t));
+  const float ad = fabsf(dl.h);
+  bool inside;
+  if (fabsf(ad - F.rce) > 1e-5f * F.rce) {
+    inside = ad < F.rce;
+  } else {
+    const int o = w / F.n1 - F.rho;
+    const int ge = wrapi(ea + o, F.ne);
+    const double X = ((double)ge + 0.5 * (F.eta[i] + 1.0)) * F.h;
+    inside = fabs(minimg(X - xa)) <= F.rc;
+  }
+  f2 f = {0.0f, 0.0f};
+  if (inside) {
+    f2 d2 = two_prod(dl.h, dl.h);
+    d2.l = fmaf(2.0f * dl.h, dl.l, d2.l);
+    d2 = fast_two_sum(d2.h, d2.l);
+    f = df_exp_neg(df_neg(df_mul(d2, F.c2)), F.tab);
+  }
+  return f;
+}
+
+// Record layout for the tensor-core deposit, WIN = (2 rho + 1) n1 window nodes per
+// axis: one thread per particle, each axis' window held in registers, normalised
+// and written once in 16-byte pairs; reach bits and the maxima of the digit scales.
+template <int WIN>
+__global__ void __launch_bounds__(128) k_proj_records(FactorArgs F) {
   const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   const int64_t n = F.n;
-  const bool recs = F.rec != nullptr;
   float fmax = 0.0f, qmax[4] = {0.0f, 0.0f, 0.0f, 0.0f};
   if (k < n) {
     const int64_t p = F.perm[k];
-    float2* rk = recs ? F.rec + k * F.rs : nullptr;
-    auto slot = [&](int a, int w) -> float2* {
-      return recs ? rk + a * F.win + w : &F.fac[((int64_t)a * F.win + w) * n + k];
-    };
+    float2* rk = F.rec + k * F.rs;
     int reach = 0;
+#pragma unroll 1
     for (int a = 0; a < 3; ++a) {
       const double xa = F.x[a * n + p];
       const int ea = cell_of(xa, F.ne);
       const f2 t = df_from_double(xa * (double)F.ne - (double)ea);
+      f2 f[WIN];
       f2 Z = {0.0f, 0.0f};
-      for (int w = 0; w < F.win; ++w) {
-        const int i = w % F.n1;
-        const f2 dl = df_add(F.sw[w], df_neg(t));
-        const float ad = fabsf(dl.h);
-        bool inside;
-        if (fabsf(ad - F.rce) > 1e-5f * F.rce) {
-          inside = ad < F.rce;
-        } else {
-          const int o = w / F.n1 - F.rho;
-          const int ge = wrapi(ea + o, F.ne);
-          const double X = ((double)ge + 0.5 * (F.eta[i] + 1.0)) * F.h;
-          inside = fabs(minimg(X - xa)) <= F.rc;
-        }
-        f2 f = {0.0f, 0.0f};
-        if (inside) {
-          f2 d2 = two_prod(dl.h, dl.h);
-          d2.l = fmaf(2.0f * dl.h, dl.l, d2.l);
-          d2 = fast_two_sum(d2.h, d2.l);
-          f = df_exp_neg(df_neg(df_mul(d2, F.c2)), F.tab);
-          Z = df_add(Z, df_mul(f, F.wq[i]));
-        }
-        *slot(a, w) = make_float2(f.h, f.l);
+#pragma unroll
+      for (int w = 0; w < WIN; ++w) {
+        f[w] = window_factor(F, t, ea, xa, w);
+        if (f[w].h != 0.0f) Z = df_add(Z, df_mul(f[w], F.wq[w % F.n1]));
       }
       const f2 rz = df_recip(Z);
-      for (int w = 0; w < F.win; ++w) {
-        float2* sl = slot(a, w);
-        const float2 v = *sl;
-        if (v.x != 0.0f) {
-          const f2 r = df_mul({v.x, v.y}, rz);
-          *sl = make_float2(r.h, r.l);
-          fmax = fmaxf(fmax, fabsf(r.h));
+#pragma unroll
+      for (int w = 0; w < WIN; ++w) {
+        if (f[w].h != 0.0f) {
+          f[w] = df_mul(f[w], rz);
+          fmax = fmaxf(fmax, fabsf(f[w].h));
           reach |= 1 << (8 * a + w / F.n1);
         }
       }
+      float2* dst = rk + a * WIN;
+      if ((WIN & 1) == 0) {
+#pragma unroll
+        for (int w = 0; w < WIN; w += 2)
+          *reinterpret_cast<float4*>(dst + w) = make_float4(f[w].h, f[w].l, f[w + 1].h, f[w + 1].l);
+      } else {
+#pragma unroll
+        for (int w = 0; w < WIN; ++w) dst[w] = make_float2(f[w].h, f[w].l);
+      }
     }
+    f2 qs[4];
 #pragma unroll
     for (int c = 0; c < 4; ++c) {
-      const f2 qs = df_mul(df_from_double(F.q[c * n + p]), F.scale);
-      if (recs)
-        rk[3 * F.win + c] = make_float2(qs.h, qs.l);
-      else
-        F.sq[c * n + k] = make_float2(qs.h, qs.l);
-      qmax[c] = fabsf(qs.h);
+      qs[c] = df_mul(df_from_double(F.q[c * n + p]), F.scale);
+      qmax[c] = fabsf(qs[c].h);
     }
-    if (recs) F.reach[k] = reach;
+    float2* dq = rk + 3 * WIN;
+    if ((WIN & 1) == 0) {
+      *reinterpret_cast<float4*>(dq) = make_float4(qs[0].h, qs[0].l, qs[1].h, qs[1].l);
+      *reinterpret_cast<float4*>(dq + 2) = make_float4(qs[2].h, qs[2].l, qs[3].h, qs[3].l);
+    } else {
+#pragma unroll
+      for (int c = 0; c < 4; ++c) dq[c] = make_float2(qs[c].h, qs[c].l);
+    }
+    F.reach[k] = reach;
   }
-  if (recs) {
-    // block-free maximum: warp reduction of the float bits, one atomic per warp
-    unsigned v = __reduce_max_sync(0xffffffffu, __float_as_uint(fmax));
-    if ((threadIdx.x & 31) == 0) atomicMax(&F.fxmax[0], v);
+  // warp reduction of the float bits, one atomic per warp
+  unsigned v = __reduce_max_sync(0xffffffffu, __float_as_uint(fmax));
+  if ((threadIdx.x & 31) == 0) atomicMax(&F.fxmax[0], v);
 #pragma unroll
-    for (int c = 0; c < 4; ++c) {
-      v = __reduce_max_sync(0xffffffffu, __float_as_uint(qmax[c]));
-      if ((threadIdx.x & 31) == 0) atomicMax(&F.fxmax[1 + c], v);
+  for (int c = 0; c < 4; ++c) {
+    v = __reduce_max_sync(0xffffffffu, __float_as_uint(qmax[c]));
+    if ((threadIdx.x & 31) == 0) atomicMax(&F.fxmax[1 + c], v);
+  }
+}
+
+cudaError_t launch_records(int win, const FactorArgs& F, cudaStream_t st) {
+  const int nb = pc_blocks(F.n, 128);
+  switch (win) {
+#define PC_REC_CASE(W) \
+  case W:              \
+    k_proj_records<W><<<nb, 128, 0, st>>>(F); \
+    return cudaGetLastError();
+    PC_REC_CASE(3) PC_REC_CASE(5) PC_REC_CASE(6) PC_REC_CASE(9) PC_REC_CASE(10) PC_REC_CASE(12) PC_REC_CASE(15)
+    PC_REC_CASE(18) PC_REC_CASE(20) PC_REC_CASE(21) PC_REC_CASE(24) PC_REC_CASE(25) PC_REC_CASE(30) PC_REC_CASE(35)
+    PC_REC_CASE(40)
+#undef PC_REC_CASE
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+__global__ void __launch_bounds__(128) k_proj_factors(FactorArgs F) {
+  const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const int64_t n = F.n;
+  if (k >= n) return;
+  const int64_t p = F.perm[k];
+  for (int a = 0; a < 3; ++a) {
+    const double xa = F.x[a * n + p];
+    const int ea = cell_of(xa, F.ne);
+    const f2 t = df_from_double(xa * (double)F.ne - (double)ea);
+    f2 Z = {0.0f, 0.0f};
+    for (int w = 0; w < F.win; ++w) {
+      const f2 f = window_factor(F, t, ea, xa, w);
+      if (f.h != 0.0f) Z = df_add(Z, df_mul(f, F.wq[w % F.n1]));
+      F.fac[((int64_t)a * F.win + w) * n + k] = make_float2(f.h, f.l);
     }
+    const f2 rz = df_recip(Z);
+    for (int w = 0; w < F.win; ++w) {
+      float2* slot = &F.fac[((int64_t)a * F.win + w) * n + k];
+      const float2 v = *slot;
+      if (v.x != 0.0f) {
+        const f2 r = df_mul({v.x, v.y}, rz);
+        *slot = make_float2(r.h, r.l);
+      }
+    }
+  }
+#pragma unroll
+  for (int c = 0; c < 4; ++c) {
+    const f2 qs = df_mul(df_from_double(F.q[c * n + p]), F.scale);
+    F.sq[c * n + k] = make_float2(qs.h, qs.l);
   }
 }
 
@@ -451,7 +518,12 @@ pc_status pc_project_impl(pc_ctx* ctx, const pc_particles* p, double* field) {
       if (e != cudaSuccess) goto fail;
     }
     const int tf = pc_phase_begin(ctx, PC_PH_FACTORS);
-    k_proj_factors<<<pc_blocks(n, 128), 128, 0, st>>>(F);
+    if (ctx->n1 <= 8) {
+      e = launch_records(ctx->win, F, st);
+      if (e != cudaSuccess) goto fail;
+    } else {
+      k_proj_factors<<<pc_blocks(n, 128), 128, 0, st>>>(F);
+    }
     ctx->launches += 1;
     pc_phase_end(ctx, tf);
   }

@@ -393,10 +393,12 @@ def test_project_every_degree(degree, ne, sigma):
     assert np.all(field_err(f.cpu().numpy(), R) <= FIELD_TOL)
 
 
-def test_project_crowded_element_in_segments():
-    """6000 particles inside one element's neighbourhood (an element keeps more than 2048
-    of them, so its deposit is accumulated in several segments) and a few far away:
-    the full field against the oracle, and conservation."""
+@pytest.mark.parametrize("degree", [3, 7])
+def test_project_crowded_element_in_segments(degree):
+    """6000 particles inside one element's neighbourhood (an element keeps more of them
+    than one accumulation segment holds, 1024 for degree 3 and 512 for degree 7, so its
+    deposit is accumulated in several segments) and a few far away: the full field
+    against the oracle, and conservation."""
     rng = np.random.default_rng(21)
     n = 6000
     x = 0.5 + 0.05 * (rng.random((3, n)) - 0.5)
@@ -404,14 +406,14 @@ def test_project_crowded_element_in_segments():
     d = dict(x=x, v=np.zeros((3, n)), r=np.full(n, 1e-4), m=np.ones(n), id=np.arange(n, dtype=np.int32),
              q=rng.normal(size=(4, n)))
     a = pc.State.from_arrays(d)
-    ctx = pc.Context(n, 8, 3, 0.02, 0.9, 0.05)
+    ctx = pc.Context(n, 8, degree, 0.02, 0.9, 0.05)
     f = ctx.new_field()
     ctx.project(a, f)
     ctx.sync()
     F = f.cpu().numpy()
-    R, _ = oracle.project(x, d["q"], 8, 3, 0.02, 3.0)
+    R, _ = oracle.project(x, d["q"], 8, degree, 0.02, 3.0)
     assert np.all(field_err(F, R) <= FIELD_TOL)
-    tot = np.einsum("ecg,g->c", F, quad_weights(8, 3))
+    tot = np.einsum("ecg,g->c", F, quad_weights(8, degree))
     assert np.all(np.abs(tot - d["q"].sum(axis=1)) <= 1e-12 * np.abs(d["q"]).sum(axis=1))
 
 
