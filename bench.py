@@ -33,13 +33,11 @@ METRIC = "particle-steps/s collide+project (FP64)"
 UNIT = "particle-steps/s"
 # FP64 pipe of a GB300: 152 SMs x 2 FP64 FMA per clock x 2 flop x 2.07 GHz (max SM clock).
 FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12
-# FP32 pipe: 152 SMs x 128 lanes x 2.07 GHz, operations (an FMA counts once) per second.
-FP32_PIPE_TOPS = 152 * 128 * 2.07e9 / 1e12
 # DRAM bytes (read + write) per launch of the dominant kernels at the bench workloads, from one
 # ncu capture of each (dram__bytes_read.sum + dram__bytes_write.sum, summarised under profiles/);
 # None once a kernel has changed since its capture.
-DEPOSIT_KERNEL = "k_proj_deposit_blk"
-DEPOSIT_DRAM_BYTES = 753.9e6   # k_proj_deposit_blk<6>, dense_1m
+DEPOSIT_KERNEL = "k_fx_deposit"
+DEPOSIT_DRAM_BYTES = 744.2e6   # k_fx_deposit<6>, dense_1m
 TC_DEPOSIT_DRAM_BYTES = 3.44e9  # k_tc_deposit<0>, mixed_16m
 
 
@@ -270,10 +268,11 @@ def deposit_roofline(x, wl, n, dep_ms, step_ms):
     """HBM roofline of the FP64 deposit (the step's dominant kernel): algorithmic bytes per
     launch = particles x (x 24 B + q 32 B) read once + the field written once (8 B per node
     and component), over the kernel's mean CUDA-event duration, against the measured HBM
-    copy bandwidth; the whole step beside it. The arithmetic that really bounds the kernel
-    is stated too: 8 flop (4 multiply-adds, one per source component) per (particle, Gauss
-    node inside its box support) of the method, computed FP64-accurately in double-float on
-    the FP32 pipe, against the FP64 pipe's derived peak."""
+    copy bandwidth; the whole step beside it. What really bounds the kernel is stated too:
+    the method's 8 flop (4 multiply-adds, one per source component) per (particle, Gauss
+    node inside its box support), computed FP64-accurately as an exact fixed-point digit
+    contraction on the tensor cores whose digit operands are built on the CUDA cores,
+    against the FP64 pipe's derived peak."""
     peak, src = hbm_peak()
     nel, nodes = wl.ne ** 3, (wl.degree + 1) ** 3
     algo = n * 56 + nel * 4 * nodes * 8
@@ -292,14 +291,13 @@ def deposit_roofline(x, wl, n, dep_ms, step_ms):
             "kernel_ms": dep_ms,
             "step": {"algorithmic_bytes": step_algo, "achieved": step_gbs, "frac": step_gbs / peak,
                      "algorithmic": "144 B per particle (read x, v, r, m, q; write x, v) + the field"},
-            "alu": {"bound_by": "FP64-accurate multiply-adds (double-float on the FP32 pipe)",
+            "alu": {"bound_by": "digit operands of the FP64-accurate tensor-core contraction, built on the CUDA "
+                                "cores (54 % issue, no pipe saturated: profiles/k_fx_deposit_dense_1m.md)",
                     "method_flop": 8.0 * support,
                     "method_flop_per_unit": "8 per (particle, Gauss node inside its box support)",
                     "achieved_fp64_equivalent_tflops": 8.0 * support / sec / 1e12,
                     "fp64_pipe_peak_tflops": FP64_PEAK_TFLOPS,
-                    "frac_of_fp64_pipe": 8.0 * support / sec / 1e12 / FP64_PEAK_TFLOPS,
-                    "fp32_pipe_ops_df32": 48.0 * support,
-                    "fp32_pipe_frac_df32": 48.0 * support / sec / 1e12 / FP32_PIPE_TOPS}}
+                    "frac_of_fp64_pipe": 8.0 * support / sec / 1e12 / FP64_PEAK_TFLOPS}}
 
 
 def mixed_run(args, rank, torch, pc, stream, workload="mixed_16m"):
