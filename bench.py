@@ -53,7 +53,8 @@ def parse():
     ap.add_argument("--no-mixed", action="store_true")
     ap.add_argument("--no-operators", action="store_true")
     ap.add_argument("--no-adjoint", action="store_true")
-    ap.add_argument("--curved", action="store_true", help="also time the 67M-particle curved-mesh workload")
+    ap.add_argument("--no-curved", action="store_true",
+                    help="skip the 67M-particle curved-mesh workload (its state takes minutes to draw on the host)")
     ap.add_argument("--mixed-steps", type=int, default=5)
     return ap.parse_args()
 
@@ -215,8 +216,11 @@ def run_ours(args, ws, rank, local):
     if not args.no_adjoint and args.workload == "dense_1m":
         adjoint = adjoint_run(args, w, wl, stream, torch, pc)
     curved = None
-    if args.curved:
-        curved = curved_run(args, rank, torch, pc, stream)
+    if not args.no_curved:
+        try:
+            curved = curved_run(args, rank, torch, pc, stream)
+        except (RuntimeError, MemoryError, pc.PcError) as exc:  # keep the line; say why the leg is missing
+            curved = {"workload": "curved_67m", "error": str(exc)[:300]}
     mixed = None
     if not args.no_mixed:
         mixed = mixed_run(args, rank, torch, pc, stream)
@@ -232,15 +236,22 @@ def run_ours(args, ws, rank, local):
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": t_max / args.steps, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": "f64", "data": "synthetic (seeded random sequential addition, N(0,1) velocities and sources)",
-        "config": {"workload": args.workload, "particles_per_gpu": n, "mesh": "%d^3 hex, degree %d" % (wl.ne, wl.degree),
-                   "sigma": wl.sigma, "cutoff": "3 sigma box", "dt": dt, "restitution": w["e"],
-                   "phi": round(w["phi"], 4), "l2": "inputs larger than L2 (state 105 MB + field 226 MB + scratch)",
-                   "parallelism": "independent replica per GPU" if ws > 1 else "1 GPU"},
+        "config": bench_config(args, w, ws),
         "phase_ms_per_call": phase_ms, "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
         "gpu_launches": launches, "clocks": clocks, "mixed": mixed, "operators": operators, "adjoint": adjoint, "curved": curved,
         "collide_stats": {k: st[k] for k in ("pairs", "candidates", "worklist", "rounds", "fp64_solves",
                                               "max_candidates", "cells_per_side", "stencil")},
     }
+
+
+def bench_config(args, w, ws):
+    """The workload description both arms print."""
+    wl = inputs.WORKLOADS[args.workload]
+    return {"workload": args.workload, "particles_per_gpu": int(w["x"].shape[1]),
+            "mesh": "%d^3 hex, degree %d" % (wl.ne, wl.degree), "sigma": wl.sigma,
+            "cutoff": "%g sigma %s" % (wl.cutoff_sigmas, wl.cutoff), "dt": w["dt"], "restitution": w["e"],
+            "phi": round(w["phi"], 4), "l2": "inputs larger than L2 (state 105 MB + field 226 MB + scratch)",
+            "parallelism": "independent replica per GPU" if ws > 1 else "1 GPU"}
 
 
 def measured_peaks():
@@ -358,8 +369,21 @@ def mixed_run(args, rank, torch, pc, stream, workload="mixed_16m"):
                        "algorithmic": "2*128*64*16 flop per MMA, %d MMAs (16 kept particles each) per launch"
                                       % pairs["chunks"]}
     out["kept_particle_element_pairs"] = pairs["pairs"]
+    # per-field error of the tensor-core fields (FP16 and BF16 splits) of the final mixed
+    # state against the FP64 path's field of the same state (the FP64 path is held to
+    # 1e-12 of the FP64 oracle by the parity tests; the sampled oracle comparison of the
+    # FP32 fields at this size is in the tests too): normwise per component
+    fbf = ctx.new_field_f32()
+    ctx.project_f32(a, fbf, "bf16")
+    nc = ctx.cells_per_side
+    cell = a.cell.long()
+    cx = torch.stack([cell % nc, (cell // nc) % nc, cell // (nc * nc)]).double()
+    s_ref = pc.State(((cx + a.o.double()) / nc).contiguous(), a.v.double().contiguous(), a.r.double(),
+                     a.m.double(), a.id.clone(), a.q.double().contiguous())
+    fields32 = {"f16": f32, "bf16": fbf}
+    torch.cuda.synchronize()
     ctx.close()
-    del a, b, f32
+    del b
     # FP64 path on the same workload (one step after one warm-up)
     with torch.cuda.stream(stream):
         c64 = pc.Context(n, wl.ne, wl.degree, wl.sigma, w["e"], pc.reach_of(w["r"], w["v"], dt),
@@ -377,7 +401,14 @@ def mixed_run(args, rank, torch, pc, stream, workload="mixed_16m"):
     c64.sync()
     out["fp64_ms_per_step_same_workload"] = ev0.elapsed_time(ev1)
     out["speedup_vs_fp64"] = out["fp64_ms_per_step_same_workload"] / ms
+    c64.project(s_ref, f64)
+    c64.sync()
+    den = f64.abs().amax(dim=(0, 2))
+    out["field_error_vs_fp64_path"] = {
+        tc: [float(v) for v in ((fl.double() - f64).abs().amax(dim=(0, 2)) / den).cpu()] for tc, fl in fields32.items()}
+    out["field_error_metric"] = "max |F_tc - F_fp64| / max |F_fp64| per component (momentum x, y, z; energy)"
     c64.close()
+    del fields32, fbf, f32, a, s_ref
     return out
 
 
@@ -476,8 +507,8 @@ def e2e_run(args, ctx, w, n, dt, stream, torch, pc, dist, ws):
 def curved_run(args, rank, torch, pc, stream, workload="curved_67m"):
     """The curved-mesh workload: 67,108,864 spheres on the 128^3 degree-3 mesh curved by
     the sine map, per step pc_collide_f32 + pc_project_curved_f32 (FP32 storage, spherical
-    cutoff, Jacobian weights, Newton localisation). Not in the default run: drawing the
-    state takes minutes on the host."""
+    cutoff, Jacobian weights, Newton localisation). Drawing the state takes minutes on
+    the host; --no-curved skips it."""
     wl = inputs.WORKLOADS[workload]
     w = inputs.draw(workload, seed=rank)
     n, dt = w["x"].shape[1], w["dt"]
@@ -782,7 +813,7 @@ def run_reference(args, ws, rank):
     return {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": 1e3 * tot / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic", "impl": "reference",
-            "config": {"workload": args.workload, "particles_per_gpu": n},
+            "config": bench_config(args, w, ws),
             "cpu_baseline": {"value": value, "unit": UNIT, "cores": pool.procs, "kind": "oracle",
                              "extrapolated": True, "sample_fraction_project": 1.0 / 64, "nproc": os.cpu_count(),
                              "cpu_model": cpu_model(),

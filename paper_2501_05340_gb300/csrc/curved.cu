@@ -159,45 +159,63 @@ __global__ void __launch_bounds__(128) k_curved_prep(CPrepArgs A) {
     int e = (int)(xip[a] * (float)ne);
     ea[a] = e < 0 ? 0 : (e >= ne ? ne - 1 : e);
   }
-  // 1-D logical candidates per axis: the window's nodes within rcl of xi_p
+  // The window's nodes, plane by plane and row by row: a node whose logical distance
+  // to xi_p exceeds rcl is outside the physical ball (|Phi(a) - Phi(b)| >= (1 - L)|a - b|),
+  // so whole planes and rows are skipped before any trigonometry; the sines of a
+  // plane's z and a row's y are taken once.
   const int win = (2 * A.rho + 1) * n1;
-  int nl[3] = {0, 0, 0};
-  int lw[3][64];
-  for (int a = 0; a < 3; ++a)
-    for (int w = 0; w < win; ++w) {
-      const int o = w / n1 - A.rho, i = w % n1;
-      const float xg = ((float)(ea[a] + o) + A.s[i]) * A.hf;
-      if (fabsf(xg - xip[a]) <= A.rcl) lw[a][nl[a]++] = w;
-    }
   const float g = 6.283185307179586f * A.amp;
+  const float rcl2 = A.rcl * A.rcl;
   float Z = 0.0f;
-  for (int kz = 0; kz < nl[2]; ++kz)
-    for (int ky = 0; ky < nl[1]; ++ky)
-      for (int kx = 0; kx < nl[0]; ++kx) {
-        const int w3[3] = {lw[0][kx], lw[1][ky], lw[2][kz]};
-        float sn[3], cs[3];
-        double xig[3];
-        float dist[3];
-        for (int a = 0; a < 3; ++a) {
-          const int o = w3[a] / n1 - A.rho, i = w3[a] % n1;
-          const f2 xg = df_mul(two_sum((float)(ea[a] + o), A.s[i]), A.h);  // logical node coordinate
-          sincospif(2.0f * xg.h, &sn[a], &cs[a]);
-          xig[a] = ((double)wrapi(ea[a] + o, ne) + 0.5 * (A.eta[i] + 1.0)) * A.hd;
-          const f2 dd = df_add(xg, df_neg(x[a]));
-          dist[a] = dd.h + dd.l;
-        }
-        const float dx = minimgf(dist[0] + A.amp * sn[1] * sn[2]);
-        const float dy = minimgf(dist[1] + A.amp * sn[2] * sn[0]);
-        const float dz = minimgf(dist[2] + A.amp * sn[0] * sn[1]);
+  for (int wz = 0; wz < win; ++wz) {
+    const int oz = wz / n1 - A.rho, iz = wz % n1;
+    const f2 xgz = df_mul(two_sum((float)(ea[2] + oz), A.s[iz]), A.h);
+    const float lz = xgz.h - xip[2];
+    if (fabsf(lz) > A.rcl) continue;
+    float snz, csz;
+    sincospif(2.0f * xgz.h, &snz, &csz);
+    const f2 ddz = df_add(xgz, df_neg(x[2]));
+    const float distz = ddz.h + ddz.l;
+    for (int wy = 0; wy < win; ++wy) {
+      const int oy = wy / n1 - A.rho, iy = wy % n1;
+      const f2 xgy = df_mul(two_sum((float)(ea[1] + oy), A.s[iy]), A.h);
+      const float ly = xgy.h - xip[1];
+      const float lyz = ly * ly + lz * lz;
+      if (lyz > rcl2) continue;
+      float sny, csy;
+      sincospif(2.0f * xgy.h, &sny, &csy);
+      const f2 ddy = df_add(xgy, df_neg(x[1]));
+      const float disty = ddy.h + ddy.l;
+      const float wyz = A.wq[iy] * A.wq[iz];
+      const float dxp = A.amp * sny * snz;  // x-perturbation of the row
+      for (int wx = 0; wx < win; ++wx) {
+        const int ox = wx / n1 - A.rho, ix = wx % n1;
+        const f2 xgx = df_mul(two_sum((float)(ea[0] + ox), A.s[ix]), A.h);
+        const float lx = xgx.h - xip[0];
+        if (lx * lx + lyz > rcl2) continue;
+        float snx, csx;
+        sincospif(2.0f * xgx.h, &snx, &csx);
+        const f2 ddx = df_add(xgx, df_neg(x[0]));
+        const float dx = minimgf((ddx.h + ddx.l) + dxp);
+        const float dy = minimgf(disty + A.amp * snz * snx);
+        const float dz = minimgf(distz + A.amp * snx * sny);
         const float r2 = dx * dx + dy * dy + dz * dz;
-        if (!inside_cut(r2, A.rc2f, c3, o3, nc, xig, A.amp, A.rc)) continue;
-        const float a01 = g * cs[1] * sn[2], a02 = g * sn[1] * cs[2];
-        const float a10 = g * cs[0] * sn[2], a12 = g * sn[0] * cs[2];
-        const float a20 = g * cs[0] * sn[1], a21 = g * sn[0] * cs[1];
+        if (r2 > A.rc2f * 1.0002f) continue;
+        if (r2 >= A.rc2f * 0.9998f) {
+          const double xig[3] = {((double)wrapi(ea[0] + ox, ne) + 0.5 * (A.eta[ix] + 1.0)) * A.hd,
+                                 ((double)wrapi(ea[1] + oy, ne) + 0.5 * (A.eta[iy] + 1.0)) * A.hd,
+                                 ((double)wrapi(ea[2] + oz, ne) + 0.5 * (A.eta[iz] + 1.0)) * A.hd};
+          if (!inside_cut(r2, A.rc2f, c3, o3, nc, xig, A.amp, A.rc)) continue;
+        }
+        const float a01 = g * csy * snz, a02 = g * sny * csz;
+        const float a10 = g * csx * snz, a12 = g * snx * csz;
+        const float a20 = g * csx * sny, a21 = g * snx * csy;
         const float det = 1.0f * (1.0f - a12 * a21) - a01 * (a10 - a12 * a20) + a02 * (a10 * a21 - a20);
-        const float W = A.wq[w3[0] % n1] * A.wq[w3[1] % n1] * A.wq[w3[2] % n1] * det;
+        const float W = A.wq[ix] * wyz * det;
         Z += W * exp2f(-r2 * A.c2l);
       }
+    }
+  }
   const float hh = 0.5f * A.hf;
   Z *= hh * hh * hh;
   const float iz = Z > 0.0f ? 1.0f / Z : 0.0f;
@@ -230,9 +248,11 @@ __global__ void k_curved_deposit(CDepArgs A) {
   extern __shared__ float4 sm4[];
   const int nodes = blockDim.x;  // n1^3
   float4* st = sm4;                                      // [nodes][3]
-  int* keep = (int*)(sm4 + 3 * nodes);                   // [nodes]
+  int* keep = (int*)(sm4 + 3 * nodes);                   // [nodes]: staged particle index + 1, or 0
+  int* clist = keep + nodes;                             // [nodes]: compacted positions of the kept ones
   __shared__ float bbox[6];
   __shared__ int pre[126], rbeg[126];
+  __shared__ int wcnt[32];
   const int t = threadIdx.x;
   const int n1 = A.n1, ne = A.ne, rho = A.rho, span = 2 * rho + 1, nrange = span * span * span;
   const int e = blockIdx.x;
@@ -301,11 +321,24 @@ __global__ void k_curved_deposit(CDepArgs A) {
       kp = d2 <= cut * cut ? jj + 1 : 0;
     }
     keep[t] = kp;
+    // compact the staged particles that pass the box test (order kept); the mask holds
+    // the lanes this warp has (n1^3 need not be a multiple of 32)
+    const int lane = t & 31, wp = t >> 5;
+    const int wl = nodes - 32 * wp;
+    const unsigned wmask = wl >= 32 ? 0xffffffffu : ((1u << wl) - 1u);
+    const unsigned bal = __ballot_sync(wmask, kp != 0);
+    if (lane == 0) wcnt[wp] = __popc(bal);
     __syncthreads();
-    const int cntb = min(nodes, total - base);
-    for (int q = 0; q < cntb; ++q) {
+    int woff = 0, nkept = 0;
+    for (int w2 = 0; w2 < (nodes + 31) / 32; ++w2) {
+      if (w2 < wp) woff += wcnt[w2];
+      nkept += wcnt[w2];
+    }
+    if (kp) clist[woff + __popc(bal & ((1u << lane) - 1u))] = t;
+    __syncthreads();
+    for (int u = 0; u < nkept; ++u) {
+      const int q = clist[u];
       const int kk = keep[q];
-      if (!kk) continue;
       const float4 r0 = st[3 * q], r1 = st[3 * q + 1], r2 = st[3 * q + 2];
       const f2 xp[3] = {{r0.x, r0.y}, {r0.z, r0.w}, {r1.x, r1.y}};
       float d[3];
@@ -433,7 +466,7 @@ pc_status pc_project_curved_f32_impl(pc_ctx* ctx, const pc_particles_f32* p, flo
     D.rec = (const float4*)ctx->fac;
     D.field = field;
     const int nodes = ctx->n1 * ctx->n1 * ctx->n1;
-    const size_t smem = (size_t)nodes * (3 * sizeof(float4) + sizeof(int));
+    const size_t smem = (size_t)nodes * (3 * sizeof(float4) + 2 * sizeof(int));
     const int td = pc_phase_begin(ctx, PC_PH_DEPOSIT);
     k_curved_deposit<<<(unsigned)nel, nodes, smem, st>>>(D);
     ctx->launches += 1;
