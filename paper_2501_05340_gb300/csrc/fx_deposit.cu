@@ -30,8 +30,9 @@
 // two 256-column accumulators so that one element drains while the next
 // accumulates): 6 gather warps take the element's candidate particles in batches
 // of 32 in a fixed order, keep those whose support reaches the element (per-axis
-// reach bits) and stage their factors; 8 builder warps turn a staged batch into
-// the digit operands; one MMA warp issues the MMAs of each batch in batch order
+// reach bits) and stage their factors; 8 builder warps, in two teams that take
+// alternate batches, turn a staged batch into the digit operands; one MMA warp
+// issues the MMAs of each batch in batch order
 // (so the result does not depend on scheduling) and hands finished elements to 4
 // epilogue warps (one per tensor-memory lane quarter). An element with more kept
 // particles than one segment holds is deposited in segments added in FP64. Every wait
@@ -49,6 +50,8 @@ constexpr float kBase = 256.0f;                       // digit radix (8 bits)
 constexpr float kInvBase = 1.0f / 256.0f;
 constexpr int kGather = 6;                            // gather warps
 constexpr int kBuild = 8;                             // builder warps
+constexpr int kTeams = 2;                             // builder teams, each on every kTeams-th batch
+constexpr int kTeamWarps = kBuild / kTeams;
 constexpr int kEpi = 4;                               // epilogue warps
 constexpr int kWarps = 1 + kEpi + kGather + kBuild;   // + the MMA warp
 constexpr int kThreads = 32 * kWarps;
@@ -344,10 +347,13 @@ __device__ void fx_gather(const FxSmem<N1>& M, const FxArgs& A, int w, int lane)
     }
     q += nb;
   }
-  // end of the stream: the warp that owns batch q writes the end marker
-  if (ok && q % kGather == w) {
-    const int fs = (int)(q % B::NF);
-    const bool free_slot = q < B::NF || fx_wait(C, &C.f_empty[fs], (uint32_t)(((q / B::NF) - 1) & 1), true);
+  // end of the stream: one end marker per builder team (batches q .. q + kTeams - 1),
+  // each written by the warp that owns its batch
+  for (int x = 0; ok && x < kTeams; ++x) {
+    const int64_t qq = q + x;
+    if (qq % kGather != w) continue;
+    const int fs = (int)(qq % B::NF);
+    const bool free_slot = qq < B::NF || fx_wait(C, &C.f_empty[fs], (uint32_t)(((qq / B::NF) - 1) & 1), true);
     if (lane == 0) {
       if (!free_slot) fail_now(C, A.counters);
       C.fmeta[fs][0] = -1;
@@ -362,12 +368,14 @@ __device__ void fx_gather(const FxSmem<N1>& M, const FxArgs& A, int w, int lane)
 // joins the remainder, whose rounding there is below 2^-47 of v's scale. |s_3| <=
 // 512, the others <= 128; the remainder after six digits is below 2^-49.
 
-// Builder warp bi: digit operands of every batch, in batch order.
+// Builder warp bi: digit operands of the batches of its team (bi % kTeams), in batch
+// order; the teams build consecutive batches at the same time.
 template <int N1>
 __device__ void fx_build(const FxSmem<N1>& M, const FxArgs& A, int bi, int lane) {
   using B = FxShape<N1>;
   FxCtl& C = *M.ctl;
-  for (int64_t q = 0;; ++q) {
+  const int team = bi % kTeams, tw = bi / kTeams;
+  for (int64_t q = team;; q += kTeams) {
     const int fs = (int)(q % B::NF);
     const int os = (int)(q % B::NS);
     if (!fx_wait(C, &C.f_full[fs], (uint32_t)((q / B::NF) & 1))) {
@@ -383,7 +391,7 @@ __device__ void fx_build(const FxSmem<N1>& M, const FxArgs& A, int bi, int lane)
       const float2* fst = M.fslot + (size_t)fs * B::NFLD * kFRow;
       uint8_t* stg = M.stage + (size_t)os * B::STAGE;
       const int nok = nk > 16 ? 4 : 2;  // particle octets the MMAs read
-      for (int it = bi * 32 + lane; it < B::NA + B::NB; it += kBuild * 32) {
+      for (int it = tw * 32 + lane; it < B::NA + B::NB; it += kTeamWarps * 32) {
         const bool isA = it < B::NA;
         const int t = isA ? it : it - B::NA;
         const int row = 8 * (t >> 5) + (t & 7), o = (t >> 3) & 3;
@@ -444,7 +452,7 @@ __device__ void fx_build(const FxSmem<N1>& M, const FxArgs& A, int bi, int lane)
     }
     __syncwarp();
     if (lane == 0) {
-      if (bi == 0) {
+      if (tw == 0) {
 #pragma unroll
         for (int x = 0; x < 4; ++x) C.opmeta[os][x] = C.fmeta[fs][x];
       }
@@ -672,10 +680,10 @@ __global__ void __launch_bounds__(kThreads, 1) k_fx_deposit(FxArgs A) {
   if (tid == 0) {
     for (int s = 0; s < B::NF; ++s) {
       mbar_init(&C.f_full[s], 1);
-      mbar_init(&C.f_empty[s], kBuild);
+      mbar_init(&C.f_empty[s], kTeamWarps);
     }
     for (int s = 0; s < B::NS; ++s) {
-      mbar_init(&C.op_full[s], kBuild);
+      mbar_init(&C.op_full[s], kTeamWarps);
       mbar_init(&C.op_empty[s], 1);
     }
     for (int s = 0; s < 2; ++s) {
