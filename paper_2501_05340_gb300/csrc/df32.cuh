@@ -121,7 +121,10 @@ struct DfExpTable {
 // P. T. P. Tang (ACM TOMS 15, 1989): u = (64 m + j) ln2/64 + r with |r| <= ln2/128,
 // exp(u) = 2^m 2^(j/64) exp(r), exp(r) = 1 + r + r^2/2 + r^3 (1/6 + r/24 + r^2/120 + r^3/720),
 // the cubic tail (below 3e-8) in plain float, the rest in df32.
-__device__ __forceinline__ f2 df_exp_neg(f2 u, const DfExpTable& T) {
+// The table entries th[j], tl[j] are read from th / tl: pass a copy of T.th / T.tl in
+// shared memory, since lanes index them with different j (from the constant bank the
+// reads would be serialised).
+__device__ __forceinline__ f2 df_exp_neg(f2 u, const DfExpTable& T, const float* th, const float* tl) {
   const float kf = rintf(u.h * T.inv);
   const int k = (int)kf;
   // r = u - k (L1 + L2 + L3); k L1 is exact and u.h - k L1 cancels exactly (Sterbenz)
@@ -139,7 +142,7 @@ __device__ __forceinline__ f2 df_exp_neg(f2 u, const DfExpTable& T) {
   const f2 e = df_add({1.0f, 0.0f}, s);
   const int m = (k >= 0) ? (k >> 6) : -((-k + 63) >> 6);
   const int j = k - 64 * m;
-  f2 res = df_mul({T.th[j], T.tl[j]}, e);
+  f2 res = df_mul({th[j], tl[j]}, e);
   const float sc = ldexpf(1.0f, m);
   return {res.h * sc, res.l * sc};
 }

@@ -98,7 +98,8 @@ struct FactorArgs {
 // Unnormalised factor k_a of window node w for a particle at element-relative
 // position t (df32) in element ea of its axis, coordinate xa (for the FP64
 // re-decision near the cutoff).
-__device__ __forceinline__ f2 window_factor(const FactorArgs& F, f2 t, int ea, double xa, int w) {
+__device__ __forceinline__ f2 window_factor(const FactorArgs& F, f2 t, int ea, double xa, int w, const float* th,
+                                            const float* tl) {
   const int i = w % F.n1;
   const f2 dl = df_add(F.sw[w], df_neg(t));
   const float ad = fabsf(dl.h);
@@ -116,7 +117,7 @@ __device__ __forceinline__ f2 window_factor(const FactorArgs& F, f2 t, int ea, d
     f2 d2 = two_prod(dl.h, dl.h);
     d2.l = fmaf(2.0f * dl.h, dl.l, d2.l);
     d2 = fast_two_sum(d2.h, d2.l);
-    f = df_exp_neg(df_neg(df_mul(d2, F.c2)), F.tab);
+    f = df_exp_neg(df_neg(df_mul(d2, F.c2)), F.tab, th, tl);
   }
   return f;
 }
@@ -126,6 +127,12 @@ __device__ __forceinline__ f2 window_factor(const FactorArgs& F, f2 t, int ea, d
 // and written once in 16-byte pairs; reach bits and the maxima of the digit scales.
 template <int WIN>
 __global__ void __launch_bounds__(128) k_proj_records(FactorArgs F) {
+  __shared__ float th[64], tl[64];
+  if (threadIdx.x < 64) {
+    th[threadIdx.x] = F.tab.th[threadIdx.x];
+    tl[threadIdx.x] = F.tab.tl[threadIdx.x];
+  }
+  __syncthreads();
   const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   const int64_t n = F.n;
   float fmax = 0.0f, qmax[4] = {0.0f, 0.0f, 0.0f, 0.0f};
@@ -142,7 +149,7 @@ __global__ void __launch_bounds__(128) k_proj_records(FactorArgs F) {
       f2 Z = {0.0f, 0.0f};
 #pragma unroll
       for (int w = 0; w < WIN; ++w) {
-        f[w] = window_factor(F, t, ea, xa, w);
+        f[w] = window_factor(F, t, ea, xa, w, th, tl);
         if (f[w].h != 0.0f) Z = df_add(Z, df_mul(f[w], F.wq[w % F.n1]));
       }
       const f2 rz = df_recip(Z);
@@ -206,6 +213,12 @@ cudaError_t launch_records(int win, const FactorArgs& F, cudaStream_t st) {
 }
 
 __global__ void __launch_bounds__(128) k_proj_factors(FactorArgs F) {
+  __shared__ float th[64], tl[64];
+  if (threadIdx.x < 64) {
+    th[threadIdx.x] = F.tab.th[threadIdx.x];
+    tl[threadIdx.x] = F.tab.tl[threadIdx.x];
+  }
+  __syncthreads();
   const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   const int64_t n = F.n;
   if (k >= n) return;
@@ -216,7 +229,7 @@ __global__ void __launch_bounds__(128) k_proj_factors(FactorArgs F) {
     const f2 t = df_from_double(xa * (double)F.ne - (double)ea);
     f2 Z = {0.0f, 0.0f};
     for (int w = 0; w < F.win; ++w) {
-      const f2 f = window_factor(F, t, ea, xa, w);
+      const f2 f = window_factor(F, t, ea, xa, w, th, tl);
       if (f.h != 0.0f) Z = df_add(Z, df_mul(f, F.wq[w % F.n1]));
       F.fac[((int64_t)a * F.win + w) * n + k] = make_float2(f.h, f.l);
     }
