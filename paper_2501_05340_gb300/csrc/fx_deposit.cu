@@ -20,7 +20,7 @@
 //
 // Tensor layout: the A operand (M = 128 rows) of MMA group g holds the YZ digits
 // a = R g .. R g + R - 1 (R = floor(128 / n1^2) digit blocks of n1^2 rows); the B
-// operand holds the A digits b = 0..7 (blocks of CP >= 4 n1 rows) and MMA group g
+// operand holds the A digits b = 0..5 (blocks of CP >= 4 n1 rows) and MMA group g
 // writes the accumulator columns from R g CP on. Accumulator cell (r, b) (row block
 // r, column block b) then sums Y_(Rg+r) A_(b-Rg) over all groups g: every product
 // in a cell has the weight 2^(-8 (r + b + 2)). The epilogue adds the cells with
@@ -28,10 +28,10 @@
 //
 // Warp roles of the persistent CTA (one per SM, all 512 tensor-memory columns as
 // two 256-column accumulators so that one element drains while the next
-// accumulates): 6 gather warps take the element's candidate particles in batches
+// accumulates): 8 gather warps take the element's candidate particles in batches
 // of 32 in a fixed order, keep those whose support reaches the element (per-axis
-// reach bits) and stage their factors; 8 builder warps, in two teams that take
-// alternate batches, turn a staged batch into the digit operands; one MMA warp
+// reach bits) and stage their factors; 9 builder warps, in three teams of three
+// that take every third batch, turn a staged batch into the digit operands; one MMA warp
 // issues the MMAs of each batch in batch order
 // (so the result does not depend on scheduling) and hands finished elements to 4
 // epilogue warps (one per tensor-memory lane quarter). An element with more kept
@@ -48,9 +48,9 @@ namespace {
 constexpr int kS = 6;                                 // digits per value
 constexpr float kBase = 256.0f;                       // digit radix (8 bits)
 constexpr float kInvBase = 1.0f / 256.0f;
-constexpr int kGather = 6;                            // gather warps
-constexpr int kBuild = 8;                             // builder warps
-constexpr int kTeams = 2;                             // builder teams, each on every kTeams-th batch
+constexpr int kGather = 8;                            // gather warps
+constexpr int kBuild = 9;                             // builder warps
+constexpr int kTeams = 3;                             // builder teams, each on every kTeams-th batch
 constexpr int kTeamWarps = kBuild / kTeams;
 constexpr int kEpi = 4;                               // epilogue warps
 constexpr int kWarps = 1 + kEpi + kGather + kBuild;   // + the MMA warp
@@ -79,7 +79,7 @@ struct FxShape {
   static constexpr int NA = 4 * rup(JK, 8);                // YZ build items: (jk, particle octet)
   static constexpr int NB = 4 * rup(CI, 8);                // A build items: (ci, particle octet)
   static constexpr int FIXED = COMB + kGather * (3 * kMaxRanges + 1) * 4 + 4096;
-  static constexpr int NF = 6;                             // staged-factor slots
+  static constexpr int NF = 8;                             // staged-factor slots
   static constexpr int NS0 = (int)((kSmemMax - 1024 - FIXED - NF * FSLOT) / STAGE);
   static constexpr int NS = NS0 > 4 ? 4 : NS0;             // operand stages
   // kept particles per accumulation segment: the exact cells hold one digit product
@@ -660,6 +660,8 @@ template <int N1>
 __global__ void __launch_bounds__(kThreads, 1) k_fx_deposit(FxArgs A) {
   using B = FxShape<N1>;
   static_assert(B::NS >= 2, "operand stages do not fit in shared memory");
+  static_assert(B::NF <= 8 && B::NS <= 4, "more slots than the control block's barriers");
+  static_assert(kBuild % kTeams == 0, "builder teams of unequal size");
   static_assert(B::R * B::JK <= 128, "YZ digit rows exceed the MMA's M");
   static_assert(B::col0(B::G - 1) + B::ncol(B::G - 1) <= 256 && B::ncol(0) <= 256, "accumulator wider than 256");
   extern __shared__ uint8_t smraw[];
