@@ -189,8 +189,9 @@ __device__ __forceinline__ int stencil_radius(const unsigned long long* counters
   return (int)s;
 }
 
-constexpr int kQCap = 1024;  // filter survivors queued per block
-constexpr int kMine = 8;     // survivors queued per particle (further ones are solved in place)
+constexpr int kPassCap = 64;  // distance-test passes queued per warp
+constexpr int kSurvCap = 64;  // filter survivors queued per warp
+constexpr unsigned kFull = 0xffffffffu;
 
 // Exact FP64 contact time of the pair (k, j) of the sorted arrays.
 __device__ __forceinline__ double solve_pair(const SearchArgs& A, int64_t k, int64_t j) {
@@ -257,31 +258,44 @@ __device__ __forceinline__ void insert_by_key(double* lt, int* lj, unsigned long
   if (cnt < cap) ++cnt;
 }
 
-// Thread per particle (sorted by cell). The certified FP32 filter runs over the
-// stencil (each row of cells along x as one range when it does not wrap); its
-// survivors are queued per block and solved in FP64 by all of the block's threads
-// together, then each particle inserts its own roots into its list sorted by
-// (t, id). On this GPU an FP64 instruction takes a warp 64 pipe cycles whatever
-// the number of active lanes, so solving a block's survivors densely instead of in
-// each diverged warp removes most of the FP64 time. The insertion does not depend
-// on the order of the roots. kSfc: the lists are sorted by the partner's rank key
-// instead (the paper's first-found selection; the matching then takes, for every
-// particle, its first free candidate in that order).
+// Per-warp queues of the contact search in shared memory.
+struct SearchQueue {
+  float dx[kPassCap], dy[kPassCap], dz[kPassCap];  // offsets of the queued distance-test passes
+  int j[kPassCap], own[kPassCap];                  // candidate and owning lane
+  int sown[kSurvCap], sj[kSurvCap];                // filter survivors
+  double st[kSurvCap];                             // their FP64 roots
+};
+
+// Thread per particle (sorted by cell), the warp's lanes in lockstep. The stencil is
+// taken row by row; a row's 2 s + 1 cells along x are one contiguous range of the
+// sorted arrays, or two where the row wraps. Each candidate first takes a distance
+// test against a reach that no pair of this particle exceeds in filter_keep (the
+// particle's radius plus the largest one, its speed plus the largest one, with
+// margins above the FP32 rounding); the passes are queued per warp and, 32 at a
+// time, go through the certified filter with one pass per lane. Its survivors are
+// queued again and solved exactly in FP64 by the warp's lanes together (on this GPU
+// an FP64 instruction takes a warp 64 pipe cycles whatever the number of active
+// lanes); every lane then inserts its own roots into its list sorted by (t, id),
+// which does not depend on the order in which they were found. kSfc: the lists are
+// sorted by the partner's rank key instead (the paper's first-found selection; the
+// matching then takes, for every particle, its first free candidate in that order).
 template <bool kSfc>
 __global__ void __launch_bounds__(256, 3) k_search(SearchArgs A) {
   const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   const int64_t n = A.n;
-  // stencil radius and speed bound from the step's maxima, once per block
+  const int nc = A.nc;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const unsigned below = (1u << lane) - 1u;
+  // stencil radius and speed and radius bounds from the step's maxima, once per block
   __shared__ int s_sh;
-  __shared__ float vmaxf_sh;
-  __shared__ int q_cnt;
-  __shared__ int q_own[kQCap], q_j[kQCap];
-  __shared__ double q_t[kQCap];
+  __shared__ float vmaxf_sh, rmaxf_sh;
+  __shared__ SearchQueue queues[8];
+  SearchQueue& Q = queues[warp];
   if (threadIdx.x == 0) {
     double reach;
     s_sh = stencil_radius(A.counters, A.nc, A.dt, &reach);
     vmaxf_sh = (float)sqrt(__longlong_as_double((long long)A.counters[CNT_VMAX2])) * 1.000001f;
-    q_cnt = 0;
+    rmaxf_sh = (float)__longlong_as_double((long long)A.counters[CNT_RMAX]) * 1.000001f;
     if (blockIdx.x == 0) {
       atomicMax(&A.counters[CNT_STENCIL], (unsigned long long)s_sh);
       if (!(reach < 0.5)) raise_status(A.counters, PC_EINVAL);
@@ -289,90 +303,160 @@ __global__ void __launch_bounds__(256, 3) k_search(SearchArgs A) {
   }
   __syncthreads();
   const int s = s_sh;
+  const float dtf = (float)A.dt * 1.000001f;
+  const float vmaxf = vmaxf_sh;
+  const bool live = k < n;
+  const int64_t kw = (int64_t)blockIdx.x * blockDim.x + 32 * warp;  // the warp's first particle
   int found = 0, solves = 0, cnt = 0;
   double lt[kMaxCap];
   int lj[kMaxCap];
   unsigned long long lk[kSfc ? kMaxCap : 1];
-  int mine[kMine];
-  int nmine = 0;
-  if (k < n) {
-    const float xf[3] = {A.sxf[k], A.sxf[n + k], A.sxf[2 * n + k]};
-    const float vf[3] = {A.svf[k], A.svf[n + k], A.svf[2 * n + k]};
-    const float rf = A.srf[k];
-    const float dtf = (float)A.dt * 1.000001f;
-    const float vmaxf = vmaxf_sh;
-    const int nc = A.nc;
-    const int cx = cell_of(A.sx[k], nc), cy = cell_of(A.sx[n + k], nc), cz = cell_of(A.sx[2 * n + k], nc);
-    auto visit = [&](int64_t j) {
-      float dxf[3], dvf[3];
+  float xf[3] = {0.0f, 0.0f, 0.0f}, vf[3] = {0.0f, 0.0f, 0.0f}, rf = 0.0f, rl2 = -1.0f;
+  int cx = 0, cy = 0, cz = 0;
+  if (live) {
 #pragma unroll
-      for (int a = 0; a < 3; ++a) {
-        dxf[a] = minimgf(xf[a] - A.sxf[a * n + j]);
-        dvf[a] = vf[a] - A.svf[a * n + j];
-      }
-      if (!filter_keep(dxf, dvf, rf + A.srf[j], dtf, vmaxf)) return;
-      const int slot = nmine < kMine ? atomicAdd(&q_cnt, 1) : kQCap;
-      if (slot < kQCap) {
-        q_own[slot] = threadIdx.x;
-        q_j[slot] = (int)j;
-        mine[nmine++] = slot;
-      }
-      // an overflowing survivor is solved on the spot; the warp-uniform test keeps the
-      // FP64 solve from being issued predicated off on every candidate
-      if (__any_sync(__activemask(), slot >= kQCap) && slot >= kQCap) {
-        ++solves;
-        const double t = solve_pair(A, k, j);
-        if (t <= A.dt) {
-          ++found;
-          if constexpr (kSfc)
-            insert_by_key(lt, lj, lk, cnt, A.cap, t, (int)j, sfc_key(A.sx, A.sid, n, nc, j));
-          else
-            insert_sorted(lt, lj, cnt, A.cap, t, (int)j, A.sid);
-        }
-      }
-    };
-    const int span = 2 * s + 1;
-    const bool full = span >= nc;  // the stencil covers the whole axis: visit every cell once
-    const int cnt_ax = full ? nc : span;
-    for (int oz = 0; oz < cnt_ax; ++oz) {
-      const int zc = full ? oz : wrapi(cz - s + oz, nc);
-      for (int oy = 0; oy < cnt_ax; ++oy) {
-        const int yc = full ? oy : wrapi(cy - s + oy, nc);
-        const int64_t row = ((int64_t)zc * nc + yc) * nc;
-        if (!full && cx - s >= 0 && cx + s < nc) {
-          const int beg = A.start[row + cx - s], end = A.start[row + cx + s + 1];
-          for (int j = beg; j < end; ++j)
-            if (j != k) visit(j);
-        } else {
-          for (int ox = 0; ox < cnt_ax; ++ox) {
-            const int xc = full ? ox : wrapi(cx - s + ox, nc);
-            const int beg = A.start[row + xc], end = A.start[row + xc + 1];
-            for (int j = beg; j < end; ++j)
-              if (j != k) visit(j);
-          }
-        }
-      }
+    for (int a = 0; a < 3; ++a) {
+      xf[a] = A.sxf[a * n + k];
+      vf[a] = A.svf[a * n + k];
     }
+    rf = A.srf[k];
+    cx = cell_of(A.sx[k], nc);
+    cy = cell_of(A.sx[n + k], nc);
+    cz = cell_of(A.sx[2 * n + k], nc);
+    const float vkf = sqrtf(vf[0] * vf[0] + vf[1] * vf[1] + vf[2] * vf[2]) * 1.000001f;
+    const float rhi = ((rf + rmaxf_sh) + (vkf + vmaxf) * dtf) * 1.00002f + 4.0e-7f + 2.5e-7f * vmaxf * dtf;
+    rl2 = rhi * rhi * 1.0001f;
   }
-  __syncthreads();
-  const int total = q_cnt < kQCap ? q_cnt : kQCap;
-  const int64_t kb = (int64_t)blockIdx.x * blockDim.x;
-  for (int e = threadIdx.x; e < total; e += blockDim.x) {
-    q_t[e] = solve_pair(A, kb + q_own[e], q_j[e]);
-    ++solves;
-  }
-  __syncthreads();
-  if (k < n) {
-    for (int i = 0; i < nmine; ++i) {
-      const double t = q_t[mine[i]];
+  int np = 0, ns = 0;  // queued passes and survivors (the same in every lane)
+
+  // the queued survivors' FP64 roots, by the lanes together; each lane then inserts its own
+  auto flush_survivors = [&]() {
+    for (int e = lane; e < ns; e += 32) {
+      Q.st[e] = solve_pair(A, kw + Q.sown[e], Q.sj[e]);
+      ++solves;
+    }
+    __syncwarp();
+    for (int e = 0; e < ns; ++e) {
+      if (Q.sown[e] != lane) continue;
+      const double t = Q.st[e];
       if (t <= A.dt) {
         ++found;
         if constexpr (kSfc)
-          insert_by_key(lt, lj, lk, cnt, A.cap, t, q_j[mine[i]], sfc_key(A.sx, A.sid, n, A.nc, q_j[mine[i]]));
+          insert_by_key(lt, lj, lk, cnt, A.cap, t, Q.sj[e], sfc_key(A.sx, A.sid, n, nc, Q.sj[e]));
         else
-          insert_sorted(lt, lj, cnt, A.cap, t, q_j[mine[i]], A.sid);
+          insert_sorted(lt, lj, cnt, A.cap, t, Q.sj[e], A.sid);
       }
     }
+    __syncwarp();
+    ns = 0;
+  };
+  // the certified filter on the first m <= 32 queued passes, one per lane
+  auto filter_passes = [&](int m) {
+    const int own = lane < m ? Q.own[lane] : lane;
+    const float vo0 = __shfl_sync(kFull, vf[0], own), vo1 = __shfl_sync(kFull, vf[1], own),
+                vo2 = __shfl_sync(kFull, vf[2], own), ro = __shfl_sync(kFull, rf, own);
+    bool keep = false;
+    int j = 0;
+    if (lane < m) {
+      j = Q.j[lane];
+      const float dxf[3] = {Q.dx[lane], Q.dy[lane], Q.dz[lane]};
+      const float dvf[3] = {vo0 - A.svf[j], vo1 - A.svf[n + j], vo2 - A.svf[2 * n + j]};
+      keep = filter_keep(dxf, dvf, ro + A.srf[j], dtf, vmaxf);
+    }
+    const unsigned bal = __ballot_sync(kFull, keep);
+    if (keep) {
+      const int p = ns + __popc(bal & below);
+      Q.sown[p] = own;
+      Q.sj[p] = j;
+    }
+    ns += __popc(bal);
+    __syncwarp();
+    if (ns > kSurvCap - 32) flush_survivors();
+  };
+
+  const int span = 2 * s + 1;
+  const bool full = span >= nc;  // the stencil covers the whole axis: visit every cell once
+  const int cnt_ax = full ? nc : span;
+  for (int oz = 0; oz < cnt_ax; ++oz) {
+    for (int oy = 0; oy < cnt_ax; ++oy) {
+      int b1 = 0, e1 = 0, b2 = 0, e2 = 0;
+      if (live) {
+        const int zc = full ? oz : wrapi(cz - s + oz, nc);
+        const int yc = full ? oy : wrapi(cy - s + oy, nc);
+        const int64_t row = ((int64_t)zc * nc + yc) * nc;
+        const int xl = cx - s, xh = cx + s;
+        if (full) {
+          b1 = A.start[row];
+          e1 = A.start[row + nc];
+        } else if (xl >= 0 && xh < nc) {
+          b1 = A.start[row + xl];
+          e1 = A.start[row + xh + 1];
+        } else if (xl < 0) {
+          b1 = A.start[row + xl + nc];
+          e1 = A.start[row + nc];
+          b2 = A.start[row];
+          e2 = A.start[row + xh + 1];
+        } else {
+          b1 = A.start[row + xl];
+          e1 = A.start[row + nc];
+          b2 = A.start[row];
+          e2 = A.start[row + xh - nc + 1];
+        }
+      }
+      const int l1 = e1 - b1, len = l1 + (e2 - b2);
+      const int m = __reduce_max_sync(kFull, len);
+      for (int t = 0; t < m; ++t) {
+        const int j = t < l1 ? b1 + t : b2 + (t - l1);
+        bool pass = false;
+        float dx = 0.0f, dy = 0.0f, dz = 0.0f;
+        if (t < len && j != k) {
+          dx = minimgf(xf[0] - A.sxf[j]);
+          dy = minimgf(xf[1] - A.sxf[n + j]);
+          dz = minimgf(xf[2] - A.sxf[2 * n + j]);
+          pass = !(dx * dx + dy * dy + dz * dz > rl2);
+        }
+        const unsigned bal = __ballot_sync(kFull, pass);
+        if (pass) {
+          const int p = np + __popc(bal & below);
+          Q.dx[p] = dx;
+          Q.dy[p] = dy;
+          Q.dz[p] = dz;
+          Q.j[p] = j;
+          Q.own[p] = lane;
+        }
+        np += __popc(bal);
+        if (np >= 32) {
+          __syncwarp();
+          filter_passes(32);
+          // move the passes beyond the first 32 to the front
+          const bool mv = lane < np - 32;
+          float mx = 0.0f, my = 0.0f, mz = 0.0f;
+          int mj = 0, mo = 0;
+          if (mv) {
+            mx = Q.dx[32 + lane];
+            my = Q.dy[32 + lane];
+            mz = Q.dz[32 + lane];
+            mj = Q.j[32 + lane];
+            mo = Q.own[32 + lane];
+          }
+          __syncwarp();
+          if (mv) {
+            Q.dx[lane] = mx;
+            Q.dy[lane] = my;
+            Q.dz[lane] = mz;
+            Q.j[lane] = mj;
+            Q.own[lane] = mo;
+          }
+          __syncwarp();
+          np -= 32;
+        }
+      }
+    }
+  }
+  __syncwarp();
+  if (np > 0) filter_passes(np);
+  if (ns > 0) flush_survivors();
+  if (live) {
     for (int q = 0; q < cnt; ++q) {
       A.cand_j[(int64_t)q * n + k] = lj[q];
       A.cand_t[(int64_t)q * n + k] = lt[q];

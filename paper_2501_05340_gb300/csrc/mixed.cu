@@ -193,7 +193,9 @@ __device__ __forceinline__ bool filter_cells(const float dxf[3], const float dvc
   return !(bf > bslack);
 }
 
-constexpr int kPend = 8;  // filter survivors deferred per particle (further ones are solved in place)
+constexpr int kPassCap = 64;  // distance-test passes queued per warp
+constexpr int kSurvCap = 64;  // filter survivors queued per warp
+constexpr unsigned kFull = 0xffffffffu;
 
 // FP64 root of the pair (k, j) in cell units, with the arguments the step defines.
 __device__ __forceinline__ double solve_cells(const SearchF32& A, int64_t k, int64_t j) {
@@ -231,26 +233,38 @@ __device__ __forceinline__ void insert_sorted(double* lt, int* lj, int& cnt, int
   if (cnt < cap) ++cnt;
 }
 
-// Thread per particle (sorted by cell). The stencil is taken row by row; a row of
-// 2 s + 1 cells along x that does not wrap is one contiguous range of the sorted
-// arrays, walked with the x cell advanced at the cell starts. Each candidate goes
-// through the certified FP32 filter. The survivors are solved exactly in FP64
-// after the warp's filter loops, by the warp's lanes together: on this GPU an FP64
-// instruction takes a warp 64 pipe cycles whatever the number of active lanes, so
-// a warp's few survivors cost one pass instead of one per survivor. Roots in
-// [0, dt] go into the particle's list sorted by (t, id), independent of order.
+// Per-warp queues of the contact search in shared memory.
+struct SearchQueueF32 {
+  float dx[kPassCap], dy[kPassCap], dz[kPassCap];  // offsets of the queued distance-test passes
+  int j[kPassCap], own[kPassCap];                  // candidate and owning lane
+  int sown[kSurvCap], sj[kSurvCap];                // filter survivors
+  double st[kSurvCap];                             // their FP64 roots
+};
+
+// Thread per particle (sorted by cell), the warp's lanes in lockstep. The stencil is
+// taken row by row; a row's 2 s + 1 cells along x are one contiguous range of the
+// sorted arrays, or two where the row wraps. Each candidate first takes a distance
+// test against a reach that no pair of this particle exceeds in the filter; the
+// passes are queued per warp and, 32 at a time, go through the certified FP32
+// filter with one pass per lane. Its survivors are queued again and solved exactly
+// in FP64 by the warp's lanes together (on this GPU an FP64 instruction takes a
+// warp 64 pipe cycles whatever the number of active lanes); every lane then inserts
+// its own roots in [0, dt] into its list sorted by (t, id), which does not depend on
+// the order in which they were found. The offsets and tests are the same
+// expressions for every pair, so the candidate lists do not depend on the queueing.
 __global__ void __launch_bounds__(256, 3) k_search_f32(SearchF32 A) {
   const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   const int64_t n = A.n;
   const int nc = A.nc;
   const float Lf = (float)nc;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const unsigned below = (1u << lane) - 1u;
   // stencil radius and speed bound from the step's maxima, once per block (FP64 is
   // 1/64 of the FP32 rate on this GPU)
   __shared__ int s_sh;
   __shared__ float vmaxc_sh, rmaxc_sh;
-  __shared__ int q_own[8][32 * kPend], q_j[8][32 * kPend];
-  __shared__ double q_t[8][32 * kPend];
+  __shared__ SearchQueueF32 queues[8];
+  SearchQueueF32& Q = queues[warp];
   if (threadIdx.x == 0) {
     const double L = (double)nc;
     const double v2max = __longlong_as_double((long long)A.counters[CNT_VMAX2]);
@@ -268,110 +282,175 @@ __global__ void __launch_bounds__(256, 3) k_search_f32(SearchF32 A) {
   }
   __syncthreads();
   const int s = s_sh;
+  const float dtf = (float)A.dt * 1.000001f;
+  const float vmaxc = vmaxc_sh;
+  const bool live = k < n;
+  const int64_t kw = (int64_t)blockIdx.x * blockDim.x + 32 * warp;  // the warp's first particle
   int found = 0, solves = 0, cnt = 0;
   double lt[kMaxCap];
   int lj[kMaxCap];
-  int pend[kPend];
-  int npend = 0;
-  if (k < n) {
-    int ck[3];
+  int ck[3] = {0, 0, 0};
+  float ok3[3] = {0.0f, 0.0f, 0.0f}, vk3[3] = {0.0f, 0.0f, 0.0f}, rk = 0.0f, rl2 = -1.0f;
+  if (live) {
     cell_coords(A.scell[k], nc, ck);
-    const float ok3[3] = {A.so[k], A.so[n + k], A.so[2 * n + k]};
-    const float vk3[3] = {A.sv[k], A.sv[n + k], A.sv[2 * n + k]};
-    const float rk = A.sr[k];
-    const float dtf = (float)A.dt * 1.000001f;
-    const float vmaxc = vmaxc_sh;
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+      ok3[a] = A.so[a * n + k];
+      vk3[a] = A.sv[a * n + k];
+    }
+    rk = A.sr[k];
     // A reach no pair of this particle exceeds in filter_cells: (r_k + r_max) nc and
-    // (|v_k| nc + vmaxc) for the radius sum and the speed, with margins. Beyond it
-    // filter_cells rejects, so those candidates skip their velocity and radius loads.
+    // (|v_k| nc + vmaxc) for the radius sum and the speed, with margins.
     const float vkc = sqrtf(vk3[0] * vk3[0] + vk3[1] * vk3[1] + vk3[2] * vk3[2]) * Lf * 1.000001f;
     const float rhi = ((rk * Lf + rmaxc_sh) + (vkc + vmaxc) * dtf) * 1.00002f + 8.0e-7f + 2.5e-7f * vmaxc * dtf;
-    const float rl2 = rhi * rhi * 1.0001f;
-    // candidate j in cell (xc, yc, zc)
-    auto visit = [&](int j, int xc, int yc, int zc) {
-      const int cj[3] = {xc, yc, zc};
-      float dxf[3], dvc[3];
-#pragma unroll
-      for (int a = 0; a < 3; ++a) {
-        int di = ck[a] - cj[a];
-        if (2 * di > nc) di -= nc;
-        else if (2 * di < -nc) di += nc;
-        dxf[a] = minimgf_box((float)di + (ok3[a] - A.so[a * n + j]), Lf);
-      }
-      if (dxf[0] * dxf[0] + dxf[1] * dxf[1] + dxf[2] * dxf[2] > rl2) return;
-#pragma unroll
-      for (int a = 0; a < 3; ++a) dvc[a] = (vk3[a] - A.sv[a * n + j]) * Lf;
-      if (!filter_cells(dxf, dvc, (rk + A.sr[j]) * Lf, dtf, vmaxc)) return;
-      const bool over = npend >= kPend;
-      if (!over) pend[npend++] = j;
-      // an overflowing survivor is solved on the spot; the warp-uniform test keeps the
-      // FP64 solve from being issued predicated off on every candidate
-      if (__any_sync(__activemask(), over) && over) {
-        ++solves;
-        const double t = solve_cells(A, k, j);
-        if (t <= A.dt) {
-          ++found;
-          insert_sorted(lt, lj, cnt, A.cap, t, j, A.sid);
-        }
-      }
-    };
-    const int span = 2 * s + 1;
-    const bool full = span >= nc;
-    const int cnt_ax = full ? nc : span;
-    const bool row_range = !full && ck[0] - s >= 0 && ck[0] + s < nc;
-    for (int oz = 0; oz < cnt_ax; ++oz) {
-      const int zc = full ? oz : wrapi(ck[2] - s + oz, nc);
-      for (int oy = 0; oy < cnt_ax; ++oy) {
-        const int yc = full ? oy : wrapi(ck[1] - s + oy, nc);
-        const int64_t row = ((int64_t)zc * nc + yc) * nc;
-        if (row_range) {
-          int xc = ck[0] - s;
-          int next = A.start[row + xc + 1];
-          const int end = A.start[row + ck[0] + s + 1];
-          for (int j = A.start[row + xc]; j < end; ++j) {
-            while (j >= next) next = A.start[row + (++xc) + 1];
-            if (j != k) visit(j, xc, yc, zc);
-          }
-        } else {
-          for (int ox = 0; ox < cnt_ax; ++ox) {
-            const int xc = full ? ox : wrapi(ck[0] - s + ox, nc);
-            const int64_t cl = row + xc;
-            const int beg = A.start[cl], end = A.start[cl + 1];
-            for (int j = beg; j < end; ++j)
-              if (j != k) visit(j, xc, yc, zc);
-          }
-        }
-      }
+    rl2 = rhi * rhi * 1.0001f;
+  }
+  int np = 0, ns = 0;  // queued passes and survivors (the same in every lane)
+
+  // the queued survivors' FP64 roots, by the lanes together; each lane then inserts its own
+  auto flush_survivors = [&]() {
+    for (int e = lane; e < ns; e += 32) {
+      Q.st[e] = solve_cells(A, kw + Q.sown[e], Q.sj[e]);
+      ++solves;
     }
-  }
-  // the warp's deferred survivors, solved by its lanes together
-  int off = npend;
-#pragma unroll
-  for (int o = 1; o < 32; o <<= 1) {
-    const int y = __shfl_up_sync(0xffffffffu, off, o);
-    if (lane >= o) off += y;
-  }
-  const int wtotal = __shfl_sync(0xffffffffu, off, 31);
-  off -= npend;
-  for (int i = 0; i < npend; ++i) {
-    q_own[warp][off + i] = lane;
-    q_j[warp][off + i] = pend[i];
-  }
-  __syncwarp();
-  const int64_t kw = (int64_t)blockIdx.x * blockDim.x + 32 * warp;
-  for (int e = lane; e < wtotal; e += 32) {
-    q_t[warp][e] = solve_cells(A, kw + q_own[warp][e], q_j[warp][e]);
-    ++solves;
-  }
-  __syncwarp();
-  if (k < n) {
-    for (int i = 0; i < npend; ++i) {
-      const double t = q_t[warp][off + i];
+    __syncwarp();
+    for (int e = 0; e < ns; ++e) {
+      if (Q.sown[e] != lane) continue;
+      const double t = Q.st[e];
       if (t <= A.dt) {
         ++found;
-        insert_sorted(lt, lj, cnt, A.cap, t, pend[i], A.sid);
+        insert_sorted(lt, lj, cnt, A.cap, t, Q.sj[e], A.sid);
       }
     }
+    __syncwarp();
+    ns = 0;
+  };
+  // the certified filter on the first m <= 32 queued passes, one per lane
+  auto filter_passes = [&](int m) {
+    const int own = lane < m ? Q.own[lane] : lane;
+    const float vo0 = __shfl_sync(kFull, vk3[0], own), vo1 = __shfl_sync(kFull, vk3[1], own),
+                vo2 = __shfl_sync(kFull, vk3[2], own), ro = __shfl_sync(kFull, rk, own);
+    bool keep = false;
+    int j = 0;
+    if (lane < m) {
+      j = Q.j[lane];
+      const float dxf[3] = {Q.dx[lane], Q.dy[lane], Q.dz[lane]};
+      const float dvc[3] = {(vo0 - A.sv[j]) * Lf, (vo1 - A.sv[n + j]) * Lf, (vo2 - A.sv[2 * n + j]) * Lf};
+      keep = filter_cells(dxf, dvc, (ro + A.sr[j]) * Lf, dtf, vmaxc);
+    }
+    const unsigned bal = __ballot_sync(kFull, keep);
+    if (keep) {
+      const int p = ns + __popc(bal & below);
+      Q.sown[p] = own;
+      Q.sj[p] = j;
+    }
+    ns += __popc(bal);
+    __syncwarp();
+    if (ns > kSurvCap - 32) flush_survivors();
+  };
+
+  const int span = 2 * s + 1;
+  const bool full = span >= nc;  // the stencil covers the whole axis: visit every cell once
+  const int cnt_ax = full ? nc : span;
+  // offsets below s + 1 <= nc / 2 are their own minimum image
+  const bool need_box = 2 * (s + 1) > nc;
+  for (int oz = 0; oz < cnt_ax; ++oz) {
+    for (int oy = 0; oy < cnt_ax; ++oy) {
+      int b1 = 0, e1 = 0, b2 = 0, e2 = 0, rowck = 0;
+      float dyf = 0.0f, dzf = 0.0f;
+      if (live) {
+        const int zc = full ? oz : wrapi(ck[2] - s + oz, nc);
+        const int yc = full ? oy : wrapi(ck[1] - s + oy, nc);
+        int dyi = ck[1] - yc, dzi = ck[2] - zc;
+        if (2 * dyi > nc) dyi -= nc;
+        else if (2 * dyi < -nc) dyi += nc;
+        if (2 * dzi > nc) dzi -= nc;
+        else if (2 * dzi < -nc) dzi += nc;
+        dyf = (float)dyi;
+        dzf = (float)dzi;
+        const int row = (zc * nc + yc) * nc;
+        rowck = row + ck[0];
+        const int xl = ck[0] - s, xh = ck[0] + s;
+        if (full) {
+          b1 = A.start[row];
+          e1 = A.start[row + nc];
+        } else if (xl >= 0 && xh < nc) {
+          b1 = A.start[row + xl];
+          e1 = A.start[row + xh + 1];
+        } else if (xl < 0) {
+          b1 = A.start[row + xl + nc];
+          e1 = A.start[row + nc];
+          b2 = A.start[row];
+          e2 = A.start[row + xh + 1];
+        } else {
+          b1 = A.start[row + xl];
+          e1 = A.start[row + nc];
+          b2 = A.start[row];
+          e2 = A.start[row + xh - nc + 1];
+        }
+      }
+      const int l1 = e1 - b1, len = l1 + (e2 - b2);
+      const int m = __reduce_max_sync(kFull, len);
+      for (int t = 0; t < m; ++t) {
+        const int j = t < l1 ? b1 + t : b2 + (t - l1);
+        bool pass = false;
+        float dx = 0.0f, dy = 0.0f, dz = 0.0f;
+        if (t < len && j != k) {
+          int di = rowck - A.scell[j];
+          if (2 * di > nc) di -= nc;
+          else if (2 * di < -nc) di += nc;
+          dx = (float)di + (ok3[0] - A.so[j]);
+          dy = dyf + (ok3[1] - A.so[n + j]);
+          dz = dzf + (ok3[2] - A.so[2 * n + j]);
+          if (need_box) {
+            dx = minimgf_box(dx, Lf);
+            dy = minimgf_box(dy, Lf);
+            dz = minimgf_box(dz, Lf);
+          }
+          pass = !(dx * dx + dy * dy + dz * dz > rl2);
+        }
+        const unsigned bal = __ballot_sync(kFull, pass);
+        if (pass) {
+          const int p = np + __popc(bal & below);
+          Q.dx[p] = dx;
+          Q.dy[p] = dy;
+          Q.dz[p] = dz;
+          Q.j[p] = j;
+          Q.own[p] = lane;
+        }
+        np += __popc(bal);
+        if (np >= 32) {
+          __syncwarp();
+          filter_passes(32);
+          // move the passes beyond the first 32 to the front
+          const bool mv = lane < np - 32;
+          float mx = 0.0f, my = 0.0f, mz = 0.0f;
+          int mj = 0, mo = 0;
+          if (mv) {
+            mx = Q.dx[32 + lane];
+            my = Q.dy[32 + lane];
+            mz = Q.dz[32 + lane];
+            mj = Q.j[32 + lane];
+            mo = Q.own[32 + lane];
+          }
+          __syncwarp();
+          if (mv) {
+            Q.dx[lane] = mx;
+            Q.dy[lane] = my;
+            Q.dz[lane] = mz;
+            Q.j[lane] = mj;
+            Q.own[lane] = mo;
+          }
+          __syncwarp();
+          np -= 32;
+        }
+      }
+    }
+  }
+  __syncwarp();
+  if (np > 0) filter_passes(np);
+  if (ns > 0) flush_survivors();
+  if (live) {
     for (int q = 0; q < cnt; ++q) {
       A.cand_j[(int64_t)q * n + k] = lj[q];
       A.cand_t[(int64_t)q * n + k] = lt[q];
