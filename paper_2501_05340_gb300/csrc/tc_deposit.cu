@@ -11,16 +11,19 @@
 // the element's deposit is the sum of the four quadrants (the lo*lo one is below
 // the accuracy of the others and harmless).
 //
-// Operands live in shared memory in the K-major layout without swizzle: core
-// matrices of 8 rows x 16 bytes, (row/8) * 256 + (k/8) * 128 + (row%8) * 16 + (k%8) * 2.
-// Each of 8 warp pairs owns one 64-column accumulator in tensor memory and works on
-// one element at a time. The scanner warp compacts the particles that reach the
-// element and writes, per 16 of them, the factor tile and the B operand; the
-// builder warp writes the A operand and its lane 0 issues the tcgen05.mma and a
-// tcgen05.commit that arrives on the slot's mbarrier when the tensor core has read
-// it (commits track the issuing thread's own MMAs, so the pairs need no common
-// issuer). After an element's last chunk the builder queues (element, pair); 4
-// epilogue warps, one per TMEM lane quarter, drain the queue. Every wait is bounded in wall-clock time: on expiry the kernel
+// Operands live in shared memory in the MN-major layout without swizzle: core
+// matrices of 8 particles (K) x 16 bytes (8 consecutive rows of M or N), the row
+// groups 128 B apart and the particle octets one row-group column apart (2048 B for
+// A, 1024 B for B). So one lane per particle writes its own 16-byte pieces: no
+// factor tile is staged, and every store is a whole core-matrix row.
+// Each of 6 worker warps owns one 64-column accumulator in tensor memory and works on
+// one element at a time: it compacts the particles that reach the element into a
+// ring (order kept), and per 32 of them every lane computes its particle's factors
+// in registers and writes the operands into one of the worker's two stages; lane 0
+// issues the two MMAs (K = 16 each) and a tcgen05.commit that arrives on the stage's
+// mbarrier when the tensor core has read it. After an element's last chunk the
+// worker queues (element, worker); 4 epilogue warps, one per TMEM lane quarter,
+// drain the queue. Every wait is bounded in wall-clock time: on expiry the kernel
 // records PC_ETIMEOUT, stops issuing, waits (bounded) for its MMAs and frees its
 // tensor memory.
 #include <cuda_bf16.h>
@@ -31,14 +34,9 @@
 
 namespace {
 
-constexpr int kChunk = 16;
 
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
-
-__device__ __forceinline__ int kmaj_off(int row, int k) {
-  return (row >> 3) * 256 + (k >> 3) * 128 + (row & 7) * 16 + (k & 7) * 2;
-}
 
 // Shared-memory matrix descriptor: start address, leading (K) and stride (M/N)
 // byte offsets, fixed version bits 46-48 = 0b001, no swizzle.
@@ -81,62 +79,46 @@ __device__ __forceinline__ void split2(float x, float y, uint32_t* hi, uint32_t*
   }
 }
 
-// 16 values (one per particle of the chunk) of one operand row, hi part to row
-// `row` and lo part to row `row + lo_off`.
-template <int kBf16>
-__device__ __forceinline__ void store_row(uint8_t* tile, int row, int lo_off, const float v[16]) {
-  uint32_t hi[8], lo[8];
-#pragma unroll
-  for (int q = 0; q < 8; ++q) split2<kBf16>(v[2 * q], v[2 * q + 1], &hi[q], &lo[q]);
-  *reinterpret_cast<uint4*>(tile + kmaj_off(row, 0)) = make_uint4(hi[0], hi[1], hi[2], hi[3]);
-  *reinterpret_cast<uint4*>(tile + kmaj_off(row, 8)) = make_uint4(hi[4], hi[5], hi[6], hi[7]);
-  *reinterpret_cast<uint4*>(tile + kmaj_off(row + lo_off, 0)) = make_uint4(lo[0], lo[1], lo[2], lo[3]);
-  *reinterpret_cast<uint4*>(tile + kmaj_off(row + lo_off, 8)) = make_uint4(lo[4], lo[5], lo[6], lo[7]);
-}
-
 __device__ __forceinline__ int wrapi(int a, int n) {
   a %= n;
   return a < 0 ? a + n : a;
 }
 
-constexpr int kPairs = 8;                           // scanner + builder warp pairs, one TMEM accumulator each
+constexpr int kChunk = 32;                          // particles per operand stage (two MMAs)
+constexpr int kWorkers = 6;                         // worker warps, one TMEM accumulator each
 constexpr int kEpiWarps = 4;                        // one per TMEM lane quarter
-constexpr int kThreads = 32 * (2 * kPairs + kEpiWarps);
-constexpr int kRing = 2;                            // operand and factor slots per pair
-constexpr int kList = 64;                           // kept-particle ring (>= 2 kChunk + 32)
-constexpr int kQ = 32;                              // finished-element queue (>= 2 kPairs)
+constexpr int kThreads = 32 * (kWorkers + kEpiWarps);
+constexpr int kStages = 2;                          // operand stages per worker
+constexpr int kList = 64;                           // kept-particle ring (>= kChunk + 32)
+constexpr int kQ = 32;                              // finished-element queue (>= 2 kWorkers)
 constexpr int kMaxRanges = 125;                     // (2 rho + 1)^3 neighbour cells, rho <= 2
-constexpr int kPf = 20;                             // words per factor row: 16 particles + pad
+constexpr int kAStage = 8192;                       // A: 128 rows x 32 particles x 2 B
+constexpr int kBStage = 4096;                       // B: 64 rows x 32 particles x 2 B
+constexpr unsigned kFull = 0xffffffffu;
 constexpr unsigned long long kWaitNs = 2000000000;  // a wait without progress for 2 s fails
 
-// Factor tiles are [v][p] with v = 8 a + i (axis a, node i) and 24 + c (charge c);
-// the row pitch of 20 words keeps both the lane-per-particle stores and the float4
-// row reads free of bank conflicts. Kept records are stored as four planes of
-// float4 so that consecutive ring positions hit consecutive banks.
+// Kept records are stored as four planes of float4 so that consecutive ring
+// positions hit consecutive banks.
 struct __align__(1024) TcSmem {
-  uint8_t a[kPairs][kRing][4096];
-  uint8_t b[kPairs][kRing][2048];
-  float pf[kPairs][kRing][28][kPf];
-  float4 lrec[kPairs][4][kList];
-  int lmeta[kPairs][kList];
+  uint8_t a[kWorkers][kStages][kAStage];
+  uint8_t b[kWorkers][kStages][kBStage];
+  float4 lrec[kWorkers][4][kList];
+  int lmeta[kWorkers][kList];
   float comb[64][33];
-  int pre[kPairs][kMaxRanges + 1];
-  int rbeg[kPairs][kMaxRanges];
-  int rmeta[kPairs][kMaxRanges];
-  int cmeta[kPairs][kRing][4];                  // chunk: element (-1 ends the stream), first, last
-  unsigned long long empty[kPairs][kRing];      // tcgen05.commit: the operand slot has been read
-  unsigned long long pf_full[kPairs][kRing];    // scanner: factors, B rows and chunk meta written
-  unsigned long long pf_empty[kPairs][kRing];   // builder: factor slot read
-  unsigned long long acc_full[kPairs];          // tcgen05.commit: the element's MMAs are done
-  unsigned long long acc_empty[kPairs];         // 2 arrivals: epilogue quarters 0 and 1
-  unsigned long long fin[kPairs];               // tcgen05.commit at builder exit
+  int pre[kWorkers][kMaxRanges + 1];
+  int rbeg[kWorkers][kMaxRanges];
+  int rmeta[kWorkers][kMaxRanges];
+  unsigned long long empty[kWorkers][kStages];  // tcgen05.commit: the operand stage has been read
+  unsigned long long acc_full[kWorkers];        // tcgen05.commit: the element's MMAs are done
+  unsigned long long acc_empty[kWorkers];       // 2 arrivals: epilogue quarters 0 and 1
+  unsigned long long fin[kWorkers];             // tcgen05.commit at worker exit
   unsigned long long qfull[kQ];                 // queue entry written
   unsigned long long comb_full;                 // 2 arrivals: epilogue quarters 2 and 3
   unsigned long long comb_empty;                // 2 arrivals: epilogue quarters 0 and 1
   int qe[kQ];
   int qb[kQ];
   int q_head;
-  int progress[kPairs];
+  int progress[kWorkers];
   int failed;
   uint32_t tmem_base;
 };
@@ -211,7 +193,7 @@ __device__ bool mbar_wait_progress(TcSmem& S, unsigned long long* bar, uint32_t 
     const unsigned long long now = gtime();
     if (now - t0 > kWaitNs) {
       int sum = 0;
-      for (int k = 0; k < kPairs; ++k) sum += vload(&S.progress[k]);
+      for (int k = 0; k < kWorkers; ++k) sum += vload(&S.progress[k]);
       if (sum == last_sum) return false;
       last_sum = sum;
       t0 = now;
@@ -224,7 +206,7 @@ __device__ __forceinline__ void fail_now(TcSmem& S, unsigned long long* counters
   atomicMax(counters, (unsigned long long)PC_ETIMEOUT);
 }
 
-// Queue push by a builder's lane 0: (element, pair) or the exit sentinel e = -1.
+// Queue push by a worker's lane 0: (element, worker) or the exit sentinel e = -1.
 __device__ __forceinline__ void queue_push(TcSmem& S, int e, int k) {
   const int t = atomicAdd(&S.q_head, 1);
   S.qe[t % kQ] = e;
@@ -232,31 +214,32 @@ __device__ __forceinline__ void queue_push(TcSmem& S, int e, int k) {
   mbar_arrive(&S.qfull[t % kQ]);  // release: the entry is visible to the waiter
 }
 
-// Scanner warp of pair k: owns elements blockIdx.x * kPairs + k + m * gridDim.x * kPairs.
+// Worker warp k: owns elements blockIdx.x * kWorkers + k + m * gridDim.x * kWorkers.
 // Per element: the (2 rho + 1)^3 neighbour cell ranges and their prefix sum, then an
 // ordered warp-level compaction of the particles whose support reaches the element
-// (per-axis reach bits), and per 16 kept particles: the factors (lane parallel) into
-// the pair's factor slot, the B operand rows q_c kx_i (hi and lo) into the operand
-// slot, and the chunk's meta for the builder.
-template <int kBf16>
-__device__ void tc_scanner(TcSmem& S, const TcDepositArgs& A, int k, int lane) {
-  const int n1 = A.n1, ne = A.ne, rho = A.rho, span = 2 * rho + 1, nrange = span * span * span;
-  const int nodes = n1 * n1 * n1;
+// (per-axis reach bits) into the ring; per 32 kept particles, lane p computes the
+// factors of particle p (kx scaled by 2^4, kz by 2^8) and writes its A rows
+// ky_j kz_k and B rows q_c kx_i, hi and lo, into the stage, and lane 0 issues the
+// MMAs. Accumulation order inside an element is the kept order, so the deposit is
+// deterministic.
+template <int kBf16, int N1>
+__device__ void tc_worker(TcSmem& S, const TcDepositArgs& A, uint32_t tmem, uint32_t idesc, int k, int lane) {
+  constexpr int NODES = N1 * N1 * N1;
+  constexpr unsigned nmask = (1u << N1) - 1u;
+  const int ne = A.ne, rho = A.rho, span = 2 * rho + 1, nrange = span * span * span;
   const int64_t nel = (int64_t)ne * ne * ne;
-  // factor slots of this lane: particle p, nodes 4 hh .. 4 hh + 3 of each axis
-  const int p = lane & 15, hh = lane >> 4;
-  const unsigned lanemask = (((1u << n1) - 1u) >> (4 * hh)) & 15u;
-  float sv[4];
+  const uint32_t acc = tmem + 64u * (uint32_t)k;
+  float sv[N1];
 #pragma unroll
-  for (int ii = 0; ii < 4; ++ii) sv[ii] = (4 * hh + ii < n1) ? A.s[4 * hh + ii] : 0.0f;
+  for (int i = 0; i < N1; ++i) sv[i] = A.s[i];
   const float c2l = A.c2l;
-  // B operand row of this lane: q_c kx_i, rows of the factor tile 24 + c and i
-  const bool brow = lane < 4 * n1;
-  const int bc = lane / n1, bq = (24 + bc) * kPf, bx = (lane - bc * n1) * kPf;
-  int chunk = 0, prog = 0;
+  // this lane's 16-byte pieces in the stages: particle octet (lane / 8), row lane % 8
+  const int pa = (lane >> 3) * (kAStage / 4) + (lane & 7) * 16;
+  const int pb = (lane >> 3) * (kBStage / 4) + (lane & 7) * 16;
+  int chunk = 0, prog = 0, used = 0;
   bool ok = true;
-  for (int64_t e = (int64_t)blockIdx.x * kPairs + k; ok && e < nel; e += (int64_t)gridDim.x * kPairs) {
-    if (__any_sync(0xffffffffu, vload(&S.failed))) break;
+  for (int64_t e = (int64_t)blockIdx.x * kWorkers + k; ok && e < nel; e += (int64_t)gridDim.x * kWorkers) {
+    if (__any_sync(kFull, vload(&S.failed))) break;
     const int ex = (int)(e % ne), ey = (int)((e / ne) % ne), ez = (int)(e / ((int64_t)ne * ne));
     int total = 0;
     for (int r0 = 0; r0 < nrange; r0 += 32) {
@@ -274,11 +257,11 @@ __device__ void tc_scanner(TcSmem& S, const TcDepositArgs& A, int k, int lane) {
       int x = cnt;
 #pragma unroll
       for (int o = 1; o < 32; o <<= 1) {
-        const int y = __shfl_up_sync(0xffffffffu, x, o);
+        const int y = __shfl_up_sync(kFull, x, o);
         if (lane >= o) x += y;
       }
       if (r < nrange) S.pre[k][r + 1] = total + x;
-      total += __shfl_sync(0xffffffffu, x, 31);
+      total += __shfl_sync(kFull, x, 31);
     }
     if (lane == 0) S.pre[k][0] = 0;
     __syncwarp();
@@ -301,19 +284,19 @@ __device__ void tc_scanner(TcSmem& S, const TcDepositArgs& A, int k, int lane) {
         c2r = A.rec[4 * j + 2];
         c3r = A.rec[4 * j + 3];
       }
-      rlo = __shfl_sync(0xffffffffu, r, 0);  // the next batch starts at or after this lane's range
+      rlo = __shfl_sync(kFull, r, 0);  // the next batch starts at or after this lane's range
     };
     if (total > 0) load_batch(0);
     for (;;) {
-      // refill until the ring holds more than two chunks or the neighbourhood is
+      // refill until the ring holds more than a chunk or the neighbourhood is
       // exhausted, so that "last chunk of the element" is known exactly
-      while (scan < total && tail - head <= 2 * kChunk) {
+      while (scan < total && tail - head <= kChunk) {
         bool keep = false;
         if (cvalid) {
           const unsigned R = __float_as_uint(c3r.y);
           keep = ((R >> (cm & 31)) & (R >> ((cm >> 8) & 31)) & (R >> ((cm >> 16) & 31)) & 1u) != 0u;
         }
-        const unsigned bal = __ballot_sync(0xffffffffu, keep);
+        const unsigned bal = __ballot_sync(kFull, keep);
         if (keep) {
           const int pos = (tail + __popc(bal & ((1u << lane) - 1u))) & (kList - 1);
           S.lrec[k][0][pos] = c0r;
@@ -332,169 +315,117 @@ __device__ void tc_scanner(TcSmem& S, const TcDepositArgs& A, int k, int lane) {
       if (avail == 0) break;
       const int take = avail < kChunk ? avail : kChunk;
       const bool last = avail <= kChunk;  // the refill stopped short only because the scan is done
-      const int slot = chunk % kRing;
-      const uint32_t par = (uint32_t)((chunk / kRing - 1) & 1);
-      // the builder has read this factor slot (chunk - kRing)
-      const bool pf_free = chunk < kRing || mbar_wait(&S.pf_empty[k][slot], par, &S.failed);
-      if (!__all_sync(0xffffffffu, pf_free)) {
+      const int st = chunk % kStages;
+      // the MMAs of chunk - kStages have read this stage
+      const bool free_stage =
+          chunk < kStages || mbar_wait(&S.empty[k][st], (uint32_t)((chunk / kStages - 1) & 1), &S.failed);
+      if (!__all_sync(kFull, free_stage)) {
         if (lane == 0) fail_now(S, A.counters + CNT_STATUS);
         ok = false;
         break;
       }
-      // factors: lane -> particle p, nodes 4 hh + ii; kx scaled by 2^4, kz by 2^8
-      {
-        float f[3][4] = {};
-        float qv[2] = {0.0f, 0.0f};
-        if (p < take) {
-          const int pos = (head + p) & (kList - 1);
-          const int meta = S.lmeta[k][pos];
-          const float4 r0 = S.lrec[k][0][pos], r1 = S.lrec[k][1][pos], r2 = S.lrec[k][2][pos], r3 = S.lrec[k][3][pos];
-          const float t3[3] = {r0.x, r0.y, r0.z};
-          const float iz[3] = {r0.w * 16.0f, r1.x, r1.y * 256.0f};
-          const unsigned mk[3] = {__float_as_uint(r2.z), __float_as_uint(r2.w), __float_as_uint(r3.x)};
+      // factors of particle `lane` of the chunk
+      float fx[N1], fy[N1], fz[N1], qv[4];
 #pragma unroll
-          for (int a = 0; a < 3; ++a) {
-            const int wo = ((meta >> (8 * a)) & 31) - 8 * a;
-            const int sh = wo * n1 + 4 * hh;
-            const unsigned bits = (sh < 32 ? (mk[a] >> sh) : 0u) & lanemask;
-            const float base = (float)(wo - rho) - t3[a];
+      for (int i = 0; i < N1; ++i) fx[i] = fy[i] = fz[i] = 0.0f;
+      qv[0] = qv[1] = qv[2] = qv[3] = 0.0f;
+      if (lane < take) {
+        const int pos = (head + lane) & (kList - 1);
+        const int meta = S.lmeta[k][pos];
+        const float4 r0 = S.lrec[k][0][pos], r1 = S.lrec[k][1][pos], r2 = S.lrec[k][2][pos], r3 = S.lrec[k][3][pos];
+        const float t3[3] = {r0.x, r0.y, r0.z};
+        const float iz[3] = {r0.w * 16.0f, r1.x, r1.y * 256.0f};
+        const unsigned mk[3] = {__float_as_uint(r2.z), __float_as_uint(r2.w), __float_as_uint(r3.x)};
 #pragma unroll
-            for (int ii = 0; ii < 4; ++ii) {
-              const float d = base + sv[ii];
-              const float g = ex2(-(d * d) * c2l) * iz[a];
-              f[a][ii] = ((bits >> ii) & 1u) ? g : 0.0f;
-            }
+        for (int a = 0; a < 3; ++a) {
+          const int wo = ((meta >> (8 * a)) & 31) - 8 * a;
+          const int sh = wo * N1;
+          const unsigned bits = (sh < 32 ? (mk[a] >> sh) : 0u) & nmask;
+          const float base = (float)(wo - rho) - t3[a];
+          float* f = a == 0 ? fx : (a == 1 ? fy : fz);
+#pragma unroll
+          for (int i = 0; i < N1; ++i) {
+            const float d = base + sv[i];
+            const float g = ex2(-(d * d) * c2l) * iz[a];
+            f[i] = ((bits >> i) & 1u) ? g : 0.0f;
           }
-          qv[0] = hh ? r2.x : r1.z;
-          qv[1] = hh ? r2.y : r1.w;
         }
-        float* pf = &S.pf[k][slot][0][0];
-#pragma unroll
-        for (int a = 0; a < 3; ++a)
-#pragma unroll
-          for (int ii = 0; ii < 4; ++ii) pf[(8 * a + 4 * hh + ii) * kPf + p] = f[a][ii];
-        pf[(24 + 2 * hh) * kPf + p] = qv[0];
-        pf[(25 + 2 * hh) * kPf + p] = qv[1];
+        qv[0] = r1.z;
+        qv[1] = r1.w;
+        qv[2] = r2.x;
+        qv[3] = r2.y;
       }
-      // the MMA of chunk - kRing has read this operand slot
-      const bool op_free = chunk < kRing || mbar_wait(&S.empty[k][slot], par, &S.failed);
-      if (!__all_sync(0xffffffffu, op_free)) {
-        if (lane == 0) fail_now(S, A.counters + CNT_STATUS);
-        ok = false;
-        break;
-      }
-      __syncwarp();
-      if (brow) {
-        const float4* x0 = reinterpret_cast<const float4*>(&S.pf[k][slot][0][0] + bq);
-        const float4* x1 = reinterpret_cast<const float4*>(&S.pf[k][slot][0][0] + bx);
-        float v[16];
+      // A rows jk = j + N1 k: YZ_hi in row groups 0..7, YZ_lo in 8..15
+      uint8_t* ta = S.a[k][st] + pa;
 #pragma unroll
-        for (int t = 0; t < 4; ++t) {
-          const float4 g = x0[t], h = x1[t];
-          v[4 * t] = g.x * h.x;
-          v[4 * t + 1] = g.y * h.y;
-          v[4 * t + 2] = g.z * h.z;
-          v[4 * t + 3] = g.w * h.w;
+      for (int g = 0; g < 8; ++g) {
+        if (8 * g < N1 * N1) {
+          uint32_t hi[4], lo[4];
+#pragma unroll
+          for (int u = 0; u < 4; ++u) {
+            const int jk0 = 8 * g + 2 * u, jk1 = jk0 + 1;
+            const float v0 = jk0 < N1 * N1 ? fy[jk0 % N1] * fz[jk0 / N1] : 0.0f;
+            const float v1 = jk1 < N1 * N1 ? fy[jk1 % N1] * fz[jk1 / N1] : 0.0f;
+            split2<kBf16>(v0, v1, &hi[u], &lo[u]);
+          }
+          *reinterpret_cast<uint4*>(ta + 128 * g) = make_uint4(hi[0], hi[1], hi[2], hi[3]);
+          *reinterpret_cast<uint4*>(ta + 128 * (8 + g)) = make_uint4(lo[0], lo[1], lo[2], lo[3]);
         }
-        store_row<kBf16>(S.b[k][slot], lane, 32, v);
+      }
+      // B rows ci = c N1 + i: A_hi in row groups 0..3, A_lo in 4..7
+      uint8_t* tb = S.b[k][st] + pb;
+#pragma unroll
+      for (int g = 0; g < 4; ++g) {
+        if (8 * g < 4 * N1) {
+          uint32_t hi[4], lo[4];
+#pragma unroll
+          for (int u = 0; u < 4; ++u) {
+            const int c0 = 8 * g + 2 * u, c1 = c0 + 1;
+            const float v0 = c0 < 4 * N1 ? qv[c0 / N1] * fx[c0 % N1] : 0.0f;
+            const float v1 = c1 < 4 * N1 ? qv[c1 / N1] * fx[c1 % N1] : 0.0f;
+            split2<kBf16>(v0, v1, &hi[u], &lo[u]);
+          }
+          *reinterpret_cast<uint4*>(tb + 128 * g) = make_uint4(hi[0], hi[1], hi[2], hi[3]);
+          *reinterpret_cast<uint4*>(tb + 128 * (4 + g)) = make_uint4(lo[0], lo[1], lo[2], lo[3]);
+        }
       }
       asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
       __syncwarp();
+      const bool first = nmma == 0;
       if (lane == 0) {
-        S.cmeta[k][slot][0] = (int)e;
-        S.cmeta[k][slot][1] = nmma == 0 ? 1 : 0;
-        S.cmeta[k][slot][2] = last ? 1 : 0;
-        mbar_arrive(&S.pf_full[k][slot]);
+        bool go = true;
+        if (first && used > 0)  // the epilogue has read this accumulator's previous element
+          go = mbar_wait(&S.acc_empty[k], (uint32_t)((used - 1) & 1), &S.failed);
+        if (go) {
+          asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+          const uint64_t da = make_desc(smem_u32(S.a[k][st]), kAStage / 4, 128);
+          const uint64_t db = make_desc(smem_u32(S.b[k][st]), kBStage / 4, 128);
+          mma_issue(acc, da, db, idesc, first ? 0u : 1u);
+          // particles 16..31: two particle octets further
+          if (take > 16) mma_issue(acc, da + (uint64_t)(kAStage / 32), db + (uint64_t)(kBStage / 32), idesc, 1u);
+          mma_commit(&S.empty[k][st]);
+          if (last) {
+            mma_commit(&S.acc_full[k]);
+            queue_push(S, (int)e, k);
+          }
+        } else {
+          fail_now(S, A.counters + CNT_STATUS);
+        }
       }
+      if (first) ++used;
       head += take;
       ++nmma;
       ++chunk;
+      if (__shfl_sync(kFull, vload(&S.failed), 0)) {
+        ok = false;
+        break;
+      }
       if (last) break;
     }
     if (ok && nmma == 0) {
-      float* out = A.field + e * 4 * nodes;
-      for (int t = lane; t < 4 * nodes; t += 32) out[t] = 0.0f;
+      float* out = A.field + e * 4 * NODES;
+      for (int t = lane; t < 4 * NODES; t += 32) out[t] = 0.0f;
     }
-  }
-  // end of stream for the builder
-  const int slot = chunk % kRing;
-  const bool free_slot =
-      chunk < kRing || mbar_wait(&S.pf_empty[k][slot], (uint32_t)((chunk / kRing - 1) & 1), &S.failed);
-  if (lane == 0) {
-    if (!free_slot) fail_now(S, A.counters + CNT_STATUS);
-    S.cmeta[k][slot][0] = -1;
-    mbar_arrive(&S.pf_full[k][slot]);
-  }
-}
-
-// Builder warp of pair k: per chunk the A operand rows ky_j kz_k (hi and lo, 2 per
-// lane) from the factor slot, then lane 0 issues one tcgen05.mma into the pair's
-// accumulator and its commits. Accumulation order inside an element is the kept
-// order, so the deposit is deterministic.
-template <int kBf16>
-__device__ void tc_builder(TcSmem& S, const TcDepositArgs& A, uint32_t tmem, uint32_t idesc, int k, int lane) {
-  const int n1 = A.n1;
-  const uint32_t acc = tmem + 64u * (uint32_t)k;
-  // A operand rows of this lane: jk = lane + 32 rr -> factor tile rows 8 + j and 16 + k
-  int ry[2], rz[2];
-#pragma unroll
-  for (int rr = 0; rr < 2; ++rr) {
-    const int row = lane + 32 * rr, kk = row / n1;
-    ry[rr] = (8 + row - kk * n1) * kPf;
-    rz[rr] = (16 + kk) * kPf;
-  }
-  const int nrow = n1 * n1;
-  int used = 0;
-  for (int c = 0;; ++c) {
-    const int slot = c % kRing;
-    const bool got = mbar_wait_progress(S, &S.pf_full[k][slot], (uint32_t)((c / kRing) & 1));
-    if (!__all_sync(0xffffffffu, got)) {
-      if (lane == 0 && !vload(&S.failed)) fail_now(S, A.counters + CNT_STATUS);
-      break;
-    }
-    const int e = S.cmeta[k][slot][0];
-    if (e < 0) break;
-    const int first = S.cmeta[k][slot][1], last = S.cmeta[k][slot][2];
-#pragma unroll
-    for (int rr = 0; rr < 2; ++rr) {
-      const int row = lane + 32 * rr;
-      if (row < nrow) {
-        const float4* x0 = reinterpret_cast<const float4*>(&S.pf[k][slot][0][0] + ry[rr]);
-        const float4* x1 = reinterpret_cast<const float4*>(&S.pf[k][slot][0][0] + rz[rr]);
-        float v[16];
-#pragma unroll
-        for (int t = 0; t < 4; ++t) {
-          const float4 g = x0[t], h = x1[t];
-          v[4 * t] = g.x * h.x;
-          v[4 * t + 1] = g.y * h.y;
-          v[4 * t + 2] = g.z * h.z;
-          v[4 * t + 3] = g.w * h.w;
-        }
-        store_row<kBf16>(S.a[k][slot], row, 64, v);
-      }
-    }
-    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-    __syncwarp();
-    if (lane == 0) {
-      mbar_arrive(&S.pf_empty[k][slot]);
-      bool go = true;
-      if (first && used > 0)  // the epilogue has read this accumulator's previous element
-        go = mbar_wait(&S.acc_empty[k], (uint32_t)((used - 1) & 1), &S.failed);
-      if (go) {
-        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-        mma_issue(acc, make_desc(smem_u32(S.a[k][slot]), 128, 256), make_desc(smem_u32(S.b[k][slot]), 128, 256), idesc,
-                  first ? 0u : 1u);
-        mma_commit(&S.empty[k][slot]);
-        if (last) {
-          mma_commit(&S.acc_full[k]);
-          queue_push(S, e, k);
-        }
-      } else {
-        fail_now(S, A.counters + CNT_STATUS);
-      }
-    }
-    if (first) ++used;
-    if (__shfl_sync(0xffffffffu, vload(&S.failed), 0)) break;
   }
   __syncwarp();
   if (lane == 0) {
@@ -520,14 +451,14 @@ __device__ __forceinline__ void tmem_ld16(uint32_t taddr, float r[16]) {
 }
 
 // Epilogue warp for TMEM lane quarter q: drains the finished-element queue in
-// order until every builder has sent its exit sentinel. Accumulator columns
+// order until every worker has sent its exit sentinel. Accumulator columns
 // 0..31 hold the products with A_hi, 32..63 those with A_lo; lanes 0..63 the YZ_hi
 // rows, 64..127 the YZ_lo rows, combined through shared memory.
 __device__ void tc_epilogue(TcSmem& S, const TcDepositArgs& A, uint32_t tmem, int q, int lane) {
   const int n1 = A.n1, nodes = n1 * n1 * n1;
   unsigned seen = 0u;  // bit k: parity of the next acc_full phase of pair k
   int exited = 0;
-  for (int t = 0; exited < kPairs; ++t) {
+  for (int t = 0; exited < kWorkers; ++t) {
     if (!mbar_wait_progress(S, &S.qfull[t % kQ], (uint32_t)((t / kQ) & 1))) {
       if (lane == 0 && q == 0 && !vload(&S.failed)) fail_now(S, A.counters + CNT_STATUS);
       return;
@@ -596,22 +527,20 @@ __device__ void tc_epilogue(TcSmem& S, const TcDepositArgs& A, uint32_t tmem, in
   }
 }
 
-template <int kBf16>
+template <int kBf16, int N1>
 __global__ void __launch_bounds__(kThreads, 1) k_tc_deposit(TcDepositArgs A) {
   extern __shared__ uint8_t smraw[];
   TcSmem& S = *reinterpret_cast<TcSmem*>(smraw + ((1024 - (smem_u32(smraw) & 1023)) & 1023));
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-  for (int i = tid; i < kPairs * kRing * 4096 / 16; i += kThreads)
+  // rows no lane writes (n1 < 8) stay zero
+  for (int i = tid; i < kWorkers * kStages * kAStage / 16; i += kThreads)
     reinterpret_cast<uint4*>(&S.a[0][0][0])[i] = make_uint4(0, 0, 0, 0);
-  for (int i = tid; i < kPairs * kRing * 2048 / 16; i += kThreads)
+  for (int i = tid; i < kWorkers * kStages * kBStage / 16; i += kThreads)
     reinterpret_cast<uint4*>(&S.b[0][0][0])[i] = make_uint4(0, 0, 0, 0);
   if (tid == 0) {
-    for (int k = 0; k < kPairs; ++k) {
-      for (int s = 0; s < kRing; ++s) {
+    for (int k = 0; k < kWorkers; ++k) {
+      for (int s = 0; s < kStages; ++s)
         asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&S.empty[k][s])));
-        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&S.pf_full[k][s])));
-        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&S.pf_empty[k][s])));
-      }
       asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&S.acc_full[k])));
       asm volatile("mbarrier.init.shared::cta.b64 [%0], 2;" ::"r"(smem_u32(&S.acc_empty[k])));
       asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&S.fin[k])));
@@ -625,7 +554,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_tc_deposit(TcDepositArgs A) {
   }
   if (warp == 0) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&S.tmem_base)),
-                 "r"(64u * kPairs));
+                 "r"(512));
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
   }
   asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
@@ -634,19 +563,40 @@ __global__ void __launch_bounds__(kThreads, 1) k_tc_deposit(TcDepositArgs A) {
   __syncthreads();
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
   const uint32_t tmem = S.tmem_base;
+  // D FP32, A and B FP16 or BF16, both MN-major (transposed), N = 64, M = 128
   const uint32_t fmt = kBf16 ? 1u : 0u;
-  const uint32_t idesc = (1u << 4) | (fmt << 7) | (fmt << 10) | (8u << 17) | (8u << 24);
-  if (warp < kPairs)
-    tc_scanner<kBf16>(S, A, warp, lane);
-  else if (warp < 2 * kPairs)
-    tc_builder<kBf16>(S, A, tmem, idesc, warp - kPairs, lane);
+  const uint32_t idesc =
+      (1u << 4) | (fmt << 7) | (fmt << 10) | (1u << 15) | (1u << 16) | (8u << 17) | (8u << 24);
+  if (warp < kWorkers)
+    tc_worker<kBf16, N1>(S, A, tmem, idesc, warp, lane);
   else
-    tc_epilogue(S, A, tmem, warp - 2 * kPairs, lane);  // warps 16..19: TMEM lane quarter = warp % 4
+    tc_epilogue(S, A, tmem, warp % 4, lane);  // a warp reaches the TMEM lane quarter warp % 4
   __syncwarp();
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
   __syncthreads();
-  if (warp == 0)
-    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(64u * kPairs));
+  if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(512));
+}
+
+template <int kBf16, int N1>
+cudaError_t tc_launch(const TcDepositArgs& A, int grid, size_t smem, cudaStream_t st) {
+  PC_CUDA_TRY(cudaFuncSetAttribute(k_tc_deposit<kBf16, N1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  k_tc_deposit<kBf16, N1><<<(unsigned)grid, kThreads, smem, st>>>(A);
+  return cudaGetLastError();
+}
+
+template <int kBf16>
+cudaError_t tc_launch_n1(const TcDepositArgs& A, int grid, size_t smem, cudaStream_t st) {
+  switch (A.n1) {
+    case 1: return tc_launch<kBf16, 1>(A, grid, smem, st);
+    case 2: return tc_launch<kBf16, 2>(A, grid, smem, st);
+    case 3: return tc_launch<kBf16, 3>(A, grid, smem, st);
+    case 4: return tc_launch<kBf16, 4>(A, grid, smem, st);
+    case 5: return tc_launch<kBf16, 5>(A, grid, smem, st);
+    case 6: return tc_launch<kBf16, 6>(A, grid, smem, st);
+    case 7: return tc_launch<kBf16, 7>(A, grid, smem, st);
+    case 8: return tc_launch<kBf16, 8>(A, grid, smem, st);
+    default: return cudaErrorInvalidValue;
+  }
 }
 
 }  // namespace
@@ -658,16 +608,9 @@ cudaError_t pc_tc_deposit_launch(const TcDepositArgs& A, cudaStream_t st, int* n
   PC_CUDA_TRY(cudaGetDevice(&dev));
   PC_CUDA_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
   // one persistent CTA per SM: it holds all 512 tensor-memory columns
-  int64_t grid = (nel + kPairs - 1) / kPairs;
+  int64_t grid = (nel + kWorkers - 1) / kWorkers;
   if (grid > sms) grid = sms;
   if (grid < 1) grid = 1;
   *nblocks = (int)grid;
-  if (A.tc_type == PC_TC_BF16) {
-    PC_CUDA_TRY(cudaFuncSetAttribute(k_tc_deposit<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    k_tc_deposit<1><<<(unsigned)grid, kThreads, smem, st>>>(A);
-  } else {
-    PC_CUDA_TRY(cudaFuncSetAttribute(k_tc_deposit<0>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    k_tc_deposit<0><<<(unsigned)grid, kThreads, smem, st>>>(A);
-  }
-  return cudaGetLastError();
+  return A.tc_type == PC_TC_BF16 ? tc_launch_n1<1>(A, (int)grid, smem, st) : tc_launch_n1<0>(A, (int)grid, smem, st);
 }
