@@ -108,14 +108,34 @@ __global__ void k_curved_locate(LocArgs A) {
   A.slot[p] = atomicAdd(&A.cnt[k], 1);
 }
 
+// sin and cos of 2 pi X at the Gauss coordinates X = (e + s_i) h of one axis (the map
+// is the same on every axis), from the double-float coordinate.
+struct TrigArgs {
+  int ne, n1;
+  f2 h;
+  float s[16];
+  float2* trig;
+};
+
+__global__ void k_curved_trig(TrigArgs T) {
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= T.ne * T.n1) return;
+  const f2 xg = df_mul(two_sum((float)(t / T.n1), T.s[t % T.n1]), T.h);
+  float sn, cs;
+  sincospif(2.0f * xg.h, &sn, &cs);
+  T.trig[t] = make_float2(sn, cs);
+}
+
 struct CPrepArgs {
   int64_t n;
-  int nc, ne, n1, rho;
-  float amp, rcl, rc2f, c2l, hf;
+  int nc, ne, n1, rho, win;
+  float amp, rcl, rc2f, c2l, inv_h;
   f2 inv_nc, h;
   double hd, rc;
   float s[16], wq[16];
   double eta[16];
+  float S[64];  // window coordinates: S[w] = (w / n1 + s[w % n1]) h
+  const float2* trig;
   const int32_t* perm;
   const int32_t* cell;
   const float* o;
@@ -141,82 +161,126 @@ __device__ __forceinline__ bool inside_cut(float r2, float rc2f, const int c3[3]
   return d2s <= rc * rc;
 }
 
+// First window node at or after window coordinate v, less one (clamped to [0, win]):
+// a conservative start of the nodes within reach of v.
+__device__ __forceinline__ int win_from(float v, float inv_h, const float* s, int n1, int win) {
+  const float u = v * inv_h;
+  const int eo = (int)floorf(u);
+  if (eo < 0) return 0;
+  if (eo * n1 >= win) return win;
+  const float t = u - (float)eo;
+  int i = 0;
+  while (i < n1 && s[i] < t) ++i;
+  const int w = eo * n1 + i - 1;
+  return w < 0 ? 0 : (w > win ? win : w);
+}
+
+// Last window node at or before v, plus one, as an exclusive end (clamped to [0, win]).
+__device__ __forceinline__ int win_to(float v, float inv_h, const float* s, int n1, int win) {
+  const float u = v * inv_h;
+  const int eo = (int)floorf(u);
+  if (eo < 0) return 0;
+  if (eo * n1 >= win) return win;
+  const float t = u - (float)eo;
+  int i = 0;
+  while (i < n1 && s[i] <= t) ++i;
+  const int w = eo * n1 + i + 1;
+  return w > win ? win : w;
+}
+
+// Z_p over the nodes of the physical ball, particle per thread (sorted order). The
+// window of (2 rho + 1) n1 nodes per axis around the particle's logical element is
+// walked plane by plane, row by row and node by node over the index ranges that the
+// logical ball of radius rcl can reach (|Phi(a) - Phi(b)| >= (1 - L)|a - b|; the
+// ranges are widened by a node on each side and every node is decided by its
+// physical distance). Node to particle offsets: the window offset of the node from
+// the particle's logical position, plus the particle's logical-minus-physical offset
+// delta, plus the map's perturbation at the node; sines and cosines come from the
+// per-axis table.
 __global__ void __launch_bounds__(128) k_curved_prep(CPrepArgs A) {
+  // window coordinates and weights in shared memory: lanes index them at different
+  // nodes, which kernel-parameter reads would serialise
+  __shared__ float S[64], wq[16];
+  if (threadIdx.x < 64) S[threadIdx.x] = A.S[threadIdx.x];
+  if (threadIdx.x < 16) wq[threadIdx.x] = A.wq[threadIdx.x];
+  __syncthreads();
   const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   const int64_t n = A.n;
   if (k >= n) return;
   const int64_t p = A.perm[k];
-  const int nc = A.nc, ne = A.ne, n1 = A.n1;
+  const int nc = A.nc, ne = A.ne, n1 = A.n1, rho = A.rho, win = A.win, nn = ne * n1;
   const int32_t cl = A.cell[p] < 0 ? 0 : A.cell[p];
   const int c3[3] = {cl % nc, (cl / nc) % nc, cl / (nc * nc)};
-  float o3[3], xip[3];
+  float o3[3], cw[3], dl[3];
   f2 x[3];
-  int ea[3];
+  int g0[3];
   for (int a = 0; a < 3; ++a) {
     o3[a] = A.o[a * n + p];
     x[a] = pos_df(c3[a], o3[a], A.inv_nc);
-    xip[a] = A.xi[a * n + p];
-    int e = (int)(xip[a] * (float)ne);
-    ea[a] = e < 0 ? 0 : (e >= ne ? ne - 1 : e);
+    const float xia = A.xi[a * n + p];
+    int e = (int)(xia * (float)ne);
+    e = e < 0 ? 0 : (e >= ne ? ne - 1 : e);
+    // the particle in window coordinates: xi - (e - rho) h, and delta = xi - x
+    const f2 base = df_mul(two_sum((float)(e - rho), 0.0f), A.h);
+    cw[a] = (xia - base.h) - base.l;
+    dl[a] = minimgf(xia - x[a].h) - x[a].l;
+    g0[a] = (e - rho) * n1;  // global node index of window node 0 (may wrap)
   }
-  // The window's nodes, plane by plane and row by row: a node whose logical distance
-  // to xi_p exceeds rcl is outside the physical ball (|Phi(a) - Phi(b)| >= (1 - L)|a - b|),
-  // so whole planes and rows are skipped before any trigonometry; the sines of a
-  // plane's z and a row's y are taken once.
-  const int win = (2 * A.rho + 1) * n1;
-  const float g = 6.283185307179586f * A.amp;
-  const float rcl2 = A.rcl * A.rcl;
+  const float amp = A.amp, g = 6.283185307179586f * amp, rcl = A.rcl, rcl2 = rcl * rcl;
+  const float cut_hi = A.rc2f * 1.0002f;
   float Z = 0.0f;
-  for (int wz = 0; wz < win; ++wz) {
-    const int oz = wz / n1 - A.rho, iz = wz % n1;
-    const f2 xgz = df_mul(two_sum((float)(ea[2] + oz), A.s[iz]), A.h);
-    const float lz = xgz.h - xip[2];
-    if (fabsf(lz) > A.rcl) continue;
-    float snz, csz;
-    sincospif(2.0f * xgz.h, &snz, &csz);
-    const f2 ddz = df_add(xgz, df_neg(x[2]));
-    const float distz = ddz.h + ddz.l;
-    for (int wy = 0; wy < win; ++wy) {
-      const int oy = wy / n1 - A.rho, iy = wy % n1;
-      const f2 xgy = df_mul(two_sum((float)(ea[1] + oy), A.s[iy]), A.h);
-      const float ly = xgy.h - xip[1];
-      const float lyz = ly * ly + lz * lz;
-      if (lyz > rcl2) continue;
-      float sny, csy;
-      sincospif(2.0f * xgy.h, &sny, &csy);
-      const f2 ddy = df_add(xgy, df_neg(x[1]));
-      const float disty = ddy.h + ddy.l;
-      const float wyz = A.wq[iy] * A.wq[iz];
-      const float dxp = A.amp * sny * snz;  // x-perturbation of the row
-      for (int wx = 0; wx < win; ++wx) {
-        const int ox = wx / n1 - A.rho, ix = wx % n1;
-        const f2 xgx = df_mul(two_sum((float)(ea[0] + ox), A.s[ix]), A.h);
-        const float lx = xgx.h - xip[0];
-        if (lx * lx + lyz > rcl2) continue;
-        float snx, csx;
-        sincospif(2.0f * xgx.h, &snx, &csx);
-        const f2 ddx = df_add(xgx, df_neg(x[0]));
-        const float dx = minimgf((ddx.h + ddx.l) + dxp);
-        const float dy = minimgf(disty + A.amp * snz * snx);
-        const float dz = minimgf(distz + A.amp * snx * sny);
+  const int z0 = win_from(cw[2] - rcl, A.inv_h, A.s, n1, win), z1 = win_to(cw[2] + rcl, A.inv_h, A.s, n1, win);
+  for (int wz = z0; wz < z1; ++wz) {
+    const float lz = S[wz] - cw[2];
+    const float ry2 = rcl2 - lz * lz;
+    if (ry2 < 0.0f) continue;
+    int gz = g0[2] + wz;
+    gz = gz < 0 ? gz + nn : (gz >= nn ? gz - nn : gz);
+    const float2 tz = A.trig[gz];
+    const float dz0 = lz + dl[2];
+    const float ry = sqrtf(ry2);
+    const int y0 = win_from(cw[1] - ry, A.inv_h, A.s, n1, win), y1 = win_to(cw[1] + ry, A.inv_h, A.s, n1, win);
+    for (int wy = y0; wy < y1; ++wy) {
+      const float ly = S[wy] - cw[1];
+      const float rx2 = ry2 - ly * ly;
+      if (rx2 < 0.0f) continue;
+      int gy = g0[1] + wy;
+      gy = gy < 0 ? gy + nn : (gy >= nn ? gy - nn : gy);
+      const float2 ty = A.trig[gy];
+      const float dy0 = ly + dl[1];
+      const float rx = sqrtf(rx2);
+      // row constants: perturbations and Jacobian entries that do not involve x
+      const float pxr = amp * ty.x * tz.x;
+      const float az = amp * tz.x, ay = amp * ty.x;
+      const float a01 = g * ty.y * tz.x, a02 = g * ty.x * tz.y;
+      const float gsz = g * tz.x, gcz = g * tz.y, gsy = g * ty.x, gcy = g * ty.y;
+      const float wyz = wq[wy % n1] * wq[wz % n1];
+      const int x0 = win_from(cw[0] - rx, A.inv_h, A.s, n1, win), x1 = win_to(cw[0] + rx, A.inv_h, A.s, n1, win);
+      for (int wx = x0; wx < x1; ++wx) {
+        const float lx = S[wx] - cw[0];
+        int gx = g0[0] + wx;
+        gx = gx < 0 ? gx + nn : (gx >= nn ? gx - nn : gx);
+        const float2 tx = A.trig[gx];
+        const float dx = (lx + dl[0]) + pxr;
+        const float dy = dy0 + az * tx.x;
+        const float dz = dz0 + ay * tx.x;
         const float r2 = dx * dx + dy * dy + dz * dz;
-        if (r2 > A.rc2f * 1.0002f) continue;
+        if (r2 > cut_hi) continue;
         if (r2 >= A.rc2f * 0.9998f) {
-          const double xig[3] = {((double)wrapi(ea[0] + ox, ne) + 0.5 * (A.eta[ix] + 1.0)) * A.hd,
-                                 ((double)wrapi(ea[1] + oy, ne) + 0.5 * (A.eta[iy] + 1.0)) * A.hd,
-                                 ((double)wrapi(ea[2] + oz, ne) + 0.5 * (A.eta[iz] + 1.0)) * A.hd};
-          if (!inside_cut(r2, A.rc2f, c3, o3, nc, xig, A.amp, A.rc)) continue;
+          const double xig[3] = {((double)(gx / n1) + 0.5 * (A.eta[gx % n1] + 1.0)) * A.hd,
+                                 ((double)(gy / n1) + 0.5 * (A.eta[gy % n1] + 1.0)) * A.hd,
+                                 ((double)(gz / n1) + 0.5 * (A.eta[gz % n1] + 1.0)) * A.hd};
+          if (!inside_cut(r2, A.rc2f, c3, o3, nc, xig, amp, A.rc)) continue;
         }
-        const float a01 = g * csy * snz, a02 = g * sny * csz;
-        const float a10 = g * csx * snz, a12 = g * snx * csz;
-        const float a20 = g * csx * sny, a21 = g * snx * csy;
+        const float a10 = gsz * tx.y, a12 = gcz * tx.x;
+        const float a20 = gsy * tx.y, a21 = gcy * tx.x;
         const float det = 1.0f * (1.0f - a12 * a21) - a01 * (a10 - a12 * a20) + a02 * (a10 * a21 - a20);
-        const float W = A.wq[ix] * wyz * det;
+        const float W = wq[wx % n1] * wyz * det;
         Z += W * exp2f(-r2 * A.c2l);
       }
     }
   }
-  const float hh = 0.5f * A.hf;
+  const float hh = 0.5f * A.h.h;
   Z *= hh * hh * hh;
   const float iz = Z > 0.0f ? 1.0f / Z : 0.0f;
   float4* rp = A.rec + 3 * k;
@@ -233,6 +297,7 @@ struct CDepArgs {
   double hd, rc;
   float s[16];
   double eta[16];
+  const float2* trig;
   const int32_t* start;
   const int32_t* perm;  // for the FP64 edge decisions (stored cell + offset)
   const int32_t* cell;
@@ -241,96 +306,134 @@ struct CDepArgs {
   float* field;
 };
 
-// One CTA per element, one thread per node. Particles of the neighbouring logical
-// elements are staged in batches (one per thread) with a bounding-box test; every
-// node then adds q_c K / Z of the staged particles that pass.
+// One CTA per element, one thread per node. Node positions relative to the element's
+// logical corner E: (s_i h) + the map's perturbation. The particles of the
+// neighbouring logical elements are staged in batches (one per thread) as their
+// positions relative to E (double-float difference, minimum image) with a bounding-box
+// test; every node then adds q_c K / Z of the staged particles that pass.
 __global__ void k_curved_deposit(CDepArgs A) {
   extern __shared__ float4 sm4[];
   const int nodes = blockDim.x;  // n1^3
-  float4* st = sm4;                                      // [nodes][3]
-  int* keep = (int*)(sm4 + 3 * nodes);                   // [nodes]: staged particle index + 1, or 0
+  float4* st = sm4;                                      // [nodes][2]: (relative x, 1/Z), q
+  int* keep = (int*)(sm4 + 2 * nodes);                   // [nodes]: staged particle index + 1, or 0
   int* clist = keep + nodes;                             // [nodes]: compacted positions of the kept ones
   __shared__ float bbox[6];
   __shared__ int pre[126], rbeg[126];
   __shared__ int wcnt[32];
-  const int t = threadIdx.x;
+  __shared__ float red[6][32];
+  const int t = threadIdx.x, lane = t & 31, wp = t >> 5, nwarps = (nodes + 31) / 32;
   const int n1 = A.n1, ne = A.ne, rho = A.rho, span = 2 * rho + 1, nrange = span * span * span;
   const int e = blockIdx.x;
   const int ex = e % ne, ey = (e / ne) % ne, ez = e / (ne * ne);
   const int i = t % n1, j = (t / n1) % n1, k = t / (n1 * n1);
   const int el[3] = {ex, ey, ez}, li[3] = {i, j, k};
-  f2 X[3];
   float sn[3];
   double xig[3];
+  f2 E[3];
   for (int a = 0; a < 3; ++a) {
-    const f2 xg = df_mul(two_sum((float)el[a], A.s[li[a]]), A.h);
-    float cs;
-    sincospif(2.0f * xg.h, &sn[a], &cs);
-    X[a] = xg;
+    sn[a] = A.trig[el[a] * n1 + li[a]].x;
     xig[a] = ((double)el[a] + 0.5 * (A.eta[li[a]] + 1.0)) * A.hd;
+    E[a] = df_mul(two_sum((float)el[a], 0.0f), A.h);
   }
-  const float pert[3] = {A.amp * sn[1] * sn[2], A.amp * sn[2] * sn[0], A.amp * sn[0] * sn[1]};
-  // bounding box of the element's physical nodes
-  __shared__ float coords[3][1024];
-  for (int a = 0; a < 3; ++a) coords[a][t] = X[a].h + pert[a];
+  const float amp = A.amp;
+  const float X[3] = {A.s[i] * A.h.h + amp * sn[1] * sn[2], A.s[j] * A.h.h + amp * sn[2] * sn[0],
+                      A.s[k] * A.h.h + amp * sn[0] * sn[1]};
+  // bounding box of the element's relative node positions
+  {
+    const unsigned wmask = nodes - 32 * wp >= 32 ? 0xffffffffu : ((1u << (nodes - 32 * wp)) - 1u);
+    float lo[3] = {X[0], X[1], X[2]}, hi[3] = {X[0], X[1], X[2]};
+    for (int o = 16; o > 0; o >>= 1)
+      for (int a = 0; a < 3; ++a) {
+        const int src = lane + o;
+        const float l2 = __shfl_down_sync(wmask, lo[a], o), h2 = __shfl_down_sync(wmask, hi[a], o);
+        if (src < 32 && ((wmask >> src) & 1u)) {
+          lo[a] = fminf(lo[a], l2);
+          hi[a] = fmaxf(hi[a], h2);
+        }
+      }
+    if (lane == 0)
+      for (int a = 0; a < 3; ++a) {
+        red[a][wp] = lo[a];
+        red[3 + a][wp] = hi[a];
+      }
+  }
+  // neighbour ranges and their prefix sum (first warp)
+  if (wp == 0) {
+    int total = 0;
+    for (int r0 = 0; r0 < nrange; r0 += 32) {
+      const int r = r0 + lane;
+      int cnt = 0;
+      if (r < nrange) {
+        const int dx = r % span - rho, dy = (r / span) % span - rho, dz = r / (span * span) - rho;
+        const int nb = (wrapi(ez + dz, ne) * ne + wrapi(ey + dy, ne)) * ne + wrapi(ex + dx, ne);
+        const int b0 = A.start[nb];
+        cnt = A.start[nb + 1] - b0;
+        rbeg[r] = b0;
+      }
+      const unsigned m = __ballot_sync(0xffffffffu, r < nrange);
+      int x = cnt;
+      for (int o = 1; o < 32; o <<= 1) {
+        const int y = __shfl_up_sync(0xffffffffu, x, o);
+        if (lane >= o) x += y;
+      }
+      if (r < nrange) pre[r + 1] = total + x;
+      total += __shfl_sync(0xffffffffu, x, 31);
+      (void)m;
+    }
+    if (lane == 0) pre[0] = 0;
+  }
   __syncthreads();
-  if (t == 0) {
+  if (t == 0)
     for (int a = 0; a < 3; ++a) {
-      float lo = 1e30f, hi = -1e30f;
-      for (int g = 0; g < nodes; ++g) {
-        lo = fminf(lo, coords[a][g]);
-        hi = fmaxf(hi, coords[a][g]);
+      float lo = red[a][0], hi = red[3 + a][0];
+      for (int w2 = 1; w2 < nwarps; ++w2) {
+        lo = fminf(lo, red[a][w2]);
+        hi = fmaxf(hi, red[3 + a][w2]);
       }
       bbox[a] = lo;
       bbox[3 + a] = hi;
     }
-    int s = 0;
-    for (int r = 0; r < nrange; ++r) {
-      const int dx = r % span - rho, dy = (r / span) % span - rho, dz = r / (span * span) - rho;
-      const int nb = (wrapi(ez + dz, ne) * ne + wrapi(ey + dy, ne)) * ne + wrapi(ex + dx, ne);
-      const int b0 = A.start[nb], b1 = A.start[nb + 1];
-      pre[r] = s;
-      rbeg[r] = b0;
-      s += b1 - b0;
-    }
-    pre[nrange] = s;
-  }
   __syncthreads();
   const float cen[3] = {0.5f * (bbox[0] + bbox[3]), 0.5f * (bbox[1] + bbox[4]), 0.5f * (bbox[2] + bbox[5])};
   const float hw[3] = {0.5f * (bbox[3] - bbox[0]), 0.5f * (bbox[4] - bbox[1]), 0.5f * (bbox[5] - bbox[2])};
   const float cut = A.rcf * 1.0002f + 1e-6f;
+  const float cut_hi = A.rc2f * 1.0002f, cut_lo = A.rc2f * 0.9998f;
   const int total = pre[nrange];
+  int top = 1;
+  while (2 * top <= nrange) top *= 2;
   float acc[4] = {0.0f, 0.0f, 0.0f, 0.0f};
   for (int base = 0; base < total; base += nodes) {
     const int idx = base + t;
     int kp = 0;
     if (idx < total) {
       int r = 0;
-      while (pre[r + 1] <= idx) ++r;
+      for (int stp = top; stp > 0; stp >>= 1)
+        if (r + stp < nrange && pre[r + stp] <= idx) r += stp;
       const int jj = rbeg[r] + (idx - pre[r]);
       const float4 r0 = A.rec[3 * (int64_t)jj], r1 = A.rec[3 * (int64_t)jj + 1], r2 = A.rec[3 * (int64_t)jj + 2];
-      st[3 * t] = r0;
-      st[3 * t + 1] = r1;
-      st[3 * t + 2] = r2;
-      const float xp[3] = {r0.x, r0.z, r1.x};
+      const f2 xp[3] = {{r0.x, r0.y}, {r0.z, r0.w}, {r1.x, r1.y}};
+      float rel[3];
       float d2 = 0.0f;
       for (int a = 0; a < 3; ++a) {
-        const float ex_ = fmaxf(fabsf(minimgf(xp[a] - cen[a])) - hw[a], 0.0f);
+        const f2 dd = df_add(xp[a], df_neg(E[a]));
+        rel[a] = minimgf(dd.h + dd.l);
+        const float ex_ = fmaxf(fabsf(rel[a] - cen[a]) - hw[a], 0.0f);
         d2 += ex_ * ex_;
       }
+      st[2 * t] = make_float4(rel[0], rel[1], rel[2], r1.z);
+      st[2 * t + 1] = make_float4(r1.w, r2.x, r2.y, r2.z);
       kp = d2 <= cut * cut ? jj + 1 : 0;
     }
     keep[t] = kp;
     // compact the staged particles that pass the box test (order kept); the mask holds
     // the lanes this warp has (n1^3 need not be a multiple of 32)
-    const int lane = t & 31, wp = t >> 5;
     const int wl = nodes - 32 * wp;
     const unsigned wmask = wl >= 32 ? 0xffffffffu : ((1u << wl) - 1u);
     const unsigned bal = __ballot_sync(wmask, kp != 0);
     if (lane == 0) wcnt[wp] = __popc(bal);
     __syncthreads();
     int woff = 0, nkept = 0;
-    for (int w2 = 0; w2 < (nodes + 31) / 32; ++w2) {
+    for (int w2 = 0; w2 < nwarps; ++w2) {
       if (w2 < wp) woff += wcnt[w2];
       nkept += wcnt[w2];
     }
@@ -338,29 +441,24 @@ __global__ void k_curved_deposit(CDepArgs A) {
     __syncthreads();
     for (int u = 0; u < nkept; ++u) {
       const int q = clist[u];
-      const int kk = keep[q];
-      const float4 r0 = st[3 * q], r1 = st[3 * q + 1], r2 = st[3 * q + 2];
-      const f2 xp[3] = {{r0.x, r0.y}, {r0.z, r0.w}, {r1.x, r1.y}};
-      float d[3];
-      for (int a = 0; a < 3; ++a) {
-        const f2 dd = df_add(X[a], df_neg(xp[a]));
-        d[a] = minimgf((dd.h + dd.l) + pert[a]);
-      }
-      const float r2s = d[0] * d[0] + d[1] * d[1] + d[2] * d[2];
-      if (r2s > A.rc2f * 1.0002f) continue;
-      if (r2s >= A.rc2f * 0.9998f) {
-        const int64_t pj = A.perm[kk - 1];
+      const float4 s0 = st[2 * q];
+      const float d0 = X[0] - s0.x, d1 = X[1] - s0.y, d2 = X[2] - s0.z;
+      const float r2s = d0 * d0 + d1 * d1 + d2 * d2;
+      if (r2s > cut_hi) continue;
+      if (r2s >= cut_lo) {
+        const int64_t pj = A.perm[keep[q] - 1];
         const int32_t cl = A.cell[pj] < 0 ? 0 : A.cell[pj];
         const int nc = A.nc;
         const int c3[3] = {cl % nc, (cl / nc) % nc, cl / (nc * nc)};
         const float o3[3] = {A.o[pj], A.o[A.n + pj], A.o[2 * A.n + pj]};
-        if (!inside_cut(r2s, A.rc2f, c3, o3, nc, xig, A.amp, A.rc)) continue;
+        if (!inside_cut(r2s, A.rc2f, c3, o3, nc, xig, amp, A.rc)) continue;
       }
-      const float K = exp2f(-r2s * A.c2l) * r1.z;
-      acc[0] += r1.w * K;
-      acc[1] += r2.x * K;
-      acc[2] += r2.y * K;
-      acc[3] += r2.z * K;
+      const float4 s1 = st[2 * q + 1];
+      const float K = exp2f(-r2s * A.c2l) * s0.w;
+      acc[0] += s1.x * K;
+      acc[1] += s1.y * K;
+      acc[2] += s1.z * K;
+      acc[3] += s1.w * K;
     }
     __syncthreads();
   }
@@ -379,10 +477,25 @@ pc_status pc_project_curved_f32_impl(pc_ctx* ctx, const pc_particles_f32* p, flo
   const f2 inv_nc = {(float)inv, (float)(inv - (double)(float)inv)};
   const f2 hdf = {(float)ctx->h, (float)(ctx->h - (double)(float)ctx->h)};
   const double rc = ctx->cfg.cutoff_sigmas * ctx->cfg.sigma;
+  float sgl[16];
+  for (int i = 0; i < ctx->n1; ++i) sgl[i] = (float)(0.5 * (ctx->eta[i] + 1.0));
   cudaError_t e = cudaMemsetAsync(ctx->cnt, 0, sizeof(int32_t) * (size_t)nel, st);
   if (e != cudaSuccess) goto fail;
   {
     const int tb = pc_phase_begin(ctx, PC_PH_PBIN);
+    {
+      // the per-axis sine and cosine table at the Gauss coordinates
+      TrigArgs T;
+      memset(&T, 0, sizeof(T));
+      T.ne = ne;
+      T.n1 = ctx->n1;
+      T.h = hdf;
+      memcpy(T.s, sgl, sizeof(sgl));
+      T.trig = ctx->trig;
+      const int nt = ne * ctx->n1;
+      k_curved_trig<<<(nt + 127) / 128, 128, 0, st>>>(T);
+      ctx->launches += 1;
+    }
     if (n > 0) {
       LocArgs L;
       L.n = n;
@@ -413,22 +526,25 @@ pc_status pc_project_curved_f32_impl(pc_ctx* ctx, const pc_particles_f32* p, flo
     P.ne = ne;
     P.n1 = ctx->n1;
     P.rho = ctx->rho;
+    P.win = ctx->win;
     P.amp = (float)ctx->cfg.amp;
     const double lip = 6.283185307179586 * 1.7320508075688772 * ctx->cfg.amp;
     P.rcl = (float)(rc / (1.0 - lip) * 1.001 + 1e-6);
     P.rc2f = (float)(rc * rc);
     P.c2l = (float)(1.4426950408889634 / (2.0 * ctx->cfg.sigma * ctx->cfg.sigma));
-    P.hf = (float)ctx->h;
+    P.inv_h = (float)ne;
     P.inv_nc = inv_nc;
     P.h = hdf;
     P.hd = ctx->h;
     P.rc = rc;
     for (int i = 0; i < ctx->n1; ++i) {
-      const double si = 0.5 * (ctx->eta[i] + 1.0);
-      P.s[i] = (float)si;
+      P.s[i] = sgl[i];
       P.wq[i] = (float)ctx->w[i];
       P.eta[i] = ctx->eta[i];
     }
+    for (int w = 0; w < ctx->win; ++w)
+      P.S[w] = (float)(((double)(w / ctx->n1) + 0.5 * (ctx->eta[w % ctx->n1] + 1.0)) * ctx->h);
+    P.trig = ctx->trig;
     P.perm = ctx->perm;
     P.cell = p->cell;
     P.o = p->o;
@@ -456,9 +572,10 @@ pc_status pc_project_curved_f32_impl(pc_ctx* ctx, const pc_particles_f32* p, flo
     D.hd = ctx->h;
     D.rc = rc;
     for (int i = 0; i < ctx->n1; ++i) {
-      D.s[i] = (float)(0.5 * (ctx->eta[i] + 1.0));
+      D.s[i] = sgl[i];
       D.eta[i] = ctx->eta[i];
     }
+    D.trig = ctx->trig;
     D.start = ctx->start;
     D.perm = ctx->perm;
     D.cell = p->cell;
@@ -466,7 +583,7 @@ pc_status pc_project_curved_f32_impl(pc_ctx* ctx, const pc_particles_f32* p, flo
     D.rec = (const float4*)ctx->fac;
     D.field = field;
     const int nodes = ctx->n1 * ctx->n1 * ctx->n1;
-    const size_t smem = (size_t)nodes * (3 * sizeof(float4) + 2 * sizeof(int));
+    const size_t smem = (size_t)nodes * (2 * sizeof(float4) + 2 * sizeof(int));
     const int td = pc_phase_begin(ctx, PC_PH_DEPOSIT);
     k_curved_deposit<<<(unsigned)nel, nodes, smem, st>>>(D);
     ctx->launches += 1;

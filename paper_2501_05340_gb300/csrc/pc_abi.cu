@@ -82,7 +82,7 @@ pc_status fail(pc_ctx* ctx, pc_status s, const char* msg) {
 void free_all(pc_ctx* c) {
   void* ptrs[] = {c->cnt, c->start, c->blocksums, c->key, c->slot, c->perm, c->sx, c->sv, c->sr,
                   c->sid, c->sxf, c->svf, c->srf, c->cand_j, c->cand_t, c->ncand, c->best, c->partner,
-                  c->work, c->tcoll, c->pair_lo, c->pair_hi, c->pair_t, c->counters, c->fac, c->sq, c->scell, c->corner, c->reach, c->fxmax};
+                  c->work, c->tcoll, c->pair_lo, c->pair_hi, c->pair_t, c->counters, c->fac, c->sq, c->scell, c->corner, c->reach, c->fxmax, c->trig};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   if (c->h_counters) cudaFreeHost(c->h_counters);
@@ -184,6 +184,7 @@ pc_status pc_init(pc_ctx** out, const pc_config* cfg) {
   chk(dalloc(&ctx->reach, n));
   chk(dalloc(&ctx->fxmax, 8));
   chk(dalloc(&ctx->corner, 36 * nel));
+  chk(dalloc(&ctx->trig, (int64_t)c.ne * ctx->n1));
   if (e == cudaSuccess) e = cudaMallocHost((void**)&ctx->h_counters, sizeof(unsigned long long) * CNT_N);
   if (e == cudaSuccess) e = cudaMemset(ctx->counters, 0, sizeof(unsigned long long) * CNT_N);
   if (e != cudaSuccess) {
