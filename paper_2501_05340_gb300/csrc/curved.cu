@@ -36,6 +36,14 @@ __device__ __forceinline__ double minimg(double d) {
   return d;
 }
 
+// 2^x for the kernel's arguments (-7 < x <= 0 inside the cutoff): the hardware
+// approximation, the same in the normalisation and in the deposit.
+__device__ __forceinline__ float ex2f(float x) {
+  float y;
+  asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+  return y;
+}
+
 __device__ __forceinline__ void raise_status(unsigned long long* counters, int code) {
   atomicMax(&counters[CNT_STATUS], (unsigned long long)code);
 }
@@ -109,18 +117,20 @@ __global__ void k_curved_locate(LocArgs A) {
 }
 
 // sin and cos of 2 pi X at the Gauss coordinates X = (e + s_i) h of one axis (the map
-// is the same on every axis), from the double-float coordinate.
+// is the same on every axis), from the double-float coordinate; rho elements of
+// periodic images on either side, so that window nodes index it without wrapping.
 struct TrigArgs {
-  int ne, n1;
+  int ne, n1, rho;
   f2 h;
   float s[16];
-  float2* trig;
+  float2* trig;  // [(ne + 2 rho) n1]: entry t holds global node index t - rho n1, wrapped
 };
 
 __global__ void k_curved_trig(TrigArgs T) {
   const int t = blockIdx.x * blockDim.x + threadIdx.x;
-  if (t >= T.ne * T.n1) return;
-  const f2 xg = df_mul(two_sum((float)(t / T.n1), T.s[t % T.n1]), T.h);
+  if (t >= (T.ne + 2 * T.rho) * T.n1) return;
+  const int e = wrapi(t / T.n1 - T.rho, T.ne);
+  const f2 xg = df_mul(two_sum((float)e, T.s[t % T.n1]), T.h);
   float sn, cs;
   sincospif(2.0f * xg.h, &sn, &cs);
   T.trig[t] = make_float2(sn, cs);
@@ -135,7 +145,7 @@ struct CPrepArgs {
   float s[16], wq[16];
   double eta[16];
   float S[64];  // window coordinates: S[w] = (w / n1 + s[w % n1]) h
-  const float2* trig;
+  const float2* trig;  // per-axis table, entry g + rho n1 for global node index g
   const int32_t* perm;
   const int32_t* cell;
   const float* o;
@@ -200,15 +210,17 @@ __device__ __forceinline__ int win_to(float v, float inv_h, const float* s, int 
 __global__ void __launch_bounds__(128) k_curved_prep(CPrepArgs A) {
   // window coordinates and weights in shared memory: lanes index them at different
   // nodes, which kernel-parameter reads would serialise
-  __shared__ float S[64], wq[16];
-  if (threadIdx.x < 64) S[threadIdx.x] = A.S[threadIdx.x];
-  if (threadIdx.x < 16) wq[threadIdx.x] = A.wq[threadIdx.x];
+  __shared__ float S[64], WQ[64];
+  if (threadIdx.x < 64) {
+    S[threadIdx.x] = A.S[threadIdx.x];
+    WQ[threadIdx.x] = A.wq[threadIdx.x % A.n1];
+  }
   __syncthreads();
   const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   const int64_t n = A.n;
   if (k >= n) return;
   const int64_t p = A.perm[k];
-  const int nc = A.nc, ne = A.ne, n1 = A.n1, rho = A.rho, win = A.win, nn = ne * n1;
+  const int nc = A.nc, ne = A.ne, n1 = A.n1, rho = A.rho, win = A.win;
   const int32_t cl = A.cell[p] < 0 ? 0 : A.cell[p];
   const int c3[3] = {cl % nc, (cl / nc) % nc, cl / (nc * nc)};
   float o3[3], cw[3], dl[3];
@@ -224,7 +236,7 @@ __global__ void __launch_bounds__(128) k_curved_prep(CPrepArgs A) {
     const f2 base = df_mul(two_sum((float)(e - rho), 0.0f), A.h);
     cw[a] = (xia - base.h) - base.l;
     dl[a] = minimgf(xia - x[a].h) - x[a].l;
-    g0[a] = (e - rho) * n1;  // global node index of window node 0 (may wrap)
+    g0[a] = e * n1;  // table entry of window node 0: global node index (e - rho) n1, plus rho n1
   }
   const float amp = A.amp, g = 6.283185307179586f * amp, rcl = A.rcl, rcl2 = rcl * rcl;
   const float cut_hi = A.rc2f * 1.0002f;
@@ -234,8 +246,7 @@ __global__ void __launch_bounds__(128) k_curved_prep(CPrepArgs A) {
     const float lz = S[wz] - cw[2];
     const float ry2 = rcl2 - lz * lz;
     if (ry2 < 0.0f) continue;
-    int gz = g0[2] + wz;
-    gz = gz < 0 ? gz + nn : (gz >= nn ? gz - nn : gz);
+    const int gz = g0[2] + wz;
     const float2 tz = A.trig[gz];
     const float dz0 = lz + dl[2];
     const float ry = sqrtf(ry2);
@@ -244,8 +255,7 @@ __global__ void __launch_bounds__(128) k_curved_prep(CPrepArgs A) {
       const float ly = S[wy] - cw[1];
       const float rx2 = ry2 - ly * ly;
       if (rx2 < 0.0f) continue;
-      int gy = g0[1] + wy;
-      gy = gy < 0 ? gy + nn : (gy >= nn ? gy - nn : gy);
+      const int gy = g0[1] + wy;
       const float2 ty = A.trig[gy];
       const float dy0 = ly + dl[1];
       const float rx = sqrtf(rx2);
@@ -254,12 +264,11 @@ __global__ void __launch_bounds__(128) k_curved_prep(CPrepArgs A) {
       const float az = amp * tz.x, ay = amp * ty.x;
       const float a01 = g * ty.y * tz.x, a02 = g * ty.x * tz.y;
       const float gsz = g * tz.x, gcz = g * tz.y, gsy = g * ty.x, gcy = g * ty.y;
-      const float wyz = wq[wy % n1] * wq[wz % n1];
+      const float wyz = WQ[wy] * WQ[wz];
       const int x0 = win_from(cw[0] - rx, A.inv_h, A.s, n1, win), x1 = win_to(cw[0] + rx, A.inv_h, A.s, n1, win);
       for (int wx = x0; wx < x1; ++wx) {
         const float lx = S[wx] - cw[0];
-        int gx = g0[0] + wx;
-        gx = gx < 0 ? gx + nn : (gx >= nn ? gx - nn : gx);
+        const int gx = g0[0] + wx;
         const float2 tx = A.trig[gx];
         const float dx = (lx + dl[0]) + pxr;
         const float dy = dy0 + az * tx.x;
@@ -267,16 +276,17 @@ __global__ void __launch_bounds__(128) k_curved_prep(CPrepArgs A) {
         const float r2 = dx * dx + dy * dy + dz * dz;
         if (r2 > cut_hi) continue;
         if (r2 >= A.rc2f * 0.9998f) {
-          const double xig[3] = {((double)(gx / n1) + 0.5 * (A.eta[gx % n1] + 1.0)) * A.hd,
-                                 ((double)(gy / n1) + 0.5 * (A.eta[gy % n1] + 1.0)) * A.hd,
-                                 ((double)(gz / n1) + 0.5 * (A.eta[gz % n1] + 1.0)) * A.hd};
+          const int gg[3] = {gx, gy, gz};
+          double xig[3];
+          for (int a = 0; a < 3; ++a)
+            xig[a] = ((double)wrapi(gg[a] / n1 - rho, ne) + 0.5 * (A.eta[gg[a] % n1] + 1.0)) * A.hd;
           if (!inside_cut(r2, A.rc2f, c3, o3, nc, xig, amp, A.rc)) continue;
         }
         const float a10 = gsz * tx.y, a12 = gcz * tx.x;
         const float a20 = gsy * tx.y, a21 = gcy * tx.x;
         const float det = 1.0f * (1.0f - a12 * a21) - a01 * (a10 - a12 * a20) + a02 * (a10 * a21 - a20);
-        const float W = wq[wx % n1] * wyz * det;
-        Z += W * exp2f(-r2 * A.c2l);
+        const float W = WQ[wx] * wyz * det;
+        Z += W * ex2f(-r2 * A.c2l);
       }
     }
   }
@@ -297,7 +307,7 @@ struct CDepArgs {
   double hd, rc;
   float s[16];
   double eta[16];
-  const float2* trig;
+  const float2* trig;  // per-axis table, entry g + rho n1 for global node index g
   const int32_t* start;
   const int32_t* perm;  // for the FP64 edge decisions (stored cell + offset)
   const int32_t* cell;
@@ -311,7 +321,7 @@ struct CDepArgs {
 // neighbouring logical elements are staged in batches (one per thread) as their
 // positions relative to E (double-float difference, minimum image) with a bounding-box
 // test; every node then adds q_c K / Z of the staged particles that pass.
-__global__ void k_curved_deposit(CDepArgs A) {
+__global__ void __launch_bounds__(64, 12) k_curved_deposit(CDepArgs A) {
   extern __shared__ float4 sm4[];
   const int nodes = blockDim.x;  // n1^3
   float4* st = sm4;                                      // [nodes][2]: (relative x, 1/Z), q
@@ -328,11 +338,9 @@ __global__ void k_curved_deposit(CDepArgs A) {
   const int i = t % n1, j = (t / n1) % n1, k = t / (n1 * n1);
   const int el[3] = {ex, ey, ez}, li[3] = {i, j, k};
   float sn[3];
-  double xig[3];
   f2 E[3];
   for (int a = 0; a < 3; ++a) {
-    sn[a] = A.trig[el[a] * n1 + li[a]].x;
-    xig[a] = ((double)el[a] + 0.5 * (A.eta[li[a]] + 1.0)) * A.hd;
+    sn[a] = A.trig[(el[a] + rho) * n1 + li[a]].x;
     E[a] = df_mul(two_sum((float)el[a], 0.0f), A.h);
   }
   const float amp = A.amp;
@@ -451,10 +459,12 @@ __global__ void k_curved_deposit(CDepArgs A) {
         const int nc = A.nc;
         const int c3[3] = {cl % nc, (cl / nc) % nc, cl / (nc * nc)};
         const float o3[3] = {A.o[pj], A.o[A.n + pj], A.o[2 * A.n + pj]};
+        double xig[3];
+        for (int a = 0; a < 3; ++a) xig[a] = ((double)el[a] + 0.5 * (A.eta[li[a]] + 1.0)) * A.hd;
         if (!inside_cut(r2s, A.rc2f, c3, o3, nc, xig, amp, A.rc)) continue;
       }
       const float4 s1 = st[2 * q + 1];
-      const float K = exp2f(-r2s * A.c2l) * s0.w;
+      const float K = ex2f(-r2s * A.c2l) * s0.w;
       acc[0] += s1.x * K;
       acc[1] += s1.y * K;
       acc[2] += s1.z * K;
@@ -489,10 +499,11 @@ pc_status pc_project_curved_f32_impl(pc_ctx* ctx, const pc_particles_f32* p, flo
       memset(&T, 0, sizeof(T));
       T.ne = ne;
       T.n1 = ctx->n1;
+      T.rho = ctx->rho;
       T.h = hdf;
       memcpy(T.s, sgl, sizeof(sgl));
       T.trig = ctx->trig;
-      const int nt = ne * ctx->n1;
+      const int nt = (ne + 2 * ctx->rho) * ctx->n1;
       k_curved_trig<<<(nt + 127) / 128, 128, 0, st>>>(T);
       ctx->launches += 1;
     }

@@ -184,7 +184,7 @@ pc_status pc_init(pc_ctx** out, const pc_config* cfg) {
   chk(dalloc(&ctx->reach, n));
   chk(dalloc(&ctx->fxmax, 8));
   chk(dalloc(&ctx->corner, 36 * nel));
-  chk(dalloc(&ctx->trig, (int64_t)c.ne * ctx->n1));
+  chk(dalloc(&ctx->trig, (int64_t)(c.ne + 2 * rho) * ctx->n1));
   if (e == cudaSuccess) e = cudaMallocHost((void**)&ctx->h_counters, sizeof(unsigned long long) * CNT_N);
   if (e == cudaSuccess) e = cudaMemset(ctx->counters, 0, sizeof(unsigned long long) * CNT_N);
   if (e != cudaSuccess) {

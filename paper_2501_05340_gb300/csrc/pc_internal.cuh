@@ -66,7 +66,8 @@ struct pc_ctx {
   DfExpTable exp_tab;
   int pair_policy;  // PC_PAIRS_EARLIEST or PC_PAIRS_SFC_FIRST (pc_set_pair_policy)
   double* corner;  // 36 ne^3 doubles: pc_project_idw's df32 corner sums [ne^3][8][4] and node densities [ne^3][4]
-  float2* trig;    // [ne n1]: sin and cos of 2 pi X at the Gauss coordinates X = (e + s_i) h of one axis
+  float2* trig;    // [(ne + 2 rho) n1]: sin and cos of 2 pi X at the Gauss coordinates X = (e + s_i) h of
+                   // one axis, with rho elements of periodic images either side
   // Legendre-Gauss nodes and weights (passed to the kernels as arguments)
   double eta[16], w[16];
   // per-phase timers (pc_set_timing) and the launch counter
