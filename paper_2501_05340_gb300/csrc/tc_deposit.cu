@@ -5,11 +5,13 @@
 // a dense contraction over the particles p whose support reaches the element.
 // Each factor is split into a high and a low part of the operand type (FP16 or
 // BF16) and one MMA of M = 128, N = 64, K = 16 computes all four products at once:
-//   A operand rows  0..63 : YZ_hi (scaled by 2^8), rows 64..127: YZ_lo
+//   A operand row 32 q + r: YZ_hi of jk = 16 q + r, row 32 q + 16 + r: its YZ_lo
+//     (q = 0..3, r = 0..15; YZ scaled by 2^8)
 //   B operand rows  0..31 : A_hi  (scaled by 2^4), rows 32..63 : A_lo
-// so D = [[hi hi, hi lo], [lo hi, lo lo]] accumulates in FP32 in tensor memory and
-// the element's deposit is the sum of the four quadrants (the lo*lo one is below
-// the accuracy of the others and harmless).
+// so D holds, in every tensor-memory lane quarter, the products hi hi, hi lo, lo hi
+// and lo lo of 16 rows jk, and the element's deposit is their sum (the lo*lo one is
+// below the accuracy of the others and harmless). An epilogue warp reads its own
+// quarter and adds the lo rows to the hi rows with one shuffle.
 //
 // Operands live in shared memory in the MN-major layout without swizzle: core
 // matrices of 8 particles (K) x 16 bytes (8 consecutive rows of M or N), the row
@@ -67,13 +69,15 @@ __device__ __forceinline__ void split2(float x, float y, uint32_t* hi, uint32_t*
   if (kBf16) {
     const __nv_bfloat162 h = __floats2bfloat162_rn(x, y);
     const float2 hf = __bfloat1622float2(h);
-    const __nv_bfloat162 l = __floats2bfloat162_rn(x - hf.x, y - hf.y);
+    const float2 r = __fadd2_rn(make_float2(x, y), make_float2(-hf.x, -hf.y));
+    const __nv_bfloat162 l = __floats2bfloat162_rn(r.x, r.y);
     *hi = *reinterpret_cast<const uint32_t*>(&h);
     *lo = *reinterpret_cast<const uint32_t*>(&l);
   } else {
     const __half2 h = __floats2half2_rn(x, y);
     const float2 hf = __half22float2(h);
-    const __half2 l = __floats2half2_rn(x - hf.x, y - hf.y);
+    const float2 r = __fadd2_rn(make_float2(x, y), make_float2(-hf.x, -hf.y));
+    const __half2 l = __floats2half2_rn(r.x, r.y);
     *hi = *reinterpret_cast<const uint32_t*>(&h);
     *lo = *reinterpret_cast<const uint32_t*>(&l);
   }
@@ -104,17 +108,14 @@ struct __align__(1024) TcSmem {
   uint8_t b[kWorkers][kStages][kBStage];
   float4 lrec[kWorkers][4][kList];
   int lmeta[kWorkers][kList];
-  float comb[64][33];
   int pre[kWorkers][kMaxRanges + 1];
   int rbeg[kWorkers][kMaxRanges];
   int rmeta[kWorkers][kMaxRanges];
   unsigned long long empty[kWorkers][kStages];  // tcgen05.commit: the operand stage has been read
   unsigned long long acc_full[kWorkers];        // tcgen05.commit: the element's MMAs are done
-  unsigned long long acc_empty[kWorkers];       // 2 arrivals: epilogue quarters 0 and 1
+  unsigned long long acc_empty[kWorkers];       // 4 arrivals: every epilogue quarter has read it
   unsigned long long fin[kWorkers];             // tcgen05.commit at worker exit
   unsigned long long qfull[kQ];                 // queue entry written
-  unsigned long long comb_full;                 // 2 arrivals: epilogue quarters 2 and 3
-  unsigned long long comb_empty;                // 2 arrivals: epilogue quarters 0 and 1
   int qe[kQ];
   int qb[kQ];
   int q_head;
@@ -324,38 +325,40 @@ __device__ void tc_worker(TcSmem& S, const TcDepositArgs& A, uint32_t tmem, uint
         ok = false;
         break;
       }
-      // factors of particle `lane` of the chunk
-      float fx[N1], fy[N1], fz[N1], qv[4];
+      // particle `lane` of the chunk (lanes beyond `take` build zero rows)
+      const bool live = lane < take;
+      const int pos = (head + lane) & (kList - 1);
+      const int meta = S.lmeta[k][pos];
+      const float4 r0 = S.lrec[k][0][pos], r1 = S.lrec[k][1][pos], r2 = S.lrec[k][2][pos], r3 = S.lrec[k][3][pos];
+      // the 1-D factors of axis a over the element's n1 nodes: kx scaled by 2^4, kz by 2^8
+      auto axis = [&](int a, float* f) {
+        const float t = a == 0 ? r0.x : (a == 1 ? r0.y : r0.z);
+        const float iz = a == 0 ? r0.w * 16.0f : (a == 1 ? r1.x : r1.y * 256.0f);
+        const unsigned mk = __float_as_uint(a == 0 ? r2.z : (a == 1 ? r2.w : r3.x));
+        const int wo = ((meta >> (8 * a)) & 31) - 8 * a;
+        const int sh = wo * N1;
+        const unsigned bits = live ? (sh < 32 ? (mk >> sh) : 0u) & nmask : 0u;
+        const float base = (float)(wo - rho) - t;
+        // pairs of nodes on the packed FP32x2 instructions (the same IEEE operations)
 #pragma unroll
-      for (int i = 0; i < N1; ++i) fx[i] = fy[i] = fz[i] = 0.0f;
-      qv[0] = qv[1] = qv[2] = qv[3] = 0.0f;
-      if (lane < take) {
-        const int pos = (head + lane) & (kList - 1);
-        const int meta = S.lmeta[k][pos];
-        const float4 r0 = S.lrec[k][0][pos], r1 = S.lrec[k][1][pos], r2 = S.lrec[k][2][pos], r3 = S.lrec[k][3][pos];
-        const float t3[3] = {r0.x, r0.y, r0.z};
-        const float iz[3] = {r0.w * 16.0f, r1.x, r1.y * 256.0f};
-        const unsigned mk[3] = {__float_as_uint(r2.z), __float_as_uint(r2.w), __float_as_uint(r3.x)};
-#pragma unroll
-        for (int a = 0; a < 3; ++a) {
-          const int wo = ((meta >> (8 * a)) & 31) - 8 * a;
-          const int sh = wo * N1;
-          const unsigned bits = (sh < 32 ? (mk[a] >> sh) : 0u) & nmask;
-          const float base = (float)(wo - rho) - t3[a];
-          float* f = a == 0 ? fx : (a == 1 ? fy : fz);
-#pragma unroll
-          for (int i = 0; i < N1; ++i) {
-            const float d = base + sv[i];
-            const float g = ex2(-(d * d) * c2l) * iz[a];
-            f[i] = ((bits >> i) & 1u) ? g : 0.0f;
-          }
+        for (int i = 0; i + 1 < N1; i += 2) {
+          const float2 d = __fadd2_rn(make_float2(base, base), make_float2(sv[i], sv[i + 1]));
+          const float2 x = __fmul2_rn(__fmul2_rn(d, d), make_float2(-c2l, -c2l));
+          const float2 g = __fmul2_rn(make_float2(ex2(x.x), ex2(x.y)), make_float2(iz, iz));
+          f[i] = ((bits >> i) & 1u) ? g.x : 0.0f;
+          f[i + 1] = ((bits >> (i + 1)) & 1u) ? g.y : 0.0f;
         }
-        qv[0] = r1.z;
-        qv[1] = r1.w;
-        qv[2] = r2.x;
-        qv[3] = r2.y;
-      }
-      // A rows jk = j + N1 k: YZ_hi in row groups 0..7, YZ_lo in 8..15
+        if (N1 & 1) {
+          const float d = base + sv[N1 - 1];
+          const float g = ex2((d * d) * -c2l) * iz;
+          f[N1 - 1] = ((bits >> (N1 - 1)) & 1u) ? g : 0.0f;
+        }
+      };
+      float fy[N1], fz[N1];
+      axis(1, fy);
+      axis(2, fz);
+      // A rows jk = j + N1 k in groups of 8: YZ_hi of group g in row group
+      // 4 (g / 2) + g % 2, YZ_lo in row group 4 (g / 2) + 2 + g % 2
       uint8_t* ta = S.a[k][st] + pa;
 #pragma unroll
       for (int g = 0; g < 8; ++g) {
@@ -364,15 +367,23 @@ __device__ void tc_worker(TcSmem& S, const TcDepositArgs& A, uint32_t tmem, uint
 #pragma unroll
           for (int u = 0; u < 4; ++u) {
             const int jk0 = 8 * g + 2 * u, jk1 = jk0 + 1;
-            const float v0 = jk0 < N1 * N1 ? fy[jk0 % N1] * fz[jk0 / N1] : 0.0f;
-            const float v1 = jk1 < N1 * N1 ? fy[jk1 % N1] * fz[jk1 / N1] : 0.0f;
-            split2<kBf16>(v0, v1, &hi[u], &lo[u]);
+            float2 v;
+            if (jk1 < N1 * N1 && jk0 / N1 == jk1 / N1)
+              v = __fmul2_rn(make_float2(fy[jk0 % N1], fy[jk1 % N1]), make_float2(fz[jk0 / N1], fz[jk0 / N1]));
+            else
+              v = make_float2(jk0 < N1 * N1 ? fy[jk0 % N1] * fz[jk0 / N1] : 0.0f,
+                              jk1 < N1 * N1 ? fy[jk1 % N1] * fz[jk1 / N1] : 0.0f);
+            split2<kBf16>(v.x, v.y, &hi[u], &lo[u]);
           }
-          *reinterpret_cast<uint4*>(ta + 128 * g) = make_uint4(hi[0], hi[1], hi[2], hi[3]);
-          *reinterpret_cast<uint4*>(ta + 128 * (8 + g)) = make_uint4(lo[0], lo[1], lo[2], lo[3]);
+          const int mg = 4 * (g >> 1) + (g & 1);
+          *reinterpret_cast<uint4*>(ta + 128 * mg) = make_uint4(hi[0], hi[1], hi[2], hi[3]);
+          *reinterpret_cast<uint4*>(ta + 128 * (mg + 2)) = make_uint4(lo[0], lo[1], lo[2], lo[3]);
         }
       }
       // B rows ci = c N1 + i: A_hi in row groups 0..3, A_lo in 4..7
+      float fx[N1];
+      axis(0, fx);
+      const float qv[4] = {live ? r1.z : 0.0f, live ? r1.w : 0.0f, live ? r2.x : 0.0f, live ? r2.y : 0.0f};
       uint8_t* tb = S.b[k][st] + pb;
 #pragma unroll
       for (int g = 0; g < 4; ++g) {
@@ -451,12 +462,15 @@ __device__ __forceinline__ void tmem_ld16(uint32_t taddr, float r[16]) {
 }
 
 // Epilogue warp for TMEM lane quarter q: drains the finished-element queue in
-// order until every worker has sent its exit sentinel. Accumulator columns
-// 0..31 hold the products with A_hi, 32..63 those with A_lo; lanes 0..63 the YZ_hi
-// rows, 64..127 the YZ_lo rows, combined through shared memory.
+// order until every worker has sent its exit sentinel. Its lanes 0..15 hold the
+// YZ_hi rows of jk = 16 q + lane and lanes 16..31 the YZ_lo rows of the same jk;
+// accumulator columns 0..31 the products with A_hi, 32..63 those with A_lo. The four
+// quarters work independently; each arrives on the accumulator's empty barrier as
+// soon as it has read it.
+template <int N1>
 __device__ void tc_epilogue(TcSmem& S, const TcDepositArgs& A, uint32_t tmem, int q, int lane) {
-  const int n1 = A.n1, nodes = n1 * n1 * n1;
-  unsigned seen = 0u;  // bit k: parity of the next acc_full phase of pair k
+  constexpr int NODES = N1 * N1 * N1;
+  unsigned seen = 0u;  // bit k: parity of the next acc_full phase of worker k
   int exited = 0;
   for (int t = 0; exited < kWorkers; ++t) {
     if (!mbar_wait_progress(S, &S.qfull[t % kQ], (uint32_t)((t / kQ) & 1))) {
@@ -475,53 +489,36 @@ __device__ void tc_epilogue(TcSmem& S, const TcDepositArgs& A, uint32_t tmem, in
     seen ^= 1u << k;
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
     const uint32_t tq = tmem + 64u * k + ((uint32_t)(32 * q) << 16);
-    const int jk = 32 * (q & 1) + lane;
-    const int m = t - exited;  // index of this element among the drained ones
-    if (q >= 2) {
-      // rows 64..127 (YZ lo): the two column halves summed into comb for quarters 0 and 1
-      if (m >= 1 && !mbar_wait(&S.comb_empty, (uint32_t)((m - 1) & 1), &S.failed)) {
-        if (lane == 0) fail_now(S, A.counters + CNT_STATUS);
-        return;
-      }
+    float v[32];
 #pragma unroll
-      for (int hf = 0; hf < 2; ++hf) {
-        float r0[16], r1[16];
-        tmem_ld16(tq + 16u * hf, r0);
-        tmem_ld16(tq + 32u + 16u * hf, r1);
+    for (int hf = 0; hf < 2; ++hf) {
+      float r0[16], r1[16];
+      tmem_ld16(tq + 16u * hf, r0);
+      tmem_ld16(tq + 32u + 16u * hf, r1);
 #pragma unroll
-        for (int ci = 0; ci < 16; ++ci) S.comb[jk][16 * hf + ci] = r0[ci] + r1[ci];
-      }
-      asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
-      __syncwarp();
-      if (lane == 0) mbar_arrive(&S.comb_full);
-    } else {
-      if (!mbar_wait(&S.comb_full, (uint32_t)(m & 1), &S.failed)) {
-        if (lane == 0) fail_now(S, A.counters + CNT_STATUS);
-        return;
-      }
-      float* out = A.field + (int64_t)e * 4 * nodes;
+      for (int cc = 0; cc < 16; ++cc) v[16 * hf + cc] = r0[cc] + r1[cc];
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncwarp();
+    if (lane == 0) mbar_arrive(&S.acc_empty[k]);
+    // hi rows plus lo rows
 #pragma unroll
-      for (int hf = 0; hf < 2; ++hf) {
-        float r0[16], r1[16];
-        tmem_ld16(tq + 16u * hf, r0);
-        tmem_ld16(tq + 32u + 16u * hf, r1);
-        if (jk < n1 * n1) {
+    for (int ci = 0; ci < 32; ++ci) v[ci] = v[ci] + __shfl_down_sync(kFull, v[ci], 16);
+    const int jk = 16 * q + lane;
+    if (lane < 16 && jk < N1 * N1) {
+      float* out = A.field + (int64_t)e * 4 * NODES + jk * N1;
 #pragma unroll
-          for (int cc = 0; cc < 16; ++cc) {
-            const int ci = 16 * hf + cc;
-            if (ci < 4 * n1) {
-              const int c = ci / n1, i = ci - c * n1;
-              out[c * nodes + jk * n1 + i] = ((r0[cc] + r1[cc]) + S.comb[jk][ci]) * A.scale_out;
-            }
-          }
+      for (int c = 0; c < 4; ++c) {
+        if constexpr (N1 % 4 == 0) {
+#pragma unroll
+          for (int i = 0; i < N1; i += 4)
+            *reinterpret_cast<float4*>(out + c * NODES + i) =
+                make_float4(v[c * N1 + i] * A.scale_out, v[c * N1 + i + 1] * A.scale_out,
+                            v[c * N1 + i + 2] * A.scale_out, v[c * N1 + i + 3] * A.scale_out);
+        } else {
+#pragma unroll
+          for (int i = 0; i < N1; ++i) out[c * NODES + i] = v[c * N1 + i] * A.scale_out;
         }
-      }
-      asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
-      __syncwarp();
-      if (lane == 0) {
-        mbar_arrive(&S.comb_empty);
-        // quarters 2 and 3 finished their loads before comb_full; 0 and 1 arrive here
-        mbar_arrive(&S.acc_empty[k]);
       }
     }
   }
@@ -542,13 +539,11 @@ __global__ void __launch_bounds__(kThreads, 1) k_tc_deposit(TcDepositArgs A) {
       for (int s = 0; s < kStages; ++s)
         asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&S.empty[k][s])));
       asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&S.acc_full[k])));
-      asm volatile("mbarrier.init.shared::cta.b64 [%0], 2;" ::"r"(smem_u32(&S.acc_empty[k])));
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], 4;" ::"r"(smem_u32(&S.acc_empty[k])));
       asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&S.fin[k])));
       S.progress[k] = 0;
     }
     for (int t = 0; t < kQ; ++t) asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&S.qfull[t])));
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], 2;" ::"r"(smem_u32(&S.comb_full)));
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], 2;" ::"r"(smem_u32(&S.comb_empty)));
     S.q_head = 0;
     S.failed = 0;
   }
@@ -570,7 +565,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_tc_deposit(TcDepositArgs A) {
   if (warp < kWorkers)
     tc_worker<kBf16, N1>(S, A, tmem, idesc, warp, lane);
   else
-    tc_epilogue(S, A, tmem, warp % 4, lane);  // a warp reaches the TMEM lane quarter warp % 4
+    tc_epilogue<N1>(S, A, tmem, warp % 4, lane);  // a warp reaches the TMEM lane quarter warp % 4
   __syncwarp();
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
   __syncthreads();
