@@ -1260,7 +1260,8 @@ pc_status pc_project_f32_impl(pc_ctx* ctx, const pc_particles_f32* p, float* fie
     T.scale_out = (float)(sc / 4096.0);  // operands scaled by 2^8 (YZ) and 2^4 (A)
     const int td = pc_phase_begin(ctx, PC_PH_DEPOSIT);
     int nb = 0;
-    e = pc_tc_deposit_launch(T, st, &nb);
+    e = cudaMemsetAsync(ctx->counters + CNT_ELEM, 0, sizeof(unsigned long long), st);
+    if (e == cudaSuccess) e = pc_tc_deposit_launch(T, st, &nb);
     ctx->launches += 1;
     pc_phase_end(ctx, td);
     if (e != cudaSuccess) goto fail;

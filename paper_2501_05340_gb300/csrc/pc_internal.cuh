@@ -20,6 +20,7 @@ enum {
   CNT_STATUS,  // pc_status raised on the GPU (max of codes)
   CNT_VMAX2,   // max |v|^2 as the bits of a non-negative double
   CNT_RMAX,    // max r as the bits of a non-negative double
+  CNT_ELEM,    // next element of the mixed deposit (zeroed before each launch)
   CNT_N
 };
 

@@ -215,7 +215,7 @@ __device__ __forceinline__ void queue_push(TcSmem& S, int e, int k) {
   mbar_arrive(&S.qfull[t % kQ]);  // release: the entry is visible to the waiter
 }
 
-// Worker warp k: owns elements blockIdx.x * kWorkers + k + m * gridDim.x * kWorkers.
+// Worker warp k: takes the next element from the ticket counter until none is left.
 // Per element: the (2 rho + 1)^3 neighbour cell ranges and their prefix sum, then an
 // ordered warp-level compaction of the particles whose support reaches the element
 // (per-axis reach bits) into the ring; per 32 kept particles, lane p computes the
@@ -239,7 +239,14 @@ __device__ void tc_worker(TcSmem& S, const TcDepositArgs& A, uint32_t tmem, uint
   const int pb = (lane >> 3) * (kBStage / 4) + (lane & 7) * 16;
   int chunk = 0, prog = 0, used = 0;
   bool ok = true;
-  for (int64_t e = (int64_t)blockIdx.x * kWorkers + k; ok && e < nel; e += (int64_t)gridDim.x * kWorkers) {
+  // elements in ticket order from a device counter: the elements in flight stay a
+  // contiguous stretch of the mesh, so their neighbourhoods share the L2
+  auto grab = [&]() -> int64_t {
+    unsigned long long t = 0;
+    if (lane == 0) t = atomicAdd(&A.counters[CNT_ELEM], 1ull);
+    return (int64_t)__shfl_sync(kFull, t, 0);
+  };
+  for (int64_t e = grab(); ok && e < nel; e = grab()) {
     if (__any_sync(kFull, vload(&S.failed))) break;
     const int ex = (int)(e % ne), ey = (int)((e / ne) % ne), ez = (int)(e / ((int64_t)ne * ne));
     int total = 0;
