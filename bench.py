@@ -37,8 +37,8 @@ FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12
 # ncu capture of each (dram__bytes_read.sum + dram__bytes_write.sum, summarised under profiles/);
 # None once a kernel has changed since its capture.
 DEPOSIT_KERNEL = "k_fx_deposit"
-DEPOSIT_DRAM_BYTES = 744.2e6   # k_fx_deposit<6>, dense_1m
-TC_DEPOSIT_DRAM_BYTES = 3.44e9  # k_tc_deposit<0>, mixed_16m
+DEPOSIT_DRAM_BYTES = 751.2e6   # k_fx_deposit<6>, dense_1m
+TC_DEPOSIT_DRAM_BYTES = 4.14e9  # k_tc_deposit<0, 8>, mixed_16m
 
 
 def parse():
