@@ -122,16 +122,7 @@ __global__ void k_collide_keys(int64_t n, const double* __restrict__ x, const do
     if (!(v2 < CUDART_INF)) v2 = 0.0;
     if (!(rr > 0.0 && rr < 0.25)) rr = 0.0;
   }
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) {
-    v2 = fmax(v2, __shfl_xor_sync(0xffffffffu, v2, o));
-    rr = fmax(rr, __shfl_xor_sync(0xffffffffu, rr, o));
-  }
-  if ((threadIdx.x & 31) == 0) {
-    // non-negative doubles order like their bit patterns
-    atomicMax(&counters[CNT_VMAX2], (unsigned long long)__double_as_longlong(v2));
-    atomicMax(&counters[CNT_RMAX], (unsigned long long)__double_as_longlong(rr));
-  }
+  pc_block_max2(&counters[CNT_VMAX2], v2, &counters[CNT_RMAX], rr);
 }
 
 // ------------------------------------------------------------------ gather
@@ -291,7 +282,9 @@ __global__ void __launch_bounds__(256, 3) k_search(SearchArgs A) {
   __shared__ float vmaxf_sh, rmaxf_sh;
   __shared__ SearchQueue queues[8];
   SearchQueue& Q = queues[warp];
+  __shared__ int stat_sh[3];  // candidates found, FP64 solves, largest list
   if (threadIdx.x == 0) {
+    stat_sh[0] = stat_sh[1] = stat_sh[2] = 0;
     double reach;
     s_sh = stencil_radius(A.counters, A.nc, A.dt, &reach);
     vmaxf_sh = (float)sqrt(__longlong_as_double((long long)A.counters[CNT_VMAX2])) * 1.000001f;
@@ -465,18 +458,25 @@ __global__ void __launch_bounds__(256, 3) k_search(SearchArgs A) {
     A.best[k] = cnt > 0 ? lj[0] : -1;
     if (found > A.cap) raise_status(A.counters, PC_ECAPACITY);
   }
-  // warp-aggregated statistics
-  int fsum = found, ssum = solves, fmax = found;
+  // statistics: warp sums into shared counters, one global atomic per block
+  int fsum = found, ssum = solves, fmx = found;
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) {
     fsum += __shfl_xor_sync(0xffffffffu, fsum, o);
     ssum += __shfl_xor_sync(0xffffffffu, ssum, o);
-    fmax = max(fmax, __shfl_xor_sync(0xffffffffu, fmax, o));
+    fmx = max(fmx, __shfl_xor_sync(0xffffffffu, fmx, o));
   }
   if ((threadIdx.x & 31) == 0) {
-    if (fsum) atomicAdd(&A.counters[CNT_CANDS], (unsigned long long)fsum);
-    if (ssum) atomicAdd(&A.counters[CNT_SOLVES], (unsigned long long)ssum);
-    if (fmax) atomicMax(&A.counters[CNT_MAXCAND], (unsigned long long)fmax);
+    if (fsum) atomicAdd(&stat_sh[0], fsum);
+    if (ssum) atomicAdd(&stat_sh[1], ssum);
+    if (fmx) atomicMax(&stat_sh[2], fmx);
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    if (stat_sh[0]) atomicAdd(&A.counters[CNT_CANDS], (unsigned long long)stat_sh[0]);
+    if (stat_sh[1]) atomicAdd(&A.counters[CNT_SOLVES], (unsigned long long)stat_sh[1]);
+    if (stat_sh[2] && (unsigned long long)stat_sh[2] > *(volatile unsigned long long*)&A.counters[CNT_MAXCAND])
+      atomicMax(&A.counters[CNT_MAXCAND], (unsigned long long)stat_sh[2]);
   }
 }
 
@@ -509,23 +509,53 @@ __device__ __forceinline__ void record_pair(const MatchArgs& M, int64_t k, int64
 }
 
 // Round 1: every particle's earliest candidate is its pick; mutual picks collide.
+// The pair list and the work list take their slots once per warp (the pair list is
+// read back sorted, the work list's order does not matter).
 __global__ void k_match_first(MatchArgs M) {
   const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (k >= M.n) return;
-  const int b = M.best[k];
-  if (b >= 0 && M.best[b] == (int)k) {
-    const double t = M.cand_t[k];
-    M.partner[k] = b;
+  const int lane = threadIdx.x & 31;
+  const unsigned below = (1u << lane) - 1u;
+  const bool in = k < M.n;
+  int b = -1;
+  bool mutual = false;
+  if (in) {
+    b = M.best[k];
+    mutual = b >= 0 && M.best[b] == (int)k;
+  }
+  double t = CUDART_INF;
+  bool rec = false;
+  if (mutual) {
+    t = M.cand_t[k];
+    rec = M.sid[k] < M.sid[b];
+  }
+  if (in) {
+    M.partner[k] = mutual ? b : -1;
     M.tcoll[k] = t;
-    record_pair(M, k, b, t);
-    if (M.sid[k] < M.sid[b]) atomicMax(&M.counters[CNT_ROUNDS], 1ull);
-  } else {
-    M.partner[k] = -1;
-    M.tcoll[k] = CUDART_INF;
-    if (b >= 0) {
-      const unsigned long long w = atomicAdd(&M.counters[CNT_WORK], 1ull);
-      M.work[w] = (int32_t)k;
+  }
+  const unsigned br = __ballot_sync(0xffffffffu, rec);
+  if (br) {
+    const int lead = __ffs(br) - 1;
+    unsigned long long base = 0;
+    if (lane == lead) {
+      base = atomicAdd(&M.counters[CNT_PAIRS], (unsigned long long)__popc(br));
+      if (*(volatile unsigned long long*)&M.counters[CNT_ROUNDS] == 0ull) atomicMax(&M.counters[CNT_ROUNDS], 1ull);
     }
+    base = __shfl_sync(0xffffffffu, base, lead);
+    if (rec) {
+      const unsigned long long q = base + __popc(br & below);
+      M.pair_lo[q] = M.sid[k];
+      M.pair_hi[q] = M.sid[b];
+      M.pair_t[q] = t;
+    }
+  }
+  const bool wk = in && !mutual && b >= 0;
+  const unsigned bw = __ballot_sync(0xffffffffu, wk);
+  if (bw) {
+    const int lead = __ffs(bw) - 1;
+    unsigned long long base = 0;
+    if (lane == lead) base = atomicAdd(&M.counters[CNT_WORK], (unsigned long long)__popc(bw));
+    base = __shfl_sync(0xffffffffu, base, lead);
+    if (wk) M.work[base + __popc(bw & below)] = (int32_t)k;
   }
 }
 

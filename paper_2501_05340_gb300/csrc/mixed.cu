@@ -109,15 +109,7 @@ __global__ void k_keys_f32(int64_t n, int nc, const int32_t* __restrict__ cell, 
       rr = ri;
     }
   }
-#pragma unroll
-  for (int s = 16; s > 0; s >>= 1) {
-    v2 = fmax(v2, __shfl_xor_sync(0xffffffffu, v2, s));
-    rr = fmax(rr, __shfl_xor_sync(0xffffffffu, rr, s));
-  }
-  if ((threadIdx.x & 31) == 0) {
-    atomicMax(&counters[CNT_VMAX2], (unsigned long long)__double_as_longlong(v2));
-    atomicMax(&counters[CNT_RMAX], (unsigned long long)__double_as_longlong(rr));
-  }
+  pc_block_max2(&counters[CNT_VMAX2], v2, &counters[CNT_RMAX], rr);
 }
 
 __global__ void k_gather_f32(int64_t n, const int32_t* __restrict__ perm, const int32_t* __restrict__ cell,
@@ -265,7 +257,9 @@ __global__ void __launch_bounds__(256, 3) k_search_f32(SearchF32 A) {
   __shared__ float vmaxc_sh, rmaxc_sh;
   __shared__ SearchQueueF32 queues[8];
   SearchQueueF32& Q = queues[warp];
+  __shared__ int stat_sh[3];  // candidates found, FP64 solves, largest list
   if (threadIdx.x == 0) {
+    stat_sh[0] = stat_sh[1] = stat_sh[2] = 0;
     const double L = (double)nc;
     const double v2max = __longlong_as_double((long long)A.counters[CNT_VMAX2]);
     const double rmax = __longlong_as_double((long long)A.counters[CNT_RMAX]);
@@ -459,6 +453,7 @@ __global__ void __launch_bounds__(256, 3) k_search_f32(SearchF32 A) {
     A.best[k] = cnt > 0 ? lj[0] : -1;
     if (found > A.cap) raise_status(A.counters, PC_ECAPACITY);
   }
+  // statistics: warp sums into shared counters, one global atomic per block
   int fsum = found, ssum = solves, fmx = found;
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) {
@@ -467,9 +462,16 @@ __global__ void __launch_bounds__(256, 3) k_search_f32(SearchF32 A) {
     fmx = max(fmx, __shfl_xor_sync(0xffffffffu, fmx, o));
   }
   if ((threadIdx.x & 31) == 0) {
-    if (fsum) atomicAdd(&A.counters[CNT_CANDS], (unsigned long long)fsum);
-    if (ssum) atomicAdd(&A.counters[CNT_SOLVES], (unsigned long long)ssum);
-    if (fmx) atomicMax(&A.counters[CNT_MAXCAND], (unsigned long long)fmx);
+    if (fsum) atomicAdd(&stat_sh[0], fsum);
+    if (ssum) atomicAdd(&stat_sh[1], ssum);
+    if (fmx) atomicMax(&stat_sh[2], fmx);
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    if (stat_sh[0]) atomicAdd(&A.counters[CNT_CANDS], (unsigned long long)stat_sh[0]);
+    if (stat_sh[1]) atomicAdd(&A.counters[CNT_SOLVES], (unsigned long long)stat_sh[1]);
+    if (stat_sh[2] && (unsigned long long)stat_sh[2] > *(volatile unsigned long long*)&A.counters[CNT_MAXCAND])
+      atomicMax(&A.counters[CNT_MAXCAND], (unsigned long long)stat_sh[2]);
   }
 }
 

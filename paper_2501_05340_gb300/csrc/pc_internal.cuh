@@ -169,3 +169,35 @@ pc_status pc_project_dirac_impl(pc_ctx* ctx, const pc_particles* p, double* fiel
   } while (0)
 
 static inline int pc_blocks(int64_t n, int threads) { return (int)((n + threads - 1) / threads); }
+
+#ifdef __CUDACC__
+// Maxima of two non-negative doubles over the block into two counters (their bit
+// patterns order like the values): one atomic per block and counter, skipped when the
+// counter already holds as much (a stale read only costs the atomic). Every thread of
+// the block calls it; every counter update of one address from all warps of a large
+// grid would serialise in the L2.
+__device__ __forceinline__ void pc_block_max2(unsigned long long* c0, double v0, unsigned long long* c1, double v1) {
+  __shared__ double red[2][32];
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    v0 = fmax(v0, __shfl_xor_sync(0xffffffffu, v0, o));
+    v1 = fmax(v1, __shfl_xor_sync(0xffffffffu, v1, o));
+  }
+  const int w = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
+  if ((threadIdx.x & 31) == 0) {
+    red[0][w] = v0;
+    red[1][w] = v1;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    for (int i = 1; i < nw; ++i) {
+      v0 = fmax(v0, red[0][i]);
+      v1 = fmax(v1, red[1][i]);
+    }
+    const unsigned long long b0 = (unsigned long long)__double_as_longlong(v0);
+    const unsigned long long b1 = (unsigned long long)__double_as_longlong(v1);
+    if (b0 > *(volatile unsigned long long*)c0) atomicMax(c0, b0);
+    if (b1 > *(volatile unsigned long long*)c1) atomicMax(c1, b1);
+  }
+}
+#endif
