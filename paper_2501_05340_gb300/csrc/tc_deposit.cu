@@ -18,10 +18,10 @@
 // groups 128 B apart and the particle octets one row-group column apart (2048 B for
 // A, 1024 B for B). So one lane per particle writes its own 16-byte pieces: no
 // factor tile is staged, and every store is a whole core-matrix row.
-// Each of 6 worker warps owns one 64-column accumulator in tensor memory and works on
+// Each of 8 worker warps owns one 64-column accumulator in tensor memory and works on
 // one element at a time: it compacts the particles that reach the element into a
 // ring (order kept), and per 32 of them every lane computes its particle's factors
-// in registers and writes the operands into one of the worker's two stages; lane 0
+// in registers and writes the operands into the worker's stage; lane 0
 // issues the two MMAs (K = 16 each) and a tcgen05.commit that arrives on the stage's
 // mbarrier when the tensor core has read it. After an element's last chunk the
 // worker queues (element, worker); 4 epilogue warps, one per TMEM lane quarter,
@@ -89,10 +89,11 @@ __device__ __forceinline__ int wrapi(int a, int n) {
 }
 
 constexpr int kChunk = 32;                          // particles per operand stage (two MMAs)
-constexpr int kWorkers = 6;                         // worker warps, one TMEM accumulator each
+constexpr int kWorkers = 8;                         // worker warps, one TMEM accumulator each (all 512 columns)
 constexpr int kEpiWarps = 4;                        // one per TMEM lane quarter
 constexpr int kThreads = 32 * (kWorkers + kEpiWarps);
-constexpr int kStages = 2;                          // operand stages per worker
+constexpr int kStages = 1;                          // operand stages per worker (a chunk's MMAs finish while
+                                                    // the worker compacts and builds the next)
 constexpr int kList = 64;                           // kept-particle ring (>= kChunk + 32)
 constexpr int kQ = 32;                              // finished-element queue (>= 2 kWorkers)
 constexpr int kMaxRanges = 125;                     // (2 rho + 1)^3 neighbour cells, rho <= 2
