@@ -664,6 +664,14 @@ __global__ void k_elem_keys_f32(int64_t n, int nc, int ne, f2 rnn, const int32_t
   slot[i] = atomicAdd(&cnt[k], 1);
 }
 
+// 2^x by the hardware approximation, the one the tensor-core deposit evaluates its
+// factors with, so that 1/Z normalises exactly those factors.
+__device__ __forceinline__ float ex2_approx(float x) {
+  float y;
+  asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+  return y;
+}
+
 struct PrepF32 {
   int64_t n;
   int nc, ne, n1, rho, win;
@@ -672,7 +680,7 @@ struct PrepF32 {
   float c2l;        // h^2 / (2 sigma^2) log2(e)
   double h, rc;
   float s[64];      // window node offsets o + (eta_i + 1)/2 in element units
-  float wq[16];     // Gauss weights
+  float wq[64];     // Gauss weight of each window node (w % n1)
   double eta[16];
   const int32_t* perm;
   const int32_t* cell;
@@ -716,7 +724,7 @@ __global__ void __launch_bounds__(128) k_proj_prep_f32(PrepF32 P) {
       }
       if (inside) {
         mk |= 1u << w;
-        Z += P.wq[w % P.n1] * exp2f(-(d * d) * P.c2l);
+        Z += P.wq[w] * ex2_approx(-(d * d) * P.c2l);
       }
     }
     t3[a] = t;
@@ -1229,10 +1237,8 @@ pc_status pc_project_f32_impl(pc_ctx* ctx, const pc_particles_f32* p, float* fie
     P.c2l = (float)(ctx->h * ctx->h / (2.0 * ctx->cfg.sigma * ctx->cfg.sigma) * 1.4426950408889634);
     for (int w = 0; w < ctx->win; ++w)
       P.s[w] = (float)((double)(w / ctx->n1 - ctx->rho) + 0.5 * (ctx->eta[w % ctx->n1] + 1.0));
-    for (int i = 0; i < ctx->n1; ++i) {
-      P.wq[i] = (float)ctx->w[i];
-      P.eta[i] = ctx->eta[i];
-    }
+    for (int w = 0; w < ctx->win; ++w) P.wq[w] = (float)ctx->w[w % ctx->n1];
+    for (int i = 0; i < ctx->n1; ++i) P.eta[i] = ctx->eta[i];
     P.perm = ctx->perm;
     P.cell = p->cell;
     P.o = p->o;
