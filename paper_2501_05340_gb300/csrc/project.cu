@@ -69,7 +69,8 @@ struct FactorArgs {
   f2 c2;               // h^2 / (2 sigma^2): exponent factor for distances in element units
   f2 scale;            // (2/h)^3
   f2 sw[kMaxWin];      // window node offsets o + (eta_i + 1)/2 (element units), o = w/n1 - rho
-  f2 wq[16];           // Gauss weights
+  f2 wq[kMaxWin];      // Gauss weight of window node w (node w % n1)
+  int wblk[kMaxWin];   // window element of node w (w / n1)
   double eta[16];      // Gauss nodes (for the exact FP64 cutoff decision)
   DfExpTable tab;
   const int32_t* perm;
@@ -100,14 +101,14 @@ struct FactorArgs {
 // re-decision near the cutoff).
 __device__ __forceinline__ f2 window_factor(const FactorArgs& F, f2 t, int ea, double xa, int w, const float* th,
                                             const float* tl) {
-  const int i = w % F.n1;
   const f2 dl = df_add(F.sw[w], df_neg(t));
   const float ad = fabsf(dl.h);
   bool inside;
   if (fabsf(ad - F.rce) > 1e-5f * F.rce) {
     inside = ad < F.rce;
   } else {
-    const int o = w / F.n1 - F.rho;
+    const int i = w % F.n1;
+    const int o = F.wblk[w] - F.rho;
     const int ge = wrapi(ea + o, F.ne);
     const double X = ((double)ge + 0.5 * (F.eta[i] + 1.0)) * F.h;
     inside = fabs(minimg(X - xa)) <= F.rc;
@@ -126,7 +127,7 @@ __device__ __forceinline__ f2 window_factor(const FactorArgs& F, f2 t, int ea, d
 // axis: one thread per particle, each axis' window held in registers, normalised
 // and written once in 16-byte pairs; reach bits and the maxima of the digit scales.
 template <int WIN>
-__global__ void __launch_bounds__(128) k_proj_records(FactorArgs F) {
+__global__ void __launch_bounds__(128, 4) k_proj_records(FactorArgs F) {
   __shared__ float th[64], tl[64];
   if (threadIdx.x < 64) {
     th[threadIdx.x] = F.tab.th[threadIdx.x];
@@ -150,7 +151,7 @@ __global__ void __launch_bounds__(128) k_proj_records(FactorArgs F) {
 #pragma unroll
       for (int w = 0; w < WIN; ++w) {
         f[w] = window_factor(F, t, ea, xa, w, th, tl);
-        if (f[w].h != 0.0f) Z = df_add(Z, df_mul(f[w], F.wq[w % F.n1]));
+        if (f[w].h != 0.0f) Z = df_add(Z, df_mul(f[w], F.wq[w]));
       }
       const f2 rz = df_recip(Z);
 #pragma unroll
@@ -158,7 +159,7 @@ __global__ void __launch_bounds__(128) k_proj_records(FactorArgs F) {
         if (f[w].h != 0.0f) {
           f[w] = df_mul(f[w], rz);
           fmax = fmaxf(fmax, fabsf(f[w].h));
-          reach |= 1 << (8 * a + w / F.n1);
+          reach |= 1 << (8 * a + F.wblk[w]);
         }
       }
       float2* dst = rk + a * WIN;
@@ -230,7 +231,7 @@ __global__ void __launch_bounds__(128) k_proj_factors(FactorArgs F) {
     f2 Z = {0.0f, 0.0f};
     for (int w = 0; w < F.win; ++w) {
       const f2 f = window_factor(F, t, ea, xa, w, th, tl);
-      if (f.h != 0.0f) Z = df_add(Z, df_mul(f, F.wq[w % F.n1]));
+      if (f.h != 0.0f) Z = df_add(Z, df_mul(f, F.wq[w]));
       F.fac[((int64_t)a * F.win + w) * n + k] = make_float2(f.h, f.l);
     }
     const f2 rz = df_recip(Z);
@@ -511,11 +512,11 @@ pc_status pc_project_impl(pc_ctx* ctx, const pc_particles* p, double* field) {
     for (int w = 0; w < ctx->win; ++w) {
       const double v = (double)(w / ctx->n1 - ctx->rho) + 0.5 * (ctx->eta[w % ctx->n1] + 1.0);
       F.sw[w] = {(float)v, (float)(v - (double)(float)v)};
+      const double wq = ctx->w[w % ctx->n1];
+      F.wq[w] = {(float)wq, (float)(wq - (double)(float)wq)};
+      F.wblk[w] = w / ctx->n1;
     }
-    for (int i = 0; i < ctx->n1; ++i) {
-      F.wq[i] = {(float)ctx->w[i], (float)(ctx->w[i] - (double)(float)ctx->w[i])};
-      F.eta[i] = ctx->eta[i];
-    }
+    for (int i = 0; i < ctx->n1; ++i) F.eta[i] = ctx->eta[i];
     F.tab = ctx->exp_tab;
     F.perm = ctx->perm;
     F.x = p->x;
