@@ -492,6 +492,8 @@ struct RespondF32 {
   int32_t* cell_out;
   float *o_out, *v_out, *r_out, *m_out, *q_out;
   int32_t* id_out;
+  int32_t* list;                    // [n]: sorted indices of the colliding particles
+  unsigned long long* counters;     // CNT_RESP counts them
 };
 
 // Free flight of one axis: o' = o + float(dt nc) v in FP32 with a carry into the
@@ -562,18 +564,17 @@ __device__ __forceinline__ void respond_pair_f32(int c[3], const int cj[3], cons
   }
 }
 
-// Free particles: advance_free_axis on each axis. Colliding pairs: respond_pair_f32
-// at the contact time found by the search, queued per block and computed by the
-// block's first threads together (its FP64 instructions would otherwise cost every
-// warp with a colliding lane the whole response).
+// Free particles: advance_free_axis on each axis. Colliding particles go to a list
+// (slots once per warp) and k_respond_pairs_f32 computes their FP64 responses with
+// every lane of a warp busy: on this GPU an FP64 instruction takes a warp 64 pipe
+// cycles whatever the number of active lanes, and a block's few colliding lanes
+// would otherwise hold it for the whole response.
 __global__ void __launch_bounds__(256) k_respond_f32(RespondF32 R) {
-  __shared__ int q_cnt;
-  __shared__ int q_k[256];
-  if (threadIdx.x == 0) q_cnt = 0;
-  __syncthreads();
   const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   const int64_t n = R.n;
   const int nc = R.nc;
+  const int lane = threadIdx.x & 31;
+  bool col = false;
   if (k < n) {
     const int64_t p = R.perm[k];
     const int32_t j = R.partner[k];
@@ -590,7 +591,7 @@ __global__ void __launch_bounds__(256) k_respond_f32(RespondF32 R) {
       }
       R.cell_out[k] = (c[2] * nc + c[1]) * nc + c[0];
     } else {
-      q_k[atomicAdd(&q_cnt, 1)] = threadIdx.x;
+      col = true;
     }
     R.r_out[k] = R.sr[k];
     R.m_out[k] = mi_f;
@@ -598,10 +599,24 @@ __global__ void __launch_bounds__(256) k_respond_f32(RespondF32 R) {
     if (R.q_out)
       for (int q = 0; q < 4; ++q) R.q_out[q * n + k] = R.q_in[q * n + p];
   }
-  __syncthreads();
-  const int nq = q_cnt;
-  for (int e = threadIdx.x; e < nq; e += blockDim.x) {
-    const int64_t kk = (int64_t)blockIdx.x * blockDim.x + q_k[e];
+  const unsigned bc = __ballot_sync(0xffffffffu, col);
+  if (bc) {
+    const int lead = __ffs(bc) - 1;
+    unsigned long long base = 0;
+    if (lane == lead) base = atomicAdd(&R.counters[CNT_RESP], (unsigned long long)__popc(bc));
+    base = __shfl_sync(0xffffffffu, base, lead);
+    if (col) R.list[base + __popc(bc & ((1u << lane) - 1u))] = (int32_t)k;
+  }
+}
+
+// Responses of the listed colliding particles (respond_pair_f32 from each particle's
+// own side), grid-stride over the list.
+__global__ void __launch_bounds__(256) k_respond_pairs_f32(RespondF32 R) {
+  const int64_t cnt = (int64_t)R.counters[CNT_RESP];
+  const int64_t n = R.n;
+  const int nc = R.nc;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < cnt; i += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t kk = R.list[i];
     const int32_t j = R.partner[kk];
     int c[3], cj[3];
     cell_coords(R.scell[kk], nc, c);
@@ -1188,9 +1203,13 @@ pc_status pc_collide_f32_impl(pc_ctx* ctx, const pc_particles_f32* in, pc_partic
     R.m_out = out->m;
     R.q_out = in->q ? out->q : nullptr;
     R.id_out = out->id;
+    R.list = ctx->work;  // the matching's work list is spent by now
+    R.counters = ctx->counters;
     const int tr = pc_phase_begin(ctx, PC_PH_RESPOND);
     k_respond_f32<<<pc_blocks(n, 256), 256, 0, st>>>(R);
-    ctx->launches += 1;
+    const int gp = pc_blocks(n, 256) < 4096 ? pc_blocks(n, 256) : 4096;
+    k_respond_pairs_f32<<<gp, 256, 0, st>>>(R);
+    ctx->launches += 2;
     pc_phase_end(ctx, tr);
   }
   e = cudaGetLastError();

@@ -21,6 +21,7 @@ enum {
   CNT_VMAX2,   // max |v|^2 as the bits of a non-negative double
   CNT_RMAX,    // max r as the bits of a non-negative double
   CNT_ELEM,    // next element of the mixed deposit (zeroed before each launch)
+  CNT_RESP,    // colliding particles listed by the FP32 response
   CNT_N
 };
 
