@@ -370,6 +370,11 @@ __global__ void __launch_bounds__(256, 3) k_search(SearchArgs A) {
   const int span = 2 * s + 1;
   const bool full = span >= nc;  // the stencil covers the whole axis: visit every cell once
   const int cnt_ax = full ? nc : span;
+  // per-axis bases of the candidate arrays and a 32-bit own index for the inner loop
+  const float* __restrict__ sx0 = A.sxf;
+  const float* __restrict__ sx1 = A.sxf + n;
+  const float* __restrict__ sx2 = A.sxf + 2 * n;
+  const int k32 = live ? (int)k : -1;
   for (int oz = 0; oz < cnt_ax; ++oz) {
     for (int oy = 0; oy < cnt_ax; ++oy) {
       int b1 = 0, e1 = 0, b2 = 0, e2 = 0;
@@ -402,10 +407,10 @@ __global__ void __launch_bounds__(256, 3) k_search(SearchArgs A) {
         const int j = t < l1 ? b1 + t : b2 + (t - l1);
         bool pass = false;
         float dx = 0.0f, dy = 0.0f, dz = 0.0f;
-        if (t < len && j != k) {
-          dx = minimgf(xf[0] - A.sxf[j]);
-          dy = minimgf(xf[1] - A.sxf[n + j]);
-          dz = minimgf(xf[2] - A.sxf[2 * n + j]);
+        if (t < len && j != k32) {
+          dx = minimgf(xf[0] - sx0[j]);
+          dy = minimgf(xf[1] - sx1[j]);
+          dz = minimgf(xf[2] - sx2[j]);
           pass = !(dx * dx + dy * dy + dz * dz > rl2);
         }
         const unsigned bal = __ballot_sync(kFull, pass);

@@ -348,6 +348,12 @@ __global__ void __launch_bounds__(256, 3) k_search_f32(SearchF32 A) {
   const int cnt_ax = full ? nc : span;
   // offsets below s + 1 <= nc / 2 are their own minimum image
   const bool need_box = 2 * (s + 1) > nc;
+  // per-axis bases of the candidate arrays and a 32-bit own index for the inner loop
+  const int32_t* __restrict__ scell_p = A.scell;
+  const float* __restrict__ so0 = A.so;
+  const float* __restrict__ so1 = A.so + n;
+  const float* __restrict__ so2 = A.so + 2 * n;
+  const int k32 = live ? (int)k : -1;
   for (int oz = 0; oz < cnt_ax; ++oz) {
     for (int oy = 0; oy < cnt_ax; ++oy) {
       int b1 = 0, e1 = 0, b2 = 0, e2 = 0, rowck = 0;
@@ -389,13 +395,13 @@ __global__ void __launch_bounds__(256, 3) k_search_f32(SearchF32 A) {
         const int j = t < l1 ? b1 + t : b2 + (t - l1);
         bool pass = false;
         float dx = 0.0f, dy = 0.0f, dz = 0.0f;
-        if (t < len && j != k) {
-          int di = rowck - A.scell[j];
+        if (t < len && j != k32) {
+          int di = rowck - scell_p[j];
           if (2 * di > nc) di -= nc;
           else if (2 * di < -nc) di += nc;
-          dx = (float)di + (ok3[0] - A.so[j]);
-          dy = dyf + (ok3[1] - A.so[n + j]);
-          dz = dzf + (ok3[2] - A.so[2 * n + j]);
+          dx = (float)di + (ok3[0] - so0[j]);
+          dy = dyf + (ok3[1] - so1[j]);
+          dz = dzf + (ok3[2] - so2[j]);
           if (need_box) {
             dx = minimgf_box(dx, Lf);
             dy = minimgf_box(dy, Lf);
