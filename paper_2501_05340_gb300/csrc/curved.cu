@@ -270,10 +270,12 @@ __global__ void __launch_bounds__(128) k_curved_prep(CPrepArgs A) {
         const float lx = S[wx] - cw[0];
         const int gx = g0[0] + wx;
         const float2 tx = A.trig[gx];
+        // this unit is compiled without implicit contraction (double-float helpers); the
+        // FP32 arithmetic of the node pairs places its multiply-adds explicitly
         const float dx = (lx + dl[0]) + pxr;
-        const float dy = dy0 + az * tx.x;
-        const float dz = dz0 + ay * tx.x;
-        const float r2 = dx * dx + dy * dy + dz * dz;
+        const float dy = fmaf(az, tx.x, dy0);
+        const float dz = fmaf(ay, tx.x, dz0);
+        const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
         if (r2 > cut_hi) continue;
         if (r2 >= A.rc2f * 0.9998f) {
           const int gg[3] = {gx, gy, gz};
@@ -284,9 +286,9 @@ __global__ void __launch_bounds__(128) k_curved_prep(CPrepArgs A) {
         }
         const float a10 = gsz * tx.y, a12 = gcz * tx.x;
         const float a20 = gsy * tx.y, a21 = gcy * tx.x;
-        const float det = 1.0f * (1.0f - a12 * a21) - a01 * (a10 - a12 * a20) + a02 * (a10 * a21 - a20);
+        const float det = fmaf(a02, fmaf(a10, a21, -a20), fmaf(-a01, fmaf(-a12, a20, a10), fmaf(-a12, a21, 1.0f)));
         const float W = WQ[wx] * wyz * det;
-        Z += W * ex2f(-r2 * A.c2l);
+        Z = fmaf(W, ex2f(-r2 * A.c2l), Z);
       }
     }
   }
@@ -451,7 +453,8 @@ __global__ void __launch_bounds__(64, 12) k_curved_deposit(CDepArgs A) {
       const int q = clist[u];
       const float4 s0 = st[2 * q];
       const float d0 = X[0] - s0.x, d1 = X[1] - s0.y, d2 = X[2] - s0.z;
-      const float r2s = d0 * d0 + d1 * d1 + d2 * d2;
+      // explicit multiply-adds: the unit is compiled without implicit contraction
+      const float r2s = fmaf(d0, d0, fmaf(d1, d1, d2 * d2));
       if (r2s > cut_hi) continue;
       if (r2s >= cut_lo) {
         const int64_t pj = A.perm[keep[q] - 1];
@@ -465,10 +468,10 @@ __global__ void __launch_bounds__(64, 12) k_curved_deposit(CDepArgs A) {
       }
       const float4 s1 = st[2 * q + 1];
       const float K = ex2f(-r2s * A.c2l) * s0.w;
-      acc[0] += s1.x * K;
-      acc[1] += s1.y * K;
-      acc[2] += s1.z * K;
-      acc[3] += s1.w * K;
+      acc[0] = fmaf(s1.x, K, acc[0]);
+      acc[1] = fmaf(s1.y, K, acc[1]);
+      acc[2] = fmaf(s1.z, K, acc[2]);
+      acc[3] = fmaf(s1.w, K, acc[3]);
     }
     __syncthreads();
   }
