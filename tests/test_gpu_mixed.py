@@ -252,6 +252,42 @@ def test_project_f32_reduced_mesh(tc, tol):
     assert np.all(err <= tol), err
 
 
+@pytest.mark.parametrize("degree", range(8))
+@pytest.mark.parametrize("tc,tol", [("f16", F16_TOL), ("bf16", BF16_TOL)])
+def test_project_f32_every_degree(degree, tc, tol):
+    """Every compiled degree of the tensor-core deposit (n1 = 1..8) on a 6^3 mesh with
+    3 sigma = 0.9 h and about 14 particles per element (several 32-particle chunks per
+    element, the last one partial), against the FP64 oracle."""
+    n, ne, sigma = 3000, 6, 0.05
+    w = inputs.draw("mixed_16m", seed=10 + degree, n=n)
+    ctx = pc.Context(n, ne, degree, sigma, w["e"], pc.reach_of(w["r"], w["v"], w["dt"]))
+    s32 = mixed_state(w, ctx)
+    f = ctx.new_field_f32()
+    ctx.project_f32(s32, f, tc)
+    ctx.sync()
+    g = s32.numpy()
+    x = oracle.dequantize(g["cell"], g["o"], ctx.cells_per_side)
+    R, _ = oracle.project(x, g["q"].astype(np.float64), ne, degree, sigma, 3.0)
+    err = field_err(f.cpu().numpy().astype(np.float64), R)
+    assert np.all(err <= tol), (degree, tc, err)
+
+
+def test_project_f32_crowded_elements():
+    """About 470 particles per element of a 4^3 mesh (degree 2): elements of many full
+    chunks plus a partial one, and more kept particles than the worker's ring holds."""
+    n, ne, degree, sigma = 30000, 4, 2, 0.06
+    w = inputs.draw("mixed_16m", seed=21, n=n)
+    ctx = pc.Context(n, ne, degree, sigma, w["e"], pc.reach_of(w["r"], w["v"], w["dt"]))
+    s32 = mixed_state(w, ctx)
+    f = ctx.new_field_f32()
+    ctx.project_f32(s32, f, "f16")
+    ctx.sync()
+    g = s32.numpy()
+    x = oracle.dequantize(g["cell"], g["o"], ctx.cells_per_side)
+    R, _ = oracle.project(x, g["q"].astype(np.float64), ne, degree, sigma, 3.0)
+    assert np.all(field_err(f.cpu().numpy().astype(np.float64), R) <= F16_TOL)
+
+
 @pytest.mark.parametrize("n", [1, 17, 300])
 def test_project_f32_small_counts(n):
     w = inputs.draw("small_8192", seed=3, n=n)
