@@ -639,6 +639,8 @@ struct RespondArgs {
   double mu;
   const double* w_in;
   double* w_out;
+  int32_t* list;                  // [n]: sorted indices of the colliding particles (k_respond)
+  unsigned long long* counters;   // CNT_RESP counts them
 };
 
 // Frictionless hard-sphere response (Sec. 2.4) from the particle's own side:
@@ -674,18 +676,15 @@ __device__ __forceinline__ void pair_response(const RespondArgs& R, int64_t k, i
   }
 }
 
-// One thread per particle for free flight and the copies; the block's colliding
-// particles are queued and their responses computed by the block's first threads
-// together: on this GPU an FP64 instruction takes a warp the same pipe time whatever
-// the number of active lanes, so the few colliding lanes of every warp would
-// otherwise cost each warp the whole FP64 response.
+// Free particles fly; colliding particles go to a list (slots once per warp) and
+// k_respond_pairs computes their responses with every lane of a warp busy (an FP64
+// instruction takes a warp 64 pipe cycles on this GPU whatever the number of
+// active lanes). The response of each particle is computed from its own side.
 __global__ void __launch_bounds__(256) k_respond(RespondArgs R) {
-  __shared__ int q_cnt;
-  __shared__ int q_k[256];
-  if (threadIdx.x == 0) q_cnt = 0;
-  __syncthreads();
   const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   const int64_t n = R.n;
+  const int lane = threadIdx.x & 31;
+  bool col = false;
   if (k < n) {
     const int64_t p = R.perm[k];
     const int32_t j = R.partner[k];
@@ -698,7 +697,7 @@ __global__ void __launch_bounds__(256) k_respond(RespondArgs R) {
         R.v_out[a * n + k] = vi;
       }
     } else {
-      q_k[atomicAdd(&q_cnt, 1)] = threadIdx.x;
+      col = true;
     }
     R.r_out[k] = R.sr[k];
     R.m_out[k] = mi;
@@ -708,10 +707,22 @@ __global__ void __launch_bounds__(256) k_respond(RespondArgs R) {
       for (int c = 0; c < 4; ++c) R.q_out[c * n + k] = R.q_in[c * n + p];
     }
   }
-  __syncthreads();
-  const int nq = q_cnt;
-  for (int e = threadIdx.x; e < nq; e += blockDim.x) {
-    const int64_t kk = (int64_t)blockIdx.x * blockDim.x + q_k[e];
+  const unsigned bc = __ballot_sync(0xffffffffu, col);
+  if (bc) {
+    const int lead = __ffs(bc) - 1;
+    unsigned long long base = 0;
+    if (lane == lead) base = atomicAdd(&R.counters[CNT_RESP], (unsigned long long)__popc(bc));
+    base = __shfl_sync(0xffffffffu, base, lead);
+    if (col) R.list[base + __popc(bc & ((1u << lane) - 1u))] = (int32_t)k;
+  }
+}
+
+// Responses of the listed colliding particles, grid-stride over the list.
+__global__ void __launch_bounds__(256) k_respond_pairs(RespondArgs R) {
+  const int64_t cnt = (int64_t)R.counters[CNT_RESP];
+  const int64_t n = R.n;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < cnt; i += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t kk = R.list[i];
     double xo[3], vo[3];
     pair_response(R, kk, R.partner[kk], R.m_in[R.perm[kk]], xo, vo);
 #pragma unroll
@@ -946,12 +957,18 @@ pc_status pc_collide_impl(pc_ctx* ctx, const pc_particles* in, pc_particles* out
     R.mu = mu;
     R.w_in = w_in;
     R.w_out = w_out;
+    R.list = ctx->work;  // the matching's work list is spent by now
+    R.counters = ctx->counters;
     const int tr = pc_phase_begin(ctx, PC_PH_RESPOND);
-    if (w_in)
+    if (w_in) {
       k_respond_rot<<<pc_blocks(n, 256), 256, 0, st>>>(R);
-    else
+      ctx->launches += 1;
+    } else {
       k_respond<<<pc_blocks(n, 256), 256, 0, st>>>(R);
-    ctx->launches += 1;
+      const int gp = pc_blocks(n, 256) < 4096 ? pc_blocks(n, 256) : 4096;
+      k_respond_pairs<<<gp, 256, 0, st>>>(R);
+      ctx->launches += 2;
+    }
     pc_phase_end(ctx, tr);
   }
   e = cudaGetLastError();
