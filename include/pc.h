@@ -269,8 +269,11 @@ pc_status pc_quantize(pc_ctx* ctx, const pc_particles* in, pc_particles_f32* out
  * rejects pairs before the FP64 solve. Colliding pairs: FP64 response (as
  * pc_collide, positions in cell units), new position stored as cell + FP32
  * offset, velocity rounded to FP32. Free particles: o' = o + float(dt nc) v in
- * FP32 with a carry into the neighbouring cell. Bit-identical to a plain
- * implementation of these rules. */
+ * FP32 with a carry into the neighbouring cell, so a step needs |v_a| dt nc < 1 on
+ * every axis (the cells' side >= reach_hint >= 2 v_max dt gives it whenever the hint
+ * bounds the step's reach; a larger move leaves an offset outside [0, 1), which the
+ * next step reports as PC_EINVAL). Bit-identical to a plain implementation of these
+ * rules. */
 pc_status pc_collide_f32(pc_ctx* ctx, const pc_particles_f32* in, pc_particles_f32* out, double dt);
 
 /* One mixed step with a given pair set (partner[p] = index of p's partner in the

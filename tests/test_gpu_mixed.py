@@ -135,6 +135,36 @@ def test_collide_f32_reach_spanning_the_box(target_reach):
         assert np.array_equal(g[key], ref), key
 
 
+def test_collide_f32_reach_above_the_hint():
+    """Mixed path, actual reach 0.076 under a hint of 0.04: 24 cells per side and a stencil
+    of 2 cells on each side (5 of 24 per axis) whose rows wrap at the faces; the largest
+    move, 0.03, stays within a cell (1/24); pairs, times, cells, offsets and velocities
+    bit-identical."""
+    rng = np.random.default_rng(12)
+    n = 3000
+    w = dict(x=rng.random((3, n)), v=rng.normal(size=(3, n)), r=np.full(n, 0.008), m=rng.uniform(0.5, 2.0, n),
+             id=np.arange(n, dtype=np.int32), q=rng.normal(size=(4, n)))
+    vmax = float(np.sqrt((w["v"] ** 2).sum(0)).max())
+    dt = (0.076 - 0.016) / (2 * vmax)
+    ctx = pc.Context(n, 8, 3, 0.02, 0.9, 0.04)
+    assert ctx.cells_per_side == 24
+    a = mixed_state(w, ctx)
+    b = pc.StateF32.empty(n)
+    cur = by_id(a.numpy())
+    ctx.collide_f32(a, b, dt)
+    ctx.sync()
+    st = ctx.stats()
+    assert st["status"] == 0 and st["stencil"] == 2
+    gids, gt = ctx.pairs()
+    cell, o, v, partner, tc, k = oracle.collide_step_cellrel(cur["cell"], cur["o"], cur["v"], cur["r"], cur["m"],
+                                                             cur["id"], 24, 0.9, dt)
+    oids, ot = oracle_pairs(partner, tc, cur["id"])
+    assert k > 5 and np.array_equal(gids, oids) and np.array_equal(gt, ot)
+    g = by_id(b.numpy())
+    for key, ref in (("cell", cell), ("o", o), ("v", v)):
+        assert np.array_equal(g[key], ref), key
+
+
 def test_collide_f32_reach_of_half_the_box_is_refused():
     """A mixed step whose actual reach is 0.8 box lengths under a hint of 0.3: refused on
     the GPU (PC_EINVAL from pc_sync), as the FP64 path refuses it."""

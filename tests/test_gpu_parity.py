@@ -228,6 +228,24 @@ def test_reach_spanning_the_box(target_reach):
     assert k > 5
 
 
+def test_reach_above_the_hint():
+    """A step whose actual reach (0.1) is 2.5 times the hint (0.04): 24 cells per side and a
+    stencil of 3 cells on each side (7 of 24 per axis), whose rows wrap at the faces; pairs,
+    times, x and v bit-identical to the oracle."""
+    rng = np.random.default_rng(11)
+    n = 3000
+    d = dict(x=rng.random((3, n)), v=rng.normal(size=(3, n)), r=np.full(n, 0.008), m=rng.uniform(0.5, 2.0, n),
+             id=np.arange(n, dtype=np.int32), q=rng.normal(size=(4, n)))
+    vmax = float(np.sqrt((d["v"] ** 2).sum(0)).max())
+    dt = (0.1 - 0.016) / (2 * vmax)
+    a, b = pc.State.from_arrays(d), pc.State.empty(n)
+    ctx = pc.Context(n, 8, 3, 0.02, 0.9, 0.04)
+    assert ctx.cells_per_side == 24
+    _, k = compare_collide_step(ctx, a, b, by_id(dict(d)), dt, 0.9)
+    st = ctx.stats()
+    assert k > 5 and st["status"] == 0 and st["stencil"] == 3
+
+
 def test_reach_of_half_the_box_is_refused():
     """A reach of half the box or more: pc_init refuses such a hint on the host, and a step
     whose actual reach reaches 0.5 under a smaller hint is refused on the GPU (PC_EINVAL
