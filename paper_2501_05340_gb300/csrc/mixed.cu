@@ -104,8 +104,12 @@ __global__ void k_keys_f32(int64_t n, int nc, const int32_t* __restrict__ cell, 
     key[i] = k;
     slot[i] = atomicAdd(&cnt[k], 1);
     if (ok) {
-      const double v0 = v[i], v1 = v[n + i], vz = v[2 * n + i];
-      v2 = (v0 * v0 + v1 * v1) + vz * vz;
+      // |v|^2 in FP32, rounded up: three roundings (below 2.4e-7 relative) under the
+      // factor's 1e-6, so an upper bound of the stored velocity's exact value, which is
+      // all the search's reach and filter bounds need (FP64 here would cost a warp 64
+      // pipe cycles per instruction on this GPU)
+      const float v0 = v[i], v1 = v[n + i], vz = v[2 * n + i];
+      v2 = (double)(fmaf(v0, v0, fmaf(v1, v1, vz * vz)) * 1.000001f);
       rr = ri;
     }
   }
