@@ -303,7 +303,8 @@ def deposit_roofline(x, wl, n, dep_ms, step_ms):
             "step": {"algorithmic_bytes": step_algo, "achieved": step_gbs, "frac": step_gbs / peak,
                      "algorithmic": "144 B per particle (read x, v, r, m, q; write x, v) + the field"},
             "alu": {"bound_by": "digit operands of the FP64-accurate tensor-core contraction, built on the CUDA "
-                                "cores (54 % issue, no pipe saturated: profiles/k_fx_deposit_dense_1m.md)",
+                                "cores, and the shared-memory pipe (ALU 48 %, FMA 41 %, LSU wavefronts 73 %, tensor "
+                                "17 %: profiles/k_fx_deposit_dense_1m.md)",
                     "method_flop": 8.0 * support,
                     "method_flop_per_unit": "8 per (particle, Gauss node inside its box support)",
                     "achieved_fp64_equivalent_tflops": 8.0 * support / sec / 1e12,
