@@ -126,8 +126,9 @@ __device__ __forceinline__ f2 window_factor(const FactorArgs& F, f2 t, int ea, d
 // Record layout for the tensor-core deposit, WIN = (2 rho + 1) n1 window nodes per
 // axis: one thread per particle, each axis' window held in registers, normalised
 // and written once in 16-byte pairs; reach bits and the maxima of the digit scales.
+constexpr int kRecThreads = 128;
 template <int WIN>
-__global__ void __launch_bounds__(128, 4) k_proj_records(FactorArgs F) {
+__global__ void __launch_bounds__(kRecThreads, 4) k_proj_records(FactorArgs F) {
   __shared__ float th[64], tl[64];
   if (threadIdx.x < 64) {
     th[threadIdx.x] = F.tab.th[threadIdx.x];
@@ -188,22 +189,33 @@ __global__ void __launch_bounds__(128, 4) k_proj_records(FactorArgs F) {
     }
     F.reach[k] = reach;
   }
-  // warp reduction of the float bits, one atomic per warp
+  // maxima of the float bits over the block, then one atomic per block and counter,
+  // skipped when the counter already holds as much (a stale read only costs the
+  // atomic): atomics of every warp on the same five words would serialise in the L2
+  __shared__ unsigned red[5][kRecThreads / 32];
+  const int wid = threadIdx.x >> 5;
   unsigned v = __reduce_max_sync(0xffffffffu, __float_as_uint(fmax));
-  if ((threadIdx.x & 31) == 0) atomicMax(&F.fxmax[0], v);
+  if ((threadIdx.x & 31) == 0) red[0][wid] = v;
 #pragma unroll
   for (int c = 0; c < 4; ++c) {
     v = __reduce_max_sync(0xffffffffu, __float_as_uint(qmax[c]));
-    if ((threadIdx.x & 31) == 0) atomicMax(&F.fxmax[1 + c], v);
+    if ((threadIdx.x & 31) == 0) red[1 + c][wid] = v;
+  }
+  __syncthreads();
+  if (threadIdx.x < 5) {
+    unsigned m = red[threadIdx.x][0];
+#pragma unroll
+    for (int i = 1; i < kRecThreads / 32; ++i) m = max(m, red[threadIdx.x][i]);
+    if (m > *(volatile unsigned*)&F.fxmax[threadIdx.x]) atomicMax(&F.fxmax[threadIdx.x], m);
   }
 }
 
 cudaError_t launch_records(int win, const FactorArgs& F, cudaStream_t st) {
-  const int nb = pc_blocks(F.n, 128);
+  const int nb = pc_blocks(F.n, kRecThreads);
   switch (win) {
 #define PC_REC_CASE(W) \
   case W:              \
-    k_proj_records<W><<<nb, 128, 0, st>>>(F); \
+    k_proj_records<W><<<nb, kRecThreads, 0, st>>>(F); \
     return cudaGetLastError();
     PC_REC_CASE(3) PC_REC_CASE(5) PC_REC_CASE(6) PC_REC_CASE(9) PC_REC_CASE(10) PC_REC_CASE(12) PC_REC_CASE(15)
     PC_REC_CASE(18) PC_REC_CASE(20) PC_REC_CASE(21) PC_REC_CASE(24) PC_REC_CASE(25) PC_REC_CASE(30) PC_REC_CASE(35)
