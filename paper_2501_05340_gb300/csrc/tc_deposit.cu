@@ -182,8 +182,8 @@ __device__ bool mbar_wait(unsigned long long* bar, uint32_t parity, const int* f
   }
 }
 
-// As mbar_wait, for waits that may legitimately last as long as a scanner needs to
-// get through a crowded neighbourhood: fails only after kWaitNs in which no scanner
+// As mbar_wait, for waits that may legitimately last as long as a worker needs to
+// get through a crowded neighbourhood: fails only after kWaitNs in which no worker
 // reported progress.
 __device__ bool mbar_wait_progress(TcSmem& S, unsigned long long* bar, uint32_t parity) {
   if (mbar_try(bar, parity)) return true;
