@@ -319,7 +319,8 @@ pc_status pc_project_f32(pc_ctx* ctx, const pc_particles_f32* p, float* field, i
  * Z_p = sum_g W_g K(X_g - x_p), W_g = w_i w_j w_k (h/2)^3 det DPhi(xi_g). Particles are
  * located in logical space by Newton's method on Phi(xi) = x (Sec. 3.2,
  * localisation). FP32 factors and accumulation; distances from double-float
- * positions; cutoff decisions within 1e-4 relative of the cutoff made in FP64.
+ * positions; cutoff decisions with the squared distance within 2e-4 relative of the
+ * squared cutoff made in FP64.
  * field: device FP32 [ne^3][4][(N+1)^3], overwritten. Deterministic (gather per
  * element). Requires cfg.amp > 0 or = 0, 2 pi sqrt(3) amp < 0.5. */
 pc_status pc_project_curved_f32(pc_ctx* ctx, const pc_particles_f32* p, float* field);
