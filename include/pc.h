@@ -309,7 +309,13 @@ pc_status pc_project_adjoint_f32(pc_ctx* ctx, const pc_particles_f32* p, const f
  * memory). Kernel factors in FP32; cutoff decisions near the cutoff are made in
  * FP64 on the stored position, as in pc_project. field: device FP32
  * [ne^3][4][(N+1)^3], overwritten. Requires N + 1 <= 8 and (2 rho + 1)(N + 1) <= 32,
- * rho = ceil(cutoff_sigmas sigma ne). */
+ * rho = ceil(cutoff_sigmas sigma ne).
+ * Operand range (PC_TC_F16): the split operands are q_c k_x 2^4 / Z_x and
+ * k_y k_z 2^8 / (Z_y Z_z), k <= 1, Z_a about 2 sqrt(2 pi) sigma ne. They overflow FP16
+ * (65504) for |q| above about 4000 Z_x, and below 2^-3 the low half of the split is
+ * subnormal, so the split's error becomes 2^-25 absolute (1e-5 relative near 3e-3).
+ * Sources of order one sit far from both ends; scale others by a power of two (exact,
+ * undone on the field) or use PC_TC_BF16, which has the exponent range of FP32. */
 pc_status pc_project_f32(pc_ctx* ctx, const pc_particles_f32* p, float* field, int32_t tc_type);
 
 /* Projection on the curved periodic mesh x = Phi(xi) = xi + amp (sin 2pi xi_y sin 2pi xi_z,
